@@ -1,0 +1,221 @@
+/*
+ * rf.h -- C ABI of the GB300 (sm_103a) Richards-equation solver.
+ *
+ * The library solves the 3-D transient Richards equation in pressure-head
+ * form (Orgogozo et al., arXiv:1809.10895, Eq. 1; z upward, h in m) with van
+ * Genuchten / Mualem closures (Eq. 2-4) on a structured grid of equal cells,
+ * by the scheme of Sec. 2.2: backward Euler in time, classical Picard
+ * linearisation with a chord-slope capacity, implicit pressure Laplacian with
+ * linearly interpolated face conductivity, explicit gravity lagged one Picard
+ * iterate, a preconditioned conjugate-gradient linear solve, a global
+ * max|dh| Picard exit test (Sec. 2.3) and EBATS adaptive time stepping.
+ *
+ * Conventions
+ *   - SI units.  h: pressure head [m]; fluxes [m/s]; times [s].
+ *   - Cells are indexed p = i + nx*(j + ny*k), x fastest, z slowest; cell
+ *     (i,j,k) has its centre at z_bottom + (k + 1/2) dz.
+ *   - Host arrays passed in are borrowed for the duration of the call and
+ *     copied; device arrays ("d_" arguments) are CUDA device pointers on the
+ *     context's device and must hold the stated number of elements.
+ *   - Every call returns rf_status.  No exception crosses the ABI.  On an
+ *     error the context state is unchanged (a step is all-or-nothing) and
+ *     rf_last_error() returns a message for the calling thread.
+ *   - There is no CPU fallback: without an sm_103 GPU, rf_mesh_create returns
+ *     RF_ERR_NO_DEVICE.
+ *   - A context is used by one host thread at a time; its work is ordered on
+ *     the CUDA stream given at creation.
+ */
+#ifndef RF_H
+#define RF_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct rf_ctx rf_ctx;
+
+typedef enum rf_status {
+    RF_OK = 0,
+    RF_ERR_ARG = 1,            /* invalid argument                                  */
+    RF_ERR_NO_DEVICE = 2,      /* no sm_103 GPU visible: there is no CPU fallback    */
+    RF_ERR_CUDA = 3,           /* a CUDA runtime call failed                         */
+    RF_ERR_NOMEM = 4,          /* device allocation failed                           */
+    RF_ERR_STATE = 5,          /* call order (e.g. rf_step before rf_state_set)      */
+    RF_ERR_PICARD = 6,         /* Picard did not converge (internal; EBATS reruns)   */
+    RF_ERR_DT_MIN = 7,         /* EBATS shrank dt below dt_min without convergence   */
+    RF_ERR_CG = 8,             /* CG non-finite / max_it where it is fatal            */
+    RF_ERR_DEVICE_TIMEOUT = 9  /* a bounded device loop exhausted its budget          */
+} rf_status;
+
+/* Soil models: van Genuchten / Mualem (Eq. 2-4) and Gardner (Eq. A6, test). */
+typedef enum rf_soil_model { RF_VG = 0, RF_GARDNER = 1 } rf_soil_model;
+
+/* Boundary conditions.  RF_BC_FLUX: imposed total Darcy flux, m/s, positive
+ * into the domain (the time-varying Neumann condition of Sec. 3.2).
+ * RF_BC_FREE_DRAINAGE: unit hydraulic gradient (zero pressure gradient),
+ * bottom face only.  RF_BC_SEEPAGE: Dirichlet h = 0 while the adjacent cell is
+ * saturated at the start of the step, zero flux otherwise. */
+typedef enum rf_bc_type {
+    RF_BC_ZERO_FLUX = 0, RF_BC_DIRICHLET = 1, RF_BC_FLUX = 2,
+    RF_BC_FREE_DRAINAGE = 3, RF_BC_SEEPAGE = 4
+} rf_bc_type;
+
+/* Face classes.  RF_ZMAX is the top face of the topmost active cell of each
+ * column (the land surface of a masked grid); RF_ZMIN the bottom face of the
+ * lowest active cell.  Lateral faces touching an inactive cell are zero-flux. */
+typedef enum rf_face { RF_XMIN = 0, RF_XMAX, RF_YMIN, RF_YMAX, RF_ZMIN, RF_ZMAX } rf_face;
+
+typedef enum rf_precision {
+    RF_PREC_FP64 = 0,   /* plain: FP64 PCG                                         */
+    RF_PREC_MIXED = 1   /* FP32 inner PCG inside FP64 defect correction; Picard test,
+                           closures, outer residual and mass balance stay FP64     */
+} rf_precision;
+
+typedef enum rf_precond { RF_PRECOND_JACOBI = 0, RF_PRECOND_MG = 1 } rf_precond;
+
+/* Solver parameters (Sec. 2.2 leaves their values to the user).
+ *   tol_picard  Picard exit test: max over active cells |h^{k+1} - h^k| <= tol [m]
+ *   tol_cg      PCG stop: ||b - A x||_2 <= tol_cg ||b||_2
+ *   cg_max_it   PCG iteration cap (hitting it rejects the step)
+ *   dt0, dt_max, dt_min  EBATS initial / maximum / minimum step [s]
+ *   f_grow, f_shrink     EBATS factors; n_inc consecutive accepted steps with
+ *                        <= n_small Picard iterations grow dt; more than n_max
+ *                        Picard iterations (or any failure) reject the step
+ *   eps_chord   chord slope is replaced by dtheta/dh when |h^k - h^n| <= eps
+ *   tol_inner, inner_max_it, outer_max_it   mixed precision inner FP32 PCG
+ *               relative tolerance and caps                               */
+typedef struct rf_solver_params {
+    double tol_picard, tol_cg;
+    int cg_max_it;
+    int precond;      /* rf_precond   */
+    int precision;    /* rf_precision */
+    double dt0, dt_max, dt_min, f_grow, f_shrink;
+    int n_inc, n_small, n_max;
+    double eps_chord;
+    double tol_inner;
+    int inner_max_it, outer_max_it;
+} rf_solver_params;
+
+/* Fill *p with the defaults: tol_picard 1e-6, tol_cg 1e-10, cg_max_it 10000,
+ * Jacobi, FP64, dt0 1, dt_max 600, dt_min 1e-3, f 1.3/1.3, n_inc 10, n_small 3,
+ * n_max 8, eps_chord 1e-10, tol_inner 1e-4, inner_max_it 2000, outer_max_it 30. */
+void rf_default_params(rf_solver_params *p);
+
+/* Structured mesh of equal cells (the paper's solver requires a constant cell
+ * volume, Restrictions paragraph).  active: nx*ny*nz bytes, nonzero = active,
+ * NULL = all active. */
+typedef struct rf_mesh_desc {
+    int nx, ny, nz;
+    double dx, dy, dz, z_bottom;
+    const uint8_t *active;
+} rf_mesh_desc;
+
+/* Optional device-memory allocator.  When NULL the library uses cudaMalloc /
+ * cudaFree.  alloc must return a device pointer aligned to 256 bytes or NULL. */
+typedef struct rf_allocator {
+    void *(*alloc)(size_t bytes, void *user);
+    void (*free)(void *ptr, void *user);
+    void *user;
+} rf_allocator;
+
+/* Create a context for a mesh on the current CUDA device; cuda_stream is a
+ * cudaStream_t (NULL = the legacy default stream).  All device memory is
+ * allocated here (through alloc when given) and released by rf_destroy. */
+rf_status rf_mesh_create(const rf_mesh_desc *mesh, const rf_solver_params *params, void *cuda_stream,
+                         const rf_allocator *alloc, rf_ctx **out);
+void rf_destroy(rf_ctx *ctx);
+rf_status rf_set_params(rf_ctx *ctx, const rf_solver_params *params);
+
+/* Soil parameters per zone (Eq. 2-4 symbols; S is the storativity for h >= 0,
+ * which the paper names but does not value).  zone_of_cell: N bytes or NULL
+ * (all zone 0).  Ks_cell: N doubles overriding each cell's Ks, or NULL. */
+typedef struct rf_soil {
+    int model;   /* rf_soil_model */
+    double theta_r, theta_s, alpha, n, Ks, S;
+} rf_soil;
+rf_status rf_soil_set(rf_ctx *ctx, const rf_soil *zones, int n_zones, const uint8_t *zone_of_cell,
+                      const double *Ks_cell);
+
+/* Boundary condition of a face class: a piecewise-constant series, v[i] on
+ * [t[i], t[i+1]) (v[0] before t[0], v[n-1] after t[n-1]); t strictly
+ * increasing; n = 1 for a constant; t may be NULL when n = 1.  Steps are
+ * clipped to the series breakpoints so each step sees one value.  ZERO_FLUX,
+ * FREE_DRAINAGE and SEEPAGE take no series (n = 0). */
+rf_status rf_bc_set(rf_ctx *ctx, rf_face face, rf_bc_type type, const double *t, const double *v, int n);
+
+/* Set the state h (N doubles, inactive entries are kept as given) at time t;
+ * resets EBATS (dt = dt0) and the mass balance (storage0 = storage of h). */
+rf_status rf_state_set(rf_ctx *ctx, const double *h, double t);
+rf_status rf_state_set_device(rf_ctx *ctx, const double *d_h, double t);
+
+typedef struct rf_state_meta {
+    double t, dt_nom;
+    int easy;          /* EBATS consecutive-easy-step counter */
+    int n_active;
+    long long steps;   /* accepted steps since rf_state_set   */
+} rf_state_meta;
+rf_status rf_state_get(rf_ctx *ctx, double *h, rf_state_meta *meta);   /* h: host, N, or NULL */
+rf_status rf_state_get_device(rf_ctx *ctx, double *d_h);               /* d_h: device, N      */
+
+/* Restore EBATS and mass-balance counters (checkpoint / resume). */
+rf_status rf_state_meta_set(rf_ctx *ctx, const rf_state_meta *meta, const double *mass7);
+
+typedef struct rf_step_info {
+    double dt, t;          /* accepted step size and the time reached             */
+    int picard_iters;      /* Picard iterations (linear solves) of the accepted try */
+    int cg_iters;          /* CG iterations over all tries of this step            */
+    int rejected;          /* EBATS reruns before acceptance                        */
+    double max_dh;         /* last Picard update max|h^{k+1} - h^k|                 */
+} rf_step_info;
+
+/* One accepted backward-Euler step (with EBATS reruns). */
+rf_status rf_step(rf_ctx *ctx, rf_step_info *out);
+
+typedef struct rf_run_stats {
+    long long steps, picard_iters, cg_iters, rejected;
+} rf_run_stats;
+
+/* Advance to t_end (the last step is clipped to t_end).  log: up to log_cap
+ * step records, or NULL. */
+rf_status rf_run(rf_ctx *ctx, double t_end, rf_run_stats *stats, rf_step_info *log, int log_cap);
+
+/* Global water balance since rf_state_set (volumes, m^3).  closure_abs is
+ * |sum over steps of [sum_P V C^k (h^{n+1}-h^n) - dt Q_boundary]| of each
+ * accepted step's last linear system; closure_rel divides it by storage0 +
+ * inflow_cum + outflow_cum.  nonlinear_defect_cum is sum of [storage change -
+ * dt Q_boundary], bounded by the Picard tolerance. */
+typedef struct rf_mass_balance_t {
+    double storage0, storage, inflow_cum, outflow_cum, closure_abs, closure_rel, nonlinear_defect_cum;
+} rf_mass_balance_t;
+rf_status rf_mass_balance(rf_ctx *ctx, rf_mass_balance_t *out);
+
+/* Message of the last failed call on this thread ("" if none). */
+const char *rf_last_error(void);
+
+/* ---- kernel-level entry points (device pointers, N doubles each) ------- */
+
+/* Evaluate the closures at d_hk and assemble the Picard system at
+ * (h^k = d_hk, h^n = d_hn, dt, t) into the context's operator; optionally
+ * copy K(h^k), theta*(h^k), c = V C^k/dt, b and diag(A) out (NULL to skip).
+ * Inactive entries are written as 0. */
+rf_status rf_assemble(rf_ctx *ctx, const double *d_hk, const double *d_hn, double dt, double t,
+                      double *d_K, double *d_theta, double *d_c, double *d_b, double *d_diag);
+
+/* d_y = A d_x with the last assembled operator (FP64). */
+rf_status rf_apply(rf_ctx *ctx, const double *d_x, double *d_y);
+
+/* Solve the last assembled system with the context's precision and
+ * preconditioner; d_x holds x0 on entry and the solution on return.
+ * *iters: CG iterations (FP64) or inner FP32 iterations summed (mixed). */
+rf_status rf_solve(rf_ctx *ctx, double *d_x, int *iters);
+
+/* Number of CUDA kernels this context has launched (for accounting). */
+unsigned long long rf_launch_count(rf_ctx *ctx);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* RF_H */

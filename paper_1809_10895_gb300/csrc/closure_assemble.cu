@@ -1,0 +1,287 @@
+// closure_assemble.cu -- per-cell closures (Eq. 2-4, Eq. A6), Picard-system
+// assembly (Sec. 2.2), water-balance reductions.
+//
+// Layout: structure-of-arrays over all nx*ny*nz cells, x fastest.  Inactive
+// cells carry K = -1 (a sentinel the stencil kernels test instead of reading
+// the flag array) and zeros elsewhere.
+#include <math.h>
+
+#include "rf_internal.cuh"
+#include "rf_reduce.cuh"
+
+namespace rf {
+
+// van Genuchten / Mualem closures in a cancellation-free form.
+// With L = log(-alpha h), x = (-alpha h)^n = exp(n L), l1 = log1p(x):
+//   Se = (1 + x)^-m = exp(-m l1)                               (Eq. 2)
+//   Se^(1/m) = 1/(1+x), so 1 - Se^(1/m) = x/(1+x) and
+//   K = Ks Se^(1/2) [1 - exp(m (n L - l1))]^2 = Ks sqrt(Se) expm1(.)^2   (Eq. 4)
+//   C = (theta_s-theta_r) alpha n m exp((n-1) L - (m+1) l1)     (Eq. 3)
+// For h >= 0 (tie included): theta* = theta_s + S h, K = Ks, C = S, which
+// makes d(theta*)/dh equal to Eq. 3 on both branches.
+// Gardner (Eq. A6): K = Ks e^(alpha h), theta = theta_r + (theta_s-theta_r) e^(alpha h).
+__device__ __forceinline__ void closure(const DevSoil &s, double Ks, double h, double &th, double &K, double &C)
+{
+    if (h >= 0.0) {
+        th = s.theta_s + s.S * h;
+        K = Ks;
+        C = s.S;
+        return;
+    }
+    const double dth = s.theta_s - s.theta_r;
+    if (s.model == M_GARDNER) {
+        const double e = exp(s.alpha * h);
+        K = Ks * e;
+        th = s.theta_r + dth * e;
+        C = dth * s.alpha * e;
+        return;
+    }
+    const double L = log(-s.alpha * h);
+    const double nL = s.n * L;
+    const double x = exp(nL);
+    const double l1 = log1p(x);
+    const double se = exp(-s.m * l1);
+    th = s.theta_r + dth * se;
+    const double omy = -expm1(s.m * (nL - l1));
+    K = Ks * sqrt(se) * omy * omy;
+    C = dth * s.alpha * s.n * s.m * exp((s.n - 1.0) * L - (s.m + 1.0) * l1);
+}
+
+__global__ void __launch_bounds__(RED_THREADS)
+k_closure(Grid g, const DevSoil *__restrict__ soils, const uint8_t *__restrict__ zone,
+          const double *__restrict__ Ks, const uint8_t *__restrict__ flags, const double *__restrict__ h,
+          const double *__restrict__ hprev, double *__restrict__ theta, double *__restrict__ K,
+          double *__restrict__ Can, double *partials, unsigned int *ticket, StepResults *res)
+{
+    double v[2] = {0.0, 0.0};   // max |h - hprev|, non-finite flag
+    const long long stride = (long long)gridDim.x * blockDim.x;
+    for (long long p = (long long)blockIdx.x * blockDim.x + threadIdx.x; p < g.N; p += stride) {
+        if (!(flags[p] & FLAG_ACTIVE)) {
+            theta[p] = 0.0;
+            K[p] = -1.0;
+            Can[p] = 0.0;
+            continue;
+        }
+        const double hp = h[p];
+        if (hprev) {
+            const double d = fabs(hp - hprev[p]);
+            if (d <= 1e300) v[0] = fmax(v[0], d);
+            else v[1] = 1.0;           // NaN or inf
+        }
+        const DevSoil s = soils[zone[p]];
+        double th, k, c;
+        closure(s, Ks[p], hp, th, k, c);
+        theta[p] = th;
+        K[p] = k;
+        Can[p] = c;
+    }
+    if (hprev) {
+        if (grid_reduce<OpMax, 2>(v, partials, ticket) && threadIdx.x == 0) {
+            res->max_dh = v[0];
+            res->nonfinite = v[1] > 0.0;
+        }
+    }
+}
+
+// Neighbour across face f of cell p = (i,j,k); false when outside the grid.
+__device__ __forceinline__ bool neighbour(const Grid &g, long long p, int i, int j, int k, int f, long long &q)
+{
+    switch (f) {
+    case F_XMIN: q = p - 1; return i > 0;
+    case F_XMAX: q = p + 1; return i < g.nx - 1;
+    case F_YMIN: q = p - g.nx; return j > 0;
+    case F_YMAX: q = p + g.nx; return j < g.ny - 1;
+    case F_ZMIN: q = p - g.sxy; return k > 0;
+    default:     q = p + g.sxy; return k < g.nz - 1;
+    }
+}
+
+// Assembly of V C^k (h - h^n)/dt = sum_f T_f (h_N - h) + G + B (Sec. 2.2):
+//   c = V C^k / dt, C^k the chord slope of theta* (or C(h^k) when
+//   |h^k - h^n| <= eps); T_f = Kbar_f A_f/d_f, Kbar_f = (K_P + K_N)/2;
+//   explicit gravity A_z (Kbar_top - Kbar_bottom) with K at h^k;
+//   boundary terms per face class (Dirichlet at the half cell with K(h_D),
+//   imposed flux, free drainage -K(h^k) A_z, seepage as Dirichlet 0 while the
+//   cell is saturated at the step start).
+// Outputs: c, b, upper-face coefficients Tx/Ty/Tz (0 where the face is not an
+// interior face), diag(A), 1/diag; FP32 copies of K and of c plus the
+// Dirichlet diagonal terms for the mixed-precision operator.
+__global__ void __launch_bounds__(RED_THREADS)
+k_assemble(Grid g, const DevSoil *__restrict__ soils, const uint8_t *__restrict__ zone,
+           const double *__restrict__ Ks, const uint8_t *__restrict__ flags, const StepParams *__restrict__ spp,
+           const double *__restrict__ hk, const double *__restrict__ hn, const double *__restrict__ thk,
+           const double *__restrict__ thn, const double *__restrict__ K, const double *__restrict__ Can,
+           double *__restrict__ c_out, double *__restrict__ b, double *__restrict__ Tx, double *__restrict__ Ty,
+           double *__restrict__ Tz, double *__restrict__ diag_out, double *__restrict__ dinv,
+           float *__restrict__ K32, float *__restrict__ cb32, float *__restrict__ dinv32)
+{
+    const double dt = spp->dt, eps = spp->eps_chord;
+    const long long stride = (long long)gridDim.x * blockDim.x;
+    for (long long p = (long long)blockIdx.x * blockDim.x + threadIdx.x; p < g.N; p += stride) {
+        const uint8_t fl = flags[p];
+        if (!(fl & FLAG_ACTIVE)) {
+            c_out[p] = 0.0; b[p] = 0.0; Tx[p] = 0.0; Ty[p] = 0.0; Tz[p] = 0.0;
+            diag_out[p] = 0.0; dinv[p] = 0.0;
+            K32[p] = -1.0f; cb32[p] = 0.0f; dinv32[p] = 0.0f;
+            continue;
+        }
+        const int i = (int)(p % g.nx);
+        const int j = (int)((p / g.nx) % g.ny);
+        const int k = (int)(p / g.sxy);
+        const double hkP = hk[p], hnP = hn[p], KP = K[p];
+        const double dh = hkP - hnP;
+        const double C = (fabs(dh) > eps) ? (thk[p] - thn[p]) / dh : Can[p];
+        const double c = g.V * C / dt;
+        double diag = c, rhs = c * hnP, cb = c;
+        double Tup[3] = {0.0, 0.0, 0.0};
+#pragma unroll
+        for (int f = 0; f < 6; f++) {
+            const double gs = (f == F_ZMIN) ? -1.0 : (f == F_ZMAX ? 1.0 : 0.0);
+            long long q;
+            if (neighbour(g, p, i, j, k, f, q)) {
+                const double KN = K[q];
+                if (KN >= 0.0) {
+                    const double Kbar = 0.5 * (KP + KN);
+                    const double T = Kbar * g.w[f];
+                    diag += T;
+                    rhs += gs * Kbar * g.A[f];
+                    if (f & 1) Tup[f >> 1] = T;
+                    continue;
+                }
+            }
+            if (!(fl & (1u << f))) continue;    // closed face (lateral face on an inactive cell)
+            int type = spp->bc_type[f];
+            double hD = 0.0;
+            if (type == BC_SEEPAGE) {
+                if (hnP >= 0.0) { type = BC_DIRICHLET; hD = 0.0; }
+                else type = BC_ZERO_FLUX;
+            } else if (type == BC_DIRICHLET) {
+                hD = spp->bc_val[f];
+            }
+            if (type == BC_DIRICHLET) {
+                const DevSoil s = soils[zone[p]];
+                double thD, KD, CD;
+                closure(s, Ks[p], hD, thD, KD, CD);
+                const double T = KD * g.wb[f];
+                diag += T;
+                cb += T;
+                rhs += T * hD + gs * KD * g.A[f];
+            } else if (type == BC_FLUX) {
+                rhs += spp->bc_val[f] * g.A[f];
+            } else if (type == BC_FREE_DRAINAGE) {
+                rhs += -KP * g.A[f];
+            }
+        }
+        c_out[p] = c;
+        b[p] = rhs;
+        Tx[p] = Tup[0];
+        Ty[p] = Tup[1];
+        Tz[p] = Tup[2];
+        diag_out[p] = diag;
+        dinv[p] = 1.0 / diag;
+        K32[p] = (float)KP;
+        cb32[p] = (float)cb;
+        dinv32[p] = (float)(1.0 / diag);
+    }
+}
+
+// Water balance of the accepted step's last linear system (x = h^{n+1}):
+// sum c dt (x - h^n), sum V (theta*(x) - theta*(h^n)), and dt times the
+// boundary inflow / outflow of that system, split per face by sign.
+__global__ void __launch_bounds__(RED_THREADS)
+k_mass_balance(Grid g, const DevSoil *__restrict__ soils, const uint8_t *__restrict__ zone,
+               const double *__restrict__ Ks, const uint8_t *__restrict__ flags,
+               const StepParams *__restrict__ spp, const double *__restrict__ x, const double *__restrict__ hn,
+               const double *__restrict__ c, const double *__restrict__ Kold, const double *__restrict__ thx,
+               const double *__restrict__ thn, double *partials, unsigned int *ticket, StepResults *res)
+{
+    const double dt = spp->dt;
+    double v[4] = {0.0, 0.0, 0.0, 0.0};   // lin, dS, in, out
+    const long long stride = (long long)gridDim.x * blockDim.x;
+    for (long long p = (long long)blockIdx.x * blockDim.x + threadIdx.x; p < g.N; p += stride) {
+        const uint8_t fl = flags[p];
+        if (!(fl & FLAG_ACTIVE)) continue;
+        const double xp = x[p], hnP = hn[p];
+        v[0] += c[p] * dt * (xp - hnP);
+        v[1] += g.V * (thx[p] - thn[p]);
+        if (!(fl & 0x3f)) continue;
+#pragma unroll
+        for (int f = 0; f < 6; f++) {
+            if (!(fl & (1u << f))) continue;
+            const double gs = (f == F_ZMIN) ? -1.0 : (f == F_ZMAX ? 1.0 : 0.0);
+            int type = spp->bc_type[f];
+            double hD = 0.0, flux = 0.0;
+            if (type == BC_SEEPAGE) {
+                if (hnP >= 0.0) { type = BC_DIRICHLET; hD = 0.0; }
+                else type = BC_ZERO_FLUX;
+            } else if (type == BC_DIRICHLET) {
+                hD = spp->bc_val[f];
+            }
+            if (type == BC_DIRICHLET) {
+                const DevSoil s = soils[zone[p]];
+                double thD, KD, CD;
+                closure(s, Ks[p], hD, thD, KD, CD);
+                const double T = KD * g.wb[f];
+                flux = T * hD + gs * KD * g.A[f] - T * xp;
+            } else if (type == BC_FLUX) {
+                flux = spp->bc_val[f] * g.A[f];
+            } else if (type == BC_FREE_DRAINAGE) {
+                flux = -Kold[p] * g.A[f];
+            }
+            if (flux > 0.0) v[2] += dt * flux;
+            else v[3] -= dt * flux;
+        }
+    }
+    if (grid_reduce<OpSum, 4>(v, partials, ticket) && threadIdx.x == 0) {
+        res->lin_change = v[0];
+        res->dstore = v[1];
+        res->bnd_in = v[2];
+        res->bnd_out = v[3];
+    }
+}
+
+__global__ void __launch_bounds__(RED_THREADS)
+k_storage(Grid g, const uint8_t *__restrict__ flags, const double *__restrict__ theta, double *partials,
+          unsigned int *ticket, StepResults *res)
+{
+    double v[1] = {0.0};
+    const long long stride = (long long)gridDim.x * blockDim.x;
+    for (long long p = (long long)blockIdx.x * blockDim.x + threadIdx.x; p < g.N; p += stride)
+        if (flags[p] & FLAG_ACTIVE) v[0] += g.V * theta[p];
+    if (grid_reduce<OpSum, 1>(v, partials, ticket) && threadIdx.x == 0) res->storage = v[0];
+}
+
+void launch_closure(cudaStream_t s, int nblk, const Grid &g, const DevSoil *soils, const uint8_t *zone,
+                    const double *Ks, const uint8_t *flags, const double *h, const double *hprev,
+                    double *theta, double *K, double *Can, double *partials, unsigned int *ticket,
+                    StepResults *res)
+{
+    k_closure<<<nblk, RED_THREADS, 0, s>>>(g, soils, zone, Ks, flags, h, hprev, theta, K, Can, partials, ticket, res);
+}
+
+void launch_assemble(cudaStream_t s, int nblk, const Grid &g, const DevSoil *soils, const uint8_t *zone,
+                     const double *Ks, const uint8_t *flags, const StepParams *sp, const double *hk,
+                     const double *hn, const double *theta_k, const double *theta_n, const double *K,
+                     const double *Can, double *c, double *b, double *Tx, double *Ty, double *Tz,
+                     double *diag, double *dinv, float *K32, float *cb32, float *dinv32)
+{
+    k_assemble<<<nblk, RED_THREADS, 0, s>>>(g, soils, zone, Ks, flags, sp, hk, hn, theta_k, theta_n, K, Can, c, b,
+                                            Tx, Ty, Tz, diag, dinv, K32, cb32, dinv32);
+}
+
+void launch_mass_balance(cudaStream_t s, int nblk, const Grid &g, const DevSoil *soils, const uint8_t *zone,
+                         const double *Ks, const uint8_t *flags, const StepParams *sp, const double *x,
+                         const double *hn, const double *c, const double *Kold, const double *theta_x,
+                         const double *theta_n, double *partials, unsigned int *ticket, StepResults *res)
+{
+    k_mass_balance<<<nblk, RED_THREADS, 0, s>>>(g, soils, zone, Ks, flags, sp, x, hn, c, Kold, theta_x, theta_n,
+                                                partials, ticket, res);
+}
+
+void launch_storage(cudaStream_t s, int nblk, const Grid &g, const uint8_t *flags, const double *theta,
+                    double *partials, unsigned int *ticket, StepResults *res)
+{
+    k_storage<<<nblk, RED_THREADS, 0, s>>>(g, flags, theta, partials, ticket, res);
+}
+
+}  // namespace rf

@@ -1,0 +1,388 @@
+// pcg.cu -- matrix-free 7-point stencil operator and Jacobi-preconditioned
+// conjugate gradient for the Picard system (Sec. 2.2: PCG on the symmetric
+// M-matrix of the backward-Euler / Picard linearisation).
+//
+// FP64 path: the operator is stored as diag(A) and the three upper-face
+// coefficients Tx, Ty, Tz per cell (GB300's FP64 rate is low, so the face
+// coefficients are read, not recomputed).
+//   (A v)_P = diag_P v_P - sum_f T_f v_N
+// FP32 inner path (mixed precision): faces are recomputed from K in FP32,
+//   (A v)_P = cb_P v_P + sum_f w_f (K_P + K_N)/2 (v_P - v_N)
+// where cb = c + Dirichlet half-cell terms; inactive neighbours carry K < 0.
+//
+// One PCG iteration is two kernels:
+//   spmv   : p = z + beta p_old (recomputed for the stencil neighbours, so p
+//            ping-pongs between two buffers), q = A p, partial p.q;
+//   update : x += alpha p, r -= alpha q, z = D^-1 r, partial r.r and r.z.
+// The scalars (alpha, beta, rho, convergence) live on the device and are
+// produced by the last block of each grid reduction, so a solve needs no host
+// round trip per iteration; kernels of a finished solve return at once.
+#include <math.h>
+
+#include "rf_internal.cuh"
+#include "rf_reduce.cuh"
+
+namespace rf {
+
+#define GRID_STRIDE_LOOP(p)                                                                 \
+    for (long long p = (long long)blockIdx.x * blockDim.x + threadIdx.x; p < g.N;           \
+         p += (long long)gridDim.x * blockDim.x)
+
+// FP64 stencil with stored coefficients; get(q) supplies the vector value.
+template <class Get>
+__device__ __forceinline__ double apply64(const Grid &g, long long p, const double *__restrict__ Tx,
+                                          const double *__restrict__ Ty, const double *__restrict__ Tz,
+                                          const double *__restrict__ diag, Get get)
+{
+    const int i = (int)(p % g.nx);
+    const int j = (int)((p / g.nx) % g.ny);
+    const int k = (int)(p / g.sxy);
+    double acc = diag[p] * get(p);
+    if (i > 0) acc -= Tx[p - 1] * get(p - 1);
+    if (i < g.nx - 1) acc -= Tx[p] * get(p + 1);
+    if (j > 0) acc -= Ty[p - g.nx] * get(p - g.nx);
+    if (j < g.ny - 1) acc -= Ty[p] * get(p + g.nx);
+    if (k > 0) acc -= Tz[p - g.sxy] * get(p - g.sxy);
+    if (k < g.nz - 1) acc -= Tz[p] * get(p + g.sxy);
+    return acc;
+}
+
+// ---------------------------------------------------------------- FP64 PCG
+__global__ void __launch_bounds__(RED_THREADS)
+k_cg64_init(Grid g, const uint8_t *__restrict__ flags, const double *__restrict__ x0, double *__restrict__ x,
+            const double *__restrict__ b, const double *__restrict__ Tx, const double *__restrict__ Ty,
+            const double *__restrict__ Tz, const double *__restrict__ diag, const double *__restrict__ dinv,
+            double *__restrict__ r, double *__restrict__ z, double tol, int max_it, double *partials,
+            unsigned int *ticket, CgScal *sc)
+{
+    double v[3] = {0.0, 0.0, 0.0};   // r.z, r.r, b.b
+    GRID_STRIDE_LOOP(p)
+    {
+        const double xp = x0[p];
+        x[p] = xp;
+        if (!(flags[p] & FLAG_ACTIVE)) {
+            r[p] = 0.0;
+            z[p] = 0.0;
+            continue;
+        }
+        const double bp = b[p];
+        const double rp = bp - apply64(g, p, Tx, Ty, Tz, diag, [&](long long q) { return x0[q]; });
+        const double zp = dinv[p] * rp;
+        r[p] = rp;
+        z[p] = zp;
+        v[0] += rp * zp;
+        v[1] += rp * rp;
+        v[2] += bp * bp;
+    }
+    if (grid_reduce<OpSum, 3>(v, partials, ticket) && threadIdx.x == 0) {
+        sc->rho = v[0];
+        sc->rr = v[1];
+        sc->bb = v[2];
+        sc->stop2 = tol * sqrt(v[2]);      // threshold on ||r||_2
+        sc->alpha = 0.0;
+        sc->beta = 0.0;
+        sc->iter = 0;
+        sc->max_it = max_it;
+        const bool finite = isfinite(v[0]) && isfinite(v[1]) && isfinite(v[2]);
+        sc->status = finite ? CG_OK : CG_NONFINITE;
+        sc->done = (!finite || sqrt(v[1]) <= sc->stop2) ? 1 : 0;
+    }
+}
+
+__global__ void __launch_bounds__(RED_THREADS)
+k_cg64_spmv(Grid g, const uint8_t *__restrict__ flags, const double *__restrict__ z, const double *__restrict__ p_in,
+            double *__restrict__ p_out, double *__restrict__ q, const double *__restrict__ Tx,
+            const double *__restrict__ Ty, const double *__restrict__ Tz, const double *__restrict__ diag,
+            double *partials, unsigned int *ticket, CgScal *sc)
+{
+    if (sc->done) return;
+    const double beta = sc->beta;
+    const bool first = sc->iter == 0;
+    auto get = [&](long long qq) { return first ? z[qq] : fma(beta, p_in[qq], z[qq]); };
+    double v[1] = {0.0};
+    GRID_STRIDE_LOOP(p)
+    {
+        if (!(flags[p] & FLAG_ACTIVE)) {
+            p_out[p] = 0.0;
+            q[p] = 0.0;
+            continue;
+        }
+        const double pp = get(p);
+        const double qp = apply64(g, p, Tx, Ty, Tz, diag, get);
+        p_out[p] = pp;
+        q[p] = qp;
+        v[0] += pp * qp;
+    }
+    if (grid_reduce<OpSum, 1>(v, partials, ticket) && threadIdx.x == 0) {
+        sc->pq = v[0];
+        const double a = sc->rho / v[0];
+        if (!(v[0] > 0.0) || !isfinite(a)) {
+            sc->status = CG_NONFINITE;
+            sc->done = 1;
+        }
+        sc->alpha = a;
+    }
+}
+
+__global__ void __launch_bounds__(RED_THREADS)
+k_cg64_update(Grid g, double *__restrict__ x, double *__restrict__ r, double *__restrict__ z,
+              const double *__restrict__ pd, const double *__restrict__ q, const double *__restrict__ dinv,
+              double *partials, unsigned int *ticket, CgScal *sc)
+{
+    if (sc->done) return;
+    const double alpha = sc->alpha;
+    double v[2] = {0.0, 0.0};   // r.r, r.z
+    GRID_STRIDE_LOOP(p)
+    {
+        const double di = dinv[p];
+        if (di == 0.0) continue;                  // inactive
+        x[p] = fma(alpha, pd[p], x[p]);
+        const double rp = fma(-alpha, q[p], r[p]);
+        const double zp = di * rp;
+        r[p] = rp;
+        z[p] = zp;
+        v[0] += rp * rp;
+        v[1] += rp * zp;
+    }
+    if (grid_reduce<OpSum, 2>(v, partials, ticket) && threadIdx.x == 0) {
+        sc->iter += 1;
+        sc->rr = v[0];
+        if (!isfinite(v[0]) || !isfinite(v[1])) {
+            sc->status = CG_NONFINITE;
+            sc->done = 1;
+        } else if (sqrt(v[0]) <= sc->stop2) {
+            sc->done = 1;
+        } else if (sc->iter >= sc->max_it) {
+            sc->status = CG_MAXIT;
+            sc->done = 1;
+        } else {
+            sc->beta = v[1] / sc->rho;
+            sc->rho = v[1];
+        }
+    }
+}
+
+__global__ void __launch_bounds__(RED_THREADS)
+k_apply64(Grid g, const uint8_t *__restrict__ flags, const double *__restrict__ x, double *__restrict__ y,
+          const double *__restrict__ Tx, const double *__restrict__ Ty, const double *__restrict__ Tz,
+          const double *__restrict__ diag)
+{
+    GRID_STRIDE_LOOP(p)
+    {
+        y[p] = (flags[p] & FLAG_ACTIVE) ? apply64(g, p, Tx, Ty, Tz, diag, [&](long long q) { return x[q]; }) : 0.0;
+    }
+}
+
+// ------------------------------------------------------ mixed precision
+// FP32 operator with faces recomputed from FP32 K.
+template <class Get>
+__device__ __forceinline__ float apply32(const Grid &g, long long p, const float *__restrict__ K32,
+                                         const float *__restrict__ cb32, Get get)
+{
+    const int i = (int)(p % g.nx);
+    const int j = (int)((p / g.nx) % g.ny);
+    const int k = (int)(p / g.sxy);
+    const float KP = K32[p];
+    const float vP = get(p);
+    float acc = cb32[p] * vP;
+    auto face = [&](bool inside, long long q, float w) {
+        if (!inside) return;
+        const float KN = K32[q];
+        if (KN < 0.0f) return;
+        acc = fmaf(w * 0.5f * (KP + KN), vP - get(q), acc);
+    };
+    face(i > 0, p - 1, g.w32[0]);
+    face(i < g.nx - 1, p + 1, g.w32[0]);
+    face(j > 0, p - g.nx, g.w32[1]);
+    face(j < g.ny - 1, p + g.nx, g.w32[1]);
+    face(k > 0, p - g.sxy, g.w32[2]);
+    face(k < g.nz - 1, p + g.sxy, g.w32[2]);
+    return acc;
+}
+
+// Outer FP64 residual r = b - A x; seeds the inner FP32 solve A d = r with
+// d0 = 0 (so r32 = r, z32 = D^-1 r32).
+__global__ void __launch_bounds__(RED_THREADS)
+k_resid64(Grid g, const uint8_t *__restrict__ flags, const double *__restrict__ x, const double *__restrict__ b,
+          const double *__restrict__ Tx, const double *__restrict__ Ty, const double *__restrict__ Tz,
+          const double *__restrict__ diag, const float *__restrict__ dinv32, float *__restrict__ r32,
+          float *__restrict__ z32, float *__restrict__ d32, double tol, double tol_inner, int inner_max_it,
+          double *partials, unsigned int *ticket, CgScal *outer, CgScal *inner)
+{
+    double v[4] = {0.0, 0.0, 0.0, 0.0};   // r.r, b.b (FP64); r32.r32, r32.z32
+    GRID_STRIDE_LOOP(p)
+    {
+        d32[p] = 0.0f;
+        if (!(flags[p] & FLAG_ACTIVE)) {
+            r32[p] = 0.0f;
+            z32[p] = 0.0f;
+            continue;
+        }
+        const double bp = b[p];
+        const double rp = bp - apply64(g, p, Tx, Ty, Tz, diag, [&](long long q) { return x[q]; });
+        const float rf = (float)rp;
+        const float zf = dinv32[p] * rf;
+        r32[p] = rf;
+        z32[p] = zf;
+        v[0] += rp * rp;
+        v[1] += bp * bp;
+        v[2] += (double)(rf * rf);
+        v[3] += (double)(rf * zf);
+    }
+    if (grid_reduce<OpSum, 4>(v, partials, ticket) && threadIdx.x == 0) {
+        const bool finite = isfinite(v[0]) && isfinite(v[1]) && isfinite(v[2]) && isfinite(v[3]);
+        outer->rr = v[0];
+        outer->bb = v[1];
+        outer->stop2 = tol * sqrt(v[1]);
+        outer->status = finite ? CG_OK : CG_NONFINITE;
+        outer->done = (!finite || sqrt(v[0]) <= outer->stop2) ? 1 : 0;
+        inner->rho = v[3];
+        inner->rr = v[2];
+        inner->bb = v[2];
+        inner->stop2 = tol_inner * sqrt(v[2]);
+        inner->alpha = 0.0;
+        inner->beta = 0.0;
+        inner->iter = 0;
+        inner->max_it = inner_max_it;
+        inner->status = finite ? CG_OK : CG_NONFINITE;
+        inner->done = (outer->done || !(v[2] > 0.0)) ? 1 : 0;
+    }
+}
+
+__global__ void __launch_bounds__(RED_THREADS)
+k_cg32_spmv(Grid g, const float *__restrict__ z, const float *__restrict__ p_in, float *__restrict__ p_out,
+            float *__restrict__ q, const float *__restrict__ K32, const float *__restrict__ cb32, double *partials,
+            unsigned int *ticket, CgScal *sc)
+{
+    if (sc->done) return;
+    const float beta = (float)sc->beta;
+    const bool first = sc->iter == 0;
+    auto get = [&](long long qq) { return first ? z[qq] : fmaf(beta, p_in[qq], z[qq]); };
+    float acc = 0.0f;
+    GRID_STRIDE_LOOP(p)
+    {
+        if (K32[p] < 0.0f) {
+            p_out[p] = 0.0f;
+            q[p] = 0.0f;
+            continue;
+        }
+        const float pp = get(p);
+        const float qp = apply32(g, p, K32, cb32, get);
+        p_out[p] = pp;
+        q[p] = qp;
+        acc = fmaf(pp, qp, acc);
+    }
+    double v[1] = {(double)acc};
+    if (grid_reduce<OpSum, 1>(v, partials, ticket) && threadIdx.x == 0) {
+        sc->pq = v[0];
+        const double a = sc->rho / v[0];
+        if (!(v[0] > 0.0) || !isfinite(a)) {
+            sc->status = CG_NONFINITE;
+            sc->done = 1;
+        }
+        sc->alpha = a;
+    }
+}
+
+__global__ void __launch_bounds__(RED_THREADS)
+k_cg32_update(Grid g, float *__restrict__ x, float *__restrict__ r, float *__restrict__ z,
+              const float *__restrict__ pd, const float *__restrict__ q, const float *__restrict__ dinv,
+              double *partials, unsigned int *ticket, CgScal *sc)
+{
+    if (sc->done) return;
+    const float alpha = (float)sc->alpha;
+    float a0 = 0.0f, a1 = 0.0f;
+    GRID_STRIDE_LOOP(p)
+    {
+        const float di = dinv[p];
+        if (di == 0.0f) continue;
+        x[p] = fmaf(alpha, pd[p], x[p]);
+        const float rp = fmaf(-alpha, q[p], r[p]);
+        const float zp = di * rp;
+        r[p] = rp;
+        z[p] = zp;
+        a0 = fmaf(rp, rp, a0);
+        a1 = fmaf(rp, zp, a1);
+    }
+    double v[2] = {(double)a0, (double)a1};
+    if (grid_reduce<OpSum, 2>(v, partials, ticket) && threadIdx.x == 0) {
+        sc->iter += 1;
+        sc->rr = v[0];
+        if (!isfinite(v[0]) || !isfinite(v[1])) {
+            sc->status = CG_NONFINITE;
+            sc->done = 1;
+        } else if (sqrt(v[0]) <= sc->stop2) {
+            sc->done = 1;
+        } else if (sc->iter >= sc->max_it) {
+            sc->status = CG_MAXIT;
+            sc->done = 1;
+        } else {
+            sc->beta = v[1] / sc->rho;
+            sc->rho = v[1];
+        }
+    }
+}
+
+__global__ void __launch_bounds__(RED_THREADS)
+k_add_correction(Grid g, double *__restrict__ x, const float *__restrict__ d)
+{
+    GRID_STRIDE_LOOP(p) { x[p] += (double)d[p]; }
+}
+
+// ------------------------------------------------------------ launchers
+void launch_cg64_init(cudaStream_t s, int nblk, const Grid &g, const uint8_t *flags, const double *x0, double *x,
+                      const double *b, const double *Tx, const double *Ty, const double *Tz, const double *diag,
+                      const double *dinv, double *r, double *z, double tol, int max_it, double *partials,
+                      unsigned int *ticket, CgScal *sc)
+{
+    k_cg64_init<<<nblk, RED_THREADS, 0, s>>>(g, flags, x0, x, b, Tx, Ty, Tz, diag, dinv, r, z, tol, max_it, partials,
+                                             ticket, sc);
+}
+
+void launch_cg64_spmv(cudaStream_t s, int nblk, const Grid &g, const uint8_t *flags, const double *z,
+                      const double *p_in, double *p_out, double *q, const double *Tx, const double *Ty,
+                      const double *Tz, const double *diag, double *partials, unsigned int *ticket, CgScal *sc)
+{
+    k_cg64_spmv<<<nblk, RED_THREADS, 0, s>>>(g, flags, z, p_in, p_out, q, Tx, Ty, Tz, diag, partials, ticket, sc);
+}
+
+void launch_cg64_update(cudaStream_t s, int nblk, const Grid &g, double *x, double *r, double *z, const double *p,
+                        const double *q, const double *dinv, double *partials, unsigned int *ticket, CgScal *sc)
+{
+    k_cg64_update<<<nblk, RED_THREADS, 0, s>>>(g, x, r, z, p, q, dinv, partials, ticket, sc);
+}
+
+void launch_apply64(cudaStream_t s, int nblk, const Grid &g, const uint8_t *flags, const double *x, double *y,
+                    const double *Tx, const double *Ty, const double *Tz, const double *diag)
+{
+    k_apply64<<<nblk, RED_THREADS, 0, s>>>(g, flags, x, y, Tx, Ty, Tz, diag);
+}
+
+void launch_resid64(cudaStream_t s, int nblk, const Grid &g, const uint8_t *flags, const double *x, const double *b,
+                    const double *Tx, const double *Ty, const double *Tz, const double *diag, const float *dinv32,
+                    float *r32, float *z32, float *d32, double tol, double tol_inner, int inner_max_it,
+                    double *partials, unsigned int *ticket, CgScal *outer, CgScal *inner)
+{
+    k_resid64<<<nblk, RED_THREADS, 0, s>>>(g, flags, x, b, Tx, Ty, Tz, diag, dinv32, r32, z32, d32, tol, tol_inner,
+                                           inner_max_it, partials, ticket, outer, inner);
+}
+
+void launch_cg32_spmv(cudaStream_t s, int nblk, const Grid &g, const float *z, const float *p_in, float *p_out,
+                      float *q, const float *K32, const float *cb32, double *partials, unsigned int *ticket,
+                      CgScal *sc)
+{
+    k_cg32_spmv<<<nblk, RED_THREADS, 0, s>>>(g, z, p_in, p_out, q, K32, cb32, partials, ticket, sc);
+}
+
+void launch_cg32_update(cudaStream_t s, int nblk, const Grid &g, float *x, float *r, float *z, const float *p,
+                        const float *q, const float *dinv, double *partials, unsigned int *ticket, CgScal *sc)
+{
+    k_cg32_update<<<nblk, RED_THREADS, 0, s>>>(g, x, r, z, p, q, dinv, partials, ticket, sc);
+}
+
+void launch_add_correction(cudaStream_t s, int nblk, const Grid &g, double *x, const float *d)
+{
+    k_add_correction<<<nblk, RED_THREADS, 0, s>>>(g, x, d);
+}
+
+}  // namespace rf

@@ -1,0 +1,762 @@
+// rf_api.cu -- host driver behind the C ABI of include/rf.h.
+//
+// Owns the device memory of a context, the EBATS controller (Sec. 2.2), the
+// Picard loop with its global max|dh| exit test (Sec. 2.3) and the water
+// balance bookkeeping.  Every step of the numerical path runs in the CUDA
+// kernels of closure_assemble.cu and pcg.cu; the host only sequences them and
+// reads back a few scalars per Picard iteration.
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "rf.h"
+#include "rf_internal.cuh"
+
+using namespace rf;
+
+namespace {
+
+thread_local std::string g_err;
+
+rf_status fail(rf_status s, const std::string &msg)
+{
+    g_err = msg;
+    return s;
+}
+
+#define CUDA_TRY(x)                                                                          \
+    do {                                                                                     \
+        cudaError_t e_ = (x);                                                                \
+        if (e_ != cudaSuccess) return fail(RF_ERR_CUDA, std::string(#x) + ": " + cudaGetErrorString(e_)); \
+    } while (0)
+
+struct BcSeries {
+    int type = BC_ZERO_FLUX;
+    std::vector<double> t, v;
+};
+
+// simulated-time comparison tolerance
+double t_tol(double t) { return 1e-9 * (std::fabs(t) > 1.0 ? std::fabs(t) : 1.0); }
+
+}  // namespace
+
+struct rf_ctx {
+    int device = 0;
+    int num_sms = 0;
+    cudaStream_t stream = nullptr;
+    rf_allocator alloc{};
+    bool has_alloc = false;
+    std::vector<void *> allocations;
+
+    Grid g{};
+    int nblk = 1;
+    int n_active = 0;
+    rf_solver_params prm{};
+    std::vector<uint8_t> flags_h;
+    BcSeries bc[6];
+
+    // device arrays (N elements unless noted)
+    uint8_t *flags = nullptr, *zone = nullptr;
+    double *Ks = nullptr;
+    DevSoil *soils = nullptr;   // 256 entries
+    double *h = nullptr, *hk = nullptr, *x = nullptr, *theta_n = nullptr, *theta_k = nullptr;
+    double *K[2] = {nullptr, nullptr}, *Can = nullptr, *c = nullptr, *b = nullptr;
+    double *Tx = nullptr, *Ty = nullptr, *Tz = nullptr, *diag = nullptr, *dinv = nullptr;
+    double *r = nullptr, *z = nullptr, *p[2] = {nullptr, nullptr}, *q = nullptr;
+    float *K32 = nullptr, *cb32 = nullptr, *dinv32 = nullptr, *r32 = nullptr, *z32 = nullptr;
+    float *p32[2] = {nullptr, nullptr}, *q32 = nullptr, *d32 = nullptr;
+    double *partials = nullptr;
+    unsigned int *ticket = nullptr;
+    CgScal *sc = nullptr, *sc_in = nullptr;
+    StepResults *res = nullptr;
+    StepParams *sp = nullptr;
+    // pinned host mirrors
+    CgScal *sc_h = nullptr, *sc_in_h = nullptr;
+    StepResults *res_h = nullptr;
+    StepParams *sp_h = nullptr;
+
+    int kcur = 0;
+    bool closure_at_h = false;   // K[kcur], Can hold the closures at h (the accepted state)
+    bool soils_set = false, has_state = false;
+    double t = 0.0, dt_nom = 1.0;
+    int easy = 0;
+    long long steps = 0;
+    double storage0 = 0.0, in_cum = 0.0, out_cum = 0.0, closure_cum = 0.0, defect_cum = 0.0;
+    unsigned long long launches = 0;
+
+    void *dalloc(size_t bytes)
+    {
+        bytes = (bytes + 255) & ~size_t(255);
+        void *ptr = nullptr;
+        if (has_alloc) ptr = alloc.alloc(bytes, alloc.user);
+        else if (cudaMalloc(&ptr, bytes) != cudaSuccess) ptr = nullptr;
+        if (ptr) allocations.push_back(ptr);
+        return ptr;
+    }
+};
+
+namespace {
+
+template <class T>
+bool alloc_n(rf_ctx *c, T *&ptr, size_t n)
+{
+    ptr = static_cast<T *>(c->dalloc(sizeof(T) * (n ? n : 1)));
+    return ptr != nullptr;
+}
+
+rf_status check_params(const rf_solver_params *p)
+{
+    if (!(p->tol_picard > 0) || !(p->tol_cg > 0) || p->cg_max_it < 1 || !(p->dt0 > 0) || !(p->dt_max > 0) ||
+        !(p->dt_min > 0) || !(p->f_grow >= 1.0) || !(p->f_shrink > 1.0) || p->n_inc < 1 || p->n_small < 0 ||
+        p->n_max < 1 || !(p->eps_chord >= 0) || !(p->tol_inner > 0 && p->tol_inner < 1) || p->inner_max_it < 1 ||
+        p->outer_max_it < 1)
+        return fail(RF_ERR_ARG, "invalid solver parameters");
+    if (p->precision != RF_PREC_FP64 && p->precision != RF_PREC_MIXED)
+        return fail(RF_ERR_ARG, "unknown precision mode");
+    if (p->precond != RF_PRECOND_JACOBI)
+        return fail(RF_ERR_ARG, "only the Jacobi preconditioner is available in this build");
+    return RF_OK;
+}
+
+double series_at(const BcSeries &b, double t)
+{
+    size_t i = 0;
+    while (i + 1 < b.v.size() && b.t[i + 1] <= t + t_tol(t)) i++;
+    return b.v.empty() ? 0.0 : b.v[i];
+}
+
+double next_breakpoint(const rf_ctx *c, double t)
+{
+    double nb = INFINITY;
+    for (int f = 0; f < 6; f++)
+        for (double ti : c->bc[f].t)
+            if (ti > t + t_tol(t) && ti < nb) nb = ti;
+    return nb;
+}
+
+rf_status sync(rf_ctx *c)
+{
+    CUDA_TRY(cudaGetLastError());
+    CUDA_TRY(cudaStreamSynchronize(c->stream));
+    return RF_OK;
+}
+
+void fill_step_params(rf_ctx *c, double dt)
+{
+    StepParams &s = *c->sp_h;
+    s.dt = dt;
+    s.t = c->t;
+    s.eps_chord = c->prm.eps_chord;
+    for (int f = 0; f < 6; f++) {
+        s.bc_type[f] = c->bc[f].type;
+        s.bc_val[f] = c->bc[f].v.empty() ? 0.0 : series_at(c->bc[f], c->t);
+    }
+}
+
+// Closures at h_eval (optionally with max|h_eval - hprev|) into theta_out,
+// K[kout], Can.
+void run_closure(rf_ctx *c, const double *h_eval, const double *hprev, double *theta_out, int kout)
+{
+    launch_closure(c->stream, c->nblk, c->g, c->soils, c->zone, c->Ks, c->flags, h_eval, hprev, theta_out,
+                   c->K[kout], c->Can, c->partials, c->ticket, c->res);
+    c->launches++;
+}
+
+void run_assemble(rf_ctx *c, const double *hk, const double *hn, const double *thk, const double *thn)
+{
+    launch_assemble(c->stream, c->nblk, c->g, c->soils, c->zone, c->Ks, c->flags, c->sp, hk, hn, thk, thn,
+                    c->K[c->kcur], c->Can, c->c, c->b, c->Tx, c->Ty, c->Tz, c->diag, c->dinv, c->K32, c->cb32,
+                    c->dinv32);
+    c->launches++;
+}
+
+// Inner FP32 / FP64 CG iterations launched in growing chunks; the device
+// marks the solve done, later kernels return at once.
+template <class Launch>
+rf_status cg_loop(rf_ctx *c, CgScal *sc_dev, CgScal *sc_host, int max_it, Launch launch_iter)
+{
+    long long launched = 0;
+    int chunk = 2;
+    for (;;) {
+        for (int i = 0; i < chunk; i++, launched++) launch_iter(launched);
+        CUDA_TRY(cudaMemcpyAsync(sc_host, sc_dev, sizeof(CgScal), cudaMemcpyDeviceToHost, c->stream));
+        rf_status st = sync(c);
+        if (st) return st;
+        if (sc_host->done) return RF_OK;
+        if (launched > (long long)max_it + 64)
+            return fail(RF_ERR_DEVICE_TIMEOUT, "CG did not report completion within its iteration budget");
+        chunk = std::min(chunk * 2, 64);
+    }
+}
+
+// Solve the assembled system from x0 (device) into c->x.  *iters: CG (FP64)
+// or summed inner iterations (mixed).  Returns RF_OK, RF_ERR_CG (max_it /
+// non-finite), or a CUDA error.
+rf_status solve_system(rf_ctx *c, const double *x0, int *iters)
+{
+    const Grid &g = c->g;
+    *iters = 0;
+    if (c->prm.precision == RF_PREC_FP64) {
+        launch_cg64_init(c->stream, c->nblk, g, c->flags, x0, c->x, c->b, c->Tx, c->Ty, c->Tz, c->diag, c->dinv,
+                         c->r, c->z, c->prm.tol_cg, c->prm.cg_max_it, c->partials, c->ticket, c->sc);
+        c->launches++;
+        rf_status st = cg_loop(c, c->sc, c->sc_h, c->prm.cg_max_it, [&](long long it) {
+            double *pin = c->p[it & 1], *pout = c->p[(it + 1) & 1];
+            launch_cg64_spmv(c->stream, c->nblk, g, c->flags, c->z, pin, pout, c->q, c->Tx, c->Ty, c->Tz, c->diag,
+                             c->partials, c->ticket, c->sc);
+            launch_cg64_update(c->stream, c->nblk, g, c->x, c->r, c->z, pout, c->q, c->dinv, c->partials, c->ticket,
+                               c->sc);
+            c->launches += 2;
+        });
+        if (st) return st;
+        *iters = c->sc_h->iter;
+        if (c->sc_h->status != CG_OK) return fail(RF_ERR_CG, c->sc_h->status == CG_MAXIT ? "CG reached max_it" : "CG non-finite");
+        return RF_OK;
+    }
+    // mixed: FP64 defect correction around an FP32 inner PCG
+    if (x0 != c->x) CUDA_TRY(cudaMemcpyAsync(c->x, x0, sizeof(double) * g.N, cudaMemcpyDeviceToDevice, c->stream));
+    for (int outer = 0; outer < c->prm.outer_max_it; outer++) {
+        launch_resid64(c->stream, c->nblk, g, c->flags, c->x, c->b, c->Tx, c->Ty, c->Tz, c->diag, c->dinv32, c->r32,
+                       c->z32, c->d32, c->prm.tol_cg, c->prm.tol_inner, c->prm.inner_max_it, c->partials, c->ticket,
+                       c->sc, c->sc_in);
+        c->launches++;
+        CUDA_TRY(cudaMemcpyAsync(c->sc_h, c->sc, sizeof(CgScal), cudaMemcpyDeviceToHost, c->stream));
+        rf_status st = sync(c);
+        if (st) return st;
+        if (c->sc_h->status != CG_OK) return fail(RF_ERR_CG, "non-finite outer residual");
+        if (c->sc_h->done) return RF_OK;
+        st = cg_loop(c, c->sc_in, c->sc_in_h, c->prm.inner_max_it, [&](long long it) {
+            float *pin = c->p32[it & 1], *pout = c->p32[(it + 1) & 1];
+            launch_cg32_spmv(c->stream, c->nblk, g, c->z32, pin, pout, c->q32, c->K32, c->cb32, c->partials,
+                             c->ticket, c->sc_in);
+            launch_cg32_update(c->stream, c->nblk, g, c->d32, c->r32, c->z32, pout, c->q32, c->dinv32, c->partials,
+                               c->ticket, c->sc_in);
+            c->launches += 2;
+        });
+        if (st) return st;
+        *iters += c->sc_in_h->iter;
+        if (c->sc_in_h->status == CG_NONFINITE) return fail(RF_ERR_CG, "inner FP32 CG non-finite");
+        launch_add_correction(c->stream, c->nblk, g, c->x, c->d32);
+        c->launches++;
+    }
+    return fail(RF_ERR_CG, "defect correction reached outer_max_it");
+}
+
+struct Attempt {
+    bool converged = false;
+    int picard = 0, cg = 0;
+    rf_status status = RF_OK;
+    double max_dh = 0.0;
+    StepResults mb{};
+};
+
+// One Picard attempt at step size dt from the accepted state h (Sec. 2.2).
+rf_status attempt(rf_ctx *c, double dt, Attempt &A)
+{
+    fill_step_params(c, dt);
+    CUDA_TRY(cudaMemcpyAsync(c->sp, c->sp_h, sizeof(StepParams), cudaMemcpyHostToDevice, c->stream));
+    CUDA_TRY(cudaMemcpyAsync(c->hk, c->h, sizeof(double) * c->g.N, cudaMemcpyDeviceToDevice, c->stream));
+    if (!c->closure_at_h) {
+        run_closure(c, c->hk, nullptr, c->theta_k, c->kcur);
+        c->closure_at_h = true;
+    }
+    for (int it = 1; it <= c->prm.n_max; it++) {
+        run_assemble(c, c->hk, c->h, c->theta_k, c->theta_n);
+        int cg = 0;
+        rf_status st = solve_system(c, c->hk, &cg);
+        A.picard = it;
+        c->closure_at_h = false;
+        if (st == RF_ERR_CG) { A.status = RF_ERR_CG; break; }
+        if (st) return st;
+        A.cg += cg;
+        // closures at the new iterate, with the Picard update max|x - h^k|
+        const int knew = c->kcur ^ 1;
+        run_closure(c, c->x, c->hk, c->theta_k, knew);
+        CUDA_TRY(cudaMemcpyAsync(c->res_h, c->res, sizeof(StepResults), cudaMemcpyDeviceToHost, c->stream));
+        st = sync(c);
+        if (st) return st;
+        std::swap(c->hk, c->x);
+        const int kold = c->kcur;
+        c->kcur = knew;
+        A.max_dh = c->res_h->max_dh;
+        if (c->res_h->nonfinite) { A.status = RF_ERR_CG; break; }
+        if (A.max_dh <= c->prm.tol_picard) {
+            A.converged = true;
+            launch_mass_balance(c->stream, c->nblk, c->g, c->soils, c->zone, c->Ks, c->flags, c->sp, c->hk, c->h,
+                                c->c, c->K[kold], c->theta_k, c->theta_n, c->partials, c->ticket, c->res);
+            c->launches++;
+            CUDA_TRY(cudaMemcpyAsync(c->res_h, c->res, sizeof(StepResults), cudaMemcpyDeviceToHost, c->stream));
+            st = sync(c);
+            if (st) return st;
+            A.mb = *c->res_h;
+            break;
+        }
+    }
+    if (!A.converged && A.status == RF_OK) A.status = RF_ERR_PICARD;
+    return RF_OK;
+}
+
+void ebats_accept(rf_ctx *c, int picard)
+{
+    if (picard <= c->prm.n_small) c->easy++;
+    else c->easy = 0;
+    if (c->easy >= c->prm.n_inc) {
+        c->dt_nom = std::min(c->dt_nom * c->prm.f_grow, c->prm.dt_max);
+        c->easy = 0;
+    }
+}
+
+// One accepted step with EBATS reruns, clipped to t_stop.
+rf_status do_step(rf_ctx *c, double t_stop, rf_step_info *info)
+{
+    if (!c->soils_set || !c->has_state) return fail(RF_ERR_STATE, "set soils and state before stepping");
+    const double dt_nom0 = c->dt_nom;
+    const int easy0 = c->easy;
+    int rejected = 0, cg_total = 0;
+    for (;;) {
+        double dt = c->dt_nom;
+        const double bp = next_breakpoint(c, c->t);
+        if (bp - c->t < dt) dt = bp - c->t;
+        if (t_stop - c->t < dt) dt = t_stop - c->t;
+        Attempt A;
+        rf_status st = attempt(c, dt, A);
+        if (st) { c->dt_nom = dt_nom0; c->easy = easy0; return st; }
+        cg_total += A.cg;
+        if (A.converged) {
+            std::swap(c->h, c->hk);
+            std::swap(c->theta_n, c->theta_k);
+            c->closure_at_h = true;
+            double tn = c->t + dt;
+            if (std::fabs(tn - bp) <= t_tol(tn)) tn = bp;
+            if (std::fabs(tn - t_stop) <= t_tol(tn)) tn = t_stop;
+            c->t = tn;
+            c->steps++;
+            const double net = A.mb.bnd_in - A.mb.bnd_out;
+            c->in_cum += A.mb.bnd_in;
+            c->out_cum += A.mb.bnd_out;
+            c->closure_cum += A.mb.lin_change - net;
+            c->defect_cum += A.mb.dstore - net;
+            ebats_accept(c, A.picard);
+            if (info) {
+                info->dt = dt;
+                info->t = c->t;
+                info->picard_iters = A.picard;
+                info->cg_iters = cg_total;
+                info->rejected = rejected;
+                info->max_dh = A.max_dh;
+            }
+            return RF_OK;
+        }
+        rejected++;
+        c->dt_nom = dt / c->prm.f_shrink;
+        c->easy = 0;
+        if (c->dt_nom < c->prm.dt_min) {
+            c->dt_nom = dt_nom0;
+            c->easy = easy0;
+            return fail(RF_ERR_DT_MIN, "EBATS: dt fell below dt_min without Picard convergence at t = " +
+                                           std::to_string(c->t));
+        }
+    }
+}
+
+rf_status storage_of_theta_n(rf_ctx *c, double *out)
+{
+    launch_storage(c->stream, c->nblk, c->g, c->flags, c->theta_n, c->partials, c->ticket, c->res);
+    c->launches++;
+    CUDA_TRY(cudaMemcpyAsync(c->res_h, c->res, sizeof(StepResults), cudaMemcpyDeviceToHost, c->stream));
+    rf_status st = sync(c);
+    if (st) return st;
+    *out = c->res_h->storage;
+    return RF_OK;
+}
+
+}  // namespace
+
+// =========================================================================
+extern "C" {
+
+void rf_default_params(rf_solver_params *p)
+{
+    if (!p) return;
+    p->tol_picard = 1e-6;
+    p->tol_cg = 1e-10;
+    p->cg_max_it = 10000;
+    p->precond = RF_PRECOND_JACOBI;
+    p->precision = RF_PREC_FP64;
+    p->dt0 = 1.0;
+    p->dt_max = 600.0;
+    p->dt_min = 1e-3;
+    p->f_grow = 1.3;
+    p->f_shrink = 1.3;
+    p->n_inc = 10;
+    p->n_small = 3;
+    p->n_max = 8;
+    p->eps_chord = 1e-10;
+    p->tol_inner = 1e-4;
+    p->inner_max_it = 2000;
+    p->outer_max_it = 30;
+}
+
+const char *rf_last_error(void) { return g_err.c_str(); }
+
+rf_status rf_mesh_create(const rf_mesh_desc *mesh, const rf_solver_params *params, void *cuda_stream,
+                         const rf_allocator *alloc, rf_ctx **out)
+{
+    if (!mesh || !out) return fail(RF_ERR_ARG, "null argument");
+    *out = nullptr;
+    if (mesh->nx < 1 || mesh->ny < 1 || mesh->nz < 1 || !(mesh->dx > 0) || !(mesh->dy > 0) || !(mesh->dz > 0))
+        return fail(RF_ERR_ARG, "mesh sizes and spacings must be positive");
+    const long long N = (long long)mesh->nx * mesh->ny * mesh->nz;
+    if (N > (1LL << 31) - 1) return fail(RF_ERR_ARG, "mesh too large (more than 2^31-1 cells)");
+    rf_solver_params prm;
+    rf_default_params(&prm);
+    if (params) prm = *params;
+    if (rf_status st = check_params(&prm)) return st;
+
+    int ndev = 0;
+    if (cudaGetDeviceCount(&ndev) != cudaSuccess || ndev < 1) {
+        cudaGetLastError();
+        return fail(RF_ERR_NO_DEVICE, "no CUDA device visible; this library has no CPU fallback");
+    }
+    int dev = 0;
+    CUDA_TRY(cudaGetDevice(&dev));
+    cudaDeviceProp prop;
+    CUDA_TRY(cudaGetDeviceProperties(&prop, dev));
+    if (prop.major != 10 || prop.minor != 3)
+        return fail(RF_ERR_NO_DEVICE, std::string("device is sm_") + std::to_string(prop.major * 10 + prop.minor) +
+                                          "; this library is built for sm_103a (GB300) only");
+
+    rf_ctx *c = new rf_ctx();
+    c->device = dev;
+    c->num_sms = prop.multiProcessorCount;
+    c->stream = static_cast<cudaStream_t>(cuda_stream);
+    if (alloc && alloc->alloc && alloc->free) { c->alloc = *alloc; c->has_alloc = true; }
+    c->prm = prm;
+
+    Grid &g = c->g;
+    g.nx = mesh->nx; g.ny = mesh->ny; g.nz = mesh->nz;
+    g.N = N;
+    g.sxy = (long long)mesh->nx * mesh->ny;
+    g.V = mesh->dx * mesh->dy * mesh->dz;
+    const double A[6] = {mesh->dy * mesh->dz, mesh->dy * mesh->dz, mesh->dx * mesh->dz, mesh->dx * mesh->dz,
+                         mesh->dx * mesh->dy, mesh->dx * mesh->dy};
+    const double d[6] = {mesh->dx, mesh->dx, mesh->dy, mesh->dy, mesh->dz, mesh->dz};
+    for (int f = 0; f < 6; f++) {
+        g.A[f] = A[f];
+        g.w[f] = A[f] / d[f];
+        g.wb[f] = A[f] / (0.5 * d[f]);
+    }
+    for (int a = 0; a < 3; a++) g.w32[a] = (float)(A[2 * a] / d[2 * a]);
+    // grid: at most 8 resident blocks of 256 threads per SM
+    const long long want = (N + RED_THREADS - 1) / RED_THREADS;
+    c->nblk = (int)std::max(1LL, std::min(want, (long long)c->num_sms * 8));
+
+    // flags: active bit + boundary faces (domain edge, or a z-face whose
+    // neighbour is inactive); lateral faces touching an inactive cell are closed
+    c->flags_h.assign(N, 0);
+    auto act = [&](long long p) { return mesh->active ? mesh->active[p] != 0 : true; };
+    for (int k = 0; k < g.nz; k++)
+        for (int j = 0; j < g.ny; j++)
+            for (int i = 0; i < g.nx; i++) {
+                const long long p = i + (long long)g.nx * (j + (long long)g.ny * k);
+                if (!act(p)) continue;
+                uint8_t fl = FLAG_ACTIVE;
+                if (i == 0) fl |= 1u << F_XMIN;
+                if (i == g.nx - 1) fl |= 1u << F_XMAX;
+                if (j == 0) fl |= 1u << F_YMIN;
+                if (j == g.ny - 1) fl |= 1u << F_YMAX;
+                if (k == 0 || !act(p - g.sxy)) fl |= 1u << F_ZMIN;
+                if (k == g.nz - 1 || !act(p + g.sxy)) fl |= 1u << F_ZMAX;
+                c->flags_h[p] = fl;
+                c->n_active++;
+            }
+
+    bool ok = alloc_n(c, c->flags, N) && alloc_n(c, c->zone, N) && alloc_n(c, c->Ks, N) &&
+              alloc_n(c, c->soils, 256) && alloc_n(c, c->h, N) && alloc_n(c, c->hk, N) && alloc_n(c, c->x, N) &&
+              alloc_n(c, c->theta_n, N) && alloc_n(c, c->theta_k, N) && alloc_n(c, c->K[0], N) &&
+              alloc_n(c, c->K[1], N) && alloc_n(c, c->Can, N) && alloc_n(c, c->c, N) && alloc_n(c, c->b, N) &&
+              alloc_n(c, c->Tx, N) && alloc_n(c, c->Ty, N) && alloc_n(c, c->Tz, N) && alloc_n(c, c->diag, N) &&
+              alloc_n(c, c->dinv, N) && alloc_n(c, c->r, N) && alloc_n(c, c->z, N) && alloc_n(c, c->p[0], N) &&
+              alloc_n(c, c->p[1], N) && alloc_n(c, c->q, N) && alloc_n(c, c->K32, N) && alloc_n(c, c->cb32, N) &&
+              alloc_n(c, c->dinv32, N) && alloc_n(c, c->r32, N) && alloc_n(c, c->z32, N) &&
+              alloc_n(c, c->p32[0], N) && alloc_n(c, c->p32[1], N) && alloc_n(c, c->q32, N) &&
+              alloc_n(c, c->d32, N) && alloc_n(c, c->partials, (size_t)8 * c->nblk) && alloc_n(c, c->ticket, 64) &&
+              alloc_n(c, c->sc, 1) && alloc_n(c, c->sc_in, 1) && alloc_n(c, c->res, 1) && alloc_n(c, c->sp, 1);
+    if (!ok) {
+        rf_destroy(c);
+        return fail(RF_ERR_NOMEM, "device allocation failed");
+    }
+    if (cudaMallocHost(&c->sc_h, sizeof(CgScal)) != cudaSuccess ||
+        cudaMallocHost(&c->sc_in_h, sizeof(CgScal)) != cudaSuccess ||
+        cudaMallocHost(&c->res_h, sizeof(StepResults)) != cudaSuccess ||
+        cudaMallocHost(&c->sp_h, sizeof(StepParams)) != cudaSuccess) {
+        rf_destroy(c);
+        return fail(RF_ERR_NOMEM, "pinned host allocation failed");
+    }
+    cudaError_t e = cudaMemcpyAsync(c->flags, c->flags_h.data(), N, cudaMemcpyHostToDevice, c->stream);
+    if (e == cudaSuccess) e = cudaMemsetAsync(c->ticket, 0, 64 * sizeof(unsigned int), c->stream);
+    // vectors whose inactive entries must read as zero
+    for (double *v : {c->p[0], c->p[1], c->q, c->r, c->z, c->h, c->hk, c->x})
+        if (e == cudaSuccess) e = cudaMemsetAsync(v, 0, sizeof(double) * N, c->stream);
+    for (float *v : {c->p32[0], c->p32[1], c->q32, c->r32, c->z32, c->d32})
+        if (e == cudaSuccess) e = cudaMemsetAsync(v, 0, sizeof(float) * N, c->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+    if (e != cudaSuccess) {
+        rf_destroy(c);
+        return fail(RF_ERR_CUDA, std::string("initialisation: ") + cudaGetErrorString(e));
+    }
+    *out = c;
+    return RF_OK;
+}
+
+void rf_destroy(rf_ctx *c)
+{
+    if (!c) return;
+    cudaStreamSynchronize(c->stream);
+    for (void *ptr : c->allocations) {
+        if (c->has_alloc) c->alloc.free(ptr, c->alloc.user);
+        else cudaFree(ptr);
+    }
+    if (c->sc_h) cudaFreeHost(c->sc_h);
+    if (c->sc_in_h) cudaFreeHost(c->sc_in_h);
+    if (c->res_h) cudaFreeHost(c->res_h);
+    if (c->sp_h) cudaFreeHost(c->sp_h);
+    delete c;
+}
+
+rf_status rf_set_params(rf_ctx *c, const rf_solver_params *params)
+{
+    if (!c || !params) return fail(RF_ERR_ARG, "null argument");
+    if (rf_status st = check_params(params)) return st;
+    c->prm = *params;
+    return RF_OK;
+}
+
+rf_status rf_soil_set(rf_ctx *c, const rf_soil *zones, int n_zones, const uint8_t *zone_of_cell,
+                      const double *Ks_cell)
+{
+    if (!c || !zones || n_zones < 1 || n_zones > 256) return fail(RF_ERR_ARG, "need 1..256 soil zones");
+    std::vector<DevSoil> soils(256);
+    for (int z = 0; z < n_zones; z++) {
+        const rf_soil &s = zones[z];
+        if ((s.model != RF_VG && s.model != RF_GARDNER) || !(s.theta_s > s.theta_r) || !(s.alpha > 0) ||
+            !(s.Ks > 0) || !(s.S >= 0) || (s.model == RF_VG && !(s.n > 1.0)))
+            return fail(RF_ERR_ARG, "invalid soil parameters in zone " + std::to_string(z));
+        soils[z] = DevSoil{s.model, s.theta_r, s.theta_s, s.alpha, s.n, s.model == RF_VG ? 1.0 - 1.0 / s.n : 0.0, s.S};
+    }
+    const long long N = c->g.N;
+    std::vector<uint8_t> zone(N, 0);
+    std::vector<double> Ks(N);
+    for (long long p = 0; p < N; p++) {
+        const int z = zone_of_cell ? zone_of_cell[p] : 0;
+        if (z >= n_zones) return fail(RF_ERR_ARG, "zone_of_cell refers to an undefined zone");
+        zone[p] = (uint8_t)z;
+        Ks[p] = Ks_cell ? Ks_cell[p] : zones[z].Ks;
+        if (c->flags_h[p] && !(Ks[p] > 0)) return fail(RF_ERR_ARG, "Ks_cell must be positive on active cells");
+    }
+    CUDA_TRY(cudaMemcpyAsync(c->soils, soils.data(), sizeof(DevSoil) * 256, cudaMemcpyHostToDevice, c->stream));
+    CUDA_TRY(cudaMemcpyAsync(c->zone, zone.data(), N, cudaMemcpyHostToDevice, c->stream));
+    CUDA_TRY(cudaMemcpyAsync(c->Ks, Ks.data(), sizeof(double) * N, cudaMemcpyHostToDevice, c->stream));
+    if (rf_status st = sync(c)) return st;
+    c->soils_set = true;
+    c->has_state = false;   // closures depend on the soils: state must be set again
+    c->closure_at_h = false;
+    return RF_OK;
+}
+
+rf_status rf_bc_set(rf_ctx *c, rf_face face, rf_bc_type type, const double *t, const double *v, int n)
+{
+    if (!c || face < RF_XMIN || face > RF_ZMAX) return fail(RF_ERR_ARG, "bad face");
+    if (type < RF_BC_ZERO_FLUX || type > RF_BC_SEEPAGE) return fail(RF_ERR_ARG, "bad boundary type");
+    if (type == RF_BC_FREE_DRAINAGE && face != RF_ZMIN) return fail(RF_ERR_ARG, "free drainage is a bottom (ZMIN) condition");
+    if ((type == RF_BC_DIRICHLET || type == RF_BC_FLUX) && (n < 1 || !v))
+        return fail(RF_ERR_ARG, "Dirichlet and flux conditions need a value series");
+    if (n > 1 && !t) return fail(RF_ERR_ARG, "a series of more than one value needs breakpoints");
+    BcSeries b;
+    b.type = type;
+    if (v && n > 0) {
+        for (int i = 0; i < n; i++) {
+            b.t.push_back(t ? t[i] : 0.0);
+            b.v.push_back(v[i]);
+            if (!std::isfinite(v[i]) || !std::isfinite(b.t.back())) return fail(RF_ERR_ARG, "non-finite series");
+            if (i > 0 && !(b.t[i] > b.t[i - 1])) return fail(RF_ERR_ARG, "breakpoints must increase strictly");
+        }
+    }
+    c->bc[face] = b;
+    return RF_OK;
+}
+
+static rf_status state_set_common(rf_ctx *c, double t)
+{
+    c->t = t;
+    c->dt_nom = std::min(c->prm.dt0, c->prm.dt_max);
+    c->easy = 0;
+    c->steps = 0;
+    run_closure(c, c->h, nullptr, c->theta_n, c->kcur);
+    c->closure_at_h = true;
+    double st0 = 0.0;
+    if (rf_status st = storage_of_theta_n(c, &st0)) return st;
+    c->storage0 = st0;
+    c->in_cum = c->out_cum = c->closure_cum = c->defect_cum = 0.0;
+    c->has_state = true;
+    return RF_OK;
+}
+
+rf_status rf_state_set(rf_ctx *c, const double *h, double t)
+{
+    if (!c || !h) return fail(RF_ERR_ARG, "null argument");
+    if (!c->soils_set) return fail(RF_ERR_STATE, "call rf_soil_set before rf_state_set");
+    if (!std::isfinite(t)) return fail(RF_ERR_ARG, "non-finite time");
+    std::vector<double> hh(h, h + c->g.N);
+    for (long long p = 0; p < c->g.N; p++) {
+        if (c->flags_h[p] && !std::isfinite(hh[p])) return fail(RF_ERR_ARG, "non-finite head on an active cell");
+        if (!c->flags_h[p] && !std::isfinite(hh[p])) hh[p] = 0.0;
+    }
+    CUDA_TRY(cudaMemcpyAsync(c->h, hh.data(), sizeof(double) * c->g.N, cudaMemcpyHostToDevice, c->stream));
+    return state_set_common(c, t);
+}
+
+rf_status rf_state_set_device(rf_ctx *c, const double *d_h, double t)
+{
+    if (!c || !d_h) return fail(RF_ERR_ARG, "null argument");
+    if (!c->soils_set) return fail(RF_ERR_STATE, "call rf_soil_set before rf_state_set_device");
+    CUDA_TRY(cudaMemcpyAsync(c->h, d_h, sizeof(double) * c->g.N, cudaMemcpyDeviceToDevice, c->stream));
+    return state_set_common(c, t);
+}
+
+rf_status rf_state_get(rf_ctx *c, double *h, rf_state_meta *meta)
+{
+    if (!c) return fail(RF_ERR_ARG, "null context");
+    if (h) {
+        CUDA_TRY(cudaMemcpyAsync(h, c->h, sizeof(double) * c->g.N, cudaMemcpyDeviceToHost, c->stream));
+        if (rf_status st = sync(c)) return st;
+    }
+    if (meta) {
+        meta->t = c->t;
+        meta->dt_nom = c->dt_nom;
+        meta->easy = c->easy;
+        meta->n_active = c->n_active;
+        meta->steps = c->steps;
+    }
+    return RF_OK;
+}
+
+rf_status rf_state_get_device(rf_ctx *c, double *d_h)
+{
+    if (!c || !d_h) return fail(RF_ERR_ARG, "null argument");
+    CUDA_TRY(cudaMemcpyAsync(d_h, c->h, sizeof(double) * c->g.N, cudaMemcpyDeviceToDevice, c->stream));
+    return sync(c);
+}
+
+rf_status rf_state_meta_set(rf_ctx *c, const rf_state_meta *meta, const double *mass7)
+{
+    if (!c || !meta) return fail(RF_ERR_ARG, "null argument");
+    if (!c->has_state) return fail(RF_ERR_STATE, "set the state first");
+    c->t = meta->t;
+    c->dt_nom = meta->dt_nom;
+    c->easy = meta->easy;
+    c->steps = meta->steps;
+    if (mass7) {
+        c->storage0 = mass7[0];
+        c->in_cum = mass7[2];
+        c->out_cum = mass7[3];
+        c->closure_cum = mass7[4];
+        c->defect_cum = mass7[6];
+    }
+    return RF_OK;
+}
+
+rf_status rf_step(rf_ctx *c, rf_step_info *out)
+{
+    if (!c) return fail(RF_ERR_ARG, "null context");
+    return do_step(c, INFINITY, out);
+}
+
+rf_status rf_run(rf_ctx *c, double t_end, rf_run_stats *stats, rf_step_info *log, int log_cap)
+{
+    if (!c) return fail(RF_ERR_ARG, "null context");
+    if (!std::isfinite(t_end)) return fail(RF_ERR_ARG, "non-finite t_end");
+    rf_run_stats s{};
+    rf_status st = RF_OK;
+    while (c->t < t_end - t_tol(t_end)) {
+        rf_step_info info{};
+        st = do_step(c, t_end, &info);
+        if (st) break;
+        if (log && s.steps < log_cap) log[s.steps] = info;
+        s.steps++;
+        s.picard_iters += info.picard_iters;
+        s.cg_iters += info.cg_iters;
+        s.rejected += info.rejected;
+    }
+    if (stats) *stats = s;
+    return st;
+}
+
+rf_status rf_mass_balance(rf_ctx *c, rf_mass_balance_t *out)
+{
+    if (!c || !out) return fail(RF_ERR_ARG, "null argument");
+    if (!c->has_state) return fail(RF_ERR_STATE, "no state");
+    double st = 0.0;
+    if (rf_status s = storage_of_theta_n(c, &st)) return s;
+    out->storage0 = c->storage0;
+    out->storage = st;
+    out->inflow_cum = c->in_cum;
+    out->outflow_cum = c->out_cum;
+    out->closure_abs = std::fabs(c->closure_cum);
+    out->closure_rel = out->closure_abs / (c->storage0 + c->in_cum + c->out_cum);
+    out->nonlinear_defect_cum = c->defect_cum;
+    return RF_OK;
+}
+
+rf_status rf_assemble(rf_ctx *c, const double *d_hk, const double *d_hn, double dt, double t, double *d_K,
+                      double *d_theta, double *d_c, double *d_b, double *d_diag)
+{
+    if (!c || !d_hk || !d_hn || !(dt > 0)) return fail(RF_ERR_ARG, "bad argument");
+    if (!c->soils_set) return fail(RF_ERR_STATE, "soils not set");
+    const double t_save = c->t;
+    c->t = t;
+    fill_step_params(c, dt);
+    c->t = t_save;
+    CUDA_TRY(cudaMemcpyAsync(c->sp, c->sp_h, sizeof(StepParams), cudaMemcpyHostToDevice, c->stream));
+    // theta*(h^n) into theta_n's scratch twin, then closures at h^k
+    run_closure(c, d_hn, nullptr, c->theta_n, c->kcur);
+    run_closure(c, d_hk, nullptr, c->theta_k, c->kcur);
+    run_assemble(c, d_hk, d_hn, c->theta_k, c->theta_n);
+    c->closure_at_h = false;
+    c->has_state = false;    // theta_n was overwritten: the state must be set again before stepping
+    const size_t nb = sizeof(double) * c->g.N;
+    if (d_K) CUDA_TRY(cudaMemcpyAsync(d_K, c->K[c->kcur], nb, cudaMemcpyDeviceToDevice, c->stream));
+    if (d_theta) CUDA_TRY(cudaMemcpyAsync(d_theta, c->theta_k, nb, cudaMemcpyDeviceToDevice, c->stream));
+    if (d_c) CUDA_TRY(cudaMemcpyAsync(d_c, c->c, nb, cudaMemcpyDeviceToDevice, c->stream));
+    if (d_b) CUDA_TRY(cudaMemcpyAsync(d_b, c->b, nb, cudaMemcpyDeviceToDevice, c->stream));
+    if (d_diag) CUDA_TRY(cudaMemcpyAsync(d_diag, c->diag, nb, cudaMemcpyDeviceToDevice, c->stream));
+    return sync(c);
+}
+
+rf_status rf_apply(rf_ctx *c, const double *d_x, double *d_y)
+{
+    if (!c || !d_x || !d_y) return fail(RF_ERR_ARG, "null argument");
+    launch_apply64(c->stream, c->nblk, c->g, c->flags, d_x, d_y, c->Tx, c->Ty, c->Tz, c->diag);
+    c->launches++;
+    return sync(c);
+}
+
+rf_status rf_solve(rf_ctx *c, double *d_x, int *iters)
+{
+    if (!c || !d_x) return fail(RF_ERR_ARG, "null argument");
+    int it = 0;
+    CUDA_TRY(cudaMemcpyAsync(c->hk, d_x, sizeof(double) * c->g.N, cudaMemcpyDeviceToDevice, c->stream));
+    rf_status st = solve_system(c, c->hk, &it);
+    if (iters) *iters = it;
+    if (st) return st;
+    CUDA_TRY(cudaMemcpyAsync(d_x, c->x, sizeof(double) * c->g.N, cudaMemcpyDeviceToDevice, c->stream));
+    c->has_state = false;   // hk was used as scratch
+    return sync(c);
+}
+
+unsigned long long rf_launch_count(rf_ctx *c) { return c ? c->launches : 0ULL; }
+
+}  // extern "C"

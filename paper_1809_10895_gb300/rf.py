@@ -1,0 +1,325 @@
+"""Thin ctypes binding of the C ABI in ``include/rf.h`` (``_build/librf.so``).
+
+Argument marshalling only: every step of the numerical path runs in the CUDA
+kernels behind the ABI.  PyTorch supplies device memory (through the ABI's
+allocator callback, so the library's buffers come from torch's caching
+allocator) and the CUDA stream.  There is no CPU fallback: loading fails
+loudly when the library is missing, and creating a solver fails without an
+sm_103 GPU.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+from dataclasses import dataclass
+from typing import Optional
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "_build", "librf.so")
+
+RF_OK, RF_ERR_ARG, RF_ERR_NO_DEVICE, RF_ERR_CUDA, RF_ERR_NOMEM, RF_ERR_STATE, RF_ERR_PICARD, \
+    RF_ERR_DT_MIN, RF_ERR_CG, RF_ERR_DEVICE_TIMEOUT = range(10)
+STATUS_NAMES = ("RF_OK", "RF_ERR_ARG", "RF_ERR_NO_DEVICE", "RF_ERR_CUDA", "RF_ERR_NOMEM", "RF_ERR_STATE",
+                "RF_ERR_PICARD", "RF_ERR_DT_MIN", "RF_ERR_CG", "RF_ERR_DEVICE_TIMEOUT")
+RF_VG, RF_GARDNER = 0, 1
+FACES = {"xmin": 0, "xmax": 1, "ymin": 2, "ymax": 3, "zmin": 4, "zmax": 5}
+BC_TYPES = {"zero_flux": 0, "dirichlet": 1, "flux": 2, "free_drainage": 3, "seepage": 4}
+MODELS = {"vg": RF_VG, "gardner": RF_GARDNER}
+PRECISION = {"fp64": 0, "mixed": 1}
+PRECOND = {"jacobi": 0, "mg": 1}
+
+
+class rf_solver_params(C.Structure):
+    _fields_ = [("tol_picard", C.c_double), ("tol_cg", C.c_double), ("cg_max_it", C.c_int),
+                ("precond", C.c_int), ("precision", C.c_int), ("dt0", C.c_double), ("dt_max", C.c_double),
+                ("dt_min", C.c_double), ("f_grow", C.c_double), ("f_shrink", C.c_double), ("n_inc", C.c_int),
+                ("n_small", C.c_int), ("n_max", C.c_int), ("eps_chord", C.c_double), ("tol_inner", C.c_double),
+                ("inner_max_it", C.c_int), ("outer_max_it", C.c_int)]
+
+
+class rf_mesh_desc(C.Structure):
+    _fields_ = [("nx", C.c_int), ("ny", C.c_int), ("nz", C.c_int), ("dx", C.c_double), ("dy", C.c_double),
+                ("dz", C.c_double), ("z_bottom", C.c_double), ("active", C.POINTER(C.c_uint8))]
+
+
+ALLOC_FN = C.CFUNCTYPE(C.c_void_p, C.c_size_t, C.c_void_p)
+FREE_FN = C.CFUNCTYPE(None, C.c_void_p, C.c_void_p)
+
+
+class rf_allocator(C.Structure):
+    _fields_ = [("alloc", ALLOC_FN), ("free", FREE_FN), ("user", C.c_void_p)]
+
+
+class rf_soil(C.Structure):
+    _fields_ = [("model", C.c_int), ("theta_r", C.c_double), ("theta_s", C.c_double), ("alpha", C.c_double),
+                ("n", C.c_double), ("Ks", C.c_double), ("S", C.c_double)]
+
+
+class rf_state_meta(C.Structure):
+    _fields_ = [("t", C.c_double), ("dt_nom", C.c_double), ("easy", C.c_int), ("n_active", C.c_int),
+                ("steps", C.c_longlong)]
+
+
+class rf_step_info(C.Structure):
+    _fields_ = [("dt", C.c_double), ("t", C.c_double), ("picard_iters", C.c_int), ("cg_iters", C.c_int),
+                ("rejected", C.c_int), ("max_dh", C.c_double)]
+
+
+class rf_run_stats(C.Structure):
+    _fields_ = [("steps", C.c_longlong), ("picard_iters", C.c_longlong), ("cg_iters", C.c_longlong),
+                ("rejected", C.c_longlong)]
+
+
+class rf_mass_balance_t(C.Structure):
+    _fields_ = [(k, C.c_double) for k in ("storage0", "storage", "inflow_cum", "outflow_cum", "closure_abs",
+                                          "closure_rel", "nonlinear_defect_cum")]
+
+
+# name -> (restype, argtypes): the functions declared in include/rf.h
+_VP, _DP, _U8P = C.c_void_p, C.POINTER(C.c_double), C.POINTER(C.c_uint8)
+SIGNATURES = {
+    "rf_default_params": (None, [C.POINTER(rf_solver_params)]),
+    "rf_last_error": (C.c_char_p, []),
+    "rf_mesh_create": (C.c_int, [C.POINTER(rf_mesh_desc), C.POINTER(rf_solver_params), _VP,
+                                 C.POINTER(rf_allocator), C.POINTER(_VP)]),
+    "rf_destroy": (None, [_VP]),
+    "rf_set_params": (C.c_int, [_VP, C.POINTER(rf_solver_params)]),
+    "rf_soil_set": (C.c_int, [_VP, C.POINTER(rf_soil), C.c_int, _U8P, _DP]),
+    "rf_bc_set": (C.c_int, [_VP, C.c_int, C.c_int, _DP, _DP, C.c_int]),
+    "rf_state_set": (C.c_int, [_VP, _DP, C.c_double]),
+    "rf_state_set_device": (C.c_int, [_VP, _VP, C.c_double]),
+    "rf_state_get": (C.c_int, [_VP, _DP, C.POINTER(rf_state_meta)]),
+    "rf_state_get_device": (C.c_int, [_VP, _VP]),
+    "rf_state_meta_set": (C.c_int, [_VP, C.POINTER(rf_state_meta), _DP]),
+    "rf_step": (C.c_int, [_VP, C.POINTER(rf_step_info)]),
+    "rf_run": (C.c_int, [_VP, C.c_double, C.POINTER(rf_run_stats), C.POINTER(rf_step_info), C.c_int]),
+    "rf_mass_balance": (C.c_int, [_VP, C.POINTER(rf_mass_balance_t)]),
+    "rf_assemble": (C.c_int, [_VP, _VP, _VP, C.c_double, C.c_double, _VP, _VP, _VP, _VP, _VP]),
+    "rf_apply": (C.c_int, [_VP, _VP, _VP]),
+    "rf_solve": (C.c_int, [_VP, _VP, C.POINTER(C.c_int)]),
+    "rf_launch_count": (C.c_ulonglong, [_VP]),
+}
+
+_lib = None
+
+
+def load(path: str = LIB_PATH):
+    """Load the CUDA library; raises if it has not been built."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(path):
+            raise RuntimeError(f"CUDA library not built: {path} is missing (run __graft_entry__.build()); "
+                               "there is no CPU fallback")
+        L = C.CDLL(path)
+        for name, (res, args) in SIGNATURES.items():
+            fn = getattr(L, name)
+            fn.restype = res
+            fn.argtypes = args
+        _lib = L
+    return _lib
+
+
+class RFError(RuntimeError):
+    def __init__(self, status: int, where: str):
+        msg = load().rf_last_error().decode(errors="replace")
+        super().__init__(f"{where}: {STATUS_NAMES[status] if 0 <= status < len(STATUS_NAMES) else status}: {msg}")
+        self.status = status
+
+
+def _check(st: int, where: str):
+    if st != RF_OK:
+        raise RFError(st, where)
+
+
+def default_params(**kw) -> rf_solver_params:
+    p = rf_solver_params()
+    load().rf_default_params(C.byref(p))
+    for k, v in kw.items():
+        if k == "precision" and isinstance(v, str):
+            v = PRECISION[v]
+        if k == "precond" and isinstance(v, str):
+            v = PRECOND[v]
+        setattr(p, k, v)
+    return p
+
+
+def _dptr(a: Optional[np.ndarray]):
+    return None if a is None else a.ctypes.data_as(_DP)
+
+
+class TorchAllocator:
+    """Device memory for the library from torch's caching allocator."""
+
+    def __init__(self, device):
+        import torch
+        self.torch = torch
+        self.device = device
+        self.blocks = {}
+        self._alloc = ALLOC_FN(self._do_alloc)
+        self._free = FREE_FN(self._do_free)
+        self.struct = rf_allocator(self._alloc, self._free, None)
+
+    def _do_alloc(self, nbytes, user):
+        t = self.torch.empty(int(nbytes), dtype=self.torch.uint8, device=self.device)
+        ptr = t.data_ptr()
+        self.blocks[ptr] = t
+        return ptr
+
+    def _do_free(self, ptr, user):
+        self.blocks.pop(ptr, None)
+
+
+@dataclass
+class StepInfo:
+    dt: float
+    t: float
+    picard: int
+    cg: int
+    rejected: int
+    max_dh: float
+
+    @staticmethod
+    def of(s: rf_step_info) -> "StepInfo":
+        return StepInfo(s.dt, s.t, s.picard_iters, s.cg_iters, s.rejected, s.max_dh)
+
+
+class Solver:
+    """One solver context on the current CUDA device and torch stream."""
+
+    def __init__(self, nx, ny, nz, dx, dy, dz, z_bottom=0.0, active=None, params=None, stream=None,
+                 use_torch_allocator=True):
+        import torch
+        L = load()
+        self.shape = (nx, ny, nz)
+        self.N = nx * ny * nz
+        self.device = torch.device("cuda", torch.cuda.current_device())
+        self._active = None if active is None else np.ascontiguousarray(active, dtype=np.uint8).ravel()
+        desc = rf_mesh_desc(nx, ny, nz, dx, dy, dz, z_bottom,
+                            None if self._active is None else self._active.ctypes.data_as(_U8P))
+        self.params = params if params is not None else default_params()
+        self.stream = stream if stream is not None else torch.cuda.current_stream()
+        self._allocator = TorchAllocator(self.device) if use_torch_allocator else None
+        h = _VP()
+        _check(L.rf_mesh_create(C.byref(desc), C.byref(self.params), C.c_void_p(self.stream.cuda_stream),
+                                C.byref(self._allocator.struct) if self._allocator else None, C.byref(h)),
+               "rf_mesh_create")
+        self.ctx = h
+
+    def close(self):
+        if getattr(self, "ctx", None):
+            load().rf_destroy(self.ctx)
+            self.ctx = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    # -- set-up
+    @classmethod
+    def from_case(cls, case, **param_overrides) -> "Solver":
+        """Build a solver from a workloads.Case (mesh, soils, BCs, params, state)."""
+        p = dict(case.params)
+        p.update(param_overrides)
+        s = cls(case.nx, case.ny, case.nz, case.dx, case.dy, case.dz, case.z_bottom, case.active,
+                params=default_params(**p))
+        s.set_soils(case.soils, case.zone_of_cell, case.Ks_cell)
+        for bc in case.bcs:
+            s.set_bc(bc.face, bc.type, bc.t, bc.v)
+        s.set_state(case.h0, case.t0)
+        return s
+
+    def set_params(self, **kw):
+        p = self.params
+        for k, v in kw.items():
+            if k == "precision" and isinstance(v, str):
+                v = PRECISION[v]
+            setattr(p, k, v)
+        _check(load().rf_set_params(self.ctx, C.byref(p)), "rf_set_params")
+
+    def set_soils(self, soils, zone_of_cell=None, Ks_cell=None):
+        arr = (rf_soil * len(soils))()
+        for i, s in enumerate(soils):
+            arr[i] = rf_soil(MODELS[s.get("model", "vg")], s["theta_r"], s["theta_s"], s["alpha"],
+                             s.get("n", 2.0), s["Ks"], s.get("S", 1e-5))
+        z = None if zone_of_cell is None else np.ascontiguousarray(zone_of_cell, dtype=np.uint8).ravel()
+        k = None if Ks_cell is None else np.ascontiguousarray(Ks_cell, dtype=np.float64).ravel()
+        _check(load().rf_soil_set(self.ctx, arr, len(soils), None if z is None else z.ctypes.data_as(_U8P),
+                                  _dptr(k)), "rf_soil_set")
+
+    def set_bc(self, face, type_, t=None, v=None):
+        if v is None:
+            _check(load().rf_bc_set(self.ctx, FACES[face], BC_TYPES[type_], None, None, 0), "rf_bc_set")
+            return
+        v = np.ascontiguousarray(np.atleast_1d(v), dtype=np.float64)
+        t = (np.zeros(len(v)) if t is None else np.ascontiguousarray(np.atleast_1d(t), dtype=np.float64))
+        _check(load().rf_bc_set(self.ctx, FACES[face], BC_TYPES[type_], _dptr(t), _dptr(v), len(v)), "rf_bc_set")
+
+    def set_state(self, h, t=0.0):
+        h = np.ascontiguousarray(h, dtype=np.float64).ravel()
+        _check(load().rf_state_set(self.ctx, _dptr(h), float(t)), "rf_state_set")
+
+    def set_state_device(self, h_dev, t=0.0):
+        _check(load().rf_state_set_device(self.ctx, C.c_void_p(h_dev.data_ptr()), float(t)), "rf_state_set_device")
+
+    # -- stepping
+    def step(self) -> StepInfo:
+        info = rf_step_info()
+        _check(load().rf_step(self.ctx, C.byref(info)), "rf_step")
+        return StepInfo.of(info)
+
+    def run(self, t_end, log_cap=1_000_000):
+        stats = rf_run_stats()
+        log = (rf_step_info * max(log_cap, 1))()
+        st = load().rf_run(self.ctx, float(t_end), C.byref(stats), log, log_cap)
+        steps = [StepInfo.of(log[i]) for i in range(min(stats.steps, log_cap))]
+        _check(st, "rf_run")
+        return steps
+
+    def get_state(self):
+        h = np.zeros(self.N)
+        meta = rf_state_meta()
+        _check(load().rf_state_get(self.ctx, _dptr(h), C.byref(meta)), "rf_state_get")
+        return h, dict(t=meta.t, dt_nom=meta.dt_nom, easy=meta.easy, n_active=meta.n_active, steps=meta.steps)
+
+    def get_state_device(self, out):
+        _check(load().rf_state_get_device(self.ctx, C.c_void_p(out.data_ptr())), "rf_state_get_device")
+        return out
+
+    def set_meta(self, meta: dict, mass7=None):
+        m = rf_state_meta(meta["t"], meta["dt_nom"], meta["easy"], meta.get("n_active", 0), meta.get("steps", 0))
+        arr = None if mass7 is None else np.ascontiguousarray(mass7, dtype=np.float64)
+        _check(load().rf_state_meta_set(self.ctx, C.byref(m), _dptr(arr)), "rf_state_meta_set")
+
+    def mass_balance(self) -> dict:
+        mb = rf_mass_balance_t()
+        _check(load().rf_mass_balance(self.ctx, C.byref(mb)), "rf_mass_balance")
+        return {k: getattr(mb, k) for k, _ in rf_mass_balance_t._fields_}
+
+    def launch_count(self) -> int:
+        return int(load().rf_launch_count(self.ctx))
+
+    # -- kernel level (torch CUDA float64 tensors of N elements)
+    def assemble(self, hk, hn, dt, t=0.0, K=None, theta=None, c=None, b=None, diag=None):
+        ptr = lambda a: None if a is None else C.c_void_p(a.data_ptr())
+        _check(load().rf_assemble(self.ctx, ptr(hk), ptr(hn), float(dt), float(t), ptr(K), ptr(theta), ptr(c),
+                                  ptr(b), ptr(diag)), "rf_assemble")
+
+    def apply(self, x, y):
+        _check(load().rf_apply(self.ctx, C.c_void_p(x.data_ptr()), C.c_void_p(y.data_ptr())), "rf_apply")
+
+    def solve(self, x) -> int:
+        it = C.c_int(0)
+        _check(load().rf_solve(self.ctx, C.c_void_p(x.data_ptr()), C.byref(it)), "rf_solve")
+        return it.value
+
+
+def header_function_names(header: str) -> list:
+    """Names of the functions declared in include/rf.h."""
+    import re
+    txt = open(header).read()
+    txt = re.sub(r"/\*.*?\*/", "", txt, flags=re.S)
+    return sorted(set(re.findall(r"\b(rf_[a-z_0-9]+)\s*\(", txt)))

@@ -211,12 +211,14 @@ def poisson_rain_series(hours: int, mean_gap_h: float, mean_dur_h: float, mean_i
 
 
 def watershed(nx: int = 512, ny: int = 512, nz: int = 64, dx: float = 10.0, dz: float = 0.5,
-              seed: int = 0, hours: int = 720, **param_overrides) -> Case:
+              seed: int = 0, hours: int = 720, water_table: float = 0.0, **param_overrides) -> Case:
     """Masked structured watershed: diamond-square terrain (roughness 0.8)
     scaled to 16-32 m above the bottom, cells above the surface inactive, four
     soil layers of nz/4 cells with uniformly sampled van Genuchten parameters,
-    hydrostatic initial head (water table 8 m above the bottom), hourly
-    Poisson rain on the surface, seepage bottom, lateral zero flux."""
+    hydrostatic initial head with the water table at ``water_table`` metres
+    above the bottom (default: at the bottom, so the seepage face starts
+    inactive), hourly Poisson rain on the surface, seepage bottom, lateral
+    zero flux."""
     rng = np.random.default_rng(seed + 7)
     k = int(np.ceil(np.log2(max(nx, ny))))
     hm = diamond_square(2 ** k, 0.8, seed)[:ny, :nx]
@@ -234,7 +236,7 @@ def watershed(nx: int = 512, ny: int = 512, nz: int = 64, dx: float = 10.0, dz: 
     case = Case(name=f"watershed_{nx}x{ny}x{nz}", nx=nx, ny=ny, nz=nz, dx=dx, dy=dx, dz=dz,
                 active=active, soils=soils, zone_of_cell=zone_of_cell,
                 params=default_params(**param_overrides), t_end=hours * 3600.0)
-    case.h0 = 8.0 - case.z_centres()
+    case.h0 = water_table - case.z_centres()
     case.bcs = [BC("zmax", "flux", t, v), BC("zmin", "seepage")]
     return case
 
