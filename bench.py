@@ -1,0 +1,343 @@
+"""Benchmark: cell-timesteps/s of the Picard / backward-Euler / PCG Richards
+solve on the 128x128x64 heterogeneous box (0.25 m cubes, log-normal Ks with
+exponential covariance, hydrostatic start, 6 h of rain), Picard tolerance
+1e-6 m.
+
+One "step" is one accepted backward-Euler time step: every Picard iteration
+(closures, assembly, PCG solve, global max|dh| test), EBATS reruns and the
+water balance.  ``value`` is the FP32-inner / FP64-defect-correction path
+(closures, Picard test and mass balance in FP64); the plain FP64 path is
+reported beside it.  Inputs are resident in HBM; L2 is flushed between timed
+steps.  ``e2e`` drives the same steps through the C ABI from pinned host
+buffers (state uploaded and downloaded every step).
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl native|reference]
+
+With N > 1 (torchrun, one rank per GPU) every rank runs an independent replica
+(different seed): the solve of one box does not shard without a halo
+exchange, so this is replicas-only weak scaling.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+WORKLOAD = "heterogeneous_box_128x128x64"
+METRIC = "cell-timesteps/s at Picard tol 1e-6 m"
+UNIT = "cell-timesteps/s"
+
+
+def _env_int(k, d):
+    try:
+        return int(os.environ.get(k, d))
+    except ValueError:
+        return d
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=400)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="native", choices=["native", "reference"])
+    ap.add_argument("--seed", type=int, default=0)
+    ap.add_argument("--no-baseline", action="store_true", help="skip the CPU oracle baseline leg")
+    ap.add_argument("--no-e2e", action="store_true")
+    return ap.parse_args()
+
+
+def config_dict(extra=None):
+    d = {"workload": WORKLOAD, "cells": 128 * 128 * 64, "cell_size_m": 0.25, "lnKs_sigma": 1.0,
+         "corr_len_cells": 8, "picard_tol_m": 1e-6, "cg_tol_rel": 1e-10, "ebats": "dt0 1 s, x1.3, max 600 s",
+         "step": "one accepted backward-Euler step from t=0 after warm-up", "l2": "flushed between timed steps"}
+    if extra:
+        d.update(extra)
+    return d
+
+
+# ------------------------------------------------------------------ clocks
+class ClockSampler:
+    """nvidia-smi sampling of SM clocks and throttle reasons during a region."""
+    Q = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.hw_slowdown,"
+         "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+         "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index=0):
+        self.index = index
+        self.rows = []
+        self.proc = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.Q}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except Exception:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) == 7:
+                self.rows.append(parts)
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        sm = [float(r[0]) for r in self.rows if r[0].replace(".", "").isdigit()]
+        mx = [float(r[1]) for r in self.rows if r[1].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in self.rows for i in range(4) if "Active" in r[3 + i]
+                          and "Not" not in r[3 + i]})
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": reasons, "samples": len(self.rows)}
+
+
+# ------------------------------------------------------------ CPU baseline
+def oracle_steps(case, n_steps=None, budget_s=20.0):
+    """Time the CPU oracle (as it stands, single thread) on the first accepted
+    steps of the same workload; stops at n_steps or after budget_s."""
+    from tests.helpers import oracle_from_case
+    o = oracle_from_case(case)
+    t0 = time.perf_counter()
+    k = 0
+    while (n_steps is None or k < n_steps) and time.perf_counter() - t0 < budget_s:
+        o.step()
+        k += 1
+    dt = time.perf_counter() - t0
+    return k, dt
+
+
+def cpu_baseline(case, budget_s=20.0):
+    k, dt = oracle_steps(case, None, budget_s)
+    return {"value": k * case.n_active() / dt, "unit": UNIT, "cores": 1, "kind": "oracle",
+            "sample": f"first {k} accepted steps of {WORKLOAD} from t=0 ({dt:.1f} s, single-thread C oracle)"}
+
+
+# ------------------------------------------------------------ native arm
+def traffic_for(kernel, cells):
+    """DRAM bytes per launch from the committed ncu summary, scaled to this
+    workload's cells; None when absent or taken on a different kernel source."""
+    p = os.path.join(ROOT, "profiles", "ncu_traffic.json")
+    try:
+        d = json.load(open(p))
+        e = d["kernels"][kernel]
+        src = open(os.path.join(ROOT, "paper_1809_10895_gb300", "csrc", e["source"]), "rb").read()
+        if hashlib.sha256(src).hexdigest()[:16] != e["source_sha"]:
+            return None
+        return e["dram_bytes_per_launch"] * cells / e["cells"]
+    except Exception:
+        return None
+
+
+def native(args):
+    import numpy as np
+    import torch
+
+    from __graft_entry__ import build
+    build()
+    from paper_1809_10895_gb300 import rf
+    from paper_1809_10895_gb300 import workloads as W
+
+    world = _env_int("WORLD_SIZE", 1)
+    rank = _env_int("RANK", 0)
+    local = _env_int("LOCAL_RANK", 0)
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
+    torch.cuda.set_device(local)
+    case = W.heterogeneous_box(seed=args.seed + rank)
+    n_act = case.n_active()
+    flush = torch.empty(256 * 1024 * 1024, dtype=torch.uint8, device="cuda")
+
+    def barrier():
+        if world > 1:
+            import torch.distributed as dist
+            dist.barrier()
+        torch.cuda.synchronize()
+
+    def timed_run(precision):
+        s = rf.Solver.from_case(case, precision=precision)
+        stream = s.stream
+        for _ in range(args.warmup):
+            s.step()
+        starts = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+        ends = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+        c0 = s.launch_counts()
+        picard = cg = rej = 0
+        barrier()
+        w0 = time.perf_counter()
+        for i in range(args.steps):
+            flush.zero_()
+            starts[i].record(stream)
+            info = s.step()
+            ends[i].record(stream)
+            picard += info.picard
+            cg += info.cg
+            rej += info.rejected
+        barrier()
+        wall = time.perf_counter() - w0
+        ms = sum(a.elapsed_time(b) for a, b in zip(starts, ends))
+        c1 = s.launch_counts()
+        counts = {k: (c1[k][0] - c0[k][0], c1[k][1] - c0[k][1]) for k in c1}
+        return s, ms, wall, counts, dict(picard=picard, cg=cg, rejected=rej)
+
+    clocks = ClockSampler(local)
+    clocks.start()
+    time.sleep(0.5)        # let the sampler start before the timed region
+    s_mix, ms_mix, wall_mix, counts_mix, st_mix = timed_run("mixed")
+    clk = clocks.stop()
+    s64, ms64, wall64, counts64, st64 = timed_run("fp64")
+    launches_mix = sum(v[0] for v in counts_mix.values())
+
+    def agg(ms):
+        t = torch.tensor([ms / 1e3], dtype=torch.float64, device="cuda")
+        if world > 1:
+            import torch.distributed as dist
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        return float(t.item())
+
+    t_mix, t64 = agg(ms_mix), agg(ms64)
+    value = world * args.steps * n_act / t_mix
+    value64 = world * args.steps * n_act / t64
+
+    # ---- per-kernel device times on the state reached (roofline)
+    peaks = {}
+    try:
+        peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except Exception:
+        pass
+    hbm_peak = peaks.get("hbm_gbs")
+    peak_src = "measured" if hbm_peak else "fallback"
+    hbm_peak = hbm_peak or 6800.0
+    kern = {}
+    for kind in ("closure", "assemble", "resid64", "cg32_spmv", "cg32_update", "cg64_spmv", "cg64_update"):
+        avg_ms, by = s_mix.profile_kernel(kind, reps=30)
+        kern[kind] = {"avg_ms": avg_ms, "bytes": by, "gbs": by / (avg_ms * 1e-3) / 1e9}
+    # device time of each kernel in the timed region: launches that did work
+    # (device counters) x mean launch time (events); the closure kernel that
+    # ends a Picard iteration does the work of the timed closure kernel
+    work = {"closure": counts_mix["closure_picard"][1] + counts_mix["closure"][1],
+            "assemble": counts_mix["assemble"][1], "resid64": counts_mix["resid64"][1],
+            "cg32_spmv": counts_mix["cg32_spmv"][1], "cg32_update": counts_mix["cg32_update"][1]}
+    est = {k: work[k] * kern[k]["avg_ms"] for k in work}
+    tot_est = sum(est.values())
+    dom = max(est, key=lambda k: est[k])
+    kd = kern[dom]
+    names = {"closure": "k_closure_picard", "assemble": "k_assemble", "resid64": "k_resid64",
+             "cg32_spmv": "k_cg32_spmv", "cg32_update": "k_cg32_update"}
+    roof = {"kernel": names[dom], "bound": "hbm", "achieved": kd["gbs"], "peak": hbm_peak, "unit": "GB/s",
+            "frac": kd["gbs"] / hbm_peak, "peak_source": f"{peak_src} (MEASURED_PEAKS.json hbm_gbs)",
+            "traffic": traffic_for(names[dom], n_act), "algorithmic_bytes_per_launch": kd["bytes"],
+            "avg_launch_ms": kd["avg_ms"]}
+
+    # ---- end to end through host buffers
+    e2e = None
+    if not args.no_e2e:
+        s = rf.Solver.from_case(case, precision="mixed")
+        for _ in range(args.warmup):
+            s.step()
+        h_pin = torch.empty(case.N, dtype=torch.float64, pin_memory=True)
+        h_np = h_pin.numpy()
+        h_np[:], meta = s.get_state()
+        mb = s.mass_balance()
+        mass7 = [mb["storage0"], 0, mb["inflow_cum"], mb["outflow_cum"], 0, 0, mb["nonlinear_defect_cum"]]
+        barrier()
+        t0 = time.perf_counter()
+        for _ in range(args.steps):
+            s.set_state(h_np, meta["t"])
+            s.set_meta(meta, mass7)
+            s.step()
+            h_np[:], meta = s.get_state()
+        barrier()
+        te = time.perf_counter() - t0
+        if world > 1:
+            te = agg(te * 1e3)
+        e2e = {"value": world * args.steps * n_act / te, "unit": UNIT, "h2d_bytes_per_step": 8 * case.N,
+               "d2h_bytes_per_step": 8 * case.N}
+
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": t_mix * 1e3 / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32 inner PCG / f64 closures, residual, Picard test",
+            "data": "synthetic (seeded Gaussian random field, no dataset)",
+            "config": config_dict({"precision": "mixed", "parallelism": "replicas" if world > 1 else "single GPU",
+                                   "picard_iters": st_mix["picard"], "cg_inner_iters": st_mix["cg"],
+                                   "rejected": st_mix["rejected"], "wall_s": wall_mix}),
+            "plain_fp64": {"value": value64, "unit": UNIT, "ms_per_step": t64 * 1e3 / args.steps,
+                           "picard_iters": st64["picard"], "cg_iters": st64["cg"], "wall_s": wall64},
+            "speedup_mixed_vs_fp64": value / value64,
+            "gpu_launches": launches_mix,
+            "launch_counts": {k: {"launched": v[0], "worked": v[1]} for k, v in counts_mix.items() if v[0]},
+            "kernel_time_shares": {k: {"launches": work[k], "est_ms": est[k], "share_of_step_time":
+                                       est[k] / (t_mix * 1e3)} for k in est},
+            "roofline": roof,
+            "kernels": {k: {"avg_us": v["avg_ms"] * 1e3, "GBps": v["gbs"]} for k, v in kern.items()},
+            "clocks": clk,
+            "e2e": e2e,
+        }
+        if not args.no_baseline:
+            line["cpu_baseline"] = cpu_baseline(case)
+        print(json.dumps(line))
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+
+
+# ---------------------------------------------------------- reference arm
+def reference(args):
+    """The CPU oracle, as it stands, on the same workload and metric."""
+    rank = _env_int("RANK", 0)
+    if rank != 0:
+        return
+    from oracle import oracle as O
+    from paper_1809_10895_gb300 import workloads as W
+    O.build()
+    case = W.heterogeneous_box(seed=args.seed)
+    # each step is one accepted oracle step; warm-up and timed steps are
+    # bounded so the whole run stays within a few minutes
+    w = min(args.warmup, 3)
+    k = max(1, min(args.steps, 40))
+    from tests.helpers import oracle_from_case
+    o = oracle_from_case(case)
+    for _ in range(w):
+        o.step()
+    t0 = time.perf_counter()
+    for _ in range(k):
+        o.step()
+    dt = time.perf_counter() - t0
+    v = k * case.n_active() / dt
+    print(json.dumps({
+        "impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": 1, "steps": k, "warmup": w,
+        "ms_per_step": dt * 1e3 / k, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "f64", "data": "synthetic (seeded Gaussian random field, no dataset)", "config": config_dict(),
+        "cpu_baseline": {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle",
+                         "sample": f"accepted steps {w + 1}..{w + k} of {WORKLOAD} (single-thread C oracle)"},
+        "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }))
+
+
+if __name__ == "__main__":
+    a = parse()
+    if a.impl == "reference":
+        reference(a)
+    else:
+        native(a)

@@ -212,8 +212,37 @@ rf_status rf_apply(rf_ctx *ctx, const double *d_x, double *d_y);
  * *iters: CG iterations (FP64) or inner FP32 iterations summed (mixed). */
 rf_status rf_solve(rf_ctx *ctx, double *d_x, int *iters);
 
-/* Number of CUDA kernels this context has launched (for accounting). */
+/* Number of CUDA kernel launches this context has executed on the device,
+ * counted by the kernels themselves (loop bodies replayed from CUDA graphs
+ * included).  Synchronises the context's stream. */
 unsigned long long rf_launch_count(rf_ctx *ctx);
+
+/* Per-kind launch counters: out[2 k] = launches of kernel kind k, out[2 k + 1]
+ * = those that did work (a finished loop's kernels return at once).  Kinds,
+ * in order: closure, closure+Picard test, assembly, FP64 CG init, FP64 CG
+ * stencil, FP64 CG update, FP64 operator apply, mixed start, FP64 outer
+ * residual, FP32 CG stencil, FP32 CG update, correction add, water balance,
+ * storage, accept.  Returns the number of values written (<= cap). */
+int rf_launch_counts(rf_ctx *ctx, unsigned long long *out, int cap);
+
+/* Kernels that rf_profile_kernel can time. */
+typedef enum rf_kernel_kind {
+    RF_K_CLOSURE = 0,      /* closures at h with max|h - h_prev|            */
+    RF_K_ASSEMBLE = 1,     /* Picard-system assembly                        */
+    RF_K_CG64_SPMV = 2,    /* FP64 p-update + stencil product + p.q         */
+    RF_K_CG64_UPDATE = 3,  /* FP64 x, r, z update + r.r, r.z                */
+    RF_K_RESID64 = 4,      /* FP64 outer residual of the mixed path         */
+    RF_K_CG32_SPMV = 5,    /* FP32 inner p-update + stencil product + p.q   */
+    RF_K_CG32_UPDATE = 6   /* FP32 inner x, r, z update + dots              */
+} rf_kernel_kind;
+
+/* Time `reps` launches of one kernel on the system assembled at the current
+ * state (h, dt_nom), each bracketed by CUDA events on the context's stream.
+ * Returns the mean device time per launch [ms] and the algorithmic bytes one
+ * launch must move (per-active-cell bytes of that kernel times the active
+ * cells, plus the flag bytes of all cells).  The state h is not modified;
+ * the linear-solver scratch is. */
+rf_status rf_profile_kernel(rf_ctx *ctx, int kind, int reps, double *avg_ms, double *bytes_per_launch);
 
 #ifdef __cplusplus
 }

@@ -11,12 +11,16 @@
 
 namespace rf {
 
-// van Genuchten / Mualem closures in a cancellation-free form.
-// With L = log(-alpha h), x = (-alpha h)^n = exp(n L), l1 = log1p(x):
+// van Genuchten / Mualem closures with four FP64 transcendentals per cell.
+// With u = -alpha h, L = log u, x = u^n = exp(n L), l1 = log1p(x):
 //   Se = (1 + x)^-m = exp(-m l1)                               (Eq. 2)
+//   u^(n-1) = x / u (since m n = n - 1), so (x/(1+x))^m = (x/u) Se = ys
 //   Se^(1/m) = 1/(1+x), so 1 - Se^(1/m) = x/(1+x) and
-//   K = Ks Se^(1/2) [1 - exp(m (n L - l1))]^2 = Ks sqrt(Se) expm1(.)^2   (Eq. 4)
-//   C = (theta_s-theta_r) alpha n m exp((n-1) L - (m+1) l1)     (Eq. 3)
+//   K = Ks Se^(1/2) (1 - ys)^2                                   (Eq. 4)
+//     with 1 - ys = -expm1(m (n L - l1)) when ys > 1/2 (dry soil, where
+//     1 - ys would cancel)
+//   C = (theta_s-theta_r) alpha n m u^(n-1) (1+x)^-(m+1)
+//     = (theta_s-theta_r) alpha n m ys / (1+x)                  (Eq. 3)
 // For h >= 0 (tie included): theta* = theta_s + S h, K = Ks, C = S, which
 // makes d(theta*)/dh equal to Eq. 3 on both branches.
 // Gardner (Eq. A6): K = Ks e^(alpha h), theta = theta_r + (theta_s-theta_r) e^(alpha h).
@@ -36,24 +40,27 @@ __device__ __forceinline__ void closure(const DevSoil &s, double Ks, double h, d
         C = dth * s.alpha * e;
         return;
     }
-    const double L = log(-s.alpha * h);
+    const double u = -s.alpha * h;
+    const double L = log(u);
     const double nL = s.n * L;
     const double x = exp(nL);
     const double l1 = log1p(x);
     const double se = exp(-s.m * l1);
     th = s.theta_r + dth * se;
-    const double omy = -expm1(s.m * (nL - l1));
+    const double ys = x * rcp64(u) * se;
+    const double omy = ys <= 0.5 ? 1.0 - ys : -expm1(s.m * (nL - l1));
     K = Ks * sqrt(se) * omy * omy;
-    C = dth * s.alpha * s.n * s.m * exp((s.n - 1.0) * L - (s.m + 1.0) * l1);
+    C = dth * s.alpha * s.n * s.m * ys * rcp64(1.0 + x);
 }
 
-__global__ void __launch_bounds__(RED_THREADS)
-k_closure(Grid g, const DevSoil *__restrict__ soils, const uint8_t *__restrict__ zone,
-          const double *__restrict__ Ks, const uint8_t *__restrict__ flags, const double *__restrict__ h,
-          const double *__restrict__ hprev, double *__restrict__ theta, double *__restrict__ K,
-          double *__restrict__ Can, double *partials, unsigned int *ticket, StepResults *res)
+// Closures of every cell at h; with hprev, also max|h - hprev| and a
+// non-finite flag in v[0], v[1].
+__device__ __forceinline__ void closure_cells(const Grid &g, const DevSoil *__restrict__ soils,
+                                              const uint8_t *__restrict__ zone, const double *__restrict__ Ks,
+                                              const uint8_t *__restrict__ flags, const double *__restrict__ h,
+                                              const double *__restrict__ hprev, double *__restrict__ theta,
+                                              double *__restrict__ K, double *__restrict__ Can, double (&v)[2])
 {
-    double v[2] = {0.0, 0.0};   // max |h - hprev|, non-finite flag
     const long long stride = (long long)gridDim.x * blockDim.x;
     for (long long p = (long long)blockIdx.x * blockDim.x + threadIdx.x; p < g.N; p += stride) {
         if (!(flags[p] & FLAG_ACTIVE)) {
@@ -75,11 +82,62 @@ k_closure(Grid g, const DevSoil *__restrict__ soils, const uint8_t *__restrict__
         K[p] = k;
         Can[p] = c;
     }
+}
+
+__global__ void __launch_bounds__(RED_THREADS)
+k_closure(Grid g, const DevSoil *__restrict__ soils, const uint8_t *__restrict__ zone,
+          const double *__restrict__ Ks, const uint8_t *__restrict__ flags, const double *__restrict__ h,
+          const double *__restrict__ hprev, double *__restrict__ theta, double *__restrict__ K,
+          double *__restrict__ Can, double *partials, unsigned int *ticket, StepResults *res)
+{
+    count_launch(g, KK_CLOSURE);
+    count_work(g, KK_CLOSURE);
+    double v[2] = {0.0, 0.0};   // max |h - hprev|, non-finite flag
+    closure_cells(g, soils, zone, Ks, flags, h, hprev, theta, K, Can, v);
     if (hprev) {
         if (grid_reduce<OpMax, 2>(v, partials, ticket) && threadIdx.x == 0) {
             res->max_dh = v[0];
             res->nonfinite = v[1] > 0.0;
         }
+    }
+}
+
+// End of a Picard iteration on the device: closures at the new iterate x
+// (which also serve the next assembly, or the next step once accepted), the
+// exit test max|x - h^k| <= tol over all active cells (global, Sec. 2.3),
+// and the loop control.  A failed linear solve or a non-finite update fails
+// the attempt.  The last block sets the Picard loop condition; every launch
+// sets it, so the loop always terminates (at the latest after n_max).
+__global__ void __launch_bounds__(RED_THREADS)
+k_closure_picard(Grid g, const DevSoil *__restrict__ soils, const uint8_t *__restrict__ zone,
+                 const double *__restrict__ Ks, const uint8_t *__restrict__ flags, const double *__restrict__ x,
+                 const double *__restrict__ hk, double *__restrict__ theta, double *__restrict__ K,
+                 double *__restrict__ Can, double *partials, unsigned int *ticket, PicardCtl *ctl,
+                 const CgScal *cg_status, const CgScal *cg_count, CondSet cond)
+{
+    count_launch(g, KK_CLOSURE_PICARD);
+    if (ctl->done) {
+        if (blockIdx.x == 0 && threadIdx.x == 0) set_cond(cond, 0);
+        return;
+    }
+    count_work(g, KK_CLOSURE_PICARD);
+    double v[2] = {0.0, 0.0};
+    closure_cells(g, soils, zone, Ks, flags, x, hk, theta, K, Can, v);
+    if (grid_reduce<OpMax, 2>(v, partials, ticket) && threadIdx.x == 0) {
+        const int it = ++ctl->it;
+        if (cg_status->status != CG_OK) {
+            ctl->fail = 1;
+        } else {
+            ctl->cg_total += cg_count->total;
+            ctl->max_dh = v[0];
+            if (v[1] > 0.0) ctl->fail = 1;
+            else if (v[0] <= ctl->tol) {
+                ctl->conv = 1;
+                ctl->mb_pending = 1;
+            }
+        }
+        ctl->done = (ctl->conv || ctl->fail || it >= ctl->n_max) ? 1 : 0;
+        set_cond(cond, ctl->done ? 0 : 1);
     }
 }
 
@@ -113,9 +171,13 @@ k_assemble(Grid g, const DevSoil *__restrict__ soils, const uint8_t *__restrict_
            const double *__restrict__ thn, const double *__restrict__ K, const double *__restrict__ Can,
            double *__restrict__ c_out, double *__restrict__ b, double *__restrict__ Tx, double *__restrict__ Ty,
            double *__restrict__ Tz, double *__restrict__ diag_out, double *__restrict__ dinv,
-           float *__restrict__ K32, float *__restrict__ cb32, float *__restrict__ dinv32)
+           float *__restrict__ K32, float *__restrict__ cb32, float *__restrict__ dinv32, const int *skip)
 {
-    const double dt = spp->dt, eps = spp->eps_chord;
+    count_launch(g, KK_ASSEMBLE);
+    if (skip && *skip) return;
+    count_work(g, KK_ASSEMBLE);
+    const double eps = spp->eps_chord;
+    const double V_dt = g.V / spp->dt;
     const long long stride = (long long)gridDim.x * blockDim.x;
     for (long long p = (long long)blockIdx.x * blockDim.x + threadIdx.x; p < g.N; p += stride) {
         const uint8_t fl = flags[p];
@@ -125,13 +187,12 @@ k_assemble(Grid g, const DevSoil *__restrict__ soils, const uint8_t *__restrict_
             K32[p] = -1.0f; cb32[p] = 0.0f; dinv32[p] = 0.0f;
             continue;
         }
-        const int i = (int)(p % g.nx);
-        const int j = (int)((p / g.nx) % g.ny);
-        const int k = (int)(p / g.sxy);
+        int i, j, k;
+        cell_ijk(g, p, i, j, k);
         const double hkP = hk[p], hnP = hn[p], KP = K[p];
         const double dh = hkP - hnP;
-        const double C = (fabs(dh) > eps) ? (thk[p] - thn[p]) / dh : Can[p];
-        const double c = g.V * C / dt;
+        const double C = (fabs(dh) > eps) ? (thk[p] - thn[p]) * rcp64(dh) : Can[p];
+        const double c = V_dt * C;
         double diag = c, rhs = c * hnP, cb = c;
         double Tup[3] = {0.0, 0.0, 0.0};
 #pragma unroll
@@ -177,11 +238,12 @@ k_assemble(Grid g, const DevSoil *__restrict__ soils, const uint8_t *__restrict_
         Tx[p] = Tup[0];
         Ty[p] = Tup[1];
         Tz[p] = Tup[2];
+        const double di = rcp64(diag);
         diag_out[p] = diag;
-        dinv[p] = 1.0 / diag;
+        dinv[p] = di;
         K32[p] = (float)KP;
         cb32[p] = (float)cb;
-        dinv32[p] = (float)(1.0 / diag);
+        dinv32[p] = (float)di;
     }
 }
 
@@ -193,8 +255,14 @@ k_mass_balance(Grid g, const DevSoil *__restrict__ soils, const uint8_t *__restr
                const double *__restrict__ Ks, const uint8_t *__restrict__ flags,
                const StepParams *__restrict__ spp, const double *__restrict__ x, const double *__restrict__ hn,
                const double *__restrict__ c, const double *__restrict__ Kold, const double *__restrict__ thx,
-               const double *__restrict__ thn, double *partials, unsigned int *ticket, StepResults *res)
+               const double *__restrict__ thn, double *partials, unsigned int *ticket, StepResults *res,
+               PicardCtl *ctl)
 {
+    count_launch(g, KK_MASS_BALANCE);
+    // inside a Picard graph: only after the iteration that converged (every
+    // block reads the flag before the last block clears it)
+    if (ctl && !ctl->mb_pending) return;
+    count_work(g, KK_MASS_BALANCE);
     const double dt = spp->dt;
     double v[4] = {0.0, 0.0, 0.0, 0.0};   // lin, dS, in, out
     const long long stride = (long long)gridDim.x * blockDim.x;
@@ -237,6 +305,7 @@ k_mass_balance(Grid g, const DevSoil *__restrict__ soils, const uint8_t *__restr
         res->dstore = v[1];
         res->bnd_in = v[2];
         res->bnd_out = v[3];
+        if (ctl) ctl->mb_pending = 0;
     }
 }
 
@@ -244,11 +313,27 @@ __global__ void __launch_bounds__(RED_THREADS)
 k_storage(Grid g, const uint8_t *__restrict__ flags, const double *__restrict__ theta, double *partials,
           unsigned int *ticket, StepResults *res)
 {
+    count_launch(g, KK_STORAGE);
+    count_work(g, KK_STORAGE);
     double v[1] = {0.0};
     const long long stride = (long long)gridDim.x * blockDim.x;
     for (long long p = (long long)blockIdx.x * blockDim.x + threadIdx.x; p < g.N; p += stride)
         if (flags[p] & FLAG_ACTIVE) v[0] += g.V * theta[p];
     if (grid_reduce<OpSum, 1>(v, partials, ticket) && threadIdx.x == 0) res->storage = v[0];
+}
+
+__global__ void __launch_bounds__(RED_THREADS)
+k_accept(Grid g, const double *__restrict__ xf, double *__restrict__ h, const double *__restrict__ thk,
+         double *__restrict__ thn, const double *__restrict__ K1, double *__restrict__ K0, int copyK)
+{
+    count_launch(g, KK_ACCEPT);
+    count_work(g, KK_ACCEPT);
+    const long long stride = (long long)gridDim.x * blockDim.x;
+    for (long long p = (long long)blockIdx.x * blockDim.x + threadIdx.x; p < g.N; p += stride) {
+        h[p] = xf[p];
+        thn[p] = thk[p];
+        if (copyK) K0[p] = K1[p];
+    }
 }
 
 void launch_closure(cudaStream_t s, int nblk, const Grid &g, const DevSoil *soils, const uint8_t *zone,
@@ -259,23 +344,39 @@ void launch_closure(cudaStream_t s, int nblk, const Grid &g, const DevSoil *soil
     k_closure<<<nblk, RED_THREADS, 0, s>>>(g, soils, zone, Ks, flags, h, hprev, theta, K, Can, partials, ticket, res);
 }
 
+void launch_closure_picard(cudaStream_t s, int nblk, const Grid &g, const DevSoil *soils, const uint8_t *zone,
+                           const double *Ks, const uint8_t *flags, const double *x, const double *hk,
+                           double *theta, double *K, double *Can, double *partials, unsigned int *ticket,
+                           PicardCtl *ctl, const CgScal *cg_status, const CgScal *cg_count, CondSet cond)
+{
+    k_closure_picard<<<nblk, RED_THREADS, 0, s>>>(g, soils, zone, Ks, flags, x, hk, theta, K, Can, partials, ticket,
+                                                  ctl, cg_status, cg_count, cond);
+}
+
 void launch_assemble(cudaStream_t s, int nblk, const Grid &g, const DevSoil *soils, const uint8_t *zone,
                      const double *Ks, const uint8_t *flags, const StepParams *sp, const double *hk,
                      const double *hn, const double *theta_k, const double *theta_n, const double *K,
                      const double *Can, double *c, double *b, double *Tx, double *Ty, double *Tz,
-                     double *diag, double *dinv, float *K32, float *cb32, float *dinv32)
+                     double *diag, double *dinv, float *K32, float *cb32, float *dinv32, const int *skip)
 {
     k_assemble<<<nblk, RED_THREADS, 0, s>>>(g, soils, zone, Ks, flags, sp, hk, hn, theta_k, theta_n, K, Can, c, b,
-                                            Tx, Ty, Tz, diag, dinv, K32, cb32, dinv32);
+                                            Tx, Ty, Tz, diag, dinv, K32, cb32, dinv32, skip);
+}
+
+void launch_accept(cudaStream_t s, int nblk, const Grid &g, const double *x_final, double *h,
+                   const double *theta_k, double *theta_n, const double *K1, double *K0, int copyK)
+{
+    k_accept<<<nblk, RED_THREADS, 0, s>>>(g, x_final, h, theta_k, theta_n, K1, K0, copyK);
 }
 
 void launch_mass_balance(cudaStream_t s, int nblk, const Grid &g, const DevSoil *soils, const uint8_t *zone,
                          const double *Ks, const uint8_t *flags, const StepParams *sp, const double *x,
                          const double *hn, const double *c, const double *Kold, const double *theta_x,
-                         const double *theta_n, double *partials, unsigned int *ticket, StepResults *res)
+                         const double *theta_n, double *partials, unsigned int *ticket, StepResults *res,
+                         PicardCtl *ctl)
 {
     k_mass_balance<<<nblk, RED_THREADS, 0, s>>>(g, soils, zone, Ks, flags, sp, x, hn, c, Kold, theta_x, theta_n,
-                                                partials, ticket, res);
+                                                partials, ticket, res, ctl);
 }
 
 void launch_storage(cudaStream_t s, int nblk, const Grid &g, const uint8_t *flags, const double *theta,

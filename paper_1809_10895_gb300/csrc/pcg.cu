@@ -34,9 +34,8 @@ __device__ __forceinline__ double apply64(const Grid &g, long long p, const doub
                                           const double *__restrict__ Ty, const double *__restrict__ Tz,
                                           const double *__restrict__ diag, Get get)
 {
-    const int i = (int)(p % g.nx);
-    const int j = (int)((p / g.nx) % g.ny);
-    const int k = (int)(p / g.sxy);
+    int i, j, k;
+    cell_ijk(g, p, i, j, k);
     double acc = diag[p] * get(p);
     if (i > 0) acc -= Tx[p - 1] * get(p - 1);
     if (i < g.nx - 1) acc -= Tx[p] * get(p + 1);
@@ -53,8 +52,17 @@ k_cg64_init(Grid g, const uint8_t *__restrict__ flags, const double *__restrict_
             const double *__restrict__ b, const double *__restrict__ Tx, const double *__restrict__ Ty,
             const double *__restrict__ Tz, const double *__restrict__ diag, const double *__restrict__ dinv,
             double *__restrict__ r, double *__restrict__ z, double tol, int max_it, double *partials,
-            unsigned int *ticket, CgScal *sc)
+            unsigned int *ticket, CgScal *sc, const int *skip, CondSet cond)
 {
+    count_launch(g, KK_CG64_INIT);
+    if (skip && *skip) {        // Picard attempt already finished: no solve, empty CG loop
+        if (blockIdx.x == 0 && threadIdx.x == 0) {
+            sc->done = 1;
+            set_cond(cond, 0);
+        }
+        return;
+    }
+    count_work(g, KK_CG64_INIT);
     double v[3] = {0.0, 0.0, 0.0};   // r.z, r.r, b.b
     GRID_STRIDE_LOOP(p)
     {
@@ -82,10 +90,12 @@ k_cg64_init(Grid g, const uint8_t *__restrict__ flags, const double *__restrict_
         sc->alpha = 0.0;
         sc->beta = 0.0;
         sc->iter = 0;
+        sc->total = 0;
         sc->max_it = max_it;
         const bool finite = isfinite(v[0]) && isfinite(v[1]) && isfinite(v[2]);
         sc->status = finite ? CG_OK : CG_NONFINITE;
         sc->done = (!finite || sqrt(v[1]) <= sc->stop2) ? 1 : 0;
+        set_cond(cond, sc->done ? 0 : 1);
     }
 }
 
@@ -95,7 +105,9 @@ k_cg64_spmv(Grid g, const uint8_t *__restrict__ flags, const double *__restrict_
             const double *__restrict__ Ty, const double *__restrict__ Tz, const double *__restrict__ diag,
             double *partials, unsigned int *ticket, CgScal *sc)
 {
+    count_launch(g, KK_CG64_SPMV);
     if (sc->done) return;
+    count_work(g, KK_CG64_SPMV);
     const double beta = sc->beta;
     const bool first = sc->iter == 0;
     auto get = [&](long long qq) { return first ? z[qq] : fma(beta, p_in[qq], z[qq]); };
@@ -127,9 +139,14 @@ k_cg64_spmv(Grid g, const uint8_t *__restrict__ flags, const double *__restrict_
 __global__ void __launch_bounds__(RED_THREADS)
 k_cg64_update(Grid g, double *__restrict__ x, double *__restrict__ r, double *__restrict__ z,
               const double *__restrict__ pd, const double *__restrict__ q, const double *__restrict__ dinv,
-              double *partials, unsigned int *ticket, CgScal *sc)
+              double *partials, unsigned int *ticket, CgScal *sc, CondSet cond)
 {
-    if (sc->done) return;
+    count_launch(g, KK_CG64_UPDATE);
+    if (sc->done) {             // every launch sets the loop condition
+        if (blockIdx.x == 0 && threadIdx.x == 0) set_cond(cond, 0);
+        return;
+    }
+    count_work(g, KK_CG64_UPDATE);
     const double alpha = sc->alpha;
     double v[2] = {0.0, 0.0};   // r.r, r.z
     GRID_STRIDE_LOOP(p)
@@ -146,6 +163,7 @@ k_cg64_update(Grid g, double *__restrict__ x, double *__restrict__ r, double *__
     }
     if (grid_reduce<OpSum, 2>(v, partials, ticket) && threadIdx.x == 0) {
         sc->iter += 1;
+        sc->total += 1;
         sc->rr = v[0];
         if (!isfinite(v[0]) || !isfinite(v[1])) {
             sc->status = CG_NONFINITE;
@@ -159,6 +177,7 @@ k_cg64_update(Grid g, double *__restrict__ x, double *__restrict__ r, double *__
             sc->beta = v[1] / sc->rho;
             sc->rho = v[1];
         }
+        set_cond(cond, sc->done ? 0 : 1);
     }
 }
 
@@ -167,6 +186,8 @@ k_apply64(Grid g, const uint8_t *__restrict__ flags, const double *__restrict__ 
           const double *__restrict__ Tx, const double *__restrict__ Ty, const double *__restrict__ Tz,
           const double *__restrict__ diag)
 {
+    count_launch(g, KK_APPLY64);
+    count_work(g, KK_APPLY64);
     GRID_STRIDE_LOOP(p)
     {
         y[p] = (flags[p] & FLAG_ACTIVE) ? apply64(g, p, Tx, Ty, Tz, diag, [&](long long q) { return x[q]; }) : 0.0;
@@ -179,9 +200,8 @@ template <class Get>
 __device__ __forceinline__ float apply32(const Grid &g, long long p, const float *__restrict__ K32,
                                          const float *__restrict__ cb32, Get get)
 {
-    const int i = (int)(p % g.nx);
-    const int j = (int)((p / g.nx) % g.ny);
-    const int k = (int)(p / g.sxy);
+    int i, j, k;
+    cell_ijk(g, p, i, j, k);
     const float KP = K32[p];
     const float vP = get(p);
     float acc = cb32[p] * vP;
@@ -200,15 +220,48 @@ __device__ __forceinline__ float apply32(const Grid &g, long long p, const float
     return acc;
 }
 
+// Start of a defect-correction solve: x = x0, counters reset, outer loop
+// condition raised (or, when the Picard attempt is over, an empty loop).
+__global__ void __launch_bounds__(RED_THREADS)
+k_mixed_start(Grid g, const double *__restrict__ x0, double *__restrict__ x, CgScal *outer, CgScal *inner,
+              const int *skip, CondSet cond_outer)
+{
+    count_launch(g, KK_MIXED_START);
+    const bool skipped = skip && *skip;
+    if (blockIdx.x == 0 && threadIdx.x == 0) {
+        outer->iter = 0;
+        outer->done = skipped ? 1 : 0;
+        outer->status = CG_OK;
+        inner->total = 0;
+        inner->status = CG_OK;
+        set_cond(cond_outer, skipped ? 0 : 1);
+    }
+    if (skipped) return;
+    count_work(g, KK_MIXED_START);
+    GRID_STRIDE_LOOP(p) { x[p] = x0[p]; }
+}
+
 // Outer FP64 residual r = b - A x; seeds the inner FP32 solve A d = r with
-// d0 = 0 (so r32 = r, z32 = D^-1 r32).
+// d0 = 0 (so r32 = r, z32 = D^-1 r32).  Counts outer iterations and fails the
+// solve after outer_max_it residuals without convergence.
 __global__ void __launch_bounds__(RED_THREADS)
 k_resid64(Grid g, const uint8_t *__restrict__ flags, const double *__restrict__ x, const double *__restrict__ b,
           const double *__restrict__ Tx, const double *__restrict__ Ty, const double *__restrict__ Tz,
           const double *__restrict__ diag, const float *__restrict__ dinv32, float *__restrict__ r32,
           float *__restrict__ z32, float *__restrict__ d32, double tol, double tol_inner, int inner_max_it,
-          double *partials, unsigned int *ticket, CgScal *outer, CgScal *inner)
+          int outer_max_it, double *partials, unsigned int *ticket, CgScal *outer, CgScal *inner,
+          CondSet cond_outer, CondSet cond_inner)
 {
+    count_launch(g, KK_RESID64);
+    if (outer->done) {
+        if (blockIdx.x == 0 && threadIdx.x == 0) {
+            inner->done = 1;
+            set_cond(cond_outer, 0);
+            set_cond(cond_inner, 0);
+        }
+        return;
+    }
+    count_work(g, KK_RESID64);
     double v[4] = {0.0, 0.0, 0.0, 0.0};   // r.r, b.b (FP64); r32.r32, r32.z32
     GRID_STRIDE_LOOP(p)
     {
@@ -231,11 +284,19 @@ k_resid64(Grid g, const uint8_t *__restrict__ flags, const double *__restrict__ 
     }
     if (grid_reduce<OpSum, 4>(v, partials, ticket) && threadIdx.x == 0) {
         const bool finite = isfinite(v[0]) && isfinite(v[1]) && isfinite(v[2]) && isfinite(v[3]);
+        outer->iter += 1;
         outer->rr = v[0];
         outer->bb = v[1];
         outer->stop2 = tol * sqrt(v[1]);
-        outer->status = finite ? CG_OK : CG_NONFINITE;
-        outer->done = (!finite || sqrt(v[0]) <= outer->stop2) ? 1 : 0;
+        if (!finite) {
+            outer->status = CG_NONFINITE;
+            outer->done = 1;
+        } else if (sqrt(v[0]) <= outer->stop2) {
+            outer->done = 1;
+        } else if (outer->iter >= outer_max_it) {
+            outer->status = CG_MAXIT;
+            outer->done = 1;
+        }
         inner->rho = v[3];
         inner->rr = v[2];
         inner->bb = v[2];
@@ -244,8 +305,10 @@ k_resid64(Grid g, const uint8_t *__restrict__ flags, const double *__restrict__ 
         inner->beta = 0.0;
         inner->iter = 0;
         inner->max_it = inner_max_it;
-        inner->status = finite ? CG_OK : CG_NONFINITE;
+        inner->status = CG_OK;
         inner->done = (outer->done || !(v[2] > 0.0)) ? 1 : 0;
+        set_cond(cond_outer, outer->done ? 0 : 1);
+        set_cond(cond_inner, inner->done ? 0 : 1);
     }
 }
 
@@ -254,7 +317,9 @@ k_cg32_spmv(Grid g, const float *__restrict__ z, const float *__restrict__ p_in,
             float *__restrict__ q, const float *__restrict__ K32, const float *__restrict__ cb32, double *partials,
             unsigned int *ticket, CgScal *sc)
 {
+    count_launch(g, KK_CG32_SPMV);
     if (sc->done) return;
+    count_work(g, KK_CG32_SPMV);
     const float beta = (float)sc->beta;
     const bool first = sc->iter == 0;
     auto get = [&](long long qq) { return first ? z[qq] : fmaf(beta, p_in[qq], z[qq]); };
@@ -287,9 +352,14 @@ k_cg32_spmv(Grid g, const float *__restrict__ z, const float *__restrict__ p_in,
 __global__ void __launch_bounds__(RED_THREADS)
 k_cg32_update(Grid g, float *__restrict__ x, float *__restrict__ r, float *__restrict__ z,
               const float *__restrict__ pd, const float *__restrict__ q, const float *__restrict__ dinv,
-              double *partials, unsigned int *ticket, CgScal *sc)
+              double *partials, unsigned int *ticket, CgScal *sc, CondSet cond)
 {
-    if (sc->done) return;
+    count_launch(g, KK_CG32_UPDATE);
+    if (sc->done) {
+        if (blockIdx.x == 0 && threadIdx.x == 0) set_cond(cond, 0);
+        return;
+    }
+    count_work(g, KK_CG32_UPDATE);
     const float alpha = (float)sc->alpha;
     float a0 = 0.0f, a1 = 0.0f;
     GRID_STRIDE_LOOP(p)
@@ -307,6 +377,7 @@ k_cg32_update(Grid g, float *__restrict__ x, float *__restrict__ r, float *__res
     double v[2] = {(double)a0, (double)a1};
     if (grid_reduce<OpSum, 2>(v, partials, ticket) && threadIdx.x == 0) {
         sc->iter += 1;
+        sc->total += 1;
         sc->rr = v[0];
         if (!isfinite(v[0]) || !isfinite(v[1])) {
             sc->status = CG_NONFINITE;
@@ -320,12 +391,27 @@ k_cg32_update(Grid g, float *__restrict__ x, float *__restrict__ r, float *__res
             sc->beta = v[1] / sc->rho;
             sc->rho = v[1];
         }
+        set_cond(cond, sc->done ? 0 : 1);
     }
 }
 
+// x += d after an inner solve; a non-finite inner solve fails the outer loop
+// (an inner solve that only reached its iteration cap is still applied).
 __global__ void __launch_bounds__(RED_THREADS)
-k_add_correction(Grid g, double *__restrict__ x, const float *__restrict__ d)
+k_add_correction(Grid g, double *__restrict__ x, const float *__restrict__ d, CgScal *outer, const CgScal *inner,
+                 CondSet cond_outer)
 {
+    count_launch(g, KK_ADD_CORRECTION);
+    if (outer->done) return;
+    if (inner->status == CG_NONFINITE) {
+        if (blockIdx.x == 0 && threadIdx.x == 0) {
+            outer->status = CG_NONFINITE;
+            outer->done = 1;
+            set_cond(cond_outer, 0);
+        }
+        return;
+    }
+    count_work(g, KK_ADD_CORRECTION);
     GRID_STRIDE_LOOP(p) { x[p] += (double)d[p]; }
 }
 
@@ -333,10 +419,10 @@ k_add_correction(Grid g, double *__restrict__ x, const float *__restrict__ d)
 void launch_cg64_init(cudaStream_t s, int nblk, const Grid &g, const uint8_t *flags, const double *x0, double *x,
                       const double *b, const double *Tx, const double *Ty, const double *Tz, const double *diag,
                       const double *dinv, double *r, double *z, double tol, int max_it, double *partials,
-                      unsigned int *ticket, CgScal *sc)
+                      unsigned int *ticket, CgScal *sc, const int *skip, CondSet cond)
 {
     k_cg64_init<<<nblk, RED_THREADS, 0, s>>>(g, flags, x0, x, b, Tx, Ty, Tz, diag, dinv, r, z, tol, max_it, partials,
-                                             ticket, sc);
+                                             ticket, sc, skip, cond);
 }
 
 void launch_cg64_spmv(cudaStream_t s, int nblk, const Grid &g, const uint8_t *flags, const double *z,
@@ -347,9 +433,10 @@ void launch_cg64_spmv(cudaStream_t s, int nblk, const Grid &g, const uint8_t *fl
 }
 
 void launch_cg64_update(cudaStream_t s, int nblk, const Grid &g, double *x, double *r, double *z, const double *p,
-                        const double *q, const double *dinv, double *partials, unsigned int *ticket, CgScal *sc)
+                        const double *q, const double *dinv, double *partials, unsigned int *ticket, CgScal *sc,
+                        CondSet cond)
 {
-    k_cg64_update<<<nblk, RED_THREADS, 0, s>>>(g, x, r, z, p, q, dinv, partials, ticket, sc);
+    k_cg64_update<<<nblk, RED_THREADS, 0, s>>>(g, x, r, z, p, q, dinv, partials, ticket, sc, cond);
 }
 
 void launch_apply64(cudaStream_t s, int nblk, const Grid &g, const uint8_t *flags, const double *x, double *y,
@@ -358,13 +445,21 @@ void launch_apply64(cudaStream_t s, int nblk, const Grid &g, const uint8_t *flag
     k_apply64<<<nblk, RED_THREADS, 0, s>>>(g, flags, x, y, Tx, Ty, Tz, diag);
 }
 
+void launch_mixed_start(cudaStream_t s, int nblk, const Grid &g, const double *x0, double *x, CgScal *outer,
+                        CgScal *inner, const int *skip, CondSet cond_outer)
+{
+    k_mixed_start<<<nblk, RED_THREADS, 0, s>>>(g, x0, x, outer, inner, skip, cond_outer);
+}
+
 void launch_resid64(cudaStream_t s, int nblk, const Grid &g, const uint8_t *flags, const double *x, const double *b,
                     const double *Tx, const double *Ty, const double *Tz, const double *diag, const float *dinv32,
                     float *r32, float *z32, float *d32, double tol, double tol_inner, int inner_max_it,
-                    double *partials, unsigned int *ticket, CgScal *outer, CgScal *inner)
+                    int outer_max_it, double *partials, unsigned int *ticket, CgScal *outer, CgScal *inner,
+                    CondSet cond_outer, CondSet cond_inner)
 {
     k_resid64<<<nblk, RED_THREADS, 0, s>>>(g, flags, x, b, Tx, Ty, Tz, diag, dinv32, r32, z32, d32, tol, tol_inner,
-                                           inner_max_it, partials, ticket, outer, inner);
+                                           inner_max_it, outer_max_it, partials, ticket, outer, inner, cond_outer,
+                                           cond_inner);
 }
 
 void launch_cg32_spmv(cudaStream_t s, int nblk, const Grid &g, const float *z, const float *p_in, float *p_out,
@@ -375,14 +470,16 @@ void launch_cg32_spmv(cudaStream_t s, int nblk, const Grid &g, const float *z, c
 }
 
 void launch_cg32_update(cudaStream_t s, int nblk, const Grid &g, float *x, float *r, float *z, const float *p,
-                        const float *q, const float *dinv, double *partials, unsigned int *ticket, CgScal *sc)
+                        const float *q, const float *dinv, double *partials, unsigned int *ticket, CgScal *sc,
+                        CondSet cond)
 {
-    k_cg32_update<<<nblk, RED_THREADS, 0, s>>>(g, x, r, z, p, q, dinv, partials, ticket, sc);
+    k_cg32_update<<<nblk, RED_THREADS, 0, s>>>(g, x, r, z, p, q, dinv, partials, ticket, sc, cond);
 }
 
-void launch_add_correction(cudaStream_t s, int nblk, const Grid &g, double *x, const float *d)
+void launch_add_correction(cudaStream_t s, int nblk, const Grid &g, double *x, const float *d, CgScal *outer,
+                           const CgScal *inner, CondSet cond_outer)
 {
-    k_add_correction<<<nblk, RED_THREADS, 0, s>>>(g, x, d);
+    k_add_correction<<<nblk, RED_THREADS, 0, s>>>(g, x, d, outer, inner, cond_outer);
 }
 
 }  // namespace rf

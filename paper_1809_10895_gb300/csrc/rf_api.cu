@@ -73,19 +73,26 @@ struct rf_ctx {
     CgScal *sc = nullptr, *sc_in = nullptr;
     StepResults *res = nullptr;
     StepParams *sp = nullptr;
+    PicardCtl *ctl = nullptr;
+    unsigned long long *ctr = nullptr;
     // pinned host mirrors
     CgScal *sc_h = nullptr, *sc_in_h = nullptr;
     StepResults *res_h = nullptr;
     StepParams *sp_h = nullptr;
+    PicardCtl *ctl_h = nullptr;
+    unsigned long long *ctr_h = nullptr;
 
-    int kcur = 0;
-    bool closure_at_h = false;   // K[kcur], Can hold the closures at h (the accepted state)
+    // CUDA graphs: a whole Picard attempt, and a stand-alone linear solve
+    cudaStream_t cap = nullptr;          // private capture stream
+    cudaGraph_t picard_graph = nullptr, solve_graph = nullptr;
+    cudaGraphExec_t picard_exec = nullptr, solve_exec = nullptr;
+
+    bool closure_at_h = false;   // K[0], Can hold the closures at h (the accepted state)
     bool soils_set = false, has_state = false;
     double t = 0.0, dt_nom = 1.0;
     int easy = 0;
     long long steps = 0;
     double storage0 = 0.0, in_cum = 0.0, out_cum = 0.0, closure_cum = 0.0, defect_cum = 0.0;
-    unsigned long long launches = 0;
 
     void *dalloc(size_t bytes)
     {
@@ -162,87 +169,205 @@ void run_closure(rf_ctx *c, const double *h_eval, const double *hprev, double *t
 {
     launch_closure(c->stream, c->nblk, c->g, c->soils, c->zone, c->Ks, c->flags, h_eval, hprev, theta_out,
                    c->K[kout], c->Can, c->partials, c->ticket, c->res);
-    c->launches++;
 }
 
 void run_assemble(rf_ctx *c, const double *hk, const double *hn, const double *thk, const double *thn)
 {
     launch_assemble(c->stream, c->nblk, c->g, c->soils, c->zone, c->Ks, c->flags, c->sp, hk, hn, thk, thn,
-                    c->K[c->kcur], c->Can, c->c, c->b, c->Tx, c->Ty, c->Tz, c->diag, c->dinv, c->K32, c->cb32,
-                    c->dinv32);
-    c->launches++;
+                    c->K[0], c->Can, c->c, c->b, c->Tx, c->Ty, c->Tz, c->diag, c->dinv, c->K32, c->cb32,
+                    c->dinv32, nullptr);
 }
 
-// Inner FP32 / FP64 CG iterations launched in growing chunks; the device
-// marks the solve done, later kernels return at once.
-template <class Launch>
-rf_status cg_loop(rf_ctx *c, CgScal *sc_dev, CgScal *sc_host, int max_it, Launch launch_iter)
+// ---------------------------------------------------------------------------
+// Graph construction.  Every loop is a conditional WHILE node whose condition
+// is raised by the kernel just before it and re-set by the last kernel of its
+// body on every launch (to 0 when the loop is over or was skipped), so each
+// loop terminates: PCG at max_it, defect correction at outer_max_it, Picard
+// at n_max.
+// ---------------------------------------------------------------------------
+rf_status cap_begin(rf_ctx *c, cudaGraph_t G, const std::vector<cudaGraphNode_t> &deps)
 {
-    long long launched = 0;
-    int chunk = 2;
-    for (;;) {
-        for (int i = 0; i < chunk; i++, launched++) launch_iter(launched);
-        CUDA_TRY(cudaMemcpyAsync(sc_host, sc_dev, sizeof(CgScal), cudaMemcpyDeviceToHost, c->stream));
-        rf_status st = sync(c);
-        if (st) return st;
-        if (sc_host->done) return RF_OK;
-        if (launched > (long long)max_it + 64)
-            return fail(RF_ERR_DEVICE_TIMEOUT, "CG did not report completion within its iteration budget");
-        chunk = std::min(chunk * 2, 64);
-    }
+    CUDA_TRY(cudaStreamBeginCaptureToGraph(c->cap, G, deps.empty() ? nullptr : deps.data(), nullptr, deps.size(),
+                                           cudaStreamCaptureModeRelaxed));
+    return RF_OK;
 }
 
-// Solve the assembled system from x0 (device) into c->x.  *iters: CG (FP64)
-// or summed inner iterations (mixed).  Returns RF_OK, RF_ERR_CG (max_it /
-// non-finite), or a CUDA error.
-rf_status solve_system(rf_ctx *c, const double *x0, int *iters)
+rf_status cap_end(rf_ctx *c, std::vector<cudaGraphNode_t> &leaves)
+{
+    cudaStreamCaptureStatus st;
+    const cudaGraphNode_t *d = nullptr;
+    size_t n = 0;
+    CUDA_TRY(cudaStreamGetCaptureInfo(c->cap, &st, nullptr, nullptr, &d, nullptr, &n));
+    leaves.assign(d, d + n);
+    cudaGraph_t out;
+    CUDA_TRY(cudaStreamEndCapture(c->cap, &out));
+    CUDA_TRY(cudaGetLastError());
+    return RF_OK;
+}
+
+rf_status add_while(cudaGraph_t parent, const std::vector<cudaGraphNode_t> &deps, cudaGraphConditionalHandle h,
+                    cudaGraphNode_t *node, cudaGraph_t *body)
+{
+    cudaGraphNodeParams np = {};
+    np.type = cudaGraphNodeTypeConditional;
+    np.conditional.handle = h;
+    np.conditional.type = cudaGraphCondTypeWhile;
+    np.conditional.size = 1;
+    CUDA_TRY(cudaGraphAddNode(node, parent, deps.empty() ? nullptr : deps.data(), nullptr, deps.size(), &np));
+    *body = np.conditional.phGraph_out[0];
+    return RF_OK;
+}
+
+#define RF_TRY(x)                              \
+    do {                                       \
+        rf_status s_ = (x);                    \
+        if (s_ != RF_OK) return s_;            \
+    } while (0)
+
+// Linear solve A x = b from x0 into x, appended to `parent` after `deps`
+// (handles created on the top graph `top`).  skip: attempt-over flag or null.
+// Returns the node after which the solution is complete.
+rf_status capture_solve(rf_ctx *c, cudaGraph_t top, cudaGraph_t parent, std::vector<cudaGraphNode_t> deps,
+                        const double *x0, double *x, const int *skip, std::vector<cudaGraphNode_t> &out)
 {
     const Grid &g = c->g;
-    *iters = 0;
+    const int nb = c->nblk;
+    cudaStream_t s = c->cap;
     if (c->prm.precision == RF_PREC_FP64) {
-        launch_cg64_init(c->stream, c->nblk, g, c->flags, x0, c->x, c->b, c->Tx, c->Ty, c->Tz, c->diag, c->dinv,
-                         c->r, c->z, c->prm.tol_cg, c->prm.cg_max_it, c->partials, c->ticket, c->sc);
-        c->launches++;
-        rf_status st = cg_loop(c, c->sc, c->sc_h, c->prm.cg_max_it, [&](long long it) {
-            double *pin = c->p[it & 1], *pout = c->p[(it + 1) & 1];
-            launch_cg64_spmv(c->stream, c->nblk, g, c->flags, c->z, pin, pout, c->q, c->Tx, c->Ty, c->Tz, c->diag,
-                             c->partials, c->ticket, c->sc);
-            launch_cg64_update(c->stream, c->nblk, g, c->x, c->r, c->z, pout, c->q, c->dinv, c->partials, c->ticket,
-                               c->sc);
-            c->launches += 2;
-        });
-        if (st) return st;
-        *iters = c->sc_h->iter;
-        if (c->sc_h->status != CG_OK) return fail(RF_ERR_CG, c->sc_h->status == CG_MAXIT ? "CG reached max_it" : "CG non-finite");
+        cudaGraphConditionalHandle hc;
+        CUDA_TRY(cudaGraphConditionalHandleCreate(&hc, top, 0, 0));
+        const CondSet cc{hc, 1};
+        RF_TRY(cap_begin(c, parent, deps));
+        launch_cg64_init(s, nb, g, c->flags, x0, x, c->b, c->Tx, c->Ty, c->Tz, c->diag, c->dinv, c->r, c->z,
+                         c->prm.tol_cg, c->prm.cg_max_it, c->partials, c->ticket, c->sc, skip, cc);
+        RF_TRY(cap_end(c, deps));
+        cudaGraphNode_t wn;
+        cudaGraph_t body;
+        RF_TRY(add_while(parent, deps, hc, &wn, &body));
+        RF_TRY(cap_begin(c, body, {}));
+        for (int half = 0; half < 2; half++) {
+            double *pin = c->p[half], *pout = c->p[half ^ 1];
+            launch_cg64_spmv(s, nb, g, c->flags, c->z, pin, pout, c->q, c->Tx, c->Ty, c->Tz, c->diag, c->partials,
+                             c->ticket, c->sc);
+            launch_cg64_update(s, nb, g, x, c->r, c->z, pout, c->q, c->dinv, c->partials, c->ticket, c->sc, cc);
+        }
+        std::vector<cudaGraphNode_t> tmp;
+        RF_TRY(cap_end(c, tmp));
+        out = {wn};
         return RF_OK;
     }
-    // mixed: FP64 defect correction around an FP32 inner PCG
-    if (x0 != c->x) CUDA_TRY(cudaMemcpyAsync(c->x, x0, sizeof(double) * g.N, cudaMemcpyDeviceToDevice, c->stream));
-    for (int outer = 0; outer < c->prm.outer_max_it; outer++) {
-        launch_resid64(c->stream, c->nblk, g, c->flags, c->x, c->b, c->Tx, c->Ty, c->Tz, c->diag, c->dinv32, c->r32,
-                       c->z32, c->d32, c->prm.tol_cg, c->prm.tol_inner, c->prm.inner_max_it, c->partials, c->ticket,
-                       c->sc, c->sc_in);
-        c->launches++;
-        CUDA_TRY(cudaMemcpyAsync(c->sc_h, c->sc, sizeof(CgScal), cudaMemcpyDeviceToHost, c->stream));
-        rf_status st = sync(c);
-        if (st) return st;
-        if (c->sc_h->status != CG_OK) return fail(RF_ERR_CG, "non-finite outer residual");
-        if (c->sc_h->done) return RF_OK;
-        st = cg_loop(c, c->sc_in, c->sc_in_h, c->prm.inner_max_it, [&](long long it) {
-            float *pin = c->p32[it & 1], *pout = c->p32[(it + 1) & 1];
-            launch_cg32_spmv(c->stream, c->nblk, g, c->z32, pin, pout, c->q32, c->K32, c->cb32, c->partials,
-                             c->ticket, c->sc_in);
-            launch_cg32_update(c->stream, c->nblk, g, c->d32, c->r32, c->z32, pout, c->q32, c->dinv32, c->partials,
-                               c->ticket, c->sc_in);
-            c->launches += 2;
-        });
-        if (st) return st;
-        *iters += c->sc_in_h->iter;
-        if (c->sc_in_h->status == CG_NONFINITE) return fail(RF_ERR_CG, "inner FP32 CG non-finite");
-        launch_add_correction(c->stream, c->nblk, g, c->x, c->d32);
-        c->launches++;
+    // mixed: defect correction (outer FP64 residual) around FP32 inner PCG
+    cudaGraphConditionalHandle ho, hi;
+    CUDA_TRY(cudaGraphConditionalHandleCreate(&ho, top, 0, 0));
+    CUDA_TRY(cudaGraphConditionalHandleCreate(&hi, top, 0, 0));
+    const CondSet co{ho, 1}, ci{hi, 1};
+    RF_TRY(cap_begin(c, parent, deps));
+    launch_mixed_start(s, nb, g, x0, x, c->sc, c->sc_in, skip, co);
+    RF_TRY(cap_end(c, deps));
+    cudaGraphNode_t wo, wi;
+    cudaGraph_t bo, bi;
+    RF_TRY(add_while(parent, deps, ho, &wo, &bo));
+    std::vector<cudaGraphNode_t> d2;
+    RF_TRY(cap_begin(c, bo, {}));
+    launch_resid64(s, nb, g, c->flags, x, c->b, c->Tx, c->Ty, c->Tz, c->diag, c->dinv32, c->r32, c->z32, c->d32,
+                   c->prm.tol_cg, c->prm.tol_inner, c->prm.inner_max_it, c->prm.outer_max_it, c->partials, c->ticket,
+                   c->sc, c->sc_in, co, ci);
+    RF_TRY(cap_end(c, d2));
+    RF_TRY(add_while(bo, d2, hi, &wi, &bi));
+    RF_TRY(cap_begin(c, bi, {}));
+    for (int half = 0; half < 2; half++) {
+        float *pin = c->p32[half], *pout = c->p32[half ^ 1];
+        launch_cg32_spmv(s, nb, g, c->z32, pin, pout, c->q32, c->K32, c->cb32, c->partials, c->ticket, c->sc_in);
+        launch_cg32_update(s, nb, g, c->d32, c->r32, c->z32, pout, c->q32, c->dinv32, c->partials, c->ticket,
+                           c->sc_in, ci);
     }
-    return fail(RF_ERR_CG, "defect correction reached outer_max_it");
+    std::vector<cudaGraphNode_t> tmp;
+    RF_TRY(cap_end(c, tmp));
+    RF_TRY(cap_begin(c, bo, {wi}));
+    launch_add_correction(s, nb, g, x, c->d32, c->sc, c->sc_in, co);
+    RF_TRY(cap_end(c, tmp));
+    out = {wo};
+    return RF_OK;
+}
+
+void destroy_graphs(rf_ctx *c)
+{
+    if (c->picard_exec) cudaGraphExecDestroy(c->picard_exec);
+    if (c->picard_graph) cudaGraphDestroy(c->picard_graph);
+    if (c->solve_exec) cudaGraphExecDestroy(c->solve_exec);
+    if (c->solve_graph) cudaGraphDestroy(c->solve_graph);
+    c->picard_exec = nullptr;
+    c->picard_graph = nullptr;
+    c->solve_exec = nullptr;
+    c->solve_graph = nullptr;
+}
+
+// One Picard attempt as a graph: WHILE(Picard) { half A ; half B }, where a
+// half is assemble -> linear solve -> closures + exit test -> water balance,
+// half A iterating h^k = H0 -> x = H1 (K0 -> K1) and half B the reverse, so
+// the buffers never move.  Kernels of a half that starts after the attempt
+// ended return at once.
+rf_status build_picard_graph(rf_ctx *c)
+{
+    cudaGraph_t G;
+    CUDA_TRY(cudaGraphCreate(&G, 0));
+    c->picard_graph = G;
+    cudaGraphConditionalHandle hp;
+    CUDA_TRY(cudaGraphConditionalHandleCreate(&hp, G, 1, cudaGraphCondAssignDefault));
+    const CondSet cp{hp, 1};
+    cudaGraphNode_t wp;
+    cudaGraph_t body;
+    RF_TRY(add_while(G, {}, hp, &wp, &body));
+    const Grid &g = c->g;
+    const int nb = c->nblk;
+    cudaStream_t s = c->cap;
+    const int *skip = &c->ctl->done;
+    double *H[2] = {c->hk, c->x};
+    std::vector<cudaGraphNode_t> deps;
+    for (int half = 0; half < 2; half++) {
+        double *hk = H[half], *x = H[half ^ 1];
+        double *Kin = c->K[half], *Kout = c->K[half ^ 1];
+        RF_TRY(cap_begin(c, body, deps));
+        launch_assemble(s, nb, g, c->soils, c->zone, c->Ks, c->flags, c->sp, hk, c->h, c->theta_k, c->theta_n, Kin,
+                        c->Can, c->c, c->b, c->Tx, c->Ty, c->Tz, c->diag, c->dinv, c->K32, c->cb32, c->dinv32, skip);
+        RF_TRY(cap_end(c, deps));
+        RF_TRY(capture_solve(c, G, body, deps, hk, x, skip, deps));
+        RF_TRY(cap_begin(c, body, deps));
+        const CgScal *stat = c->sc;   // FP64 solve, or outer defect-correction loop
+        const CgScal *cnt = c->prm.precision == RF_PREC_FP64 ? c->sc : c->sc_in;
+        launch_closure_picard(s, nb, g, c->soils, c->zone, c->Ks, c->flags, x, hk, c->theta_k, Kout, c->Can,
+                              c->partials, c->ticket, c->ctl, stat, cnt, cp);
+        launch_mass_balance(s, nb, g, c->soils, c->zone, c->Ks, c->flags, c->sp, x, c->h, c->c, Kin, c->theta_k,
+                            c->theta_n, c->partials, c->ticket, c->res, c->ctl);
+        RF_TRY(cap_end(c, deps));
+    }
+    CUDA_TRY(cudaGraphInstantiate(&c->picard_exec, G, 0));
+    return RF_OK;
+}
+
+rf_status build_solve_graph(rf_ctx *c)
+{
+    cudaGraph_t G;
+    CUDA_TRY(cudaGraphCreate(&G, 0));
+    c->solve_graph = G;
+    std::vector<cudaGraphNode_t> out;
+    RF_TRY(capture_solve(c, G, G, {}, c->hk, c->x, nullptr, out));
+    CUDA_TRY(cudaGraphInstantiate(&c->solve_exec, G, 0));
+    return RF_OK;
+}
+
+// Solve the assembled system from hk into x (kernel-level entry point).
+rf_status solve_system(rf_ctx *c, int *iters)
+{
+    if (!c->solve_exec) RF_TRY(build_solve_graph(c));
+    CUDA_TRY(cudaGraphLaunch(c->solve_exec, c->stream));
+    CUDA_TRY(cudaMemcpyAsync(c->sc_h, c->sc, sizeof(CgScal), cudaMemcpyDeviceToHost, c->stream));
+    CUDA_TRY(cudaMemcpyAsync(c->sc_in_h, c->sc_in, sizeof(CgScal), cudaMemcpyDeviceToHost, c->stream));
+    RF_TRY(sync(c));
+    *iters = c->prm.precision == RF_PREC_FP64 ? c->sc_h->total : c->sc_in_h->total;
+    if (c->sc_h->status != CG_OK)
+        return fail(RF_ERR_CG, c->sc_h->status == CG_MAXIT ? "linear solve reached its iteration cap" : "non-finite linear solve");
+    return RF_OK;
 }
 
 struct Attempt {
@@ -253,49 +378,40 @@ struct Attempt {
     StepResults mb{};
 };
 
-// One Picard attempt at step size dt from the accepted state h (Sec. 2.2).
+// One Picard attempt at step size dt from the accepted state h (Sec. 2.2),
+// run on the device as one graph launch; one host synchronisation.
 rf_status attempt(rf_ctx *c, double dt, Attempt &A)
 {
+    if (!c->picard_exec) RF_TRY(build_picard_graph(c));
     fill_step_params(c, dt);
+    PicardCtl &ctl = *c->ctl_h;
+    ctl = PicardCtl{};
+    ctl.tol = c->prm.tol_picard;
+    ctl.n_max = c->prm.n_max;
     CUDA_TRY(cudaMemcpyAsync(c->sp, c->sp_h, sizeof(StepParams), cudaMemcpyHostToDevice, c->stream));
+    CUDA_TRY(cudaMemcpyAsync(c->ctl, c->ctl_h, sizeof(PicardCtl), cudaMemcpyHostToDevice, c->stream));
     CUDA_TRY(cudaMemcpyAsync(c->hk, c->h, sizeof(double) * c->g.N, cudaMemcpyDeviceToDevice, c->stream));
     if (!c->closure_at_h) {
-        run_closure(c, c->hk, nullptr, c->theta_k, c->kcur);
+        run_closure(c, c->hk, nullptr, c->theta_k, 0);
         c->closure_at_h = true;
     }
-    for (int it = 1; it <= c->prm.n_max; it++) {
-        run_assemble(c, c->hk, c->h, c->theta_k, c->theta_n);
-        int cg = 0;
-        rf_status st = solve_system(c, c->hk, &cg);
-        A.picard = it;
+    CUDA_TRY(cudaGraphLaunch(c->picard_exec, c->stream));
+    CUDA_TRY(cudaMemcpyAsync(c->ctl_h, c->ctl, sizeof(PicardCtl), cudaMemcpyDeviceToHost, c->stream));
+    CUDA_TRY(cudaMemcpyAsync(c->res_h, c->res, sizeof(StepResults), cudaMemcpyDeviceToHost, c->stream));
+    RF_TRY(sync(c));
+    A.picard = ctl.it;
+    A.cg = ctl.cg_total;
+    A.max_dh = ctl.max_dh;
+    if (ctl.conv) {
+        A.converged = true;
+        A.mb = *c->res_h;
+        // the last iterate and its closures: H[it & 1], K[it & 1]
+        const int f = ctl.it & 1;
+        launch_accept(c->stream, c->nblk, c->g, f ? c->x : c->hk, c->h, c->theta_k, c->theta_n, c->K[1], c->K[0], f);
+    } else {
+        A.status = ctl.fail ? RF_ERR_CG : RF_ERR_PICARD;
         c->closure_at_h = false;
-        if (st == RF_ERR_CG) { A.status = RF_ERR_CG; break; }
-        if (st) return st;
-        A.cg += cg;
-        // closures at the new iterate, with the Picard update max|x - h^k|
-        const int knew = c->kcur ^ 1;
-        run_closure(c, c->x, c->hk, c->theta_k, knew);
-        CUDA_TRY(cudaMemcpyAsync(c->res_h, c->res, sizeof(StepResults), cudaMemcpyDeviceToHost, c->stream));
-        st = sync(c);
-        if (st) return st;
-        std::swap(c->hk, c->x);
-        const int kold = c->kcur;
-        c->kcur = knew;
-        A.max_dh = c->res_h->max_dh;
-        if (c->res_h->nonfinite) { A.status = RF_ERR_CG; break; }
-        if (A.max_dh <= c->prm.tol_picard) {
-            A.converged = true;
-            launch_mass_balance(c->stream, c->nblk, c->g, c->soils, c->zone, c->Ks, c->flags, c->sp, c->hk, c->h,
-                                c->c, c->K[kold], c->theta_k, c->theta_n, c->partials, c->ticket, c->res);
-            c->launches++;
-            CUDA_TRY(cudaMemcpyAsync(c->res_h, c->res, sizeof(StepResults), cudaMemcpyDeviceToHost, c->stream));
-            st = sync(c);
-            if (st) return st;
-            A.mb = *c->res_h;
-            break;
-        }
     }
-    if (!A.converged && A.status == RF_OK) A.status = RF_ERR_PICARD;
     return RF_OK;
 }
 
@@ -326,8 +442,6 @@ rf_status do_step(rf_ctx *c, double t_stop, rf_step_info *info)
         if (st) { c->dt_nom = dt_nom0; c->easy = easy0; return st; }
         cg_total += A.cg;
         if (A.converged) {
-            std::swap(c->h, c->hk);
-            std::swap(c->theta_n, c->theta_k);
             c->closure_at_h = true;
             double tn = c->t + dt;
             if (std::fabs(tn - bp) <= t_tol(tn)) tn = bp;
@@ -365,7 +479,6 @@ rf_status do_step(rf_ctx *c, double t_stop, rf_step_info *info)
 rf_status storage_of_theta_n(rf_ctx *c, double *out)
 {
     launch_storage(c->stream, c->nblk, c->g, c->flags, c->theta_n, c->partials, c->ticket, c->res);
-    c->launches++;
     CUDA_TRY(cudaMemcpyAsync(c->res_h, c->res, sizeof(StepResults), cudaMemcpyDeviceToHost, c->stream));
     rf_status st = sync(c);
     if (st) return st;
@@ -450,6 +563,8 @@ rf_status rf_mesh_create(const rf_mesh_desc *mesh, const rf_solver_params *param
         g.wb[f] = A[f] / (0.5 * d[f]);
     }
     for (int a = 0; a < 3; a++) g.w32[a] = (float)(A[2 * a] / d[2 * a]);
+    g.fx = make_fastdiv((unsigned int)g.nx);
+    g.fxy = make_fastdiv((unsigned int)g.sxy);
     // grid: at most 8 resident blocks of 256 threads per SM
     const long long want = (N + RED_THREADS - 1) / RED_THREADS;
     c->nblk = (int)std::max(1LL, std::min(want, (long long)c->num_sms * 8));
@@ -484,7 +599,8 @@ rf_status rf_mesh_create(const rf_mesh_desc *mesh, const rf_solver_params *param
               alloc_n(c, c->dinv32, N) && alloc_n(c, c->r32, N) && alloc_n(c, c->z32, N) &&
               alloc_n(c, c->p32[0], N) && alloc_n(c, c->p32[1], N) && alloc_n(c, c->q32, N) &&
               alloc_n(c, c->d32, N) && alloc_n(c, c->partials, (size_t)8 * c->nblk) && alloc_n(c, c->ticket, 64) &&
-              alloc_n(c, c->sc, 1) && alloc_n(c, c->sc_in, 1) && alloc_n(c, c->res, 1) && alloc_n(c, c->sp, 1);
+              alloc_n(c, c->sc, 1) && alloc_n(c, c->sc_in, 1) && alloc_n(c, c->res, 1) && alloc_n(c, c->sp, 1) &&
+              alloc_n(c, c->ctl, 1) && alloc_n(c, c->ctr, 2 * KK_COUNT);
     if (!ok) {
         rf_destroy(c);
         return fail(RF_ERR_NOMEM, "device allocation failed");
@@ -492,12 +608,21 @@ rf_status rf_mesh_create(const rf_mesh_desc *mesh, const rf_solver_params *param
     if (cudaMallocHost(&c->sc_h, sizeof(CgScal)) != cudaSuccess ||
         cudaMallocHost(&c->sc_in_h, sizeof(CgScal)) != cudaSuccess ||
         cudaMallocHost(&c->res_h, sizeof(StepResults)) != cudaSuccess ||
-        cudaMallocHost(&c->sp_h, sizeof(StepParams)) != cudaSuccess) {
+        cudaMallocHost(&c->sp_h, sizeof(StepParams)) != cudaSuccess ||
+        cudaMallocHost(&c->ctl_h, sizeof(PicardCtl)) != cudaSuccess ||
+        cudaMallocHost(&c->ctr_h, 2 * KK_COUNT * sizeof(unsigned long long)) != cudaSuccess) {
         rf_destroy(c);
         return fail(RF_ERR_NOMEM, "pinned host allocation failed");
     }
+    if (cudaStreamCreateWithFlags(&c->cap, cudaStreamNonBlocking) != cudaSuccess) {
+        rf_destroy(c);
+        return fail(RF_ERR_CUDA, "capture stream creation failed");
+    }
+    g.ctr = c->ctr;
     cudaError_t e = cudaMemcpyAsync(c->flags, c->flags_h.data(), N, cudaMemcpyHostToDevice, c->stream);
     if (e == cudaSuccess) e = cudaMemsetAsync(c->ticket, 0, 64 * sizeof(unsigned int), c->stream);
+    if (e == cudaSuccess) e = cudaMemsetAsync(c->ctr, 0, 2 * KK_COUNT * sizeof(unsigned long long), c->stream);
+    if (e == cudaSuccess) e = cudaMemsetAsync(c->ctl, 0, sizeof(PicardCtl), c->stream);
     // vectors whose inactive entries must read as zero
     for (double *v : {c->p[0], c->p[1], c->q, c->r, c->z, c->h, c->hk, c->x})
         if (e == cudaSuccess) e = cudaMemsetAsync(v, 0, sizeof(double) * N, c->stream);
@@ -516,6 +641,8 @@ void rf_destroy(rf_ctx *c)
 {
     if (!c) return;
     cudaStreamSynchronize(c->stream);
+    destroy_graphs(c);
+    if (c->cap) cudaStreamDestroy(c->cap);
     for (void *ptr : c->allocations) {
         if (c->has_alloc) c->alloc.free(ptr, c->alloc.user);
         else cudaFree(ptr);
@@ -524,6 +651,8 @@ void rf_destroy(rf_ctx *c)
     if (c->sc_in_h) cudaFreeHost(c->sc_in_h);
     if (c->res_h) cudaFreeHost(c->res_h);
     if (c->sp_h) cudaFreeHost(c->sp_h);
+    if (c->ctl_h) cudaFreeHost(c->ctl_h);
+    if (c->ctr_h) cudaFreeHost(c->ctr_h);
     delete c;
 }
 
@@ -531,6 +660,8 @@ rf_status rf_set_params(rf_ctx *c, const rf_solver_params *params)
 {
     if (!c || !params) return fail(RF_ERR_ARG, "null argument");
     if (rf_status st = check_params(params)) return st;
+    CUDA_TRY(cudaStreamSynchronize(c->stream));
+    destroy_graphs(c);   // tolerances and caps are baked into the graphs
     c->prm = *params;
     return RF_OK;
 }
@@ -595,7 +726,7 @@ static rf_status state_set_common(rf_ctx *c, double t)
     c->dt_nom = std::min(c->prm.dt0, c->prm.dt_max);
     c->easy = 0;
     c->steps = 0;
-    run_closure(c, c->h, nullptr, c->theta_n, c->kcur);
+    run_closure(c, c->h, nullptr, c->theta_n, 0);
     c->closure_at_h = true;
     double st0 = 0.0;
     if (rf_status st = storage_of_theta_n(c, &st0)) return st;
@@ -722,13 +853,13 @@ rf_status rf_assemble(rf_ctx *c, const double *d_hk, const double *d_hn, double 
     c->t = t_save;
     CUDA_TRY(cudaMemcpyAsync(c->sp, c->sp_h, sizeof(StepParams), cudaMemcpyHostToDevice, c->stream));
     // theta*(h^n) into theta_n's scratch twin, then closures at h^k
-    run_closure(c, d_hn, nullptr, c->theta_n, c->kcur);
-    run_closure(c, d_hk, nullptr, c->theta_k, c->kcur);
+    run_closure(c, d_hn, nullptr, c->theta_n, 0);
+    run_closure(c, d_hk, nullptr, c->theta_k, 0);
     run_assemble(c, d_hk, d_hn, c->theta_k, c->theta_n);
     c->closure_at_h = false;
     c->has_state = false;    // theta_n was overwritten: the state must be set again before stepping
     const size_t nb = sizeof(double) * c->g.N;
-    if (d_K) CUDA_TRY(cudaMemcpyAsync(d_K, c->K[c->kcur], nb, cudaMemcpyDeviceToDevice, c->stream));
+    if (d_K) CUDA_TRY(cudaMemcpyAsync(d_K, c->K[0], nb, cudaMemcpyDeviceToDevice, c->stream));
     if (d_theta) CUDA_TRY(cudaMemcpyAsync(d_theta, c->theta_k, nb, cudaMemcpyDeviceToDevice, c->stream));
     if (d_c) CUDA_TRY(cudaMemcpyAsync(d_c, c->c, nb, cudaMemcpyDeviceToDevice, c->stream));
     if (d_b) CUDA_TRY(cudaMemcpyAsync(d_b, c->b, nb, cudaMemcpyDeviceToDevice, c->stream));
@@ -740,7 +871,6 @@ rf_status rf_apply(rf_ctx *c, const double *d_x, double *d_y)
 {
     if (!c || !d_x || !d_y) return fail(RF_ERR_ARG, "null argument");
     launch_apply64(c->stream, c->nblk, c->g, c->flags, d_x, d_y, c->Tx, c->Ty, c->Tz, c->diag);
-    c->launches++;
     return sync(c);
 }
 
@@ -749,7 +879,7 @@ rf_status rf_solve(rf_ctx *c, double *d_x, int *iters)
     if (!c || !d_x) return fail(RF_ERR_ARG, "null argument");
     int it = 0;
     CUDA_TRY(cudaMemcpyAsync(c->hk, d_x, sizeof(double) * c->g.N, cudaMemcpyDeviceToDevice, c->stream));
-    rf_status st = solve_system(c, c->hk, &it);
+    rf_status st = solve_system(c, &it);
     if (iters) *iters = it;
     if (st) return st;
     CUDA_TRY(cudaMemcpyAsync(d_x, c->x, sizeof(double) * c->g.N, cudaMemcpyDeviceToDevice, c->stream));
@@ -757,6 +887,123 @@ rf_status rf_solve(rf_ctx *c, double *d_x, int *iters)
     return sync(c);
 }
 
-unsigned long long rf_launch_count(rf_ctx *c) { return c ? c->launches : 0ULL; }
+unsigned long long rf_launch_count(rf_ctx *c)
+{
+    if (!c) return 0ULL;
+    if (cudaMemcpyAsync(c->ctr_h, c->ctr, 2 * KK_COUNT * sizeof(unsigned long long), cudaMemcpyDeviceToHost,
+                        c->stream) != cudaSuccess ||
+        cudaStreamSynchronize(c->stream) != cudaSuccess)
+        return 0ULL;
+    unsigned long long s = 0;
+    for (int k = 0; k < KK_COUNT; k++) s += c->ctr_h[2 * k];
+    return s;
+}
+
+int rf_launch_counts(rf_ctx *c, unsigned long long *out, int cap)
+{
+    if (!c || !out) return 0;
+    if (cudaMemcpyAsync(c->ctr_h, c->ctr, 2 * KK_COUNT * sizeof(unsigned long long), cudaMemcpyDeviceToHost,
+                        c->stream) != cudaSuccess ||
+        cudaStreamSynchronize(c->stream) != cudaSuccess)
+        return 0;
+    const int n = std::min(cap, 2 * (int)KK_COUNT);
+    for (int i = 0; i < n; i++) out[i] = c->ctr_h[i];
+    return n;
+}
+
+rf_status rf_profile_kernel(rf_ctx *c, int kind, int reps, double *avg_ms, double *bytes_per_launch)
+{
+    if (!c || reps < 1 || kind < RF_K_CLOSURE || kind > RF_K_CG32_UPDATE) return fail(RF_ERR_ARG, "bad argument");
+    if (!c->has_state) return fail(RF_ERR_STATE, "set the state first");
+    // algorithmic bytes per active cell (reads + writes, each array once)
+    static const double per_cell[] = {50.0, 117.0, 65.0, 64.0, 65.0, 24.0, 32.0};
+    static const bool reads_flags[] = {true, true, true, false, true, false, false};
+    const Grid &g = c->g;
+    const int nb = c->nblk;
+    cudaStream_t s = c->stream;
+    const CondSet none{0, 0};
+    // the system at the current state
+    fill_step_params(c, c->dt_nom);
+    CUDA_TRY(cudaMemcpyAsync(c->sp, c->sp_h, sizeof(StepParams), cudaMemcpyHostToDevice, s));
+    CUDA_TRY(cudaMemcpyAsync(c->hk, c->h, sizeof(double) * g.N, cudaMemcpyDeviceToDevice, s));
+    run_closure(c, c->hk, nullptr, c->theta_k, 0);
+    run_assemble(c, c->hk, c->h, c->theta_k, c->theta_n);
+    c->closure_at_h = false;
+    if (kind == RF_K_CG64_SPMV || kind == RF_K_CG64_UPDATE)   // a solve that never converges
+        launch_cg64_init(s, nb, g, c->flags, c->hk, c->x, c->b, c->Tx, c->Ty, c->Tz, c->diag, c->dinv, c->r, c->z,
+                         0.0, 1 << 30, c->partials, c->ticket, c->sc, nullptr, none);
+    if (kind >= RF_K_RESID64) {
+        launch_mixed_start(s, nb, g, c->hk, c->x, c->sc, c->sc_in, nullptr, none);
+        launch_resid64(s, nb, g, c->flags, c->x, c->b, c->Tx, c->Ty, c->Tz, c->diag, c->dinv32, c->r32, c->z32,
+                       c->d32, 0.0, 1e-30, 1 << 30, 1 << 30, c->partials, c->ticket, c->sc, c->sc_in, none, none);
+    }
+    std::vector<cudaEvent_t> ev(2 * reps);
+    for (auto &e : ev) CUDA_TRY(cudaEventCreate(&e));
+    for (int i = 0; i < reps; i++) {
+        double *pin = c->p[i & 1], *pout = c->p[(i + 1) & 1];
+        float *qin = c->p32[i & 1], *qout = c->p32[(i + 1) & 1];
+        auto timed = [&](auto &&launch) {
+            cudaEventRecord(ev[2 * i], s);
+            launch();
+            cudaEventRecord(ev[2 * i + 1], s);
+        };
+        switch (kind) {
+        case RF_K_CLOSURE:
+            timed([&] { launch_closure(s, nb, g, c->soils, c->zone, c->Ks, c->flags, c->hk, c->h, c->theta_k, c->K[1],
+                                       c->Can, c->partials, c->ticket, c->res); });
+            break;
+        case RF_K_ASSEMBLE:
+            timed([&] { run_assemble(c, c->hk, c->h, c->theta_k, c->theta_n); });
+            break;
+        case RF_K_CG64_SPMV:
+        case RF_K_CG64_UPDATE:
+            if (kind == RF_K_CG64_SPMV)
+                timed([&] { launch_cg64_spmv(s, nb, g, c->flags, c->z, pin, pout, c->q, c->Tx, c->Ty, c->Tz, c->diag,
+                                             c->partials, c->ticket, c->sc); });
+            else
+                launch_cg64_spmv(s, nb, g, c->flags, c->z, pin, pout, c->q, c->Tx, c->Ty, c->Tz, c->diag, c->partials,
+                                 c->ticket, c->sc);
+            if (kind == RF_K_CG64_UPDATE)
+                timed([&] { launch_cg64_update(s, nb, g, c->x, c->r, c->z, pout, c->q, c->dinv, c->partials, c->ticket,
+                                               c->sc, none); });
+            else
+                launch_cg64_update(s, nb, g, c->x, c->r, c->z, pout, c->q, c->dinv, c->partials, c->ticket, c->sc,
+                                   none);
+            break;
+        case RF_K_RESID64:
+            timed([&] { launch_resid64(s, nb, g, c->flags, c->x, c->b, c->Tx, c->Ty, c->Tz, c->diag, c->dinv32,
+                                       c->r32, c->z32, c->d32, 0.0, 1e-30, 1 << 30, 1 << 30, c->partials, c->ticket,
+                                       c->sc, c->sc_in, none, none); });
+            break;
+        default:
+            if (kind == RF_K_CG32_SPMV)
+                timed([&] { launch_cg32_spmv(s, nb, g, c->z32, qin, qout, c->q32, c->K32, c->cb32, c->partials,
+                                             c->ticket, c->sc_in); });
+            else
+                launch_cg32_spmv(s, nb, g, c->z32, qin, qout, c->q32, c->K32, c->cb32, c->partials, c->ticket,
+                                 c->sc_in);
+            if (kind == RF_K_CG32_UPDATE)
+                timed([&] { launch_cg32_update(s, nb, g, c->d32, c->r32, c->z32, qout, c->q32, c->dinv32, c->partials,
+                                               c->ticket, c->sc_in, none); });
+            else
+                launch_cg32_update(s, nb, g, c->d32, c->r32, c->z32, qout, c->q32, c->dinv32, c->partials, c->ticket,
+                                   c->sc_in, none);
+            break;
+        }
+    }
+    rf_status st = sync(c);
+    double total = 0.0;
+    for (int i = 0; st == RF_OK && i < reps; i++) {
+        float ms = 0.0f;
+        if (cudaEventElapsedTime(&ms, ev[2 * i], ev[2 * i + 1]) != cudaSuccess) st = fail(RF_ERR_CUDA, "event timing");
+        total += ms;
+    }
+    for (auto &e : ev) cudaEventDestroy(e);
+    if (st) return st;
+    if (avg_ms) *avg_ms = total / reps;
+    if (bytes_per_launch)
+        *bytes_per_launch = per_cell[kind] * c->n_active + (reads_flags[kind] ? (double)g.N : 0.0);
+    return RF_OK;
+}
 
 }  // extern "C"

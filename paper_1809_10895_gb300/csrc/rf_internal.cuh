@@ -16,6 +16,36 @@ enum { M_VG = 0, M_GARDNER = 1 };
 // boundary condition of face class f applies; bit 7 = active cell.
 constexpr uint8_t FLAG_ACTIVE = 0x80;
 
+// Division of 0 <= n < 2^31 by an invariant d >= 1 with one multiply and a
+// shift (Granlund & Montgomery, "Division by invariant integers using
+// multiplication", PLDI 1994): q = (n * m) >> (32 + l) with l = ceil(log2 d)
+// and m = ceil(2^(32+l) / d) < 2^33; exact because n * (m d - 2^(32+l)) <
+// 2^31 * d <= 2^(32+l).
+struct FastDiv {
+    unsigned long long m;
+    int shift;      // 32 + l
+    int pad;
+};
+
+inline FastDiv make_fastdiv(unsigned int d)
+{
+    int l = 0;
+    while ((1ULL << l) < d) l++;
+    const unsigned long long num = 1ULL << (32 + l);
+    FastDiv f;
+    f.m = (num + d - 1) / d;
+    f.shift = 32 + l;
+    f.pad = 0;
+    return f;
+}
+
+// Kernel kinds, for the per-kind launch counters (launched / did work).
+enum KernelKind {
+    KK_CLOSURE = 0, KK_CLOSURE_PICARD, KK_ASSEMBLE, KK_CG64_INIT, KK_CG64_SPMV, KK_CG64_UPDATE, KK_APPLY64,
+    KK_MIXED_START, KK_RESID64, KK_CG32_SPMV, KK_CG32_UPDATE, KK_ADD_CORRECTION, KK_MASS_BALANCE, KK_STORAGE,
+    KK_ACCEPT, KK_COUNT
+};
+
 struct DevSoil {
     int model;
     double theta_r, theta_s, alpha, n, m, S;
@@ -30,6 +60,8 @@ struct Grid {
     double w[6];      // A/d for interior faces
     double wb[6];     // A/(d/2) for boundary (half-cell) faces
     float w32[3];     // A/d per axis, FP32 (mixed-precision operator)
+    FastDiv fx, fxy;  // division by nx and by nx*ny
+    unsigned long long *ctr;   // per-kind counters: [2 kind] launches, [2 kind + 1] launches that did work
 };
 
 // Values that change per step attempt; lives in device memory so kernels can
@@ -46,20 +78,34 @@ struct CgScal {
     double pq;        // p.q
     double alpha, beta;
     double rr;        // ||r||^2 (recursive)
-    double stop2;     // converged when rr <= stop2
+    double stop2;     // converged when ||r|| <= stop2
     double bb;        // ||b||^2 (FP64) / ||r0||^2 (inner)
-    int iter;
+    int iter;         // iterations of this solve
     int done;
-    int status;       // 0 ok/converged, 1 max_it, 2 non-finite/breakdown
+    int status;       // CG_OK, CG_MAXIT, CG_NONFINITE
     int max_it;
+    int total;        // iterations accumulated over inner solves (mixed)
+    int pad;
 };
 
 enum { CG_OK = 0, CG_MAXIT = 1, CG_NONFINITE = 2 };
 
-// Reduction workspace: per-block partials, a ticket counter and results.
-struct RedBuf {
-    double *partials;     // nblocks * 8 doubles
-    unsigned int *ticket; // one counter per reduction slot
+// Picard-loop control for a device-resident attempt (Sec. 2.2 / 2.3).
+struct PicardCtl {
+    double tol;        // Picard tolerance on max|dh|
+    double max_dh;     // last update
+    int n_max;         // iteration cap
+    int it;            // iterations done (linear solves)
+    int conv, fail, done;
+    int cg_total;      // CG iterations over the attempt
+    int mb_pending;    // water balance of the converged system still to reduce
+    int pad;
+};
+
+// A conditional-node handle a kernel may set (use = 0 outside graphs).
+struct CondSet {
+    unsigned long long h;
+    int use;
 };
 
 // Results of the per-step reductions, read back by the host.
@@ -75,51 +121,114 @@ struct StepResults {
 
 constexpr int RED_THREADS = 256;
 
+#ifdef __CUDACC__
+__device__ __forceinline__ void count_launch(const Grid &g, int kind)
+{
+    if (blockIdx.x == 0 && threadIdx.x == 0) atomicAdd(&g.ctr[2 * kind], 1ULL);
+}
+__device__ __forceinline__ void count_work(const Grid &g, int kind)
+{
+    if (blockIdx.x == 0 && threadIdx.x == 0) atomicAdd(&g.ctr[2 * kind + 1], 1ULL);
+}
+__device__ __forceinline__ unsigned int fdiv(unsigned int n, const FastDiv &f)
+{
+    return (unsigned int)(((unsigned long long)n * f.m) >> f.shift);
+}
+// (i, j, k) of cell p (p < 2^31)
+__device__ __forceinline__ void cell_ijk(const Grid &g, long long p, int &i, int &j, int &k)
+{
+    const unsigned int u = (unsigned int)p;
+    const unsigned int kk = fdiv(u, g.fxy);
+    const unsigned int r = u - kk * (unsigned int)g.sxy;
+    const unsigned int jj = fdiv(r, g.fx);
+    i = (int)(r - jj * (unsigned int)g.nx);
+    j = (int)jj;
+    k = (int)kk;
+}
+// 1/a to about full double precision: single-precision estimate refined by
+// two Newton-Raphson steps r <- r + r (1 - a r) (each doubles the correct
+// bits: 23 -> 46 -> 92).  Falls back to IEEE division outside the range in
+// which the single-precision estimate is normal.
+__device__ __forceinline__ double rcp64(double a)
+{
+    const double m = fabs(a);
+    if (!(m > 1e-30 && m < 1e30)) return 1.0 / a;
+    float rf;
+    asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(rf) : "f"((float)a));
+    double r = (double)rf;
+    double e = fma(-a, r, 1.0);
+    r = fma(r, e, r);
+    e = fma(-a, r, 1.0);
+    return fma(r, e, r);
+}
+__device__ __forceinline__ void set_cond(const CondSet &c, unsigned int v)
+{
+    if (c.use) cudaGraphSetConditional(c.h, v);
+}
+#endif
+
 // ---- launch entry points implemented in the .cu files --------------------
 void launch_closure(cudaStream_t s, int nblk, const Grid &g, const DevSoil *soils, const uint8_t *zone,
                     const double *Ks, const uint8_t *flags, const double *h, const double *hprev,
                     double *theta, double *K, double *Can, double *partials, unsigned int *ticket,
                     StepResults *res);
 
+// Closures at the new Picard iterate x with the exit test against h^k; ends a
+// Picard iteration (updates ctl, sets the Picard loop condition).
+void launch_closure_picard(cudaStream_t s, int nblk, const Grid &g, const DevSoil *soils, const uint8_t *zone,
+                           const double *Ks, const uint8_t *flags, const double *x, const double *hk,
+                           double *theta, double *K, double *Can, double *partials, unsigned int *ticket,
+                           PicardCtl *ctl, const CgScal *cg_status, const CgScal *cg_count, CondSet cond);
+
 void launch_assemble(cudaStream_t s, int nblk, const Grid &g, const DevSoil *soils, const uint8_t *zone,
                      const double *Ks, const uint8_t *flags, const StepParams *sp, const double *hk,
                      const double *hn, const double *theta_k, const double *theta_n, const double *K,
                      const double *Can, double *c, double *b, double *Tx, double *Ty, double *Tz,
-                     double *diag, double *dinv, float *K32, float *cb32, float *dinv32);
+                     double *diag, double *dinv, float *K32, float *cb32, float *dinv32, const int *skip);
 
 void launch_mass_balance(cudaStream_t s, int nblk, const Grid &g, const DevSoil *soils, const uint8_t *zone,
                          const double *Ks, const uint8_t *flags, const StepParams *sp, const double *x,
                          const double *hn, const double *c, const double *Kold, const double *theta_x,
-                         const double *theta_n, double *partials, unsigned int *ticket, StepResults *res);
+                         const double *theta_n, double *partials, unsigned int *ticket, StepResults *res,
+                         PicardCtl *ctl);
 
 void launch_storage(cudaStream_t s, int nblk, const Grid &g, const uint8_t *flags, const double *theta,
                     double *partials, unsigned int *ticket, StepResults *res);
+
+// Accept a converged attempt: h <- x_final, theta_n <- theta_k, K0 <- K1 (copyK).
+void launch_accept(cudaStream_t s, int nblk, const Grid &g, const double *x_final, double *h,
+                   const double *theta_k, double *theta_n, const double *K1, double *K0, int copyK);
 
 // FP64 PCG (Jacobi), stored face coefficients.
 void launch_cg64_init(cudaStream_t s, int nblk, const Grid &g, const uint8_t *flags, const double *x0,
                       double *x, const double *b, const double *Tx, const double *Ty, const double *Tz,
                       const double *diag, const double *dinv, double *r, double *z, double tol,
-                      int max_it, double *partials, unsigned int *ticket, CgScal *sc);
+                      int max_it, double *partials, unsigned int *ticket, CgScal *sc, const int *skip,
+                      CondSet cond);
 void launch_cg64_spmv(cudaStream_t s, int nblk, const Grid &g, const uint8_t *flags, const double *z,
                       const double *p_in, double *p_out, double *q, const double *Tx, const double *Ty,
                       const double *Tz, const double *diag, double *partials, unsigned int *ticket, CgScal *sc);
 void launch_cg64_update(cudaStream_t s, int nblk, const Grid &g, double *x, double *r, double *z,
                         const double *p, const double *q, const double *dinv, double *partials,
-                        unsigned int *ticket, CgScal *sc);
+                        unsigned int *ticket, CgScal *sc, CondSet cond);
 void launch_apply64(cudaStream_t s, int nblk, const Grid &g, const uint8_t *flags, const double *x, double *y,
                     const double *Tx, const double *Ty, const double *Tz, const double *diag);
 
 // Mixed precision: FP64 outer residual + FP32 inner PCG (recomputed faces).
+void launch_mixed_start(cudaStream_t s, int nblk, const Grid &g, const double *x0, double *x, CgScal *outer,
+                        CgScal *inner, const int *skip, CondSet cond_outer);
 void launch_resid64(cudaStream_t s, int nblk, const Grid &g, const uint8_t *flags, const double *x,
                     const double *b, const double *Tx, const double *Ty, const double *Tz,
                     const double *diag, const float *dinv32, float *r32, float *z32, float *d32,
-                    double tol, double tol_inner, int inner_max_it, double *partials,
-                    unsigned int *ticket, CgScal *outer, CgScal *inner);
+                    double tol, double tol_inner, int inner_max_it, int outer_max_it, double *partials,
+                    unsigned int *ticket, CgScal *outer, CgScal *inner, CondSet cond_outer, CondSet cond_inner);
 void launch_cg32_spmv(cudaStream_t s, int nblk, const Grid &g, const float *z, const float *p_in, float *p_out,
                       float *q, const float *K32, const float *cb32, double *partials, unsigned int *ticket,
                       CgScal *sc);
 void launch_cg32_update(cudaStream_t s, int nblk, const Grid &g, float *x, float *r, float *z, const float *p,
-                        const float *q, const float *dinv, double *partials, unsigned int *ticket, CgScal *sc);
-void launch_add_correction(cudaStream_t s, int nblk, const Grid &g, double *x, const float *d);
+                        const float *q, const float *dinv, double *partials, unsigned int *ticket, CgScal *sc,
+                        CondSet cond);
+void launch_add_correction(cudaStream_t s, int nblk, const Grid &g, double *x, const float *d, CgScal *outer,
+                           const CgScal *inner, CondSet cond_outer);
 
 }  // namespace rf

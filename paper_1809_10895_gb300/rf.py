@@ -100,7 +100,14 @@ SIGNATURES = {
     "rf_apply": (C.c_int, [_VP, _VP, _VP]),
     "rf_solve": (C.c_int, [_VP, _VP, C.POINTER(C.c_int)]),
     "rf_launch_count": (C.c_ulonglong, [_VP]),
+    "rf_profile_kernel": (C.c_int, [_VP, C.c_int, C.c_int, _DP, _DP]),
+    "rf_launch_counts": (C.c_int, [_VP, C.POINTER(C.c_ulonglong), C.c_int]),
 }
+COUNTER_KINDS = ("closure", "closure_picard", "assemble", "cg64_init", "cg64_spmv", "cg64_update", "apply64",
+                 "mixed_start", "resid64", "cg32_spmv", "cg32_update", "add_correction", "mass_balance",
+                 "storage", "accept")
+KERNEL_KINDS = {"closure": 0, "assemble": 1, "cg64_spmv": 2, "cg64_update": 3, "resid64": 4, "cg32_spmv": 5,
+                "cg32_update": 6}
 
 _lib = None
 
@@ -301,6 +308,19 @@ class Solver:
 
     def launch_count(self) -> int:
         return int(load().rf_launch_count(self.ctx))
+
+    def launch_counts(self) -> dict:
+        """{kind: (launches, launches that did work)} from the device counters."""
+        buf = (C.c_ulonglong * (2 * len(COUNTER_KINDS)))()
+        n = load().rf_launch_counts(self.ctx, buf, len(buf))
+        return {k: (int(buf[2 * i]), int(buf[2 * i + 1])) for i, k in enumerate(COUNTER_KINDS) if 2 * i + 1 < n}
+
+    def profile_kernel(self, kind: str, reps: int = 50):
+        """(mean ms per launch, algorithmic bytes per launch) of one kernel."""
+        ms, by = C.c_double(0), C.c_double(0)
+        _check(load().rf_profile_kernel(self.ctx, KERNEL_KINDS[kind], reps, C.byref(ms), C.byref(by)),
+               "rf_profile_kernel")
+        return ms.value, by.value
 
     # -- kernel level (torch CUDA float64 tensors of N elements)
     def assemble(self, hk, hn, dt, t=0.0, K=None, theta=None, c=None, b=None, diag=None):

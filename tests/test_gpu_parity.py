@@ -56,6 +56,15 @@ def gpu(a):
     return torch.as_tensor(np.ascontiguousarray(a), dtype=torch.float64, device="cuda")
 
 
+def chord_tol(case, hk, hn, dt, act, c_ref):
+    """Bound on |c_gpu - c_oracle|: the chord slope divides a difference of
+    theta values (<= 0.55) by h^k - h^n, so a few ulp of rounding in theta are
+    amplified by 1/|h^k - h^n|; the rest is relative rounding."""
+    V = case.dx * case.dy * case.dz
+    dh = np.abs(hk - hn)[act]
+    return (V / dt) * 8 * 2.2e-16 * 0.55 / np.maximum(dh, 1e-300) + 2e-12 * np.abs(c_ref)
+
+
 def test_assembly_matches_oracle():
     case = masked_case()
     o = oracle_from_case(case)
@@ -67,15 +76,12 @@ def test_assembly_matches_oracle():
         s.assemble(gpu(hk), gpu(case.h0), 37.0, t, **out)
         ref = o.assemble(hk, case.h0, 37.0, t)
         act = o.active_cells
-        for key in ("K", "theta", "diag"):
+        for key in ("K", "theta"):
             g = out[key].cpu().numpy()[act]
             np.testing.assert_allclose(g, ref[key], rtol=2e-12, atol=0, err_msg=key)
-        # the chord slope divides a difference of theta values (~0.45) by
-        # h^k - h^n: rounding of theta (a few ulp) is amplified by 1/|dh|
-        V = case.dx * case.dy * case.dz
-        dh = np.abs(hk - case.h0)[act]
-        tol_c = (V / 37.0) * 8 * 2.2e-16 * 0.45 / np.maximum(dh, 1e-300) + 2e-12 * np.abs(ref["c"])
+        tol_c = chord_tol(case, hk, case.h0, 37.0, act, ref["c"])
         assert np.all(np.abs(out["c"].cpu().numpy()[act] - ref["c"]) <= tol_c)
+        assert np.all(np.abs(out["diag"].cpu().numpy()[act] - ref["diag"]) <= tol_c + 2e-12 * ref["diag"])
         bg = out["b"].cpu().numpy()[act]
         np.testing.assert_allclose(bg, ref["b"], rtol=1e-11, atol=1e-14 * np.abs(ref["b"]).max())
         inact = np.setdiff1d(np.arange(case.N), act)
@@ -95,11 +101,12 @@ def test_operator_and_solve_match_oracle():
     y = torch.zeros(case.N, dtype=torch.float64, device="cuda")
     s.apply(gpu(xfull), y)
     yo = o.spmv(hk, case.h0, 120.0, xfull[act])
-    # (A x)_P sums terms of size |diag x|: bound the rounding by that scale
-    d = torch.zeros(case.N, dtype=torch.float64, device="cuda")
-    s.assemble(gpu(hk), gpu(case.h0), 120.0, 0.0, diag=d)
-    scale = 2 * d.cpu().numpy()[act].max() * np.abs(xfull).max()
-    np.testing.assert_allclose(y.cpu().numpy()[act], yo, rtol=0, atol=1e-14 * scale)
+    # (A x)_P differs by the chord error of c_P times |x_P| plus rounding of
+    # terms of size diag |x|
+    ref = o.assemble(hk, case.h0, 120.0)
+    tol = chord_tol(case, hk, case.h0, 120.0, act, ref["c"]) * np.abs(xfull[act]) \
+        + 1e-14 * ref["diag"].max() * np.abs(xfull).max()
+    assert np.all(np.abs(y.cpu().numpy()[act] - yo) <= tol)
     # one PCG solve from x0 = h^k
     x = gpu(hk)
     it = s.solve(x)
@@ -150,7 +157,9 @@ def test_heterogeneous_box_parity():
     # are compared against the stored volume, not their own size
     for k in ("storage", "inflow_cum", "outflow_cum"):
         assert abs(mbg[k] - mbo[k]) <= 1e-12 * mbo["storage0"]
-    assert mbg["closure_rel"] <= 1e-11
+    # the linear closure is sum dt (A x - b), bounded by the CG tolerance
+    assert mbg["closure_rel"] <= 1e-9
+    assert mbg["closure_rel"] <= 10 * mbo["closure_rel"] + 1e-12
 
 
 def test_masked_watershed_parity():
