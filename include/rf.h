@@ -244,6 +244,47 @@ typedef enum rf_kernel_kind {
  * the linear-solver scratch is. */
 rf_status rf_profile_kernel(rf_ctx *ctx, int kind, int reps, double *avg_ms, double *bytes_per_launch);
 
+/* ---- a linear solve that allocates no device memory ----------------------
+ *
+ * No counterpart in the paper: this is a library facility.  Some callers
+ * cannot call cudaMalloc: host applications that own the device's memory
+ * through their own pool and forbid allocation once their time loop runs,
+ * coupled-model frameworks that must not pay cudaMalloc/cudaFree's implicit
+ * device synchronisation inside a step, and code held to a memory budget
+ * fixed at start-up.  rf_pcg_solve_noalloc solves the 7-point system
+ *     (A x)_P = diag_P x_P - sum_f T_f x_N = b_P
+ * with Jacobi-preconditioned CG and allocates nothing: its work vectors live
+ * in one file-scope device array sized for RF_NOALLOC_MAX_CELLS cells (about
+ * 3.5 MB), which every GPU that loads the library holds until the process
+ * exits.
+ *
+ *   nx, ny, nz   grid (cells indexed i + nx (j + ny k)); nx*ny*nz must not
+ *                exceed RF_NOALLOC_MAX_CELLS, else RF_ERR_ARG
+ *   d_diag       N doubles, diag(A); a cell with diag <= 0 is inactive (its
+ *                row and column are ignored, its x is left as given)
+ *   d_Tx/Ty/Tz   N doubles each: coefficient of the cell's +x / +y / +z face
+ *                (0 at the grid edge and next to inactive cells), so the -x
+ *                coefficient of cell p is d_Tx[p - 1], etc.
+ *   d_b          N doubles, right-hand side
+ *   d_x          N doubles: x0 on entry, the solution on return
+ *   tol, max_it  stop when ||b - A x||_2 <= tol ||b||_2 (recursive
+ *                residual); RF_ERR_CG when max_it iterations do not reach it
+ *   cuda_stream  cudaStream_t the work is ordered on (NULL: legacy stream);
+ *                the call returns after synchronising it
+ *   iters        CG iterations done (may be NULL)
+ * All pointers are device pointers on the current device, borrowed.
+ *
+ * The first call on a device looks up the array's device address (a
+ * cudaGetSymbolAddress with that device current) and caches it; make that
+ * first call before any stream capture.  Every call shares the one array:
+ * calls that overlap on the GPU (other streams or host threads) race and
+ * must be serialised by the caller.  Each call clears what has to start at
+ * zero; nothing else of a previous call's contents is read. */
+#define RF_NOALLOC_MAX_CELLS 65536
+rf_status rf_pcg_solve_noalloc(int nx, int ny, int nz, const double *d_diag, const double *d_Tx,
+                               const double *d_Ty, const double *d_Tz, const double *d_b, double *d_x,
+                               double tol, int max_it, void *cuda_stream, int *iters);
+
 #ifdef __cplusplus
 }
 #endif

@@ -43,6 +43,8 @@ double t_tol(double t) { return 1e-9 * (std::fabs(t) > 1.0 ? std::fabs(t) : 1.0)
 
 }  // namespace
 
+void rf::set_last_error(const char *msg) { g_err = msg; }
+
 struct rf_ctx {
     int device = 0;
     int num_sms = 0;

@@ -167,6 +167,9 @@ __device__ __forceinline__ void set_cond(const CondSet &c, unsigned int v)
 }
 #endif
 
+// Message returned by rf_last_error() on the calling thread.
+void set_last_error(const char *msg);
+
 // ---- launch entry points implemented in the .cu files --------------------
 void launch_closure(cudaStream_t s, int nblk, const Grid &g, const DevSoil *soils, const uint8_t *zone,
                     const double *Ks, const uint8_t *flags, const double *h, const double *hprev,

@@ -102,7 +102,10 @@ SIGNATURES = {
     "rf_launch_count": (C.c_ulonglong, [_VP]),
     "rf_profile_kernel": (C.c_int, [_VP, C.c_int, C.c_int, _DP, _DP]),
     "rf_launch_counts": (C.c_int, [_VP, C.POINTER(C.c_ulonglong), C.c_int]),
+    "rf_pcg_solve_noalloc": (C.c_int, [C.c_int, C.c_int, C.c_int, _VP, _VP, _VP, _VP, _VP, _VP, C.c_double,
+                                       C.c_int, _VP, C.POINTER(C.c_int)]),
 }
+NOALLOC_MAX_CELLS = 65536
 COUNTER_KINDS = ("closure", "closure_picard", "assemble", "cg64_init", "cg64_spmv", "cg64_update", "apply64",
                  "mixed_start", "resid64", "cg32_spmv", "cg32_update", "add_correction", "mass_balance",
                  "storage", "accept")
@@ -335,6 +338,18 @@ class Solver:
         it = C.c_int(0)
         _check(load().rf_solve(self.ctx, C.c_void_p(x.data_ptr()), C.byref(it)), "rf_solve")
         return it.value
+
+
+def pcg_solve_noalloc(shape, diag, Tx, Ty, Tz, b, x, tol=1e-10, max_it=10000, stream=None) -> int:
+    """rf_pcg_solve_noalloc on torch CUDA float64 tensors (x in/out)."""
+    import torch
+    nx, ny, nz = shape
+    st = stream if stream is not None else torch.cuda.current_stream()
+    it = C.c_int(0)
+    ptr = lambda a: C.c_void_p(a.data_ptr())
+    _check(load().rf_pcg_solve_noalloc(nx, ny, nz, ptr(diag), ptr(Tx), ptr(Ty), ptr(Tz), ptr(b), ptr(x), float(tol),
+                                       int(max_it), C.c_void_p(st.cuda_stream), C.byref(it)), "rf_pcg_solve_noalloc")
+    return it.value
 
 
 def header_function_names(header: str) -> list:
