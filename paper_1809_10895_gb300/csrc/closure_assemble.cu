@@ -11,20 +11,23 @@
 
 namespace rf {
 
-// van Genuchten / Mualem closures with four FP64 transcendentals per cell.
-// With u = -alpha h, L = log u, x = u^n = exp(n L), l1 = log1p(x):
+// van Genuchten / Mualem closures (Eq. 2-4), evaluated in double-float
+// arithmetic (ff.cuh) with FP64 only at the input and the outputs.
+// With u = -alpha h, L = log u, x = u^n = exp(n L), l1 = log(1 + x):
 //   Se = (1 + x)^-m = exp(-m l1)                               (Eq. 2)
 //   u^(n-1) = x / u (since m n = n - 1), so (x/(1+x))^m = (x/u) Se = ys
-//   Se^(1/m) = 1/(1+x), so 1 - Se^(1/m) = x/(1+x) and
+//   Se^(1/m) = 1/(1+x) = w, so 1 - Se^(1/m) = x/(1+x) and
 //   K = Ks Se^(1/2) (1 - ys)^2                                   (Eq. 4)
-//     with 1 - ys = -expm1(m (n L - l1)) when ys > 1/2 (dry soil, where
+//     with 1 - ys = -expm1(m log(1 - w)) when ys > 1/2 (dry soil, where
 //     1 - ys would cancel)
 //   C = (theta_s-theta_r) alpha n m u^(n-1) (1+x)^-(m+1)
-//     = (theta_s-theta_r) alpha n m ys / (1+x)                  (Eq. 3)
+//     = (theta_s-theta_r) alpha n m ys w                         (Eq. 3)
 // For h >= 0 (tie included): theta* = theta_s + S h, K = Ks, C = S, which
 // makes d(theta*)/dh equal to Eq. 3 on both branches.
-// Gardner (Eq. A6): K = Ks e^(alpha h), theta = theta_r + (theta_s-theta_r) e^(alpha h).
-__device__ __forceinline__ void closure(const DevSoil &s, double Ks, double h, double &th, double &K, double &C)
+// Gardner (Eq. A6, a test model): K = Ks e^(alpha h), theta = theta_r +
+// (theta_s-theta_r) e^(alpha h), in FP64.
+__device__ __forceinline__ void closure(const DevSoil &s, double Ks, double h, const FFTables *__restrict__ tab,
+                                        double &th, double &K, double &C)
 {
     if (h >= 0.0) {
         th = s.theta_s + s.S * h;
@@ -40,17 +43,40 @@ __device__ __forceinline__ void closure(const DevSoil &s, double Ks, double h, d
         C = dth * s.alpha * e;
         return;
     }
-    const double u = -s.alpha * h;
-    const double L = log(u);
-    const double nL = s.n * L;
-    const double x = exp(nL);
-    const double l1 = log1p(x);
-    const double se = exp(-s.m * l1);
-    th = s.theta_r + dth * se;
-    const double ys = x * rcp64(u) * se;
-    const double omy = ys <= 0.5 ? 1.0 - ys : -expm1(s.m * (nL - l1));
-    K = Ks * sqrt(se) * omy * omy;
-    C = dth * s.alpha * s.n * s.m * ys * rcp64(1.0 + x);
+    const double ud = -s.alpha * h;
+    if (ud < 1e-30) {                     // (-alpha h)^n underflows: the wet limit
+        th = s.theta_s;
+        K = Ks;
+        C = 0.0;
+        return;
+    }
+    const ff u = ff_from_d(ud);
+    const ff L = ff_log(u, tab);
+    const ff nL = ff_mul(ff_make(s.n_hi, s.n_lo), L);
+    if (nL.hi > 80.0f) {                  // x > e^80: Se = x^-m, K and C vanish at double range
+        th = s.theta_r + dth * ff_to_d(ff_exp(ff_neg(ff_mul(ff_make(s.m_hi, s.m_lo), nL)), tab));
+        K = 0.0;
+        C = 0.0;
+        return;
+    }
+    const ff x = ff_exp(nL, tab);
+    const ff onepx = ff_add_f(x, 1.0f);
+    const ff l1 = ff_log(onepx, tab);
+    const ff mm = ff_make(s.m_hi, s.m_lo);
+    const ff se = ff_exp(ff_neg(ff_mul(mm, l1)), tab);
+    const ff w = ff_div(ff_make(1.0f, 0.0f), onepx);
+    const ff ys = ff_mul(ff_div(x, u), se);
+    ff omy;
+    if (ys.hi <= 0.5f) {
+        omy = ff_add_f(ff_neg(ys), 1.0f);
+    } else {
+        const ff lg = (w.hi < 0.0078125f) ? ff_log1p_small(ff_neg(w)) : ff_log(ff_add_f(ff_neg(w), 1.0f), tab);
+        const ff z = ff_mul(mm, lg);
+        omy = (z.hi > -0.0078125f) ? ff_neg(ff_expm1_small(z)) : ff_add_f(ff_neg(ff_exp(z, tab)), 1.0f);
+    }
+    th = s.theta_r + dth * ff_to_d(se);
+    K = Ks * ff_to_d(ff_mul(ff_sqrt(se), ff_mul(omy, omy)));
+    C = (dth * s.alpha * s.n * s.m) * ff_to_d(ff_mul(ys, w));
 }
 
 // Closures of every cell at h; with hprev, also max|h - hprev| and a
@@ -77,7 +103,7 @@ __device__ __forceinline__ void closure_cells(const Grid &g, const DevSoil *__re
         }
         const DevSoil s = soils[zone[p]];
         double th, k, c;
-        closure(s, Ks[p], hp, th, k, c);
+        closure(s, Ks[p], hp, g.tab, th, k, c);
         theta[p] = th;
         K[p] = k;
         Can[p] = c;
@@ -164,6 +190,7 @@ __device__ __forceinline__ bool neighbour(const Grid &g, long long p, int i, int
 // Outputs: c, b, upper-face coefficients Tx/Ty/Tz (0 where the face is not an
 // interior face), diag(A), 1/diag; FP32 copies of K and of c plus the
 // Dirichlet diagonal terms for the mixed-precision operator.
+template <int MODE>
 __global__ void __launch_bounds__(RED_THREADS)
 k_assemble(Grid g, const DevSoil *__restrict__ soils, const uint8_t *__restrict__ zone,
            const double *__restrict__ Ks, const uint8_t *__restrict__ flags, const StepParams *__restrict__ spp,
@@ -171,13 +198,26 @@ k_assemble(Grid g, const DevSoil *__restrict__ soils, const uint8_t *__restrict_
            const double *__restrict__ thn, const double *__restrict__ K, const double *__restrict__ Can,
            double *__restrict__ c_out, double *__restrict__ b, double *__restrict__ Tx, double *__restrict__ Ty,
            double *__restrict__ Tz, double *__restrict__ diag_out, double *__restrict__ dinv,
-           float *__restrict__ K32, float *__restrict__ cb32, float *__restrict__ dinv32, const int *skip)
+           float *__restrict__ K32, float *__restrict__ cb32, float *__restrict__ dinv32, const int *skip,
+           SolveStart st, double *partials, unsigned int *ticket)
 {
     count_launch(g, KK_ASSEMBLE);
-    if (skip && *skip) return;
+    if (skip && *skip) {
+        if (MODE != ASM_ONLY && blockIdx.x == 0 && threadIdx.x == 0) {
+            // the Picard attempt is over: the linear-solve loops that follow are empty
+            st.sc->done = 1;
+            set_cond(st.cond, 0);
+            if (MODE == ASM_MIXED) {
+                st.inner->done = 1;
+                set_cond(st.cond_inner, 0);
+            }
+        }
+        return;
+    }
     count_work(g, KK_ASSEMBLE);
     const double eps = spp->eps_chord;
     const double V_dt = g.V / spp->dt;
+    double v[4] = {0.0, 0.0, 0.0, 0.0};
     const long long stride = (long long)gridDim.x * blockDim.x;
     for (long long p = (long long)blockIdx.x * blockDim.x + threadIdx.x; p < g.N; p += stride) {
         const uint8_t fl = flags[p];
@@ -185,31 +225,38 @@ k_assemble(Grid g, const DevSoil *__restrict__ soils, const uint8_t *__restrict_
             c_out[p] = 0.0; b[p] = 0.0; Tx[p] = 0.0; Ty[p] = 0.0; Tz[p] = 0.0;
             diag_out[p] = 0.0; dinv[p] = 0.0;
             K32[p] = -1.0f; cb32[p] = 0.0f; dinv32[p] = 0.0f;
+            if (MODE != ASM_ONLY) st.x[p] = hk[p];
+            if (MODE == ASM_CG64) { st.r[p] = 0.0; st.z[p] = 0.0; }
+            if (MODE == ASM_MIXED) { st.r32[p] = 0.0f; st.z32[p] = 0.0f; st.d32[p] = 0.0f; }
             continue;
         }
         int i, j, k;
         cell_ijk(g, p, i, j, k);
         const double hkP = hk[p], hnP = hn[p], KP = K[p];
         const double dh = hkP - hnP;
-        const double C = (fabs(dh) > eps) ? (thk[p] - thn[p]) * rcp64(dh) : Can[p];
+        // |dh| > eps compared on the IEEE bit patterns (both non-negative)
+        const bool chord = (__double_as_longlong(dh) & 0x7fffffffffffffffLL) > __double_as_longlong(eps);
+        const double C = chord ? (thk[p] - thn[p]) * rcp64(dh) : Can[p];
         const double c = V_dt * C;
         double diag = c, rhs = c * hnP, cb = c;
+        double sT = 0.0;                         // sum over interior faces of T_f h^k_N
         double Tup[3] = {0.0, 0.0, 0.0};
 #pragma unroll
         for (int f = 0; f < 6; f++) {
-            const double gs = (f == F_ZMIN) ? -1.0 : (f == F_ZMAX ? 1.0 : 0.0);
             long long q;
             if (neighbour(g, p, i, j, k, f, q)) {
                 const double KN = K[q];
-                if (KN >= 0.0) {
-                    const double Kbar = 0.5 * (KP + KN);
-                    const double T = Kbar * g.w[f];
+                if (__double_as_longlong(KN) >= 0) {          // active neighbour (K >= 0; inactive K = -1)
+                    const double Ks2 = KP + KN;
+                    const double T = Ks2 * g.hw[f];            // (K_P + K_N)/2 A/d
                     diag += T;
-                    rhs += gs * Kbar * g.A[f];
+                    if (f >= F_ZMIN) rhs = fma(Ks2, g.hg[f], rhs);   // explicit gravity, +-Kbar A_z
                     if (f & 1) Tup[f >> 1] = T;
+                    if (MODE != ASM_ONLY) sT = fma(T, hk[q], sT);
                     continue;
                 }
             }
+            const double gs = (f == F_ZMIN) ? -1.0 : (f == F_ZMAX ? 1.0 : 0.0);
             if (!(fl & (1u << f))) continue;    // closed face (lateral face on an inactive cell)
             int type = spp->bc_type[f];
             double hD = 0.0;
@@ -222,7 +269,7 @@ k_assemble(Grid g, const DevSoil *__restrict__ soils, const uint8_t *__restrict_
             if (type == BC_DIRICHLET) {
                 const DevSoil s = soils[zone[p]];
                 double thD, KD, CD;
-                closure(s, Ks[p], hD, thD, KD, CD);
+                closure(s, Ks[p], hD, g.tab, thD, KD, CD);
                 const double T = KD * g.wb[f];
                 diag += T;
                 cb += T;
@@ -243,7 +290,45 @@ k_assemble(Grid g, const DevSoil *__restrict__ soils, const uint8_t *__restrict_
         dinv[p] = di;
         K32[p] = (float)KP;
         cb32[p] = (float)cb;
-        dinv32[p] = (float)di;
+        const float di32 = (float)di;
+        dinv32[p] = di32;
+        if (MODE != ASM_ONLY) {
+            // first residual of the linear solve from x0 = h^k
+            const double rp = rhs - (diag * hkP - sT);
+            st.x[p] = hkP;
+            if (MODE == ASM_CG64) {
+                const double zp = di * rp;
+                st.r[p] = rp;
+                st.z[p] = zp;
+                v[0] += rp * zp;
+                v[1] += rp * rp;
+                v[2] += rhs * rhs;
+            } else {
+                const float rf = (float)rp;
+                const float zf = di32 * rf;
+                st.r32[p] = rf;
+                st.z32[p] = zf;
+                st.d32[p] = 0.0f;
+                v[0] += rp * rp;
+                v[1] += rhs * rhs;
+                v[2] += (double)(rf * rf);
+                v[3] += (double)(rf * zf);
+            }
+        }
+    }
+    if (MODE == ASM_CG64) {
+        double w3[3] = {v[0], v[1], v[2]};
+        if (grid_reduce<OpSum, 3>(w3, partials, ticket) && threadIdx.x == 0)
+            cg64_start_scalars(st.sc, w3, st.tol, st.max_it, st.cond);
+    } else if (MODE == ASM_MIXED) {
+        if (grid_reduce<OpSum, 4>(v, partials, ticket) && threadIdx.x == 0) {
+            st.sc->iter = 1;
+            st.sc->done = 0;
+            st.sc->status = CG_OK;
+            st.inner->total = 0;
+            outer_residual_scalars(st.sc, st.inner, v, st.tol, st.tol_inner, st.inner_max_it, st.outer_max_it,
+                                   st.cond, st.cond_inner);
+        }
     }
 }
 
@@ -288,7 +373,7 @@ k_mass_balance(Grid g, const DevSoil *__restrict__ soils, const uint8_t *__restr
             if (type == BC_DIRICHLET) {
                 const DevSoil s = soils[zone[p]];
                 double thD, KD, CD;
-                closure(s, Ks[p], hD, thD, KD, CD);
+                closure(s, Ks[p], hD, g.tab, thD, KD, CD);
                 const double T = KD * g.wb[f];
                 flux = T * hD + gs * KD * g.A[f] - T * xp;
             } else if (type == BC_FLUX) {
@@ -336,6 +421,19 @@ k_accept(Grid g, const double *__restrict__ xf, double *__restrict__ h, const do
     }
 }
 
+void make_ff_tables(FFTables *t)
+{
+    for (int j = 0; j < 64; j++) {
+        const double e = exp2((double)j / 64.0);
+        const double c = 1.0 + ((double)j + 0.5) / 64.0;
+        const double lc = log(c), ic = 1.0 / c;
+        const float eh = (float)e, lh = (float)lc, ih = (float)ic;
+        t->exp2j[j] = make_float2(eh, (float)(e - (double)eh));
+        t->logc[j] = make_float2(lh, (float)(lc - (double)lh));
+        t->invc[j] = make_float2(ih, (float)(ic - (double)ih));
+    }
+}
+
 void launch_closure(cudaStream_t s, int nblk, const Grid &g, const DevSoil *soils, const uint8_t *zone,
                     const double *Ks, const uint8_t *flags, const double *h, const double *hprev,
                     double *theta, double *K, double *Can, double *partials, unsigned int *ticket,
@@ -357,10 +455,23 @@ void launch_assemble(cudaStream_t s, int nblk, const Grid &g, const DevSoil *soi
                      const double *Ks, const uint8_t *flags, const StepParams *sp, const double *hk,
                      const double *hn, const double *theta_k, const double *theta_n, const double *K,
                      const double *Can, double *c, double *b, double *Tx, double *Ty, double *Tz,
-                     double *diag, double *dinv, float *K32, float *cb32, float *dinv32, const int *skip)
+                     double *diag, double *dinv, float *K32, float *cb32, float *dinv32, const int *skip,
+                     int mode, const SolveStart *start, double *partials, unsigned int *ticket)
 {
-    k_assemble<<<nblk, RED_THREADS, 0, s>>>(g, soils, zone, Ks, flags, sp, hk, hn, theta_k, theta_n, K, Can, c, b,
-                                            Tx, Ty, Tz, diag, dinv, K32, cb32, dinv32, skip);
+    SolveStart st{};
+    if (start) st = *start;
+    if (mode == ASM_CG64)
+        k_assemble<ASM_CG64><<<nblk, RED_THREADS, 0, s>>>(g, soils, zone, Ks, flags, sp, hk, hn, theta_k, theta_n, K,
+                                                          Can, c, b, Tx, Ty, Tz, diag, dinv, K32, cb32, dinv32, skip,
+                                                          st, partials, ticket);
+    else if (mode == ASM_MIXED)
+        k_assemble<ASM_MIXED><<<nblk, RED_THREADS, 0, s>>>(g, soils, zone, Ks, flags, sp, hk, hn, theta_k, theta_n,
+                                                           K, Can, c, b, Tx, Ty, Tz, diag, dinv, K32, cb32, dinv32,
+                                                           skip, st, partials, ticket);
+    else
+        k_assemble<ASM_ONLY><<<nblk, RED_THREADS, 0, s>>>(g, soils, zone, Ks, flags, sp, hk, hn, theta_k, theta_n, K,
+                                                          Can, c, b, Tx, Ty, Tz, diag, dinv, K32, cb32, dinv32, skip,
+                                                          st, partials, ticket);
 }
 
 void launch_accept(cudaStream_t s, int nblk, const Grid &g, const double *x_final, double *h,

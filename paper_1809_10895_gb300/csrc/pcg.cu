@@ -82,21 +82,8 @@ k_cg64_init(Grid g, const uint8_t *__restrict__ flags, const double *__restrict_
         v[1] += rp * rp;
         v[2] += bp * bp;
     }
-    if (grid_reduce<OpSum, 3>(v, partials, ticket) && threadIdx.x == 0) {
-        sc->rho = v[0];
-        sc->rr = v[1];
-        sc->bb = v[2];
-        sc->stop2 = tol * sqrt(v[2]);      // threshold on ||r||_2
-        sc->alpha = 0.0;
-        sc->beta = 0.0;
-        sc->iter = 0;
-        sc->total = 0;
-        sc->max_it = max_it;
-        const bool finite = isfinite(v[0]) && isfinite(v[1]) && isfinite(v[2]);
-        sc->status = finite ? CG_OK : CG_NONFINITE;
-        sc->done = (!finite || sqrt(v[1]) <= sc->stop2) ? 1 : 0;
-        set_cond(cond, sc->done ? 0 : 1);
-    }
+    if (grid_reduce<OpSum, 3>(v, partials, ticket) && threadIdx.x == 0)
+        cg64_start_scalars(sc, v, tol, max_it, cond);
 }
 
 __global__ void __launch_bounds__(RED_THREADS)
@@ -283,32 +270,8 @@ k_resid64(Grid g, const uint8_t *__restrict__ flags, const double *__restrict__ 
         v[3] += (double)(rf * zf);
     }
     if (grid_reduce<OpSum, 4>(v, partials, ticket) && threadIdx.x == 0) {
-        const bool finite = isfinite(v[0]) && isfinite(v[1]) && isfinite(v[2]) && isfinite(v[3]);
         outer->iter += 1;
-        outer->rr = v[0];
-        outer->bb = v[1];
-        outer->stop2 = tol * sqrt(v[1]);
-        if (!finite) {
-            outer->status = CG_NONFINITE;
-            outer->done = 1;
-        } else if (sqrt(v[0]) <= outer->stop2) {
-            outer->done = 1;
-        } else if (outer->iter >= outer_max_it) {
-            outer->status = CG_MAXIT;
-            outer->done = 1;
-        }
-        inner->rho = v[3];
-        inner->rr = v[2];
-        inner->bb = v[2];
-        inner->stop2 = tol_inner * sqrt(v[2]);
-        inner->alpha = 0.0;
-        inner->beta = 0.0;
-        inner->iter = 0;
-        inner->max_it = inner_max_it;
-        inner->status = CG_OK;
-        inner->done = (outer->done || !(v[2] > 0.0)) ? 1 : 0;
-        set_cond(cond_outer, outer->done ? 0 : 1);
-        set_cond(cond_inner, inner->done ? 0 : 1);
+        outer_residual_scalars(outer, inner, v, tol, tol_inner, inner_max_it, outer_max_it, cond_outer, cond_inner);
     }
 }
 
@@ -337,8 +300,9 @@ k_cg32_spmv(Grid g, const float *__restrict__ z, const float *__restrict__ p_in,
         q[p] = qp;
         acc = fmaf(pp, qp, acc);
     }
-    double v[1] = {(double)acc};
-    if (grid_reduce<OpSum, 1>(v, partials, ticket) && threadIdx.x == 0) {
+    float vf[1] = {acc};
+    double v[1];
+    if (grid_reduce_f32<1>(vf, v, partials, ticket) && threadIdx.x == 0) {
         sc->pq = v[0];
         const double a = sc->rho / v[0];
         if (!(v[0] > 0.0) || !isfinite(a)) {
@@ -374,8 +338,9 @@ k_cg32_update(Grid g, float *__restrict__ x, float *__restrict__ r, float *__res
         a0 = fmaf(rp, rp, a0);
         a1 = fmaf(rp, zp, a1);
     }
-    double v[2] = {(double)a0, (double)a1};
-    if (grid_reduce<OpSum, 2>(v, partials, ticket) && threadIdx.x == 0) {
+    float vf[2] = {a0, a1};
+    double v[2];
+    if (grid_reduce_f32<2>(vf, v, partials, ticket) && threadIdx.x == 0) {
         sc->iter += 1;
         sc->total += 1;
         sc->rr = v[0];

@@ -64,6 +64,7 @@ struct rf_ctx {
     uint8_t *flags = nullptr, *zone = nullptr;
     double *Ks = nullptr;
     DevSoil *soils = nullptr;   // 256 entries
+    FFTables *fftab = nullptr;
     double *h = nullptr, *hk = nullptr, *x = nullptr, *theta_n = nullptr, *theta_k = nullptr;
     double *K[2] = {nullptr, nullptr}, *Can = nullptr, *c = nullptr, *b = nullptr;
     double *Tx = nullptr, *Ty = nullptr, *Tz = nullptr, *diag = nullptr, *dinv = nullptr;
@@ -228,24 +229,28 @@ rf_status add_while(cudaGraph_t parent, const std::vector<cudaGraphNode_t> &deps
 
 // Linear solve A x = b from x0 into x, appended to `parent` after `deps`
 // (handles created on the top graph `top`).  skip: attempt-over flag or null.
-// Returns the node after which the solution is complete.
+// With `fused`, the assembly kernel before `deps` has already started the
+// solve (x = x0, first residual, loop conditions) through `start`; otherwise
+// a start kernel is captured here.  Returns the node after which the
+// solution is complete.
 rf_status capture_solve(rf_ctx *c, cudaGraph_t top, cudaGraph_t parent, std::vector<cudaGraphNode_t> deps,
-                        const double *x0, double *x, const int *skip, std::vector<cudaGraphNode_t> &out)
+                        const double *x0, double *x, const int *skip, bool fused, const SolveStart *start,
+                        std::vector<cudaGraphNode_t> &out)
 {
     const Grid &g = c->g;
     const int nb = c->nblk;
     cudaStream_t s = c->cap;
     if (c->prm.precision == RF_PREC_FP64) {
-        cudaGraphConditionalHandle hc;
-        CUDA_TRY(cudaGraphConditionalHandleCreate(&hc, top, 0, 0));
-        const CondSet cc{hc, 1};
-        RF_TRY(cap_begin(c, parent, deps));
-        launch_cg64_init(s, nb, g, c->flags, x0, x, c->b, c->Tx, c->Ty, c->Tz, c->diag, c->dinv, c->r, c->z,
-                         c->prm.tol_cg, c->prm.cg_max_it, c->partials, c->ticket, c->sc, skip, cc);
-        RF_TRY(cap_end(c, deps));
+        const CondSet cc = start->cond;
+        if (!fused) {
+            RF_TRY(cap_begin(c, parent, deps));
+            launch_cg64_init(s, nb, g, c->flags, x0, x, c->b, c->Tx, c->Ty, c->Tz, c->diag, c->dinv, c->r, c->z,
+                             c->prm.tol_cg, c->prm.cg_max_it, c->partials, c->ticket, c->sc, skip, cc);
+            RF_TRY(cap_end(c, deps));
+        }
         cudaGraphNode_t wn;
         cudaGraph_t body;
-        RF_TRY(add_while(parent, deps, hc, &wn, &body));
+        RF_TRY(add_while(parent, deps, cc.h, &wn, &body));
         RF_TRY(cap_begin(c, body, {}));
         for (int half = 0; half < 2; half++) {
             double *pin = c->p[half], *pout = c->p[half ^ 1];
@@ -258,24 +263,20 @@ rf_status capture_solve(rf_ctx *c, cudaGraph_t top, cudaGraph_t parent, std::vec
         out = {wn};
         return RF_OK;
     }
-    // mixed: defect correction (outer FP64 residual) around FP32 inner PCG
-    cudaGraphConditionalHandle ho, hi;
-    CUDA_TRY(cudaGraphConditionalHandleCreate(&ho, top, 0, 0));
-    CUDA_TRY(cudaGraphConditionalHandleCreate(&hi, top, 0, 0));
-    const CondSet co{ho, 1}, ci{hi, 1};
-    RF_TRY(cap_begin(c, parent, deps));
-    launch_mixed_start(s, nb, g, x0, x, c->sc, c->sc_in, skip, co);
-    RF_TRY(cap_end(c, deps));
+    // mixed: WHILE(outer) { WHILE(inner FP32 PCG) ; x += d ; FP64 residual }
+    const CondSet co = start->cond, ci = start->cond_inner;
+    if (!fused) {
+        RF_TRY(cap_begin(c, parent, deps));
+        launch_mixed_start(s, nb, g, x0, x, c->sc, c->sc_in, skip, co);
+        launch_resid64(s, nb, g, c->flags, x, c->b, c->Tx, c->Ty, c->Tz, c->diag, c->dinv32, c->r32, c->z32, c->d32,
+                       c->prm.tol_cg, c->prm.tol_inner, c->prm.inner_max_it, c->prm.outer_max_it, c->partials,
+                       c->ticket, c->sc, c->sc_in, co, ci);
+        RF_TRY(cap_end(c, deps));
+    }
     cudaGraphNode_t wo, wi;
     cudaGraph_t bo, bi;
-    RF_TRY(add_while(parent, deps, ho, &wo, &bo));
-    std::vector<cudaGraphNode_t> d2;
-    RF_TRY(cap_begin(c, bo, {}));
-    launch_resid64(s, nb, g, c->flags, x, c->b, c->Tx, c->Ty, c->Tz, c->diag, c->dinv32, c->r32, c->z32, c->d32,
-                   c->prm.tol_cg, c->prm.tol_inner, c->prm.inner_max_it, c->prm.outer_max_it, c->partials, c->ticket,
-                   c->sc, c->sc_in, co, ci);
-    RF_TRY(cap_end(c, d2));
-    RF_TRY(add_while(bo, d2, hi, &wi, &bi));
+    RF_TRY(add_while(parent, deps, co.h, &wo, &bo));
+    RF_TRY(add_while(bo, {}, ci.h, &wi, &bi));
     RF_TRY(cap_begin(c, bi, {}));
     for (int half = 0; half < 2; half++) {
         float *pin = c->p32[half], *pout = c->p32[half ^ 1];
@@ -287,8 +288,38 @@ rf_status capture_solve(rf_ctx *c, cudaGraph_t top, cudaGraph_t parent, std::vec
     RF_TRY(cap_end(c, tmp));
     RF_TRY(cap_begin(c, bo, {wi}));
     launch_add_correction(s, nb, g, x, c->d32, c->sc, c->sc_in, co);
+    launch_resid64(s, nb, g, c->flags, x, c->b, c->Tx, c->Ty, c->Tz, c->diag, c->dinv32, c->r32, c->z32, c->d32,
+                   c->prm.tol_cg, c->prm.tol_inner, c->prm.inner_max_it, c->prm.outer_max_it, c->partials, c->ticket,
+                   c->sc, c->sc_in, co, ci);
     RF_TRY(cap_end(c, tmp));
     out = {wo};
+    return RF_OK;
+}
+
+// Loop handles and start description of one linear solve in graph G.
+rf_status make_start(rf_ctx *c, cudaGraph_t G, double *x, SolveStart &st)
+{
+    st = SolveStart{};
+    cudaGraphConditionalHandle h1, h2;
+    CUDA_TRY(cudaGraphConditionalHandleCreate(&h1, G, 0, 0));
+    st.cond = CondSet{h1, 1};
+    if (c->prm.precision == RF_PREC_MIXED) {
+        CUDA_TRY(cudaGraphConditionalHandleCreate(&h2, G, 0, 0));
+        st.cond_inner = CondSet{h2, 1};
+    }
+    st.x = x;
+    st.r = c->r;
+    st.z = c->z;
+    st.r32 = c->r32;
+    st.z32 = c->z32;
+    st.d32 = c->d32;
+    st.sc = c->sc;
+    st.inner = c->sc_in;
+    st.tol = c->prm.tol_cg;
+    st.tol_inner = c->prm.tol_inner;
+    st.max_it = c->prm.cg_max_it;
+    st.inner_max_it = c->prm.inner_max_it;
+    st.outer_max_it = c->prm.outer_max_it;
     return RF_OK;
 }
 
@@ -329,11 +360,14 @@ rf_status build_picard_graph(rf_ctx *c)
     for (int half = 0; half < 2; half++) {
         double *hk = H[half], *x = H[half ^ 1];
         double *Kin = c->K[half], *Kout = c->K[half ^ 1];
+        SolveStart st;
+        RF_TRY(make_start(c, G, x, st));
         RF_TRY(cap_begin(c, body, deps));
         launch_assemble(s, nb, g, c->soils, c->zone, c->Ks, c->flags, c->sp, hk, c->h, c->theta_k, c->theta_n, Kin,
-                        c->Can, c->c, c->b, c->Tx, c->Ty, c->Tz, c->diag, c->dinv, c->K32, c->cb32, c->dinv32, skip);
+                        c->Can, c->c, c->b, c->Tx, c->Ty, c->Tz, c->diag, c->dinv, c->K32, c->cb32, c->dinv32, skip,
+                        c->prm.precision == RF_PREC_FP64 ? ASM_CG64 : ASM_MIXED, &st, c->partials, c->ticket);
         RF_TRY(cap_end(c, deps));
-        RF_TRY(capture_solve(c, G, body, deps, hk, x, skip, deps));
+        RF_TRY(capture_solve(c, G, body, deps, hk, x, skip, true, &st, deps));
         RF_TRY(cap_begin(c, body, deps));
         const CgScal *stat = c->sc;   // FP64 solve, or outer defect-correction loop
         const CgScal *cnt = c->prm.precision == RF_PREC_FP64 ? c->sc : c->sc_in;
@@ -353,7 +387,9 @@ rf_status build_solve_graph(rf_ctx *c)
     CUDA_TRY(cudaGraphCreate(&G, 0));
     c->solve_graph = G;
     std::vector<cudaGraphNode_t> out;
-    RF_TRY(capture_solve(c, G, G, {}, c->hk, c->x, nullptr, out));
+    SolveStart st;
+    RF_TRY(make_start(c, G, c->x, st));
+    RF_TRY(capture_solve(c, G, G, {}, c->hk, c->x, nullptr, false, &st, out));
     CUDA_TRY(cudaGraphInstantiate(&c->solve_exec, G, 0));
     return RF_OK;
 }
@@ -563,6 +599,8 @@ rf_status rf_mesh_create(const rf_mesh_desc *mesh, const rf_solver_params *param
         g.A[f] = A[f];
         g.w[f] = A[f] / d[f];
         g.wb[f] = A[f] / (0.5 * d[f]);
+        g.hw[f] = 0.5 * (A[f] / d[f]);
+        g.hg[f] = f == F_ZMIN ? -0.5 * A[f] : (f == F_ZMAX ? 0.5 * A[f] : 0.0);
     }
     for (int a = 0; a < 3; a++) g.w32[a] = (float)(A[2 * a] / d[2 * a]);
     g.fx = make_fastdiv((unsigned int)g.nx);
@@ -602,7 +640,7 @@ rf_status rf_mesh_create(const rf_mesh_desc *mesh, const rf_solver_params *param
               alloc_n(c, c->p32[0], N) && alloc_n(c, c->p32[1], N) && alloc_n(c, c->q32, N) &&
               alloc_n(c, c->d32, N) && alloc_n(c, c->partials, (size_t)8 * c->nblk) && alloc_n(c, c->ticket, 64) &&
               alloc_n(c, c->sc, 1) && alloc_n(c, c->sc_in, 1) && alloc_n(c, c->res, 1) && alloc_n(c, c->sp, 1) &&
-              alloc_n(c, c->ctl, 1) && alloc_n(c, c->ctr, 2 * KK_COUNT);
+              alloc_n(c, c->ctl, 1) && alloc_n(c, c->ctr, 2 * KK_COUNT) && alloc_n(c, c->fftab, 1);
     if (!ok) {
         rf_destroy(c);
         return fail(RF_ERR_NOMEM, "device allocation failed");
@@ -621,7 +659,11 @@ rf_status rf_mesh_create(const rf_mesh_desc *mesh, const rf_solver_params *param
         return fail(RF_ERR_CUDA, "capture stream creation failed");
     }
     g.ctr = c->ctr;
+    g.tab = c->fftab;
+    FFTables tab;
+    make_ff_tables(&tab);
     cudaError_t e = cudaMemcpyAsync(c->flags, c->flags_h.data(), N, cudaMemcpyHostToDevice, c->stream);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(c->fftab, &tab, sizeof(FFTables), cudaMemcpyHostToDevice, c->stream);
     if (e == cudaSuccess) e = cudaMemsetAsync(c->ticket, 0, 64 * sizeof(unsigned int), c->stream);
     if (e == cudaSuccess) e = cudaMemsetAsync(c->ctr, 0, 2 * KK_COUNT * sizeof(unsigned long long), c->stream);
     if (e == cudaSuccess) e = cudaMemsetAsync(c->ctl, 0, sizeof(PicardCtl), c->stream);
@@ -678,7 +720,10 @@ rf_status rf_soil_set(rf_ctx *c, const rf_soil *zones, int n_zones, const uint8_
         if ((s.model != RF_VG && s.model != RF_GARDNER) || !(s.theta_s > s.theta_r) || !(s.alpha > 0) ||
             !(s.Ks > 0) || !(s.S >= 0) || (s.model == RF_VG && !(s.n > 1.0)))
             return fail(RF_ERR_ARG, "invalid soil parameters in zone " + std::to_string(z));
-        soils[z] = DevSoil{s.model, s.theta_r, s.theta_s, s.alpha, s.n, s.model == RF_VG ? 1.0 - 1.0 / s.n : 0.0, s.S};
+        const double m = s.model == RF_VG ? 1.0 - 1.0 / s.n : 0.0;
+        const float nh = (float)s.n, mh = (float)m;
+        soils[z] = DevSoil{s.model, s.theta_r, s.theta_s, s.alpha, s.n, m, s.S,
+                           nh, (float)(s.n - (double)nh), mh, (float)(m - (double)mh)};
     }
     const long long N = c->g.N;
     std::vector<uint8_t> zone(N, 0);

@@ -5,6 +5,8 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include "ff.cuh"
+
 namespace rf {
 
 // Face order used everywhere: 0 -x, 1 +x, 2 -y, 3 +y, 4 -z (bottom), 5 +z (top).
@@ -49,6 +51,7 @@ enum KernelKind {
 struct DevSoil {
     int model;
     double theta_r, theta_s, alpha, n, m, S;
+    float n_hi, n_lo, m_hi, m_lo;   // n and m as double-float pairs
 };
 
 struct Grid {
@@ -59,8 +62,11 @@ struct Grid {
     double A[6];      // face areas
     double w[6];      // A/d for interior faces
     double wb[6];     // A/(d/2) for boundary (half-cell) faces
+    double hw[6];     // A/(2 d): T_f = (K_P + K_N) hw_f
+    double hg[6];     // gravity: +A_z/2 on the top face, -A_z/2 on the bottom face, 0 lateral
     float w32[3];     // A/d per axis, FP32 (mixed-precision operator)
     FastDiv fx, fxy;  // division by nx and by nx*ny
+    const FFTables *tab;       // double-float exp/log tables (device)
     unsigned long long *ctr;   // per-kind counters: [2 kind] launches, [2 kind + 1] launches that did work
 };
 
@@ -106,6 +112,21 @@ struct PicardCtl {
 struct CondSet {
     unsigned long long h;
     int use;
+};
+
+// Start of the linear solve fused into the assembly kernel: x = h^k and the
+// first residual b - A h^k from the freshly computed face coefficients.
+enum { ASM_ONLY = 0, ASM_CG64 = 1, ASM_MIXED = 2 };
+struct SolveStart {
+    double *x;                 // x0 = h^k copied here
+    double *r, *z;             // FP64 residual and D^-1 r (ASM_CG64)
+    float *r32, *z32, *d32;    // FP32 inner seeds (ASM_MIXED)
+    CgScal *sc;                // FP64 solve, or the outer defect-correction loop
+    CgScal *inner;             // inner FP32 solve (ASM_MIXED)
+    double tol, tol_inner;
+    int max_it, inner_max_it, outer_max_it;
+    int pad;
+    CondSet cond, cond_inner;  // loop conditions raised for the solve
 };
 
 // Results of the per-step reductions, read back by the host.
@@ -165,6 +186,59 @@ __device__ __forceinline__ void set_cond(const CondSet &c, unsigned int v)
 {
     if (c.use) cudaGraphSetConditional(c.h, v);
 }
+
+// FP64 PCG start from the reduced (r.z, r.r, b.b) of the initial residual.
+__device__ __forceinline__ void cg64_start_scalars(CgScal *sc, const double (&v)[3], double tol, int max_it,
+                                                   const CondSet &cond)
+{
+    sc->rho = v[0];
+    sc->rr = v[1];
+    sc->bb = v[2];
+    sc->stop2 = tol * sqrt(v[2]);      // threshold on ||r||_2
+    sc->alpha = 0.0;
+    sc->beta = 0.0;
+    sc->iter = 0;
+    sc->total = 0;
+    sc->max_it = max_it;
+    const bool finite = isfinite(v[0]) && isfinite(v[1]) && isfinite(v[2]);
+    sc->status = finite ? CG_OK : CG_NONFINITE;
+    sc->done = (!finite || sqrt(v[1]) <= sc->stop2) ? 1 : 0;
+    set_cond(cond, sc->done ? 0 : 1);
+}
+
+// Defect correction: test of an outer FP64 residual (r.r, b.b) and seeds of
+// the inner FP32 solve (r32.r32, r32.z32); outer->iter already counts this
+// residual, and the solve fails after outer_max_it residuals.
+__device__ __forceinline__ void outer_residual_scalars(CgScal *outer, CgScal *inner, const double (&v)[4], double tol,
+                                                       double tol_inner, int inner_max_it, int outer_max_it,
+                                                       const CondSet &co, const CondSet &ci)
+{
+    const bool finite = isfinite(v[0]) && isfinite(v[1]) && isfinite(v[2]) && isfinite(v[3]);
+    outer->rr = v[0];
+    outer->bb = v[1];
+    outer->stop2 = tol * sqrt(v[1]);
+    if (!finite) {
+        outer->status = CG_NONFINITE;
+        outer->done = 1;
+    } else if (sqrt(v[0]) <= outer->stop2) {
+        outer->done = 1;
+    } else if (outer->iter >= outer_max_it) {
+        outer->status = CG_MAXIT;
+        outer->done = 1;
+    }
+    inner->rho = v[3];
+    inner->rr = v[2];
+    inner->bb = v[2];
+    inner->stop2 = tol_inner * sqrt(v[2]);
+    inner->alpha = 0.0;
+    inner->beta = 0.0;
+    inner->iter = 0;
+    inner->max_it = inner_max_it;
+    inner->status = CG_OK;
+    inner->done = (outer->done || !(v[2] > 0.0)) ? 1 : 0;
+    set_cond(co, outer->done ? 0 : 1);
+    set_cond(ci, inner->done ? 0 : 1);
+}
 #endif
 
 // Message returned by rf_last_error() on the calling thread.
@@ -187,7 +261,9 @@ void launch_assemble(cudaStream_t s, int nblk, const Grid &g, const DevSoil *soi
                      const double *Ks, const uint8_t *flags, const StepParams *sp, const double *hk,
                      const double *hn, const double *theta_k, const double *theta_n, const double *K,
                      const double *Can, double *c, double *b, double *Tx, double *Ty, double *Tz,
-                     double *diag, double *dinv, float *K32, float *cb32, float *dinv32, const int *skip);
+                     double *diag, double *dinv, float *K32, float *cb32, float *dinv32, const int *skip,
+                     int mode = ASM_ONLY, const SolveStart *start = nullptr, double *partials = nullptr,
+                     unsigned int *ticket = nullptr);
 
 void launch_mass_balance(cudaStream_t s, int nblk, const Grid &g, const DevSoil *soils, const uint8_t *zone,
                          const double *Ks, const uint8_t *flags, const StepParams *sp, const double *x,

@@ -80,4 +80,49 @@ __device__ __forceinline__ bool grid_reduce(double (&v)[NV], double *partials, u
     return true;
 }
 
+// Grid-level sum of float thread values: warp and block levels in FP32 (no
+// FP64 instructions per thread), the cross-block fold in FP64.  Same
+// contract as grid_reduce.
+template <int NV>
+__device__ __forceinline__ bool grid_reduce_f32(float (&vf)[NV], double (&v)[NV], double *partials,
+                                                unsigned int *ticket)
+{
+    __shared__ float smf[NV * 32];
+    __shared__ double sm[NV * 32];
+    __shared__ bool am_last;
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
+#pragma unroll
+    for (int i = 0; i < NV; i++) {
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) vf[i] += __shfl_xor_sync(0xffffffffu, vf[i], o);
+    }
+    if (lane == 0) {
+#pragma unroll
+        for (int i = 0; i < NV; i++) smf[i * 32 + wid] = vf[i];
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+#pragma unroll
+        for (int i = 0; i < NV; i++) {
+            float t = 0.0f;
+            for (int w = 0; w < nw; w++) t += smf[i * 32 + w];
+            partials[i * gridDim.x + blockIdx.x] = (double)t;
+        }
+        __threadfence();
+        unsigned int t = atomicInc(ticket, gridDim.x - 1);
+        am_last = (t == gridDim.x - 1);
+    }
+    __syncthreads();
+    if (!am_last) return false;
+    __threadfence();
+#pragma unroll
+    for (int i = 0; i < NV; i++) {
+        double t = 0.0;
+        for (int b = threadIdx.x; b < (int)gridDim.x; b += blockDim.x) t += __ldcg(&partials[i * gridDim.x + b]);
+        v[i] = t;
+    }
+    block_reduce<OpSum, NV>(v, sm);
+    return true;
+}
+
 }  // namespace rf
