@@ -53,6 +53,7 @@ def parse():
     ap.add_argument("--seed", type=int, default=0)
     ap.add_argument("--no-baseline", action="store_true", help="skip the CPU oracle baseline leg")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-pcg-hbm", action="store_true", help="skip the large-grid PCG kernel bandwidth leg")
     return ap.parse_args()
 
 
@@ -248,6 +249,22 @@ def native(args):
             "traffic": traffic_for(names[dom], n_act), "algorithmic_bytes_per_launch": kd["bytes"],
             "avg_launch_ms": kd["avg_ms"]}
 
+    # ---- PCG stencil kernels on a grid far larger than L2 (HBM regime):
+    # the 512x512x64 watershed (16.8 M cells), kernels timed by events
+    pcg_hbm = None
+    if not args.no_pcg_hbm:
+        ws = W.watershed(512, 512, 64, seed=args.seed + rank, hours=24)
+        sw = rf.Solver.from_case(ws, precision="mixed")
+        pcg_hbm = {"workload": "watershed_512x512x64", "cells": ws.N, "active_cells": ws.n_active(),
+                   "peak_gbs": hbm_peak, "kernels": {}}
+        for kind in ("cg32_spmv", "cg32_update", "cg64_spmv", "cg64_update", "resid64"):
+            avg_ms, by = sw.profile_kernel(kind, reps=20)
+            gbs = by / (avg_ms * 1e-3) / 1e9
+            pcg_hbm["kernels"][kind] = {"avg_us": avg_ms * 1e3, "algorithmic_MB": by / 1e6, "GBps": gbs,
+                                        "frac_of_hbm_peak": gbs / hbm_peak}
+        sw.close()
+        del sw
+
     # ---- end to end through host buffers
     e2e = None
     if not args.no_e2e:
@@ -293,6 +310,7 @@ def native(args):
             "kernels": {k: {"avg_us": v["avg_ms"] * 1e3, "GBps": v["gbs"]} for k, v in kern.items()},
             "clocks": clk,
             "e2e": e2e,
+            "pcg_hbm": pcg_hbm,
         }
         if not args.no_baseline:
             line["cpu_baseline"] = cpu_baseline(case)

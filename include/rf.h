@@ -244,6 +244,53 @@ typedef enum rf_kernel_kind {
  * the linear-solver scratch is. */
 rf_status rf_profile_kernel(rf_ctx *ctx, int kind, int reps, double *avg_ms, double *bytes_per_launch);
 
+/* ---- batched ensemble of independent problems ----------------------------
+ *
+ * Many independent instances of uneven size (soil columns and blocks), each
+ * with its own grid, van Genuchten soil, uniform initial head, top and bottom
+ * conditions (lateral faces zero-flux) and its own EBATS / Picard / PCG state,
+ * advanced together by one persistent kernel launched from a CUDA graph.  A
+ * work unit is a thread-block cluster of `cluster` CTAs that takes instances
+ * from a device queue (largest first) and integrates each one in time; the
+ * per-cell arithmetic is the single-domain solver's. */
+typedef struct rf_ens rf_ens;
+
+typedef struct rf_ens_instance {
+    int nx, ny, nz;
+    double dx, dy, dz;
+    rf_soil soil;
+    double h0;                            /* uniform initial head [m]                 */
+    int top_type;                         /* RF_BC_DIRICHLET, RF_BC_FLUX, ZERO_FLUX   */
+    double top_value;
+    int bottom_type;                      /* RF_BC_FREE_DRAINAGE, DIRICHLET, ZERO_FLUX */
+    double bottom_value;
+} rf_ens_instance;
+
+typedef struct rf_ens_stats {
+    double t, dt_nom;
+    long long steps, picard_iters, cg_iters, rejected;
+    int status;                           /* RF_OK, RF_ERR_DT_MIN, RF_ERR_DEVICE_TIMEOUT */
+    long long cells;
+    double storage0, inflow_cum, outflow_cum, closure_abs, nonlinear_defect_cum;
+} rf_ens_stats;
+
+/* Create an ensemble (instances copied; params as for rf_mesh_create; the
+ * precision selects FP64 PCG or FP32 inner PCG in FP64 defect correction). */
+rf_status rf_ens_create(const rf_ens_instance *inst, int n, const rf_solver_params *params, void *cuda_stream,
+                        const rf_allocator *alloc, rf_ens **out);
+void rf_ens_destroy(rf_ens *ens);
+/* Cluster size (CTAs per work unit): 1, 2, 4 or 8. */
+rf_status rf_ens_set_tiling(rf_ens *ens, int cluster);
+/* Advance every instance to t_end (one graph launch; synchronises). */
+rf_status rf_ens_run(rf_ens *ens, double t_end);
+/* State of instance i (user order): h (host, its nx*ny*nz cells, or NULL). */
+rf_status rf_ens_get(rf_ens *ens, int i, double *h, rf_ens_stats *stats);
+/* Return every instance to its initial state. */
+rf_status rf_ens_reset(rf_ens *ens);
+/* Tuner: time each cluster size from the initial state to t_probe, keep the
+ * fastest, and reset to the initial state. */
+rf_status rf_ens_tune(rf_ens *ens, double t_probe, int *best_cluster, double *best_ms);
+
 /* ---- a linear solve that allocates no device memory ----------------------
  *
  * No counterpart in the paper: this is a library facility.  Some callers

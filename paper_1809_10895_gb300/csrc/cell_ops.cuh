@@ -1,0 +1,251 @@
+// cell_ops.cuh -- per-cell device arithmetic shared by the single-domain
+// kernels and the batched-ensemble kernel: closures (Eq. 2-4, Eq. A6), grid
+// neighbours and the two stencil forms of the Picard operator.
+#pragma once
+
+#include <math.h>
+
+#include "rf_internal.cuh"
+
+namespace rf {
+
+// van Genuchten / Mualem closures (Eq. 2-4), evaluated in double-float
+// arithmetic (ff.cuh) with FP64 only at the input and the outputs.
+// With u = -alpha h, L = log u, x = u^n = exp(n L), l1 = log(1 + x):
+//   Se = (1 + x)^-m = exp(-m l1)                               (Eq. 2)
+//   u^(n-1) = x / u (since m n = n - 1), so (x/(1+x))^m = (x/u) Se = ys
+//   Se^(1/m) = 1/(1+x) = w, so 1 - Se^(1/m) = x/(1+x) and
+//   K = Ks Se^(1/2) (1 - ys)^2                                   (Eq. 4)
+//     with 1 - ys = -expm1(m log(1 - w)) when ys > 1/2 (dry soil, where
+//     1 - ys would cancel)
+//   C = (theta_s-theta_r) alpha n m u^(n-1) (1+x)^-(m+1)
+//     = (theta_s-theta_r) alpha n m ys w                         (Eq. 3)
+// For h >= 0 (tie included): theta* = theta_s + S h, K = Ks, C = S, which
+// makes d(theta*)/dh equal to Eq. 3 on both branches.
+// Gardner (Eq. A6, a test model): K = Ks e^(alpha h), theta = theta_r +
+// (theta_s-theta_r) e^(alpha h), in FP64.
+__device__ __forceinline__ void closure(const DevSoil &s, double Ks, double h, const FFTables *__restrict__ tab,
+                                        double &th, double &K, double &C)
+{
+    if (h >= 0.0) {
+        th = s.theta_s + s.S * h;
+        K = Ks;
+        C = s.S;
+        return;
+    }
+    const double dth = s.theta_s - s.theta_r;
+    if (s.model == M_GARDNER) {
+        const double e = exp(s.alpha * h);
+        K = Ks * e;
+        th = s.theta_r + dth * e;
+        C = dth * s.alpha * e;
+        return;
+    }
+    const double ud = -s.alpha * h;
+    if (ud < 1e-30) {                     // (-alpha h)^n underflows: the wet limit
+        th = s.theta_s;
+        K = Ks;
+        C = 0.0;
+        return;
+    }
+    const ff u = ff_from_d(ud);
+    const ff L = ff_log(u, tab);
+    const ff nL = ff_mul(ff_make(s.n_hi, s.n_lo), L);
+    if (nL.hi > 80.0f) {                  // x > e^80: Se = x^-m, K and C vanish at double range
+        th = s.theta_r + dth * ff_to_d(ff_exp(ff_neg(ff_mul(ff_make(s.m_hi, s.m_lo), nL)), tab));
+        K = 0.0;
+        C = 0.0;
+        return;
+    }
+    const ff x = ff_exp(nL, tab);
+    const ff onepx = ff_add_f(x, 1.0f);
+    const ff l1 = ff_log(onepx, tab);
+    const ff mm = ff_make(s.m_hi, s.m_lo);
+    const ff se = ff_exp(ff_neg(ff_mul(mm, l1)), tab);
+    const ff w = ff_div(ff_make(1.0f, 0.0f), onepx);
+    const ff ys = ff_mul(ff_div(x, u), se);
+    ff omy;
+    if (ys.hi <= 0.5f) {
+        omy = ff_add_f(ff_neg(ys), 1.0f);
+    } else {
+        const ff lg = (w.hi < 0.0078125f) ? ff_log1p_small(ff_neg(w)) : ff_log(ff_add_f(ff_neg(w), 1.0f), tab);
+        const ff z = ff_mul(mm, lg);
+        omy = (z.hi > -0.0078125f) ? ff_neg(ff_expm1_small(z)) : ff_add_f(ff_neg(ff_exp(z, tab)), 1.0f);
+    }
+    th = s.theta_r + dth * ff_to_d(se);
+    K = Ks * ff_to_d(ff_mul(ff_sqrt(se), ff_mul(omy, omy)));
+    C = (dth * s.alpha * s.n * s.m) * ff_to_d(ff_mul(ys, w));
+}
+
+// Neighbour across face f of cell p = (i,j,k); false when outside the grid.
+__device__ __forceinline__ bool neighbour(const Grid &g, long long p, int i, int j, int k, int f, long long &q)
+{
+    switch (f) {
+    case F_XMIN: q = p - 1; return i > 0;
+    case F_XMAX: q = p + 1; return i < g.nx - 1;
+    case F_YMIN: q = p - g.nx; return j > 0;
+    case F_YMAX: q = p + g.nx; return j < g.ny - 1;
+    case F_ZMIN: q = p - g.sxy; return k > 0;
+    default:     q = p + g.sxy; return k < g.nz - 1;
+    }
+}
+
+// FP64 stencil with stored coefficients; get(q) supplies the vector value.
+template <class Get>
+__device__ __forceinline__ double apply64(const Grid &g, long long p, const double *__restrict__ Tx,
+                                          const double *__restrict__ Ty, const double *__restrict__ Tz,
+                                          const double *__restrict__ diag, Get get)
+{
+    int i, j, k;
+    cell_ijk(g, p, i, j, k);
+    double acc = diag[p] * get(p);
+    if (i > 0) acc -= Tx[p - 1] * get(p - 1);
+    if (i < g.nx - 1) acc -= Tx[p] * get(p + 1);
+    if (j > 0) acc -= Ty[p - g.nx] * get(p - g.nx);
+    if (j < g.ny - 1) acc -= Ty[p] * get(p + g.nx);
+    if (k > 0) acc -= Tz[p - g.sxy] * get(p - g.sxy);
+    if (k < g.nz - 1) acc -= Tz[p] * get(p + g.sxy);
+    return acc;
+}
+
+// FP32 operator with faces recomputed from FP32 K.
+template <class Get>
+__device__ __forceinline__ float apply32(const Grid &g, long long p, const float *__restrict__ K32,
+                                         const float *__restrict__ cb32, Get get)
+{
+    int i, j, k;
+    cell_ijk(g, p, i, j, k);
+    const float KP = K32[p];
+    const float vP = get(p);
+    float acc = cb32[p] * vP;
+    auto face = [&](bool inside, long long q, float w) {
+        if (!inside) return;
+        const float KN = K32[q];
+        if (KN < 0.0f) return;
+        acc = fmaf(w * 0.5f * (KP + KN), vP - get(q), acc);
+    };
+    face(i > 0, p - 1, g.w32[0]);
+    face(i < g.nx - 1, p + 1, g.w32[0]);
+    face(j > 0, p - g.nx, g.w32[1]);
+    face(j < g.ny - 1, p + g.nx, g.w32[1]);
+    face(k > 0, p - g.sxy, g.w32[2]);
+    face(k < g.nz - 1, p + g.sxy, g.w32[2]);
+    return acc;
+}
+
+// One cell of the Picard system (Sec. 2.2; see k_assemble):
+//   c = V C^k / dt (chord slope of theta*, or C(h^k) when |h^k - h^n| <= eps),
+//   interior faces T_f = (K_P + K_N)/2 A_f/d_f with explicit gravity,
+//   boundary terms of the face classes flagged in fl.
+// With RESID, sT = sum over interior faces of T_f h^k_N (for b - A h^k).
+struct CellSystem {
+    double c, rhs, diag, cb, sT, KP;
+    double Tup[3];
+};
+
+template <bool RESID>
+__device__ __forceinline__ void assemble_cell(const Grid &g, const DevSoil *__restrict__ soils,
+                                              const uint8_t *__restrict__ zone, const double *__restrict__ Ks,
+                                              uint8_t fl, const StepParams &sp, long long p, int i, int j, int k,
+                                              const double *__restrict__ hk, const double *__restrict__ hn,
+                                              const double *__restrict__ thk, const double *__restrict__ thn,
+                                              const double *__restrict__ K, const double *__restrict__ Can,
+                                              double eps, double V_dt, CellSystem &out)
+{
+    const double hkP = hk[p], hnP = hn[p], KP = K[p];
+    const double dh = hkP - hnP;
+    // |dh| > eps compared on the IEEE bit patterns (both non-negative)
+    const bool chord = (__double_as_longlong(dh) & 0x7fffffffffffffffLL) > __double_as_longlong(eps);
+    const double C = chord ? (thk[p] - thn[p]) * rcp64(dh) : Can[p];
+    const double c = V_dt * C;
+    double diag = c, rhs = c * hnP, cb = c;
+    double sT = 0.0;
+    double Tup[3] = {0.0, 0.0, 0.0};
+#pragma unroll
+    for (int f = 0; f < 6; f++) {
+        long long q;
+        if (neighbour(g, p, i, j, k, f, q)) {
+            const double KN = K[q];
+            if (__double_as_longlong(KN) >= 0) {          // active neighbour (K >= 0; inactive K = -1)
+                const double Ks2 = KP + KN;
+                const double T = Ks2 * g.hw[f];            // (K_P + K_N)/2 A/d
+                diag += T;
+                if (f >= F_ZMIN) rhs = fma(Ks2, g.hg[f], rhs);   // explicit gravity, +-Kbar A_z
+                if (f & 1) Tup[f >> 1] = T;
+                if (RESID) sT = fma(T, hk[q], sT);
+                continue;
+            }
+        }
+        const double gs = (f == F_ZMIN) ? -1.0 : (f == F_ZMAX ? 1.0 : 0.0);
+        if (!(fl & (1u << f))) continue;    // closed face (lateral face on an inactive cell)
+        int type = sp.bc_type[f];
+        double hD = 0.0;
+        if (type == BC_SEEPAGE) {
+            if (hnP >= 0.0) { type = BC_DIRICHLET; hD = 0.0; }
+            else type = BC_ZERO_FLUX;
+        } else if (type == BC_DIRICHLET) {
+            hD = sp.bc_val[f];
+        }
+        if (type == BC_DIRICHLET) {
+            const DevSoil s = soils[zone[p]];
+            double thD, KD, CD;
+            closure(s, Ks[p], hD, g.tab, thD, KD, CD);
+            const double T = KD * g.wb[f];
+            diag += T;
+            cb += T;
+            rhs += T * hD + gs * KD * g.A[f];
+        } else if (type == BC_FLUX) {
+            rhs += sp.bc_val[f] * g.A[f];
+        } else if (type == BC_FREE_DRAINAGE) {
+            rhs += -KP * g.A[f];
+        }
+    }
+    out.c = c;
+    out.rhs = rhs;
+    out.diag = diag;
+    out.cb = cb;
+    out.sT = sT;
+    out.KP = KP;
+    out.Tup[0] = Tup[0];
+    out.Tup[1] = Tup[1];
+    out.Tup[2] = Tup[2];
+}
+
+// Boundary inflow (fin >= 0) and outflow (fout >= 0) of one cell's boundary
+// faces in the linear system solved for x (the water balance of Sec. 2.2's
+// chord-slope scheme): Dirichlet T_D (h_D - x) +- K(h_D) A_z, imposed flux,
+// free drainage -K(h^k) A_z, seepage as Dirichlet 0 while h^n >= 0.
+__device__ __forceinline__ void boundary_fluxes(const Grid &g, const DevSoil &s, double Ksp, uint8_t fl,
+                                                const StepParams &sp, double xp, double hnP, double Kold,
+                                                double &fin, double &fout)
+{
+    fin = 0.0;
+    fout = 0.0;
+#pragma unroll
+    for (int f = 0; f < 6; f++) {
+        if (!(fl & (1u << f))) continue;
+        const double gs = (f == F_ZMIN) ? -1.0 : (f == F_ZMAX ? 1.0 : 0.0);
+        int type = sp.bc_type[f];
+        double hD = 0.0, flux = 0.0;
+        if (type == BC_SEEPAGE) {
+            if (hnP >= 0.0) { type = BC_DIRICHLET; hD = 0.0; }
+            else type = BC_ZERO_FLUX;
+        } else if (type == BC_DIRICHLET) {
+            hD = sp.bc_val[f];
+        }
+        if (type == BC_DIRICHLET) {
+            double thD, KD, CD;
+            closure(s, Ksp, hD, g.tab, thD, KD, CD);
+            const double T = KD * g.wb[f];
+            flux = T * hD + gs * KD * g.A[f] - T * xp;
+        } else if (type == BC_FLUX) {
+            flux = sp.bc_val[f] * g.A[f];
+        } else if (type == BC_FREE_DRAINAGE) {
+            flux = -Kold * g.A[f];
+        }
+        if (flux > 0.0) fin += flux;
+        else fout -= flux;
+    }
+}
+
+}  // namespace rf

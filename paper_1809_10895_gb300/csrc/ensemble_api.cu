@@ -1,0 +1,393 @@
+// ensemble_api.cu -- C ABI of the batched ensemble (rf_ens_*): packing of
+// uneven instances, the persistent kernel captured in a CUDA graph, and the
+// tuner that picks the cluster size (CTAs per instance work unit).
+#include <algorithm>
+#include <cmath>
+#include <numeric>
+#include <string>
+#include <vector>
+
+#include "ensemble.cuh"
+#include "rf.h"
+
+using namespace rf;
+
+namespace {
+
+rf_status efail(rf_status s, const std::string &m)
+{
+    set_last_error(m.c_str());
+    return s;
+}
+
+#define ECUDA(x)                                                                                          \
+    do {                                                                                                  \
+        cudaError_t e_ = (x);                                                                             \
+        if (e_ != cudaSuccess) return efail(RF_ERR_CUDA, std::string(#x) + ": " + cudaGetErrorString(e_)); \
+    } while (0)
+
+}  // namespace
+
+struct rf_ens {
+    cudaStream_t stream = nullptr;
+    rf_allocator alloc{};
+    bool has_alloc = false;
+    std::vector<void *> allocations;
+    int n = 0, precision = 0, cluster = 1;
+    long long ncells = 0;
+    std::vector<int> order;            // queue position -> user index
+    std::vector<int> pos;              // user index -> queue position
+    std::vector<EnsDesc> desc0;        // initial descriptors (queue order)
+    std::vector<double> h0;            // initial heads (packed, queue order)
+    EnsDesc *D = nullptr;
+    EnsBuffers B{};
+    EnsParams P{};
+    FFTables *tab = nullptr;
+    unsigned long long *ctr = nullptr;
+    double *t_end = nullptr, *t_end_h = nullptr;
+    unsigned int *queue = nullptr;
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t exec = nullptr;
+    int graph_cluster = 0;
+
+    void *dalloc(size_t bytes)
+    {
+        bytes = (bytes + 255) & ~size_t(255);
+        void *ptr = nullptr;
+        if (has_alloc) ptr = alloc.alloc(bytes, alloc.user);
+        else if (cudaMalloc(&ptr, bytes) != cudaSuccess) ptr = nullptr;
+        if (ptr) allocations.push_back(ptr);
+        return ptr;
+    }
+    template <class T>
+    bool get(T *&p, size_t n_)
+    {
+        p = static_cast<T *>(dalloc(sizeof(T) * (n_ ? n_ : 1)));
+        return p != nullptr;
+    }
+};
+
+namespace {
+
+void destroy_graph(rf_ens *e)
+{
+    if (e->exec) cudaGraphExecDestroy(e->exec);
+    if (e->graph) cudaGraphDestroy(e->graph);
+    e->exec = nullptr;
+    e->graph = nullptr;
+    e->graph_cluster = 0;
+}
+
+rf_status upload_initial(rf_ens *e)
+{
+    ECUDA(cudaMemcpyAsync(e->D, e->desc0.data(), sizeof(EnsDesc) * e->n, cudaMemcpyHostToDevice, e->stream));
+    ECUDA(cudaMemcpyAsync(e->B.H[0], e->h0.data(), sizeof(double) * e->ncells, cudaMemcpyHostToDevice, e->stream));
+    ECUDA(cudaStreamSynchronize(e->stream));
+    return RF_OK;
+}
+
+// One graph: queue reset, then the persistent kernel.
+rf_status build_graph(rf_ens *e)
+{
+    destroy_graph(e);
+    const int ncl = ensemble_max_clusters(e->cluster, e->precision);
+    if (ncl < 1) return efail(RF_ERR_CUDA, "no cluster of that size fits on this device");
+    cudaStream_t cap;
+    ECUDA(cudaStreamCreateWithFlags(&cap, cudaStreamNonBlocking));
+    cudaError_t err = cudaStreamBeginCapture(cap, cudaStreamCaptureModeRelaxed);
+    if (err == cudaSuccess) err = cudaMemsetAsync(e->queue, 0, sizeof(unsigned int), cap);
+    if (err == cudaSuccess)
+        err = launch_ensemble(cap, e->cluster, ncl, e->precision, e->D, e->n, e->B, e->P, e->t_end, e->queue);
+    cudaGraph_t g = nullptr;
+    const cudaError_t err2 = cudaStreamEndCapture(cap, &g);
+    cudaStreamDestroy(cap);
+    if (err != cudaSuccess || err2 != cudaSuccess) {
+        if (g) cudaGraphDestroy(g);
+        return efail(RF_ERR_CUDA, std::string("ensemble graph capture: ") +
+                                      cudaGetErrorString(err != cudaSuccess ? err : err2));
+    }
+    e->graph = g;
+    ECUDA(cudaGraphInstantiate(&e->exec, g, 0));
+    e->graph_cluster = e->cluster;
+    return RF_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+rf_status rf_ens_create(const rf_ens_instance *inst, int n, const rf_solver_params *params, void *cuda_stream,
+                        const rf_allocator *alloc, rf_ens **out)
+{
+    if (!inst || n < 1 || !out) return efail(RF_ERR_ARG, "rf_ens_create: need at least one instance");
+    *out = nullptr;
+    rf_solver_params prm;
+    rf_default_params(&prm);
+    if (params) prm = *params;
+    if (prm.precision != RF_PREC_FP64 && prm.precision != RF_PREC_MIXED)
+        return efail(RF_ERR_ARG, "rf_ens_create: unknown precision");
+    int ndev = 0;
+    if (cudaGetDeviceCount(&ndev) != cudaSuccess || ndev < 1) {
+        cudaGetLastError();
+        return efail(RF_ERR_NO_DEVICE, "no CUDA device visible; this library has no CPU fallback");
+    }
+    int dev = 0;
+    ECUDA(cudaGetDevice(&dev));
+    cudaDeviceProp prop;
+    ECUDA(cudaGetDeviceProperties(&prop, dev));
+    if (prop.major != 10 || prop.minor != 3)
+        return efail(RF_ERR_NO_DEVICE, "this library is built for sm_103a (GB300) only");
+    long long total = 0;
+    for (int i = 0; i < n; i++) {
+        const rf_ens_instance &a = inst[i];
+        if (a.nx < 1 || a.ny < 1 || a.nz < 1 || !(a.dx > 0) || !(a.dy > 0) || !(a.dz > 0))
+            return efail(RF_ERR_ARG, "rf_ens_create: bad grid in instance " + std::to_string(i));
+        const rf_soil &s = a.soil;
+        if ((s.model != RF_VG && s.model != RF_GARDNER) || !(s.theta_s > s.theta_r) || !(s.alpha > 0) ||
+            !(s.Ks > 0) || !(s.S >= 0) || (s.model == RF_VG && !(s.n > 1.0)))
+            return efail(RF_ERR_ARG, "rf_ens_create: bad soil in instance " + std::to_string(i));
+        if (a.top_type != RF_BC_DIRICHLET && a.top_type != RF_BC_FLUX && a.top_type != RF_BC_ZERO_FLUX)
+            return efail(RF_ERR_ARG, "rf_ens_create: top must be Dirichlet, flux or zero flux");
+        if (a.bottom_type != RF_BC_FREE_DRAINAGE && a.bottom_type != RF_BC_DIRICHLET &&
+            a.bottom_type != RF_BC_ZERO_FLUX)
+            return efail(RF_ERR_ARG, "rf_ens_create: bottom must be free drainage, Dirichlet or zero flux");
+        total += (long long)a.nx * a.ny * a.nz;
+    }
+    if (total > (1LL << 31) - 1) return efail(RF_ERR_ARG, "rf_ens_create: too many cells");
+
+    rf_ens *e = new rf_ens();
+    e->stream = static_cast<cudaStream_t>(cuda_stream);
+    if (alloc && alloc->alloc && alloc->free) { e->alloc = *alloc; e->has_alloc = true; }
+    e->n = n;
+    e->precision = prm.precision;
+    e->ncells = total;
+    // largest instances first in the work queue
+    e->order.resize(n);
+    std::iota(e->order.begin(), e->order.end(), 0);
+    auto cells = [&](int i) { return (long long)inst[i].nx * inst[i].ny * inst[i].nz; };
+    std::stable_sort(e->order.begin(), e->order.end(), [&](int a, int b) { return cells(a) > cells(b); });
+    e->pos.resize(n);
+    for (int k = 0; k < n; k++) e->pos[e->order[k]] = k;
+
+    const long long N = total;
+    bool ok = e->get(e->D, n) && e->get(e->tab, 1) && e->get(e->ctr, 2 * KK_COUNT) && e->get(e->t_end, 1) &&
+              e->get(e->queue, 1);
+    for (int b = 0; b < 3 && ok; b++) ok = e->get(e->B.H[b], N);
+    for (int b = 0; b < 2 && ok; b++) ok = e->get(e->B.TH[b], N) && e->get(e->B.K[b], N) && e->get(e->B.p[b], N) &&
+                                            e->get(e->B.p32[b], N);
+    ok = ok && e->get(e->B.Can, N) && e->get(e->B.c, N) && e->get(e->B.b, N) && e->get(e->B.Tx, N) &&
+         e->get(e->B.Ty, N) && e->get(e->B.Tz, N) && e->get(e->B.diag, N) && e->get(e->B.dinv, N) &&
+         e->get(e->B.r, N) && e->get(e->B.z, N) && e->get(e->B.q, N) && e->get(e->B.K32, N) &&
+         e->get(e->B.cb32, N) && e->get(e->B.dinv32, N) && e->get(e->B.r32, N) && e->get(e->B.z32, N) &&
+         e->get(e->B.q32, N) && e->get(e->B.d32, N) && e->get(e->B.flags, N) && e->get(e->B.zone, N) &&
+         e->get(e->B.Ks, N);
+    if (!ok || cudaMallocHost(&e->t_end_h, sizeof(double)) != cudaSuccess) {
+        rf_ens_destroy(e);
+        return efail(RF_ERR_NOMEM, "rf_ens_create: allocation failed");
+    }
+
+    FFTables tab;
+    make_ff_tables(&tab);
+    std::vector<uint8_t> flags(N), zone(N, 0);
+    std::vector<double> Ks(N);
+    e->h0.assign(N, 0.0);
+    e->desc0.resize(n);
+    long long off = 0;
+    for (int k = 0; k < n; k++) {
+        const rf_ens_instance &a = inst[e->order[k]];
+        EnsDesc d{};
+        Grid &g = d.g;
+        g.nx = a.nx; g.ny = a.ny; g.nz = a.nz;
+        g.N = (long long)a.nx * a.ny * a.nz;
+        g.sxy = (long long)a.nx * a.ny;
+        g.V = a.dx * a.dy * a.dz;
+        const double A[6] = {a.dy * a.dz, a.dy * a.dz, a.dx * a.dz, a.dx * a.dz, a.dx * a.dy, a.dx * a.dy};
+        const double dd[6] = {a.dx, a.dx, a.dy, a.dy, a.dz, a.dz};
+        for (int f = 0; f < 6; f++) {
+            g.A[f] = A[f];
+            g.w[f] = A[f] / dd[f];
+            g.wb[f] = A[f] / (0.5 * dd[f]);
+            g.hw[f] = 0.5 * (A[f] / dd[f]);
+            g.hg[f] = f == F_ZMIN ? -0.5 * A[f] : (f == F_ZMAX ? 0.5 * A[f] : 0.0);
+        }
+        for (int ax = 0; ax < 3; ax++) g.w32[ax] = (float)(A[2 * ax] / dd[2 * ax]);
+        g.fx = make_fastdiv((unsigned int)a.nx);
+        g.fxy = make_fastdiv((unsigned int)g.sxy);
+        g.tab = e->tab;
+        g.ctr = e->ctr;
+        const rf_soil &s = a.soil;
+        const double m = s.model == RF_VG ? 1.0 - 1.0 / s.n : 0.0;
+        const float nh = (float)s.n, mh = (float)m;
+        d.soil = DevSoil{s.model, s.theta_r, s.theta_s, s.alpha, s.n, m, s.S, nh, (float)(s.n - (double)nh), mh,
+                         (float)(m - (double)mh)};
+        for (int f = 0; f < 6; f++) { d.sp.bc_type[f] = BC_ZERO_FLUX; d.sp.bc_val[f] = 0.0; }
+        d.sp.bc_type[F_ZMAX] = a.top_type;
+        d.sp.bc_val[F_ZMAX] = a.top_value;
+        d.sp.bc_type[F_ZMIN] = a.bottom_type;
+        d.sp.bc_val[F_ZMIN] = a.bottom_value;
+        d.sp.eps_chord = prm.eps_chord;
+        d.off = off;
+        d.t = 0.0;
+        d.dt_nom = std::min(prm.dt0, prm.dt_max);
+        d.status = ENS_NEW;
+        e->desc0[k] = d;
+        for (int kk = 0; kk < a.nz; kk++)
+            for (int j = 0; j < a.ny; j++)
+                for (int i = 0; i < a.nx; i++) {
+                    const long long p = off + i + (long long)a.nx * (j + (long long)a.ny * kk);
+                    uint8_t fl = FLAG_ACTIVE;
+                    if (i == 0) fl |= 1u << F_XMIN;
+                    if (i == a.nx - 1) fl |= 1u << F_XMAX;
+                    if (j == 0) fl |= 1u << F_YMIN;
+                    if (j == a.ny - 1) fl |= 1u << F_YMAX;
+                    if (kk == 0) fl |= 1u << F_ZMIN;
+                    if (kk == a.nz - 1) fl |= 1u << F_ZMAX;
+                    flags[p] = fl;
+                    Ks[p] = s.Ks;
+                    e->h0[p] = a.h0;
+                }
+        off += g.N;
+    }
+    EnsParams &P = e->P;
+    P.tol_picard = prm.tol_picard;
+    P.tol_cg = prm.tol_cg;
+    P.tol_inner = prm.tol_inner;
+    P.dt_max = prm.dt_max;
+    P.dt_min = prm.dt_min;
+    P.f_grow = prm.f_grow;
+    P.f_shrink = prm.f_shrink;
+    P.eps_chord = prm.eps_chord;
+    P.n_inc = prm.n_inc;
+    P.n_small = prm.n_small;
+    P.n_max = prm.n_max;
+    P.cg_max_it = prm.cg_max_it;
+    P.inner_max_it = prm.inner_max_it;
+    P.outer_max_it = prm.outer_max_it;
+    P.step_budget = 10000000;
+    cudaError_t err = cudaMemcpyAsync(e->tab, &tab, sizeof(FFTables), cudaMemcpyHostToDevice, e->stream);
+    if (err == cudaSuccess) err = cudaMemcpyAsync(e->B.flags, flags.data(), N, cudaMemcpyHostToDevice, e->stream);
+    if (err == cudaSuccess) err = cudaMemcpyAsync(e->B.zone, zone.data(), N, cudaMemcpyHostToDevice, e->stream);
+    if (err == cudaSuccess) err = cudaMemcpyAsync(e->B.Ks, Ks.data(), sizeof(double) * N, cudaMemcpyHostToDevice, e->stream);
+    if (err == cudaSuccess) err = cudaMemsetAsync(e->ctr, 0, 2 * KK_COUNT * sizeof(unsigned long long), e->stream);
+    if (err == cudaSuccess) err = cudaStreamSynchronize(e->stream);
+    if (err != cudaSuccess) {
+        rf_ens_destroy(e);
+        return efail(RF_ERR_CUDA, std::string("rf_ens_create: ") + cudaGetErrorString(err));
+    }
+    if (rf_status st = upload_initial(e)) {
+        rf_ens_destroy(e);
+        return st;
+    }
+    *out = e;
+    return RF_OK;
+}
+
+void rf_ens_destroy(rf_ens *e)
+{
+    if (!e) return;
+    cudaStreamSynchronize(e->stream);
+    destroy_graph(e);
+    for (void *p : e->allocations) {
+        if (e->has_alloc) e->alloc.free(p, e->alloc.user);
+        else cudaFree(p);
+    }
+    if (e->t_end_h) cudaFreeHost(e->t_end_h);
+    delete e;
+}
+
+rf_status rf_ens_set_tiling(rf_ens *e, int cluster)
+{
+    if (!e || (cluster != 1 && cluster != 2 && cluster != 4 && cluster != 8))
+        return efail(RF_ERR_ARG, "rf_ens_set_tiling: cluster must be 1, 2, 4 or 8");
+    if (ensemble_max_clusters(cluster, e->precision) < 1)
+        return efail(RF_ERR_ARG, "rf_ens_set_tiling: clusters of that size do not fit on this device");
+    e->cluster = cluster;
+    return RF_OK;
+}
+
+rf_status rf_ens_run(rf_ens *e, double t_end)
+{
+    if (!e || !std::isfinite(t_end)) return efail(RF_ERR_ARG, "rf_ens_run: bad argument");
+    if (!e->exec || e->graph_cluster != e->cluster)
+        if (rf_status st = build_graph(e)) return st;
+    *e->t_end_h = t_end;
+    ECUDA(cudaMemcpyAsync(e->t_end, e->t_end_h, sizeof(double), cudaMemcpyHostToDevice, e->stream));
+    ECUDA(cudaGraphLaunch(e->exec, e->stream));
+    ECUDA(cudaStreamSynchronize(e->stream));
+    ECUDA(cudaGetLastError());
+    return RF_OK;
+}
+
+rf_status rf_ens_get(rf_ens *e, int i, double *h, rf_ens_stats *st)
+{
+    if (!e || i < 0 || i >= e->n) return efail(RF_ERR_ARG, "rf_ens_get: bad instance index");
+    const int k = e->pos[i];
+    EnsDesc d;
+    ECUDA(cudaMemcpyAsync(&d, e->D + k, sizeof(EnsDesc), cudaMemcpyDeviceToHost, e->stream));
+    ECUDA(cudaStreamSynchronize(e->stream));
+    if (h) {
+        const int hb = d.status == ENS_NEW ? 0 : d.hbuf;
+        ECUDA(cudaMemcpyAsync(h, e->B.H[hb] + d.off, sizeof(double) * d.g.N, cudaMemcpyDeviceToHost, e->stream));
+        ECUDA(cudaStreamSynchronize(e->stream));
+    }
+    if (st) {
+        st->t = d.t;
+        st->dt_nom = d.dt_nom;
+        st->steps = d.steps;
+        st->picard_iters = d.picard;
+        st->cg_iters = d.cg;
+        st->rejected = d.rejected;
+        st->status = d.status == ENS_DT_MIN ? RF_ERR_DT_MIN : (d.status == ENS_BUDGET ? RF_ERR_DEVICE_TIMEOUT : RF_OK);
+        st->cells = d.g.N;
+        st->storage0 = d.storage0;
+        st->inflow_cum = d.in_cum;
+        st->outflow_cum = d.out_cum;
+        st->closure_abs = std::fabs(d.closure_cum);
+        st->nonlinear_defect_cum = d.defect_cum;
+    }
+    return RF_OK;
+}
+
+rf_status rf_ens_reset(rf_ens *e)
+{
+    if (!e) return efail(RF_ERR_ARG, "null ensemble");
+    return upload_initial(e);
+}
+
+rf_status rf_ens_tune(rf_ens *e, double t_probe, int *best_cluster, double *best_ms)
+{
+    if (!e || !(t_probe > 0)) return efail(RF_ERR_ARG, "rf_ens_tune: bad argument");
+    int best = 0;
+    double best_t = INFINITY;
+    cudaEvent_t a, b;
+    ECUDA(cudaEventCreate(&a));
+    ECUDA(cudaEventCreate(&b));
+    for (int c : {1, 2, 4, 8}) {
+        if (ensemble_max_clusters(c, e->precision) < 1) continue;
+        e->cluster = c;
+        if (rf_status st = upload_initial(e)) return st;
+        if (rf_status st = build_graph(e)) return st;
+        *e->t_end_h = t_probe;
+        ECUDA(cudaMemcpyAsync(e->t_end, e->t_end_h, sizeof(double), cudaMemcpyHostToDevice, e->stream));
+        ECUDA(cudaEventRecord(a, e->stream));
+        ECUDA(cudaGraphLaunch(e->exec, e->stream));
+        ECUDA(cudaEventRecord(b, e->stream));
+        ECUDA(cudaEventSynchronize(b));
+        float ms = 0.0f;
+        ECUDA(cudaEventElapsedTime(&ms, a, b));
+        if (ms < best_t) {
+            best_t = ms;
+            best = c;
+        }
+    }
+    cudaEventDestroy(a);
+    cudaEventDestroy(b);
+    if (!best) return efail(RF_ERR_CUDA, "rf_ens_tune: no cluster size fits");
+    e->cluster = best;
+    if (rf_status st = upload_initial(e)) return st;
+    if (best_cluster) *best_cluster = best;
+    if (best_ms) *best_ms = best_t;
+    return RF_OK;
+}
+
+}  // extern "C"

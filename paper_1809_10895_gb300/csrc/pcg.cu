@@ -19,6 +19,7 @@
 // round trip per iteration; kernels of a finished solve return at once.
 #include <math.h>
 
+#include "cell_ops.cuh"
 #include "rf_internal.cuh"
 #include "rf_reduce.cuh"
 
@@ -27,24 +28,6 @@ namespace rf {
 #define GRID_STRIDE_LOOP(p)                                                                 \
     for (long long p = (long long)blockIdx.x * blockDim.x + threadIdx.x; p < g.N;           \
          p += (long long)gridDim.x * blockDim.x)
-
-// FP64 stencil with stored coefficients; get(q) supplies the vector value.
-template <class Get>
-__device__ __forceinline__ double apply64(const Grid &g, long long p, const double *__restrict__ Tx,
-                                          const double *__restrict__ Ty, const double *__restrict__ Tz,
-                                          const double *__restrict__ diag, Get get)
-{
-    int i, j, k;
-    cell_ijk(g, p, i, j, k);
-    double acc = diag[p] * get(p);
-    if (i > 0) acc -= Tx[p - 1] * get(p - 1);
-    if (i < g.nx - 1) acc -= Tx[p] * get(p + 1);
-    if (j > 0) acc -= Ty[p - g.nx] * get(p - g.nx);
-    if (j < g.ny - 1) acc -= Ty[p] * get(p + g.nx);
-    if (k > 0) acc -= Tz[p - g.sxy] * get(p - g.sxy);
-    if (k < g.nz - 1) acc -= Tz[p] * get(p + g.sxy);
-    return acc;
-}
 
 // ---------------------------------------------------------------- FP64 PCG
 __global__ void __launch_bounds__(RED_THREADS)
@@ -182,31 +165,6 @@ k_apply64(Grid g, const uint8_t *__restrict__ flags, const double *__restrict__ 
 }
 
 // ------------------------------------------------------ mixed precision
-// FP32 operator with faces recomputed from FP32 K.
-template <class Get>
-__device__ __forceinline__ float apply32(const Grid &g, long long p, const float *__restrict__ K32,
-                                         const float *__restrict__ cb32, Get get)
-{
-    int i, j, k;
-    cell_ijk(g, p, i, j, k);
-    const float KP = K32[p];
-    const float vP = get(p);
-    float acc = cb32[p] * vP;
-    auto face = [&](bool inside, long long q, float w) {
-        if (!inside) return;
-        const float KN = K32[q];
-        if (KN < 0.0f) return;
-        acc = fmaf(w * 0.5f * (KP + KN), vP - get(q), acc);
-    };
-    face(i > 0, p - 1, g.w32[0]);
-    face(i < g.nx - 1, p + 1, g.w32[0]);
-    face(j > 0, p - g.nx, g.w32[1]);
-    face(j < g.ny - 1, p + g.nx, g.w32[1]);
-    face(k > 0, p - g.sxy, g.w32[2]);
-    face(k < g.nz - 1, p + g.sxy, g.w32[2]);
-    return acc;
-}
-
 // Start of a defect-correction solve: x = x0, counters reset, outer loop
 // condition raised (or, when the Picard attempt is over, an empty loop).
 __global__ void __launch_bounds__(RED_THREADS)

@@ -976,11 +976,14 @@ rf_status rf_profile_kernel(rf_ctx *c, int kind, int reps, double *avg_ms, doubl
     run_closure(c, c->hk, nullptr, c->theta_k, 0);
     run_assemble(c, c->hk, c->h, c->theta_k, c->theta_n);
     c->closure_at_h = false;
-    if (kind == RF_K_CG64_SPMV || kind == RF_K_CG64_UPDATE)   // a solve that never converges
-        launch_cg64_init(s, nb, g, c->flags, c->hk, c->x, c->b, c->Tx, c->Ty, c->Tz, c->diag, c->dinv, c->r, c->z,
+    // the timed solves start from x0 = 0 (r0 = b, never zero) with a zero
+    // tolerance, so every timed launch does its full work whatever the state
+    CUDA_TRY(cudaMemsetAsync(c->q, 0, sizeof(double) * g.N, s));
+    if (kind == RF_K_CG64_SPMV || kind == RF_K_CG64_UPDATE)
+        launch_cg64_init(s, nb, g, c->flags, c->q, c->x, c->b, c->Tx, c->Ty, c->Tz, c->diag, c->dinv, c->r, c->z,
                          0.0, 1 << 30, c->partials, c->ticket, c->sc, nullptr, none);
     if (kind >= RF_K_RESID64) {
-        launch_mixed_start(s, nb, g, c->hk, c->x, c->sc, c->sc_in, nullptr, none);
+        launch_mixed_start(s, nb, g, c->q, c->x, c->sc, c->sc_in, nullptr, none);
         launch_resid64(s, nb, g, c->flags, c->x, c->b, c->Tx, c->Ty, c->Tz, c->diag, c->dinv32, c->r32, c->z32,
                        c->d32, 0.0, 1e-30, 1 << 30, 1 << 30, c->partials, c->ticket, c->sc, c->sc_in, none, none);
     }

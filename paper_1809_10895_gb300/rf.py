@@ -77,6 +77,19 @@ class rf_mass_balance_t(C.Structure):
                                           "closure_rel", "nonlinear_defect_cum")]
 
 
+class rf_ens_instance(C.Structure):
+    _fields_ = [("nx", C.c_int), ("ny", C.c_int), ("nz", C.c_int), ("dx", C.c_double), ("dy", C.c_double),
+                ("dz", C.c_double), ("soil", rf_soil), ("h0", C.c_double), ("top_type", C.c_int),
+                ("top_value", C.c_double), ("bottom_type", C.c_int), ("bottom_value", C.c_double)]
+
+
+class rf_ens_stats(C.Structure):
+    _fields_ = [("t", C.c_double), ("dt_nom", C.c_double), ("steps", C.c_longlong), ("picard_iters", C.c_longlong),
+                ("cg_iters", C.c_longlong), ("rejected", C.c_longlong), ("status", C.c_int), ("cells", C.c_longlong),
+                ("storage0", C.c_double), ("inflow_cum", C.c_double), ("outflow_cum", C.c_double),
+                ("closure_abs", C.c_double), ("nonlinear_defect_cum", C.c_double)]
+
+
 # name -> (restype, argtypes): the functions declared in include/rf.h
 _VP, _DP, _U8P = C.c_void_p, C.POINTER(C.c_double), C.POINTER(C.c_uint8)
 SIGNATURES = {
@@ -102,6 +115,14 @@ SIGNATURES = {
     "rf_launch_count": (C.c_ulonglong, [_VP]),
     "rf_profile_kernel": (C.c_int, [_VP, C.c_int, C.c_int, _DP, _DP]),
     "rf_launch_counts": (C.c_int, [_VP, C.POINTER(C.c_ulonglong), C.c_int]),
+    "rf_ens_create": (C.c_int, [C.POINTER(rf_ens_instance), C.c_int, C.POINTER(rf_solver_params), _VP,
+                                C.POINTER(rf_allocator), C.POINTER(_VP)]),
+    "rf_ens_destroy": (None, [_VP]),
+    "rf_ens_set_tiling": (C.c_int, [_VP, C.c_int]),
+    "rf_ens_run": (C.c_int, [_VP, C.c_double]),
+    "rf_ens_get": (C.c_int, [_VP, C.c_int, _DP, C.POINTER(rf_ens_stats)]),
+    "rf_ens_reset": (C.c_int, [_VP]),
+    "rf_ens_tune": (C.c_int, [_VP, C.c_double, C.POINTER(C.c_int), _DP]),
     "rf_pcg_solve_noalloc": (C.c_int, [C.c_int, C.c_int, C.c_int, _VP, _VP, _VP, _VP, _VP, _VP, C.c_double,
                                        C.c_int, _VP, C.POINTER(C.c_int)]),
 }
@@ -338,6 +359,77 @@ class Solver:
         it = C.c_int(0)
         _check(load().rf_solve(self.ctx, C.c_void_p(x.data_ptr()), C.byref(it)), "rf_solve")
         return it.value
+
+
+class Ensemble:
+    """A batched ensemble of independent instances (rf_ens_*)."""
+
+    def __init__(self, instances, params=None, stream=None, use_torch_allocator=True):
+        import torch
+        L = load()
+        self.n = len(instances)
+        arr = (rf_ens_instance * self.n)(*instances)
+        self.params = params if params is not None else default_params()
+        self.stream = stream if stream is not None else torch.cuda.current_stream()
+        self._allocator = TorchAllocator(torch.device("cuda", torch.cuda.current_device())) \
+            if use_torch_allocator else None
+        h = _VP()
+        _check(L.rf_ens_create(arr, self.n, C.byref(self.params), C.c_void_p(self.stream.cuda_stream),
+                               C.byref(self._allocator.struct) if self._allocator else None, C.byref(h)),
+               "rf_ens_create")
+        self.ctx = h
+        self.cells = [i.nx * i.ny * i.nz for i in instances]
+
+    @staticmethod
+    def instance_of_case(case) -> rf_ens_instance:
+        """A workloads.Case with one soil, uniform initial head, top/bottom
+        conditions and zero-flux lateral faces as an ensemble instance."""
+        s = case.soils[0]
+        soil = rf_soil(MODELS[s.get("model", "vg")], s["theta_r"], s["theta_s"], s["alpha"], s.get("n", 2.0),
+                       s["Ks"], s.get("S", 1e-5))
+        top = next((b for b in case.bcs if b.face == "zmax"), None)
+        bot = next((b for b in case.bcs if b.face == "zmin"), None)
+        tt, tv = (BC_TYPES[top.type], float(top.v[0]) if top.v is not None else 0.0) if top else (0, 0.0)
+        bt, bv = (BC_TYPES[bot.type], float(bot.v[0]) if bot.v is not None else 0.0) if bot else (0, 0.0)
+        return rf_ens_instance(case.nx, case.ny, case.nz, case.dx, case.dy, case.dz, soil, float(case.h0[0]),
+                               tt, tv, bt, bv)
+
+    @classmethod
+    def from_cases(cls, cases, **param_overrides):
+        p = dict(cases[0].params)
+        p.update(param_overrides)
+        return cls([cls.instance_of_case(c) for c in cases], params=default_params(**p))
+
+    def close(self):
+        if getattr(self, "ctx", None):
+            load().rf_ens_destroy(self.ctx)
+            self.ctx = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def set_tiling(self, cluster: int):
+        _check(load().rf_ens_set_tiling(self.ctx, int(cluster)), "rf_ens_set_tiling")
+
+    def run(self, t_end):
+        _check(load().rf_ens_run(self.ctx, float(t_end)), "rf_ens_run")
+
+    def get(self, i, want_h=True):
+        st = rf_ens_stats()
+        h = np.zeros(self.cells[i]) if want_h else None
+        _check(load().rf_ens_get(self.ctx, int(i), _dptr(h), C.byref(st)), "rf_ens_get")
+        return h, {k: getattr(st, k) for k, _ in rf_ens_stats._fields_}
+
+    def reset(self):
+        _check(load().rf_ens_reset(self.ctx), "rf_ens_reset")
+
+    def tune(self, t_probe):
+        c, ms = C.c_int(0), C.c_double(0)
+        _check(load().rf_ens_tune(self.ctx, float(t_probe), C.byref(c), C.byref(ms)), "rf_ens_tune")
+        return c.value, ms.value
 
 
 def pcg_solve_noalloc(shape, diag, Tx, Ty, Tz, b, x, tol=1e-10, max_it=10000, stream=None) -> int:

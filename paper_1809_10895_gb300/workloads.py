@@ -245,11 +245,14 @@ def watershed(nx: int = 512, ny: int = 512, nz: int = 64, dx: float = 10.0, dz: 
 # Uneven ensemble
 # --------------------------------------------------------------------------
 def ensemble(n: int = 256, seed: int = 0, t_end: float = 2 * 86400.0, max_side: int = 16,
-             nz_range=(50, 400), dz: float = 0.01, **param_overrides) -> list:
+             nz_range=(50, 400), dz: float = 0.01, top_head: float = -0.01, **param_overrides) -> list:
     """Independent instances of uneven size: footprint nx, ny ~ U{1..max_side},
     depth nz ~ U{nz_range}, 1 cm cells, uniformly sampled van Genuchten
-    parameters, uniform initial head in [-3, -0.1] m, ponded top (h = 0),
-    free-draining bottom, lateral zero flux."""
+    parameters, uniform initial head in [-3, -0.1] m, top held at
+    ``top_head`` (default -1 cm: water at the surface without positive
+    pressure; a head of exactly 0 drives soils with n < 2 to the h = 0 state in
+    which classical Picard cannot contract), free-draining bottom, lateral
+    zero flux."""
     rng = np.random.default_rng(seed)
     cases = []
     for i in range(n):
@@ -261,6 +264,6 @@ def ensemble(n: int = 256, seed: int = 0, t_end: float = 2 * 86400.0, max_side: 
         c = Case(name=f"ensemble_{i}_{nx}x{ny}x{nz}", nx=nx, ny=ny, nz=nz, dx=dz, dy=dz, dz=dz,
                  soils=[soil], params=default_params(**param_overrides), t_end=t_end)
         c.h0 = np.full(c.N, h_init)
-        c.bcs = [BC("zmax", "dirichlet", np.array([0.0]), np.array([0.0])), BC("zmin", "free_drainage")]
+        c.bcs = [BC("zmax", "dirichlet", np.array([0.0]), np.array([top_head])), BC("zmin", "free_drainage")]
         cases.append(c)
     return cases
