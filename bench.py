@@ -54,6 +54,8 @@ def parse():
     ap.add_argument("--no-baseline", action="store_true", help="skip the CPU oracle baseline leg")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-pcg-hbm", action="store_true", help="skip the large-grid PCG kernel bandwidth leg")
+    ap.add_argument("--no-ensemble", action="store_true", help="skip the batched-ensemble leg")
+    ap.add_argument("--ensemble-window", type=float, default=600.0, help="simulated seconds of the ensemble leg")
     return ap.parse_args()
 
 
@@ -264,6 +266,51 @@ def native(args):
                                         "frac_of_hbm_peak": gbs / hbm_peak}
         sw.close()
         del sw
+        # one stiff solve on that grid (x0 = 0, dt = 600 s): inner FP32 PCG
+        # preconditioned by Jacobi vs by the multigrid V-cycle
+        hk = torch.as_tensor(ws.h0, dtype=torch.float64, device="cuda")
+        pcg_hbm["solve_x0_zero"] = {}
+        for pc in ("jacobi", "mg"):
+            sv = rf.Solver.from_case(ws, precision="mixed", precond=pc)
+            sv.assemble(hk, hk, 600.0, 0.0)
+            res = None
+            for rep in range(2):                      # the first call captures the graph
+                x = torch.zeros(ws.N, dtype=torch.float64, device="cuda")
+                a, b_ = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                a.record(sv.stream)
+                its = sv.solve(x)
+                b_.record(sv.stream)
+                torch.cuda.synchronize()
+                res = {"inner_iterations": its, "ms": a.elapsed_time(b_)}
+            pcg_hbm["solve_x0_zero"][pc] = res
+            sv.close()
+            del sv
+
+    # ---- batched ensemble: 256 uneven instances (1 cm cells, footprints
+    # 1..16 x 1..16, depths 50..400) in one persistent graph-launched kernel
+    ens = None
+    if not args.no_ensemble:
+        cases = W.ensemble(256, seed=args.seed + rank)
+        e = rf.Ensemble.from_cases(cases, precision="mixed")
+        cluster, probe_ms = e.tune(min(60.0, args.ensemble_window))
+        barrier()
+        ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        ev0.record(e.stream)
+        e.run(args.ensemble_window)
+        ev1.record(e.stream)
+        torch.cuda.synchronize()
+        ens_ms = ev0.elapsed_time(ev1)
+        cell_steps = 0
+        stats = [e.get(i, want_h=False)[1] for i in range(len(cases))]
+        cell_steps = sum(st["steps"] * st["cells"] for st in stats)
+        ens = {"workload": "ensemble_256_uneven", "instances": len(cases), "cells": sum(c.N for c in cases),
+               "simulated_window_s": args.ensemble_window, "cluster_ctas": cluster, "tuner_probe_ms": probe_ms,
+               "kernel_ms": ens_ms, "cell_timesteps": cell_steps, "value": cell_steps / (ens_ms * 1e-3),
+               "unit": UNIT, "steps_total": sum(st["steps"] for st in stats),
+               "picard_total": sum(st["picard_iters"] for st in stats),
+               "failed_instances": sum(1 for st in stats if st["status"] != 0), "precision": "mixed"}
+        e.close()
+        del e
 
     # ---- end to end through host buffers
     e2e = None
@@ -311,6 +358,7 @@ def native(args):
             "clocks": clk,
             "e2e": e2e,
             "pcg_hbm": pcg_hbm,
+            "ensemble": ens,
         }
         if not args.no_baseline:
             line["cpu_baseline"] = cpu_baseline(case)

@@ -12,6 +12,7 @@
 #include <string>
 #include <vector>
 
+#include "mg.cuh"
 #include "rf.h"
 #include "rf_internal.cuh"
 
@@ -85,6 +86,9 @@ struct rf_ctx {
     PicardCtl *ctl_h = nullptr;
     unsigned long long *ctr_h = nullptr;
 
+    MgHierarchy mg;                      // multigrid levels (RF_PRECOND_MG)
+    bool mg_alloc = false;
+
     // CUDA graphs: a whole Picard attempt, and a stand-alone linear solve
     cudaStream_t cap = nullptr;          // private capture stream
     cudaGraph_t picard_graph = nullptr, solve_graph = nullptr;
@@ -126,8 +130,10 @@ rf_status check_params(const rf_solver_params *p)
         return fail(RF_ERR_ARG, "invalid solver parameters");
     if (p->precision != RF_PREC_FP64 && p->precision != RF_PREC_MIXED)
         return fail(RF_ERR_ARG, "unknown precision mode");
-    if (p->precond != RF_PRECOND_JACOBI)
-        return fail(RF_ERR_ARG, "only the Jacobi preconditioner is available in this build");
+    if (p->precond != RF_PRECOND_JACOBI && p->precond != RF_PRECOND_MG)
+        return fail(RF_ERR_ARG, "unknown preconditioner");
+    if (p->precond == RF_PRECOND_MG && p->precision != RF_PREC_MIXED)
+        return fail(RF_ERR_ARG, "the multigrid preconditioner serves the FP32 inner solve: use RF_PREC_MIXED");
     return RF_OK;
 }
 
@@ -227,6 +233,54 @@ rf_status add_while(cudaGraph_t parent, const std::vector<cudaGraphNode_t> &deps
         if (s_ != RF_OK) return s_;            \
     } while (0)
 
+// Multigrid levels of this grid (allocated on first use).
+rf_status ensure_mg(rf_ctx *c)
+{
+    if (c->mg_alloc) return RF_OK;
+    const Grid &g = c->g;
+    const double dx = g.A[0] / g.w[0], dy = g.A[2] / g.w[2], dz = g.A[4] / g.w[4];
+    MgShape shp[MG_MAX_LEVELS];
+    const int nl = mg_plan(g.nx, g.ny, g.nz, dx, dy, dz, shp, MG_MAX_LEVELS);
+    if (nl < 2) return fail(RF_ERR_ARG, "grid too small for a multigrid hierarchy");
+    MgHierarchy &H = c->mg;
+    H.nlev = nl;
+    for (int l = 0; l < nl; l++) {
+        MgLevel &L = H.lev[l];
+        L = MgLevel{};
+        L.level = l;
+        L.nx = shp[l].nx;
+        L.ny = shp[l].ny;
+        L.nz = shp[l].nz;
+        L.N = (long long)L.nx * L.ny * L.nz;
+        L.sxy = (long long)L.nx * L.ny;
+        L.fx = make_fastdiv((unsigned int)L.nx);
+        L.fxy = make_fastdiv((unsigned int)L.sxy);
+        if (l + 1 < nl) {
+            L.cx = shp[l + 1].nx == L.nx ? 1 : 2;
+            L.cy = shp[l + 1].ny == L.ny ? 1 : 2;
+            L.cz = shp[l + 1].nz == L.nz ? 1 : 2;
+        } else {
+            L.cx = L.cy = L.cz = 1;
+        }
+        const size_t n = (size_t)L.N;
+        bool ok = true;
+        if (l == 0) {
+            L.w32[0] = g.w32[0];
+            L.w32[1] = g.w32[1];
+            L.w32[2] = g.w32[2];
+            L.cb = c->cb32;
+            L.dinv0 = c->dinv32;
+            ok = alloc_n(c, L.e[1], n);
+        } else {
+            ok = alloc_n(c, L.cb, n) && alloc_n(c, L.T[0], n) && alloc_n(c, L.T[1], n) && alloc_n(c, L.T[2], n) &&
+                 alloc_n(c, L.dinv, n) && alloc_n(c, L.r, n) && alloc_n(c, L.e[0], n) && alloc_n(c, L.e[1], n);
+        }
+        if (!ok) return fail(RF_ERR_NOMEM, "multigrid allocation failed");
+    }
+    c->mg_alloc = true;
+    return RF_OK;
+}
+
 // Linear solve A x = b from x0 into x, appended to `parent` after `deps`
 // (handles created on the top graph `top`).  skip: attempt-over flag or null.
 // With `fused`, the assembly kernel before `deps` has already started the
@@ -265,12 +319,23 @@ rf_status capture_solve(rf_ctx *c, cudaGraph_t top, cudaGraph_t parent, std::vec
     }
     // mixed: WHILE(outer) { WHILE(inner FP32 PCG) ; x += d ; FP64 residual }
     const CondSet co = start->cond, ci = start->cond_inner;
+    const bool mg = c->prm.precond == RF_PRECOND_MG;
+    const int *idone = &c->sc_in->done;
+    const CondSet none{0, 0};
     if (!fused) {
         RF_TRY(cap_begin(c, parent, deps));
         launch_mixed_start(s, nb, g, x0, x, c->sc, c->sc_in, skip, co);
         launch_resid64(s, nb, g, c->flags, x, c->b, c->Tx, c->Ty, c->Tz, c->diag, c->dinv32, c->r32, c->z32, c->d32,
                        c->prm.tol_cg, c->prm.tol_inner, c->prm.inner_max_it, c->prm.outer_max_it, c->partials,
                        c->ticket, c->sc, c->sc_in, co, ci);
+        RF_TRY(cap_end(c, deps));
+    }
+    if (mg) {
+        // coarse operators from this assembly, then z0 = V(r0) and rho = r0.z0
+        RF_TRY(cap_begin(c, parent, deps));
+        launch_mg_build(s, nb, c->mg, c->K32, skip);
+        launch_mg_vcycle(s, nb, c->mg, c->K32, c->r32, c->z32, idone);
+        launch_cg32_rz(s, nb, g, c->r32, c->z32, c->partials, c->ticket, c->sc_in, 1, ci);
         RF_TRY(cap_end(c, deps));
     }
     cudaGraphNode_t wo, wi;
@@ -281,8 +346,14 @@ rf_status capture_solve(rf_ctx *c, cudaGraph_t top, cudaGraph_t parent, std::vec
     for (int half = 0; half < 2; half++) {
         float *pin = c->p32[half], *pout = c->p32[half ^ 1];
         launch_cg32_spmv(s, nb, g, c->z32, pin, pout, c->q32, c->K32, c->cb32, c->partials, c->ticket, c->sc_in);
-        launch_cg32_update(s, nb, g, c->d32, c->r32, c->z32, pout, c->q32, c->dinv32, c->partials, c->ticket,
-                           c->sc_in, ci);
+        if (mg) {
+            launch_cg32_update_mg(s, nb, g, c->d32, c->r32, pout, c->q32, c->dinv32, c->partials, c->ticket, c->sc_in);
+            launch_mg_vcycle(s, nb, c->mg, c->K32, c->r32, c->z32, idone);
+            launch_cg32_rz(s, nb, g, c->r32, c->z32, c->partials, c->ticket, c->sc_in, 0, ci);
+        } else {
+            launch_cg32_update(s, nb, g, c->d32, c->r32, c->z32, pout, c->q32, c->dinv32, c->partials, c->ticket,
+                               c->sc_in, ci);
+        }
     }
     std::vector<cudaGraphNode_t> tmp;
     RF_TRY(cap_end(c, tmp));
@@ -291,6 +362,11 @@ rf_status capture_solve(rf_ctx *c, cudaGraph_t top, cudaGraph_t parent, std::vec
     launch_resid64(s, nb, g, c->flags, x, c->b, c->Tx, c->Ty, c->Tz, c->diag, c->dinv32, c->r32, c->z32, c->d32,
                    c->prm.tol_cg, c->prm.tol_inner, c->prm.inner_max_it, c->prm.outer_max_it, c->partials, c->ticket,
                    c->sc, c->sc_in, co, ci);
+    if (mg) {
+        launch_mg_vcycle(s, nb, c->mg, c->K32, c->r32, c->z32, idone);
+        launch_cg32_rz(s, nb, g, c->r32, c->z32, c->partials, c->ticket, c->sc_in, 1, ci);
+    }
+    (void)none;
     RF_TRY(cap_end(c, tmp));
     out = {wo};
     return RF_OK;
@@ -342,6 +418,7 @@ void destroy_graphs(rf_ctx *c)
 // ended return at once.
 rf_status build_picard_graph(rf_ctx *c)
 {
+    if (c->prm.precond == RF_PRECOND_MG) RF_TRY(ensure_mg(c));
     cudaGraph_t G;
     CUDA_TRY(cudaGraphCreate(&G, 0));
     c->picard_graph = G;
@@ -383,6 +460,7 @@ rf_status build_picard_graph(rf_ctx *c)
 
 rf_status build_solve_graph(rf_ctx *c)
 {
+    if (c->prm.precond == RF_PRECOND_MG) RF_TRY(ensure_mg(c));
     cudaGraph_t G;
     CUDA_TRY(cudaGraphCreate(&G, 0));
     c->solve_graph = G;
@@ -992,6 +1070,10 @@ rf_status rf_profile_kernel(rf_ctx *c, int kind, int reps, double *avg_ms, doubl
     for (int i = 0; i < reps; i++) {
         double *pin = c->p[i & 1], *pout = c->p[(i + 1) & 1];
         float *qin = c->p32[i & 1], *qout = c->p32[(i + 1) & 1];
+        // every timed launch does its full work: the solve is never marked
+        // finished (values may stop being meaningful; the traffic does not)
+        cudaMemsetAsync(&c->sc->done, 0, sizeof(int), s);
+        cudaMemsetAsync(&c->sc_in->done, 0, sizeof(int), s);
         auto timed = [&](auto &&launch) {
             cudaEventRecord(ev[2 * i], s);
             launch();
