@@ -267,3 +267,28 @@ def ensemble(n: int = 256, seed: int = 0, t_end: float = 2 * 86400.0, max_side: 
         c.bcs = [BC("zmax", "dirichlet", np.array([0.0]), np.array([top_head])), BC("zmin", "free_drainage")]
         cases.append(c)
     return cases
+
+
+# Layer shapes (cin, cout) of the warm-start network: input convolution,
+# two per residual block (four blocks), output convolution.
+NN_LAYERS = [(4, 32)] + [(32, 32)] * 8 + [(32, 1)]
+
+
+def nn_init_params(seed: int = 0) -> np.ndarray:
+    """Seeded initial parameters of the warm-start network, flat FP64.
+
+    Layer by layer: W[cout, 3, 3, 3, cin] then b[cout].  Weights are normal
+    with std sqrt(2 / fan_in) (He et al. 2015), scaled by 0.1 for the second
+    convolution of each residual block and for the output convolution so
+    the network starts close to the identity map plus a small output;
+    biases are zero.
+    """
+    rng = np.random.default_rng(seed)
+    parts = []
+    for li, (ci, co) in enumerate(NN_LAYERS):
+        std = np.sqrt(2.0 / (27 * ci))
+        if li == len(NN_LAYERS) - 1 or (li >= 1 and li % 2 == 0):
+            std *= 0.1
+        parts.append(rng.normal(0.0, std, size=27 * ci * co))
+        parts.append(np.zeros(co))
+    return np.concatenate(parts)
