@@ -332,6 +332,93 @@ rf_status rf_pcg_solve_noalloc(int nx, int ny, int nz, const double *d_diag, con
                                const double *d_Ty, const double *d_Tz, const double *d_b, double *d_x,
                                double tol, int max_it, void *cuda_stream, int *iters);
 
+/* ---------------------------------------------------------------------
+ * Learned warm start.  The paper starts each Picard sequence (Sec. 2.2) from
+ * the previous time level h^n; this extension starts it from a network's
+ * guess instead.  Picard still runs to tol_picard from that guess, so the
+ * method judges the guess's error; when an attempt from a guess does not
+ * converge, the step falls back to the plain method (restart from h^n with
+ * dt / f_shrink, as for any rejected attempt).
+ *
+ * Network: a 3-D convolutional residual network in BF16 with FP32
+ * accumulation -- input convolution 4 -> 32, four residual blocks of two
+ * 32 -> 32 convolutions (ReLU after the first; the block input is added
+ * before the second ReLU), output convolution 32 -> 1.  All convolutions
+ * are 3x3x3, stride 1, zero padding 1, cross-correlation.  Volumes are
+ * channels-last, voxel index x + W (y + H (z + D b)); a mesh is one volume
+ * with D = nz, H = ny, W = nx, so voxel = cell index p.
+ *
+ * Parameters are exchanged as RF_NN_PARAMS floats, layer by layer (input,
+ * block 1 conv 1, block 1 conv 2, ..., output): W[cout][3][3][3][cin] (the
+ * first index of each 3 is the -1 offset along z, y, x) then b[cout].
+ * --------------------------------------------------------------------- */
+typedef struct rf_nn rf_nn;
+#define RF_NN_PARAMS 225793
+
+/* Feature and output scales.  Features of an active cell:
+ *   0: h / h_scale                       1: (ln Ks - lnK_mean) / lnK_std
+ *   2: q_top / q_scale on cells that carry the top (z max) boundary face, 0
+ *      elsewhere; q_top is the top flux condition's value at the step's
+ *      start time (0 if the top condition is not RF_BC_FLUX)
+ *   3: ln(dt / t_scale)
+ * and all zero on inactive cells.  The guess is h + y out_scale dt. */
+typedef struct rf_ws_scales {
+    double h_scale, lnK_mean, lnK_std, q_scale, t_scale, out_scale;
+} rf_ws_scales;
+
+/* Adam (Kingma & Ba 2015) settings of a training step. */
+typedef struct rf_adam {
+    float lr, beta1, beta2, eps;
+} rf_adam;
+
+/* Create a network on the current device, parameters zero, work ordered on
+ * cuda_stream (a cudaStream_t, NULL = legacy stream).  Device memory
+ * (parameters, optimizer moments, activations sized for the largest volume
+ * seen) comes from alloc when given. */
+rf_status rf_nn_create(void *cuda_stream, const rf_allocator *alloc, rf_nn **out);
+void rf_nn_destroy(rf_nn *net);
+/* Copy RF_NN_PARAMS host floats in / out (n must equal RF_NN_PARAMS).
+ * Setting parameters also clears the Adam moments and step count. */
+rf_status rf_nn_set_params(rf_nn *net, const float *params, long long n);
+rf_status rf_nn_get_params(rf_nn *net, float *params, long long n);
+/* Forward pass.  d_x: B*D*H*W*4 floats (features, channels-last, 16-byte
+ * aligned); d_y: B*D*H*W floats (output).  Asynchronous on the network's
+ * stream. */
+rf_status rf_nn_forward(rf_nn *net, const float *d_x, int B, int D, int H, int W, float *d_y);
+/* Loss L = (1/M) sum_v mask_v (y_v - target_v)^2 over the M = B*D*H*W
+ * voxels (d_mask may be NULL: all ones), and its gradient.  grad: NULL or
+ * RF_NN_PARAMS host floats (parameter order above).  Synchronises. */
+rf_status rf_nn_loss_grad(rf_nn *net, const float *d_x, const float *d_target, const float *d_mask, int B, int D,
+                          int H, int W, float *loss, float *grad);
+/* One training step: loss, gradient, Adam update of the FP32 master
+ * parameters.  loss: NULL (asynchronous) or where to write L (synchronises). */
+rf_status rf_nn_train_step(rf_nn *net, const float *d_x, const float *d_target, const float *d_mask, int B, int D,
+                           int H, int W, const rf_adam *opt, float *loss);
+/* Kernel launches issued by this network so far (host count). */
+long long rf_nn_launch_count(const rf_nn *net);
+
+/* Features of a state of the mesh for a step of size dt from time t (the
+ * top flux feature takes the top condition's value at t): d_h is N doubles
+ * on the device, or NULL for the context's current state; d_x receives N*4
+ * floats (16-byte aligned).  Ordered on the context's stream.  The warm
+ * start computes the same features from the current state and time. */
+rf_status rf_ws_features(rf_ctx *ctx, const rf_ws_scales *sc, const double *d_h, double t, double dt, float *d_x);
+/* Training target of the step just taken from d_h_old (N doubles, the state
+ * before the step) with size dt: d_target[p] = (h[p] - h_old[p]) /
+ * (out_scale dt) on active cells, else 0; d_mask (may be NULL) 1 / 0. */
+rf_status rf_ws_target(rf_ctx *ctx, const rf_ws_scales *sc, const double *d_h_old, double dt, float *d_target,
+                       float *d_mask);
+/* Attach a network (borrowed; NULL detaches): every step's first attempt
+ * starts Picard from the network's guess.  The network must live on the
+ * context's device; its inference then runs on the context's stream. */
+rf_status rf_ws_attach(rf_ctx *ctx, rf_nn *net, const rf_ws_scales *sc);
+typedef struct rf_ws_stats {
+    long long guesses;     /* attempts started from a guess                    */
+    long long fallbacks;   /* of those, attempts that did not converge         */
+} rf_ws_stats;
+rf_status rf_ws_get_stats(rf_ctx *ctx, rf_ws_stats *out);
+
+
 #ifdef __cplusplus
 }
 #endif

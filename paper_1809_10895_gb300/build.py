@@ -16,7 +16,8 @@ CSRC = os.path.join(HERE, "csrc")
 INCLUDE = os.path.join(ROOT, "include")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(BUILD, "librf.so")
-SOURCES = ["closure_assemble.cu", "pcg.cu", "rf_api.cu", "noalloc.cu", "ensemble.cu", "ensemble_api.cu", "mg.cu"]
+SOURCES = ["closure_assemble.cu", "pcg.cu", "rf_api.cu", "noalloc.cu", "ensemble.cu", "ensemble_api.cu", "mg.cu",
+           "nn.cu", "nn_api.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-Xcompiler", "-O2", "-Xptxas", "-v"]
 

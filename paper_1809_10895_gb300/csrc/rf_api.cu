@@ -13,6 +13,7 @@
 #include <vector>
 
 #include "mg.cuh"
+#include "nn.cuh"
 #include "rf.h"
 #include "rf_internal.cuh"
 
@@ -93,6 +94,11 @@ struct rf_ctx {
     cudaStream_t cap = nullptr;          // private capture stream
     cudaGraph_t picard_graph = nullptr, solve_graph = nullptr;
     cudaGraphExec_t picard_exec = nullptr, solve_exec = nullptr;
+
+    // learned warm start: each step's first attempt starts from the network's guess
+    rf_nn *ws_net = nullptr;
+    nn::WsScales ws_sc{};
+    long long ws_guesses = 0, ws_fallbacks = 0;
 
     bool closure_at_h = false;   // K[0], Can hold the closures at h (the accepted state)
     bool soils_set = false, has_state = false;
@@ -496,7 +502,16 @@ struct Attempt {
 
 // One Picard attempt at step size dt from the accepted state h (Sec. 2.2),
 // run on the device as one graph launch; one host synchronisation.
-rf_status attempt(rf_ctx *c, double dt, Attempt &A)
+// Feature values of the top flux and the step size (the scalar features).
+void ws_scalar_features(const rf_ctx *c, const nn::WsScales &sc, double t, double dt, float &q_feat, float &dt_feat)
+{
+    const BcSeries &top = c->bc[F_ZMAX];
+    const double q = (top.type == BC_FLUX && !top.v.empty()) ? series_at(top, t) : 0.0;
+    q_feat = (float)(q / sc.q_scale);
+    dt_feat = (float)std::log(dt / sc.t_scale);
+}
+
+rf_status attempt(rf_ctx *c, double dt, Attempt &A, bool guess)
 {
     if (!c->picard_exec) RF_TRY(build_picard_graph(c));
     fill_step_params(c, dt);
@@ -506,10 +521,21 @@ rf_status attempt(rf_ctx *c, double dt, Attempt &A)
     ctl.n_max = c->prm.n_max;
     CUDA_TRY(cudaMemcpyAsync(c->sp, c->sp_h, sizeof(StepParams), cudaMemcpyHostToDevice, c->stream));
     CUDA_TRY(cudaMemcpyAsync(c->ctl, c->ctl_h, sizeof(PicardCtl), cudaMemcpyHostToDevice, c->stream));
-    CUDA_TRY(cudaMemcpyAsync(c->hk, c->h, sizeof(double) * c->g.N, cudaMemcpyDeviceToDevice, c->stream));
-    if (!c->closure_at_h) {
+    if (guess) {
+        // first iterate from the network: hk = h + y out_scale dt, closures at hk
+        float q_feat, dt_feat;
+        ws_scalar_features(c, c->ws_sc, c->t, dt, q_feat, dt_feat);
+        RF_TRY(rf_nn_mesh_guess(c->ws_net, c->stream, c->g, c->flags, c->h, c->Ks, c->ws_sc, q_feat, dt_feat,
+                                c->ws_sc.out_scale * dt, c->hk));
         run_closure(c, c->hk, nullptr, c->theta_k, 0);
-        c->closure_at_h = true;
+        c->closure_at_h = false;
+        c->ws_guesses++;
+    } else {
+        CUDA_TRY(cudaMemcpyAsync(c->hk, c->h, sizeof(double) * c->g.N, cudaMemcpyDeviceToDevice, c->stream));
+        if (!c->closure_at_h) {
+            run_closure(c, c->hk, nullptr, c->theta_k, 0);
+            c->closure_at_h = true;
+        }
     }
     CUDA_TRY(cudaGraphLaunch(c->picard_exec, c->stream));
     CUDA_TRY(cudaMemcpyAsync(c->ctl_h, c->ctl, sizeof(PicardCtl), cudaMemcpyDeviceToHost, c->stream));
@@ -527,6 +553,7 @@ rf_status attempt(rf_ctx *c, double dt, Attempt &A)
     } else {
         A.status = ctl.fail ? RF_ERR_CG : RF_ERR_PICARD;
         c->closure_at_h = false;
+        if (guess) c->ws_fallbacks++;
     }
     return RF_OK;
 }
@@ -554,7 +581,8 @@ rf_status do_step(rf_ctx *c, double t_stop, rf_step_info *info)
         if (bp - c->t < dt) dt = bp - c->t;
         if (t_stop - c->t < dt) dt = t_stop - c->t;
         Attempt A;
-        rf_status st = attempt(c, dt, A);
+        // a rejected attempt from the guess falls back to the plain start
+        rf_status st = attempt(c, dt, A, c->ws_net != nullptr && rejected == 0);
         if (st) { c->dt_nom = dt_nom0; c->easy = easy0; return st; }
         cg_total += A.cg;
         if (A.converged) {
@@ -1012,6 +1040,61 @@ rf_status rf_solve(rf_ctx *c, double *d_x, int *iters)
     return sync(c);
 }
 
+static bool ws_scales_ok(const rf_ws_scales *sc)
+{
+    return sc && sc->h_scale > 0 && std::isfinite(sc->lnK_mean) && sc->lnK_std > 0 && sc->q_scale > 0 &&
+           sc->t_scale > 0 && std::isfinite(sc->out_scale) && std::isfinite(sc->h_scale) &&
+           std::isfinite(sc->lnK_std) && std::isfinite(sc->q_scale) && std::isfinite(sc->t_scale);
+}
+
+static nn::WsScales ws_scales_of(const rf_ws_scales *sc)
+{
+    return nn::WsScales{sc->h_scale, sc->lnK_mean, sc->lnK_std, sc->q_scale, sc->t_scale, sc->out_scale};
+}
+
+rf_status rf_ws_features(rf_ctx *c, const rf_ws_scales *sc, const double *d_h, double t, double dt, float *d_x)
+{
+    if (!c || !d_x || !ws_scales_ok(sc) || !(dt > 0) || !std::isfinite(t)) return fail(RF_ERR_ARG, "bad argument");
+    if ((reinterpret_cast<uintptr_t>(d_x) & 15u) != 0) return fail(RF_ERR_ARG, "d_x must be 16-byte aligned");
+    if (!c->soils_set || (!d_h && !c->has_state)) return fail(RF_ERR_STATE, "set soils and state first");
+    const nn::WsScales s = ws_scales_of(sc);
+    float q_feat, dt_feat;
+    ws_scalar_features(c, s, t, dt, q_feat, dt_feat);
+    nn::ws_features_f32(c->stream, c->g, c->flags, d_h ? d_h : c->h, c->Ks, s, q_feat, dt_feat, d_x);
+    CUDA_TRY(cudaGetLastError());
+    return RF_OK;
+}
+
+rf_status rf_ws_target(rf_ctx *c, const rf_ws_scales *sc, const double *d_h_old, double dt, float *d_target,
+                       float *d_mask)
+{
+    if (!c || !d_h_old || !d_target || !ws_scales_ok(sc) || !(dt > 0) || !(sc->out_scale != 0))
+        return fail(RF_ERR_ARG, "bad argument");
+    if (!c->has_state) return fail(RF_ERR_STATE, "no state");
+    nn::ws_target(c->stream, c->g, c->flags, c->h, d_h_old, 1.0 / (sc->out_scale * dt), d_target, d_mask);
+    CUDA_TRY(cudaGetLastError());
+    return RF_OK;
+}
+
+rf_status rf_ws_attach(rf_ctx *c, rf_nn *net, const rf_ws_scales *sc)
+{
+    if (!c) return fail(RF_ERR_ARG, "ctx is NULL");
+    if (net && !ws_scales_ok(sc)) return fail(RF_ERR_ARG, "invalid warm-start scales");
+    c->ws_net = net;
+    if (net) c->ws_sc = ws_scales_of(sc);
+    c->ws_guesses = 0;
+    c->ws_fallbacks = 0;
+    return RF_OK;
+}
+
+rf_status rf_ws_get_stats(rf_ctx *c, rf_ws_stats *out)
+{
+    if (!c || !out) return fail(RF_ERR_ARG, "NULL argument");
+    out->guesses = c->ws_guesses;
+    out->fallbacks = c->ws_fallbacks;
+    return RF_OK;
+}
+
 unsigned long long rf_launch_count(rf_ctx *c)
 {
     if (!c) return 0ULL;
@@ -1055,26 +1138,47 @@ rf_status rf_profile_kernel(rf_ctx *c, int kind, int reps, double *avg_ms, doubl
     run_assemble(c, c->hk, c->h, c->theta_k, c->theta_n);
     c->closure_at_h = false;
     // the timed solves start from x0 = 0 (r0 = b, never zero) with a zero
-    // tolerance, so every timed launch does its full work whatever the state
-    CUDA_TRY(cudaMemsetAsync(c->q, 0, sizeof(double) * g.N, s));
-    if (kind == RF_K_CG64_SPMV || kind == RF_K_CG64_UPDATE)
-        launch_cg64_init(s, nb, g, c->flags, c->q, c->x, c->b, c->Tx, c->Ty, c->Tz, c->diag, c->dinv, c->r, c->z,
-                         0.0, 1 << 30, c->partials, c->ticket, c->sc, nullptr, none);
-    if (kind >= RF_K_RESID64) {
-        launch_mixed_start(s, nb, g, c->q, c->x, c->sc, c->sc_in, nullptr, none);
-        launch_resid64(s, nb, g, c->flags, c->x, c->b, c->Tx, c->Ty, c->Tz, c->diag, c->dinv32, c->r32, c->z32,
-                       c->d32, 0.0, 1e-30, 1 << 30, 1 << 30, c->partials, c->ticket, c->sc, c->sc_in, none, none);
-    }
+    // tolerance and restart every 8 launches, so every timed launch does its
+    // full work on values that stay meaningful whatever the state
+    auto restart = [&]() -> rf_status {
+        CUDA_TRY(cudaMemsetAsync(c->q, 0, sizeof(double) * g.N, s));
+        if (kind == RF_K_CG64_SPMV || kind == RF_K_CG64_UPDATE)
+            launch_cg64_init(s, nb, g, c->flags, c->q, c->x, c->b, c->Tx, c->Ty, c->Tz, c->diag, c->dinv, c->r, c->z,
+                             0.0, 1 << 30, c->partials, c->ticket, c->sc, nullptr, none);
+        if (kind >= RF_K_RESID64) {
+            launch_mixed_start(s, nb, g, c->q, c->x, c->sc, c->sc_in, nullptr, none);
+            launch_resid64(s, nb, g, c->flags, c->x, c->b, c->Tx, c->Ty, c->Tz, c->diag, c->dinv32, c->r32, c->z32,
+                           c->d32, 0.0, 1e-30, 1 << 30, 1 << 30, c->partials, c->ticket, c->sc, c->sc_in, none, none);
+        }
+        // one untimed iteration, so the timed ones read the previous direction
+        if (kind == RF_K_CG64_SPMV || kind == RF_K_CG64_UPDATE) {
+            launch_cg64_spmv(s, nb, g, c->flags, c->z, c->p[1], c->p[0], c->q, c->Tx, c->Ty, c->Tz, c->diag,
+                             c->partials, c->ticket, c->sc);
+            launch_cg64_update(s, nb, g, c->x, c->r, c->z, c->p[0], c->q, c->dinv, c->partials, c->ticket, c->sc,
+                               none);
+        } else if (kind == RF_K_CG32_SPMV || kind == RF_K_CG32_UPDATE) {
+            launch_cg32_spmv(s, nb, g, c->z32, c->p32[1], c->p32[0], c->q32, c->K32, c->cb32, c->partials, c->ticket,
+                             c->sc_in);
+            launch_cg32_update(s, nb, g, c->d32, c->r32, c->z32, c->p32[0], c->q32, c->dinv32, c->partials,
+                               c->ticket, c->sc_in, none);
+        }
+        return RF_OK;
+    };
+    auto undone = [&]() {
+        cudaMemsetAsync(&c->sc->done, 0, sizeof(int), s);
+        cudaMemsetAsync(&c->sc_in->done, 0, sizeof(int), s);
+    };
     std::vector<cudaEvent_t> ev(2 * reps);
     for (auto &e : ev) CUDA_TRY(cudaEventCreate(&e));
     for (int i = 0; i < reps; i++) {
+        if (i % 8 == 0) RF_TRY(restart());
         double *pin = c->p[i & 1], *pout = c->p[(i + 1) & 1];
         float *qin = c->p32[i & 1], *qout = c->p32[(i + 1) & 1];
         // every timed launch does its full work: the solve is never marked
-        // finished (values may stop being meaningful; the traffic does not)
-        cudaMemsetAsync(&c->sc->done, 0, sizeof(int), s);
-        cudaMemsetAsync(&c->sc_in->done, 0, sizeof(int), s);
+        // finished before it
+        undone();
         auto timed = [&](auto &&launch) {
+            undone();
             cudaEventRecord(ev[2 * i], s);
             launch();
             cudaEventRecord(ev[2 * i + 1], s);

@@ -90,6 +90,19 @@ class rf_ens_stats(C.Structure):
                 ("closure_abs", C.c_double), ("nonlinear_defect_cum", C.c_double)]
 
 
+class rf_ws_scales(C.Structure):
+    _fields_ = [("h_scale", C.c_double), ("lnK_mean", C.c_double), ("lnK_std", C.c_double), ("q_scale", C.c_double),
+                ("t_scale", C.c_double), ("out_scale", C.c_double)]
+
+
+class rf_adam(C.Structure):
+    _fields_ = [("lr", C.c_float), ("beta1", C.c_float), ("beta2", C.c_float), ("eps", C.c_float)]
+
+
+class rf_ws_stats(C.Structure):
+    _fields_ = [("guesses", C.c_longlong), ("fallbacks", C.c_longlong)]
+
+
 # name -> (restype, argtypes): the functions declared in include/rf.h
 _VP, _DP, _U8P = C.c_void_p, C.POINTER(C.c_double), C.POINTER(C.c_uint8)
 SIGNATURES = {
@@ -125,8 +138,23 @@ SIGNATURES = {
     "rf_ens_tune": (C.c_int, [_VP, C.c_double, C.POINTER(C.c_int), _DP]),
     "rf_pcg_solve_noalloc": (C.c_int, [C.c_int, C.c_int, C.c_int, _VP, _VP, _VP, _VP, _VP, _VP, C.c_double,
                                        C.c_int, _VP, C.POINTER(C.c_int)]),
+    "rf_nn_create": (C.c_int, [_VP, C.POINTER(rf_allocator), C.POINTER(_VP)]),
+    "rf_nn_destroy": (None, [_VP]),
+    "rf_nn_set_params": (C.c_int, [_VP, _VP, C.c_longlong]),
+    "rf_nn_get_params": (C.c_int, [_VP, _VP, C.c_longlong]),
+    "rf_nn_forward": (C.c_int, [_VP, _VP, C.c_int, C.c_int, C.c_int, C.c_int, _VP]),
+    "rf_nn_loss_grad": (C.c_int, [_VP, _VP, _VP, _VP, C.c_int, C.c_int, C.c_int, C.c_int,
+                                  C.POINTER(C.c_float), _VP]),
+    "rf_nn_train_step": (C.c_int, [_VP, _VP, _VP, _VP, C.c_int, C.c_int, C.c_int, C.c_int, C.POINTER(rf_adam),
+                                   C.POINTER(C.c_float)]),
+    "rf_nn_launch_count": (C.c_longlong, [_VP]),
+    "rf_ws_features": (C.c_int, [_VP, C.POINTER(rf_ws_scales), _VP, C.c_double, C.c_double, _VP]),
+    "rf_ws_target": (C.c_int, [_VP, C.POINTER(rf_ws_scales), _VP, C.c_double, _VP, _VP]),
+    "rf_ws_attach": (C.c_int, [_VP, _VP, C.POINTER(rf_ws_scales)]),
+    "rf_ws_get_stats": (C.c_int, [_VP, C.POINTER(rf_ws_stats)]),
 }
 NOALLOC_MAX_CELLS = 65536
+NN_PARAMS = 225793
 COUNTER_KINDS = ("closure", "closure_picard", "assemble", "cg64_init", "cg64_spmv", "cg64_update", "apply64",
                  "mixed_start", "resid64", "cg32_spmv", "cg32_update", "add_correction", "mass_balance",
                  "storage", "accept")
@@ -359,6 +387,98 @@ class Solver:
         it = C.c_int(0)
         _check(load().rf_solve(self.ctx, C.c_void_p(x.data_ptr()), C.byref(it)), "rf_solve")
         return it.value
+
+    # -- learned warm start
+    def ws_features(self, scales: "rf_ws_scales", t: float, dt: float, out, h=None):
+        """Network features of state h (device, N doubles; None = current state) for a step dt
+        from time t into out (N x 4 float32, device)."""
+        _check(load().rf_ws_features(self.ctx, C.byref(scales), None if h is None else C.c_void_p(h.data_ptr()),
+                                     float(t), float(dt), C.c_void_p(out.data_ptr())), "rf_ws_features")
+
+    def ws_target(self, scales: "rf_ws_scales", h_old, dt: float, target, mask=None):
+        _check(load().rf_ws_target(self.ctx, C.byref(scales), C.c_void_p(h_old.data_ptr()), float(dt),
+                                   C.c_void_p(target.data_ptr()),
+                                   None if mask is None else C.c_void_p(mask.data_ptr())), "rf_ws_target")
+
+    def ws_attach(self, net: Optional["Network"], scales: Optional["rf_ws_scales"] = None):
+        self._ws_net = net   # keep the network alive while attached
+        _check(load().rf_ws_attach(self.ctx, None if net is None else net.handle,
+                                   None if scales is None else C.byref(scales)), "rf_ws_attach")
+
+    def ws_stats(self) -> dict:
+        st = rf_ws_stats()
+        _check(load().rf_ws_get_stats(self.ctx, C.byref(st)), "rf_ws_get_stats")
+        return {"guesses": st.guesses, "fallbacks": st.fallbacks}
+
+
+class Network:
+    """The warm-start network (BF16 3-D conv residual net) on the current device and torch stream."""
+
+    def __init__(self, stream=None, use_torch_allocator=True):
+        import torch
+        L = load()
+        self.device = torch.device("cuda", torch.cuda.current_device())
+        self.stream = stream if stream is not None else torch.cuda.current_stream()
+        self._allocator = TorchAllocator(self.device) if use_torch_allocator else None
+        h = _VP()
+        _check(L.rf_nn_create(C.c_void_p(self.stream.cuda_stream),
+                              C.byref(self._allocator.struct) if self._allocator else None, C.byref(h)),
+               "rf_nn_create")
+        self.handle = h
+
+    def close(self):
+        if getattr(self, "handle", None):
+            load().rf_nn_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def set_params(self, theta):
+        a = np.ascontiguousarray(theta, dtype=np.float32)
+        _check(load().rf_nn_set_params(self.handle, a.ctypes.data_as(_VP), a.size), "rf_nn_set_params")
+
+    def get_params(self) -> np.ndarray:
+        a = np.empty(NN_PARAMS, dtype=np.float32)
+        _check(load().rf_nn_get_params(self.handle, a.ctypes.data_as(_VP), a.size), "rf_nn_get_params")
+        return a
+
+    @staticmethod
+    def _dims(x):
+        B, D, H, W, c = x.shape
+        assert c == 4 and x.is_contiguous()
+        return B, D, H, W
+
+    def forward(self, x, y):
+        """x: (B, D, H, W, 4) float32 device tensor; y: (B, D, H, W) float32."""
+        B, D, H, W = self._dims(x)
+        _check(load().rf_nn_forward(self.handle, C.c_void_p(x.data_ptr()), B, D, H, W, C.c_void_p(y.data_ptr())),
+               "rf_nn_forward")
+
+    def loss_grad(self, x, target, mask=None, want_grad=True):
+        B, D, H, W = self._dims(x)
+        loss = C.c_float(0.0)
+        g = np.empty(NN_PARAMS, dtype=np.float32) if want_grad else None
+        _check(load().rf_nn_loss_grad(self.handle, C.c_void_p(x.data_ptr()), C.c_void_p(target.data_ptr()),
+                                      None if mask is None else C.c_void_p(mask.data_ptr()), B, D, H, W,
+                                      C.byref(loss), None if g is None else g.ctypes.data_as(_VP)),
+               "rf_nn_loss_grad")
+        return loss.value, g
+
+    def train_step(self, x, target, mask=None, lr=1e-3, beta1=0.9, beta2=0.999, eps=1e-8, want_loss=True):
+        B, D, H, W = self._dims(x)
+        opt = rf_adam(lr, beta1, beta2, eps)
+        loss = C.c_float(0.0)
+        _check(load().rf_nn_train_step(self.handle, C.c_void_p(x.data_ptr()), C.c_void_p(target.data_ptr()),
+                                       None if mask is None else C.c_void_p(mask.data_ptr()), B, D, H, W,
+                                       C.byref(opt), C.byref(loss) if want_loss else None), "rf_nn_train_step")
+        return loss.value if want_loss else None
+
+    def launch_count(self) -> int:
+        return int(load().rf_nn_launch_count(self.handle))
 
 
 class Ensemble:
