@@ -19,6 +19,8 @@
 // round trip per iteration; kernels of a finished solve return at once.
 #include <math.h>
 
+#include <algorithm>
+
 #include "cell_ops.cuh"
 #include "rf_internal.cuh"
 #include "rf_reduce.cuh"
@@ -28,6 +30,63 @@ namespace rf {
 #define GRID_STRIDE_LOOP(p)                                                                 \
     for (long long p = (long long)blockIdx.x * blockDim.x + threadIdx.x; p < g.N;           \
          p += (long long)gridDim.x * blockDim.x)
+
+// Tiled sweeps for the stencil kernels.  A block owns a TX x TY column tile
+// and a range of z planes and walks up through them: the x/y neighbours of a
+// plane come from shared memory (the plane plus a one-cell halo, double
+// buffered so each plane needs one barrier), the z neighbours from registers
+// (the planes below and above), and the plane above is loaded while the
+// current one is in use.  Blocks loop over (tile, z-range) items; the grid
+// never exceeds the reduction's block count.
+constexpr int TX = 32, TY = RED_THREADS / 32;
+constexpr int HALO = 2 * TY + 2 * TX;   // x- and y-halo cells of a plane (no corners)
+
+struct Tiles {
+    int ntx, nty, zc;       // tiles along x, y; planes per item
+    long long items;
+};
+
+static Tiles make_tiles(const Grid &g, int nblk)
+{
+    Tiles t;
+    t.ntx = (g.nx + TX - 1) / TX;
+    t.nty = (g.ny + TY - 1) / TY;
+    const long long tiles = (long long)t.ntx * t.nty;
+    const long long want_chunks = (nblk + tiles - 1) / tiles;
+    const int chunks = (int)std::min<long long>(std::max<long long>(want_chunks, 1), g.nz);
+    t.zc = (g.nz + chunks - 1) / chunks;
+    t.items = tiles * ((g.nz + t.zc - 1) / t.zc);
+    return t;
+}
+
+static int tile_blocks(const Tiles &t, int nblk) { return (int)std::min<long long>(t.items, nblk); }
+
+struct TileItem {
+    int i0, j0, k0, k1;
+};
+
+__device__ __forceinline__ TileItem tile_item(const Grid &g, const Tiles &t, long long item)
+{
+    const long long per_plane = (long long)t.ntx * t.nty;
+    const int chunk = (int)(item / per_plane);
+    const long long r = item - chunk * per_plane;
+    TileItem it;
+    it.j0 = (int)(r / t.ntx) * TY;
+    it.i0 = (int)(r % t.ntx) * TX;
+    it.k0 = chunk * t.zc;
+    it.k1 = min(g.nz, it.k0 + t.zc);
+    return it;
+}
+
+// Halo cell h (0 <= h < HALO) of a tile, as offsets (hx, hy) from (i0, j0):
+// -x column, +x column, -y row, +y row.
+__device__ __forceinline__ void halo_cell(int h, int &hx, int &hy)
+{
+    if (h < TY) { hx = -1; hy = h; }
+    else if (h < 2 * TY) { hx = TX; hy = h - TY; }
+    else if (h < 2 * TY + TX) { hx = h - 2 * TY; hy = -1; }
+    else { hx = h - 2 * TY - TX; hy = TY; }
+}
 
 // ---------------------------------------------------------------- FP64 PCG
 __global__ void __launch_bounds__(RED_THREADS)
@@ -69,31 +128,121 @@ k_cg64_init(Grid g, const uint8_t *__restrict__ flags, const double *__restrict_
         cg64_start_scalars(sc, v, tol, max_it, cond);
 }
 
+// One plane of the FP64 operator's face coefficients around a tile, staged by
+// the tiled FP64 kernels: Ty of rows j0-1 .. j0+TY-1 and Tx of the -x halo
+// column (the +x / +y / +z coefficients of a cell are its own).
+struct Faces64 {
+    double ty[2][TY + 1][TX];
+    double tx[2][TY];
+};
+
+// Stage the values v (own cell pc, halo via val) and face coefficients of
+// plane k; returns the cell's own coefficients (0 on inactive cells).
+template <class Val>
+__device__ __forceinline__ void stage64(const Grid &g, const TileItem &it, int k, int buf, int tx, int ty, int hx,
+                                        int hy, bool inside, long long c, const uint8_t *__restrict__ flags,
+                                        const double *__restrict__ Tx, const double *__restrict__ Ty,
+                                        const double *__restrict__ Tz, const double *__restrict__ diag, double pc,
+                                        Val val, double (&sP)[2][TY + 2][TX + 2], Faces64 &sF, bool &act,
+                                        double &dg, double &txp, double &typ, double &tzp)
+{
+    sP[buf][ty + 1][tx + 1] = pc;
+    act = inside && (flags[c] & FLAG_ACTIVE);
+    dg = txp = typ = tzp = 0.0;
+    if (act) {
+        dg = diag[c];
+        txp = Tx[c];
+        typ = Ty[c];
+        tzp = Tz[c];
+    }
+    sF.ty[buf][ty + 1][tx] = typ;
+    if (threadIdx.x < HALO) {
+        const int ii = it.i0 + hx, jj = it.j0 + hy;
+        const bool in = ii >= 0 && ii < g.nx && jj >= 0 && jj < g.ny;
+        const long long hc = ii + (long long)g.nx * jj + g.sxy * k;
+        const bool hact = in && (flags[hc] & FLAG_ACTIVE);
+        sP[buf][hy + 1][hx + 1] = hact ? val(hc) : 0.0;
+        if (hx == -1) sF.tx[buf][hy] = hact ? Tx[hc] : 0.0;
+        if (hy == -1) sF.ty[buf][0][hx] = hact ? Ty[hc] : 0.0;
+    }
+}
+
+// (A v)_P = diag_P v_P - sum_f T_f v_N with faces in the order -x +x -y +y -z +z.
+__device__ __forceinline__ double apply64_tile(const Grid &g, int i, int j, int k, int tx, int ty, int buf,
+                                               const double (&sP)[2][TY + 2][TX + 2], const Faces64 &sF,
+                                               double txm_lane, double dg, double txp, double typ, double tzm,
+                                               double tzp, double vm, double vc, double vn)
+{
+    const double txm = tx > 0 ? txm_lane : sF.tx[buf][ty];
+    double acc = dg * vc;
+    if (i > 0) acc -= txm * sP[buf][ty + 1][tx];
+    if (i < g.nx - 1) acc -= txp * sP[buf][ty + 1][tx + 2];
+    if (j > 0) acc -= sF.ty[buf][ty][tx] * sP[buf][ty][tx + 1];
+    if (j < g.ny - 1) acc -= typ * sP[buf][ty + 2][tx + 1];
+    if (k > 0) acc -= tzm * vm;
+    if (k < g.nz - 1) acc -= tzp * vn;
+    return acc;
+}
+
 __global__ void __launch_bounds__(RED_THREADS)
-k_cg64_spmv(Grid g, const uint8_t *__restrict__ flags, const double *__restrict__ z, const double *__restrict__ p_in,
-            double *__restrict__ p_out, double *__restrict__ q, const double *__restrict__ Tx,
-            const double *__restrict__ Ty, const double *__restrict__ Tz, const double *__restrict__ diag,
-            double *partials, unsigned int *ticket, CgScal *sc)
+k_cg64_spmv(Grid g, Tiles tw, const uint8_t *__restrict__ flags, const double *__restrict__ z,
+            const double *__restrict__ p_in, double *__restrict__ p_out, double *__restrict__ q,
+            const double *__restrict__ Tx, const double *__restrict__ Ty, const double *__restrict__ Tz,
+            const double *__restrict__ diag, double *partials, unsigned int *ticket, CgScal *sc)
 {
     count_launch(g, KK_CG64_SPMV);
     if (sc->done) return;
     count_work(g, KK_CG64_SPMV);
     const double beta = sc->beta;
     const bool first = sc->iter == 0;
-    auto get = [&](long long qq) { return first ? z[qq] : fma(beta, p_in[qq], z[qq]); };
+    auto val = [&](long long c) { return first ? z[c] : fma(beta, p_in[c], z[c]); };
+    // p = z + beta p_old on active cells of the grid, 0 elsewhere
+    auto pval = [&](int i, int j, int k) -> double {
+        if (i >= g.nx || j >= g.ny || k < 0 || k >= g.nz) return 0.0;
+        const long long c = i + (long long)g.nx * j + g.sxy * k;
+        return (flags[c] & FLAG_ACTIVE) ? val(c) : 0.0;
+    };
+    __shared__ double sP[2][TY + 2][TX + 2];
+    __shared__ Faces64 sF;
+    const int tx = threadIdx.x % TX, ty = threadIdx.x / TX;
+    int hx = 0, hy = 0;
+    if (threadIdx.x < HALO) halo_cell(threadIdx.x, hx, hy);
     double v[1] = {0.0};
-    GRID_STRIDE_LOOP(p)
-    {
-        if (!(flags[p] & FLAG_ACTIVE)) {
-            p_out[p] = 0.0;
-            q[p] = 0.0;
-            continue;
+    for (long long item = blockIdx.x; item < tw.items; item += gridDim.x) {
+        const TileItem it = tile_item(g, tw, item);
+        const int i = it.i0 + tx, j = it.j0 + ty;
+        const bool inside = i < g.nx && j < g.ny;
+        double pm = pval(i, j, it.k0 - 1), pc = pval(i, j, it.k0);
+        double tzm = 0.0;
+        if (inside && it.k0 > 0) {
+            const long long cm = i + (long long)g.nx * j + g.sxy * (it.k0 - 1);
+            tzm = (flags[cm] & FLAG_ACTIVE) ? Tz[cm] : 0.0;
         }
-        const double pp = get(p);
-        const double qp = apply64(g, p, Tx, Ty, Tz, diag, get);
-        p_out[p] = pp;
-        q[p] = qp;
-        v[0] += pp * qp;
+        for (int k = it.k0; k < it.k1; k++) {
+            const int buf = k & 1;
+            const long long c = i + (long long)g.nx * j + g.sxy * k;
+            bool act;
+            double dg, txp, typ, tzp;
+            stage64(g, it, k, buf, tx, ty, hx, hy, inside, c, flags, Tx, Ty, Tz, diag, pc, val, sP, sF, act, dg,
+                    txp, typ, tzp);
+            const double pn = pval(i, j, k + 1);
+            const double txm_lane = __shfl_up_sync(0xffffffffu, txp, 1);
+            __syncthreads();
+            if (act) {
+                const double acc = apply64_tile(g, i, j, k, tx, ty, buf, sP, sF, txm_lane, dg, txp, typ, tzm, tzp,
+                                                pm, pc, pn);
+                p_out[c] = pc;
+                q[c] = acc;
+                v[0] += pc * acc;
+            } else if (inside) {
+                p_out[c] = 0.0;
+                q[c] = 0.0;
+            }
+            tzm = tzp;
+            pm = pc;
+            pc = pn;
+        }
+        __syncthreads();
     }
     if (grid_reduce<OpSum, 1>(v, partials, ticket) && threadIdx.x == 0) {
         sc->pq = v[0];
@@ -187,14 +336,16 @@ k_mixed_start(Grid g, const double *__restrict__ x0, double *__restrict__ x, CgS
 }
 
 // Outer FP64 residual r = b - A x; seeds the inner FP32 solve A d = r with
-// d0 = 0 (so r32 = r, z32 = D^-1 r32).  Counts outer iterations and fails the
-// solve after outer_max_it residuals without convergence.
+// d0 = 0 (so r32 = r, z32 = D^-1 r32).  The residual is formed in FP64; its
+// norms (a stopping test and CG seeds) are summed from the FP32 residual in
+// FP32 within a block, in FP64 across blocks.  Counts outer iterations and
+// fails the solve after outer_max_it residuals without convergence.
 __global__ void __launch_bounds__(RED_THREADS)
-k_resid64(Grid g, const uint8_t *__restrict__ flags, const double *__restrict__ x, const double *__restrict__ b,
-          const double *__restrict__ Tx, const double *__restrict__ Ty, const double *__restrict__ Tz,
-          const double *__restrict__ diag, const float *__restrict__ dinv32, float *__restrict__ r32,
-          float *__restrict__ z32, float *__restrict__ d32, double tol, double tol_inner, int inner_max_it,
-          int outer_max_it, double *partials, unsigned int *ticket, CgScal *outer, CgScal *inner,
+k_resid64(Grid g, Tiles tw, const uint8_t *__restrict__ flags, const double *__restrict__ x,
+          const double *__restrict__ b, const double *__restrict__ Tx, const double *__restrict__ Ty,
+          const double *__restrict__ Tz, const double *__restrict__ diag, const float *__restrict__ dinv32,
+          float *__restrict__ r32, float *__restrict__ z32, float *__restrict__ d32, double tol, double tol_inner,
+          int inner_max_it, int outer_max_it, double *partials, unsigned int *ticket, CgScal *outer, CgScal *inner,
           CondSet cond_outer, CondSet cond_inner)
 {
     count_launch(g, KK_RESID64);
@@ -207,34 +358,74 @@ k_resid64(Grid g, const uint8_t *__restrict__ flags, const double *__restrict__ 
         return;
     }
     count_work(g, KK_RESID64);
-    double v[4] = {0.0, 0.0, 0.0, 0.0};   // r.r, b.b (FP64); r32.r32, r32.z32
-    GRID_STRIDE_LOOP(p)
-    {
-        d32[p] = 0.0f;
-        if (!(flags[p] & FLAG_ACTIVE)) {
-            r32[p] = 0.0f;
-            z32[p] = 0.0f;
-            continue;
+    auto val = [&](long long c) { return x[c]; };
+    auto xval = [&](int i, int j, int k) -> double {
+        if (i >= g.nx || j >= g.ny || k < 0 || k >= g.nz) return 0.0;
+        const long long c = i + (long long)g.nx * j + g.sxy * k;
+        return (flags[c] & FLAG_ACTIVE) ? x[c] : 0.0;
+    };
+    __shared__ double sP[2][TY + 2][TX + 2];
+    __shared__ Faces64 sF;
+    const int tx = threadIdx.x % TX, ty = threadIdx.x / TX;
+    int hx = 0, hy = 0;
+    if (threadIdx.x < HALO) halo_cell(threadIdx.x, hx, hy);
+    float a_rr = 0.0f, a_bb = 0.0f, a_rz = 0.0f;   // r32.r32, b.b, r32.z32
+    for (long long item = blockIdx.x; item < tw.items; item += gridDim.x) {
+        const TileItem it = tile_item(g, tw, item);
+        const int i = it.i0 + tx, j = it.j0 + ty;
+        const bool inside = i < g.nx && j < g.ny;
+        double xm = xval(i, j, it.k0 - 1), xc = xval(i, j, it.k0);
+        double tzm = 0.0;
+        if (inside && it.k0 > 0) {
+            const long long cm = i + (long long)g.nx * j + g.sxy * (it.k0 - 1);
+            tzm = (flags[cm] & FLAG_ACTIVE) ? Tz[cm] : 0.0;
         }
-        const double bp = b[p];
-        const double rp = bp - apply64(g, p, Tx, Ty, Tz, diag, [&](long long q) { return x[q]; });
-        const float rf = (float)rp;
-        const float zf = dinv32[p] * rf;
-        r32[p] = rf;
-        z32[p] = zf;
-        v[0] += rp * rp;
-        v[1] += bp * bp;
-        v[2] += (double)(rf * rf);
-        v[3] += (double)(rf * zf);
+        for (int k = it.k0; k < it.k1; k++) {
+            const int buf = k & 1;
+            const long long c = i + (long long)g.nx * j + g.sxy * k;
+            bool act;
+            double dg, txp, typ, tzp;
+            stage64(g, it, k, buf, tx, ty, hx, hy, inside, c, flags, Tx, Ty, Tz, diag, xc, val, sP, sF, act, dg,
+                    txp, typ, tzp);
+            const double xn = xval(i, j, k + 1);
+            const double bp = act ? b[c] : 0.0;
+            const float di = act ? dinv32[c] : 0.0f;
+            const double txm_lane = __shfl_up_sync(0xffffffffu, txp, 1);
+            __syncthreads();
+            if (act) {
+                const double rp = bp - apply64_tile(g, i, j, k, tx, ty, buf, sP, sF, txm_lane, dg, txp, typ, tzm,
+                                                    tzp, xm, xc, xn);
+                const float rf = (float)rp;
+                const float zf = di * rf;
+                const float bf = (float)bp;
+                r32[c] = rf;
+                z32[c] = zf;
+                d32[c] = 0.0f;
+                a_rr = fmaf(rf, rf, a_rr);
+                a_bb = fmaf(bf, bf, a_bb);
+                a_rz = fmaf(rf, zf, a_rz);
+            } else if (inside) {
+                r32[c] = 0.0f;
+                z32[c] = 0.0f;
+                d32[c] = 0.0f;
+            }
+            tzm = tzp;
+            xm = xc;
+            xc = xn;
+        }
+        __syncthreads();
     }
-    if (grid_reduce<OpSum, 4>(v, partials, ticket) && threadIdx.x == 0) {
+    float vf[3] = {a_rr, a_bb, a_rz};
+    double w[3];
+    if (grid_reduce_f32<3>(vf, w, partials, ticket) && threadIdx.x == 0) {
         outer->iter += 1;
+        const double v[4] = {w[0], w[1], w[0], w[2]};
         outer_residual_scalars(outer, inner, v, tol, tol_inner, inner_max_it, outer_max_it, cond_outer, cond_inner);
     }
 }
 
 __global__ void __launch_bounds__(RED_THREADS)
-k_cg32_spmv(Grid g, const float *__restrict__ z, const float *__restrict__ p_in, float *__restrict__ p_out,
+k_cg32_spmv(Grid g, Tiles tw, const float *__restrict__ z, const float *__restrict__ p_in, float *__restrict__ p_out,
             float *__restrict__ q, const float *__restrict__ K32, const float *__restrict__ cb32, double *partials,
             unsigned int *ticket, CgScal *sc)
 {
@@ -243,20 +434,68 @@ k_cg32_spmv(Grid g, const float *__restrict__ z, const float *__restrict__ p_in,
     count_work(g, KK_CG32_SPMV);
     const float beta = (float)sc->beta;
     const bool first = sc->iter == 0;
-    auto get = [&](long long qq) { return first ? z[qq] : fmaf(beta, p_in[qq], z[qq]); };
+    // (p, K) of a cell: p = z + beta p_old, K < 0 marks inactive / outside cells
+    auto load = [&](int i, int j, int k, float &pv, float &kv) {
+        pv = 0.0f;
+        kv = -1.0f;
+        if (i < 0 || i >= g.nx || j < 0 || j >= g.ny || k < 0 || k >= g.nz) return;
+        const long long c = i + (long long)g.nx * j + g.sxy * k;
+        kv = K32[c];
+        if (kv >= 0.0f) pv = first ? z[c] : fmaf(beta, p_in[c], z[c]);
+    };
+    __shared__ float sP[2][TY + 2][TX + 2], sK[2][TY + 2][TX + 2];
+    const int tx = threadIdx.x % TX, ty = threadIdx.x / TX;
+    int hx = 0, hy = 0;
+    if (threadIdx.x < HALO) halo_cell(threadIdx.x, hx, hy);
+    const float wx = g.w32[0] * 0.5f, wy = g.w32[1] * 0.5f, wz = g.w32[2] * 0.5f;
     float acc = 0.0f;
-    GRID_STRIDE_LOOP(p)
-    {
-        if (K32[p] < 0.0f) {
-            p_out[p] = 0.0f;
-            q[p] = 0.0f;
-            continue;
+    for (long long item = blockIdx.x; item < tw.items; item += gridDim.x) {
+        const TileItem it = tile_item(g, tw, item);
+        const int i = it.i0 + tx, j = it.j0 + ty;
+        const bool inside = i < g.nx && j < g.ny;
+        float pm, km, pc, kc;
+        load(i, j, it.k0 - 1, pm, km);
+        load(i, j, it.k0, pc, kc);
+        for (int k = it.k0; k < it.k1; k++) {
+            const int buf = k & 1;
+            const long long c = i + (long long)g.nx * j + g.sxy * k;
+            sP[buf][ty + 1][tx + 1] = pc;
+            sK[buf][ty + 1][tx + 1] = kc;
+            if (threadIdx.x < HALO) {
+                float hp, hk;
+                load(it.i0 + hx, it.j0 + hy, k, hp, hk);
+                sP[buf][hy + 1][hx + 1] = hp;
+                sK[buf][hy + 1][hx + 1] = hk;
+            }
+            float pn, kn;
+            load(i, j, k + 1, pn, kn);
+            const float cb = (inside && kc >= 0.0f) ? cb32[c] : 0.0f;
+            __syncthreads();
+            if (inside && kc >= 0.0f) {
+                // (A p)_P = cb_P p_P + sum_f w_f (K_P + K_N)/2 (p_P - p_N), faces -x +x -y +y -z +z
+                float qp = cb * pc;
+                auto face = [&](float KN, float vN, float w) {
+                    if (KN >= 0.0f) qp = fmaf(w * (kc + KN), pc - vN, qp);
+                };
+                face(sK[buf][ty + 1][tx], sP[buf][ty + 1][tx], wx);
+                face(sK[buf][ty + 1][tx + 2], sP[buf][ty + 1][tx + 2], wx);
+                face(sK[buf][ty][tx + 1], sP[buf][ty][tx + 1], wy);
+                face(sK[buf][ty + 2][tx + 1], sP[buf][ty + 2][tx + 1], wy);
+                face(km, pm, wz);
+                face(kn, pn, wz);
+                p_out[c] = pc;
+                q[c] = qp;
+                acc = fmaf(pc, qp, acc);
+            } else if (inside) {
+                p_out[c] = 0.0f;
+                q[c] = 0.0f;
+            }
+            pm = pc;
+            km = kc;
+            pc = pn;
+            kc = kn;
         }
-        const float pp = get(p);
-        const float qp = apply32(g, p, K32, cb32, get);
-        p_out[p] = pp;
-        q[p] = qp;
-        acc = fmaf(pp, qp, acc);
+        __syncthreads();
     }
     float vf[1] = {acc};
     double v[1];
@@ -352,7 +591,9 @@ void launch_cg64_spmv(cudaStream_t s, int nblk, const Grid &g, const uint8_t *fl
                       const double *p_in, double *p_out, double *q, const double *Tx, const double *Ty,
                       const double *Tz, const double *diag, double *partials, unsigned int *ticket, CgScal *sc)
 {
-    k_cg64_spmv<<<nblk, RED_THREADS, 0, s>>>(g, flags, z, p_in, p_out, q, Tx, Ty, Tz, diag, partials, ticket, sc);
+    const Tiles tw = make_tiles(g, nblk);
+    k_cg64_spmv<<<tile_blocks(tw, nblk), RED_THREADS, 0, s>>>(g, tw, flags, z, p_in, p_out, q, Tx, Ty, Tz, diag,
+                                                              partials, ticket, sc);
 }
 
 void launch_cg64_update(cudaStream_t s, int nblk, const Grid &g, double *x, double *r, double *z, const double *p,
@@ -380,16 +621,19 @@ void launch_resid64(cudaStream_t s, int nblk, const Grid &g, const uint8_t *flag
                     int outer_max_it, double *partials, unsigned int *ticket, CgScal *outer, CgScal *inner,
                     CondSet cond_outer, CondSet cond_inner)
 {
-    k_resid64<<<nblk, RED_THREADS, 0, s>>>(g, flags, x, b, Tx, Ty, Tz, diag, dinv32, r32, z32, d32, tol, tol_inner,
-                                           inner_max_it, outer_max_it, partials, ticket, outer, inner, cond_outer,
-                                           cond_inner);
+    const Tiles tw = make_tiles(g, nblk);
+    k_resid64<<<tile_blocks(tw, nblk), RED_THREADS, 0, s>>>(g, tw, flags, x, b, Tx, Ty, Tz, diag, dinv32, r32, z32,
+                                                            d32, tol, tol_inner, inner_max_it, outer_max_it,
+                                                            partials, ticket, outer, inner, cond_outer, cond_inner);
 }
 
 void launch_cg32_spmv(cudaStream_t s, int nblk, const Grid &g, const float *z, const float *p_in, float *p_out,
                       float *q, const float *K32, const float *cb32, double *partials, unsigned int *ticket,
                       CgScal *sc)
 {
-    k_cg32_spmv<<<nblk, RED_THREADS, 0, s>>>(g, z, p_in, p_out, q, K32, cb32, partials, ticket, sc);
+    const Tiles tw = make_tiles(g, nblk);
+    k_cg32_spmv<<<tile_blocks(tw, nblk), RED_THREADS, 0, s>>>(g, tw, z, p_in, p_out, q, K32, cb32, partials, ticket,
+                                                              sc);
 }
 
 void launch_cg32_update(cudaStream_t s, int nblk, const Grid &g, float *x, float *r, float *z, const float *p,
