@@ -24,6 +24,7 @@
 #include "cell_ops.cuh"
 #include "rf_internal.cuh"
 #include "rf_reduce.cuh"
+#include "tma.cuh"
 
 namespace rf {
 
@@ -43,23 +44,58 @@ constexpr int HALO = 2 * TY + 2 * TX;   // x- and y-halo cells of a plane (no co
 
 struct Tiles {
     int ntx, nty, zc;       // tiles along x, y; planes per item
+    int tx;                 // tile width in x
     long long items;
 };
 
 static Tiles make_tiles(const Grid &g, int nblk)
 {
+    if (g.cap > nblk) nblk = g.cap;
     Tiles t;
+    t.tx = TX;
     t.ntx = (g.nx + TX - 1) / TX;
     t.nty = (g.ny + TY - 1) / TY;
     const long long tiles = (long long)t.ntx * t.nty;
-    const long long want_chunks = (nblk + tiles - 1) / tiles;
+    // split z so that the items fill the grid in one wave when the tiles alone
+    // do not (every block then walks the same number of planes)
+    const long long want_chunks = nblk / tiles;
     const int chunks = (int)std::min<long long>(std::max<long long>(want_chunks, 1), g.nz);
     t.zc = (g.nz + chunks - 1) / chunks;
     t.items = tiles * ((g.nz + t.zc - 1) / t.zc);
     return t;
 }
 
-static int tile_blocks(const Tiles &t, int nblk) { return (int)std::min<long long>(t.items, nblk); }
+// Tiles with the z split that minimises (waves of `resident` blocks) x
+// (planes per item + the two extra planes an item reads); at most `cap` items
+// per wave are launched.
+static Tiles make_tiles_balanced(const Grid &g, int resident, int tile_x)
+{
+    Tiles t;
+    t.tx = tile_x;
+    t.ntx = (g.nx + tile_x - 1) / tile_x;
+    t.nty = (g.ny + TY - 1) / TY;
+    const long long tiles = (long long)t.ntx * t.nty;
+    long long best = -1;
+    int best_zc = g.nz;
+    for (int ch = 1; ch <= g.nz; ch++) {
+        const int zc = (g.nz + ch - 1) / ch;
+        const long long items = tiles * ((g.nz + zc - 1) / zc);
+        const long long waves = (items + resident - 1) / resident;
+        const long long cost = waves * (zc + 2);
+        if (best < 0 || cost < best) {
+            best = cost;
+            best_zc = zc;
+        }
+    }
+    t.zc = best_zc;
+    t.items = tiles * ((g.nz + t.zc - 1) / t.zc);
+    return t;
+}
+
+static int tile_blocks(const Tiles &t, const Grid &g, int nblk)
+{
+    return (int)std::min<long long>(t.items, g.cap > nblk ? g.cap : nblk);
+}
 
 struct TileItem {
     int i0, j0, k0, k1;
@@ -72,7 +108,7 @@ __device__ __forceinline__ TileItem tile_item(const Grid &g, const Tiles &t, lon
     const long long r = item - chunk * per_plane;
     TileItem it;
     it.j0 = (int)(r / t.ntx) * TY;
-    it.i0 = (int)(r % t.ntx) * TX;
+    it.i0 = (int)(r % t.ntx) * t.tx;
     it.k0 = chunk * t.zc;
     it.k1 = min(g.nz, it.k0 + t.zc);
     return it;
@@ -510,6 +546,186 @@ k_cg32_spmv(Grid g, Tiles tw, const float *__restrict__ z, const float *__restri
     }
 }
 
+// The FP32 stencil step with planes staged by TMA.  Per plane the block
+// copies four 72 x 10 boxes (z, p_old, K, cb) around its 64 x 8 tile into
+// shared memory with bulk tensor copies; each thread owns two x-adjacent
+// cells.  A ring of stages holds the planes below, at and above the current
+// one and the next ones in flight.  Warp 0 alone polls the copy's mbarrier
+// (bounded); the others meet it at the one barrier per plane and then
+// confirm the completed phase once.  When a plane arrives each thread forms
+// p = z + beta p_old (in place of z) for its own cells and one halo cell.  A
+// wait that runs out sets *fault, ends the solve and drains the copies in
+// flight.
+#ifndef RF_TMA_STAGES
+#define RF_TMA_STAGES 4
+#endif
+constexpr int TMA_WAIT_TRIES = 1 << 20;   // about a second of suspending polls
+constexpr int TMA_HALO = 2 * TY + 2 * TMA_TX;
+
+// TMA_STAGES = planes k-1, k, k+1 resident plus TMA_STAGES - 3 in flight.
+template <int TMA_STAGES>
+__global__ void __launch_bounds__(RED_THREADS)
+k_cg32_spmv_tma(Grid g, Tiles tw, const __grid_constant__ TmaMaps32 maps, int pin_sel, float *__restrict__ p_out,
+                float *__restrict__ q, double *partials, unsigned int *ticket, CgScal *sc, int *fault)
+{
+    static_assert(TMA_STAGES >= 4 && TMA_STAGES <= 8, "the ring needs planes k-1..k+1 plus one in flight");
+    count_launch(g, KK_CG32_SPMV);
+    if (sc->done) return;
+    count_work(g, KK_CG32_SPMV);
+    const float beta = (float)sc->beta;
+    const bool first = sc->iter == 0;
+    constexpr int SLOT = TMA_SLOT_BYTES / 4;
+    __shared__ __align__(128) float sbuf[TMA_STAGES][4][SLOT];   // z (then p), p_old, K, cb
+    __shared__ __align__(8) uint64_t bar[TMA_STAGES];
+    __shared__ int s_timeout;
+    const CUtensorMap *mp = pin_sel ? &maps.p1 : &maps.p0;
+    if (threadIdx.x == 0) {
+        for (int st = 0; st < TMA_STAGES; st++) mbar_init(&bar[st], 1);
+        mbar_init_fence();
+        s_timeout = 0;
+    }
+    __syncthreads();
+    const uint32_t tx_bytes = (first ? 3 : 4) * TMA_BOX_BYTES;
+    const int tx = threadIdx.x % 32, ty = threadIdx.x / 32;
+    const bool poller = threadIdx.x < 32;
+    const int idx = (ty + 1) * TMA_BX + 2 * tx + TMA_X0;   // even: the pair is one float2
+    int hidx = -1;                       // the x/y halo cell this thread converts
+    if (threadIdx.x < TMA_HALO) {
+        const int h = threadIdx.x;
+        int hx, hy;
+        if (h < TY) { hx = -1; hy = h; }
+        else if (h < 2 * TY) { hx = TMA_TX; hy = h - TY; }
+        else if (h < 2 * TY + TMA_TX) { hx = h - 2 * TY; hy = -1; }
+        else { hx = h - 2 * TY - TMA_TX; hy = TY; }
+        hidx = (hy + 1) * TMA_BX + hx + TMA_X0;
+    }
+    const float wx = g.w32[0] * 0.5f, wy = g.w32[1] * 0.5f, wz = g.w32[2] * 0.5f;
+    uint32_t phase = 0, pending = 0;   // per stage: parity of its next completion; copy in flight
+    float acc = 0.0f;
+    auto ld2 = [](const float *a, int e) { return *reinterpret_cast<const float2 *>(a + e); };
+    for (long long item = blockIdx.x; item < tw.items && !s_timeout; item += gridDim.x) {
+        const TileItem it = tile_item(g, tw, item);
+        const int i = it.i0 + 2 * tx, j = it.j0 + ty;      // first cell of the pair (nx is even)
+        const bool inside = i < g.nx && j < g.ny;
+        const bool fxm = i > 0, fxp = i + 2 < g.nx, fym = j > 0, fyp = j < g.ny - 1;
+        // plane kk = it.k0 - 1 + L goes to stage L % TMA_STAGES (stage
+        // indices advance incrementally); planes outside the grid are neither
+        // copied nor read
+        auto present = [&](int kk) { return kk >= 0 && kk < g.nz && kk <= it.k1; };
+        auto issue = [&](int kk, int st) {   // every thread tracks pending; thread 0 copies
+            if (!present(kk)) return;
+            pending |= 1u << st;
+            if (threadIdx.x == 0) {
+                mbar_expect_tx(&bar[st], tx_bytes);
+                const int x = it.i0 - TMA_X0, y = it.j0 - 1;
+                tma_load_3d(sbuf[st][0], &maps.z, &bar[st], x, y, kk);
+                if (!first) tma_load_3d(sbuf[st][1], mp, &bar[st], x, y, kk);
+                tma_load_3d(sbuf[st][2], &maps.K, &bar[st], x, y, kk);
+                tma_load_3d(sbuf[st][3], &maps.cb, &bar[st], x, y, kk);
+            }
+        };
+        // warp 0: poll stage st (bounded); false when the wait ran out
+        auto poll = [&](int st) -> bool {
+            if (!poller || !(pending & (1u << st))) return true;
+            return mbar_wait_bounded(&bar[st], (phase >> st) & 1u, TMA_WAIT_TRIES);
+        };
+        // after the barrier that follows a successful poll: confirm the phase
+        // (completes at once) and form p for the own cells and halo cell of plane kk
+        auto take = [&](int kk, int st) {
+            if (pending & (1u << st)) {
+                mbar_try_wait(&bar[st], (phase >> st) & 1u);
+                phase ^= 1u << st;
+                pending &= ~(1u << st);
+            }
+            if (!first && present(kk)) {
+                float *pz = sbuf[st][0];
+                const float *po = sbuf[st][1];
+                const float2 z2 = ld2(pz, idx), o2 = ld2(po, idx);
+                *reinterpret_cast<float2 *>(pz + idx) = make_float2(fmaf(beta, o2.x, z2.x), fmaf(beta, o2.y, z2.y));
+                if (hidx >= 0) pz[hidx] = fmaf(beta, po[hidx], pz[hidx]);
+                fence_proxy_async_smem();   // the stage is refilled by tensor copies later
+            }
+        };
+        auto next = [](int st) { return st + 1 == TMA_STAGES ? 0 : st + 1; };
+        for (int L = 0; L < TMA_STAGES - 1; L++) issue(it.k0 - 1 + L, L);
+        if (!(poll(0) && poll(1))) s_timeout = 1;
+        __syncthreads();
+        if (s_timeout) break;
+        take(it.k0 - 1, 0);
+        take(it.k0, 1);
+        // stages of planes k-1, k, k+1 and of plane k + TMA_STAGES - 2 (copied into the stage of k-2)
+        int s_m = 0, s_c = 1, s_p = 2, s_i = TMA_STAGES - 1;
+        long long c = i + (long long)g.nx * j + g.sxy * it.k0;
+        for (int k = it.k0; k < it.k1; k++, c += g.sxy) {
+            if (!poll(s_p)) s_timeout = 1;
+            __syncthreads();              // plane k+1 landed; plane k-2 is no longer read
+            if (s_timeout) break;
+            issue(k + TMA_STAGES - 2, s_i);
+            take(k + 1, s_p);
+            if (inside) {
+                const float *P0 = sbuf[s_c][0], *K0 = sbuf[s_c][2];
+                const float2 kc = ld2(K0, idx), pc = ld2(P0, idx), cb = ld2(sbuf[s_c][3], idx);
+                const float2 kym = ld2(K0, idx - TMA_BX), pym = ld2(P0, idx - TMA_BX);
+                const float2 kyp = ld2(K0, idx + TMA_BX), pyp = ld2(P0, idx + TMA_BX);
+                const float2 kzm = ld2(sbuf[s_m][2], idx), pzm = ld2(sbuf[s_m][0], idx);
+                const float2 kzp = ld2(sbuf[s_p][2], idx), pzp = ld2(sbuf[s_p][0], idx);
+                // (A p)_P = cb_P p_P + sum_f w_f (K_P + K_N)/2 (p_P - p_N), faces -x +x -y +y -z +z
+                auto cell = [&](float kP, float pP, float cbP, bool inxm, float kxm, float pxm, bool inxp, float kxp,
+                                float pxp, float kym_, float pym_, float kyp_, float pyp_, float kzm_, float pzm_,
+                                float kzp_, float pzp_, float &pout, float &qout) {
+                    if (!(kP >= 0.0f)) {
+                        pout = 0.0f;
+                        qout = 0.0f;
+                        return;
+                    }
+                    float qp = cbP * pP;
+                    auto face = [&](bool in, float KN, float vN, float w) {
+                        if (in && KN >= 0.0f) qp = fmaf(w * (kP + KN), pP - vN, qp);
+                    };
+                    face(inxm, kxm, pxm, wx);
+                    face(inxp, kxp, pxp, wx);
+                    face(fym, kym_, pym_, wy);
+                    face(fyp, kyp_, pyp_, wy);
+                    face(k > 0, kzm_, pzm_, wz);
+                    face(k < g.nz - 1, kzp_, pzp_, wz);
+                    pout = pP;
+                    qout = qp;
+                    acc = fmaf(pP, qp, acc);
+                };
+                float2 po, qo;
+                cell(kc.x, pc.x, cb.x, fxm, K0[idx - 1], P0[idx - 1], true, kc.y, pc.y, kym.x, pym.x, kyp.x, pyp.x,
+                     kzm.x, pzm.x, kzp.x, pzp.x, po.x, qo.x);
+                cell(kc.y, pc.y, cb.y, true, kc.x, pc.x, fxp, K0[idx + 2], P0[idx + 2], kym.y, pym.y, kyp.y, pyp.y,
+                     kzm.y, pzm.y, kzp.y, pzp.y, po.y, qo.y);
+                *reinterpret_cast<float2 *>(p_out + c) = po;
+                *reinterpret_cast<float2 *>(q + c) = qo;
+            }
+            s_m = s_c;
+            s_c = s_p;
+            s_p = next(s_p);
+            s_i = next(s_i);
+        }
+        __syncthreads();                  // the item's planes are no longer read
+    }
+    if (s_timeout) {
+        // drain the copies in flight (bounded), report, end the solve
+        for (int st = 0; st < TMA_STAGES; st++)
+            if (pending & (1u << st)) mbar_wait_bounded(&bar[st], (phase >> st) & 1u, TMA_WAIT_TRIES);
+        if (threadIdx.x == 0) atomicExch(fault, 1);
+    }
+    float vf[1] = {acc};
+    double v[1];
+    if (grid_reduce_f32<1>(vf, v, partials, ticket) && threadIdx.x == 0) {
+        sc->pq = v[0];
+        const double a = sc->rho / v[0];
+        if (!(v[0] > 0.0) || !isfinite(a) || __ldcg(fault)) {
+            sc->status = CG_NONFINITE;
+            sc->done = 1;
+        }
+        sc->alpha = a;
+    }
+}
+
 __global__ void __launch_bounds__(RED_THREADS)
 k_cg32_update(Grid g, float *__restrict__ x, float *__restrict__ r, float *__restrict__ z,
               const float *__restrict__ pd, const float *__restrict__ q, const float *__restrict__ dinv,
@@ -592,7 +808,7 @@ void launch_cg64_spmv(cudaStream_t s, int nblk, const Grid &g, const uint8_t *fl
                       const double *Tz, const double *diag, double *partials, unsigned int *ticket, CgScal *sc)
 {
     const Tiles tw = make_tiles(g, nblk);
-    k_cg64_spmv<<<tile_blocks(tw, nblk), RED_THREADS, 0, s>>>(g, tw, flags, z, p_in, p_out, q, Tx, Ty, Tz, diag,
+    k_cg64_spmv<<<tile_blocks(tw, g, nblk), RED_THREADS, 0, s>>>(g, tw, flags, z, p_in, p_out, q, Tx, Ty, Tz, diag,
                                                               partials, ticket, sc);
 }
 
@@ -622,17 +838,33 @@ void launch_resid64(cudaStream_t s, int nblk, const Grid &g, const uint8_t *flag
                     CondSet cond_outer, CondSet cond_inner)
 {
     const Tiles tw = make_tiles(g, nblk);
-    k_resid64<<<tile_blocks(tw, nblk), RED_THREADS, 0, s>>>(g, tw, flags, x, b, Tx, Ty, Tz, diag, dinv32, r32, z32,
+    k_resid64<<<tile_blocks(tw, g, nblk), RED_THREADS, 0, s>>>(g, tw, flags, x, b, Tx, Ty, Tz, diag, dinv32, r32, z32,
                                                             d32, tol, tol_inner, inner_max_it, outer_max_it,
                                                             partials, ticket, outer, inner, cond_outer, cond_inner);
 }
 
 void launch_cg32_spmv(cudaStream_t s, int nblk, const Grid &g, const float *z, const float *p_in, float *p_out,
                       float *q, const float *K32, const float *cb32, double *partials, unsigned int *ticket,
-                      CgScal *sc)
+                      CgScal *sc, const TmaMaps32 *tma, int *fault)
 {
     const Tiles tw = make_tiles(g, nblk);
-    k_cg32_spmv<<<tile_blocks(tw, nblk), RED_THREADS, 0, s>>>(g, tw, z, p_in, p_out, q, K32, cb32, partials, ticket,
+    if (tma && fault && z == tma->z_ptr && K32 == tma->K_ptr && cb32 == tma->cb_ptr &&
+        (p_in == tma->p_ptr[0] || p_in == tma->p_ptr[1]) && TY == 8) {
+        // one wave: as many items as blocks resident at this kernel's occupancy
+        static int occ = 0;
+        if (occ == 0 && (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_cg32_spmv_tma<RF_TMA_STAGES>,
+                                                                        RED_THREADS, 0) != cudaSuccess || occ < 1))
+            occ = 1;
+        int dev = 0, sms = 0;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+        const int resident = std::max(1, std::min(occ * sms, std::max(g.cap, nblk)));
+        const Tiles tt = make_tiles_balanced(g, resident, TMA_TX);
+        k_cg32_spmv_tma<RF_TMA_STAGES><<<(int)std::min<long long>(tt.items, resident), RED_THREADS, 0, s>>>(
+            g, tt, *tma, p_in == tma->p_ptr[1] ? 1 : 0, p_out, q, partials, ticket, sc, fault);
+        return;
+    }
+    k_cg32_spmv<<<tile_blocks(tw, g, nblk), RED_THREADS, 0, s>>>(g, tw, z, p_in, p_out, q, K32, cb32, partials, ticket,
                                                               sc);
 }
 
@@ -647,6 +879,40 @@ void launch_add_correction(cudaStream_t s, int nblk, const Grid &g, double *x, c
                            const CgScal *inner, CondSet cond_outer)
 {
     k_add_correction<<<nblk, RED_THREADS, 0, s>>>(g, x, d, outer, inner, cond_outer);
+}
+
+bool make_tma_maps32(int nx, int ny, int nz, const float *z, const float *p0, const float *p1, const float *K,
+                     const float *cb, TmaMaps32 *out)
+{
+    if (nx % 4 != 0 || nx < 4) return false;
+    for (const float *ptr : {z, p0, p1, K, cb})
+        if (!ptr || (reinterpret_cast<uintptr_t>(ptr) & 15u) != 0) return false;
+    void *fn = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &fn, 12000, cudaEnableDefault, &q) != cudaSuccess ||
+        q != cudaDriverEntryPointSuccess || !fn)
+        return false;
+    auto encode = reinterpret_cast<CUresult (*)(CUtensorMap *, CUtensorMapDataType, cuuint32_t, void *,
+                                                const cuuint64_t *, const cuuint64_t *, const cuuint32_t *,
+                                                const cuuint32_t *, CUtensorMapInterleave, CUtensorMapSwizzle,
+                                                CUtensorMapL2promotion, CUtensorMapFloatOOBfill)>(fn);
+    const cuuint64_t dims[3] = {(cuuint64_t)nx, (cuuint64_t)ny, (cuuint64_t)nz};
+    const cuuint64_t strides[2] = {(cuuint64_t)nx * 4, (cuuint64_t)nx * ny * 4};
+    const cuuint32_t box[3] = {TMA_BX, TMA_BY, 1};
+    const cuuint32_t estr[3] = {1, 1, 1};
+    auto one = [&](CUtensorMap *m, const float *ptr) {
+        return encode(m, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3, const_cast<float *>(ptr), dims, strides, box, estr,
+                      CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+                      CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+    };
+    if (!(one(&out->z, z) && one(&out->p0, p0) && one(&out->p1, p1) && one(&out->K, K) && one(&out->cb, cb)))
+        return false;
+    out->z_ptr = z;
+    out->p_ptr[0] = p0;
+    out->p_ptr[1] = p1;
+    out->K_ptr = K;
+    out->cb_ptr = cb;
+    return true;
 }
 
 }  // namespace rf

@@ -87,6 +87,10 @@ struct rf_ctx {
     PicardCtl *ctl_h = nullptr;
     unsigned long long *ctr_h = nullptr;
 
+    TmaMaps32 tma{};                     // tensor maps of the FP32 inner-solve arrays
+    bool tma_ok = false;
+    int *dev_fault = nullptr, *fault_h = nullptr;   // set by a device wait that ran out
+
     MgHierarchy mg;                      // multigrid levels (RF_PRECOND_MG)
     bool mg_alloc = false;
 
@@ -162,7 +166,10 @@ double next_breakpoint(const rf_ctx *c, double t)
 rf_status sync(rf_ctx *c)
 {
     CUDA_TRY(cudaGetLastError());
+    if (c->dev_fault) CUDA_TRY(cudaMemcpyAsync(c->fault_h, c->dev_fault, sizeof(int), cudaMemcpyDeviceToHost, c->stream));
     CUDA_TRY(cudaStreamSynchronize(c->stream));
+    if (c->dev_fault && *c->fault_h)
+        return fail(RF_ERR_DEVICE_TIMEOUT, "a device wait for staged data ran out (the solve was stopped)");
     return RF_OK;
 }
 
@@ -351,7 +358,8 @@ rf_status capture_solve(rf_ctx *c, cudaGraph_t top, cudaGraph_t parent, std::vec
     RF_TRY(cap_begin(c, bi, {}));
     for (int half = 0; half < 2; half++) {
         float *pin = c->p32[half], *pout = c->p32[half ^ 1];
-        launch_cg32_spmv(s, nb, g, c->z32, pin, pout, c->q32, c->K32, c->cb32, c->partials, c->ticket, c->sc_in);
+        launch_cg32_spmv(s, nb, g, c->z32, pin, pout, c->q32, c->K32, c->cb32, c->partials, c->ticket, c->sc_in,
+                         c->tma_ok ? &c->tma : nullptr, c->dev_fault);
         if (mg) {
             launch_cg32_update_mg(s, nb, g, c->d32, c->r32, pout, c->q32, c->dinv32, c->partials, c->ticket, c->sc_in);
             launch_mg_vcycle(s, nb, c->mg, c->K32, c->r32, c->z32, idone);
@@ -714,6 +722,7 @@ rf_status rf_mesh_create(const rf_mesh_desc *mesh, const rf_solver_params *param
     // grid: at most 8 resident blocks of 256 threads per SM
     const long long want = (N + RED_THREADS - 1) / RED_THREADS;
     c->nblk = (int)std::max(1LL, std::min(want, (long long)c->num_sms * 8));
+    g.cap = std::max(c->nblk, c->num_sms * 8);
 
     // flags: active bit + boundary faces (domain edge, or a z-face whose
     // neighbour is inactive); lateral faces touching an inactive cell are closed
@@ -744,9 +753,10 @@ rf_status rf_mesh_create(const rf_mesh_desc *mesh, const rf_solver_params *param
               alloc_n(c, c->p[1], N) && alloc_n(c, c->q, N) && alloc_n(c, c->K32, N) && alloc_n(c, c->cb32, N) &&
               alloc_n(c, c->dinv32, N) && alloc_n(c, c->r32, N) && alloc_n(c, c->z32, N) &&
               alloc_n(c, c->p32[0], N) && alloc_n(c, c->p32[1], N) && alloc_n(c, c->q32, N) &&
-              alloc_n(c, c->d32, N) && alloc_n(c, c->partials, (size_t)8 * c->nblk) && alloc_n(c, c->ticket, 64) &&
+              alloc_n(c, c->d32, N) && alloc_n(c, c->partials, (size_t)8 * g.cap) && alloc_n(c, c->ticket, 64) &&
               alloc_n(c, c->sc, 1) && alloc_n(c, c->sc_in, 1) && alloc_n(c, c->res, 1) && alloc_n(c, c->sp, 1) &&
-              alloc_n(c, c->ctl, 1) && alloc_n(c, c->ctr, 2 * KK_COUNT) && alloc_n(c, c->fftab, 1);
+              alloc_n(c, c->ctl, 1) && alloc_n(c, c->ctr, 2 * KK_COUNT) && alloc_n(c, c->fftab, 1) &&
+              alloc_n(c, c->dev_fault, 1);
     if (!ok) {
         rf_destroy(c);
         return fail(RF_ERR_NOMEM, "device allocation failed");
@@ -756,7 +766,8 @@ rf_status rf_mesh_create(const rf_mesh_desc *mesh, const rf_solver_params *param
         cudaMallocHost(&c->res_h, sizeof(StepResults)) != cudaSuccess ||
         cudaMallocHost(&c->sp_h, sizeof(StepParams)) != cudaSuccess ||
         cudaMallocHost(&c->ctl_h, sizeof(PicardCtl)) != cudaSuccess ||
-        cudaMallocHost(&c->ctr_h, 2 * KK_COUNT * sizeof(unsigned long long)) != cudaSuccess) {
+        cudaMallocHost(&c->ctr_h, 2 * KK_COUNT * sizeof(unsigned long long)) != cudaSuccess ||
+        cudaMallocHost(&c->fault_h, sizeof(int)) != cudaSuccess) {
         rf_destroy(c);
         return fail(RF_ERR_NOMEM, "pinned host allocation failed");
     }
@@ -773,6 +784,7 @@ rf_status rf_mesh_create(const rf_mesh_desc *mesh, const rf_solver_params *param
     if (e == cudaSuccess) e = cudaMemsetAsync(c->ticket, 0, 64 * sizeof(unsigned int), c->stream);
     if (e == cudaSuccess) e = cudaMemsetAsync(c->ctr, 0, 2 * KK_COUNT * sizeof(unsigned long long), c->stream);
     if (e == cudaSuccess) e = cudaMemsetAsync(c->ctl, 0, sizeof(PicardCtl), c->stream);
+    if (e == cudaSuccess) e = cudaMemsetAsync(c->dev_fault, 0, sizeof(int), c->stream);
     // vectors whose inactive entries must read as zero
     for (double *v : {c->p[0], c->p[1], c->q, c->r, c->z, c->h, c->hk, c->x})
         if (e == cudaSuccess) e = cudaMemsetAsync(v, 0, sizeof(double) * N, c->stream);
@@ -783,6 +795,9 @@ rf_status rf_mesh_create(const rf_mesh_desc *mesh, const rf_solver_params *param
         rf_destroy(c);
         return fail(RF_ERR_CUDA, std::string("initialisation: ") + cudaGetErrorString(e));
     }
+    // TMA plane staging for the FP32 stencil (grids with nx a multiple of 4)
+    c->tma_ok = make_tma_maps32(g.nx, g.ny, g.nz, c->z32, c->p32[0], c->p32[1], c->K32, c->cb32, &c->tma);
+    cudaGetLastError();
     *out = c;
     return RF_OK;
 }
@@ -797,6 +812,7 @@ void rf_destroy(rf_ctx *c)
         if (c->has_alloc) c->alloc.free(ptr, c->alloc.user);
         else cudaFree(ptr);
     }
+    if (c->fault_h) cudaFreeHost(c->fault_h);
     if (c->sc_h) cudaFreeHost(c->sc_h);
     if (c->sc_in_h) cudaFreeHost(c->sc_in_h);
     if (c->res_h) cudaFreeHost(c->res_h);
@@ -1158,7 +1174,7 @@ rf_status rf_profile_kernel(rf_ctx *c, int kind, int reps, double *avg_ms, doubl
                                none);
         } else if (kind == RF_K_CG32_SPMV || kind == RF_K_CG32_UPDATE) {
             launch_cg32_spmv(s, nb, g, c->z32, c->p32[1], c->p32[0], c->q32, c->K32, c->cb32, c->partials, c->ticket,
-                             c->sc_in);
+                             c->sc_in, c->tma_ok ? &c->tma : nullptr, c->dev_fault);
             launch_cg32_update(s, nb, g, c->d32, c->r32, c->z32, c->p32[0], c->q32, c->dinv32, c->partials,
                                c->ticket, c->sc_in, none);
         }
@@ -1214,10 +1230,10 @@ rf_status rf_profile_kernel(rf_ctx *c, int kind, int reps, double *avg_ms, doubl
         default:
             if (kind == RF_K_CG32_SPMV)
                 timed([&] { launch_cg32_spmv(s, nb, g, c->z32, qin, qout, c->q32, c->K32, c->cb32, c->partials,
-                                             c->ticket, c->sc_in); });
+                                             c->ticket, c->sc_in, c->tma_ok ? &c->tma : nullptr, c->dev_fault); });
             else
                 launch_cg32_spmv(s, nb, g, c->z32, qin, qout, c->q32, c->K32, c->cb32, c->partials, c->ticket,
-                                 c->sc_in);
+                                 c->sc_in, c->tma_ok ? &c->tma : nullptr, c->dev_fault);
             if (kind == RF_K_CG32_UPDATE)
                 timed([&] { launch_cg32_update(s, nb, g, c->d32, c->r32, c->z32, qout, c->q32, c->dinv32, c->partials,
                                                c->ticket, c->sc_in, none); });

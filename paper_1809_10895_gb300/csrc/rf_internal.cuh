@@ -6,6 +6,7 @@
 #include <stdint.h>
 
 #include "ff.cuh"
+#include "tma.cuh"
 
 namespace rf {
 
@@ -66,6 +67,7 @@ struct Grid {
     double hg[6];     // gravity: +A_z/2 on the top face, -A_z/2 on the bottom face, 0 lateral
     float w32[3];     // A/d per axis, FP32 (mixed-precision operator)
     FastDiv fx, fxy;  // division by nx and by nx*ny
+    int cap;          // most blocks a tiled stencil kernel launches (partials hold 8 values per block)
     const FFTables *tab;       // double-float exp/log tables (device)
     unsigned long long *ctr;   // per-kind counters: [2 kind] launches, [2 kind + 1] launches that did work
 };
@@ -303,7 +305,7 @@ void launch_resid64(cudaStream_t s, int nblk, const Grid &g, const uint8_t *flag
                     unsigned int *ticket, CgScal *outer, CgScal *inner, CondSet cond_outer, CondSet cond_inner);
 void launch_cg32_spmv(cudaStream_t s, int nblk, const Grid &g, const float *z, const float *p_in, float *p_out,
                       float *q, const float *K32, const float *cb32, double *partials, unsigned int *ticket,
-                      CgScal *sc);
+                      CgScal *sc, const TmaMaps32 *tma = nullptr, int *fault = nullptr);
 void launch_cg32_update(cudaStream_t s, int nblk, const Grid &g, float *x, float *r, float *z, const float *p,
                         const float *q, const float *dinv, double *partials, unsigned int *ticket, CgScal *sc,
                         CondSet cond);
