@@ -56,6 +56,13 @@ def parse():
     ap.add_argument("--no-pcg-hbm", action="store_true", help="skip the large-grid PCG kernel bandwidth leg")
     ap.add_argument("--no-ensemble", action="store_true", help="skip the batched-ensemble leg")
     ap.add_argument("--ensemble-window", type=float, default=600.0, help="simulated seconds of the ensemble leg")
+    ap.add_argument("--no-warmstart", action="store_true", help="skip the learned warm-start leg")
+    ap.add_argument("--ws-train-size", type=int, default=128, help="nx = ny of the training box (nz = 64)")
+    ap.add_argument("--ws-eval-size", type=int, default=256, help="nx = ny of the held-out boxes (nz = 64)")
+    ap.add_argument("--ws-eval-seeds", type=int, default=1, help="held-out seeds evaluated")
+    ap.add_argument("--ws-snapshots", type=int, default=48, help="training snapshots (accepted plain steps)")
+    ap.add_argument("--ws-train-steps", type=int, default=300, help="Adam steps (one full box per step)")
+    ap.add_argument("--ws-eval-hours", type=float, default=1.0, help="simulated hours of each held-out run")
     return ap.parse_args()
 
 
@@ -312,6 +319,13 @@ def native(args):
         e.close()
         del e
 
+    # ---- learned warm start: snapshots from the plain solver on one box,
+    # Adam training by the library's kernels, then held-out boxes run with and
+    # without the network's first Picard iterate (same tolerance, same EBATS)
+    wsl = None
+    if not args.no_warmstart:
+        wsl = warmstart_leg(args, rank, rf, W, peaks)
+
     # ---- end to end through host buffers
     e2e = None
     if not args.no_e2e:
@@ -359,6 +373,7 @@ def native(args):
             "e2e": e2e,
             "pcg_hbm": pcg_hbm,
             "ensemble": ens,
+            "warmstart": wsl,
         }
         if not args.no_baseline:
             line["cpu_baseline"] = cpu_baseline(case)
@@ -366,6 +381,138 @@ def native(args):
     if world > 1:
         import torch.distributed as dist
         dist.destroy_process_group()
+
+
+def warmstart_leg(args, rank, rf, W, peaks):
+    import numpy as np
+    import torch
+    from paper_1809_10895_gb300 import warmstart as WS
+
+    def ev():
+        return torch.cuda.Event(enable_timing=True)
+
+    n_tr, n_ev = args.ws_train_size, args.ws_eval_size
+    tc = W.heterogeneous_box(n_tr, n_tr, 64, seed=1000 + rank)
+    sc = WS.scales_for(tc)
+    s = rf.Solver.from_case(tc, precision="mixed")
+    pilot = WS.collect(s, tc, sc, 16)
+    sc.out_scale = WS.target_rms(pilot)
+    del pilot
+    s.close()
+    # snapshots spread over the first day (rain, then redistribution)
+    s = rf.Solver.from_case(tc, precision="mixed")
+    a, b = ev(), ev()
+    a.record(s.stream)
+    snaps = WS.collect(s, tc, sc, args.ws_snapshots, t_end=86400.0, stride=4)
+    b.record(s.stream)
+    torch.cuda.synchronize()
+    collect_ms = a.elapsed_time(b)
+    s.close()
+    net = rf.Network()
+    net.set_params(W.nn_init_params(7 + rank))
+    l0 = net.launch_count()
+    a, b = ev(), ev()
+    a.record(net.stream)
+    losses = WS.train(net, snaps, steps=args.ws_train_steps, batch=1, lr=2e-3, log_every=max(1, args.ws_train_steps // 6))
+    b.record(net.stream)
+    torch.cuda.synchronize()
+    train_ms = a.elapsed_time(b)
+    train_launches = net.launch_count() - l0
+    vox = tc.N
+    flop_fwd = 2.0 * 27 * (8 * 32 + 8 * 32 * 32 + 32 * 8) * vox   # padded channels, per forward
+    # forward (inference) kernel throughput on a held-out box
+    ec = W.heterogeneous_box(n_ev, n_ev, 64, seed=2000 + rank)
+    xf = torch.empty((1, 64, n_ev, n_ev, 4), dtype=torch.float32, device="cuda")
+    yf = torch.empty((1, 64, n_ev, n_ev), dtype=torch.float32, device="cuda")
+    se = rf.Solver.from_case(ec)
+    se.ws_features(sc, 0.0, 600.0, xf.view(-1, 4))
+    se.close()
+    for _ in range(2):
+        net.forward(xf, yf)
+    a, b = ev(), ev()
+    a.record(net.stream)
+    reps = 5
+    for _ in range(reps):
+        net.forward(xf, yf)
+    b.record(net.stream)
+    torch.cuda.synchronize()
+    fwd_ms = a.elapsed_time(b) / reps
+    fwd_flop = 2.0 * 27 * (8 * 32 + 8 * 32 * 32 + 32 * 8) * ec.N
+    bf16_peak = peaks.get("bf16_tflops")
+    runs = {}
+    t_eval = args.ws_eval_hours * 3600.0
+    max_diff = 0.0
+    for seed in range(args.ws_eval_seeds):
+        ec = W.heterogeneous_box(n_ev, n_ev, 64, seed=2000 + 97 * seed + rank)
+        states = {}
+        for prec in ("fp64", "mixed"):
+            for warm in (False, True):
+                key = f"{'warm' if warm else 'plain'}_{prec}"
+                s = rf.Solver.from_case(ec, precision=prec)
+                if warm:
+                    s.ws_attach(net, sc)
+                s.step()                            # graph capture, workspaces: outside the timing
+                h0 = torch.as_tensor(ec.h0, dtype=torch.float64, device="cuda")
+                s.set_state_device(h0, 0.0)
+                if warm:
+                    s.ws_attach(net, sc)            # counters from zero
+                a, b = ev(), ev()
+                a.record(s.stream)
+                steps = picard = rej = 0
+                t = 0.0
+                while t < t_eval * (1 - 1e-12):
+                    info = s.step()
+                    t = info.t
+                    steps += 1
+                    picard += info.picard
+                    rej += info.rejected
+                b.record(s.stream)
+                torch.cuda.synchronize()
+                r = runs.setdefault(key, {"steps": 0, "picard": 0, "rejected": 0, "ms": 0.0, "fallbacks": 0,
+                                          "guesses": 0})
+                r["steps"] += steps
+                r["picard"] += picard
+                r["rejected"] += rej
+                r["ms"] += a.elapsed_time(b)
+                if warm:
+                    st = s.ws_stats()
+                    r["fallbacks"] += st["fallbacks"]
+                    r["guesses"] += st["guesses"]
+                states[key] = s.get_state()[0]
+                s.close()
+        for prec in ("fp64", "mixed"):
+            max_diff = max(max_diff, float(np.max(np.abs(states[f"warm_{prec}"] - states[f"plain_{prec}"]))))
+    # equal-accuracy check at an identical step sequence (fixed dt = 300 s):
+    # the warm-started and plain solutions differ only within the Picard tolerance
+    ec = W.heterogeneous_box(n_ev, n_ev, 64, seed=2000 + rank)
+    fixed = {}
+    for warm in (False, True):
+        s = rf.Solver.from_case(ec, precision="mixed", dt0=300.0, f_grow=1.0)
+        if warm:
+            s.ws_attach(net, sc)
+        its = [s.step().picard for _ in range(12)]
+        fixed["warm" if warm else "plain"] = (s.get_state()[0], sum(its))
+        s.close()
+    fixed_diff = float(np.max(np.abs(fixed["warm"][0] - fixed["plain"][0])))
+    for r in runs.values():
+        r["picard_per_step"] = r["picard"] / max(r["steps"], 1)
+        r["time_to_solution_s"] = r["ms"] / 1e3
+        if r["guesses"]:
+            r["fallback_rate"] = r["fallbacks"] / r["guesses"]
+    return {
+        "train_workload": f"heterogeneous_box_{n_tr}x{n_tr}x64", "eval_workload": f"heterogeneous_box_{n_ev}x{n_ev}x64",
+        "eval_seeds": args.ws_eval_seeds, "eval_window_s": t_eval, "snapshots": len(snaps),
+        "snapshot_collect_ms": collect_ms, "train_steps": args.ws_train_steps, "train_ms": train_ms,
+        "train_voxels_per_s": args.ws_train_steps * vox / (train_ms / 1e3),
+        "train_tflops": 3 * flop_fwd * args.ws_train_steps / (train_ms / 1e3) / 1e12,
+        "train_kernel_launches": train_launches, "loss_log": losses,
+        "forward_ms": fwd_ms, "forward_tflops": fwd_flop / (fwd_ms / 1e3) / 1e12,
+        "forward_frac_of_bf16_peak": (fwd_flop / (fwd_ms / 1e3) / 1e12 / bf16_peak) if bf16_peak else None,
+        "runs": runs, "max_abs_h_diff_warm_vs_plain_ebats_m": max_diff,
+        "fixed_dt_check": {"dt_s": 300.0, "steps": 12, "max_abs_h_diff_m": fixed_diff,
+                           "picard_plain": fixed["plain"][1], "picard_warm": fixed["warm"][1]},
+        "speedup_warm_mixed_vs_plain_fp64": runs["plain_fp64"]["ms"] / runs["warm_mixed"]["ms"],
+    }
 
 
 # ---------------------------------------------------------- reference arm

@@ -1,0 +1,76 @@
+"""Event-timed launches of single solver / network kernels on a workload
+(``rf_profile_kernel`` for the solver kernels, ``rf_nn_forward`` for the
+network), for profiling one kernel at a time.
+
+    python -m paper_1809_10895_gb300.kernel_timing box --kinds assemble,resid64
+    python -m paper_1809_10895_gb300.kernel_timing watershed --nx 512 --ny 256 --kinds cg32_spmv
+    python -m paper_1809_10895_gb300.kernel_timing network --nx 128 --ny 128 --nz 64
+
+Prints one JSON line: per kind the mean launch time and the algorithmic bytes
+per launch (solver kernels) or the forward time and TFLOP/s (network).
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import sys
+
+sys.path.insert(0, os.path.dirname(os.path.dirname(os.path.abspath(__file__))))
+
+
+def main(argv=None):
+    ap = argparse.ArgumentParser()
+    ap.add_argument("workload", choices=["box", "watershed", "network"])
+    ap.add_argument("--nx", type=int, default=None)
+    ap.add_argument("--ny", type=int, default=None)
+    ap.add_argument("--nz", type=int, default=64)
+    ap.add_argument("--kinds", default="assemble,closure,resid64,cg32_spmv,cg32_update")
+    ap.add_argument("--steps", type=int, default=5, help="accepted steps before timing (box)")
+    ap.add_argument("--reps", type=int, default=24)
+    ap.add_argument("--precision", default="mixed")
+    a = ap.parse_args(argv)
+
+    import torch
+    from paper_1809_10895_gb300 import build, rf
+    from paper_1809_10895_gb300 import workloads as W
+    build.build()
+    rf.load()
+    torch.cuda.set_device(0)
+    out = {"workload": a.workload}
+    if a.workload == "network":
+        nx, ny = a.nx or 128, a.ny or 128
+        shape = (1, a.nz, ny, nx)
+        x = torch.randn(shape + (4,), device="cuda", generator=torch.Generator(device="cuda").manual_seed(0))
+        y = torch.empty(shape, device="cuda")
+        net = rf.Network()
+        net.set_params(W.nn_init_params(1))
+        for _ in range(2):
+            net.forward(x, y)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(net.stream)
+        for _ in range(a.reps):
+            net.forward(x, y)
+        e1.record(net.stream)
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1) / a.reps
+        flop = 2.0 * 27 * (8 * 32 + 8 * 32 * 32 + 32 * 8) * x[..., 0].numel()
+        out.update(shape=list(shape), forward_ms=ms, tflops=flop / ms / 1e9)
+    else:
+        if a.workload == "box":
+            case = W.heterogeneous_box(a.nx or 128, a.ny or 128, a.nz, seed=0)
+        else:
+            case = W.watershed(a.nx or 512, a.ny or 512, a.nz, seed=0, hours=24)
+        s = rf.Solver.from_case(case, precision=a.precision)
+        if a.workload == "box":
+            for _ in range(a.steps):
+                s.step()
+        out.update(cells=case.N, active=case.n_active(), kernels={})
+        for k in a.kinds.split(","):
+            ms, by = s.profile_kernel(k, reps=a.reps)
+            out["kernels"][k] = {"us": ms * 1e3, "MB": by / 1e6, "GBps": by / ms / 1e6}
+    print(json.dumps(out))
+
+
+if __name__ == "__main__":
+    main()
