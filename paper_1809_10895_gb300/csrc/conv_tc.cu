@@ -1,0 +1,386 @@
+// conv_tc.cu -- the 32 -> 32 channel 3x3x3 convolution of the warm-start
+// network on the 5th-generation tensor cores: tcgen05.mma with operands in
+// shared memory (staged by TMA) and FP32 accumulators in tensor memory.
+//
+// Implicit GEMM over a tile of 32 x 6 x 2 output voxels (x, y, z).  The input
+// tile with its one-voxel halo (34 x 8 x 4 voxels) is copied by four bulk
+// tensor copies, one per group of 8 channels; each copy lands as a "plane" of
+// 16-byte rows in halo-linear voxel order hl = (z (H+2) + y) (W+2) + x, which
+// is the K-major, no-swizzle operand layout (core matrices of 8 rows x 16
+// bytes).  For a filter tap (dz, dy, dx) the A operand of GEMM rows hl is the
+// same plane read from hl + off(tap), off = (dz (Ty+2) + dy) (Tx+2) + dx, so
+// every tap is a shifted descriptor of the same shared-memory tile.  Output
+// rows hl run over the tile's interior span in four blocks of M = 128;
+// rows on the halo ring are computed and discarded.  N = 32 output channels,
+// K = 16 per instruction (two 8-channel planes), 27 taps x 2 = 54 MMAs per
+// row block.  The weights (32 x 864) sit in shared memory for the whole
+// kernel in the same layout.
+//
+// Warp roles (persistent, one CTA per SM): warp 5 lane 0 issues the tensor
+// copies (two input stages), warp 4 lane 0 the MMAs (two accumulator stages
+// of 4 x 32 TMEM columns), warps 0-3 the epilogue (tcgen05.ld of one TMEM lane
+// = one voxel's 32 channels per thread; bias, residual, ReLU; BF16 / FP32
+// stores).  Every mbarrier wait is bounded: a wait that runs out raises the
+// CTA's abort flag and the device fault flag, every role leaves its loop,
+// and TMEM is freed before the kernel returns.
+#include <cuda.h>
+#include <cuda_bf16.h>
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "nn.cuh"
+#include "tma.cuh"
+
+namespace rf {
+namespace nn {
+
+namespace {
+
+constexpr int TC_TX = 32, TC_TY = 6, TC_TZ = 2;                      // output tile
+constexpr int TC_HX = TC_TX + 2, TC_HY = TC_TY + 2, TC_HZ = TC_TZ + 2;   // halo box
+constexpr int TC_HALO = TC_HX * TC_HY * TC_HZ;                           // 1088 voxels
+constexpr int TC_ROW0 = (TC_HY + 1) * TC_HX + 1;                         // first interior hl (307)
+constexpr int TC_OFFMAX = TC_HY * TC_HX + TC_HX + 1;                     // largest |tap offset| (307)
+constexpr int TC_RB = 4;                                                 // row blocks of 128
+constexpr int TC_PLANE_ROWS = 1152;   // >= TC_ROW0 + 128 TC_RB + TC_OFFMAX - 1 (rows past 1088 feed discarded outputs)
+constexpr int TC_PLANE_BYTES = TC_PLANE_ROWS * 16;                       // 18 432
+constexpr int TC_A_BYTES = 4 * TC_PLANE_BYTES;                           // 73 728 per stage
+constexpr int TC_BOX_BYTES = TC_HALO * 16;                               // 17 408 per plane copy
+constexpr int TC_KP = 27 * 32;                                           // 864
+constexpr int TC_B_BYTES = (TC_KP / 8) * 32 * 16;                        // 55 296
+constexpr int TC_SMEM = 2 * TC_A_BYTES + TC_B_BYTES + 1024;              // + alignment slack
+constexpr int TC_THREADS = 192;
+constexpr int TC_TMEM_COLS = 256;                                        // 2 stages x 4 blocks x 32
+constexpr int TC_WAIT_TRIES = 1 << 20;
+
+static_assert(TC_ROW0 + 128 * TC_RB - 1 + TC_OFFMAX < TC_PLANE_ROWS, "plane rows cover every shifted read");
+static_assert(TC_ROW0 + 128 * TC_RB - 1 >= (TC_TZ * TC_HY + TC_TY) * TC_HX + TC_TX, "row blocks cover the interior");
+static_assert(TC_PLANE_BYTES % 128 == 0 && TC_A_BYTES % 1024 == 0, "TMA destinations 128-byte aligned");
+
+struct TcParams {
+    int B, D, H, W;
+    int ntx, nty, ntz;       // tiles along x, y, z
+    long long tiles;
+};
+
+__device__ __forceinline__ uint64_t smem_desc(uint32_t addr, uint32_t lbo, uint32_t sbo)
+{
+    // K-major, no swizzle: start, leading (K-direction core-matrix) and stride
+    // (8-row group) byte offsets >> 4, descriptor version 1 at bit 46
+    return (uint64_t)((addr & 0x3FFFFu) >> 4) | ((uint64_t)(lbo >> 4) << 16) | ((uint64_t)(sbo >> 4) << 32) |
+           (1ull << 46);
+}
+
+// kind::f16 instruction descriptor: D FP32, A and B BF16, both K-major,
+// N = 32, M = 128.
+constexpr uint32_t TC_IDESC = (1u << 4) | (1u << 7) | (1u << 10) | ((32u >> 3) << 17) | ((128u >> 4) << 24);
+
+__device__ __forceinline__ void tc_mma(uint32_t d_tmem, uint64_t adesc, uint64_t bdesc, uint32_t accum)
+{
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "setp.ne.b32 p, %4, 0;\n\t"
+        "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}"
+        ::"r"(d_tmem), "l"(adesc), "l"(bdesc), "r"(TC_IDESC), "r"(accum)
+        : "memory");
+}
+
+__device__ __forceinline__ void tc_commit(uint64_t *bar)
+{
+    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(smem_addr(bar))
+                 : "memory");
+}
+
+__device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
+__device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
+
+__device__ __forceinline__ void mbar_arrive(uint64_t *bar)
+{
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_addr(bar)) : "memory");
+}
+
+// 32 consecutive TMEM columns of this thread's lane.
+__device__ __forceinline__ void tc_ld32(uint32_t taddr, float (&v)[32])
+{
+    uint32_t r[32];
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,"
+        "%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
+        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+          "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15]),
+          "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]),
+          "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
+        : "r"(taddr));
+    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+    for (int i = 0; i < 32; i++) v[i] = __uint_as_float(r[i]);
+}
+
+// Bounded wait that also gives up when another role raised the abort flag.
+__device__ __forceinline__ bool wait_or_abort(uint64_t *bar, uint32_t parity, volatile int *abort_flag)
+{
+    for (int t = 0; t < TC_WAIT_TRIES; t++) {
+        if (mbar_try_wait_sleep(bar, parity, 1000u)) return true;
+        if (*abort_flag) return false;
+    }
+    *abort_flag = 1;
+    return false;
+}
+
+__device__ __forceinline__ void tile_origin(const TcParams &p, long long tile, int &b, int &z0, int &y0, int &x0)
+{
+    long long r = tile;
+    const int tx = (int)(r % p.ntx);
+    r /= p.ntx;
+    const int ty = (int)(r % p.nty);
+    r /= p.nty;
+    const int tz = (int)(r % p.ntz);
+    b = (int)(r / p.ntz);
+    x0 = tx * TC_TX;
+    y0 = ty * TC_TY;
+    z0 = tz * TC_TZ;
+}
+
+}  // namespace
+
+__global__ void __launch_bounds__(TC_THREADS, 1)
+k_conv3d_tc(TcParams p, const __grid_constant__ CUtensorMap in_map, const __nv_bfloat16 *__restrict__ Wb,
+            const float *__restrict__ bias, const __nv_bfloat16 *__restrict__ res, __nv_bfloat16 *__restrict__ out_b,
+            float *__restrict__ out_f, int relu, int *fault)
+{
+    extern __shared__ unsigned char smem_raw[];
+    unsigned char *smem = reinterpret_cast<unsigned char *>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
+    unsigned char *sA = smem;                       // 2 stages x 4 planes
+    unsigned char *sB = smem + 2 * TC_A_BYTES;      // weights, [k/8][n][8 k]
+    __shared__ __align__(8) uint64_t full_bar[2], free_bar[2], tfull_bar[2], tempty_bar[2];
+    __shared__ uint32_t s_tmem;
+    __shared__ int s_abort;
+    // tiles whose copies were issued / consumed, whose MMAs were committed /
+    // drained by the epilogue (for the drain after an abort)
+    __shared__ int s_issued, s_consumed, s_committed, s_drained;
+    const int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
+
+    // weights into shared memory (generic stores, then made visible to the async proxy)
+    for (int e = threadIdx.x; e < (TC_KP / 8) * 32; e += TC_THREADS) {
+        const int n = e % 32, kg = e / 32;
+        const uint4 w = *reinterpret_cast<const uint4 *>(Wb + (size_t)n * TC_KP + kg * 8);
+        *reinterpret_cast<uint4 *>(sB + (size_t)(kg * 32 + n) * 16) = w;
+    }
+    fence_proxy_async_smem();
+    if (threadIdx.x == 0) {
+        for (int i = 0; i < 2; i++) {
+            mbar_init(&full_bar[i], 1);
+            mbar_init(&free_bar[i], 1);
+            mbar_init(&tfull_bar[i], 1);
+            mbar_init(&tempty_bar[i], 128);
+        }
+        mbar_init_fence();
+        s_abort = 0;
+        s_issued = s_consumed = s_committed = s_drained = 0;
+    }
+    if (warp == 4) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_addr(&s_tmem)),
+                     "r"(TC_TMEM_COLS)
+                     : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    }
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tmem = s_tmem;
+    volatile int *abort_flag = &s_abort;
+
+    if (warp == 5) {
+        // ---------------- producer: halo tiles by tensor copies
+        if (lane == 0) {
+            int i = 0;
+            for (long long tile = blockIdx.x; tile < p.tiles; tile += gridDim.x, i++) {
+                const int s = i & 1;
+                if (i >= 2 && !wait_or_abort(&free_bar[s], ((i >> 1) - 1) & 1, abort_flag)) break;
+                int b, z0, y0, x0;
+                tile_origin(p, tile, b, z0, y0, x0);
+                mbar_expect_tx(&full_bar[s], 4 * TC_BOX_BYTES);
+                unsigned char *dst = sA + s * TC_A_BYTES;
+                for (int cg = 0; cg < 4; cg++) {
+                    asm volatile(
+                        "cp.async.bulk.tensor.5d.shared::cluster.global.mbarrier::complete_tx::bytes"
+                        " [%0], [%1, {%3, %4, %5, %6, %7}], [%2];"
+                        ::"r"(smem_addr(dst + cg * TC_PLANE_BYTES)), "l"(reinterpret_cast<uint64_t>(&in_map)),
+                          "r"(smem_addr(&full_bar[s])), "r"(cg * 8), "r"(x0 - 1), "r"(y0 - 1), "r"(z0 - 1), "r"(b)
+                        : "memory");
+                }
+                s_issued = i + 1;
+            }
+        }
+    } else if (warp == 4) {
+        // ---------------- MMA issuer
+        if (lane == 0) {
+            int i = 0;
+            for (long long tile = blockIdx.x; tile < p.tiles; tile += gridDim.x, i++) {
+                const int s = i & 1;
+                if (!wait_or_abort(&full_bar[s], (i >> 1) & 1, abort_flag)) break;
+                s_consumed = i + 1;
+                if (i >= 2 && !wait_or_abort(&tempty_bar[s], ((i >> 1) - 1) & 1, abort_flag)) break;
+                tc_fence_after();
+                const uint32_t a_base = smem_addr(sA + s * TC_A_BYTES);
+                const uint32_t b_base = smem_addr(sB);
+                for (int rb = 0; rb < TC_RB; rb++) {
+                    const uint32_t d = tmem + (uint32_t)(s * 128 + rb * 32);
+                    const int r0 = TC_ROW0 + 128 * rb;
+                    for (int tap = 0; tap < 27; tap++) {
+                        const int dz = tap / 9 - 1, dy = (tap / 3) % 3 - 1, dx = tap % 3 - 1;
+                        const int off = (dz * TC_HY + dy) * TC_HX + dx;
+                        for (int kc = 0; kc < 2; kc++) {
+                            const uint64_t ad =
+                                smem_desc(a_base + (uint32_t)(2 * kc * TC_PLANE_BYTES + (r0 + off) * 16), TC_PLANE_BYTES, 128);
+                            const uint64_t bd = smem_desc(b_base + (uint32_t)((4 * tap + 2 * kc) * 512), 512, 128);
+                            tc_mma(d, ad, bd, (tap | kc) ? 1u : 0u);
+                        }
+                    }
+                }
+                tc_commit(&free_bar[s]);
+                tc_commit(&tfull_bar[s]);
+                s_committed = i + 1;
+            }
+        }
+    } else {
+        // ---------------- epilogue: warps 0-3, TMEM lanes 32 warp .. 32 warp + 31
+        int i = 0;
+        const long long HW = (long long)p.H * p.W;
+        for (long long tile = blockIdx.x; tile < p.tiles; tile += gridDim.x, i++) {
+            const int s = i & 1;
+            if (!wait_or_abort(&tfull_bar[s], (i >> 1) & 1, abort_flag)) break;
+            if (threadIdx.x == 0) s_drained = i + 1;
+            tc_fence_after();
+            int b, z0, y0, x0;
+            tile_origin(p, tile, b, z0, y0, x0);
+            for (int rb = 0; rb < TC_RB; rb++) {
+                float v[32];
+                __syncwarp();
+                tc_ld32(tmem + ((uint32_t)(32 * warp) << 16) + (uint32_t)(s * 128 + rb * 32), v);
+                const int hl = TC_ROW0 + 128 * rb + 32 * warp + lane;
+                const int hx = hl % TC_HX, hy = (hl / TC_HX) % TC_HY, hz = hl / (TC_HX * TC_HY);
+                const int x = x0 + hx - 1, y = y0 + hy - 1, z = z0 + hz - 1;
+                const bool interior = hx >= 1 && hx <= TC_TX && hy >= 1 && hy <= TC_TY && hz >= 1 && hz <= TC_TZ;
+                if (!interior || x >= p.W || y >= p.H || z >= p.D) continue;
+                const long long m = x + (long long)p.W * y + HW * (z + (long long)p.D * b);
+#pragma unroll
+                for (int c = 0; c < 32; c++) v[c] += bias ? __ldg(&bias[c]) : 0.0f;
+                if (res) {
+                    const uint4 *r4 = reinterpret_cast<const uint4 *>(res + m * 32);
+#pragma unroll
+                    for (int q = 0; q < 4; q++) {
+                        const uint4 u = __ldg(&r4[q]);
+                        const uint32_t w[4] = {u.x, u.y, u.z, u.w};
+#pragma unroll
+                        for (int h = 0; h < 4; h++) {
+                            const float2 f = __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162 *>(&w[h]));
+                            v[8 * q + 2 * h] += f.x;
+                            v[8 * q + 2 * h + 1] += f.y;
+                        }
+                    }
+                }
+                if (relu) {
+#pragma unroll
+                    for (int c = 0; c < 32; c++) v[c] = fmaxf(v[c], 0.0f);
+                }
+                if (out_b) {
+                    uint4 *o4 = reinterpret_cast<uint4 *>(out_b + m * 32);
+#pragma unroll
+                    for (int q = 0; q < 4; q++) {
+                        uint32_t w[4];
+#pragma unroll
+                        for (int h = 0; h < 4; h++) {
+                            const __nv_bfloat162 t = __floats2bfloat162_rn(v[8 * q + 2 * h], v[8 * q + 2 * h + 1]);
+                            w[h] = *reinterpret_cast<const uint32_t *>(&t);
+                        }
+                        o4[q] = make_uint4(w[0], w[1], w[2], w[3]);
+                    }
+                }
+                if (out_f) {
+                    float4 *o4 = reinterpret_cast<float4 *>(out_f + m * 32);
+#pragma unroll
+                    for (int q = 0; q < 8; q++) o4[q] = make_float4(v[4 * q], v[4 * q + 1], v[4 * q + 2], v[4 * q + 3]);
+                }
+            }
+            tc_fence_before();
+            mbar_arrive(&tempty_bar[s]);
+        }
+    }
+
+    // every role is done (or aborted): wait out this CTA's copies and MMAs,
+    // then free the tensor memory
+    __syncthreads();
+    if (*abort_flag && threadIdx.x == 0) {
+        atomicExch(fault, 1);
+        // copies issued but not consumed, MMAs committed but not drained
+        for (int j = s_consumed; j < s_issued; j++) mbar_wait_bounded(&full_bar[j & 1], (j >> 1) & 1, TC_WAIT_TRIES);
+        for (int j = s_drained; j < s_committed; j++) mbar_wait_bounded(&tfull_bar[j & 1], (j >> 1) & 1, TC_WAIT_TRIES);
+    }
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    __syncwarp();
+    if (warp == 4)
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(TC_TMEM_COLS) : "memory");
+}
+
+// ------------------------------------------------------------------- host
+static bool encode_activation_map(CUtensorMap *m, const void *in, int B, int D, int H, int W)
+{
+    static void *fn = nullptr;
+    if (!fn) {
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &fn, 12000, cudaEnableDefault, &q) !=
+                cudaSuccess ||
+            q != cudaDriverEntryPointSuccess)
+            fn = nullptr;
+        if (!fn) return false;
+    }
+    auto encode = reinterpret_cast<CUresult (*)(CUtensorMap *, CUtensorMapDataType, cuuint32_t, void *,
+                                                const cuuint64_t *, const cuuint64_t *, const cuuint32_t *,
+                                                const cuuint32_t *, CUtensorMapInterleave, CUtensorMapSwizzle,
+                                                CUtensorMapL2promotion, CUtensorMapFloatOOBfill)>(fn);
+    const cuuint64_t dims[5] = {32, (cuuint64_t)W, (cuuint64_t)H, (cuuint64_t)D, (cuuint64_t)B};
+    const cuuint64_t strides[4] = {64, (cuuint64_t)W * 64, (cuuint64_t)H * W * 64, (cuuint64_t)D * H * W * 64};
+    const cuuint32_t box[5] = {8, TC_HX, TC_HY, TC_HZ, 1};
+    const cuuint32_t estr[5] = {1, 1, 1, 1, 1};
+    return encode(m, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 5, const_cast<void *>(in), dims, strides, box, estr,
+                  CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+                  CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
+bool conv3d_tc_available(const void *in, const void *Wb)
+{
+    return (reinterpret_cast<uintptr_t>(in) & 15u) == 0 && (reinterpret_cast<uintptr_t>(Wb) & 15u) == 0;
+}
+
+cudaError_t conv3d_tc(cudaStream_t s, const void *in, const void *Wb, const float *bias, const void *res, void *out_b,
+                      float *out_f, int B, int D, int H, int W, int relu, int *fault, int num_sms)
+{
+    static bool attr = false;
+    if (!attr) {
+        cudaError_t e = cudaFuncSetAttribute(k_conv3d_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, TC_SMEM);
+        if (e != cudaSuccess) return e;
+        attr = true;
+    }
+    CUtensorMap map;
+    if (!encode_activation_map(&map, in, B, D, H, W)) return cudaErrorInvalidValue;
+    TcParams p;
+    p.B = B;
+    p.D = D;
+    p.H = H;
+    p.W = W;
+    p.ntx = (W + TC_TX - 1) / TC_TX;
+    p.nty = (H + TC_TY - 1) / TC_TY;
+    p.ntz = (D + TC_TZ - 1) / TC_TZ;
+    p.tiles = (long long)p.ntx * p.nty * p.ntz * B;
+    const int grid = (int)(p.tiles < num_sms ? p.tiles : num_sms);
+    k_conv3d_tc<<<grid, TC_THREADS, TC_SMEM, s>>>(p, map, static_cast<const __nv_bfloat16 *>(Wb), bias,
+                                                   static_cast<const __nv_bfloat16 *>(res),
+                                                   static_cast<__nv_bfloat16 *>(out_b), out_f, relu, fault);
+    return cudaGetLastError();
+}
+
+}  // namespace nn
+}  // namespace rf

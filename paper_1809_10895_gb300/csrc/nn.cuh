@@ -31,6 +31,12 @@ cudaError_t conv3d(cudaStream_t s, int cin, int cout, const void *in, const void
 // dW[co][tap cin + ci] += sum_v in[v + tap][ci] dout[v][co], db[co] += sum_v dout[v][co]
 cudaError_t conv3d_wgrad(cudaStream_t s, int cin, int cout, const void *in, const float *dout, int B, int D, int H,
                          int W, float *dW, float *db, int num_sms);
+// The 32 -> 32 convolution on the tcgen05 tensor cores (conv_tc.cu); same
+// contract as conv3d with cin = cout = 32.  A device wait that runs out sets
+// *fault (and the output is then undefined).
+cudaError_t conv3d_tc(cudaStream_t s, const void *in, const void *Wb, const float *bias, const void *res, void *out_b,
+                      float *out_f, int B, int D, int H, int W, int relu, int *fault, int num_sms);
+bool conv3d_tc_available(const void *in, const void *Wb);
 void relu_bwd(cudaStream_t s, const void *y, const float *dy, float *dx, long long n, const float *add);
 void to_bf16(cudaStream_t s, const float *a, void *b, long long n);
 void add(cudaStream_t s, float *a, const float *b, long long n);
@@ -58,4 +64,4 @@ void ws_target(cudaStream_t s, const Grid &g, const uint8_t *flags, const double
 // network's forward pass, hk = h + y scale on active cells; ordered on s.
 rf_status rf_nn_mesh_guess(rf_nn *net, cudaStream_t s, const rf::Grid &g, const uint8_t *flags, const double *h,
                            const double *Ks, const rf::nn::WsScales &sc, float q_feat, float dt_feat, double scale,
-                           double *hk);
+                           double *hk, int *fault);

@@ -40,6 +40,7 @@ struct rf_nn {
     float *P = nullptr, *G = nullptr, *M1 = nullptr, *M2 = nullptr;
     __nv_bfloat16 *Wb = nullptr, *Wt = nullptr;
     float *loss_d = nullptr, *loss_h = nullptr;
+    int *fault = nullptr, *fault_h = nullptr;   // set by a device wait that ran out
     int adam_t = 0;
     long long launches = 0;
 
@@ -180,10 +181,19 @@ rf_status ensure_training(rf_nn *n, long long M)
 }
 
 rf_status conv(rf_nn *n, cudaStream_t s, int l, bool transposed, const void *in, const void *res, void *out_b,
-               float *out_f, int B, int D, int H, int W, int relu)
+               float *out_f, int B, int D, int H, int W, int relu, int *fault = nullptr)
 {
     const LayerDims &d = n->L[l];
     cudaError_t e;
+    const void *w = transposed ? (const void *)(n->Wt + d.wt) : (const void *)(n->Wb + d.wb);
+    if (d.cinp == 32 && d.coutp == 32 && nn::conv3d_tc_available(in, w)) {
+        // 32 -> 32 layers (forward and input-gradient) on the tcgen05 tensor cores
+        e = nn::conv3d_tc(s, in, w, transposed ? nullptr : n->P + d.b, transposed ? nullptr : res, out_b, out_f, B, D,
+                          H, W, transposed ? 0 : relu, fault ? fault : n->fault, n->num_sms);
+        n->launches++;
+        NN_CUDA(e);
+        return RF_OK;
+    }
     if (!transposed)
         e = nn::conv3d(s, d.cinp, d.coutp, in, n->Wb + d.wb, n->P + d.b, res, out_b, out_f, B, D, H, W, relu);
     else
@@ -196,15 +206,16 @@ rf_status conv(rf_nn *n, cudaStream_t s, int l, bool transposed, const void *in,
 // Forward pass from BF16 padded features x (M x 8) into y (M x 8, FP32).
 // Inference ping-pongs three M x 32 BF16 buffers; training keeps every
 // activation for the backward pass.
-rf_status forward(rf_nn *n, cudaStream_t s, const void *x, int B, int D, int H, int W, float *y, bool train)
+rf_status forward(rf_nn *n, cudaStream_t s, const void *x, int B, int D, int H, int W, float *y, bool train,
+                  int *fault = nullptr)
 {
     __nv_bfloat16 *A = train ? n->ta[0] : n->iA;
     NN_TRY(conv(n, s, 0, false, x, nullptr, A, nullptr, B, D, H, W, 1));
     for (int blk = 0; blk < 4; blk++) {
         __nv_bfloat16 *U = train ? n->tu[blk] : n->iU;
         __nv_bfloat16 *A2 = train ? n->ta[blk + 1] : n->iA2;
-        NN_TRY(conv(n, s, 1 + 2 * blk, false, A, nullptr, U, nullptr, B, D, H, W, 1));
-        NN_TRY(conv(n, s, 2 + 2 * blk, false, U, A, A2, nullptr, B, D, H, W, 1));
+        NN_TRY(conv(n, s, 1 + 2 * blk, false, A, nullptr, U, nullptr, B, D, H, W, 1, fault));
+        NN_TRY(conv(n, s, 2 + 2 * blk, false, U, A, A2, nullptr, B, D, H, W, 1, fault));
         if (train) A = A2;
         else std::swap(n->iA, n->iA2), A = n->iA;
     }
@@ -271,18 +282,27 @@ rf_status check_dims(int B, int D, int H, int W)
 
 bool aligned16(const void *p) { return (reinterpret_cast<uintptr_t>(p) & 15u) == 0; }
 
+// Synchronise the network's stream and report a device wait that ran out.
+rf_status sync_checked(rf_nn *n)
+{
+    NN_CUDA(cudaMemcpyAsync(n->fault_h, n->fault, sizeof(int), cudaMemcpyDeviceToHost, n->stream));
+    NN_CUDA(cudaStreamSynchronize(n->stream));
+    if (*n->fault_h) return nfail(RF_ERR_DEVICE_TIMEOUT, "warm-start network: a device wait ran out");
+    return RF_OK;
+}
+
 }  // namespace
 
 // Warm-start guess for a mesh (called by the solver): hk = h + y out_scale dt.
 rf_status rf_nn_mesh_guess(rf_nn *n, cudaStream_t s, const Grid &g, const uint8_t *flags, const double *h,
                            const double *Ks, const nn::WsScales &sc, float q_feat, float dt_feat, double scale,
-                           double *hk)
+                           double *hk, int *fault)
 {
     NN_TRY(ensure_inference(n, g.N));
     NN_TRY(begin(n, s));
     nn::ws_features_bf16(s, g, flags, h, Ks, sc, q_feat, dt_feat, n->ix);
     n->launches++;
-    NN_TRY(forward(n, s, n->ix, 1, g.nz, g.ny, g.nx, n->iy, false));
+    NN_TRY(forward(n, s, n->ix, 1, g.nz, g.ny, g.nx, n->iy, false, fault));
     nn::ws_guess(s, g, flags, h, n->iy, scale, hk);
     n->launches++;
     return end(n, s);
@@ -312,12 +332,14 @@ rf_status rf_nn_create(void *cuda_stream, const rf_allocator *alloc, rf_nn **out
     bool ok = cudaEventCreateWithFlags(&n->ev, cudaEventDisableTiming) == cudaSuccess && nalloc(n, n->P, n->nP) &&
               nalloc(n, n->G, n->nP) && nalloc(n, n->M1, n->nP) && nalloc(n, n->M2, n->nP) &&
               nalloc(n, n->Wb, n->nWb) && nalloc(n, n->Wt, n->nWt) && nalloc(n, n->loss_d, 1) &&
-              cudaMallocHost(&n->loss_h, sizeof(float)) == cudaSuccess;
+              nalloc(n, n->fault, 1) && cudaMallocHost(&n->loss_h, sizeof(float)) == cudaSuccess &&
+              cudaMallocHost(&n->fault_h, sizeof(int)) == cudaSuccess;
     if (ok) {
         cudaStream_t s = n->stream;
         for (void *p : {(void *)n->P, (void *)n->G, (void *)n->M1, (void *)n->M2})
             ok = ok && cudaMemsetAsync(p, 0, sizeof(float) * n->nP, s) == cudaSuccess;
-        ok = ok && cudaMemsetAsync(n->Wb, 0, sizeof(__nv_bfloat16) * n->nWb, s) == cudaSuccess &&
+        ok = ok && cudaMemsetAsync(n->fault, 0, sizeof(int), s) == cudaSuccess &&
+             cudaMemsetAsync(n->Wb, 0, sizeof(__nv_bfloat16) * n->nWb, s) == cudaSuccess &&
              cudaMemsetAsync(n->Wt, 0, sizeof(__nv_bfloat16) * n->nWt, s) == cudaSuccess &&
              cudaEventRecord(n->ev, s) == cudaSuccess && cudaStreamSynchronize(s) == cudaSuccess;
     }
@@ -339,6 +361,7 @@ void rf_nn_destroy(rf_nn *n)
         else cudaFree(p);
     }
     if (n->loss_h) cudaFreeHost(n->loss_h);
+    if (n->fault_h) cudaFreeHost(n->fault_h);
     if (n->ev) cudaEventDestroy(n->ev);
     delete n;
 }
@@ -428,7 +451,7 @@ rf_status rf_nn_loss_grad(rf_nn *n, const float *d_x, const float *d_target, con
     NN_CUDA(cudaMemcpyAsync(n->loss_h, n->loss_d, sizeof(float), cudaMemcpyDeviceToHost, n->stream));
     NN_TRY(end(n, n->stream));
     if (grad) NN_TRY(copy_out_logical(n, n->G, grad));
-    NN_CUDA(cudaStreamSynchronize(n->stream));
+    NN_TRY(sync_checked(n));
     if (loss) *loss = *n->loss_h;
     return RF_OK;
 }
@@ -454,7 +477,7 @@ rf_status rf_nn_train_step(rf_nn *n, const float *d_x, const float *d_target, co
     if (loss) NN_CUDA(cudaMemcpyAsync(n->loss_h, n->loss_d, sizeof(float), cudaMemcpyDeviceToHost, s));
     NN_TRY(end(n, s));
     if (loss) {
-        NN_CUDA(cudaStreamSynchronize(s));
+        NN_TRY(sync_checked(n));
         *loss = *n->loss_h;
     }
     return RF_OK;

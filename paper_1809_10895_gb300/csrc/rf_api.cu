@@ -534,7 +534,7 @@ rf_status attempt(rf_ctx *c, double dt, Attempt &A, bool guess)
         float q_feat, dt_feat;
         ws_scalar_features(c, c->ws_sc, c->t, dt, q_feat, dt_feat);
         RF_TRY(rf_nn_mesh_guess(c->ws_net, c->stream, c->g, c->flags, c->h, c->Ks, c->ws_sc, q_feat, dt_feat,
-                                c->ws_sc.out_scale * dt, c->hk));
+                                c->ws_sc.out_scale * dt, c->hk, c->dev_fault));
         run_closure(c, c->hk, nullptr, c->theta_k, 0);
         c->closure_at_h = false;
         c->ws_guesses++;
