@@ -91,6 +91,16 @@ def closure(soil: dict, h: float):
     return out[0], out[1], out[2]
 
 
+def gardner_steady_profile(z, q, Ks, alpha):
+    """Appendix A, Eq. A8: steady pressure head of a Gardner column with the
+    water table (h = 0) at z = 0 and a constant flux q at the top, q positive
+    downward (infiltration), valid for -Ks e^{-alpha L}/(1 - e^{-alpha L}) < q < Ks:
+    h(z) = ln[(q + (Ks - q) e^{-alpha z}) / Ks] / alpha."""
+    import numpy as np
+    z = np.asarray(z, dtype=np.float64)
+    return np.log((q + (Ks - q) * np.exp(-alpha * z)) / Ks) / alpha
+
+
 def ebats_accept(dt_nom, easy, picard, n_small, n_inc, f_grow, dt_max):
     d = C.c_double(dt_nom)
     e = C.c_int(easy)
