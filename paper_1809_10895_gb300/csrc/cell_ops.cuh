@@ -74,7 +74,7 @@ __device__ __forceinline__ void closure(const DevSoil &s, double Ks, double h, c
     }
     th = s.theta_r + dth * ff_to_d(se);
     K = Ks * ff_to_d(ff_mul(ff_sqrt(se), ff_mul(omy, omy)));
-    C = (dth * s.alpha * s.n * s.m) * ff_to_d(ff_mul(ys, w));
+    C = s.cfac * ff_to_d(ff_mul(ys, w));
 }
 
 // Neighbour across face f of cell p = (i,j,k); false when outside the grid.

@@ -138,6 +138,7 @@ k_assemble(Grid g, const DevSoil *__restrict__ soils, const uint8_t *__restrict_
     const double eps = spp->eps_chord;
     const double V_dt = g.V / spp->dt;
     double v[4] = {0.0, 0.0, 0.0, 0.0};
+    float a_rr = 0.0f, a_bb = 0.0f, a_rz = 0.0f;   // mixed start: norms of the FP32 seeds, summed in FP32
     const long long stride = (long long)gridDim.x * blockDim.x;
     for (long long p = (long long)blockIdx.x * blockDim.x + threadIdx.x; p < g.N; p += stride) {
         const uint8_t fl = flags[p];
@@ -184,13 +185,13 @@ k_assemble(Grid g, const DevSoil *__restrict__ soils, const uint8_t *__restrict_
             } else {
                 const float rf = (float)rp;
                 const float zf = di32 * rf;
+                const float bf = (float)rhs;
                 st.r32[p] = rf;
                 st.z32[p] = zf;
                 st.d32[p] = 0.0f;
-                v[0] += rp * rp;
-                v[1] += rhs * rhs;
-                v[2] += (double)(rf * rf);
-                v[3] += (double)(rf * zf);
+                a_rr = fmaf(rf, rf, a_rr);
+                a_bb = fmaf(bf, bf, a_bb);
+                a_rz = fmaf(rf, zf, a_rz);
             }
         }
     }
@@ -199,7 +200,15 @@ k_assemble(Grid g, const DevSoil *__restrict__ soils, const uint8_t *__restrict_
         if (grid_reduce<OpSum, 3>(w3, partials, ticket) && threadIdx.x == 0)
             cg64_start_scalars(st.sc, w3, st.tol, st.max_it, st.cond);
     } else if (MODE == ASM_MIXED) {
-        if (grid_reduce<OpSum, 4>(v, partials, ticket) && threadIdx.x == 0) {
+        // the residual is formed in FP64; its norms (a stopping test and CG
+        // seeds) are summed in FP32 within a block, in FP64 across blocks
+        float vf[3] = {a_rr, a_bb, a_rz};
+        double w[3];
+        if (grid_reduce_f32<3>(vf, w, partials, ticket) && threadIdx.x == 0) {
+            v[0] = w[0];
+            v[1] = w[1];
+            v[2] = w[0];
+            v[3] = w[2];
             st.sc->iter = 1;
             st.sc->done = 0;
             st.sc->status = CG_OK;

@@ -44,18 +44,31 @@ constexpr int TC_OFFMAX = TC_HY * TC_HX + TC_HX + 1;                     // larg
 constexpr int TC_RB = 4;                                                 // row blocks of 128
 constexpr int TC_PLANE_ROWS = 1152;   // >= TC_ROW0 + 128 TC_RB + TC_OFFMAX - 1 (rows past 1088 feed discarded outputs)
 constexpr int TC_PLANE_BYTES = TC_PLANE_ROWS * 16;                       // 18 432
-constexpr int TC_A_BYTES = 4 * TC_PLANE_BYTES;                           // 73 728 per stage
 constexpr int TC_BOX_BYTES = TC_HALO * 16;                               // 17 408 per plane copy
-constexpr int TC_KP = 27 * 32;                                           // 864
-constexpr int TC_B_BYTES = (TC_KP / 8) * 32 * 16;                        // 55 296
-constexpr int TC_SMEM = 2 * TC_A_BYTES + TC_B_BYTES + 1024;              // + alignment slack
 constexpr int TC_THREADS = 192;
-constexpr int TC_TMEM_COLS = 256;                                        // 2 stages x 4 blocks x 32
 constexpr int TC_WAIT_TRIES = 1 << 20;
+
+// Per instantiation: CINP input channels (16 or 32, in planes of 8), NOUT
+// GEMM columns (16 or 32).
+template <int CINP, int NOUT>
+struct TcShape {
+    static constexpr int PLANES = CINP / 8;
+    static constexpr int KC = CINP / 16;                      // K = 16 chunks per tap
+    static constexpr int KP = 27 * CINP;                      // weights per output channel
+    static constexpr int A_BYTES = PLANES * TC_PLANE_BYTES;   // per stage
+    static constexpr int B_BYTES = (KP / 8) * NOUT * 16;
+    static constexpr int SMEM = 2 * A_BYTES + B_BYTES + 1024;
+    static constexpr int TMEM_COLS = 2 * 4 * NOUT;            // 2 stages x 4 row blocks
+    static constexpr uint32_t IDESC = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(NOUT >> 3) << 17) |
+                                      ((128u >> 4) << 24);
+    static_assert(CINP == 16 || CINP == 32, "input planes");
+    static_assert(NOUT == 16 || NOUT == 32, "M = 128 needs N a multiple of 16");
+    static_assert(SMEM <= 227 * 1024, "shared memory");
+};
 
 static_assert(TC_ROW0 + 128 * TC_RB - 1 + TC_OFFMAX < TC_PLANE_ROWS, "plane rows cover every shifted read");
 static_assert(TC_ROW0 + 128 * TC_RB - 1 >= (TC_TZ * TC_HY + TC_TY) * TC_HX + TC_TX, "row blocks cover the interior");
-static_assert(TC_PLANE_BYTES % 128 == 0 && TC_A_BYTES % 1024 == 0, "TMA destinations 128-byte aligned");
+static_assert(TC_PLANE_BYTES % 1024 == 0, "TMA destinations 128-byte aligned, stages 1024-byte aligned");
 
 struct TcParams {
     int B, D, H, W;
@@ -71,17 +84,15 @@ __device__ __forceinline__ uint64_t smem_desc(uint32_t addr, uint32_t lbo, uint3
            (1ull << 46);
 }
 
-// kind::f16 instruction descriptor: D FP32, A and B BF16, both K-major,
-// N = 32, M = 128.
-constexpr uint32_t TC_IDESC = (1u << 4) | (1u << 7) | (1u << 10) | ((32u >> 3) << 17) | ((128u >> 4) << 24);
-
-__device__ __forceinline__ void tc_mma(uint32_t d_tmem, uint64_t adesc, uint64_t bdesc, uint32_t accum)
+// kind::f16 MMA, M = 128: D FP32, A and B BF16, both K-major (idesc).
+__device__ __forceinline__ void tc_mma(uint32_t d_tmem, uint64_t adesc, uint64_t bdesc, uint32_t idesc,
+                                       uint32_t accum)
 {
     asm volatile(
         "{\n\t.reg .pred p;\n\t"
         "setp.ne.b32 p, %4, 0;\n\t"
         "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}"
-        ::"r"(d_tmem), "l"(adesc), "l"(bdesc), "r"(TC_IDESC), "r"(accum)
+        ::"r"(d_tmem), "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accum)
         : "memory");
 }
 
@@ -97,6 +108,20 @@ __device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::
 __device__ __forceinline__ void mbar_arrive(uint64_t *bar)
 {
     asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_addr(bar)) : "memory");
+}
+
+// 16 consecutive TMEM columns of this thread's lane.
+__device__ __forceinline__ void tc_ld16(uint32_t taddr, float (&v)[16])
+{
+    uint32_t r[16];
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
+        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+          "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+        : "r"(taddr));
+    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+    for (int i = 0; i < 16; i++) v[i] = __uint_as_float(r[i]);
 }
 
 // 32 consecutive TMEM columns of this thread's lane.
@@ -143,15 +168,22 @@ __device__ __forceinline__ void tile_origin(const TcParams &p, long long tile, i
 
 }  // namespace
 
+// Wb: NOUT x 27 CINP BF16 weights, K = tap CINP + c.  The input tensor has
+// cin_mem channels (8 or 32); planes past cin_mem / 8 stay zero.  out_ch
+// output channels (<= NOUT) are written, the row stride of out_b / out_f.
+template <int CINP, int NOUT>
 __global__ void __launch_bounds__(TC_THREADS, 1)
-k_conv3d_tc(TcParams p, const __grid_constant__ CUtensorMap in_map, const __nv_bfloat16 *__restrict__ Wb,
-            const float *__restrict__ bias, const __nv_bfloat16 *__restrict__ res, __nv_bfloat16 *__restrict__ out_b,
-            float *__restrict__ out_f, int relu, int *fault)
+k_conv3d_tc(TcParams p, const __grid_constant__ CUtensorMap in_map, int cin_mem, int out_ch,
+            const __nv_bfloat16 *__restrict__ Wb, const float *__restrict__ bias,
+            const __nv_bfloat16 *__restrict__ res, __nv_bfloat16 *__restrict__ out_b, float *__restrict__ out_f,
+            int relu, int *fault)
 {
+    using S = TcShape<CINP, NOUT>;
     extern __shared__ unsigned char smem_raw[];
     unsigned char *smem = reinterpret_cast<unsigned char *>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
-    unsigned char *sA = smem;                       // 2 stages x 4 planes
-    unsigned char *sB = smem + 2 * TC_A_BYTES;      // weights, [k/8][n][8 k]
+    unsigned char *sA = smem;                       // 2 stages x PLANES planes
+    unsigned char *sB = smem + 2 * S::A_BYTES;      // weights, [k/8][n][8 k]
+    const int loaded = cin_mem / 8;                 // planes filled by tensor copies
     __shared__ __align__(8) uint64_t full_bar[2], free_bar[2], tfull_bar[2], tempty_bar[2];
     __shared__ uint32_t s_tmem;
     __shared__ int s_abort;
@@ -160,12 +192,18 @@ k_conv3d_tc(TcParams p, const __grid_constant__ CUtensorMap in_map, const __nv_b
     __shared__ int s_issued, s_consumed, s_committed, s_drained;
     const int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
 
-    // weights into shared memory (generic stores, then made visible to the async proxy)
-    for (int e = threadIdx.x; e < (TC_KP / 8) * 32; e += TC_THREADS) {
-        const int n = e % 32, kg = e / 32;
-        const uint4 w = *reinterpret_cast<const uint4 *>(Wb + (size_t)n * TC_KP + kg * 8);
-        *reinterpret_cast<uint4 *>(sB + (size_t)(kg * 32 + n) * 16) = w;
+    // weights into shared memory, zero planes for the channels the input does
+    // not have (generic stores, then made visible to the async proxy)
+    for (int e = threadIdx.x; e < (S::KP / 8) * NOUT; e += TC_THREADS) {
+        const int n = e % NOUT, kg = e / NOUT;
+        const uint4 w = *reinterpret_cast<const uint4 *>(Wb + (size_t)n * S::KP + kg * 8);
+        *reinterpret_cast<uint4 *>(sB + (size_t)(kg * NOUT + n) * 16) = w;
     }
+    for (int st = 0; st < 2; st++)
+        for (int pl = loaded; pl < S::PLANES; pl++) {
+            uint4 *z = reinterpret_cast<uint4 *>(sA + st * S::A_BYTES + pl * TC_PLANE_BYTES);
+            for (int e = threadIdx.x; e < TC_PLANE_ROWS; e += TC_THREADS) z[e] = make_uint4(0u, 0u, 0u, 0u);
+        }
     fence_proxy_async_smem();
     if (threadIdx.x == 0) {
         for (int i = 0; i < 2; i++) {
@@ -180,7 +218,7 @@ k_conv3d_tc(TcParams p, const __grid_constant__ CUtensorMap in_map, const __nv_b
     }
     if (warp == 4) {
         asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_addr(&s_tmem)),
-                     "r"(TC_TMEM_COLS)
+                     "r"(S::TMEM_COLS)
                      : "memory");
         asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
     }
@@ -199,9 +237,9 @@ k_conv3d_tc(TcParams p, const __grid_constant__ CUtensorMap in_map, const __nv_b
                 if (i >= 2 && !wait_or_abort(&free_bar[s], ((i >> 1) - 1) & 1, abort_flag)) break;
                 int b, z0, y0, x0;
                 tile_origin(p, tile, b, z0, y0, x0);
-                mbar_expect_tx(&full_bar[s], 4 * TC_BOX_BYTES);
-                unsigned char *dst = sA + s * TC_A_BYTES;
-                for (int cg = 0; cg < 4; cg++) {
+                mbar_expect_tx(&full_bar[s], loaded * TC_BOX_BYTES);
+                unsigned char *dst = sA + s * S::A_BYTES;
+                for (int cg = 0; cg < loaded; cg++) {
                     asm volatile(
                         "cp.async.bulk.tensor.5d.shared::cluster.global.mbarrier::complete_tx::bytes"
                         " [%0], [%1, {%3, %4, %5, %6, %7}], [%2];"
@@ -222,19 +260,21 @@ k_conv3d_tc(TcParams p, const __grid_constant__ CUtensorMap in_map, const __nv_b
                 s_consumed = i + 1;
                 if (i >= 2 && !wait_or_abort(&tempty_bar[s], ((i >> 1) - 1) & 1, abort_flag)) break;
                 tc_fence_after();
-                const uint32_t a_base = smem_addr(sA + s * TC_A_BYTES);
+                const uint32_t a_base = smem_addr(sA + s * S::A_BYTES);
                 const uint32_t b_base = smem_addr(sB);
                 for (int rb = 0; rb < TC_RB; rb++) {
-                    const uint32_t d = tmem + (uint32_t)(s * 128 + rb * 32);
+                    const uint32_t d = tmem + (uint32_t)((s * 4 + rb) * NOUT);
                     const int r0 = TC_ROW0 + 128 * rb;
                     for (int tap = 0; tap < 27; tap++) {
                         const int dz = tap / 9 - 1, dy = (tap / 3) % 3 - 1, dx = tap % 3 - 1;
                         const int off = (dz * TC_HY + dy) * TC_HX + dx;
-                        for (int kc = 0; kc < 2; kc++) {
+                        for (int kc = 0; kc < S::KC; kc++) {
+                            // A: planes 2kc, 2kc+1 (LBO) from row r0 + off; B: k-groups tap CINP/8 + 2kc, + 1
                             const uint64_t ad =
                                 smem_desc(a_base + (uint32_t)(2 * kc * TC_PLANE_BYTES + (r0 + off) * 16), TC_PLANE_BYTES, 128);
-                            const uint64_t bd = smem_desc(b_base + (uint32_t)((4 * tap + 2 * kc) * 512), 512, 128);
-                            tc_mma(d, ad, bd, (tap | kc) ? 1u : 0u);
+                            const uint64_t bd = smem_desc(
+                                b_base + (uint32_t)((tap * S::PLANES + 2 * kc) * NOUT * 16), NOUT * 16, 128);
+                            tc_mma(d, ad, bd, S::IDESC, (tap | kc) ? 1u : 0u);
                         }
                     }
                 }
@@ -257,50 +297,74 @@ k_conv3d_tc(TcParams p, const __grid_constant__ CUtensorMap in_map, const __nv_b
             for (int rb = 0; rb < TC_RB; rb++) {
                 float v[32];
                 __syncwarp();
-                tc_ld32(tmem + ((uint32_t)(32 * warp) << 16) + (uint32_t)(s * 128 + rb * 32), v);
+                const uint32_t taddr = tmem + ((uint32_t)(32 * warp) << 16) + (uint32_t)((s * 4 + rb) * NOUT);
+                if constexpr (NOUT == 32) {
+                    tc_ld32(taddr, v);
+                } else {
+                    float v16[16];
+                    tc_ld16(taddr, v16);
+#pragma unroll
+                    for (int c = 0; c < 16; c++) v[c] = v16[c];
+                }
                 const int hl = TC_ROW0 + 128 * rb + 32 * warp + lane;
                 const int hx = hl % TC_HX, hy = (hl / TC_HX) % TC_HY, hz = hl / (TC_HX * TC_HY);
                 const int x = x0 + hx - 1, y = y0 + hy - 1, z = z0 + hz - 1;
                 const bool interior = hx >= 1 && hx <= TC_TX && hy >= 1 && hy <= TC_TY && hz >= 1 && hz <= TC_TZ;
                 if (!interior || x >= p.W || y >= p.H || z >= p.D) continue;
                 const long long m = x + (long long)p.W * y + HW * (z + (long long)p.D * b);
+                if (out_ch == 32) {
 #pragma unroll
-                for (int c = 0; c < 32; c++) v[c] += bias ? __ldg(&bias[c]) : 0.0f;
-                if (res) {
-                    const uint4 *r4 = reinterpret_cast<const uint4 *>(res + m * 32);
+                    for (int c = 0; c < 32; c++) v[c] += bias ? __ldg(&bias[c]) : 0.0f;
+                    if (res) {
+                        const uint4 *r4 = reinterpret_cast<const uint4 *>(res + m * 32);
 #pragma unroll
-                    for (int q = 0; q < 4; q++) {
-                        const uint4 u = __ldg(&r4[q]);
-                        const uint32_t w[4] = {u.x, u.y, u.z, u.w};
+                        for (int q = 0; q < 4; q++) {
+                            const uint4 u = __ldg(&r4[q]);
+                            const uint32_t w[4] = {u.x, u.y, u.z, u.w};
 #pragma unroll
-                        for (int h = 0; h < 4; h++) {
-                            const float2 f = __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162 *>(&w[h]));
-                            v[8 * q + 2 * h] += f.x;
-                            v[8 * q + 2 * h + 1] += f.y;
+                            for (int h = 0; h < 4; h++) {
+                                const float2 f = __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162 *>(&w[h]));
+                                v[8 * q + 2 * h] += f.x;
+                                v[8 * q + 2 * h + 1] += f.y;
+                            }
                         }
                     }
-                }
-                if (relu) {
+                    if (relu) {
 #pragma unroll
-                    for (int c = 0; c < 32; c++) v[c] = fmaxf(v[c], 0.0f);
-                }
-                if (out_b) {
-                    uint4 *o4 = reinterpret_cast<uint4 *>(out_b + m * 32);
-#pragma unroll
-                    for (int q = 0; q < 4; q++) {
-                        uint32_t w[4];
-#pragma unroll
-                        for (int h = 0; h < 4; h++) {
-                            const __nv_bfloat162 t = __floats2bfloat162_rn(v[8 * q + 2 * h], v[8 * q + 2 * h + 1]);
-                            w[h] = *reinterpret_cast<const uint32_t *>(&t);
-                        }
-                        o4[q] = make_uint4(w[0], w[1], w[2], w[3]);
+                        for (int c = 0; c < 32; c++) v[c] = fmaxf(v[c], 0.0f);
                     }
-                }
-                if (out_f) {
-                    float4 *o4 = reinterpret_cast<float4 *>(out_f + m * 32);
+                    if (out_b) {
+                        uint4 *o4 = reinterpret_cast<uint4 *>(out_b + m * 32);
 #pragma unroll
-                    for (int q = 0; q < 8; q++) o4[q] = make_float4(v[4 * q], v[4 * q + 1], v[4 * q + 2], v[4 * q + 3]);
+                        for (int q = 0; q < 4; q++) {
+                            uint32_t w[4];
+#pragma unroll
+                            for (int h = 0; h < 4; h++) {
+                                const __nv_bfloat162 t = __floats2bfloat162_rn(v[8 * q + 2 * h], v[8 * q + 2 * h + 1]);
+                                w[h] = *reinterpret_cast<const uint32_t *>(&t);
+                            }
+                            o4[q] = make_uint4(w[0], w[1], w[2], w[3]);
+                        }
+                    }
+                    if (out_f) {
+                        float4 *o4 = reinterpret_cast<float4 *>(out_f + m * 32);
+#pragma unroll
+                        for (int q = 0; q < 8; q++)
+                            o4[q] = make_float4(v[4 * q], v[4 * q + 1], v[4 * q + 2], v[4 * q + 3]);
+                    }
+                } else {
+                    // 8 output channels (the output convolution): FP32 out only
+#pragma unroll
+                    for (int c = 0; c < 8; c++) v[c] += bias ? __ldg(&bias[c]) : 0.0f;
+                    if (relu) {
+#pragma unroll
+                        for (int c = 0; c < 8; c++) v[c] = fmaxf(v[c], 0.0f);
+                    }
+                    if (out_f) {
+                        float4 *o4 = reinterpret_cast<float4 *>(out_f + m * 8);
+                        o4[0] = make_float4(v[0], v[1], v[2], v[3]);
+                        o4[1] = make_float4(v[4], v[5], v[6], v[7]);
+                    }
                 }
             }
             tc_fence_before();
@@ -322,11 +386,11 @@ k_conv3d_tc(TcParams p, const __grid_constant__ CUtensorMap in_map, const __nv_b
     tc_fence_after();
     __syncwarp();
     if (warp == 4)
-        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(TC_TMEM_COLS) : "memory");
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(S::TMEM_COLS) : "memory");
 }
 
 // ------------------------------------------------------------------- host
-static bool encode_activation_map(CUtensorMap *m, const void *in, int B, int D, int H, int W)
+static bool encode_activation_map(CUtensorMap *m, const void *in, int cin_mem, int B, int D, int H, int W)
 {
     static void *fn = nullptr;
     if (!fn) {
@@ -341,8 +405,9 @@ static bool encode_activation_map(CUtensorMap *m, const void *in, int B, int D, 
                                                 const cuuint64_t *, const cuuint64_t *, const cuuint32_t *,
                                                 const cuuint32_t *, CUtensorMapInterleave, CUtensorMapSwizzle,
                                                 CUtensorMapL2promotion, CUtensorMapFloatOOBfill)>(fn);
-    const cuuint64_t dims[5] = {32, (cuuint64_t)W, (cuuint64_t)H, (cuuint64_t)D, (cuuint64_t)B};
-    const cuuint64_t strides[4] = {64, (cuuint64_t)W * 64, (cuuint64_t)H * W * 64, (cuuint64_t)D * H * W * 64};
+    const cuuint64_t row = (cuuint64_t)cin_mem * 2;   // bytes per voxel
+    const cuuint64_t dims[5] = {(cuuint64_t)cin_mem, (cuuint64_t)W, (cuuint64_t)H, (cuuint64_t)D, (cuuint64_t)B};
+    const cuuint64_t strides[4] = {row, (cuuint64_t)W * row, (cuuint64_t)H * W * row, (cuuint64_t)D * H * W * row};
     const cuuint32_t box[5] = {8, TC_HX, TC_HY, TC_HZ, 1};
     const cuuint32_t estr[5] = {1, 1, 1, 1, 1};
     return encode(m, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 5, const_cast<void *>(in), dims, strides, box, estr,
@@ -355,17 +420,34 @@ bool conv3d_tc_available(const void *in, const void *Wb)
     return (reinterpret_cast<uintptr_t>(in) & 15u) == 0 && (reinterpret_cast<uintptr_t>(Wb) & 15u) == 0;
 }
 
-cudaError_t conv3d_tc(cudaStream_t s, const void *in, const void *Wb, const float *bias, const void *res, void *out_b,
-                      float *out_f, int B, int D, int H, int W, int relu, int *fault, int num_sms)
+template <int CINP, int NOUT>
+static cudaError_t launch_tc(cudaStream_t s, const CUtensorMap &map, const TcParams &p, int cin_mem, int out_ch,
+                             const void *Wb, const float *bias, const void *res, void *out_b, float *out_f, int relu,
+                             int *fault, int num_sms)
 {
+    using S = TcShape<CINP, NOUT>;
     static bool attr = false;
     if (!attr) {
-        cudaError_t e = cudaFuncSetAttribute(k_conv3d_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, TC_SMEM);
+        cudaError_t e =
+            cudaFuncSetAttribute(k_conv3d_tc<CINP, NOUT>, cudaFuncAttributeMaxDynamicSharedMemorySize, S::SMEM);
         if (e != cudaSuccess) return e;
         attr = true;
     }
+    const int grid = (int)(p.tiles < num_sms ? p.tiles : num_sms);
+    k_conv3d_tc<CINP, NOUT><<<grid, TC_THREADS, S::SMEM, s>>>(
+        p, map, cin_mem, out_ch, static_cast<const __nv_bfloat16 *>(Wb), bias, static_cast<const __nv_bfloat16 *>(res),
+        static_cast<__nv_bfloat16 *>(out_b), out_f, relu, fault);
+    return cudaGetLastError();
+}
+
+cudaError_t conv3d_tc(cudaStream_t s, int cin_mem, int cinp, int nout, int out_ch, const void *in, const void *Wb,
+                      const float *bias, const void *res, void *out_b, float *out_f, int B, int D, int H, int W,
+                      int relu, int *fault, int num_sms)
+{
+    if (!(cin_mem == 8 || cin_mem == 32) || cin_mem > cinp) return cudaErrorInvalidValue;
+    if (out_ch > nout || (nout == 16 && (out_ch != 8 || res || out_b))) return cudaErrorInvalidValue;
     CUtensorMap map;
-    if (!encode_activation_map(&map, in, B, D, H, W)) return cudaErrorInvalidValue;
+    if (!encode_activation_map(&map, in, cin_mem, B, D, H, W)) return cudaErrorInvalidValue;
     TcParams p;
     p.B = B;
     p.D = D;
@@ -375,11 +457,33 @@ cudaError_t conv3d_tc(cudaStream_t s, const void *in, const void *Wb, const floa
     p.nty = (H + TC_TY - 1) / TC_TY;
     p.ntz = (D + TC_TZ - 1) / TC_TZ;
     p.tiles = (long long)p.ntx * p.nty * p.ntz * B;
-    const int grid = (int)(p.tiles < num_sms ? p.tiles : num_sms);
-    k_conv3d_tc<<<grid, TC_THREADS, TC_SMEM, s>>>(p, map, static_cast<const __nv_bfloat16 *>(Wb), bias,
-                                                   static_cast<const __nv_bfloat16 *>(res),
-                                                   static_cast<__nv_bfloat16 *>(out_b), out_f, relu, fault);
-    return cudaGetLastError();
+    if (cinp == 32 && nout == 32)
+        return launch_tc<32, 32>(s, map, p, cin_mem, out_ch, Wb, bias, res, out_b, out_f, relu, fault, num_sms);
+    if (cinp == 16 && nout == 32)
+        return launch_tc<16, 32>(s, map, p, cin_mem, out_ch, Wb, bias, res, out_b, out_f, relu, fault, num_sms);
+    if (cinp == 32 && nout == 16)
+        return launch_tc<32, 16>(s, map, p, cin_mem, out_ch, Wb, bias, res, out_b, out_f, relu, fault, num_sms);
+    return cudaErrorInvalidValue;
+}
+
+// Weights for the tensor-core kernel: dst[n][tap cinp + c] = src[n][tap cin + c]
+// (src rows of kp_src), zero for n >= n_src or c >= cin.
+__global__ void k_prep_tc_weights(const __nv_bfloat16 *__restrict__ src, int n_src, int cin, int kp_src, int nout,
+                                  int cinp, __nv_bfloat16 *__restrict__ dst)
+{
+    const int total = nout * 27 * cinp;
+    for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < total; e += gridDim.x * blockDim.x) {
+        const int n = e / (27 * cinp), k = e % (27 * cinp);
+        const int tap = k / cinp, c = k % cinp;
+        dst[e] = (n < n_src && c < cin) ? src[(size_t)n * kp_src + tap * cin + c] : __float2bfloat16(0.0f);
+    }
+}
+
+void prep_tc_weights(cudaStream_t s, const void *src, int n_src, int cin, int kp_src, int nout, int cinp, void *dst)
+{
+    const int total = nout * 27 * cinp;
+    k_prep_tc_weights<<<(total + 255) / 256, 256, 0, s>>>(static_cast<const __nv_bfloat16 *>(src), n_src, cin, kp_src,
+                                                          nout, cinp, static_cast<__nv_bfloat16 *>(dst));
 }
 
 }  // namespace nn

@@ -219,7 +219,7 @@ rf_status rf_ens_create(const rf_ens_instance *inst, int n, const rf_solver_para
         const double m = s.model == RF_VG ? 1.0 - 1.0 / s.n : 0.0;
         const float nh = (float)s.n, mh = (float)m;
         d.soil = DevSoil{s.model, s.theta_r, s.theta_s, s.alpha, s.n, m, s.S, nh, (float)(s.n - (double)nh), mh,
-                         (float)(m - (double)mh)};
+                         (float)(m - (double)mh), (s.theta_s - s.theta_r) * s.alpha * s.n * m};
         for (int f = 0; f < 6; f++) { d.sp.bc_type[f] = BC_ZERO_FLUX; d.sp.bc_val[f] = 0.0; }
         d.sp.bc_type[F_ZMAX] = a.top_type;
         d.sp.bc_val[F_ZMAX] = a.top_value;

@@ -31,12 +31,19 @@ cudaError_t conv3d(cudaStream_t s, int cin, int cout, const void *in, const void
 // dW[co][tap cin + ci] += sum_v in[v + tap][ci] dout[v][co], db[co] += sum_v dout[v][co]
 cudaError_t conv3d_wgrad(cudaStream_t s, int cin, int cout, const void *in, const float *dout, int B, int D, int H,
                          int W, float *dW, float *db, int num_sms);
-// The 32 -> 32 convolution on the tcgen05 tensor cores (conv_tc.cu); same
-// contract as conv3d with cin = cout = 32.  A device wait that runs out sets
-// *fault (and the output is then undefined).
-cudaError_t conv3d_tc(cudaStream_t s, const void *in, const void *Wb, const float *bias, const void *res, void *out_b,
-                      float *out_f, int B, int D, int H, int W, int relu, int *fault, int num_sms);
+// Convolutions on the tcgen05 tensor cores (conv_tc.cu).  in: cin_mem (8 or
+// 32) BF16 channels per voxel, zero-padded to cinp (16 or 32) planes; Wb:
+// nout x 27 cinp BF16 weights (K = tap cinp + c); nout GEMM columns (16 or
+// 32), of which out_ch are written (the row stride of out_b / out_f; with
+// nout = 16 only out_ch = 8 and FP32 output).  A device wait that runs out
+// sets *fault (and the output is then undefined).
+cudaError_t conv3d_tc(cudaStream_t s, int cin_mem, int cinp, int nout, int out_ch, const void *in, const void *Wb,
+                      const float *bias, const void *res, void *out_b, float *out_f, int B, int D, int H, int W,
+                      int relu, int *fault, int num_sms);
 bool conv3d_tc_available(const void *in, const void *Wb);
+// dst[n][tap cinp + c] = src[n][tap cin + c] (src rows of kp_src), zero for
+// n >= n_src or c >= cin.
+void prep_tc_weights(cudaStream_t s, const void *src, int n_src, int cin, int kp_src, int nout, int cinp, void *dst);
 void relu_bwd(cudaStream_t s, const void *y, const float *dy, float *dx, long long n, const float *add);
 void to_bf16(cudaStream_t s, const float *a, void *b, long long n);
 void add(cudaStream_t s, float *a, const float *b, long long n);

@@ -39,6 +39,9 @@ struct rf_nn {
     long long nP = 0, nWb = 0, nWt = 0;
     float *P = nullptr, *G = nullptr, *M1 = nullptr, *M2 = nullptr;
     __nv_bfloat16 *Wb = nullptr, *Wt = nullptr;
+    // tensor-core layouts of the input and output convolutions (channels
+    // padded to the MMA's K = 16 and N = 16 granules)
+    __nv_bfloat16 *tcw0 = nullptr, *tcw9 = nullptr, *tcw9t = nullptr;
     float *loss_d = nullptr, *loss_h = nullptr;
     int *fault = nullptr, *fault_h = nullptr;   // set by a device wait that ran out
     int adam_t = 0;
@@ -146,6 +149,11 @@ rf_status refresh_weights(rf_nn *n, cudaStream_t s)
         nn::prep_weights(s, n->P + d.w, d.cinp, d.coutp, d.kp, d.kpt, n->Wb + d.wb, l == 0 ? nullptr : n->Wt + d.wt);
         n->launches++;
     }
+    const LayerDims &d0 = n->L[0], &d9 = n->L[nn::N_LAYERS - 1];
+    nn::prep_tc_weights(s, n->Wb + d0.wb, d0.coutp, d0.cinp, d0.kp, 32, 16, n->tcw0);     // 8 -> 32
+    nn::prep_tc_weights(s, n->Wb + d9.wb, d9.coutp, d9.cinp, d9.kp, 16, 32, n->tcw9);     // 32 -> 8 (N 16)
+    nn::prep_tc_weights(s, n->Wt + d9.wt, d9.cinp, d9.coutp, d9.kpt, 32, 16, n->tcw9t);   // its input gradient
+    n->launches += 3;
     return RF_OK;
 }
 
@@ -186,10 +194,33 @@ rf_status conv(rf_nn *n, cudaStream_t s, int l, bool transposed, const void *in,
     const LayerDims &d = n->L[l];
     cudaError_t e;
     const void *w = transposed ? (const void *)(n->Wt + d.wt) : (const void *)(n->Wb + d.wb);
+    int *f = fault ? fault : n->fault;
+    const bool last = l == nn::N_LAYERS - 1;
+    // every layer shape of the network runs on the tcgen05 tensor cores
     if (d.cinp == 32 && d.coutp == 32 && nn::conv3d_tc_available(in, w)) {
-        // 32 -> 32 layers (forward and input-gradient) on the tcgen05 tensor cores
-        e = nn::conv3d_tc(s, in, w, transposed ? nullptr : n->P + d.b, transposed ? nullptr : res, out_b, out_f, B, D,
-                          H, W, transposed ? 0 : relu, fault ? fault : n->fault, n->num_sms);
+        e = nn::conv3d_tc(s, 32, 32, 32, 32, in, w, transposed ? nullptr : n->P + d.b, transposed ? nullptr : res,
+                          out_b, out_f, B, D, H, W, transposed ? 0 : relu, f, n->num_sms);
+        n->launches++;
+        NN_CUDA(e);
+        return RF_OK;
+    }
+    if (l == 0 && !transposed && nn::conv3d_tc_available(in, n->tcw0)) {
+        e = nn::conv3d_tc(s, 8, 16, 32, 32, in, n->tcw0, n->P + d.b, res, out_b, out_f, B, D, H, W, relu, f,
+                          n->num_sms);
+        n->launches++;
+        NN_CUDA(e);
+        return RF_OK;
+    }
+    if (last && !transposed && !out_b && !res && nn::conv3d_tc_available(in, n->tcw9)) {
+        e = nn::conv3d_tc(s, 32, 32, 16, 8, in, n->tcw9, n->P + d.b, nullptr, nullptr, out_f, B, D, H, W, relu, f,
+                          n->num_sms);
+        n->launches++;
+        NN_CUDA(e);
+        return RF_OK;
+    }
+    if (last && transposed && nn::conv3d_tc_available(in, n->tcw9t)) {
+        e = nn::conv3d_tc(s, 8, 16, 32, 32, in, n->tcw9t, nullptr, nullptr, out_b, out_f, B, D, H, W, 0, f,
+                          n->num_sms);
         n->launches++;
         NN_CUDA(e);
         return RF_OK;
@@ -332,7 +363,8 @@ rf_status rf_nn_create(void *cuda_stream, const rf_allocator *alloc, rf_nn **out
     bool ok = cudaEventCreateWithFlags(&n->ev, cudaEventDisableTiming) == cudaSuccess && nalloc(n, n->P, n->nP) &&
               nalloc(n, n->G, n->nP) && nalloc(n, n->M1, n->nP) && nalloc(n, n->M2, n->nP) &&
               nalloc(n, n->Wb, n->nWb) && nalloc(n, n->Wt, n->nWt) && nalloc(n, n->loss_d, 1) &&
-              nalloc(n, n->fault, 1) && cudaMallocHost(&n->loss_h, sizeof(float)) == cudaSuccess &&
+              nalloc(n, n->fault, 1) && nalloc(n, n->tcw0, 32 * 27 * 16) && nalloc(n, n->tcw9, 16 * 27 * 32) &&
+              nalloc(n, n->tcw9t, 32 * 27 * 16) && cudaMallocHost(&n->loss_h, sizeof(float)) == cudaSuccess &&
               cudaMallocHost(&n->fault_h, sizeof(int)) == cudaSuccess;
     if (ok) {
         cudaStream_t s = n->stream;

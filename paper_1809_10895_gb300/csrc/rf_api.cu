@@ -845,7 +845,8 @@ rf_status rf_soil_set(rf_ctx *c, const rf_soil *zones, int n_zones, const uint8_
         const double m = s.model == RF_VG ? 1.0 - 1.0 / s.n : 0.0;
         const float nh = (float)s.n, mh = (float)m;
         soils[z] = DevSoil{s.model, s.theta_r, s.theta_s, s.alpha, s.n, m, s.S,
-                           nh, (float)(s.n - (double)nh), mh, (float)(m - (double)mh)};
+                           nh, (float)(s.n - (double)nh), mh, (float)(m - (double)mh),
+                           (s.theta_s - s.theta_r) * s.alpha * s.n * m};
     }
     const long long N = c->g.N;
     std::vector<uint8_t> zone(N, 0);

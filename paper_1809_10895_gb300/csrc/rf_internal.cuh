@@ -53,6 +53,7 @@ struct DevSoil {
     int model;
     double theta_r, theta_s, alpha, n, m, S;
     float n_hi, n_lo, m_hi, m_lo;   // n and m as double-float pairs
+    double cfac;                    // ((theta_s - theta_r) alpha) n m, the factor of C (Eq. 3)
 };
 
 struct Grid {
