@@ -16,6 +16,7 @@
 #include <cuda_bf16.h>
 
 #include "nn.cuh"
+#include "tma.cuh"
 
 namespace rf {
 namespace nn {
@@ -179,6 +180,131 @@ k_conv3d_wgrad(const __nv_bfloat16 *__restrict__ in, const float *__restrict__ d
 #pragma unroll
     for (int e = 0; e < PT; e++) atomicAdd(&dW[(long long)(co0 + e) * KP + tap * CIN + ci], acc[e]);
     if (tap == 13 && threadIdx.x < COUT && db) atomicAdd(&db[threadIdx.x], accb);
+}
+
+// Weight gradient of a 32 -> 32 convolution on the tensor cores (mma.sync
+// m16n8k16, BF16 in, FP32 accumulate):
+//   dW[co][tap 32 + ci] += sum_v G[v][co] X[v + off(tap)][ci],  db[co] += sum_v G[v][co].
+// Blocks walk tiles of 32 x 4 x 2 voxels; the input tile with its halo
+// (34 x 6 x 4) and the gradient tile sit in shared memory (16-byte chunks
+// XOR-swizzled so ldmatrix rows hit distinct banks).  blockIdx.y selects one
+// dz plane of 9 taps; warp w of the block owns tap (dz, w / 3 - 1, w % 3 - 1)
+// and accumulates its 32 x 32 block in registers across all of the block's
+// tiles; one atomic add per weight per block at the end.  K = 16 consecutive
+// x voxels of one (y, z) row per MMA.
+constexpr int WG_TX = 32, WG_TY = 4, WG_TZ = 2;
+constexpr int WG_HX = WG_TX + 2, WG_HY = WG_TY + 2, WG_HZ = WG_TZ + 2;
+constexpr int WG_HALO = WG_HX * WG_HY * WG_HZ;        // 816
+constexpr int WG_INT = WG_TX * WG_TY * WG_TZ;          // 256
+constexpr int WG_THREADS = 9 * 32;
+
+__device__ __forceinline__ int wg_swz(int row, int chunk) { return row * 64 + ((chunk ^ ((row >> 1) & 3)) << 4); }
+
+__device__ __forceinline__ void ldsm_x4_t(uint32_t addr, unsigned (&r)[4])
+{
+    asm volatile("ldmatrix.sync.aligned.m8n8.x4.trans.shared.b16 {%0,%1,%2,%3}, [%4];"
+                 : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3])
+                 : "r"(addr));
+}
+
+__global__ void __launch_bounds__(WG_THREADS)
+k_wgrad_mma32(const __nv_bfloat16 *__restrict__ X, const __nv_bfloat16 *__restrict__ G, int B, int D, int H, int W,
+              long long tiles, int ntx, int nty, int ntz, float *__restrict__ dW, float *__restrict__ db)
+{
+    extern __shared__ __align__(128) unsigned char wg_smem[];
+    unsigned char *sX = wg_smem;                  // WG_HALO x 64 bytes
+    unsigned char *sG = wg_smem + WG_HALO * 64;   // WG_INT x 64 bytes
+    const int warp = threadIdx.x / 32, lane = threadIdx.x % 32, g = lane >> 2, t = lane & 3;
+    const int dz = (int)blockIdx.y - 1, dy = warp / 3 - 1, dx = warp % 3 - 1;
+    const int tap = (dz + 1) * 9 + (dy + 1) * 3 + (dx + 1);
+    const int off = (dz * WG_HY + dy) * WG_HX + dx;
+    float acc[2][4][4];   // [co block][ci block][frag]
+#pragma unroll
+    for (int a = 0; a < 2; a++)
+#pragma unroll
+        for (int b = 0; b < 4; b++)
+#pragma unroll
+            for (int e = 0; e < 4; e++) acc[a][b][e] = 0.0f;
+    float accb = 0.0f;   // bias gradient of channel threadIdx.x (dz = 0 blocks, threads < 32)
+    const uint32_t sXa = smem_addr(sX), sGa = smem_addr(sG);
+    const long long HW = (long long)H * W;
+    for (long long tile = blockIdx.x; tile < tiles; tile += gridDim.x) {
+        long long r = tile;
+        const int tx = (int)(r % ntx);
+        r /= ntx;
+        const int ty = (int)(r % nty);
+        r /= nty;
+        const int tz = (int)(r % ntz);
+        const int b = (int)(r / ntz);
+        const int x0 = tx * WG_TX, y0 = ty * WG_TY, z0 = tz * WG_TZ;
+        __syncthreads();   // the previous tile's shared data is no longer read
+        for (int e = threadIdx.x; e < WG_HALO * 4; e += WG_THREADS) {
+            const int row = e >> 2, ch = e & 3;
+            const int hx = row % WG_HX, hy = (row / WG_HX) % WG_HY, hz = row / (WG_HX * WG_HY);
+            const int x = x0 + hx - 1, y = y0 + hy - 1, z = z0 + hz - 1;
+            uint4 v = make_uint4(0u, 0u, 0u, 0u);
+            if (x >= 0 && x < W && y >= 0 && y < H && z >= 0 && z < D)
+                v = __ldg(reinterpret_cast<const uint4 *>(X + (x + (long long)W * y + HW * (z + (long long)D * b)) * 32) + ch);
+            *reinterpret_cast<uint4 *>(sX + wg_swz(row, ch)) = v;
+        }
+        for (int e = threadIdx.x; e < WG_INT * 4; e += WG_THREADS) {
+            const int row = e >> 2, ch = e & 3;
+            const int ix = row % WG_TX, iy = (row / WG_TX) % WG_TY, iz = row / (WG_TX * WG_TY);
+            const int x = x0 + ix, y = y0 + iy, z = z0 + iz;
+            uint4 v = make_uint4(0u, 0u, 0u, 0u);   // voxels outside the volume add nothing
+            if (x < W && y < H && z < D)
+                v = __ldg(reinterpret_cast<const uint4 *>(G + (x + (long long)W * y + HW * (z + (long long)D * b)) * 32) + ch);
+            *reinterpret_cast<uint4 *>(sG + wg_swz(row, ch)) = v;
+        }
+        __syncthreads();
+        if (dz == 0 && threadIdx.x < 32 && db) {
+            for (int row = 0; row < WG_INT; row++) {
+                const __nv_bfloat16 *gr = reinterpret_cast<const __nv_bfloat16 *>(sG + wg_swz(row, threadIdx.x >> 3));
+                accb += __bfloat162float(gr[threadIdx.x & 7]);
+            }
+        }
+        // 16 K-steps: (iz, iy) rows x two halves of 16 x voxels
+        for (int ks = 0; ks < WG_INT / 16; ks++) {
+            const int iv0 = ks * 16;                                    // interior row of the first voxel
+            const int ix0 = iv0 % WG_TX, iy = (iv0 / WG_TX) % WG_TY, iz = iv0 / (WG_TX * WG_TY);
+            const int hl0 = ((iz + 1) * WG_HY + (iy + 1)) * WG_HX + (ix0 + 1) + off;   // shifted input row
+            // A = G^T (co x v): matrices (co 8c..8c+7, v 0-7), (co +8, v 0-7), (co, v 8-15), (co +8, v 8-15)
+            unsigned af[2][4];
+#pragma unroll
+            for (int cb = 0; cb < 2; cb++) {
+                const int mtx = lane >> 3, rr = lane & 7;
+                const int row = iv0 + rr + ((mtx >> 1) << 3);
+                const int chunk = 2 * cb + (mtx & 1);
+                ldsm_x4_t(sGa + wg_swz(row, chunk), af[cb]);
+            }
+            // B = X shift (v x ci): matrices (v 0-7, ci blk j), (v 8-15, ci blk j), (v 0-7, j+1), (v 8-15, j+1)
+#pragma unroll
+            for (int jb = 0; jb < 2; jb++) {
+                unsigned bf[4];
+                const int mtx = lane >> 3, rr = lane & 7;
+                const int row = hl0 + rr + ((mtx & 1) << 3);
+                const int chunk = 2 * jb + (mtx >> 1);
+                ldsm_x4_t(sXa + wg_swz(row, chunk), bf);
+#pragma unroll
+                for (int cb = 0; cb < 2; cb++) {
+                    const unsigned b0[2] = {bf[0], bf[1]}, b1[2] = {bf[2], bf[3]};
+                    mma_bf16(acc[cb][2 * jb], af[cb], b0);
+                    mma_bf16(acc[cb][2 * jb + 1], af[cb], b1);
+                }
+            }
+        }
+    }
+    // one atomic add per weight (and per bias) per block
+#pragma unroll
+    for (int cb = 0; cb < 2; cb++)
+#pragma unroll
+        for (int j = 0; j < 4; j++)
+#pragma unroll
+            for (int e = 0; e < 4; e++) {
+                const int co = 16 * cb + g + 8 * (e >> 1), ci = 8 * j + 2 * t + (e & 1);
+                atomicAdd(&dW[(long long)co * (27 * 32) + tap * 32 + ci], acc[cb][j][e]);
+            }
+    if (dz == 0 && threadIdx.x < 32 && db) atomicAdd(&db[threadIdx.x], accb);
 }
 
 __global__ void k_relu_bwd(const __nv_bfloat16 *__restrict__ y, const float *__restrict__ dy, float *__restrict__ dx,
@@ -364,6 +490,25 @@ cudaError_t conv3d_wgrad(cudaStream_t s, int cin, int cout, const void *in, cons
     else if (cin == 32 && cout == 32) k_conv3d_wgrad<32, 32><<<grid, 256, 0, s>>>(i, dout, B, D, H, W, dW, db);
     else if (cin == 32 && cout == 8) k_conv3d_wgrad<32, 8><<<grid, 256, 0, s>>>(i, dout, B, D, H, W, dW, db);
     else return cudaErrorInvalidValue;
+    return cudaGetLastError();
+}
+
+cudaError_t wgrad_mma32(cudaStream_t s, const void *X, const void *G, int B, int D, int H, int W, float *dW,
+                        float *db, int num_sms)
+{
+    const int ntx = (W + WG_TX - 1) / WG_TX, nty = (H + WG_TY - 1) / WG_TY, ntz = (D + WG_TZ - 1) / WG_TZ;
+    const long long tiles = (long long)ntx * nty * ntz * B;
+    const long long want = 2LL * num_sms;   // x 3 dz planes: about 6 blocks of 9 warps per SM
+    dim3 grid((unsigned)(tiles < want ? tiles : want), 3);
+    constexpr int smem = (WG_HALO + WG_INT) * 64;   // 68 608 bytes
+    static bool attr = false;
+    if (!attr) {
+        cudaError_t e = cudaFuncSetAttribute(k_wgrad_mma32, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+        if (e != cudaSuccess) return e;
+        attr = true;
+    }
+    k_wgrad_mma32<<<grid, WG_THREADS, smem, s>>>(static_cast<const __nv_bfloat16 *>(X), static_cast<const __nv_bfloat16 *>(G),
+                                              B, D, H, W, tiles, ntx, nty, ntz, dW, db);
     return cudaGetLastError();
 }
 

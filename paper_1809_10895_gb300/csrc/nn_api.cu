@@ -268,6 +268,16 @@ rf_status wgrad(rf_nn *n, cudaStream_t s, int l, const void *in, const float *do
     return RF_OK;
 }
 
+// Weight gradient of a 32 -> 32 layer from its BF16 input and BF16 output
+// gradient, on the tensor cores.
+rf_status wgrad_tc(rf_nn *n, cudaStream_t s, int l, const void *in, const void *g_bf16, int B, int D, int H, int W)
+{
+    const LayerDims &d = n->L[l];
+    n->launches++;
+    NN_CUDA(nn::wgrad_mma32(s, in, g_bf16, B, D, H, W, n->G + d.w, n->G + d.b, n->num_sms));
+    return RF_OK;
+}
+
 // Loss and gradient (into n->G, padded layout); the loss lands in n->loss_d.
 rf_status loss_grad(rf_nn *n, const float *x4, const float *target, const float *mask, int B, int D, int H, int W)
 {
@@ -288,12 +298,12 @@ rf_status loss_grad(rf_nn *n, const float *x4, const float *target, const float 
     n->launches += 2;   // mse, to_bf16
     for (int blk = 3; blk >= 0; blk--) {
         nn::relu_bwd(s, n->ta[blk + 1], n->tgA, n->tgB, MH, nullptr);                  // g2
-        NN_TRY(wgrad(n, s, 2 + 2 * blk, n->tu[blk], n->tgB, B, D, H, W));
         nn::to_bf16(s, n->tgB, n->tgb, MH);
+        NN_TRY(wgrad_tc(n, s, 2 + 2 * blk, n->tu[blk], n->tgb, B, D, H, W));
         NN_TRY(conv(n, s, 2 + 2 * blk, true, n->tgb, nullptr, nullptr, n->tgA, B, D, H, W, 0));   // du
         nn::relu_bwd(s, n->tu[blk], n->tgA, n->tgC, MH, nullptr);                      // g1
-        NN_TRY(wgrad(n, s, 1 + 2 * blk, n->ta[blk], n->tgC, B, D, H, W));
         nn::to_bf16(s, n->tgC, n->tgb, MH);
+        NN_TRY(wgrad_tc(n, s, 1 + 2 * blk, n->ta[blk], n->tgb, B, D, H, W));
         NN_TRY(conv(n, s, 1 + 2 * blk, true, n->tgb, nullptr, nullptr, n->tgA, B, D, H, W, 0));
         nn::add(s, n->tgA, n->tgB, MH);                                                 // + identity branch
         n->launches += 5;   // relu_bwd x2, to_bf16 x2, add
