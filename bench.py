@@ -60,8 +60,8 @@ def parse():
     ap.add_argument("--ws-train-size", type=int, default=128, help="nx = ny of the training box (nz = 64)")
     ap.add_argument("--ws-eval-size", type=int, default=256, help="nx = ny of the held-out boxes (nz = 64)")
     ap.add_argument("--ws-eval-seeds", type=int, default=1, help="held-out seeds evaluated")
-    ap.add_argument("--ws-snapshots", type=int, default=48, help="training snapshots (accepted plain steps)")
-    ap.add_argument("--ws-train-steps", type=int, default=300, help="Adam steps (one full box per step)")
+    ap.add_argument("--ws-snapshots", type=int, default=64, help="training snapshots (accepted plain steps)")
+    ap.add_argument("--ws-train-steps", type=int, default=600, help="Adam steps (one full box per step)")
     ap.add_argument("--ws-eval-hours", type=float, default=1.0, help="simulated hours of each held-out run")
     return ap.parse_args()
 

@@ -182,23 +182,31 @@ k_conv3d_wgrad(const __nv_bfloat16 *__restrict__ in, const float *__restrict__ d
     if (tap == 13 && threadIdx.x < COUT && db) atomicAdd(&db[threadIdx.x], accb);
 }
 
-// Weight gradient of a 32 -> 32 convolution on the tensor cores (mma.sync
-// m16n8k16, BF16 in, FP32 accumulate):
-//   dW[co][tap 32 + ci] += sum_v G[v][co] X[v + off(tap)][ci],  db[co] += sum_v G[v][co].
+// Weight gradient of a convolution on the tensor cores (mma.sync m16n8k16,
+// BF16 in, FP32 accumulate):
+//   dW[co][tap CIN + ci] += sum_v G[v][co] X[v + off(tap)][ci],  db[co] += sum_v G[v][co].
 // Blocks walk tiles of 32 x 4 x 2 voxels; the input tile with its halo
-// (34 x 6 x 4) and the gradient tile sit in shared memory (16-byte chunks
-// XOR-swizzled so ldmatrix rows hit distinct banks).  blockIdx.y selects one
-// dz plane of 9 taps; warp w of the block owns tap (dz, w / 3 - 1, w % 3 - 1)
-// and accumulates its 32 x 32 block in registers across all of the block's
-// tiles; one atomic add per weight per block at the end.  K = 16 consecutive
-// x voxels of one (y, z) row per MMA.
+// (34 x 6 x 4) and the gradient tile sit in shared memory (64-byte rows with
+// their 16-byte chunks XOR-swizzled so ldmatrix rows hit distinct banks;
+// 16-byte rows are conflict-free as they are).  blockIdx.y selects one dz
+// plane of 9 taps; warp w of the block owns tap (dz, w / 3 - 1, w % 3 - 1)
+// and accumulates its COUT x CIN block in registers across all of the
+// block's tiles; one atomic add per weight per block at the end.  K = 16
+// consecutive x voxels of one (y, z) row per MMA; COUT = 8 uses the lower
+// half of the M = 16 rows.
 constexpr int WG_TX = 32, WG_TY = 4, WG_TZ = 2;
 constexpr int WG_HX = WG_TX + 2, WG_HY = WG_TY + 2, WG_HZ = WG_TZ + 2;
 constexpr int WG_HALO = WG_HX * WG_HY * WG_HZ;        // 816
 constexpr int WG_INT = WG_TX * WG_TY * WG_TZ;          // 256
 constexpr int WG_THREADS = 9 * 32;
 
-__device__ __forceinline__ int wg_swz(int row, int chunk) { return row * 64 + ((chunk ^ ((row >> 1) & 3)) << 4); }
+// byte offset of 16-byte chunk `chunk` of row `row` in a tile of `chunks`-chunk rows
+template <int CHUNKS>
+__device__ __forceinline__ int wg_off(int row, int chunk)
+{
+    if constexpr (CHUNKS == 4) return row * 64 + ((chunk ^ ((row >> 1) & 3)) << 4);
+    else return row * 16;
+}
 
 __device__ __forceinline__ void ldsm_x4_t(uint32_t addr, unsigned (&r)[4])
 {
@@ -207,27 +215,40 @@ __device__ __forceinline__ void ldsm_x4_t(uint32_t addr, unsigned (&r)[4])
                  : "r"(addr));
 }
 
-__global__ void __launch_bounds__(WG_THREADS)
-k_wgrad_mma32(const __nv_bfloat16 *__restrict__ X, const __nv_bfloat16 *__restrict__ G, int B, int D, int H, int W,
-              long long tiles, int ntx, int nty, int ntz, float *__restrict__ dW, float *__restrict__ db)
+__device__ __forceinline__ void ldsm_x2_t(uint32_t addr, unsigned (&r)[2])
 {
+    asm volatile("ldmatrix.sync.aligned.m8n8.x2.trans.shared.b16 {%0,%1}, [%2];"
+                 : "=r"(r[0]), "=r"(r[1])
+                 : "r"(addr));
+}
+
+template <int CIN, int COUT>
+__global__ void __launch_bounds__(WG_THREADS)
+k_wgrad_mma(const __nv_bfloat16 *__restrict__ X, const __nv_bfloat16 *__restrict__ G, int B, int D, int H, int W,
+            long long tiles, int ntx, int nty, int ntz, float *__restrict__ dW, float *__restrict__ db)
+{
+    constexpr int XC = CIN / 8, GC = COUT / 8;        // 16-byte chunks per row
+    constexpr int COB = COUT >= 16 ? COUT / 16 : 1;   // M = 16 blocks of output channels
+    constexpr int CIB = CIN / 8;                      // N = 8 blocks of input channels
+    constexpr int KP = (27 * CIN + 15) / 16 * 16;
     extern __shared__ __align__(128) unsigned char wg_smem[];
-    unsigned char *sX = wg_smem;                  // WG_HALO x 64 bytes
-    unsigned char *sG = wg_smem + WG_HALO * 64;   // WG_INT x 64 bytes
+    unsigned char *sX = wg_smem;                       // WG_HALO rows of 16 XC bytes
+    unsigned char *sG = wg_smem + WG_HALO * 16 * XC;   // WG_INT rows of 16 GC bytes
     const int warp = threadIdx.x / 32, lane = threadIdx.x % 32, g = lane >> 2, t = lane & 3;
     const int dz = (int)blockIdx.y - 1, dy = warp / 3 - 1, dx = warp % 3 - 1;
     const int tap = (dz + 1) * 9 + (dy + 1) * 3 + (dx + 1);
     const int off = (dz * WG_HY + dy) * WG_HX + dx;
-    float acc[2][4][4];   // [co block][ci block][frag]
+    float acc[COB][CIB][4];
 #pragma unroll
-    for (int a = 0; a < 2; a++)
+    for (int a = 0; a < COB; a++)
 #pragma unroll
-        for (int b = 0; b < 4; b++)
+        for (int b = 0; b < CIB; b++)
 #pragma unroll
             for (int e = 0; e < 4; e++) acc[a][b][e] = 0.0f;
-    float accb = 0.0f;   // bias gradient of channel threadIdx.x (dz = 0 blocks, threads < 32)
+    float accb = 0.0f;   // bias gradient of channel threadIdx.x (dz = 0 blocks, threads < COUT)
     const uint32_t sXa = smem_addr(sX), sGa = smem_addr(sG);
     const long long HW = (long long)H * W;
+    const int mtx = lane >> 3, rr = lane & 7;
     for (long long tile = blockIdx.x; tile < tiles; tile += gridDim.x) {
         long long r = tile;
         const int tx = (int)(r % ntx);
@@ -238,28 +259,28 @@ k_wgrad_mma32(const __nv_bfloat16 *__restrict__ X, const __nv_bfloat16 *__restri
         const int b = (int)(r / ntz);
         const int x0 = tx * WG_TX, y0 = ty * WG_TY, z0 = tz * WG_TZ;
         __syncthreads();   // the previous tile's shared data is no longer read
-        for (int e = threadIdx.x; e < WG_HALO * 4; e += WG_THREADS) {
-            const int row = e >> 2, ch = e & 3;
+        for (int e = threadIdx.x; e < WG_HALO * XC; e += WG_THREADS) {
+            const int row = e / XC, ch = e % XC;
             const int hx = row % WG_HX, hy = (row / WG_HX) % WG_HY, hz = row / (WG_HX * WG_HY);
             const int x = x0 + hx - 1, y = y0 + hy - 1, z = z0 + hz - 1;
             uint4 v = make_uint4(0u, 0u, 0u, 0u);
             if (x >= 0 && x < W && y >= 0 && y < H && z >= 0 && z < D)
-                v = __ldg(reinterpret_cast<const uint4 *>(X + (x + (long long)W * y + HW * (z + (long long)D * b)) * 32) + ch);
-            *reinterpret_cast<uint4 *>(sX + wg_swz(row, ch)) = v;
+                v = __ldg(reinterpret_cast<const uint4 *>(X + (x + (long long)W * y + HW * (z + (long long)D * b)) * CIN) + ch);
+            *reinterpret_cast<uint4 *>(sX + wg_off<XC>(row, ch)) = v;
         }
-        for (int e = threadIdx.x; e < WG_INT * 4; e += WG_THREADS) {
-            const int row = e >> 2, ch = e & 3;
+        for (int e = threadIdx.x; e < WG_INT * GC; e += WG_THREADS) {
+            const int row = e / GC, ch = e % GC;
             const int ix = row % WG_TX, iy = (row / WG_TX) % WG_TY, iz = row / (WG_TX * WG_TY);
             const int x = x0 + ix, y = y0 + iy, z = z0 + iz;
             uint4 v = make_uint4(0u, 0u, 0u, 0u);   // voxels outside the volume add nothing
             if (x < W && y < H && z < D)
-                v = __ldg(reinterpret_cast<const uint4 *>(G + (x + (long long)W * y + HW * (z + (long long)D * b)) * 32) + ch);
-            *reinterpret_cast<uint4 *>(sG + wg_swz(row, ch)) = v;
+                v = __ldg(reinterpret_cast<const uint4 *>(G + (x + (long long)W * y + HW * (z + (long long)D * b)) * COUT) + ch);
+            *reinterpret_cast<uint4 *>(sG + wg_off<GC>(row, ch)) = v;
         }
         __syncthreads();
-        if (dz == 0 && threadIdx.x < 32 && db) {
+        if (dz == 0 && threadIdx.x < COUT && db) {
             for (int row = 0; row < WG_INT; row++) {
-                const __nv_bfloat16 *gr = reinterpret_cast<const __nv_bfloat16 *>(sG + wg_swz(row, threadIdx.x >> 3));
+                const __nv_bfloat16 *gr = reinterpret_cast<const __nv_bfloat16 *>(sG + wg_off<GC>(row, threadIdx.x >> 3));
                 accb += __bfloat162float(gr[threadIdx.x & 7]);
             }
         }
@@ -268,43 +289,52 @@ k_wgrad_mma32(const __nv_bfloat16 *__restrict__ X, const __nv_bfloat16 *__restri
             const int iv0 = ks * 16;                                    // interior row of the first voxel
             const int ix0 = iv0 % WG_TX, iy = (iv0 / WG_TX) % WG_TY, iz = iv0 / (WG_TX * WG_TY);
             const int hl0 = ((iz + 1) * WG_HY + (iy + 1)) * WG_HX + (ix0 + 1) + off;   // shifted input row
-            // A = G^T (co x v): matrices (co 8c..8c+7, v 0-7), (co +8, v 0-7), (co, v 8-15), (co +8, v 8-15)
-            unsigned af[2][4];
+            // A = G^T (co x v): matrices (co lo, v 0-7), (co hi, v 0-7), (co lo, v 8-15), (co hi, v 8-15)
+            unsigned af[COB][4];
+            if constexpr (COUT >= 16) {
 #pragma unroll
-            for (int cb = 0; cb < 2; cb++) {
-                const int mtx = lane >> 3, rr = lane & 7;
-                const int row = iv0 + rr + ((mtx >> 1) << 3);
-                const int chunk = 2 * cb + (mtx & 1);
-                ldsm_x4_t(sGa + wg_swz(row, chunk), af[cb]);
+                for (int cb = 0; cb < COB; cb++)
+                    ldsm_x4_t(sGa + wg_off<GC>(iv0 + rr + ((mtx >> 1) << 3), 2 * cb + (mtx & 1)), af[cb]);
+            } else {
+                unsigned a2[2];   // co 0-7 only; rows 8-15 of the M = 16 block are zero
+                ldsm_x2_t(sGa + wg_off<GC>(iv0 + rr + ((mtx & 1) << 3), 0), a2);
+                af[0][0] = a2[0];
+                af[0][1] = 0u;
+                af[0][2] = a2[1];
+                af[0][3] = 0u;
             }
             // B = X shift (v x ci): matrices (v 0-7, ci blk j), (v 8-15, ci blk j), (v 0-7, j+1), (v 8-15, j+1)
+            if constexpr (CIB >= 2) {
 #pragma unroll
-            for (int jb = 0; jb < 2; jb++) {
-                unsigned bf[4];
-                const int mtx = lane >> 3, rr = lane & 7;
-                const int row = hl0 + rr + ((mtx & 1) << 3);
-                const int chunk = 2 * jb + (mtx >> 1);
-                ldsm_x4_t(sXa + wg_swz(row, chunk), bf);
+                for (int jb = 0; jb < CIB / 2; jb++) {
+                    unsigned bf[4];
+                    ldsm_x4_t(sXa + wg_off<XC>(hl0 + rr + ((mtx & 1) << 3), 2 * jb + (mtx >> 1)), bf);
 #pragma unroll
-                for (int cb = 0; cb < 2; cb++) {
-                    const unsigned b0[2] = {bf[0], bf[1]}, b1[2] = {bf[2], bf[3]};
-                    mma_bf16(acc[cb][2 * jb], af[cb], b0);
-                    mma_bf16(acc[cb][2 * jb + 1], af[cb], b1);
+                    for (int cb = 0; cb < COB; cb++) {
+                        const unsigned b0[2] = {bf[0], bf[1]}, b1[2] = {bf[2], bf[3]};
+                        mma_bf16(acc[cb][2 * jb], af[cb], b0);
+                        mma_bf16(acc[cb][2 * jb + 1], af[cb], b1);
+                    }
                 }
+            } else {
+                unsigned bf[2];
+                ldsm_x2_t(sXa + wg_off<XC>(hl0 + rr + ((mtx & 1) << 3), 0), bf);
+#pragma unroll
+                for (int cb = 0; cb < COB; cb++) mma_bf16(acc[cb][0], af[cb], bf);
             }
         }
     }
     // one atomic add per weight (and per bias) per block
 #pragma unroll
-    for (int cb = 0; cb < 2; cb++)
+    for (int cb = 0; cb < COB; cb++)
 #pragma unroll
-        for (int j = 0; j < 4; j++)
+        for (int j = 0; j < CIB; j++)
 #pragma unroll
             for (int e = 0; e < 4; e++) {
                 const int co = 16 * cb + g + 8 * (e >> 1), ci = 8 * j + 2 * t + (e & 1);
-                atomicAdd(&dW[(long long)co * (27 * 32) + tap * 32 + ci], acc[cb][j][e]);
+                if (co < COUT) atomicAdd(&dW[(long long)co * KP + tap * CIN + ci], acc[cb][j][e]);
             }
-    if (dz == 0 && threadIdx.x < 32 && db) atomicAdd(&db[threadIdx.x], accb);
+    if (dz == 0 && threadIdx.x < COUT && db) atomicAdd(&db[threadIdx.x], accb);
 }
 
 __global__ void k_relu_bwd(const __nv_bfloat16 *__restrict__ y, const float *__restrict__ dy, float *__restrict__ dx,
@@ -493,23 +523,34 @@ cudaError_t conv3d_wgrad(cudaStream_t s, int cin, int cout, const void *in, cons
     return cudaGetLastError();
 }
 
-cudaError_t wgrad_mma32(cudaStream_t s, const void *X, const void *G, int B, int D, int H, int W, float *dW,
-                        float *db, int num_sms)
+template <int CIN, int COUT>
+static cudaError_t launch_wgrad_mma(cudaStream_t s, const void *X, const void *G, int B, int D, int H, int W,
+                                    float *dW, float *db, int num_sms)
 {
     const int ntx = (W + WG_TX - 1) / WG_TX, nty = (H + WG_TY - 1) / WG_TY, ntz = (D + WG_TZ - 1) / WG_TZ;
     const long long tiles = (long long)ntx * nty * ntz * B;
-    const long long want = 2LL * num_sms;   // x 3 dz planes: about 6 blocks of 9 warps per SM
+    const long long want = 2LL * num_sms;   // x 3 dz planes
     dim3 grid((unsigned)(tiles < want ? tiles : want), 3);
-    constexpr int smem = (WG_HALO + WG_INT) * 64;   // 68 608 bytes
+    constexpr int smem = WG_HALO * 2 * CIN + WG_INT * 2 * COUT;
     static bool attr = false;
     if (!attr) {
-        cudaError_t e = cudaFuncSetAttribute(k_wgrad_mma32, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+        cudaError_t e = cudaFuncSetAttribute(k_wgrad_mma<CIN, COUT>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
         if (e != cudaSuccess) return e;
         attr = true;
     }
-    k_wgrad_mma32<<<grid, WG_THREADS, smem, s>>>(static_cast<const __nv_bfloat16 *>(X), static_cast<const __nv_bfloat16 *>(G),
-                                              B, D, H, W, tiles, ntx, nty, ntz, dW, db);
+    k_wgrad_mma<CIN, COUT><<<grid, WG_THREADS, smem, s>>>(static_cast<const __nv_bfloat16 *>(X),
+                                                          static_cast<const __nv_bfloat16 *>(G), B, D, H, W, tiles,
+                                                          ntx, nty, ntz, dW, db);
     return cudaGetLastError();
+}
+
+cudaError_t wgrad_mma(cudaStream_t s, int cin, int cout, const void *X, const void *G, int B, int D, int H, int W,
+                      float *dW, float *db, int num_sms)
+{
+    if (cin == 32 && cout == 32) return launch_wgrad_mma<32, 32>(s, X, G, B, D, H, W, dW, db, num_sms);
+    if (cin == 8 && cout == 32) return launch_wgrad_mma<8, 32>(s, X, G, B, D, H, W, dW, db, num_sms);
+    if (cin == 32 && cout == 8) return launch_wgrad_mma<32, 8>(s, X, G, B, D, H, W, dW, db, num_sms);
+    return cudaErrorInvalidValue;
 }
 
 void relu_bwd(cudaStream_t s, const void *y, const float *dy, float *dx, long long n, const float *add)

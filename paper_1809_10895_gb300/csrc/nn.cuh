@@ -44,11 +44,12 @@ bool conv3d_tc_available(const void *in, const void *Wb);
 // dst[n][tap cinp + c] = src[n][tap cin + c] (src rows of kp_src), zero for
 // n >= n_src or c >= cin.
 void prep_tc_weights(cudaStream_t s, const void *src, int n_src, int cin, int kp_src, int nout, int cinp, void *dst);
-// Weight (and bias) gradient of a 32 -> 32 convolution on the tensor cores
-// (mma.sync): X = the layer's BF16 input, G = the BF16 output gradient, both
-// [voxel][32]; dW [32][864], db [32] are accumulated into.
-cudaError_t wgrad_mma32(cudaStream_t s, const void *X, const void *G, int B, int D, int H, int W, float *dW,
-                        float *db, int num_sms);
+// Weight (and bias) gradient of a convolution on the tensor cores (mma.sync):
+// X = the layer's BF16 input [voxel][cin], G = the BF16 output gradient
+// [voxel][cout]; dW [cout][round16(27 cin)], db [cout] are accumulated into.
+// (cin, cout) in {(32, 32), (8, 32), (32, 8)}.
+cudaError_t wgrad_mma(cudaStream_t s, int cin, int cout, const void *X, const void *G, int B, int D, int H, int W,
+                      float *dW, float *db, int num_sms);
 void relu_bwd(cudaStream_t s, const void *y, const float *dy, float *dx, long long n, const float *add);
 void to_bf16(cudaStream_t s, const float *a, void *b, long long n);
 void add(cudaStream_t s, float *a, const float *b, long long n);

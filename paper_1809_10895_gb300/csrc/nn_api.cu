@@ -274,7 +274,7 @@ rf_status wgrad_tc(rf_nn *n, cudaStream_t s, int l, const void *in, const void *
 {
     const LayerDims &d = n->L[l];
     n->launches++;
-    NN_CUDA(nn::wgrad_mma32(s, in, g_bf16, B, D, H, W, n->G + d.w, n->G + d.b, n->num_sms));
+    NN_CUDA(nn::wgrad_mma(s, d.cinp, d.coutp, in, g_bf16, B, D, H, W, n->G + d.w, n->G + d.b, n->num_sms));
     return RF_OK;
 }
 
@@ -292,8 +292,8 @@ rf_status loss_grad(rf_nn *n, const float *x4, const float *target, const float 
     NN_CUDA(cudaMemsetAsync(n->G, 0, sizeof(float) * n->nP, s));
     const long long MH = M * nn::C_HID;
     // output convolution
-    NN_TRY(wgrad(n, s, 9, n->ta[4], n->tdy, B, D, H, W));
     nn::to_bf16(s, n->tdy, n->tdyb, M * nn::C_OUT_P);
+    NN_TRY(wgrad_tc(n, s, 9, n->ta[4], n->tdyb, B, D, H, W));
     NN_TRY(conv(n, s, 9, true, n->tdyb, nullptr, nullptr, n->tgA, B, D, H, W, 0));   // dL/da4
     n->launches += 2;   // mse, to_bf16
     for (int blk = 3; blk >= 0; blk--) {
@@ -309,8 +309,9 @@ rf_status loss_grad(rf_nn *n, const float *x4, const float *target, const float 
         n->launches += 5;   // relu_bwd x2, to_bf16 x2, add
     }
     nn::relu_bwd(s, n->ta[0], n->tgA, n->tgC, MH, nullptr);
-    NN_TRY(wgrad(n, s, 0, n->tx, n->tgC, B, D, H, W));
-    n->launches += 1;   // relu_bwd
+    nn::to_bf16(s, n->tgC, n->tgb, MH);
+    NN_TRY(wgrad_tc(n, s, 0, n->tx, n->tgb, B, D, H, W));
+    n->launches += 2;   // relu_bwd, to_bf16
     return RF_OK;
 }
 

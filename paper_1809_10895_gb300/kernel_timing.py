@@ -5,9 +5,11 @@ network), for profiling one kernel at a time.
     python -m paper_1809_10895_gb300.kernel_timing box --kinds assemble,resid64
     python -m paper_1809_10895_gb300.kernel_timing watershed --nx 512 --ny 256 --kinds cg32_spmv
     python -m paper_1809_10895_gb300.kernel_timing network --nx 128 --ny 128 --nz 64
+    python -m paper_1809_10895_gb300.kernel_timing training --nx 128 --ny 128 --nz 64
 
 Prints one JSON line: per kind the mean launch time and the algorithmic bytes
-per launch (solver kernels) or the forward time and TFLOP/s (network).
+per launch (solver kernels), or the forward / training-step time and TFLOP/s
+(network).
 """
 from __future__ import annotations
 
@@ -21,7 +23,7 @@ sys.path.insert(0, os.path.dirname(os.path.dirname(os.path.abspath(__file__))))
 
 def main(argv=None):
     ap = argparse.ArgumentParser()
-    ap.add_argument("workload", choices=["box", "watershed", "network"])
+    ap.add_argument("workload", choices=["box", "watershed", "network", "training"])
     ap.add_argument("--nx", type=int, default=None)
     ap.add_argument("--ny", type=int, default=None)
     ap.add_argument("--nz", type=int, default=64)
@@ -38,7 +40,26 @@ def main(argv=None):
     rf.load()
     torch.cuda.set_device(0)
     out = {"workload": a.workload}
-    if a.workload == "network":
+    if a.workload == "training":
+        nx, ny = a.nx or 128, a.ny or 128
+        shape = (1, a.nz, ny, nx)
+        gen = torch.Generator(device="cuda").manual_seed(0)
+        x = torch.randn(shape + (4,), device="cuda", generator=gen)
+        t = torch.randn(shape, device="cuda", generator=gen)
+        net = rf.Network()
+        net.set_params(W.nn_init_params(1))
+        for _ in range(2):
+            net.train_step(x, t, want_loss=False)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(net.stream)
+        for _ in range(a.reps):
+            net.train_step(x, t, want_loss=False)
+        e1.record(net.stream)
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1) / a.reps
+        flop = 3 * 2.0 * 27 * (8 * 32 + 8 * 32 * 32 + 32 * 8) * x[..., 0].numel()
+        out.update(shape=list(shape), train_step_ms=ms, tflops_3x_forward=flop / ms / 1e9)
+    elif a.workload == "network":
         nx, ny = a.nx or 128, a.ny or 128
         shape = (1, a.nz, ny, nx)
         x = torch.randn(shape + (4,), device="cuda", generator=torch.Generator(device="cuda").manual_seed(0))
