@@ -57,6 +57,8 @@ def parse():
     ap.add_argument("--no-ensemble", action="store_true", help="skip the batched-ensemble leg")
     ap.add_argument("--ensemble-window", type=float, default=600.0, help="simulated seconds of the ensemble leg")
     ap.add_argument("--no-warmstart", action="store_true", help="skip the learned warm-start leg")
+    ap.add_argument("--no-configs", action="store_true", help="skip the column and watershed step legs")
+    ap.add_argument("--config-steps", type=int, default=20, help="timed steps of the watershed step leg")
     ap.add_argument("--ws-train-size", type=int, default=128, help="nx = ny of the training box (nz = 64)")
     ap.add_argument("--ws-eval-size", type=int, default=256, help="nx = ny of the held-out boxes (nz = 64)")
     ap.add_argument("--ws-eval-seeds", type=int, default=1, help="held-out seeds evaluated")
@@ -326,6 +328,12 @@ def native(args):
     if not args.no_warmstart:
         wsl = warmstart_leg(args, rank, rf, W, peaks)
 
+    # ---- the other synthetic configurations, whole steps: the 1-D column
+    # (plain FP64 path) and the 512x512x64 watershed (mixed, Jacobi and MG)
+    cfg = None
+    if not args.no_configs:
+        cfg = configs_leg(args, rank, rf, W)
+
     # ---- end to end through host buffers
     e2e = None
     if not args.no_e2e:
@@ -374,6 +382,7 @@ def native(args):
             "pcg_hbm": pcg_hbm,
             "ensemble": ens,
             "warmstart": wsl,
+            "other_configs": cfg,
         }
         if not args.no_baseline:
             line["cpu_baseline"] = cpu_baseline(case)
@@ -381,6 +390,44 @@ def native(args):
     if world > 1:
         import torch.distributed as dist
         dist.destroy_process_group()
+
+
+def configs_leg(args, rank, rf, W):
+    import torch
+
+    def timed_steps(s, n):
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(s.stream)
+        picard = 0
+        for _ in range(n):
+            picard += s.step().picard
+        b.record(s.stream)
+        torch.cuda.synchronize()
+        return a.elapsed_time(b), picard
+
+    out = {}
+    col = W.infiltration_column()
+    s = rf.Solver.from_case(col, precision="fp64")
+    for _ in range(5):
+        s.step()
+    n = 400
+    ms, pic = timed_steps(s, n)
+    out["infiltration_column_1x1x200"] = {"precision": "fp64", "steps": n, "ms_per_step": ms / n,
+                                          "picard_per_step": pic / n, "value": n * col.N / (ms / 1e3), "unit": UNIT,
+                                          "note": "200 cells: launch- and synchronisation-bound"}
+    s.close()
+    ws = W.watershed(512, 512, 64, seed=args.seed + rank, hours=24)
+    for pc in ("jacobi", "mg"):
+        s = rf.Solver.from_case(ws, precision="mixed", precond=pc)
+        for _ in range(3):
+            s.step()
+        n = args.config_steps
+        ms, pic = timed_steps(s, n)
+        out[f"watershed_512x512x64_{pc}"] = {"precision": "mixed", "precond": pc, "steps": n, "ms_per_step": ms / n,
+                                              "picard_per_step": pic / n, "active_cells": ws.n_active(),
+                                              "value": n * ws.n_active() / (ms / 1e3), "unit": UNIT}
+        s.close()
+    return out
 
 
 def warmstart_leg(args, rank, rf, W, peaks):

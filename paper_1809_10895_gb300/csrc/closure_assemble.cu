@@ -222,19 +222,25 @@ k_assemble(Grid g, const DevSoil *__restrict__ soils, const uint8_t *__restrict_
 // Water balance of the accepted step's last linear system (x = h^{n+1}):
 // sum c dt (x - h^n), sum V (theta*(x) - theta*(h^n)), and dt times the
 // boundary inflow / outflow of that system, split per face by sign.
+// After a Picard attempt (ctl given): only when it converged; the final
+// iterate and the K of its last system sit in the buffers of the last
+// iteration's half: x_odd / K_odd after an odd number of iterations, x_even /
+// K_even after an even number.
 __global__ void __launch_bounds__(RED_THREADS)
 k_mass_balance(Grid g, const DevSoil *__restrict__ soils, const uint8_t *__restrict__ zone,
                const double *__restrict__ Ks, const uint8_t *__restrict__ flags,
-               const StepParams *__restrict__ spp, const double *__restrict__ x, const double *__restrict__ hn,
-               const double *__restrict__ c, const double *__restrict__ Kold, const double *__restrict__ thx,
+               const StepParams *__restrict__ spp, const double *__restrict__ x_odd,
+               const double *__restrict__ x_even, const double *__restrict__ hn, const double *__restrict__ c,
+               const double *__restrict__ K_odd, const double *__restrict__ K_even, const double *__restrict__ thx,
                const double *__restrict__ thn, double *partials, unsigned int *ticket, StepResults *res,
-               PicardCtl *ctl)
+               const PicardCtl *ctl)
 {
     count_launch(g, KK_MASS_BALANCE);
-    // inside a Picard graph: only after the iteration that converged (every
-    // block reads the flag before the last block clears it)
-    if (ctl && !ctl->mb_pending) return;
+    if (ctl && !ctl->conv) return;
     count_work(g, KK_MASS_BALANCE);
+    const bool odd = !ctl || (ctl->it & 1);
+    const double *__restrict__ x = odd ? x_odd : x_even;
+    const double *__restrict__ Kold = odd ? K_odd : K_even;
     const double dt = spp->dt;
     double v[4] = {0.0, 0.0, 0.0, 0.0};   // lin, dS, in, out
     const long long stride = (long long)gridDim.x * blockDim.x;
@@ -255,7 +261,6 @@ k_mass_balance(Grid g, const DevSoil *__restrict__ soils, const uint8_t *__restr
         res->dstore = v[1];
         res->bnd_in = v[2];
         res->bnd_out = v[3];
-        if (ctl) ctl->mb_pending = 0;
     }
 }
 
@@ -346,13 +351,13 @@ void launch_accept(cudaStream_t s, int nblk, const Grid &g, const double *x_fina
 }
 
 void launch_mass_balance(cudaStream_t s, int nblk, const Grid &g, const DevSoil *soils, const uint8_t *zone,
-                         const double *Ks, const uint8_t *flags, const StepParams *sp, const double *x,
-                         const double *hn, const double *c, const double *Kold, const double *theta_x,
-                         const double *theta_n, double *partials, unsigned int *ticket, StepResults *res,
-                         PicardCtl *ctl)
+                         const double *Ks, const uint8_t *flags, const StepParams *sp, const double *x_odd,
+                         const double *x_even, const double *hn, const double *c, const double *K_odd,
+                         const double *K_even, const double *theta_x, const double *theta_n, double *partials,
+                         unsigned int *ticket, StepResults *res, const PicardCtl *ctl)
 {
-    k_mass_balance<<<nblk, RED_THREADS, 0, s>>>(g, soils, zone, Ks, flags, sp, x, hn, c, Kold, theta_x, theta_n,
-                                                partials, ticket, res, ctl);
+    k_mass_balance<<<nblk, RED_THREADS, 0, s>>>(g, soils, zone, Ks, flags, sp, x_odd, x_even, hn, c, K_odd, K_even,
+                                                theta_x, theta_n, partials, ticket, res, ctl);
 }
 
 void launch_storage(cudaStream_t s, int nblk, const Grid &g, const uint8_t *flags, const double *theta,

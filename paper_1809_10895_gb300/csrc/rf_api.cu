@@ -464,10 +464,16 @@ rf_status build_picard_graph(rf_ctx *c)
         const CgScal *cnt = c->prm.precision == RF_PREC_FP64 ? c->sc : c->sc_in;
         launch_closure_picard(s, nb, g, c->soils, c->zone, c->Ks, c->flags, x, hk, c->theta_k, Kout, c->Can,
                               c->partials, c->ticket, c->ctl, stat, cnt, cp);
-        launch_mass_balance(s, nb, g, c->soils, c->zone, c->Ks, c->flags, c->sp, x, c->h, c->c, Kin, c->theta_k,
-                            c->theta_n, c->partials, c->ticket, c->res, c->ctl);
         RF_TRY(cap_end(c, deps));
     }
+    // water balance of the converged system, once, after the Picard loop: an
+    // odd iteration count ends in half 0 (iterate in x, system K in K[0]),
+    // an even one in half 1 (iterate in hk, K[1])
+    std::vector<cudaGraphNode_t> after;
+    RF_TRY(cap_begin(c, G, {wp}));
+    launch_mass_balance(s, nb, g, c->soils, c->zone, c->Ks, c->flags, c->sp, c->x, c->hk, c->h, c->c, c->K[0],
+                        c->K[1], c->theta_k, c->theta_n, c->partials, c->ticket, c->res, c->ctl);
+    RF_TRY(cap_end(c, after));
     CUDA_TRY(cudaGraphInstantiate(&c->picard_exec, G, 0));
     return RF_OK;
 }

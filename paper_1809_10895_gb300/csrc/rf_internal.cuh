@@ -107,7 +107,7 @@ struct PicardCtl {
     int it;            // iterations done (linear solves)
     int conv, fail, done;
     int cg_total;      // CG iterations over the attempt
-    int mb_pending;    // water balance of the converged system still to reduce
+    int mb_pending;    // (unused)
     int pad;
 };
 
@@ -269,10 +269,10 @@ void launch_assemble(cudaStream_t s, int nblk, const Grid &g, const DevSoil *soi
                      unsigned int *ticket = nullptr);
 
 void launch_mass_balance(cudaStream_t s, int nblk, const Grid &g, const DevSoil *soils, const uint8_t *zone,
-                         const double *Ks, const uint8_t *flags, const StepParams *sp, const double *x,
-                         const double *hn, const double *c, const double *Kold, const double *theta_x,
-                         const double *theta_n, double *partials, unsigned int *ticket, StepResults *res,
-                         PicardCtl *ctl);
+                         const double *Ks, const uint8_t *flags, const StepParams *sp, const double *x_odd,
+                         const double *x_even, const double *hn, const double *c, const double *K_odd,
+                         const double *K_even, const double *theta_x, const double *theta_n, double *partials,
+                         unsigned int *ticket, StepResults *res, const PicardCtl *ctl);
 
 void launch_storage(cudaStream_t s, int nblk, const Grid &g, const uint8_t *flags, const double *theta,
                     double *partials, unsigned int *ticket, StepResults *res);
