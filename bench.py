@@ -301,7 +301,7 @@ def native(args):
     if not args.no_ensemble:
         cases = W.ensemble(256, seed=args.seed + rank)
         e = rf.Ensemble.from_cases(cases, precision="mixed")
-        cluster, probe_ms = e.tune(min(60.0, args.ensemble_window))
+        cluster, cta_threads, n_wide, probe_ms = e.tune(min(10.0, args.ensemble_window))
         barrier()
         ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         ev0.record(e.stream)
@@ -313,7 +313,8 @@ def native(args):
         stats = [e.get(i, want_h=False)[1] for i in range(len(cases))]
         cell_steps = sum(st["steps"] * st["cells"] for st in stats)
         ens = {"workload": "ensemble_256_uneven", "instances": len(cases), "cells": sum(c.N for c in cases),
-               "simulated_window_s": args.ensemble_window, "cluster_ctas": cluster, "tuner_probe_ms": probe_ms,
+               "simulated_window_s": args.ensemble_window, "cluster_ctas": cluster, "cta_threads": cta_threads, "wide_instances": n_wide,
+               "tuner_probe_ms": probe_ms,
                "kernel_ms": ens_ms, "cell_timesteps": cell_steps, "value": cell_steps / (ens_ms * 1e-3),
                "unit": UNIT, "steps_total": sum(st["steps"] for st in stats),
                "picard_total": sum(st["picard_iters"] for st in stats),

@@ -272,6 +272,8 @@ typedef struct rf_ens_stats {
     int status;                           /* RF_OK, RF_ERR_DT_MIN, RF_ERR_DEVICE_TIMEOUT */
     long long cells;
     double storage0, inflow_cum, outflow_cum, closure_abs, nonlinear_defect_cum;
+    double busy_s;                        /* device wall time the instance held its CTAs (all runs) */
+    int ctas;                             /* CTAs that ran it in the last run (cluster size or 1) */
 } rf_ens_stats;
 
 /* Create an ensemble (instances copied; params as for rf_mesh_create; the
@@ -279,17 +281,31 @@ typedef struct rf_ens_stats {
 rf_status rf_ens_create(const rf_ens_instance *inst, int n, const rf_solver_params *params, void *cuda_stream,
                         const rf_allocator *alloc, rf_ens **out);
 void rf_ens_destroy(rf_ens *ens);
-/* Cluster size (CTAs per work unit): 1, 2, 4 or 8. */
-rf_status rf_ens_set_tiling(rf_ens *ens, int cluster);
+/* Tiling of the work units: cluster size 1, 2, 4 or 8 CTAs and CTA size
+ * (threads) 128, 256 or 512 (smaller CTAs put more instances on an SM at
+ * once).  Default: clusters of 1 CTA of 512 threads. */
+rf_status rf_ens_set_tiling(rf_ens *ens, int cluster, int threads);
+/* Schedule of the work queue: order[k] = the instance (user index) popped
+ * k-th, a permutation of 0..n-1 (NULL: largest instances first, the
+ * default); the first n_wide of them run on a whole cluster each, the rest on
+ * one CTA each (n_wide < 0 or >= n: all on clusters, the default).  Applies
+ * to later runs; the state is untouched. */
+rf_status rf_ens_set_schedule(rf_ens *ens, const int *order, int n_wide);
 /* Advance every instance to t_end (one graph launch; synchronises). */
 rf_status rf_ens_run(rf_ens *ens, double t_end);
 /* State of instance i (user order): h (host, its nx*ny*nz cells, or NULL). */
 rf_status rf_ens_get(rf_ens *ens, int i, double *h, rf_ens_stats *stats);
 /* Return every instance to its initial state. */
 rf_status rf_ens_reset(rf_ens *ens);
-/* Tuner: time each cluster size from the initial state to t_probe, keep the
- * fastest, and reset to the initial state. */
-rf_status rf_ens_tune(rf_ens *ens, double t_probe, int *best_cluster, double *best_ms);
+/* Tuner: from the initial state to t_probe, time every tiling that fits
+ * (cluster 1, 2, 4, 8 x 256 or 512 threads) with every instance on a whole
+ * work unit, recording each instance's run time at each width; predict with
+ * a list-scheduling model of the persistent queue (heaviest first) the
+ * makespan of every (tiling, n_wide); time the three best predictions; keep
+ * the fastest measured tiling and schedule, and reset to the initial state.
+ * Outputs may be NULL. */
+rf_status rf_ens_tune(rf_ens *ens, double t_probe, int *best_cluster, int *best_threads, int *best_wide,
+                      double *best_ms);
 
 /* ---- a linear solve that allocates no device memory ----------------------
  *

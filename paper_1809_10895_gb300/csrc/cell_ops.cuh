@@ -108,31 +108,6 @@ __device__ __forceinline__ double apply64(const Grid &g, long long p, const doub
     return acc;
 }
 
-// FP32 operator with faces recomputed from FP32 K.
-template <class Get>
-__device__ __forceinline__ float apply32(const Grid &g, long long p, const float *__restrict__ K32,
-                                         const float *__restrict__ cb32, Get get)
-{
-    int i, j, k;
-    cell_ijk(g, p, i, j, k);
-    const float KP = K32[p];
-    const float vP = get(p);
-    float acc = cb32[p] * vP;
-    auto face = [&](bool inside, long long q, float w) {
-        if (!inside) return;
-        const float KN = K32[q];
-        if (KN < 0.0f) return;
-        acc = fmaf(w * 0.5f * (KP + KN), vP - get(q), acc);
-    };
-    face(i > 0, p - 1, g.w32[0]);
-    face(i < g.nx - 1, p + 1, g.w32[0]);
-    face(j > 0, p - g.nx, g.w32[1]);
-    face(j < g.ny - 1, p + g.nx, g.w32[1]);
-    face(k > 0, p - g.sxy, g.w32[2]);
-    face(k < g.nz - 1, p + g.sxy, g.w32[2]);
-    return acc;
-}
-
 // One cell of the Picard system (Sec. 2.2; see k_assemble):
 //   c = V C^k / dt (chord slope of theta*, or C(h^k) when |h^k - h^n| <= eps),
 //   interior faces T_f = (K_P + K_N)/2 A_f/d_f with explicit gravity,

@@ -1,15 +1,21 @@
 // ensemble.cu -- many independent Richards problems of uneven size in one
 // persistent kernel launch (captured in a CUDA graph).
 //
-// Work unit: a thread-block cluster of CL CTAs (CL chosen by the tuner).  A
-// cluster pops an instance from a device queue (instances are ordered largest
-// first), splits its cells across its CTAs, and runs that instance's whole
-// time integration -- EBATS steps, Picard iterations, PCG -- with the same
-// per-cell arithmetic as the single-domain kernels (cell_ops.cuh).  Global
-// reductions of the single-domain path become cluster reductions: each CTA
-// reduces in shared memory, the cluster barrier publishes the partials, and
-// every CTA folds them in rank order through distributed shared memory, so all
-// CTAs hold bit-identical scalars and take identical control decisions.
+// Work unit: a thread-block cluster of CL CTAs (CL chosen by the tuner) for
+// the heavy instances, a single CTA for the others.  The work queue is a
+// schedule: a list of instances, the "wide" ones first (by default every
+// instance, largest first; the tuner orders it by measured work).  While the
+// queue yields wide instances, a cluster pops one, splits its cells across
+// its CTAs, and runs that instance's whole time integration -- EBATS steps,
+// Picard iterations, PCG -- with the same per-cell arithmetic as the
+// single-domain kernels (cell_ops.cuh).  Global reductions of the
+// single-domain path become cluster reductions: each CTA reduces in shared
+// memory, the cluster barrier publishes the partials, and every CTA folds
+// them in the same order through distributed shared memory, so all CTAs hold
+// bit-identical scalars and take identical control decisions.  Once the
+// queue reaches the other instances the cluster's CTAs go solo: each pops and
+// runs instances on its own, with block barriers and block reductions in
+// place of the cluster ones.
 // Every loop is bounded: PCG by max_it, defect correction by outer_max_it,
 // Picard by n_max, EBATS by dt_min, and each instance by a step budget.
 #include <cooperative_groups.h>
@@ -25,56 +31,303 @@ namespace rf {
 namespace {
 
 constexpr int RB_SLOTS = 8;
+constexpr int RB_WARPS = 16;   // warps of the largest CTA (512 threads)
 
 struct ClusterCtx {
     cg::cluster_group cl;
-    int rank, ncta;
-    double (*red)[RB_SLOTS];   // shared [2][RB_SLOTS]
-    int rb;                    // reduction double-buffer index (same in every CTA)
+    int rank, ncta;                        // rank 0, ncta 1 when solo
+    bool solo;                             // this CTA runs its instance alone
+    double (*red)[RB_SLOTS][RB_WARPS];     // shared [2][RB_SLOTS][RB_WARPS]: per-warp FP64 partials
+    double (*bc)[RB_SLOTS];                // shared [2][RB_SLOTS]: FP64 totals for the whole CTA
+    float (*redf)[RB_SLOTS][RB_WARPS];     // shared [2][RB_SLOTS][RB_WARPS]: per-warp FP32 partials
+    int rb;                                // reduction double-buffer index (same in every CTA)
 };
 
-// Sum (or max) NV values over all threads of the cluster; every thread gets
-// the totals.  Contains a cluster barrier.
+// Barrier over the threads that share the current instance.
+__device__ __forceinline__ void unit_sync(ClusterCtx &C)
+{
+    if (C.solo) __syncthreads();
+    else C.cl.sync();
+}
+
+struct FSum {
+    __device__ static float id() { return 0.0f; }
+    __device__ static float op(float a, float b) { return a + b; }
+};
+
+// Butterfly (xor) reduction: every lane ends with the same bits, because
+// each level combines the same two operands in every lane of a pair.
+template <class Op, class T>
+__device__ __forceinline__ T warp_allreduce(T x)
+{
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) x = Op::op(x, __shfl_xor_sync(0xffffffffu, x, o));
+    return x;
+}
+
+// Tree reduction to lane 0.
+template <class Op>
+__device__ __forceinline__ double warp_reduce_lane0(double x)
+{
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) x = Op::op(x, __shfl_down_sync(0xffffffffu, x, o));
+    return x;
+}
+
+// Sum (or max) NV FP64 values over all threads of the instance's CTAs; every
+// thread gets the totals, bit-identical in every CTA.  FP64 runs on a narrow
+// pipe on this GPU, so the FP64 adds are kept to one tree per warp plus one
+// fold in warp 0: each warp reduces its values to lane 0, which publishes
+// them; one barrier (block or cluster); warp 0 of every CTA folds all
+// partials of all CTAs (lane l reads partials l, l+32, ..., remote ones
+// through distributed shared memory, all loads in flight at once), in the
+// same order in every CTA, and a block barrier hands the totals to the other
+// warps.  The double-buffered slots are rewritten two reductions later,
+// after the next barrier, which every reader has passed.
 template <class Op, int NV>
 __device__ __forceinline__ void cl_reduce(ClusterCtx &C, double (&v)[NV])
 {
-    __shared__ double sm[RB_SLOTS * 32];
-    block_reduce<Op, NV>(v, sm);
-    if (threadIdx.x == 0) {
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
 #pragma unroll
-        for (int i = 0; i < NV; i++) C.red[C.rb][i] = v[i];
-    }
-    C.cl.sync();
+    for (int i = 0; i < NV; i++) v[i] = warp_reduce_lane0<Op>(v[i]);
+    if (lane == 0) {
 #pragma unroll
-    for (int i = 0; i < NV; i++) {
-        double t = Op::id();
-        for (int r = 0; r < C.ncta; r++) t = Op::op(t, C.cl.map_shared_rank(&C.red[C.rb][0], r)[i]);
-        v[i] = t;
+        for (int i = 0; i < NV; i++) C.red[C.rb][i][wid] = v[i];
     }
+    unit_sync(C);
+    if (wid == 0) {
+        const int total = C.ncta * nw;   // <= 8 * 16
+        double t[NV];
+#pragma unroll
+        for (int i = 0; i < NV; i++) t[i] = Op::id();
+#pragma unroll
+        for (int u = 0; u < 4; u++) {
+            const int s = lane + 32 * u;
+            if (s < total) {
+                const int r = s / nw, w = s - r * nw;
+                const double *src = C.solo ? &C.red[C.rb][0][w] : C.cl.map_shared_rank(&C.red[C.rb][0][w], r);
+#pragma unroll
+                for (int i = 0; i < NV; i++) t[i] = Op::op(t[i], src[i * RB_WARPS]);
+            }
+        }
+#pragma unroll
+        for (int i = 0; i < NV; i++) t[i] = warp_reduce_lane0<Op>(t[i]);
+        if (lane == 0) {
+#pragma unroll
+            for (int i = 0; i < NV; i++) C.bc[C.rb][i] = t[i];
+        }
+    }
+    __syncthreads();
+#pragma unroll
+    for (int i = 0; i < NV; i++) v[i] = C.bc[C.rb][i];
     C.rb ^= 1;
+}
+
+// FP32 sums for the inner PCG: FP32 adds are cheap, so every warp folds all
+// partials itself (butterflies, identical bits in every lane, warp and CTA)
+// and the reduction costs one barrier.
+template <int NV>
+__device__ __forceinline__ void cl_reduce_f32(ClusterCtx &C, float (&v)[NV])
+{
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
+#pragma unroll
+    for (int i = 0; i < NV; i++) v[i] = warp_allreduce<FSum>(v[i]);
+    if (lane == 0) {
+#pragma unroll
+        for (int i = 0; i < NV; i++) C.redf[C.rb][i][wid] = v[i];
+    }
+    unit_sync(C);
+    const int total = C.ncta * nw;
+    float t[NV];
+#pragma unroll
+    for (int i = 0; i < NV; i++) t[i] = FSum::id();
+#pragma unroll
+    for (int u = 0; u < 4; u++) {
+        const int s = lane + 32 * u;
+        if (s < total) {
+            const int r = s / nw, w = s - r * nw;
+            const float *src = C.solo ? &C.redf[C.rb][0][w] : C.cl.map_shared_rank(&C.redf[C.rb][0][w], r);
+#pragma unroll
+            for (int i = 0; i < NV; i++) t[i] = FSum::op(t[i], src[i * RB_WARPS]);
+        }
+    }
+#pragma unroll
+    for (int i = 0; i < NV; i++) v[i] = warp_allreduce<FSum>(t[i]);
+    C.rb ^= 1;
+}
+
+// The grid fields the FP32 operator reads, held in registers by value.
+struct Geo32 {
+    FastDiv fx, fxy;
+    int nx, ny, nz, sxy;
+    float w[3];
+};
+
+__device__ __forceinline__ Geo32 geo32(const Grid &g)
+{
+    return Geo32{g.fx, g.fxy, g.nx, g.ny, g.nz, (int)g.sxy, {g.w32[0], g.w32[1], g.w32[2]}};
+}
+
+// FP32 operator of cell p, (A v)_p = cb_p v_p + sum over interior faces of
+// w (K_P + K_N)/2 (v_p - v_N), faces recomputed from FP32 K (a neighbour with
+// K < 0 is inactive); 32-bit indices.  Both loads of a face issue before the
+// inactive test, so a cell costs one memory round trip.
+template <class Get>
+__device__ __forceinline__ float apply32_i(const Geo32 &g, int p, const float *__restrict__ K32,
+                                           const float *__restrict__ cb32, Get get)
+{
+    const unsigned int u = (unsigned int)p;
+    const unsigned int kk = fdiv(u, g.fxy);
+    const unsigned int r = u - kk * (unsigned int)g.sxy;
+    const unsigned int jj = fdiv(r, g.fx);
+    const int i = (int)(r - jj * (unsigned int)g.nx), j = (int)jj, k = (int)kk;
+    const float KP = K32[p];
+    const float vP = get(p);
+    float acc = cb32[p] * vP;
+    auto face = [&](bool inside, int q, float w) {
+        if (!inside) return;
+        const float KN = K32[q];
+        const float vN = get(q);
+        const float t = fmaf(w * 0.5f * (KP + KN), vP - vN, acc);
+        acc = KN < 0.0f ? acc : t;
+    };
+    face(i > 0, p - 1, g.w[0]);
+    face(i < g.nx - 1, p + 1, g.w[0]);
+    face(j > 0, p - g.nx, g.w[1]);
+    face(j < g.ny - 1, p + g.nx, g.w[1]);
+    face(k > 0, p - g.sxy, g.w[2]);
+    face(k < g.nz - 1, p + g.sxy, g.w[2]);
+    return acc;
+}
+
+// Inner FP32 Jacobi-PCG of one defect-correction pass, A d = r32 from d = 0,
+// on this CTA's cells [lo, hi) of an instance (views offset to the
+// instance); scalars in FP32 too, since every thread computes them.  Kept
+// out of line so that its loops get registers of their own, apart from the
+// instance state of the caller.  Returns false on breakdown; its = inner
+// iterations.
+__device__ __noinline__ bool inner_pcg32(ClusterCtx &C, const Geo32 g, int lo, int hi, const float *__restrict__ K32,
+                                         const float *__restrict__ cb32, const float *__restrict__ di32,
+                                         float *__restrict__ r32, float *__restrict__ z32, float *__restrict__ pa_,
+                                         float *__restrict__ pb_, float *__restrict__ q32, float *__restrict__ d32,
+                                         float rho, float stop, int max_it, int &its)
+{
+    float beta = 0.0f;
+    int pi = 0;
+    its = 0;
+    const int bd = (int)blockDim.x;
+    for (;;) {
+        float *pin = pi ? pb_ : pa_, *pout = pi ? pa_ : pb_;
+        const bool first = its == 0;
+        auto get = [&](int qq) { return first ? z32[qq] : fmaf(beta, pin[qq], z32[qq]); };
+        // two cells per thread and pass, all loads of both before any store,
+        // so their round trips overlap (same accumulation order as one cell
+        // per pass)
+        float a0 = 0.0f;
+        for (int p = lo + (int)threadIdx.x; p < hi; p += 2 * bd) {
+            const bool has2 = p + bd < hi;
+            const int p2 = has2 ? p + bd : p;
+            const float pp = get(p);
+            const float qp = apply32_i(g, p, K32, cb32, get);
+            const float pp2 = get(p2);
+            const float qp2 = apply32_i(g, p2, K32, cb32, get);
+            pout[p] = pp;
+            q32[p] = qp;
+            a0 = fmaf(pp, qp, a0);
+            if (has2) {
+                pout[p2] = pp2;
+                q32[p2] = qp2;
+                a0 = fmaf(pp2, qp2, a0);
+            }
+        }
+        float w1[1] = {a0};
+        cl_reduce_f32<1>(C, w1);
+        const float af = rho / w1[0];
+        if (!(w1[0] > 0.0f) || !isfinite(af)) return false;
+        float b0 = 0.0f, b1 = 0.0f;
+        for (int p = lo + (int)threadIdx.x; p < hi; p += 2 * bd) {
+            const bool has2 = p + bd < hi;
+            const int p2 = has2 ? p + bd : p;
+            const float pa = pout[p], da = d32[p], qa = q32[p], ra = r32[p], ia = di32[p];
+            const float pb = pout[p2], db = d32[p2], qb = q32[p2], rb = r32[p2], ib = di32[p2];
+            const float ra2 = fmaf(-af, qa, ra), za2 = ia * ra2;
+            d32[p] = fmaf(af, pa, da);
+            r32[p] = ra2;
+            z32[p] = za2;
+            b0 = fmaf(ra2, ra2, b0);
+            b1 = fmaf(ra2, za2, b1);
+            if (has2) {
+                const float rb2 = fmaf(-af, qb, rb), zb2 = ib * rb2;
+                d32[p2] = fmaf(af, pb, db);
+                r32[p2] = rb2;
+                z32[p2] = zb2;
+                b0 = fmaf(rb2, rb2, b0);
+                b1 = fmaf(rb2, zb2, b1);
+            }
+        }
+        float w2[2] = {b0, b1};
+        cl_reduce_f32<2>(C, w2);
+        its++;
+        pi ^= 1;
+        if (!isfinite(w2[0]) || !isfinite(w2[1])) return false;
+        if (sqrtf(w2[0]) <= stop || its >= max_it) return true;
+        beta = w2[1] / rho;
+        rho = w2[1];
+    }
 }
 
 __device__ __forceinline__ double t_tol_d(double t) { return 1e-9 * (fabs(t) > 1.0 ? fabs(t) : 1.0); }
 
 }  // namespace
 
-template <int PREC>
-__global__ void __launch_bounds__(ENS_THREADS, 1)
-k_ensemble(EnsDesc *__restrict__ D, int n_inst, EnsBuffers B, EnsParams P, const double *t_end_p, unsigned int *queue)
+template <int PREC, int THREADS>
+__global__ void __launch_bounds__(THREADS, 512 / THREADS)
+k_ensemble(EnsDesc *__restrict__ D, int n_inst, EnsBuffers B, EnsParams P, const double *t_end_p, unsigned int *queue,
+           const int *__restrict__ sched)
 {
     const double t_end = *t_end_p;
-    __shared__ double red[2][RB_SLOTS];
+    static_assert(THREADS <= 32 * RB_WARPS, "partial slots");
+    __shared__ double red[2][RB_SLOTS][RB_WARPS];
+    __shared__ double bc[2][RB_SLOTS];
+    __shared__ float redf[2][RB_SLOTS][RB_WARPS];
     __shared__ int s_inst;
-    ClusterCtx C{cg::this_cluster(), 0, 1, red, 0};
-    C.rank = (int)C.cl.block_rank();
-    C.ncta = (int)C.cl.num_blocks();
+    ClusterCtx C{cg::this_cluster(), 0, 1, false, red, bc, redf, 0};
+    const int cl_rank = (int)C.cl.block_rank(), cl_size = (int)C.cl.num_blocks();
+    C.rank = cl_rank;
+    C.ncta = cl_size;
 
     for (;;) {
-        if (C.rank == 0 && threadIdx.x == 0) s_inst = (int)atomicAdd(queue, 1u);
-        C.cl.sync();
-        const int inst = *C.cl.map_shared_rank(&s_inst, 0);
-        C.cl.sync();
-        if (inst >= n_inst) break;
+        int inst;
+        if (!C.solo) {
+            if (C.rank == 0 && threadIdx.x == 0) {
+                const unsigned int k = atomicAdd(queue, 1u);
+                s_inst = k < (unsigned int)n_inst ? sched[k] : -1;
+            }
+            C.cl.sync();
+            const int e = *C.cl.map_shared_rank(&s_inst, 0);
+            C.cl.sync();   // no remote shared access after this point when going solo
+            if (e < 0) break;
+            inst = e & ENS_SCHED_INDEX;
+            if (cl_size > 1 && !(e & ENS_SCHED_WIDE)) {
+                // the queue has reached the instances that run on single
+                // CTAs: rank 0 runs this one alone, the others pop their own
+                C.solo = true;
+                C.rank = 0;
+                C.ncta = 1;
+                if (cl_rank != 0) continue;
+            }
+        } else {
+            if (threadIdx.x == 0) {
+                const unsigned int k = atomicAdd(queue, 1u);
+                s_inst = k < (unsigned int)n_inst ? (sched[k] & ENS_SCHED_INDEX) : -1;
+            }
+            __syncthreads();
+            inst = s_inst;
+            __syncthreads();
+            if (inst < 0) break;
+        }
+        unsigned long long t_start = 0;
+        if (C.rank == 0 && threadIdx.x == 0) asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t_start));
 
         EnsDesc &d = D[inst];
         const Grid &g = d.g;
@@ -148,7 +401,7 @@ k_ensemble(EnsDesc *__restrict__ D, int n_inst, EnsBuffers B, EnsParams P, const
                     closure_at(H[hkb], nullptr, TH[tn ^ 1], KB[kb], v2);
                     closure_valid = true;
                 }
-                C.cl.sync();
+                unit_sync(C);
                 int kin = kb, it = 0, cg_att = 0;
                 bool conv = false, fail = false;
                 for (it = 1; it <= P.n_max; it++) {
@@ -250,52 +503,16 @@ k_ensemble(EnsDesc *__restrict__ D, int n_inst, EnsBuffers B, EnsParams P, const
                             if (!finite) { lin_ok = false; break; }
                             if (sqrt(v[0]) <= P.tol_cg * sqrt(v[1])) break;
                             if (outer >= P.outer_max_it) { lin_ok = false; break; }
-                            // inner solve A d = r32 from d = 0
-                            double rho = v[3];
-                            const double stop = P.tol_inner * sqrt(v[2]);
-                            bool done = !(v[2] > 0.0);
-                            float beta = 0.0f;
-                            int pi = 0, inner_it = 0;
-                            while (!done) {
-                                float *pin = P32[pi], *pout = P32[pi ^ 1];
-                                const bool first = inner_it == 0;
-                                auto get = [&](long long qq) { return first ? z32[qq] : fmaf(beta, pin[qq], z32[qq]); };
-                                float a0 = 0.0f;
-                                for (long long p = lo + threadIdx.x; p < hi; p += blockDim.x) {
-                                    const float pp = get(p);
-                                    const float qp = apply32(g, p, K32, cb32, get);
-                                    pout[p] = pp;
-                                    q32[p] = qp;
-                                    a0 = fmaf(pp, qp, a0);
-                                }
-                                double w1[1] = {(double)a0};
-                                cl_reduce<OpSum, 1>(C, w1);
-                                const double alpha = rho / w1[0];
-                                if (!(w1[0] > 0.0) || !isfinite(alpha)) { lin_ok = false; break; }
-                                const float af = (float)alpha;
-                                float b0 = 0.0f, b1 = 0.0f;
-                                for (long long p = lo + threadIdx.x; p < hi; p += blockDim.x) {
-                                    d32[p] = fmaf(af, pout[p], d32[p]);
-                                    const float rp2 = fmaf(-af, q32[p], r32[p]);
-                                    const float zp2 = di32[p] * rp2;
-                                    r32[p] = rp2;
-                                    z32[p] = zp2;
-                                    b0 = fmaf(rp2, rp2, b0);
-                                    b1 = fmaf(rp2, zp2, b1);
-                                }
-                                double w2[2] = {(double)b0, (double)b1};
-                                cl_reduce<OpSum, 2>(C, w2);
-                                inner_it++;
-                                pi ^= 1;
-                                if (!isfinite(w2[0]) || !isfinite(w2[1])) { lin_ok = false; break; }
-                                if (sqrt(w2[0]) <= stop || inner_it >= P.inner_max_it) break;
-                                beta = (float)(w2[1] / rho);
-                                rho = w2[1];
-                            }
+                            // inner solve A d = r32 from d = 0, FP32 throughout
+                            int inner_it = 0;
+                            if (v[2] > 0.0)
+                                lin_ok = inner_pcg32(C, geo32(g), (int)lo, (int)hi, K32, cb32, di32, r32, z32, P32[0], P32[1],
+                                                     q32, d32, (float)v[3], (float)(P.tol_inner * sqrt(v[2])),
+                                                     P.inner_max_it, inner_it);
                             cg_it += inner_it;
                             if (!lin_ok) break;
                             for (long long p = lo + threadIdx.x; p < hi; p += blockDim.x) x[p] += (double)d32[p];
-                            C.cl.sync();
+                            unit_sync(C);
                             // FP64 outer residual and new inner seeds
                             v[0] = v[1] = v[2] = v[3] = 0.0;
                             for (long long p = lo + threadIdx.x; p < hi; p += blockDim.x) {
@@ -384,12 +601,16 @@ k_ensemble(EnsDesc *__restrict__ D, int n_inst, EnsBuffers B, EnsParams P, const
                     status = ENS_DT_MIN;
                     break;
                 }
-                C.cl.sync();
+                unit_sync(C);
             }
             if (!accepted) break;
         }
-        C.cl.sync();
+        unit_sync(C);
         if (C.rank == 0 && threadIdx.x == 0) {
+            unsigned long long t_stop;
+            asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t_stop));
+            d.busy_ns += (long long)(t_stop - t_start);
+            d.ctas = C.ncta;
             d.t = t;
             d.dt_nom = dt_nom;
             d.easy = easy;
@@ -406,16 +627,33 @@ k_ensemble(EnsDesc *__restrict__ D, int n_inst, EnsBuffers B, EnsParams P, const
             d.closure_cum = clo_cum;
             d.defect_cum = def_cum;
         }
-        C.cl.sync();
+        unit_sync(C);
     }
 }
 
-cudaError_t launch_ensemble(cudaStream_t s, int cluster, int nclusters, int precision, EnsDesc *D, int n_inst,
-                            const EnsBuffers &B, const EnsParams &P, const double *t_end, unsigned int *queue)
+template <int PREC>
+static void *ensemble_kernel(int threads)
 {
+    if (threads == 128) return (void *)k_ensemble<PREC, 128>;
+    if (threads == 256) return (void *)k_ensemble<PREC, 256>;
+    if (threads == 512) return (void *)k_ensemble<PREC, 512>;
+    return nullptr;
+}
+
+static void *ensemble_kernel(int threads, int precision)
+{
+    return precision == 0 ? ensemble_kernel<0>(threads) : ensemble_kernel<1>(threads);
+}
+
+cudaError_t launch_ensemble(cudaStream_t s, int cluster, int threads, int nclusters, int precision, EnsDesc *D,
+                            int n_inst, const EnsBuffers &B, const EnsParams &P, const double *t_end,
+                            unsigned int *queue, const int *sched)
+{
+    void *fn = ensemble_kernel(threads, precision);
+    if (!fn) return cudaErrorInvalidValue;
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = dim3((unsigned)(cluster * nclusters), 1, 1);
-    cfg.blockDim = dim3(ENS_THREADS, 1, 1);
+    cfg.blockDim = dim3((unsigned)threads, 1, 1);
     cfg.dynamicSmemBytes = 0;
     cfg.stream = s;
     cudaLaunchAttribute attr[1];
@@ -425,15 +663,17 @@ cudaError_t launch_ensemble(cudaStream_t s, int cluster, int nclusters, int prec
     attr[0].val.clusterDim.z = 1;
     cfg.attrs = attr;
     cfg.numAttrs = 1;
-    if (precision == 0) return cudaLaunchKernelEx(&cfg, k_ensemble<0>, D, n_inst, B, P, t_end, queue);
-    return cudaLaunchKernelEx(&cfg, k_ensemble<1>, D, n_inst, B, P, t_end, queue);
+    void *args[] = {&D, &n_inst, const_cast<EnsBuffers *>(&B), const_cast<EnsParams *>(&P), &t_end, &queue, &sched};
+    return cudaLaunchKernelExC(&cfg, fn, args);
 }
 
-int ensemble_max_clusters(int cluster, int precision)
+int ensemble_max_clusters(int cluster, int threads, int precision)
 {
+    void *fn = ensemble_kernel(threads, precision);
+    if (!fn) return 0;
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = dim3((unsigned)cluster, 1, 1);
-    cfg.blockDim = dim3(ENS_THREADS, 1, 1);
+    cfg.blockDim = dim3((unsigned)threads, 1, 1);
     cudaLaunchAttribute attr[1];
     attr[0].id = cudaLaunchAttributeClusterDimension;
     attr[0].val.clusterDim.x = (unsigned)cluster;
@@ -442,10 +682,7 @@ int ensemble_max_clusters(int cluster, int precision)
     cfg.attrs = attr;
     cfg.numAttrs = 1;
     int n = 0;
-    const cudaError_t e = precision == 0
-                              ? cudaOccupancyMaxActiveClusters(&n, (void *)k_ensemble<0>, &cfg)
-                              : cudaOccupancyMaxActiveClusters(&n, (void *)k_ensemble<1>, &cfg);
-    if (e != cudaSuccess) {
+    if (cudaOccupancyMaxActiveClusters(&n, fn, &cfg) != cudaSuccess) {
         cudaGetLastError();
         return 0;
     }

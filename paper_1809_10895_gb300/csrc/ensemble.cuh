@@ -6,7 +6,7 @@
 
 namespace rf {
 
-constexpr int ENS_THREADS = 512;
+constexpr int ENS_THREADS = 512;   // default CTA size; 128 and 256 are the other tilings
 
 enum { ENS_NEW = 0, ENS_RUNNING = 1, ENS_DT_MIN = 2, ENS_BUDGET = 3 };
 
@@ -20,8 +20,9 @@ struct EnsDesc {
     double t, dt_nom;
     int easy, status;
     int hbuf, kbuf, tnbuf;  // buffers holding h, K(h), theta*(h)
-    int pad;
+    int ctas;               // CTAs that ran the instance in its last run
     long long steps, picard, cg, rejected;
+    long long busy_ns;      // wall time the instance held its work unit
     double in_cum, out_cum, closure_cum, defect_cum, storage0;
 };
 
@@ -41,9 +42,16 @@ struct EnsParams {
     long long step_budget;
 };
 
-cudaError_t launch_ensemble(cudaStream_t s, int cluster, int nclusters, int precision, EnsDesc *D, int n_inst,
-                            const EnsBuffers &B, const EnsParams &P, const double *t_end, unsigned int *queue);
-// clusters of `cluster` CTAs that fit on the device at once
-int ensemble_max_clusters(int cluster, int precision);
+// Schedule entry: descriptor index, plus ENS_SCHED_WIDE when the instance runs
+// on a whole cluster (wide entries come first in a schedule).
+constexpr int ENS_SCHED_WIDE = 1 << 30;
+constexpr int ENS_SCHED_INDEX = ENS_SCHED_WIDE - 1;
+
+cudaError_t launch_ensemble(cudaStream_t s, int cluster, int threads, int nclusters, int precision, EnsDesc *D,
+                            int n_inst, const EnsBuffers &B, const EnsParams &P, const double *t_end,
+                            unsigned int *queue, const int *sched);
+// clusters of `cluster` CTAs of `threads` threads (128, 256 or 512) that fit
+// on the device at once (0 when none fits)
+int ensemble_max_clusters(int cluster, int threads, int precision);
 
 }  // namespace rf

@@ -1,9 +1,11 @@
 // ensemble_api.cu -- C ABI of the batched ensemble (rf_ens_*): packing of
 // uneven instances, the persistent kernel captured in a CUDA graph, and the
-// tuner that picks the cluster size (CTAs per instance work unit).
+// tuner that picks the tiling (cluster size, CTA size) and the schedule
+// (queue order by measured work, instances run on whole clusters).
 #include <algorithm>
 #include <cmath>
 #include <numeric>
+#include <queue>
 #include <string>
 #include <vector>
 
@@ -33,7 +35,7 @@ struct rf_ens {
     rf_allocator alloc{};
     bool has_alloc = false;
     std::vector<void *> allocations;
-    int n = 0, precision = 0, cluster = 1;
+    int n = 0, precision = 0, cluster = 1, threads = ENS_THREADS;
     long long ncells = 0;
     std::vector<int> order;            // queue position -> user index
     std::vector<int> pos;              // user index -> queue position
@@ -46,9 +48,11 @@ struct rf_ens {
     unsigned long long *ctr = nullptr;
     double *t_end = nullptr, *t_end_h = nullptr;
     unsigned int *queue = nullptr;
+    int *sched = nullptr;              // work queue: descriptor index | ENS_SCHED_WIDE
+    std::vector<int> sched_h;
     cudaGraph_t graph = nullptr;
     cudaGraphExec_t exec = nullptr;
-    int graph_cluster = 0;
+    int graph_cluster = 0, graph_threads = 0;
 
     void *dalloc(size_t bytes)
     {
@@ -76,6 +80,18 @@ void destroy_graph(rf_ens *e)
     e->exec = nullptr;
     e->graph = nullptr;
     e->graph_cluster = 0;
+    e->graph_threads = 0;
+}
+
+// Schedule from an order of descriptor indices; the first n_wide run on
+// whole clusters.
+rf_status upload_schedule(rf_ens *e, const std::vector<int> &desc_order, int n_wide)
+{
+    e->sched_h.resize(e->n);
+    for (int k = 0; k < e->n; k++) e->sched_h[k] = desc_order[k] | (k < n_wide ? ENS_SCHED_WIDE : 0);
+    ECUDA(cudaMemcpyAsync(e->sched, e->sched_h.data(), sizeof(int) * e->n, cudaMemcpyHostToDevice, e->stream));
+    ECUDA(cudaStreamSynchronize(e->stream));
+    return RF_OK;
 }
 
 rf_status upload_initial(rf_ens *e)
@@ -90,14 +106,15 @@ rf_status upload_initial(rf_ens *e)
 rf_status build_graph(rf_ens *e)
 {
     destroy_graph(e);
-    const int ncl = ensemble_max_clusters(e->cluster, e->precision);
+    const int ncl = ensemble_max_clusters(e->cluster, e->threads, e->precision);
     if (ncl < 1) return efail(RF_ERR_CUDA, "no cluster of that size fits on this device");
     cudaStream_t cap;
     ECUDA(cudaStreamCreateWithFlags(&cap, cudaStreamNonBlocking));
     cudaError_t err = cudaStreamBeginCapture(cap, cudaStreamCaptureModeRelaxed);
     if (err == cudaSuccess) err = cudaMemsetAsync(e->queue, 0, sizeof(unsigned int), cap);
     if (err == cudaSuccess)
-        err = launch_ensemble(cap, e->cluster, ncl, e->precision, e->D, e->n, e->B, e->P, e->t_end, e->queue);
+        err = launch_ensemble(cap, e->cluster, e->threads, ncl, e->precision, e->D, e->n, e->B, e->P, e->t_end,
+                              e->queue, e->sched);
     cudaGraph_t g = nullptr;
     const cudaError_t err2 = cudaStreamEndCapture(cap, &g);
     cudaStreamDestroy(cap);
@@ -109,6 +126,7 @@ rf_status build_graph(rf_ens *e)
     e->graph = g;
     ECUDA(cudaGraphInstantiate(&e->exec, g, 0));
     e->graph_cluster = e->cluster;
+    e->graph_threads = e->threads;
     return RF_OK;
 }
 
@@ -171,7 +189,7 @@ rf_status rf_ens_create(const rf_ens_instance *inst, int n, const rf_solver_para
 
     const long long N = total;
     bool ok = e->get(e->D, n) && e->get(e->tab, 1) && e->get(e->ctr, 2 * KK_COUNT) && e->get(e->t_end, 1) &&
-              e->get(e->queue, 1);
+              e->get(e->queue, 1) && e->get(e->sched, n);
     for (int b = 0; b < 3 && ok; b++) ok = e->get(e->B.H[b], N);
     for (int b = 0; b < 2 && ok; b++) ok = e->get(e->B.TH[b], N) && e->get(e->B.K[b], N) && e->get(e->B.p[b], N) &&
                                             e->get(e->B.p32[b], N);
@@ -274,7 +292,11 @@ rf_status rf_ens_create(const rf_ens_instance *inst, int n, const rf_solver_para
         rf_ens_destroy(e);
         return efail(RF_ERR_CUDA, std::string("rf_ens_create: ") + cudaGetErrorString(err));
     }
-    if (rf_status st = upload_initial(e)) {
+    std::vector<int> size_order(n);
+    std::iota(size_order.begin(), size_order.end(), 0);
+    rf_status st = upload_initial(e);
+    if (!st) st = upload_schedule(e, size_order, n);
+    if (st) {
         rf_ens_destroy(e);
         return st;
     }
@@ -295,20 +317,42 @@ void rf_ens_destroy(rf_ens *e)
     delete e;
 }
 
-rf_status rf_ens_set_tiling(rf_ens *e, int cluster)
+rf_status rf_ens_set_tiling(rf_ens *e, int cluster, int threads)
 {
     if (!e || (cluster != 1 && cluster != 2 && cluster != 4 && cluster != 8))
         return efail(RF_ERR_ARG, "rf_ens_set_tiling: cluster must be 1, 2, 4 or 8");
-    if (ensemble_max_clusters(cluster, e->precision) < 1)
+    if (threads != 128 && threads != 256 && threads != 512)
+        return efail(RF_ERR_ARG, "rf_ens_set_tiling: threads must be 128, 256 or 512");
+    if (ensemble_max_clusters(cluster, threads, e->precision) < 1)
         return efail(RF_ERR_ARG, "rf_ens_set_tiling: clusters of that size do not fit on this device");
     e->cluster = cluster;
+    e->threads = threads;
     return RF_OK;
+}
+
+rf_status rf_ens_set_schedule(rf_ens *e, const int *order, int n_wide)
+{
+    if (!e) return efail(RF_ERR_ARG, "null ensemble");
+    std::vector<int> desc_order(e->n);
+    if (order) {
+        std::vector<char> seen(e->n, 0);
+        for (int k = 0; k < e->n; k++) {
+            const int i = order[k];
+            if (i < 0 || i >= e->n || seen[i])
+                return efail(RF_ERR_ARG, "rf_ens_set_schedule: order must be a permutation of the instances");
+            seen[i] = 1;
+            desc_order[k] = e->pos[i];
+        }
+    } else {
+        std::iota(desc_order.begin(), desc_order.end(), 0);
+    }
+    return upload_schedule(e, desc_order, n_wide < 0 || n_wide > e->n ? e->n : n_wide);
 }
 
 rf_status rf_ens_run(rf_ens *e, double t_end)
 {
     if (!e || !std::isfinite(t_end)) return efail(RF_ERR_ARG, "rf_ens_run: bad argument");
-    if (!e->exec || e->graph_cluster != e->cluster)
+    if (!e->exec || e->graph_cluster != e->cluster || e->graph_threads != e->threads)
         if (rf_status st = build_graph(e)) return st;
     *e->t_end_h = t_end;
     ECUDA(cudaMemcpyAsync(e->t_end, e->t_end_h, sizeof(double), cudaMemcpyHostToDevice, e->stream));
@@ -344,6 +388,8 @@ rf_status rf_ens_get(rf_ens *e, int i, double *h, rf_ens_stats *st)
         st->outflow_cum = d.out_cum;
         st->closure_abs = std::fabs(d.closure_cum);
         st->nonlinear_defect_cum = d.defect_cum;
+        st->busy_s = 1e-9 * (double)d.busy_ns;
+        st->ctas = d.ctas;
     }
     return RF_OK;
 }
@@ -354,18 +400,22 @@ rf_status rf_ens_reset(rf_ens *e)
     return upload_initial(e);
 }
 
-rf_status rf_ens_tune(rf_ens *e, double t_probe, int *best_cluster, double *best_ms)
+rf_status rf_ens_tune(rf_ens *e, double t_probe, int *best_cluster, int *best_threads, int *best_wide,
+                      double *best_ms)
 {
     if (!e || !(t_probe > 0)) return efail(RF_ERR_ARG, "rf_ens_tune: bad argument");
-    int best = 0;
-    double best_t = INFINITY;
+    const int n = e->n;
     cudaEvent_t a, b;
     ECUDA(cudaEventCreate(&a));
     ECUDA(cudaEventCreate(&b));
-    for (int c : {1, 2, 4, 8}) {
-        if (ensemble_max_clusters(c, e->precision) < 1) continue;
+    std::vector<EnsDesc> dh(n);
+    // one timed run from the initial state; busy[k] = seconds descriptor k held its unit
+    auto probe = [&](int c, int th, const std::vector<int> &ord, int n_wide, float &ms,
+                     std::vector<double> *busy) -> rf_status {
         e->cluster = c;
+        e->threads = th;
         if (rf_status st = upload_initial(e)) return st;
+        if (rf_status st = upload_schedule(e, ord, n_wide)) return st;
         if (rf_status st = build_graph(e)) return st;
         *e->t_end_h = t_probe;
         ECUDA(cudaMemcpyAsync(e->t_end, e->t_end_h, sizeof(double), cudaMemcpyHostToDevice, e->stream));
@@ -373,20 +423,98 @@ rf_status rf_ens_tune(rf_ens *e, double t_probe, int *best_cluster, double *best
         ECUDA(cudaGraphLaunch(e->exec, e->stream));
         ECUDA(cudaEventRecord(b, e->stream));
         ECUDA(cudaEventSynchronize(b));
-        float ms = 0.0f;
         ECUDA(cudaEventElapsedTime(&ms, a, b));
-        if (ms < best_t) {
-            best_t = ms;
-            best = c;
+        if (busy) {
+            ECUDA(cudaMemcpyAsync(dh.data(), e->D, sizeof(EnsDesc) * n, cudaMemcpyDeviceToHost, e->stream));
+            ECUDA(cudaStreamSynchronize(e->stream));
+            busy->resize(n);
+            for (int k = 0; k < n; k++) (*busy)[k] = 1e-9 * (double)dh[k].busy_ns;
         }
+        return RF_OK;
+    };
+    struct Cand {
+        int c, th, wide;
+        double t;
+        std::vector<int> order;
+    };
+    std::vector<int> size_order(n);
+    std::iota(size_order.begin(), size_order.end(), 0);
+    Cand best{0, 0, n, INFINITY, size_order};
+    // 1. every tiling with every instance on a whole unit, largest first:
+    // a timed run, and each instance's time at that width
+    const int ths[2] = {512, 256}, cls[4] = {1, 2, 4, 8};
+    std::vector<double> busy[2][4];
+    int ncl[2][4] = {};
+    for (int ti = 0; ti < 2; ti++)
+        for (int ci = 0; ci < 4; ci++) {
+            ncl[ti][ci] = ensemble_max_clusters(cls[ci], ths[ti], e->precision);
+            if (ncl[ti][ci] < 1) continue;
+            float ms = 0.0f;
+            if (rf_status st = probe(cls[ci], ths[ti], size_order, n, ms, &busy[ti][ci])) return st;
+            if (ms < best.t) best = Cand{cls[ci], ths[ti], n, ms, size_order};
+        }
+    if (!best.c) {
+        cudaEventDestroy(a);
+        cudaEventDestroy(b);
+        return efail(RF_ERR_CUDA, "rf_ens_tune: no tiling fits");
+    }
+    // 2. list-scheduling model of the persistent kernel: ncl clusters pop the
+    // queue (heaviest first at that width); a wide instance holds its cluster
+    // for its measured wide time; the first non-wide pop splits the cluster
+    // into single CTAs, which then run instances for their measured time on
+    // one CTA.  Predict every (tiling, n_wide) and keep the best few.
+    std::vector<Cand> preds;
+    for (int ti = 0; ti < 2; ti++) {
+        if (ncl[ti][0] < 1) continue;
+        const std::vector<double> &solo = busy[ti][0];
+        for (int ci = 1; ci < 4; ci++) {
+            if (ncl[ti][ci] < 1) continue;
+            const std::vector<double> &wide = busy[ti][ci];
+            const int c = cls[ci], units = ncl[ti][ci];
+            std::vector<int> lpt = size_order;
+            std::stable_sort(lpt.begin(), lpt.end(), [&](int x, int y) { return wide[x] > wide[y]; });
+            for (int w = 0; w <= n; w++) {
+                // (free time, is a whole cluster) per unit, earliest first
+                std::priority_queue<std::pair<double, int>, std::vector<std::pair<double, int>>,
+                                    std::greater<std::pair<double, int>>> units_q;
+                for (int u = 0; u < units; u++) units_q.push({0.0, 1});
+                double end = 0.0;
+                int k = 0;
+                while (!units_q.empty()) {
+                    auto [t, whole] = units_q.top();
+                    units_q.pop();
+                    if (k >= n) { end = std::max(end, t); continue; }
+                    const int d = lpt[k];
+                    if (whole && k < w) {
+                        units_q.push({t + wide[d], 1});
+                    } else {
+                        if (whole)
+                            for (int r = 1; r < c; r++) units_q.push({t, 0});
+                        units_q.push({t + solo[d], 0});
+                    }
+                    k++;
+                }
+                preds.push_back(Cand{c, ths[ti], w, end, lpt});
+            }
+        }
+    }
+    std::stable_sort(preds.begin(), preds.end(), [](const Cand &x, const Cand &y) { return x.t < y.t; });
+    // 3. time the three best predictions; keep the fastest measured run
+    for (size_t i = 0; i < preds.size() && i < 3; i++) {
+        float ms = 0.0f;
+        if (rf_status st = probe(preds[i].c, preds[i].th, preds[i].order, preds[i].wide, ms, nullptr)) return st;
+        if (ms < best.t) best = Cand{preds[i].c, preds[i].th, preds[i].wide, ms, preds[i].order};
     }
     cudaEventDestroy(a);
     cudaEventDestroy(b);
-    if (!best) return efail(RF_ERR_CUDA, "rf_ens_tune: no cluster size fits");
-    e->cluster = best;
+    e->cluster = best.c;
+    e->threads = best.th;
+    if (rf_status st = upload_schedule(e, best.order, best.wide)) return st;
     if (rf_status st = upload_initial(e)) return st;
-    if (best_cluster) *best_cluster = best;
-    if (best_ms) *best_ms = best_t;
+    if (best_cluster) *best_cluster = best.c;
+    if (best_threads) *best_threads = best.th;
+    if (best_wide) *best_wide = best.wide;
+    if (best_ms) *best_ms = best.t;
     return RF_OK;
 }
 

@@ -6,10 +6,12 @@ network), for profiling one kernel at a time.
     python -m paper_1809_10895_gb300.kernel_timing watershed --nx 512 --ny 256 --kinds cg32_spmv
     python -m paper_1809_10895_gb300.kernel_timing network --nx 128 --ny 128 --nz 64
     python -m paper_1809_10895_gb300.kernel_timing training --nx 128 --ny 128 --nz 64
+    python -m paper_1809_10895_gb300.kernel_timing ensemble --instances 64 --window 10 --cluster 4
 
 Prints one JSON line: per kind the mean launch time and the algorithmic bytes
 per launch (solver kernels), or the forward / training-step time and TFLOP/s
-(network).
+(network), or the persistent ensemble launch time with per-instance busy
+times (ensemble).
 """
 from __future__ import annotations
 
@@ -23,7 +25,7 @@ sys.path.insert(0, os.path.dirname(os.path.dirname(os.path.abspath(__file__))))
 
 def main(argv=None):
     ap = argparse.ArgumentParser()
-    ap.add_argument("workload", choices=["box", "watershed", "network", "training"])
+    ap.add_argument("workload", choices=["box", "watershed", "network", "training", "ensemble"])
     ap.add_argument("--nx", type=int, default=None)
     ap.add_argument("--ny", type=int, default=None)
     ap.add_argument("--nz", type=int, default=64)
@@ -31,6 +33,10 @@ def main(argv=None):
     ap.add_argument("--steps", type=int, default=5, help="accepted steps before timing (box)")
     ap.add_argument("--reps", type=int, default=24)
     ap.add_argument("--precision", default="mixed")
+    ap.add_argument("--instances", type=int, default=64, help="ensemble instances")
+    ap.add_argument("--window", type=float, default=10.0, help="simulated seconds (ensemble)")
+    ap.add_argument("--cluster", type=int, default=4, help="CTAs per cluster (ensemble)")
+    ap.add_argument("--threads", type=int, default=512, help="threads per CTA (ensemble)")
     a = ap.parse_args(argv)
 
     import torch
@@ -40,6 +46,22 @@ def main(argv=None):
     rf.load()
     torch.cuda.set_device(0)
     out = {"workload": a.workload}
+    if a.workload == "ensemble":
+        cases = W.ensemble(a.instances, seed=0)
+        e = rf.Ensemble.from_cases(cases, precision=a.precision)
+        e.set_tiling(a.cluster, a.threads)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(e.stream)
+        e.run(a.window)
+        e1.record(e.stream)
+        torch.cuda.synchronize()
+        st = [e.get(i, want_h=False)[1] for i in range(len(cases))]
+        out.update(instances=a.instances, window_s=a.window, cluster=a.cluster, threads=a.threads,
+                   ms=e0.elapsed_time(e1), cell_timesteps=sum(x["steps"] * x["cells"] for x in st),
+                   cg_iters=sum(x["cg_iters"] for x in st), max_busy_s=max(x["busy_s"] for x in st),
+                   failed=sum(1 for x in st if x["status"] != 0))
+        print(json.dumps(out))
+        return
     if a.workload == "training":
         nx, ny = a.nx or 128, a.ny or 128
         shape = (1, a.nz, ny, nx)

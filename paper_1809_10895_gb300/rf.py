@@ -87,7 +87,8 @@ class rf_ens_stats(C.Structure):
     _fields_ = [("t", C.c_double), ("dt_nom", C.c_double), ("steps", C.c_longlong), ("picard_iters", C.c_longlong),
                 ("cg_iters", C.c_longlong), ("rejected", C.c_longlong), ("status", C.c_int), ("cells", C.c_longlong),
                 ("storage0", C.c_double), ("inflow_cum", C.c_double), ("outflow_cum", C.c_double),
-                ("closure_abs", C.c_double), ("nonlinear_defect_cum", C.c_double)]
+                ("closure_abs", C.c_double), ("nonlinear_defect_cum", C.c_double), ("busy_s", C.c_double),
+                ("ctas", C.c_int)]
 
 
 class rf_ws_scales(C.Structure):
@@ -131,11 +132,12 @@ SIGNATURES = {
     "rf_ens_create": (C.c_int, [C.POINTER(rf_ens_instance), C.c_int, C.POINTER(rf_solver_params), _VP,
                                 C.POINTER(rf_allocator), C.POINTER(_VP)]),
     "rf_ens_destroy": (None, [_VP]),
-    "rf_ens_set_tiling": (C.c_int, [_VP, C.c_int]),
+    "rf_ens_set_tiling": (C.c_int, [_VP, C.c_int, C.c_int]),
+    "rf_ens_set_schedule": (C.c_int, [_VP, C.POINTER(C.c_int), C.c_int]),
     "rf_ens_run": (C.c_int, [_VP, C.c_double]),
     "rf_ens_get": (C.c_int, [_VP, C.c_int, _DP, C.POINTER(rf_ens_stats)]),
     "rf_ens_reset": (C.c_int, [_VP]),
-    "rf_ens_tune": (C.c_int, [_VP, C.c_double, C.POINTER(C.c_int), _DP]),
+    "rf_ens_tune": (C.c_int, [_VP, C.c_double, C.POINTER(C.c_int), C.POINTER(C.c_int), C.POINTER(C.c_int), _DP]),
     "rf_pcg_solve_noalloc": (C.c_int, [C.c_int, C.c_int, C.c_int, _VP, _VP, _VP, _VP, _VP, _VP, C.c_double,
                                        C.c_int, _VP, C.POINTER(C.c_int)]),
     "rf_nn_create": (C.c_int, [_VP, C.POINTER(rf_allocator), C.POINTER(_VP)]),
@@ -531,8 +533,17 @@ class Ensemble:
         except Exception:
             pass
 
-    def set_tiling(self, cluster: int):
-        _check(load().rf_ens_set_tiling(self.ctx, int(cluster)), "rf_ens_set_tiling")
+    def set_tiling(self, cluster: int, threads: int = 512):
+        _check(load().rf_ens_set_tiling(self.ctx, int(cluster), int(threads)), "rf_ens_set_tiling")
+
+    def set_schedule(self, order=None, n_wide: int = -1):
+        """Queue order (instance indices; None = largest first) and how many
+        leading instances run on whole clusters (-1 = all)."""
+        arr = None
+        if order is not None:
+            order = [int(i) for i in order]
+            arr = (C.c_int * len(order))(*order)
+        _check(load().rf_ens_set_schedule(self.ctx, arr, int(n_wide)), "rf_ens_set_schedule")
 
     def run(self, t_end):
         _check(load().rf_ens_run(self.ctx, float(t_end)), "rf_ens_run")
@@ -547,9 +558,11 @@ class Ensemble:
         _check(load().rf_ens_reset(self.ctx), "rf_ens_reset")
 
     def tune(self, t_probe):
-        c, ms = C.c_int(0), C.c_double(0)
-        _check(load().rf_ens_tune(self.ctx, float(t_probe), C.byref(c), C.byref(ms)), "rf_ens_tune")
-        return c.value, ms.value
+        """Tile and schedule; returns (cluster, threads, n_wide, ms) of the fastest."""
+        c, th, w, ms = C.c_int(0), C.c_int(0), C.c_int(0), C.c_double(0)
+        _check(load().rf_ens_tune(self.ctx, float(t_probe), C.byref(c), C.byref(th), C.byref(w), C.byref(ms)),
+               "rf_ens_tune")
+        return c.value, th.value, w.value, ms.value
 
 
 def pcg_solve_noalloc(shape, diag, Tx, Ty, Tz, b, x, tol=1e-10, max_it=10000, stream=None) -> int:

@@ -1,8 +1,9 @@
 """Batched ensemble (one persistent graph-launched kernel) against the CPU
 oracle run instance by instance: identical step / Picard / rejection totals,
 heads within 1e-8 m (FP64) or 1e-6 m (mixed), for single-CTA and multi-CTA
-cluster work units; laterally uniform instances equal their 1x1 column; the
-tuner picks a working tile."""
+cluster work units, every CTA size, and clusters that hand the smaller
+instances to single CTAs; laterally uniform instances equal their 1x1
+column; the tuner picks a working tile."""
 import numpy as np
 import pytest
 
@@ -39,15 +40,23 @@ def oracle_runs():
     return cases, out
 
 
-@pytest.mark.parametrize("cluster", [1, 4])
-def test_ensemble_fp64_matches_oracle(oracle_runs, cluster):
+@pytest.mark.parametrize("cluster,threads,wide", [(1, 512, 0), (4, 512, 0), (1, 128, 0), (2, 256, 0), (4, 128, 1),
+                                                  (8, 256, 2)])
+def test_ensemble_fp64_matches_oracle(oracle_runs, cluster, threads, wide):
     cases, ref = oracle_runs
     e = rf.Ensemble.from_cases(cases, precision="fp64")
-    e.set_tiling(cluster)
+    e.set_tiling(cluster, threads)
+    # wide k: the first k instances of a reversed order on whole clusters, the
+    # rest on single CTAs
+    order = list(range(len(cases)))[::-1]
+    if wide:
+        e.set_schedule(order, wide)
     e.run(cases[0].t_end)
     for i, (c, (ho, so, mbo)) in enumerate(zip(cases, ref)):
         h, st = e.get(i)
         assert st["status"] == 0 and st["t"] == pytest.approx(c.t_end, abs=1e-6)
+        assert st["ctas"] == (cluster if not wide or order.index(i) < wide else 1)
+        assert st["busy_s"] > 0
         assert st["steps"] == len(so)
         assert st["picard_iters"] == sum(s.picard for s in so)
         assert st["rejected"] == sum(s.rejected for s in so)
@@ -62,7 +71,7 @@ def test_ensemble_fp64_matches_oracle(oracle_runs, cluster):
 def test_ensemble_mixed_matches_oracle(oracle_runs):
     cases, ref = oracle_runs
     e = rf.Ensemble.from_cases(cases, precision="mixed")
-    e.set_tiling(2)
+    e.set_tiling(2, 128)
     e.run(cases[0].t_end)
     for i, (c, (ho, so, mbo)) in enumerate(zip(cases, ref)):
         h, st = e.get(i)
@@ -96,8 +105,8 @@ def test_laterally_uniform_instance_equals_its_column():
 def test_tuner_picks_a_working_tile(oracle_runs):
     cases, ref = oracle_runs
     e = rf.Ensemble.from_cases(cases, precision="fp64")
-    cl, ms = e.tune(300.0)
-    assert cl in (1, 2, 4, 8) and ms > 0
+    cl, th, wide, ms = e.tune(300.0)
+    assert cl in (1, 2, 4, 8) and th in (256, 512) and 0 < wide <= len(cases) and ms > 0
     e.run(cases[0].t_end)
     for i, (ho, so, _) in enumerate(ref):
         h, st = e.get(i)
