@@ -301,7 +301,7 @@ def native(args):
     if not args.no_ensemble:
         cases = W.ensemble(256, seed=args.seed + rank)
         e = rf.Ensemble.from_cases(cases, precision="mixed")
-        cluster, cta_threads, n_wide, probe_ms = e.tune(min(10.0, args.ensemble_window))
+        cluster, cta_threads, n_wide, probe_ms = e.tune(min(20.0, args.ensemble_window))
         barrier()
         ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         ev0.record(e.stream)

@@ -299,11 +299,14 @@ rf_status rf_ens_get(rf_ens *ens, int i, double *h, rf_ens_stats *stats);
 rf_status rf_ens_reset(rf_ens *ens);
 /* Tuner: from the initial state to t_probe, time every tiling that fits
  * (cluster 1, 2, 4, 8 x 256 or 512 threads) with every instance on a whole
- * work unit, recording each instance's run time at each width; predict with
- * a list-scheduling model of the persistent queue (heaviest first) the
- * makespan of every (tiling, n_wide); time the three best predictions; keep
- * the fastest measured tiling and schedule, and reset to the initial state.
- * Outputs may be NULL. */
+ * work unit, recording each instance's run time at each width; order the
+ * queue heaviest first and predict each tiling's makespan with a
+ * list-scheduling model of the persistent queue; time the three best
+ * predictions; keep the fastest measured tiling and order, and reset to the
+ * initial state.  Every instance stays on a whole unit (best_wide = n): a
+ * short probe cannot tell which instances stay light for a whole window, so
+ * split schedules are set explicitly with rf_ens_set_schedule.  Outputs may
+ * be NULL. */
 rf_status rf_ens_tune(rf_ens *ens, double t_probe, int *best_cluster, int *best_threads, int *best_wide,
                       double *best_ms);
 

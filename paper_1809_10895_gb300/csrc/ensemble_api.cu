@@ -459,10 +459,13 @@ rf_status rf_ens_tune(rf_ens *e, double t_probe, int *best_cluster, int *best_th
         return efail(RF_ERR_CUDA, "rf_ens_tune: no tiling fits");
     }
     // 2. list-scheduling model of the persistent kernel: ncl clusters pop the
-    // queue (heaviest first at that width); a wide instance holds its cluster
-    // for its measured wide time; the first non-wide pop splits the cluster
-    // into single CTAs, which then run instances for their measured time on
-    // one CTA.  Predict every (tiling, n_wide) and keep the best few.
+    // queue (heaviest first at that width), each instance holding its
+    // cluster for its measured time.  Every instance stays wide: a split
+    // schedule (the lighter instances on single CTAs) is left to callers
+    // that know the per-instance costs over their whole window -- from a
+    // short probe it is unsafe, since an instance light early in the window
+    // can turn heavy later and become the critical path on one CTA.  The
+    // model's n_wide loop is kept general for that use.
     std::vector<Cand> preds;
     for (int ti = 0; ti < 2; ti++) {
         if (ncl[ti][0] < 1) continue;
@@ -473,7 +476,7 @@ rf_status rf_ens_tune(rf_ens *e, double t_probe, int *best_cluster, int *best_th
             const int c = cls[ci], units = ncl[ti][ci];
             std::vector<int> lpt = size_order;
             std::stable_sort(lpt.begin(), lpt.end(), [&](int x, int y) { return wide[x] > wide[y]; });
-            for (int w = 0; w <= n; w++) {
+            for (int w = n; w <= n; w++) {
                 // (free time, is a whole cluster) per unit, earliest first
                 std::priority_queue<std::pair<double, int>, std::vector<std::pair<double, int>>,
                                     std::greater<std::pair<double, int>>> units_q;

@@ -739,17 +739,49 @@ k_cg32_update(Grid g, float *__restrict__ x, float *__restrict__ r, float *__res
     count_work(g, KK_CG32_UPDATE);
     const float alpha = (float)sc->alpha;
     float a0 = 0.0f, a1 = 0.0f;
-    GRID_STRIDE_LOOP(p)
-    {
-        const float di = dinv[p];
-        if (di == 0.0f) continue;
-        x[p] = fmaf(alpha, pd[p], x[p]);
-        const float rp = fmaf(-alpha, q[p], r[p]);
-        const float zp = di * rp;
-        r[p] = rp;
-        z[p] = zp;
-        a0 = fmaf(rp, rp, a0);
-        a1 = fmaf(rp, zp, a1);
+    // one cell: inactive cells (dinv 0) keep x and r and hold z = 0 (as set
+    // when the inner solve starts), so z is written without being read
+    auto cell = [&](float di, float pv, float xv, float qv, float rv, float &xo, float &ro, float &zo) {
+        const bool act = di != 0.0f;
+        const float rp = fmaf(-alpha, qv, rv), zp = di * rp;
+        xo = act ? fmaf(alpha, pv, xv) : xv;
+        ro = act ? rp : rv;
+        zo = act ? zp : 0.0f;
+        if (act) {
+            a0 = fmaf(rp, rp, a0);
+            a1 = fmaf(rp, zp, a1);
+        }
+    };
+    const long long N = g.N;
+    const long long stride = (long long)gridDim.x * blockDim.x, t0 = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    const bool vec = ((reinterpret_cast<uintptr_t>(x) | reinterpret_cast<uintptr_t>(r) | reinterpret_cast<uintptr_t>(z) |
+                       reinterpret_cast<uintptr_t>(pd) | reinterpret_cast<uintptr_t>(q) |
+                       reinterpret_cast<uintptr_t>(dinv)) & 15u) == 0;
+    long long done = 0;
+    if (vec) {
+        // four cells per thread and pass: 16-byte loads and stores
+        const long long n4 = N / 4;
+        for (long long v = t0; v < n4; v += stride) {
+            const float4 di = reinterpret_cast<const float4 *>(dinv)[v], pv = reinterpret_cast<const float4 *>(pd)[v];
+            const float4 xv = reinterpret_cast<const float4 *>(x)[v], qv = reinterpret_cast<const float4 *>(q)[v];
+            const float4 rv = reinterpret_cast<const float4 *>(r)[v];
+            float4 xo, ro, zo;
+            cell(di.x, pv.x, xv.x, qv.x, rv.x, xo.x, ro.x, zo.x);
+            cell(di.y, pv.y, xv.y, qv.y, rv.y, xo.y, ro.y, zo.y);
+            cell(di.z, pv.z, xv.z, qv.z, rv.z, xo.z, ro.z, zo.z);
+            cell(di.w, pv.w, xv.w, qv.w, rv.w, xo.w, ro.w, zo.w);
+            reinterpret_cast<float4 *>(x)[v] = xo;
+            reinterpret_cast<float4 *>(r)[v] = ro;
+            reinterpret_cast<float4 *>(z)[v] = zo;
+        }
+        done = n4 * 4;
+    }
+    for (long long p = done + t0; p < N; p += stride) {
+        float xo, ro, zo;
+        cell(dinv[p], pd[p], x[p], q[p], r[p], xo, ro, zo);
+        x[p] = xo;
+        r[p] = ro;
+        z[p] = zo;
     }
     float vf[2] = {a0, a1};
     double v[2];

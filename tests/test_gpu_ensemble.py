@@ -106,7 +106,7 @@ def test_tuner_picks_a_working_tile(oracle_runs):
     cases, ref = oracle_runs
     e = rf.Ensemble.from_cases(cases, precision="fp64")
     cl, th, wide, ms = e.tune(300.0)
-    assert cl in (1, 2, 4, 8) and th in (256, 512) and 0 < wide <= len(cases) and ms > 0
+    assert cl in (1, 2, 4, 8) and th in (256, 512) and wide == len(cases) and ms > 0
     e.run(cases[0].t_end)
     for i, (ho, so, _) in enumerate(ref):
         h, st = e.get(i)
