@@ -144,9 +144,9 @@ def cpu_baseline(case, budget_s=20.0):
 
 
 # ------------------------------------------------------------ native arm
-def traffic_for(kernel, cells):
-    """DRAM bytes per launch from the committed ncu summary, scaled to this
-    workload's cells; None when absent or taken on a different kernel source."""
+def profile_entry(kernel):
+    """The committed ncu summary of a kernel; None when absent or taken on a
+    different kernel source."""
     p = os.path.join(ROOT, "profiles", "ncu_traffic.json")
     try:
         d = json.load(open(p))
@@ -154,9 +154,16 @@ def traffic_for(kernel, cells):
         src = open(os.path.join(ROOT, "paper_1809_10895_gb300", "csrc", e["source"]), "rb").read()
         if hashlib.sha256(src).hexdigest()[:16] != e["source_sha"]:
             return None
-        return e["dram_bytes_per_launch"] * cells / e["cells"]
+        return e
     except Exception:
         return None
+
+
+def traffic_for(kernel, cells):
+    """DRAM bytes per launch from the committed ncu summary, scaled to this
+    workload's cells."""
+    e = profile_entry(kernel)
+    return None if e is None else e["dram_bytes_per_launch"] * cells / e["cells"]
 
 
 def native(args):
@@ -259,6 +266,25 @@ def native(args):
             "frac": kd["gbs"] / hbm_peak, "peak_source": f"{peak_src} (MEASURED_PEAKS.json hbm_gbs)",
             "traffic": traffic_for(names[dom], n_act), "algorithmic_bytes_per_launch": kd["bytes"],
             "avg_launch_ms": kd["avg_ms"]}
+    # FP64-pipe roof: GB300 issues 2 FP64 thread instructions per clock per
+    # SM; a kernel whose FP64 arithmetic takes longer at that rate than its
+    # bytes at the HBM peak is bound by the FP64 pipe (reported as "alu")
+    ent = profile_entry(names[dom])
+    if ent and ent.get("fp64_arith_inst_per_cell"):
+        sms = torch.cuda.get_device_properties(local).multi_processor_count
+        fp64_peak = 2.0 * sms * peaks.get("sm_max_mhz", 2070.0) * 1e6 / 1e9   # G FP64 instructions / s
+        fp64_inst = ent["fp64_arith_inst_per_cell"] * n_act
+        if fp64_inst / (fp64_peak * 1e9) > kd["bytes"] / (hbm_peak * 1e9):
+            achieved = fp64_inst / (kd["avg_ms"] * 1e-3) / 1e9
+            roof = {"kernel": names[dom], "bound": "alu", "achieved": achieved, "peak": fp64_peak,
+                    "unit": "G FP64 inst/s", "frac": achieved / fp64_peak,
+                    "peak_source": f"derived: 2 FP64 instructions/clk/SM x {sms} SMs x "
+                                   f"{peaks.get('sm_max_mhz', 2070.0):.0f} MHz (MEASURED_PEAKS.json sm_max_mhz)",
+                    "traffic": traffic_for(names[dom], n_act), "algorithmic_fp64_inst_per_launch": fp64_inst,
+                    "fp64_arith_inst_per_cell": ent["fp64_arith_inst_per_cell"],
+                    "fp64_pipe_active_pct_ncu": ent.get("fp64_pipe_active_pct"),
+                    "algorithmic_bytes_per_launch": kd["bytes"], "avg_launch_ms": kd["avg_ms"],
+                    "hbm": {"achieved": kd["gbs"], "peak": hbm_peak, "unit": "GB/s", "frac": kd["gbs"] / hbm_peak}}
 
     # ---- PCG stencil kernels on a grid far larger than L2 (HBM regime):
     # the 512x512x64 watershed (16.8 M cells), kernels timed by events
