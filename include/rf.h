@@ -87,6 +87,15 @@ typedef enum rf_precond { RF_PRECOND_JACOBI = 0, RF_PRECOND_MG = 1 } rf_precond;
  *   eps_chord   chord slope is replaced by dtheta/dh when |h^k - h^n| <= eps
  *   tol_inner, inner_max_it, outer_max_it   mixed precision inner FP32 PCG
  *               relative tolerance and caps                               */
+/* Picard linearisation (Sec. 2.2).  CHORD: the classical Picard iteration
+ * with the chord slope of theta* between h^n and h^k as capacity (the
+ * paper's scheme).  MODIFIED: the mass-conservative modified Picard
+ * iteration the paper also implements (the mixed form of Celia et al. 1990):
+ * capacity C(h^k), storage V [theta*(h^k) + C(h^k)(h^{k+1} - h^k) -
+ * theta*(h^n)] / dt.  Both converge to the same backward-Euler solution.
+ * The batched ensemble supports CHORD only. */
+typedef enum { RF_PICARD_CHORD = 0, RF_PICARD_MODIFIED = 1 } rf_picard_form;
+
 typedef struct rf_solver_params {
     double tol_picard, tol_cg;
     int cg_max_it;
@@ -97,11 +106,13 @@ typedef struct rf_solver_params {
     double eps_chord;
     double tol_inner;
     int inner_max_it, outer_max_it;
+    int picard_form;  /* rf_picard_form */
 } rf_solver_params;
 
 /* Fill *p with the defaults: tol_picard 1e-6, tol_cg 1e-10, cg_max_it 10000,
  * Jacobi, FP64, dt0 1, dt_max 600, dt_min 1e-3, f 1.3/1.3, n_inc 10, n_small 3,
- * n_max 8, eps_chord 1e-10, tol_inner 1e-4, inner_max_it 2000, outer_max_it 30. */
+ * n_max 8, eps_chord 1e-10, tol_inner 1e-4, inner_max_it 2000, outer_max_it 30,
+ * classical (chord) Picard. */
 void rf_default_params(rf_solver_params *p);
 
 /* Structured mesh of equal cells (the paper's solver requires a constant cell

@@ -15,6 +15,10 @@
  *     backward Euler for the pressure term, explicit (lagged one Picard iterate)
  *     gravity with linearly interpolated face conductivity, PCG linear solve,
  *     EBATS adaptive time stepping;
+ *   - Sec. 2.2 also names a modified Picard linearisation, kept for mass
+ *     conservation: the mixed-form scheme (theta expanded about the current
+ *     iterate, theta(h^{k+1}) ~ theta(h^k) + C(h^k) (h^{k+1} - h^k)), selected
+ *     with the parameter picard_form = 1;
  *   - Sec. 2.3: the Picard exit test is a global max over the domain;
  *   - Appendix A: Gardner conductivity K = Ks exp(alpha h) (test model).
  * Readings of passages the paper leaves open (storage S for h >= 0, the form
@@ -71,6 +75,7 @@ typedef struct or_problem {
     /* parameters */
     double tol_picard, tol_cg, dt0, dt_max, dt_min, f_grow, f_shrink, eps_chord;
     int cg_max_it, n_inc, n_small, n_max, solver;
+    int picard_form;     /* 0 classical Picard with chord capacity, 1 modified Picard */
 
     /* state */
     double *h;           /* N */
@@ -212,7 +217,7 @@ int or_set_param(or_problem *P, const char *name, double value)
 #define DP(nm) if (!strcmp(name, #nm)) { P->nm = value; return OR_OK; }
 #define IP(nm) if (!strcmp(name, #nm)) { P->nm = (int)value; return OR_OK; }
     DP(tol_picard) DP(tol_cg) DP(dt0) DP(dt_max) DP(dt_min) DP(f_grow) DP(f_shrink) DP(eps_chord)
-    IP(cg_max_it) IP(n_inc) IP(n_small) IP(n_max) IP(solver)
+    IP(cg_max_it) IP(n_inc) IP(n_small) IP(n_max) IP(solver) IP(picard_form)
 #undef DP
 #undef IP
     return OR_ERR_ARG;
@@ -275,6 +280,7 @@ typedef struct {
     double *val;
     double *b, *diag;      /* na */
     double *K, *theta, *c; /* na: K(h^k), theta*(h^k), V C^k / dt */
+    double *s0;            /* na: storage part of b (c h^n, or c h^k - V (theta^k - theta^n) / dt) */
     /* boundary-face bookkeeping for the mass balance: per active cell and
      * face, the flux into the cell as an affine function of x_P:
      *   flux = fa + fb * x_P  */
@@ -292,6 +298,7 @@ static void sys_alloc(or_system *S, int na)
     S->K = (double *)malloc(sizeof(double) * na);
     S->theta = (double *)malloc(sizeof(double) * na);
     S->c = (double *)malloc(sizeof(double) * na);
+    S->s0 = (double *)malloc(sizeof(double) * na);
     S->fa = (double *)malloc(sizeof(double) * 6 * (size_t)na);
     S->fb = (double *)malloc(sizeof(double) * 6 * (size_t)na);
 }
@@ -299,7 +306,7 @@ static void sys_alloc(or_system *S, int na)
 static void sys_free(or_system *S)
 {
     free(S->row_ptr); free(S->col); free(S->val); free(S->b); free(S->diag);
-    free(S->K); free(S->theta); free(S->c); free(S->fa); free(S->fb);
+    free(S->K); free(S->theta); free(S->c); free(S->s0); free(S->fa); free(S->fb);
 }
 
 /* neighbour of cell (i,j,k) across face f, or -1 outside the domain */
@@ -328,19 +335,29 @@ static void assemble(const or_problem *P, const double *hk, const double *hn, do
     double bcv[6];
     for (int f = 0; f < 6; f++) bcv[f] = P->bc[f].n > 0 ? series_at(&P->bc[f], t) : 0.0;
 
-    /* closures at h^k and the chord capacity */
+    /* closures at h^k and the capacity term.  Classical Picard: the chord
+     * slope C^k = (theta*(h^k) - theta*(h^n)) / (h^k - h^n), storage
+     * c (h^{k+1} - h^n).  Modified Picard: C^k = C(h^k), storage
+     * c (h^{k+1} - h^k) + V (theta*(h^k) - theta*(h^n)) / dt.  Both vanish
+     * in the same way at a converged iterate, V (theta* - theta*^n) / dt. */
     for (int a = 0; a < P->na; a++) {
         int p = P->cell[a];
         const or_soil *s = &P->zones[P->zone[p]];
         double thk, Kk, Ck, thn, Kn, Cn;
         closure(s, P->Ks[p], hk[p], &thk, &Kk, &Ck);
         closure(s, P->Ks[p], hn[p], &thn, &Kn, &Cn);
-        double Cch;
-        if (fabs(hk[p] - hn[p]) > P->eps_chord) Cch = (thk - thn) / (hk[p] - hn[p]);
-        else Cch = Ck;
         S->K[a] = Kk;
         S->theta[a] = thk;
-        S->c[a] = V * Cch / dt;
+        if (P->picard_form == 1) {
+            S->c[a] = V * Ck / dt;
+            S->s0[a] = S->c[a] * hk[p] - V * (thk - thn) / dt;
+        } else {
+            double Cch;
+            if (fabs(hk[p] - hn[p]) > P->eps_chord) Cch = (thk - thn) / (hk[p] - hn[p]);
+            else Cch = Ck;
+            S->c[a] = V * Cch / dt;
+            S->s0[a] = S->c[a] * hn[p];
+        }
     }
 
     int nnz = 0;
@@ -349,7 +366,7 @@ static void assemble(const or_problem *P, const double *hk, const double *hn, do
         int i = p % P->nx, j = (p / P->nx) % P->ny, k = p / (P->nx * P->ny);
         const or_soil *s = &P->zones[P->zone[p]];
         double diag = S->c[a];
-        double rhs = S->c[a] * hn[p];
+        double rhs = S->s0[a];
         int nb_col[6];
         double nb_val[6];
         for (int f = 0; f < 6; f++) {
@@ -547,7 +564,10 @@ static void attempt(const or_problem *P, double dt, double *hk_out, or_attempt *
             double lin = 0.0, bin = 0.0, bout = 0.0, ds = 0.0;
             for (int a = 0; a < na; a++) {
                 int p = P->cell[a];
-                lin += S.c[a] * dt * (x[a] - P->h[p]);
+                /* storage of the solved system: c (x - h^n), or for modified
+                 * Picard c (x - h^k) + V (theta*^k - theta*^n) / dt (= c x - s0) */
+                if (P->picard_form == 1) lin += dt * (S.c[a] * x[a] - S.s0[a]);
+                else lin += S.c[a] * dt * (x[a] - P->h[p]);
                 for (int f = 0; f < 6; f++) {
                     double fl = S.fa[6 * a + f] + S.fb[6 * a + f] * x[a];
                     if (fl > 0) bin += dt * fl; else bout -= dt * fl;

@@ -115,6 +115,7 @@ __device__ __forceinline__ double apply64(const Grid &g, long long p, const doub
 // With RESID, sT = sum over interior faces of T_f h^k_N (for b - A h^k).
 struct CellSystem {
     double c, rhs, diag, cb, sT, KP;
+    double s0;        // storage part of rhs
     double Tup[3];
 };
 
@@ -128,12 +129,23 @@ __device__ __forceinline__ void assemble_cell(const Grid &g, const DevSoil *__re
                                               double eps, double V_dt, CellSystem &out)
 {
     const double hkP = hk[p], hnP = hn[p], KP = K[p];
-    const double dh = hkP - hnP;
-    // |dh| > eps compared on the IEEE bit patterns (both non-negative)
-    const bool chord = (__double_as_longlong(dh) & 0x7fffffffffffffffLL) > __double_as_longlong(eps);
-    const double C = chord ? (thk[p] - thn[p]) * rcp64(dh) : Can[p];
+    double C, s0;
+    if (sp.modified) {
+        // modified Picard (Sec. 2.2, mass-conservative variant): theta*(h^{k+1})
+        // ~ theta*(h^k) + C(h^k) (h^{k+1} - h^k), so the storage term is
+        // c (h^{k+1} - h^k) + V (theta*(h^k) - theta*(h^n)) / dt
+        C = Can[p];
+        s0 = V_dt * C * hkP - V_dt * (thk[p] - thn[p]);
+    } else {
+        // classical Picard with the chord slope of theta* between h^n and h^k
+        const double dh = hkP - hnP;
+        // |dh| > eps compared on the IEEE bit patterns (both non-negative)
+        const bool chord = (__double_as_longlong(dh) & 0x7fffffffffffffffLL) > __double_as_longlong(eps);
+        C = chord ? (thk[p] - thn[p]) * rcp64(dh) : Can[p];
+        s0 = V_dt * C * hnP;
+    }
     const double c = V_dt * C;
-    double diag = c, rhs = c * hnP, cb = c;
+    double diag = c, rhs = s0, cb = c;
     double sT = 0.0;
     double Tup[3] = {0.0, 0.0, 0.0};
 #pragma unroll
@@ -176,6 +188,7 @@ __device__ __forceinline__ void assemble_cell(const Grid &g, const DevSoil *__re
         }
     }
     out.c = c;
+    out.s0 = s0;
     out.rhs = rhs;
     out.diag = diag;
     out.cb = cb;

@@ -119,7 +119,7 @@ k_assemble(Grid g, const DevSoil *__restrict__ soils, const uint8_t *__restrict_
            double *__restrict__ c_out, double *__restrict__ b, double *__restrict__ Tx, double *__restrict__ Ty,
            double *__restrict__ Tz, double *__restrict__ diag_out, double *__restrict__ dinv,
            float *__restrict__ K32, float *__restrict__ cb32, float *__restrict__ dinv32, const int *skip,
-           SolveStart st, double *partials, unsigned int *ticket)
+           SolveStart st, double *partials, unsigned int *ticket, double *__restrict__ s0_out)
 {
     count_launch(g, KK_ASSEMBLE);
     if (skip && *skip) {
@@ -161,6 +161,7 @@ k_assemble(Grid g, const DevSoil *__restrict__ soils, const uint8_t *__restrict_
         const double *Tup = cs.Tup;
         c_out[p] = c;
         b[p] = rhs;
+        if (s0_out) s0_out[p] = cs.s0;   // modified Picard: the water balance needs the storage part
         Tx[p] = Tup[0];
         Ty[p] = Tup[1];
         Tz[p] = Tup[2];
@@ -233,7 +234,7 @@ k_mass_balance(Grid g, const DevSoil *__restrict__ soils, const uint8_t *__restr
                const double *__restrict__ x_even, const double *__restrict__ hn, const double *__restrict__ c,
                const double *__restrict__ K_odd, const double *__restrict__ K_even, const double *__restrict__ thx,
                const double *__restrict__ thn, double *partials, unsigned int *ticket, StepResults *res,
-               const PicardCtl *ctl)
+               const PicardCtl *ctl, const double *__restrict__ s0)
 {
     count_launch(g, KK_MASS_BALANCE);
     if (ctl && !ctl->conv) return;
@@ -248,7 +249,9 @@ k_mass_balance(Grid g, const DevSoil *__restrict__ soils, const uint8_t *__restr
         const uint8_t fl = flags[p];
         if (!(fl & FLAG_ACTIVE)) continue;
         const double xp = x[p], hnP = hn[p];
-        v[0] += c[p] * dt * (xp - hnP);
+        // storage of the solved system: c (x - h^n), or with modified Picard
+        // c x - s0 = c (x - h^k) + V (theta*^k - theta*^n) / dt (times dt)
+        v[0] += s0 ? dt * (c[p] * xp - s0[p]) : c[p] * dt * (xp - hnP);
         v[1] += g.V * (thx[p] - thn[p]);
         if (!(fl & 0x3f)) continue;
         double fin, fout;
@@ -326,22 +329,22 @@ void launch_assemble(cudaStream_t s, int nblk, const Grid &g, const DevSoil *soi
                      const double *hn, const double *theta_k, const double *theta_n, const double *K,
                      const double *Can, double *c, double *b, double *Tx, double *Ty, double *Tz,
                      double *diag, double *dinv, float *K32, float *cb32, float *dinv32, const int *skip,
-                     int mode, const SolveStart *start, double *partials, unsigned int *ticket)
+                     int mode, const SolveStart *start, double *partials, unsigned int *ticket, double *s0)
 {
     SolveStart st{};
     if (start) st = *start;
     if (mode == ASM_CG64)
         k_assemble<ASM_CG64><<<nblk, RED_THREADS, 0, s>>>(g, soils, zone, Ks, flags, sp, hk, hn, theta_k, theta_n, K,
                                                           Can, c, b, Tx, Ty, Tz, diag, dinv, K32, cb32, dinv32, skip,
-                                                          st, partials, ticket);
+                                                          st, partials, ticket, s0);
     else if (mode == ASM_MIXED)
         k_assemble<ASM_MIXED><<<nblk, RED_THREADS, 0, s>>>(g, soils, zone, Ks, flags, sp, hk, hn, theta_k, theta_n,
                                                            K, Can, c, b, Tx, Ty, Tz, diag, dinv, K32, cb32, dinv32,
-                                                           skip, st, partials, ticket);
+                                                           skip, st, partials, ticket, s0);
     else
         k_assemble<ASM_ONLY><<<nblk, RED_THREADS, 0, s>>>(g, soils, zone, Ks, flags, sp, hk, hn, theta_k, theta_n, K,
                                                           Can, c, b, Tx, Ty, Tz, diag, dinv, K32, cb32, dinv32, skip,
-                                                          st, partials, ticket);
+                                                          st, partials, ticket, s0);
 }
 
 void launch_accept(cudaStream_t s, int nblk, const Grid &g, const double *x_final, double *h,
@@ -354,10 +357,10 @@ void launch_mass_balance(cudaStream_t s, int nblk, const Grid &g, const DevSoil 
                          const double *Ks, const uint8_t *flags, const StepParams *sp, const double *x_odd,
                          const double *x_even, const double *hn, const double *c, const double *K_odd,
                          const double *K_even, const double *theta_x, const double *theta_n, double *partials,
-                         unsigned int *ticket, StepResults *res, const PicardCtl *ctl)
+                         unsigned int *ticket, StepResults *res, const PicardCtl *ctl, const double *s0)
 {
     k_mass_balance<<<nblk, RED_THREADS, 0, s>>>(g, soils, zone, Ks, flags, sp, x_odd, x_even, hn, c, K_odd, K_even,
-                                                theta_x, theta_n, partials, ticket, res, ctl);
+                                                theta_x, theta_n, partials, ticket, res, ctl, s0);
 }
 
 void launch_storage(cudaStream_t s, int nblk, const Grid &g, const uint8_t *flags, const double *theta,

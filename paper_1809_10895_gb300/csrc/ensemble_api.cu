@@ -144,6 +144,8 @@ rf_status rf_ens_create(const rf_ens_instance *inst, int n, const rf_solver_para
     if (params) prm = *params;
     if (prm.precision != RF_PREC_FP64 && prm.precision != RF_PREC_MIXED)
         return efail(RF_ERR_ARG, "rf_ens_create: unknown precision");
+    if (prm.picard_form != RF_PICARD_CHORD)
+        return efail(RF_ERR_ARG, "rf_ens_create: the ensemble runs the classical (chord) Picard iteration only");
     int ndev = 0;
     if (cudaGetDeviceCount(&ndev) != cudaSuccess || ndev < 1) {
         cudaGetLastError();

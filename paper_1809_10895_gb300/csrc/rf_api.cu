@@ -69,6 +69,7 @@ struct rf_ctx {
     FFTables *fftab = nullptr;
     double *h = nullptr, *hk = nullptr, *x = nullptr, *theta_n = nullptr, *theta_k = nullptr;
     double *K[2] = {nullptr, nullptr}, *Can = nullptr, *c = nullptr, *b = nullptr;
+    double *s0 = nullptr;                // modified Picard: storage part of b (water balance)
     double *Tx = nullptr, *Ty = nullptr, *Tz = nullptr, *diag = nullptr, *dinv = nullptr;
     double *r = nullptr, *z = nullptr, *p[2] = {nullptr, nullptr}, *q = nullptr;
     float *K32 = nullptr, *cb32 = nullptr, *dinv32 = nullptr, *r32 = nullptr, *z32 = nullptr;
@@ -142,6 +143,8 @@ rf_status check_params(const rf_solver_params *p)
         return fail(RF_ERR_ARG, "unknown precision mode");
     if (p->precond != RF_PRECOND_JACOBI && p->precond != RF_PRECOND_MG)
         return fail(RF_ERR_ARG, "unknown preconditioner");
+    if (p->picard_form != RF_PICARD_CHORD && p->picard_form != RF_PICARD_MODIFIED)
+        return fail(RF_ERR_ARG, "unknown Picard linearisation");
     if (p->precond == RF_PRECOND_MG && p->precision != RF_PREC_MIXED)
         return fail(RF_ERR_ARG, "the multigrid preconditioner serves the FP32 inner solve: use RF_PREC_MIXED");
     return RF_OK;
@@ -173,12 +176,16 @@ rf_status sync(rf_ctx *c)
     return RF_OK;
 }
 
+// storage part of b, written and read only with modified Picard
+double *s0_of(rf_ctx *c) { return c->prm.picard_form == RF_PICARD_MODIFIED ? c->s0 : nullptr; }
+
 void fill_step_params(rf_ctx *c, double dt)
 {
     StepParams &s = *c->sp_h;
     s.dt = dt;
     s.t = c->t;
     s.eps_chord = c->prm.eps_chord;
+    s.modified = c->prm.picard_form == RF_PICARD_MODIFIED ? 1 : 0;
     for (int f = 0; f < 6; f++) {
         s.bc_type[f] = c->bc[f].type;
         s.bc_val[f] = c->bc[f].v.empty() ? 0.0 : series_at(c->bc[f], c->t);
@@ -197,7 +204,7 @@ void run_assemble(rf_ctx *c, const double *hk, const double *hn, const double *t
 {
     launch_assemble(c->stream, c->nblk, c->g, c->soils, c->zone, c->Ks, c->flags, c->sp, hk, hn, thk, thn,
                     c->K[0], c->Can, c->c, c->b, c->Tx, c->Ty, c->Tz, c->diag, c->dinv, c->K32, c->cb32,
-                    c->dinv32, nullptr);
+                    c->dinv32, nullptr, ASM_ONLY, nullptr, nullptr, nullptr, s0_of(c));
 }
 
 // ---------------------------------------------------------------------------
@@ -456,7 +463,8 @@ rf_status build_picard_graph(rf_ctx *c)
         RF_TRY(cap_begin(c, body, deps));
         launch_assemble(s, nb, g, c->soils, c->zone, c->Ks, c->flags, c->sp, hk, c->h, c->theta_k, c->theta_n, Kin,
                         c->Can, c->c, c->b, c->Tx, c->Ty, c->Tz, c->diag, c->dinv, c->K32, c->cb32, c->dinv32, skip,
-                        c->prm.precision == RF_PREC_FP64 ? ASM_CG64 : ASM_MIXED, &st, c->partials, c->ticket);
+                        c->prm.precision == RF_PREC_FP64 ? ASM_CG64 : ASM_MIXED, &st, c->partials, c->ticket,
+                        s0_of(c));
         RF_TRY(cap_end(c, deps));
         RF_TRY(capture_solve(c, G, body, deps, hk, x, skip, true, &st, deps));
         RF_TRY(cap_begin(c, body, deps));
@@ -472,7 +480,7 @@ rf_status build_picard_graph(rf_ctx *c)
     std::vector<cudaGraphNode_t> after;
     RF_TRY(cap_begin(c, G, {wp}));
     launch_mass_balance(s, nb, g, c->soils, c->zone, c->Ks, c->flags, c->sp, c->x, c->hk, c->h, c->c, c->K[0],
-                        c->K[1], c->theta_k, c->theta_n, c->partials, c->ticket, c->res, c->ctl);
+                        c->K[1], c->theta_k, c->theta_n, c->partials, c->ticket, c->res, c->ctl, s0_of(c));
     RF_TRY(cap_end(c, after));
     CUDA_TRY(cudaGraphInstantiate(&c->picard_exec, G, 0));
     return RF_OK;
@@ -669,6 +677,7 @@ void rf_default_params(rf_solver_params *p)
     p->tol_inner = 1e-4;
     p->inner_max_it = 2000;
     p->outer_max_it = 30;
+    p->picard_form = RF_PICARD_CHORD;
 }
 
 const char *rf_last_error(void) { return g_err.c_str(); }
@@ -754,6 +763,7 @@ rf_status rf_mesh_create(const rf_mesh_desc *mesh, const rf_solver_params *param
               alloc_n(c, c->soils, 256) && alloc_n(c, c->h, N) && alloc_n(c, c->hk, N) && alloc_n(c, c->x, N) &&
               alloc_n(c, c->theta_n, N) && alloc_n(c, c->theta_k, N) && alloc_n(c, c->K[0], N) &&
               alloc_n(c, c->K[1], N) && alloc_n(c, c->Can, N) && alloc_n(c, c->c, N) && alloc_n(c, c->b, N) &&
+              (c->prm.picard_form != RF_PICARD_MODIFIED || alloc_n(c, c->s0, N)) &&
               alloc_n(c, c->Tx, N) && alloc_n(c, c->Ty, N) && alloc_n(c, c->Tz, N) && alloc_n(c, c->diag, N) &&
               alloc_n(c, c->dinv, N) && alloc_n(c, c->r, N) && alloc_n(c, c->z, N) && alloc_n(c, c->p[0], N) &&
               alloc_n(c, c->p[1], N) && alloc_n(c, c->q, N) && alloc_n(c, c->K32, N) && alloc_n(c, c->cb32, N) &&
@@ -833,6 +843,8 @@ rf_status rf_set_params(rf_ctx *c, const rf_solver_params *params)
     if (!c || !params) return fail(RF_ERR_ARG, "null argument");
     if (rf_status st = check_params(params)) return st;
     CUDA_TRY(cudaStreamSynchronize(c->stream));
+    if (params->picard_form == RF_PICARD_MODIFIED && !c->s0 && !alloc_n(c, c->s0, c->g.N))
+        return fail(RF_ERR_NOMEM, "rf_set_params: device allocation failed");
     destroy_graphs(c);   // tolerances and caps are baked into the graphs
     c->prm = *params;
     return RF_OK;
@@ -903,6 +915,9 @@ static rf_status state_set_common(rf_ctx *c, double t)
     c->easy = 0;
     c->steps = 0;
     run_closure(c, c->h, nullptr, c->theta_n, 0);
+    // closure_at_h promises K[0], C and theta_k at h: theta_k too (the
+    // modified Picard form reads theta*(h^k) on the first iteration)
+    CUDA_TRY(cudaMemcpyAsync(c->theta_k, c->theta_n, sizeof(double) * c->g.N, cudaMemcpyDeviceToDevice, c->stream));
     c->closure_at_h = true;
     double st0 = 0.0;
     if (rf_status st = storage_of_theta_n(c, &st0)) return st;

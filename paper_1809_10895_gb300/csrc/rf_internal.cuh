@@ -79,6 +79,7 @@ struct StepParams {
     double dt, t, eps_chord;
     int bc_type[6];
     double bc_val[6];
+    int modified;   // 1: modified Picard (tangent capacity, mixed-form storage); 0: chord capacity
 };
 
 // Device-side scalars of one PCG solve.
@@ -266,13 +267,13 @@ void launch_assemble(cudaStream_t s, int nblk, const Grid &g, const DevSoil *soi
                      const double *Can, double *c, double *b, double *Tx, double *Ty, double *Tz,
                      double *diag, double *dinv, float *K32, float *cb32, float *dinv32, const int *skip,
                      int mode = ASM_ONLY, const SolveStart *start = nullptr, double *partials = nullptr,
-                     unsigned int *ticket = nullptr);
+                     unsigned int *ticket = nullptr, double *s0 = nullptr);
 
 void launch_mass_balance(cudaStream_t s, int nblk, const Grid &g, const DevSoil *soils, const uint8_t *zone,
                          const double *Ks, const uint8_t *flags, const StepParams *sp, const double *x_odd,
                          const double *x_even, const double *hn, const double *c, const double *K_odd,
                          const double *K_even, const double *theta_x, const double *theta_n, double *partials,
-                         unsigned int *ticket, StepResults *res, const PicardCtl *ctl);
+                         unsigned int *ticket, StepResults *res, const PicardCtl *ctl, const double *s0 = nullptr);
 
 void launch_storage(cudaStream_t s, int nblk, const Grid &g, const uint8_t *flags, const double *theta,
                     double *partials, unsigned int *ticket, StepResults *res);

@@ -29,6 +29,7 @@ BC_TYPES = {"zero_flux": 0, "dirichlet": 1, "flux": 2, "free_drainage": 3, "seep
 MODELS = {"vg": RF_VG, "gardner": RF_GARDNER}
 PRECISION = {"fp64": 0, "mixed": 1}
 PRECOND = {"jacobi": 0, "mg": 1}
+PICARD_FORM = {"chord": 0, "modified": 1}
 
 
 class rf_solver_params(C.Structure):
@@ -36,7 +37,7 @@ class rf_solver_params(C.Structure):
                 ("precond", C.c_int), ("precision", C.c_int), ("dt0", C.c_double), ("dt_max", C.c_double),
                 ("dt_min", C.c_double), ("f_grow", C.c_double), ("f_shrink", C.c_double), ("n_inc", C.c_int),
                 ("n_small", C.c_int), ("n_max", C.c_int), ("eps_chord", C.c_double), ("tol_inner", C.c_double),
-                ("inner_max_it", C.c_int), ("outer_max_it", C.c_int)]
+                ("inner_max_it", C.c_int), ("outer_max_it", C.c_int), ("picard_form", C.c_int)]
 
 
 class rf_mesh_desc(C.Structure):
@@ -202,6 +203,8 @@ def default_params(**kw) -> rf_solver_params:
             v = PRECISION[v]
         if k == "precond" and isinstance(v, str):
             v = PRECOND[v]
+        if k == "picard_form" and isinstance(v, str):
+            v = PICARD_FORM[v]
         setattr(p, k, v)
     return p
 
@@ -298,6 +301,10 @@ class Solver:
         for k, v in kw.items():
             if k == "precision" and isinstance(v, str):
                 v = PRECISION[v]
+            if k == "precond" and isinstance(v, str):
+                v = PRECOND[v]
+            if k == "picard_form" and isinstance(v, str):
+                v = PICARD_FORM[v]
             setattr(p, k, v)
         _check(load().rf_set_params(self.ctx, C.byref(p)), "rf_set_params")
 

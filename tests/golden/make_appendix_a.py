@@ -26,7 +26,7 @@ CONFIG = dict(L=1.0, nz=100, Ks=1e-6, alpha=0.06, theta_r=0.05, theta_s=0.40, S=
 FLUXES = [-4e-6, -1e-6, 5e-7, 9e-7]     # evaporation (< 0) and infiltration (> 0)
 
 
-def oracle_column(q, cfg=CONFIG):
+def oracle_column(q, cfg=CONFIG, picard_form=0):
     nz = cfg["nz"]
     dz = cfg["L"] / nz
     o = O.Oracle(1, 1, nz, 1.0, 1.0, dz, 0.0, None)
@@ -36,7 +36,7 @@ def oracle_column(q, cfg=CONFIG):
     o.set_bc(O.ZMAX, O.FLUX, np.array([0.0]), np.array([q]))
     o.set_params(tol_cg=cfg["tol_cg"], tol_picard=cfg["tol_picard"], dt0=cfg["dt0"], dt_max=cfg["dt_max"],
                  cg_max_it=10000, dt_min=1e-3, f_grow=1.3, f_shrink=1.3, n_inc=10, n_small=3, n_max=8,
-                 eps_chord=1e-10)
+                 eps_chord=1e-10, picard_form=picard_form)
     zc = (np.arange(nz) + 0.5) * dz
     o.set_state(-zc, 0.0)
     o.run(cfg["t_end"])

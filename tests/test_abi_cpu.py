@@ -31,11 +31,15 @@ def test_default_params_match_documented_defaults(lib):
     assert (p.tol_picard, p.tol_cg, p.cg_max_it) == (1e-6, 1e-10, 10000)
     assert (p.dt0, p.dt_max, p.dt_min, p.f_grow, p.f_shrink) == (1.0, 600.0, 1e-3, 1.3, 1.3)
     assert (p.n_inc, p.n_small, p.n_max) == (10, 3, 8)
+    assert p.picard_form == rf.PICARD_FORM["chord"]
 
 
 def test_struct_layouts_match_header(lib):
     # sizes of the ABI structs on this platform (LP64)
-    assert C.sizeof(rf.rf_solver_params) == 8 * 2 + 4 * 3 + 4 + 8 * 5 + 4 * 3 + 4 + 8 * 2 + 4 * 2
+    # ... picard_form and the tail padding to 8 bytes
+    assert C.sizeof(rf.rf_solver_params) == 8 * 2 + 4 * 3 + 4 + 8 * 5 + 4 * 3 + 4 + 8 * 2 + 4 * 2 + 4 + 4
+    # rf_ens_stats: t, dt_nom; 4 counters; status (+4); cells; 5 balances; busy_s; ctas (+4)
+    assert C.sizeof(rf.rf_ens_stats) == 8 * 2 + 8 * 4 + 4 + 4 + 8 + 8 * 5 + 8 + 4 + 4
     assert C.sizeof(rf.rf_step_info) == 8 * 2 + 4 * 3 + 4 + 8
     assert C.sizeof(rf.rf_mesh_desc) == 4 * 3 + 4 + 8 * 4 + 8
 
