@@ -120,67 +120,6 @@ k_conv3d(const __nv_bfloat16 *__restrict__ in, const __nv_bfloat16 *__restrict__
             }
 }
 
-// dW[co][tap CIN + ci] += sum_v in[v + tap][ci] dout[v][co]; db[co] += sum_v dout[v][co].
-// blockIdx.y = tap; the x blocks stride over chunks of VC voxels, each thread
-// keeps PT (ci, co) sums in registers and adds them to dW once at the end.
-template <int CIN, int COUT>
-__global__ void __launch_bounds__(256)
-k_conv3d_wgrad(const __nv_bfloat16 *__restrict__ in, const float *__restrict__ dout, int B, int D, int H, int W,
-               float *__restrict__ dW, float *__restrict__ db)
-{
-    constexpr int VC = 32;
-    constexpr int K = 27 * CIN;
-    constexpr int KP = (K + 15) / 16 * 16;
-    constexpr int PT = CIN * COUT / 256;
-    static_assert(PT >= 1 && CIN * COUT == 256 * PT, "one thread per PT (ci, co) pairs");
-    __shared__ float s_in[VC][CIN];
-    __shared__ __align__(16) float s_d[VC][COUT];
-    const long long M = (long long)B * D * H * W;
-    const int tap = blockIdx.y;
-    const int dz = tap / 9 - 1, dy = (tap / 3) % 3 - 1, dx = tap % 3 - 1;
-    const int ci = threadIdx.x % CIN, co0 = (threadIdx.x / CIN) * PT;
-    float acc[PT];
-#pragma unroll
-    for (int e = 0; e < PT; e++) acc[e] = 0.0f;
-    float accb = 0.0f;
-    for (long long v0 = (long long)blockIdx.x * VC; v0 < M; v0 += (long long)gridDim.x * VC) {
-        for (int e = threadIdx.x; e < VC * COUT; e += blockDim.x) {
-            const long long m = v0 + e / COUT;
-            s_d[e / COUT][e % COUT] = m < M ? dout[m * COUT + e % COUT] : 0.0f;
-        }
-        for (int e = threadIdx.x; e < VC * CIN; e += blockDim.x) {
-            const long long m = v0 + e / CIN;
-            float val = 0.0f;
-            if (m < M) {
-                const int x = (int)(m % W);
-                long long q = m / W;
-                const int y = (int)(q % H);
-                q /= H;
-                const int z = (int)(q % D);
-                const int b = (int)(q / D);
-                const int zz = z + dz, yy = y + dy, xx = x + dx;
-                if (zz >= 0 && zz < D && yy >= 0 && yy < H && xx >= 0 && xx < W) {
-                    const long long vv = xx + (long long)W * (yy + (long long)H * (zz + (long long)D * b));
-                    val = __bfloat162float(in[vv * CIN + e % CIN]);
-                }
-            }
-            s_in[e / CIN][e % CIN] = val;
-        }
-        __syncthreads();
-#pragma unroll 4
-        for (int u = 0; u < VC; u++) {
-            const float xv = s_in[u][ci];
-#pragma unroll
-            for (int e = 0; e < PT; e++) acc[e] = fmaf(xv, s_d[u][co0 + e], acc[e]);
-        }
-        if (tap == 13 && threadIdx.x < COUT)
-            for (int u = 0; u < VC; u++) accb += s_d[u][threadIdx.x];
-        __syncthreads();
-    }
-#pragma unroll
-    for (int e = 0; e < PT; e++) atomicAdd(&dW[(long long)(co0 + e) * KP + tap * CIN + ci], acc[e]);
-    if (tap == 13 && threadIdx.x < COUT && db) atomicAdd(&db[threadIdx.x], accb);
-}
 
 // Weight gradient of a convolution on the tensor cores (mma.sync m16n8k16,
 // BF16 in, FP32 accumulate):
@@ -504,21 +443,6 @@ cudaError_t conv3d(cudaStream_t s, int cin, int cout, const void *in, const void
     if (cin == 8 && cout == 32) k_conv3d<8, 32><<<grid, 32 * CONV_WARPS, 0, s>>>(i, w, bias, r, ob, out_f, B, D, H, W, relu);
     else if (cin == 32 && cout == 32) k_conv3d<32, 32><<<grid, 32 * CONV_WARPS, 0, s>>>(i, w, bias, r, ob, out_f, B, D, H, W, relu);
     else if (cin == 32 && cout == 8) k_conv3d<32, 8><<<grid, 32 * CONV_WARPS, 0, s>>>(i, w, bias, r, ob, out_f, B, D, H, W, relu);
-    else return cudaErrorInvalidValue;
-    return cudaGetLastError();
-}
-
-cudaError_t conv3d_wgrad(cudaStream_t s, int cin, int cout, const void *in, const float *dout, int B, int D, int H,
-                         int W, float *dW, float *db, int num_sms)
-{
-    const long long M = (long long)B * D * H * W;
-    const long long chunks = (M + 31) / 32;
-    const long long want = (8LL * num_sms) / 27 > 0 ? (8LL * num_sms) / 27 : 1;   // about 8 blocks per SM in all
-    dim3 grid((unsigned)(chunks < want ? chunks : want), 27);
-    auto i = static_cast<const __nv_bfloat16 *>(in);
-    if (cin == 8 && cout == 32) k_conv3d_wgrad<8, 32><<<grid, 256, 0, s>>>(i, dout, B, D, H, W, dW, db);
-    else if (cin == 32 && cout == 32) k_conv3d_wgrad<32, 32><<<grid, 256, 0, s>>>(i, dout, B, D, H, W, dW, db);
-    else if (cin == 32 && cout == 8) k_conv3d_wgrad<32, 8><<<grid, 256, 0, s>>>(i, dout, B, D, H, W, dW, db);
     else return cudaErrorInvalidValue;
     return cudaGetLastError();
 }

@@ -28,9 +28,6 @@ struct WsScales {
 // BF16 in, FP32 accumulate; out_b (BF16) and/or out_f (FP32) written.
 cudaError_t conv3d(cudaStream_t s, int cin, int cout, const void *in, const void *Wb, const float *bias,
                    const void *res, void *out_b, float *out_f, int B, int D, int H, int W, int relu);
-// dW[co][tap cin + ci] += sum_v in[v + tap][ci] dout[v][co], db[co] += sum_v dout[v][co]
-cudaError_t conv3d_wgrad(cudaStream_t s, int cin, int cout, const void *in, const float *dout, int B, int D, int H,
-                         int W, float *dW, float *db, int num_sms);
 // Convolutions on the tcgen05 tensor cores (conv_tc.cu).  in: cin_mem (8 or
 // 32) BF16 channels per voxel, zero-padded to cinp (16 or 32) planes; Wb:
 // nout x 27 cinp BF16 weights (K = tap cinp + c); nout GEMM columns (16 or

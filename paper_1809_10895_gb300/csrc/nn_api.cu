@@ -260,14 +260,6 @@ __global__ void k_take0(const float *__restrict__ y8, float *__restrict__ y, lon
         y[i] = y8[i * nn::C_OUT_P];
 }
 
-rf_status wgrad(rf_nn *n, cudaStream_t s, int l, const void *in, const float *dout, int B, int D, int H, int W)
-{
-    const LayerDims &d = n->L[l];
-    n->launches++;
-    NN_CUDA(nn::conv3d_wgrad(s, d.cinp, d.coutp, in, dout, B, D, H, W, n->G + d.w, n->G + d.b, n->num_sms));
-    return RF_OK;
-}
-
 // Weight gradient of a 32 -> 32 layer from its BF16 input and BF16 output
 // gradient, on the tensor cores.
 rf_status wgrad_tc(rf_nn *n, cudaStream_t s, int l, const void *in, const void *g_bf16, int B, int D, int H, int W)
