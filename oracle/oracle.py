@@ -26,7 +26,7 @@ LIB = os.path.join(BUILD_DIR, "liboracle.so")
 VG, GARDNER = 0, 1
 ZERO_FLUX, DIRICHLET, FLUX, FREE_DRAINAGE, SEEPAGE = range(5)
 XMIN, XMAX, YMIN, YMAX, ZMIN, ZMAX = range(6)
-SOLVER_PCG, SOLVER_DENSE = 0, 1
+SOLVER_PCG, SOLVER_DENSE, SOLVER_DIC, SOLVER_DIC_RB = 0, 1, 2, 3
 
 
 def build(force: bool = False) -> str:
@@ -228,12 +228,15 @@ class Oracle:
             out["csr"] = (rp, col[:nnz.value].copy(), val[:nnz.value].copy())
         return out
 
-    def solve(self, hk, hn, dt, t=0.0, x0=None, dense=False):
+    def solve(self, hk, hn, dt, t=0.0, x0=None, dense=False, method=None):
+        """One linear solve of the system at (hk, hn, dt, t): Jacobi-PCG by
+        default, dense Cholesky (dense=True) or method = SOLVER_* ."""
         hk = np.ascontiguousarray(hk, dtype=np.float64).ravel()
         hn = np.ascontiguousarray(hn, dtype=np.float64).ravel()
         x = (hk[self.active_cells] if x0 is None else np.asarray(x0, dtype=np.float64)).copy()
         res = C.c_double(0.0)
-        it = lib().or_solve(self.h, _d(hk), _d(hn), float(dt), float(t), _d(x), int(dense), C.byref(res))
+        m = SOLVER_DENSE if dense else (SOLVER_PCG if method is None else int(method))
+        it = lib().or_solve(self.h, _d(hk), _d(hn), float(dt), float(t), _d(x), m, C.byref(res))
         return x, it, res.value
 
     def spmv(self, hk, hn, dt, x, t=0.0):

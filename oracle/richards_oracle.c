@@ -44,7 +44,10 @@ enum { OR_VG = 0, OR_GARDNER = 1 };
 enum { OR_ZERO_FLUX = 0, OR_DIRICHLET = 1, OR_FLUX = 2, OR_FREE_DRAINAGE = 3, OR_SEEPAGE = 4 };
 enum { OR_XMIN = 0, OR_XMAX, OR_YMIN, OR_YMAX, OR_ZMIN, OR_ZMAX, OR_NFACES };
 enum { OR_OK = 0, OR_ERR_ARG = 1, OR_ERR_PICARD = 6, OR_ERR_DT_MIN = 7, OR_ERR_CG = 8 };
-enum { OR_SOLVER_PCG = 0, OR_SOLVER_DENSE = 1 };
+/* linear solvers: Jacobi-PCG, dense Cholesky (tiny grids), and PCG with the
+ * diagonal incomplete Cholesky (DIC) preconditioner the paper uses (Sec. 2.2),
+ * eliminating cells in natural (cell index) order or red-black order */
+enum { OR_SOLVER_PCG = 0, OR_SOLVER_DENSE = 1, OR_SOLVER_DIC = 2, OR_SOLVER_DIC_RB = 3 };
 
 typedef struct {
     int model;
@@ -488,6 +491,93 @@ static int pcg_jacobi(int n, const int *rp, const int *col, const double *val, c
     return status ? status : it;
 }
 
+/* PCG with the diagonal incomplete Cholesky (DIC) preconditioner of Sec. 2.2:
+ * with L the strictly lower part of A in the elimination order and D the
+ * diagonal with d_a = a_aa - sum_{b before a} a_ab^2 / d_b, M = (D + L) D^{-1}
+ * (D + L^T) has the diagonal of A and the couplings of A.  z = M^{-1} r by a
+ * forward sweep (D + L) u = r and a backward sweep (D + L^T) z = D u.  order:
+ * the compact cells in elimination order; rank: the inverse permutation.
+ * The rest is the textbook PCG of pcg_jacobi. */
+static int pcg_dic(int n, const int *rp, const int *col, const double *val, const double *b, double *x,
+                   double tol, int max_it, const int *order, const int *rank, double *res_out)
+{
+    double *d = (double *)malloc(sizeof(double) * n), *u = (double *)malloc(sizeof(double) * n);
+    double *r = (double *)malloc(sizeof(double) * n), *z = (double *)malloc(sizeof(double) * n);
+    double *p = (double *)malloc(sizeof(double) * n), *q = (double *)malloc(sizeof(double) * n);
+    int status = 0, it = 0;
+    /* D: the pivots of the incomplete factorisation */
+    for (int o = 0; o < n && !status; o++) {
+        int a = order[o];
+        double s = 0.0, aa = 0.0;
+        for (int e = rp[a]; e < rp[a + 1]; e++) {
+            int c = col[e];
+            if (c == a) aa = val[e];
+            else if (rank[c] < rank[a]) s += val[e] * val[e] / d[c];
+        }
+        d[a] = aa - s;
+        if (!(d[a] > 0.0)) status = -2;
+    }
+    double rnorm = 0.0;
+    if (!status) {
+        csr_spmv(n, rp, col, val, x, q);
+        for (int i = 0; i < n; i++) r[i] = b[i] - q[i];
+        double bnorm = sqrt(dot(n, b, b));
+        rnorm = sqrt(dot(n, r, r));
+        double rz = 0.0;
+        for (it = 0; it <= max_it; it++) {
+            if (rnorm <= tol * bnorm) break;
+            if (it == max_it) { status = -1; break; }
+            /* z = M^{-1} r */
+            for (int o = 0; o < n; o++) {
+                int a = order[o];
+                double s = r[a];
+                for (int e = rp[a]; e < rp[a + 1]; e++)
+                    if (col[e] != a && rank[col[e]] < rank[a]) s -= val[e] * u[col[e]];
+                u[a] = s / d[a];
+            }
+            for (int o = n - 1; o >= 0; o--) {
+                int a = order[o];
+                double s = 0.0;
+                for (int e = rp[a]; e < rp[a + 1]; e++)
+                    if (col[e] != a && rank[col[e]] > rank[a]) s += val[e] * z[col[e]];
+                z[a] = u[a] - s / d[a];
+            }
+            double rz_new = dot(n, r, z);
+            if (it == 0) for (int i = 0; i < n; i++) p[i] = z[i];
+            else {
+                double beta = rz_new / rz;
+                for (int i = 0; i < n; i++) p[i] = z[i] + beta * p[i];
+            }
+            rz = rz_new;
+            csr_spmv(n, rp, col, val, p, q);
+            double alpha = rz / dot(n, p, q);
+            for (int i = 0; i < n; i++) { x[i] += alpha * p[i]; r[i] -= alpha * q[i]; }
+            rnorm = sqrt(dot(n, r, r));
+            if (!isfinite(rnorm)) { status = -2; break; }
+        }
+    }
+    if (res_out) *res_out = rnorm;
+    free(d); free(u); free(r); free(z); free(p); free(q);
+    return status ? status : it;
+}
+
+/* Elimination order of the compact cells: natural (cell index), or red-black
+ * (cells with i + j + k even first, each colour in cell index order). */
+static void dic_order(const or_problem *P, int red_black, int *order, int *rank)
+{
+    int o = 0;
+    for (int pass = 0; pass < (red_black ? 2 : 1); pass++)
+        for (int a = 0; a < P->na; a++) {
+            int c = P->cell[a];
+            int i = c % P->nx, j = (c / P->nx) % P->ny, k = c / (P->nx * P->ny);
+            if (!red_black || ((i + j + k) & 1) == pass) order[o++] = a;
+        }
+    for (int q = 0; q < P->na; q++) rank[order[q]] = q;
+}
+
+/* One linear solve of an assembled system with the problem's solver. */
+static int solve_system(const or_problem *P, int method, const or_system *S, double *x, double *res_out);
+
 /* Dense Cholesky solve of the same system (tiny grids only): A = L L^T. */
 static int dense_cholesky(int n, const int *rp, const int *col, const double *val, const double *b, double *x)
 {
@@ -542,8 +632,7 @@ static void attempt(const or_problem *P, double dt, double *hk_out, or_attempt *
         assemble(P, hk, P->h, dt, P->t, &S);
         for (int a = 0; a < na; a++) x[a] = hk[P->cell[a]];
         int cg;
-        if (P->solver == OR_SOLVER_DENSE) cg = dense_cholesky(na, S.row_ptr, S.col, S.val, S.b, x);
-        else cg = pcg_jacobi(na, S.row_ptr, S.col, S.val, S.diag, S.b, x, P->tol_cg, P->cg_max_it, NULL);
+        cg = solve_system(P, P->solver, &S, x, NULL);
         R->picard = it;
         if (cg < 0) { R->status = OR_ERR_CG; break; }
         R->cg += cg;
@@ -726,17 +815,32 @@ int or_assemble(or_problem *P, const double *hk, const double *hn, double dt, do
     return OR_OK;
 }
 
-/* Solve A x = b for the system assembled at (h^k, h^n, dt, t); x holds x0 on
- * entry (compact active order).  Returns iterations (PCG) or a negative code. */
+static int solve_system(const or_problem *P, int method, const or_system *S, double *x, double *res_out)
+{
+    if (method == OR_SOLVER_DENSE) return dense_cholesky(P->na, S->row_ptr, S->col, S->val, S->b, x);
+    if (method == OR_SOLVER_DIC || method == OR_SOLVER_DIC_RB) {
+        int *order = (int *)malloc(sizeof(int) * (P->na ? P->na : 1));
+        int *rank = (int *)malloc(sizeof(int) * (P->na ? P->na : 1));
+        dic_order(P, method == OR_SOLVER_DIC_RB, order, rank);
+        int r = pcg_dic(P->na, S->row_ptr, S->col, S->val, S->b, x, P->tol_cg, P->cg_max_it, order, rank,
+                        res_out);
+        free(order);
+        free(rank);
+        return r;
+    }
+    return pcg_jacobi(P->na, S->row_ptr, S->col, S->val, S->diag, S->b, x, P->tol_cg, P->cg_max_it, res_out);
+}
+
+/* Solve A x = b for the system assembled at (h^k, h^n, dt, t) with method
+ * (an OR_SOLVER_* value); x holds x0 on entry (compact active order).
+ * Returns iterations (PCG) or a negative code. */
 int or_solve(or_problem *P, const double *hk, const double *hn, double dt, double t,
-             double *x, int dense, double *res_out)
+             double *x, int method, double *res_out)
 {
     or_system S;
     sys_alloc(&S, P->na);
     assemble(P, hk, hn, dt, t, &S);
-    int r = dense ? dense_cholesky(P->na, S.row_ptr, S.col, S.val, S.b, x)
-                  : pcg_jacobi(P->na, S.row_ptr, S.col, S.val, S.diag, S.b, x, P->tol_cg,
-                               P->cg_max_it, res_out);
+    int r = solve_system(P, method, &S, x, res_out);
     sys_free(&S);
     return r;
 }
