@@ -407,9 +407,18 @@ rf_status rf_ens_tune(rf_ens *e, double t_probe, int *best_cluster, int *best_th
 {
     if (!e || !(t_probe > 0)) return efail(RF_ERR_ARG, "rf_ens_tune: bad argument");
     const int n = e->n;
-    cudaEvent_t a, b;
-    ECUDA(cudaEventCreate(&a));
-    ECUDA(cudaEventCreate(&b));
+    // timing events, released on every return path
+    struct Events {
+        cudaEvent_t a = nullptr, b = nullptr;
+        ~Events()
+        {
+            if (a) cudaEventDestroy(a);
+            if (b) cudaEventDestroy(b);
+        }
+    } ev;
+    ECUDA(cudaEventCreate(&ev.a));
+    ECUDA(cudaEventCreate(&ev.b));
+    cudaEvent_t a = ev.a, b = ev.b;
     std::vector<EnsDesc> dh(n);
     // one timed run from the initial state; busy[k] = seconds descriptor k held its unit
     auto probe = [&](int c, int th, const std::vector<int> &ord, int n_wide, float &ms,
@@ -455,11 +464,7 @@ rf_status rf_ens_tune(rf_ens *e, double t_probe, int *best_cluster, int *best_th
             if (rf_status st = probe(cls[ci], ths[ti], size_order, n, ms, &busy[ti][ci])) return st;
             if (ms < best.t) best = Cand{cls[ci], ths[ti], n, ms, size_order};
         }
-    if (!best.c) {
-        cudaEventDestroy(a);
-        cudaEventDestroy(b);
-        return efail(RF_ERR_CUDA, "rf_ens_tune: no tiling fits");
-    }
+    if (!best.c) return efail(RF_ERR_CUDA, "rf_ens_tune: no tiling fits");
     // 2. list-scheduling model of the persistent kernel: ncl clusters pop the
     // queue (heaviest first at that width), each instance holding its
     // cluster for its measured time.  Every instance stays wide: a split
@@ -510,8 +515,6 @@ rf_status rf_ens_tune(rf_ens *e, double t_probe, int *best_cluster, int *best_th
         if (rf_status st = probe(preds[i].c, preds[i].th, preds[i].order, preds[i].wide, ms, nullptr)) return st;
         if (ms < best.t) best = Cand{preds[i].c, preds[i].th, preds[i].wide, ms, preds[i].order};
     }
-    cudaEventDestroy(a);
-    cudaEventDestroy(b);
     e->cluster = best.c;
     e->threads = best.th;
     if (rf_status st = upload_schedule(e, best.order, best.wide)) return st;
