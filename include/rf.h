@@ -74,7 +74,11 @@ typedef enum rf_precision {
                            closures, outer residual and mass balance stay FP64     */
 } rf_precision;
 
-typedef enum rf_precond { RF_PRECOND_JACOBI = 0, RF_PRECOND_MG = 1 } rf_precond;
+/* Preconditioner of the inner PCG.  MG and DIC need RF_PREC_MIXED.  DIC is
+ * the diagonal incomplete Cholesky preconditioner Sec. 2.2 solves with, the
+ * cells eliminated in red-black order (colour (i + j + k) mod 2) so that its
+ * sweeps are data-parallel. */
+typedef enum rf_precond { RF_PRECOND_JACOBI = 0, RF_PRECOND_MG = 1, RF_PRECOND_DIC = 2 } rf_precond;
 
 /* Solver parameters (Sec. 2.2 leaves their values to the user).
  *   tol_picard  Picard exit test: max over active cells |h^{k+1} - h^k| <= tol [m]

@@ -17,7 +17,7 @@ INCLUDE = os.path.join(ROOT, "include")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(BUILD, "librf.so")
 SOURCES = ["closure_assemble.cu", "pcg.cu", "rf_api.cu", "noalloc.cu", "ensemble.cu", "ensemble_api.cu", "mg.cu",
-           "nn.cu", "nn_api.cu", "conv_tc.cu"]
+           "nn.cu", "nn_api.cu", "conv_tc.cu", "dic.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-Xcompiler", "-O2", "-Xptxas", "-v"]
 

@@ -12,6 +12,7 @@
 #include <string>
 #include <vector>
 
+#include "dic.cuh"
 #include "mg.cuh"
 #include "nn.cuh"
 #include "rf.h"
@@ -93,6 +94,7 @@ struct rf_ctx {
     int *dev_fault = nullptr, *fault_h = nullptr;   // set by a device wait that ran out
 
     MgHierarchy mg;                      // multigrid levels (RF_PRECOND_MG)
+    float *dic_diag = nullptr, *dic_rd = nullptr;   // DIC diagonal and pivots (RF_PRECOND_DIC)
     bool mg_alloc = false;
 
     // CUDA graphs: a whole Picard attempt, and a stand-alone linear solve
@@ -141,12 +143,14 @@ rf_status check_params(const rf_solver_params *p)
         return fail(RF_ERR_ARG, "invalid solver parameters");
     if (p->precision != RF_PREC_FP64 && p->precision != RF_PREC_MIXED)
         return fail(RF_ERR_ARG, "unknown precision mode");
-    if (p->precond != RF_PRECOND_JACOBI && p->precond != RF_PRECOND_MG)
+    if (p->precond != RF_PRECOND_JACOBI && p->precond != RF_PRECOND_MG && p->precond != RF_PRECOND_DIC)
         return fail(RF_ERR_ARG, "unknown preconditioner");
     if (p->picard_form != RF_PICARD_CHORD && p->picard_form != RF_PICARD_MODIFIED)
         return fail(RF_ERR_ARG, "unknown Picard linearisation");
     if (p->precond == RF_PRECOND_MG && p->precision != RF_PREC_MIXED)
         return fail(RF_ERR_ARG, "the multigrid preconditioner serves the FP32 inner solve: use RF_PREC_MIXED");
+    if (p->precond == RF_PRECOND_DIC && p->precision != RF_PREC_MIXED)
+        return fail(RF_ERR_ARG, "the DIC preconditioner serves the FP32 inner solve: use RF_PREC_MIXED");
     return RF_OK;
 }
 
@@ -253,6 +257,15 @@ rf_status add_while(cudaGraph_t parent, const std::vector<cudaGraphNode_t> &deps
         if (s_ != RF_OK) return s_;            \
     } while (0)
 
+// DIC arrays (allocated on first use).
+rf_status ensure_dic(rf_ctx *c)
+{
+    if (c->dic_rd) return RF_OK;
+    if (!alloc_n(c, c->dic_diag, c->g.N) || !alloc_n(c, c->dic_rd, c->g.N))
+        return fail(RF_ERR_NOMEM, "DIC allocation failed");
+    return RF_OK;
+}
+
 // Multigrid levels of this grid (allocated on first use).
 rf_status ensure_mg(rf_ctx *c)
 {
@@ -339,8 +352,13 @@ rf_status capture_solve(rf_ctx *c, cudaGraph_t top, cudaGraph_t parent, std::vec
     }
     // mixed: WHILE(outer) { WHILE(inner FP32 PCG) ; x += d ; FP64 residual }
     const CondSet co = start->cond, ci = start->cond_inner;
-    const bool mg = c->prm.precond == RF_PRECOND_MG;
+    const bool mg = c->prm.precond == RF_PRECOND_MG, dic = c->prm.precond == RF_PRECOND_DIC;
     const int *idone = &c->sc_in->done;
+    // z = M r for the MG and DIC preconditioners
+    auto precondition = [&]() {
+        if (mg) launch_mg_vcycle(s, nb, c->mg, c->K32, c->r32, c->z32, idone);
+        else launch_dic_apply(s, nb, g, c->K32, c->dic_rd, c->r32, c->z32, idone);
+    };
     const CondSet none{0, 0};
     if (!fused) {
         RF_TRY(cap_begin(c, parent, deps));
@@ -350,11 +368,13 @@ rf_status capture_solve(rf_ctx *c, cudaGraph_t top, cudaGraph_t parent, std::vec
                        c->ticket, c->sc, c->sc_in, co, ci);
         RF_TRY(cap_end(c, deps));
     }
-    if (mg) {
-        // coarse operators from this assembly, then z0 = V(r0) and rho = r0.z0
+    if (mg || dic) {
+        // coarse operators (MG) or pivots (DIC) from this assembly, then
+        // z0 = M r0 and rho = r0.z0
         RF_TRY(cap_begin(c, parent, deps));
-        launch_mg_build(s, nb, c->mg, c->K32, skip);
-        launch_mg_vcycle(s, nb, c->mg, c->K32, c->r32, c->z32, idone);
+        if (mg) launch_mg_build(s, nb, c->mg, c->K32, skip);
+        else launch_dic_setup(s, nb, g, c->K32, c->cb32, c->dic_diag, c->dic_rd, skip);
+        precondition();
         launch_cg32_rz(s, nb, g, c->r32, c->z32, c->partials, c->ticket, c->sc_in, 1, ci);
         RF_TRY(cap_end(c, deps));
     }
@@ -367,9 +387,9 @@ rf_status capture_solve(rf_ctx *c, cudaGraph_t top, cudaGraph_t parent, std::vec
         float *pin = c->p32[half], *pout = c->p32[half ^ 1];
         launch_cg32_spmv(s, nb, g, c->z32, pin, pout, c->q32, c->K32, c->cb32, c->partials, c->ticket, c->sc_in,
                          c->tma_ok ? &c->tma : nullptr, c->dev_fault);
-        if (mg) {
+        if (mg || dic) {
             launch_cg32_update_mg(s, nb, g, c->d32, c->r32, pout, c->q32, c->dinv32, c->partials, c->ticket, c->sc_in);
-            launch_mg_vcycle(s, nb, c->mg, c->K32, c->r32, c->z32, idone);
+            precondition();
             launch_cg32_rz(s, nb, g, c->r32, c->z32, c->partials, c->ticket, c->sc_in, 0, ci);
         } else {
             launch_cg32_update(s, nb, g, c->d32, c->r32, c->z32, pout, c->q32, c->dinv32, c->partials, c->ticket,
@@ -383,8 +403,8 @@ rf_status capture_solve(rf_ctx *c, cudaGraph_t top, cudaGraph_t parent, std::vec
     launch_resid64(s, nb, g, c->flags, x, c->b, c->Tx, c->Ty, c->Tz, c->diag, c->dinv32, c->r32, c->z32, c->d32,
                    c->prm.tol_cg, c->prm.tol_inner, c->prm.inner_max_it, c->prm.outer_max_it, c->partials, c->ticket,
                    c->sc, c->sc_in, co, ci);
-    if (mg) {
-        launch_mg_vcycle(s, nb, c->mg, c->K32, c->r32, c->z32, idone);
+    if (mg || dic) {
+        precondition();
         launch_cg32_rz(s, nb, g, c->r32, c->z32, c->partials, c->ticket, c->sc_in, 1, ci);
     }
     (void)none;
@@ -440,6 +460,7 @@ void destroy_graphs(rf_ctx *c)
 rf_status build_picard_graph(rf_ctx *c)
 {
     if (c->prm.precond == RF_PRECOND_MG) RF_TRY(ensure_mg(c));
+    if (c->prm.precond == RF_PRECOND_DIC) RF_TRY(ensure_dic(c));
     cudaGraph_t G;
     CUDA_TRY(cudaGraphCreate(&G, 0));
     c->picard_graph = G;
@@ -489,6 +510,7 @@ rf_status build_picard_graph(rf_ctx *c)
 rf_status build_solve_graph(rf_ctx *c)
 {
     if (c->prm.precond == RF_PRECOND_MG) RF_TRY(ensure_mg(c));
+    if (c->prm.precond == RF_PRECOND_DIC) RF_TRY(ensure_dic(c));
     cudaGraph_t G;
     CUDA_TRY(cudaGraphCreate(&G, 0));
     c->solve_graph = G;

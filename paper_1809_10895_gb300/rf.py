@@ -28,7 +28,7 @@ FACES = {"xmin": 0, "xmax": 1, "ymin": 2, "ymax": 3, "zmin": 4, "zmax": 5}
 BC_TYPES = {"zero_flux": 0, "dirichlet": 1, "flux": 2, "free_drainage": 3, "seepage": 4}
 MODELS = {"vg": RF_VG, "gardner": RF_GARDNER}
 PRECISION = {"fp64": 0, "mixed": 1}
-PRECOND = {"jacobi": 0, "mg": 1}
+PRECOND = {"jacobi": 0, "mg": 1, "dic": 2}
 PICARD_FORM = {"chord": 0, "modified": 1}
 
 
