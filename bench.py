@@ -144,6 +144,21 @@ def cpu_baseline(case, budget_s=20.0):
 
 
 # ------------------------------------------------------------ native arm
+def max_over_ranks(x, world, device):
+    """The largest x over all ranks: the job's time is its slowest rank's."""
+    import torch
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device)
+    if world > 1:
+        import torch.distributed as dist
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_value(units_per_rank, world, t_max):
+    """Whole-job throughput: the units every rank processed over the slowest rank's time."""
+    return world * units_per_rank / t_max
+
+
 def profile_entry(kernel):
     """The committed ncu summary of a kernel; None when absent or taken on a
     different kernel source."""
@@ -226,16 +241,9 @@ def native(args):
     s64, ms64, wall64, counts64, st64 = timed_run("fp64")
     launches_mix = sum(v[0] for v in counts_mix.values())
 
-    def agg(ms):
-        t = torch.tensor([ms / 1e3], dtype=torch.float64, device="cuda")
-        if world > 1:
-            import torch.distributed as dist
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        return float(t.item())
-
-    t_mix, t64 = agg(ms_mix), agg(ms64)
-    value = world * args.steps * n_act / t_mix
-    value64 = world * args.steps * n_act / t64
+    t_mix, t64 = max_over_ranks(ms_mix / 1e3, world, "cuda"), max_over_ranks(ms64 / 1e3, world, "cuda")
+    value = job_value(args.steps * n_act, world, t_mix)
+    value64 = job_value(args.steps * n_act, world, t64)
 
     # ---- per-kernel device times on the state reached (roofline)
     peaks = {}
@@ -384,9 +392,8 @@ def native(args):
             h_np[:], meta = s.get_state()
         barrier()
         te = time.perf_counter() - t0
-        if world > 1:
-            te = agg(te * 1e3)
-        e2e = {"value": world * args.steps * n_act / te, "unit": UNIT, "h2d_bytes_per_step": 8 * case.N,
+        te = max_over_ranks(te, world, "cuda")
+        e2e = {"value": job_value(args.steps * n_act, world, te), "unit": UNIT, "h2d_bytes_per_step": 8 * case.N,
                "d2h_bytes_per_step": 8 * case.N}
 
     if rank == 0:
