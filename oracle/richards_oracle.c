@@ -79,6 +79,8 @@ typedef struct or_problem {
     double tol_picard, tol_cg, dt0, dt_max, dt_min, f_grow, f_shrink, eps_chord;
     int cg_max_it, n_inc, n_small, n_max, solver;
     int picard_form;     /* 0 classical Picard with chord capacity, 1 modified Picard */
+    double grav[3];      /* gradient of elevation in grid axes (x, y, z); (0, 0, 1) for z up.
+                          * Eq. 1's gravity term for a grid aligned with a tilted slab */
 
     /* state */
     double *h;           /* N */
@@ -160,6 +162,7 @@ or_problem *or_create(int nx, int ny, int nz, double dx, double dy, double dz, d
     P->tol_picard = 1e-6; P->tol_cg = 1e-10; P->cg_max_it = 10000;
     P->dt0 = 1.0; P->dt_max = 600.0; P->dt_min = 1e-3; P->f_grow = 1.3; P->f_shrink = 1.3;
     P->n_inc = 10; P->n_small = 3; P->n_max = 8; P->eps_chord = 1e-10;
+    P->grav[0] = 0.0; P->grav[1] = 0.0; P->grav[2] = 1.0;
     P->solver = OR_SOLVER_PCG;
     P->dt_nom = P->dt0;
     return P;
@@ -220,6 +223,9 @@ int or_set_param(or_problem *P, const char *name, double value)
 #define DP(nm) if (!strcmp(name, #nm)) { P->nm = value; return OR_OK; }
 #define IP(nm) if (!strcmp(name, #nm)) { P->nm = (int)value; return OR_OK; }
     DP(tol_picard) DP(tol_cg) DP(dt0) DP(dt_max) DP(dt_min) DP(f_grow) DP(f_shrink) DP(eps_chord)
+    if (!strcmp(name, "grav_x")) { P->grav[0] = value; return OR_OK; }
+    if (!strcmp(name, "grav_y")) { P->grav[1] = value; return OR_OK; }
+    if (!strcmp(name, "grav_z")) { P->grav[2] = value; return OR_OK; }
     IP(cg_max_it) IP(n_inc) IP(n_small) IP(n_max) IP(solver) IP(picard_form)
 #undef DP
 #undef IP
@@ -332,9 +338,11 @@ static void assemble(const or_problem *P, const double *hk, const double *hn, do
     const double A[6] = { P->dy * P->dz, P->dy * P->dz, P->dx * P->dz, P->dx * P->dz,
                           P->dx * P->dy, P->dx * P->dy };
     const double d[6] = { P->dx, P->dx, P->dy, P->dy, P->dz, P->dz };
-    /* sign of the gravity flux through each face for a cell: +1 for the top
-     * face (water enters from above), -1 for the bottom face, 0 lateral */
-    const double g[6] = { 0, 0, 0, 0, -1.0, +1.0 };
+    /* gravity flux factor of each face of a cell, grad(elevation) . n_out:
+     * with z up, +1 for the top face (water enters from above), -1 for the
+     * bottom face, 0 lateral; along a tilted frame every axis carries its
+     * component of the elevation gradient */
+    const double g[6] = { -P->grav[0], P->grav[0], -P->grav[1], P->grav[1], -P->grav[2], P->grav[2] };
     double bcv[6];
     for (int f = 0; f < 6; f++) bcv[f] = P->bc[f].n > 0 ? series_at(&P->bc[f], t) : 0.0;
 
@@ -414,9 +422,10 @@ static void assemble(const or_problem *P, const double *hk, const double *hn, do
                 S->fa[6 * a + f] = bcv[f] * A[f];
             } else if (type == OR_FREE_DRAINAGE) {
                 /* unit hydraulic gradient: pressure gradient zero, gravity
-                 * drives an outflow K(h^k_P) A_z */
-                rhs += -S->K[a] * A[f];
-                S->fa[6 * a + f] = -S->K[a] * A[f];
+                 * drives an outflow K(h^k_P) A_z (times the elevation
+                 * gradient across the face in a tilted frame) */
+                rhs += g[f] * S->K[a] * A[f];
+                S->fa[6 * a + f] = g[f] * S->K[a] * A[f];
             }
         }
         /* CSR row with columns in ascending cell order */

@@ -1,0 +1,58 @@
+"""Pins of the oracle's gravity direction (Eq. 1's elevation gradient in
+the grid's axes, for a grid aligned with a tilted slab, as in the paper's
+slope of Sec. 4.2): the same column laid along x, y or z with gravity along
+its axis gives the same solution step for step; a hydrostatic head
+h = c - z_e(x) under a tilted gravity is a fixed point with zero-flux faces."""
+import numpy as np
+import pytest
+
+from oracle import oracle as O
+
+SOIL = dict(model=O.VG, theta_r=0.078, theta_s=0.43, alpha=3.6, n=1.56, Ks=2.89e-6, S=1e-5)
+FACES = {"x": (O.XMIN, O.XMAX), "y": (O.YMIN, O.YMAX), "z": (O.ZMIN, O.ZMAX)}
+
+
+def _column(axis, n=40, d=0.01):
+    shape = {"x": (n, 1, 1), "y": (1, n, 1), "z": (1, 1, n)}[axis]
+    size = {"x": (d, 1.0, 1.0), "y": (1.0, d, 1.0), "z": (1.0, 1.0, d)}[axis]
+    o = O.Oracle(*shape, *size, 0.0, None)
+    o.set_soils([SOIL], None, None)
+    lo, hi = FACES[axis]
+    o.set_bc(lo, O.DIRICHLET, np.array([0.0]), np.array([-1.0]))
+    o.set_bc(hi, O.DIRICHLET, np.array([0.0]), np.array([-0.05]))
+    grav = {"x": (1.0, 0.0, 0.0), "y": (0.0, 1.0, 0.0), "z": (0.0, 0.0, 1.0)}[axis]
+    o.set_params(grav_x=grav[0], grav_y=grav[1], grav_z=grav[2], tol_cg=1e-13)
+    o.set_state(np.full(n, -1.0), 0.0)
+    return o
+
+
+def test_column_along_any_axis_is_the_same_column():
+    runs = {}
+    for axis in "xyz":
+        o = _column(axis)
+        steps = o.run(1800.0)
+        runs[axis] = (o.get_state()[0], [(s.dt, s.picard, s.rejected) for s in steps], o.mass_balance())
+    for axis in "xy":
+        assert runs[axis][1] == runs["z"][1]
+        np.testing.assert_allclose(runs[axis][0], runs["z"][0], rtol=0, atol=1e-11)
+        assert runs[axis][2]["inflow_cum"] == pytest.approx(runs["z"][2]["inflow_cum"], rel=1e-10)
+    # the infiltration moved water: the test is not trivially static
+    assert np.max(np.abs(runs["z"][0] + 1.0)) > 0.1
+
+
+def test_tilted_hydrostatic_head_is_a_fixed_point():
+    a, b = np.radians(20.0), np.radians(3.0)
+    g = np.array([np.sin(a), np.cos(a) * np.sin(b), np.cos(a) * np.cos(b)])   # unit elevation gradient
+    nx, ny, nz, d = 6, 5, 4, (2.0, 2.0, 0.2)
+    o = O.Oracle(nx, ny, nz, *d, 0.0, None)
+    o.set_soils([SOIL], None, None)                # every face zero flux (the default)
+    o.set_params(grav_x=g[0], grav_y=g[1], grav_z=g[2])
+    k, j, i = np.meshgrid(np.arange(nz), np.arange(ny), np.arange(nx), indexing="ij")
+    ze = g[0] * (i + 0.5) * d[0] + g[1] * (j + 0.5) * d[1] + g[2] * (k + 0.5) * d[2]
+    h0 = (-0.5 - ze).ravel()
+    o.set_state(h0, 0.0)
+    steps = o.run(86400.0)
+    assert np.max(np.abs(o.get_state()[0] - h0)) <= 1e-9
+    assert all(s.picard == 1 for s in steps)
+    mb = o.mass_balance()
+    assert mb["inflow_cum"] == 0.0 and mb["outflow_cum"] == 0.0
