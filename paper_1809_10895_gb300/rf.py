@@ -286,6 +286,8 @@ class Solver:
     @classmethod
     def from_case(cls, case, **param_overrides) -> "Solver":
         """Build a solver from a workloads.Case (mesh, soils, BCs, params, state)."""
+        if tuple(getattr(case, "gravity", (0.0, 0.0, 1.0))) != (0.0, 0.0, 1.0):
+            raise NotImplementedError(f"{case.name}: gravity along {case.gravity}; this solver's grid is z-up")
         p = dict(case.params)
         p.update(param_overrides)
         s = cls(case.nx, case.ny, case.nz, case.dx, case.dy, case.dz, case.z_bottom, case.active,

@@ -23,6 +23,8 @@ def oracle_from_case(case, **param_overrides) -> O.Oracle:
     for bc in case.bcs:
         o.set_bc(_FACE[bc.face], _BC[bc.type], bc.t, bc.v)
     p = dict(case.params)
+    if tuple(case.gravity) != (0.0, 0.0, 1.0):
+        p.update(grav_x=case.gravity[0], grav_y=case.gravity[1], grav_z=case.gravity[2])
     p.update(param_overrides)
     o.set_params(**p)
     o.set_state(case.h0, case.t0)

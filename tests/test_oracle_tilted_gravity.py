@@ -56,3 +56,31 @@ def test_tilted_hydrostatic_head_is_a_fixed_point():
     assert all(s.picard == 1 for s in steps)
     mb = o.mass_balance()
     assert mb["inflow_cum"] == 0.0 and mb["outflow_cum"] == 0.0
+
+
+def test_tilted_slope_workload_in_the_oracle():
+    # a small piece of the Sec. 4.2 slope for one day: the balance closes;
+    # a level river (no slope along y) leaves the solution uniform along y,
+    # the 3 degree river does not
+    from paper_1809_10895_gb300 import workloads as W
+    from tests.helpers import oracle_from_case
+    spread = {}
+    for rd in (0.0, 3.0):
+        c = W.tilted_slope(nx=24, ny=6, nz=10, river_deg=rd, days=1.0)
+        o = oracle_from_case(c)
+        o.run(c.t_end)
+        h = o.get_state()[0].reshape(c.nz, c.ny, c.nx)
+        spread[rd] = np.max(np.ptp(h, axis=1))
+        mb = o.mass_balance()
+        assert mb["closure_rel"] <= 1e-9
+        assert mb["inflow_cum"] > 0.0
+    assert spread[0.0] <= 1e-9
+    assert spread[3.0] >= 1e-5
+
+
+def test_binding_refuses_tilted_gravity():
+    # the CUDA path is z-up: a tilted case must not run there silently
+    from paper_1809_10895_gb300 import rf
+    from paper_1809_10895_gb300 import workloads as W
+    with pytest.raises(NotImplementedError):
+        rf.Solver.from_case(W.tilted_slope(nx=4, ny=4, nz=4))
