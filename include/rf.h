@@ -324,6 +324,14 @@ rf_status rf_ens_reset(rf_ens *ens);
  * be NULL. */
 rf_status rf_ens_tune(rf_ens *ens, double t_probe, int *best_cluster, int *best_threads, int *best_wide,
                       double *best_ms);
+/* The tuner's model of the persistent queue (host arithmetic only, no
+ * device): `units` work units of `cluster` CTAs pop the n instances in
+ * `order` (a permutation of 0..n-1); the first n_wide run on a whole unit
+ * for wide_s[i] seconds; the first other pop splits its unit into `cluster`
+ * single CTAs, which run instances for solo_s[i] seconds (solo_s may be NULL
+ * when n_wide >= n).  *makespan: when the last instance ends. */
+rf_status rf_ens_model_makespan(const double *wide_s, const double *solo_s, const int *order, int n, int n_wide,
+                                int units, int cluster, double *makespan);
 
 /* ---- a linear solve that allocates no device memory ----------------------
  *

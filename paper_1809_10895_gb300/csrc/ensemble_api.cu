@@ -130,6 +130,41 @@ rf_status build_graph(rf_ens *e)
     return RF_OK;
 }
 
+// List-scheduling model of the persistent queue: `units` work units of
+// `cluster` CTAs pop instances in `order`; the first n_wide run on a whole
+// unit for wide_s[i]; the first other pop splits its unit into `cluster`
+// single CTAs (the popping CTA runs that instance), and single CTAs run
+// instances for solo_s[i].  Units that free at the same time pop single CTAs
+// first.  Returns when the last instance ends.
+double model_makespan(const double *wide_s, const double *solo_s, const int *order, int n, int n_wide, int units,
+                      int cluster)
+{
+    // (free time, is a whole cluster) per unit, earliest first
+    std::priority_queue<std::pair<double, int>, std::vector<std::pair<double, int>>,
+                        std::greater<std::pair<double, int>>> q;
+    for (int u = 0; u < units; u++) q.push({0.0, 1});
+    double end = 0.0;
+    int k = 0;
+    while (!q.empty()) {
+        auto [t, whole] = q.top();
+        q.pop();
+        if (k >= n) {
+            end = std::max(end, t);
+            continue;
+        }
+        const int d = order[k];
+        if (whole && k < n_wide) {
+            q.push({t + wide_s[d], 1});
+        } else {
+            if (whole)
+                for (int r = 1; r < cluster; r++) q.push({t, 0});
+            q.push({t + solo_s[d], 0});
+        }
+        k++;
+    }
+    return end;
+}
+
 }  // namespace
 
 extern "C" {
@@ -483,29 +518,9 @@ rf_status rf_ens_tune(rf_ens *e, double t_probe, int *best_cluster, int *best_th
             const int c = cls[ci], units = ncl[ti][ci];
             std::vector<int> lpt = size_order;
             std::stable_sort(lpt.begin(), lpt.end(), [&](int x, int y) { return wide[x] > wide[y]; });
-            for (int w = n; w <= n; w++) {
-                // (free time, is a whole cluster) per unit, earliest first
-                std::priority_queue<std::pair<double, int>, std::vector<std::pair<double, int>>,
-                                    std::greater<std::pair<double, int>>> units_q;
-                for (int u = 0; u < units; u++) units_q.push({0.0, 1});
-                double end = 0.0;
-                int k = 0;
-                while (!units_q.empty()) {
-                    auto [t, whole] = units_q.top();
-                    units_q.pop();
-                    if (k >= n) { end = std::max(end, t); continue; }
-                    const int d = lpt[k];
-                    if (whole && k < w) {
-                        units_q.push({t + wide[d], 1});
-                    } else {
-                        if (whole)
-                            for (int r = 1; r < c; r++) units_q.push({t, 0});
-                        units_q.push({t + solo[d], 0});
-                    }
-                    k++;
-                }
-                preds.push_back(Cand{c, ths[ti], w, end, lpt});
-            }
+            for (int w = n; w <= n; w++)
+                preds.push_back(Cand{c, ths[ti], w,
+                                     model_makespan(wide.data(), solo.data(), lpt.data(), n, w, units, c), lpt});
         }
     }
     std::stable_sort(preds.begin(), preds.end(), [](const Cand &x, const Cand &y) { return x.t < y.t; });
@@ -523,6 +538,22 @@ rf_status rf_ens_tune(rf_ens *e, double t_probe, int *best_cluster, int *best_th
     if (best_threads) *best_threads = best.th;
     if (best_wide) *best_wide = best.wide;
     if (best_ms) *best_ms = best.t;
+    return RF_OK;
+}
+
+rf_status rf_ens_model_makespan(const double *wide_s, const double *solo_s, const int *order, int n, int n_wide,
+                                int units, int cluster, double *makespan)
+{
+    if (!wide_s || !order || !makespan || n < 1 || units < 1 || cluster < 1 || n_wide < 0)
+        return efail(RF_ERR_ARG, "rf_ens_model_makespan: bad argument");
+    if (n_wide < n && !solo_s) return efail(RF_ERR_ARG, "rf_ens_model_makespan: split schedules need solo_s");
+    std::vector<char> seen(n, 0);
+    for (int k = 0; k < n; k++) {
+        if (order[k] < 0 || order[k] >= n || seen[order[k]])
+            return efail(RF_ERR_ARG, "rf_ens_model_makespan: order must be a permutation");
+        seen[order[k]] = 1;
+    }
+    *makespan = model_makespan(wide_s, solo_s ? solo_s : wide_s, order, n, n_wide > n ? n : n_wide, units, cluster);
     return RF_OK;
 }
 

@@ -139,6 +139,7 @@ SIGNATURES = {
     "rf_ens_get": (C.c_int, [_VP, C.c_int, _DP, C.POINTER(rf_ens_stats)]),
     "rf_ens_reset": (C.c_int, [_VP]),
     "rf_ens_tune": (C.c_int, [_VP, C.c_double, C.POINTER(C.c_int), C.POINTER(C.c_int), C.POINTER(C.c_int), _DP]),
+    "rf_ens_model_makespan": (C.c_int, [_DP, _DP, C.POINTER(C.c_int), C.c_int, C.c_int, C.c_int, C.c_int, _DP]),
     "rf_pcg_solve_noalloc": (C.c_int, [C.c_int, C.c_int, C.c_int, _VP, _VP, _VP, _VP, _VP, _VP, C.c_double,
                                        C.c_int, _VP, C.POINTER(C.c_int)]),
     "rf_nn_create": (C.c_int, [_VP, C.POINTER(rf_allocator), C.POINTER(_VP)]),
@@ -572,6 +573,19 @@ class Ensemble:
         _check(load().rf_ens_tune(self.ctx, float(t_probe), C.byref(c), C.byref(th), C.byref(w), C.byref(ms)),
                "rf_ens_tune")
         return c.value, th.value, w.value, ms.value
+
+
+def ens_model_makespan(wide_s, order, units, cluster=1, n_wide=None, solo_s=None) -> float:
+    """The ensemble tuner's list-scheduling model (host arithmetic, no GPU)."""
+    w = np.ascontiguousarray(wide_s, dtype=np.float64)
+    so = None if solo_s is None else np.ascontiguousarray(solo_s, dtype=np.float64)
+    o = np.ascontiguousarray(order, dtype=np.int32)
+    n = len(w)
+    out = C.c_double(0.0)
+    _check(load().rf_ens_model_makespan(_dptr(w), _dptr(so), o.ctypes.data_as(C.POINTER(C.c_int)), n,
+                                        n if n_wide is None else int(n_wide), int(units), int(cluster),
+                                        C.byref(out)), "rf_ens_model_makespan")
+    return out.value
 
 
 def pcg_solve_noalloc(shape, diag, Tx, Ty, Tz, b, x, tol=1e-10, max_it=10000, stream=None) -> int:
