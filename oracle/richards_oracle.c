@@ -79,6 +79,7 @@ typedef struct or_problem {
     double tol_picard, tol_cg, dt0, dt_max, dt_min, f_grow, f_shrink, eps_chord;
     int cg_max_it, n_inc, n_small, n_max, solver;
     int picard_form;     /* 0 classical Picard with chord capacity, 1 modified Picard */
+    int face_mean;       /* interface K: 0 arithmetic (linear interpolation, Sec. 2.2), 1 harmonic */
     double grav[3];      /* gradient of elevation in grid axes (x, y, z); (0, 0, 1) for z up.
                           * Eq. 1's gravity term for a grid aligned with a tilted slab */
 
@@ -226,7 +227,7 @@ int or_set_param(or_problem *P, const char *name, double value)
     if (!strcmp(name, "grav_x")) { P->grav[0] = value; return OR_OK; }
     if (!strcmp(name, "grav_y")) { P->grav[1] = value; return OR_OK; }
     if (!strcmp(name, "grav_z")) { P->grav[2] = value; return OR_OK; }
-    IP(cg_max_it) IP(n_inc) IP(n_small) IP(n_max) IP(solver) IP(picard_form)
+    IP(cg_max_it) IP(n_inc) IP(n_small) IP(n_max) IP(solver) IP(picard_form) IP(face_mean)
 #undef DP
 #undef IP
     return OR_ERR_ARG;
@@ -387,7 +388,12 @@ static void assemble(const or_problem *P, const double *hk, const double *hn, do
             int q = neighbour(P, i, j, k, f);
             if (q >= 0 && P->active[q]) {
                 int aq = P->idx[q];
-                double Kbar = 0.5 * (S->K[a] + S->K[aq]);
+                /* interface conductivity: the linear interpolation of Sec. 2.2
+                 * (arithmetic mean), or the harmonic mean, the exact series
+                 * conductance of two half cells in steady flow */
+                double Kbar = P->face_mean == 1
+                                  ? (S->K[a] + S->K[aq] > 0.0 ? 2.0 * S->K[a] * S->K[aq] / (S->K[a] + S->K[aq]) : 0.0)
+                                  : 0.5 * (S->K[a] + S->K[aq]);
                 double T = Kbar * A[f] / d[f];
                 diag += T;
                 nb_col[f] = aq;

@@ -1,8 +1,15 @@
-"""Pins of the oracle's gravity direction (Eq. 1's elevation gradient in
-the grid's axes, for a grid aligned with a tilted slab, as in the paper's
-slope of Sec. 4.2): the same column laid along x, y or z with gravity along
-its axis gives the same solution step for step; a hydrostatic head
-h = c - z_e(x) under a tilted gravity is a fixed point with zero-flux faces."""
+"""Pins of the oracle's variants beyond the paper's default scheme.
+
+Gravity direction (Eq. 1's elevation gradient in the grid's axes, for a grid
+aligned with a tilted slab, as in the paper's slope of Sec. 4.2): the same
+column laid along x, y or z with gravity along its axis gives the same
+solution step for step; a hydrostatic head h = c - z_e(x) under a tilted
+gravity is a fixed point with zero-flux faces; the tilted-slope workload
+closes its balance and is uniform along a level river.
+
+Interface conductivity: the harmonic mean reproduces the closed-form steady
+state across layers (series resistance), the arithmetic mean of Sec. 2.2
+does not."""
 import numpy as np
 import pytest
 
@@ -84,3 +91,30 @@ def test_binding_refuses_tilted_gravity():
     from paper_1809_10895_gb300 import workloads as W
     with pytest.raises(NotImplementedError):
         rf.Solver.from_case(W.tilted_slope(nx=4, ny=4, nz=4))
+
+
+def test_harmonic_face_mean_gives_the_exact_layered_steady_state():
+    # saturated steady flow across two layers (Ks 1e-5 over 1e-7 m/s), heads
+    # held at both ends: the exact solution is linear in total head within
+    # each layer with the series resistance 0.5/K1 + 0.5/K2 (closed form);
+    # the harmonic interface mean reproduces it at the cell centres, the
+    # arithmetic mean of Sec. 2.2 does not at the interface
+    nz, dz, K1, K2 = 20, 0.05, 1e-5, 1e-7
+    zc = (np.arange(nz) + 0.5) * dz
+    Hb, Ht = 2.0 + 0.0, 0.5 + nz * dz
+    q = (Hb - Ht) / (0.5 / K1 + 0.5 / K2)
+    H = np.where(zc <= 0.5, Hb - q * zc / K1, Hb - q * 0.5 / K1 - q * (zc - 0.5) / K2)
+    exact = H - zc
+    err = {}
+    for fm in (0, 1):
+        o = O.Oracle(1, 1, nz, 1.0, 1.0, dz, 0.0, None)
+        soil = dict(model=O.VG, theta_r=0.05, theta_s=0.4, alpha=2.0, n=1.8, Ks=K1, S=1e-4)
+        o.set_soils([soil, dict(soil, Ks=K2)], np.array([0] * 10 + [1] * 10, np.uint8), None)
+        o.set_bc(O.ZMIN, O.DIRICHLET, np.array([0.0]), np.array([2.0]))
+        o.set_bc(O.ZMAX, O.DIRICHLET, np.array([0.0]), np.array([0.5]))
+        o.set_params(face_mean=fm, dt_max=1e6, tol_cg=1e-14)
+        o.set_state(np.full(nz, 2.0), 0.0)
+        o.run(3e8)
+        err[fm] = np.max(np.abs(o.get_state()[0] - exact))
+    assert err[1] <= 1e-9
+    assert err[0] >= 1e-4
