@@ -23,7 +23,7 @@ SRC = os.path.join(HERE, "richards_oracle.c")
 BUILD_DIR = os.path.join(HERE, "_build")
 LIB = os.path.join(BUILD_DIR, "liboracle.so")
 
-VG, GARDNER = 0, 1
+VG, GARDNER, BROOKS_COREY = 0, 1, 2
 ZERO_FLUX, DIRICHLET, FLUX, FREE_DRAINAGE, SEEPAGE = range(5)
 XMIN, XMAX, YMIN, YMAX, ZMIN, ZMAX = range(6)
 SOLVER_PCG, SOLVER_DENSE, SOLVER_DIC, SOLVER_DIC_RB = 0, 1, 2, 3

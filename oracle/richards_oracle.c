@@ -40,7 +40,7 @@
 #include <stdlib.h>
 #include <string.h>
 
-enum { OR_VG = 0, OR_GARDNER = 1 };
+enum { OR_VG = 0, OR_GARDNER = 1, OR_BROOKS_COREY = 2 };
 enum { OR_ZERO_FLUX = 0, OR_DIRICHLET = 1, OR_FLUX = 2, OR_FREE_DRAINAGE = 3, OR_SEEPAGE = 4 };
 enum { OR_XMIN = 0, OR_XMAX, OR_YMIN, OR_YMAX, OR_ZMIN, OR_ZMAX, OR_NFACES };
 enum { OR_OK = 0, OR_ERR_ARG = 1, OR_ERR_PICARD = 6, OR_ERR_DT_MIN = 7, OR_ERR_CG = 8 };
@@ -105,6 +105,25 @@ static void closure(const or_soil *s, double Ks, double h, double *theta, double
         *theta = s->theta_s + s->S * h;
         *K = Ks;
         *C = s->S;
+        return;
+    }
+    if (s->model == OR_BROOKS_COREY) {
+        /* Brooks and Corey, the alternative closure Sec. 1 names: air-entry
+         * head h_b = -1/alpha, pore-size index lambda = n;
+         * Se = (h_b / h)^lambda below h_b, 1 above;
+         * theta = theta_r + (theta_s - theta_r) Se, C = d theta / dh,
+         * K = Ks Se^((2 + 3 lambda) / lambda) (Brooks and Corey's own form). */
+        double hb = -1.0 / s->alpha, lam = s->n;
+        if (h >= hb) {
+            *theta = s->theta_s;
+            *K = Ks;
+            *C = 0.0;
+            return;
+        }
+        double se = pow(hb / h, lam);
+        *theta = s->theta_r + (s->theta_s - s->theta_r) * se;
+        *C = -lam * (s->theta_s - s->theta_r) * se / h;
+        *K = Ks * pow(se, (2.0 + 3.0 * lam) / lam);
         return;
     }
     if (s->model == OR_GARDNER) {
@@ -190,6 +209,7 @@ int or_set_soils(or_problem *P, int nzones, const int *model, const double *thet
     for (int z = 0; z < nzones; z++) {
         or_soil s = { model[z], theta_r[z], theta_s[z], alpha[z], n[z], Ks[z], S[z] };
         if (s.model == OR_VG && !(s.n > 1.0)) return OR_ERR_ARG;
+        if (s.model == OR_BROOKS_COREY && !(s.n > 0.0)) return OR_ERR_ARG;
         P->zones[z] = s;
     }
     for (int p = 0; p < P->N; p++) {

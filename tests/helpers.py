@@ -8,7 +8,7 @@ from oracle import oracle as O
 _FACE = {"xmin": O.XMIN, "xmax": O.XMAX, "ymin": O.YMIN, "ymax": O.YMAX, "zmin": O.ZMIN, "zmax": O.ZMAX}
 _BC = {"zero_flux": O.ZERO_FLUX, "dirichlet": O.DIRICHLET, "flux": O.FLUX,
        "free_drainage": O.FREE_DRAINAGE, "seepage": O.SEEPAGE}
-_MODEL = {"vg": O.VG, "gardner": O.GARDNER}
+_MODEL = {"vg": O.VG, "gardner": O.GARDNER, "brooks_corey": O.BROOKS_COREY}
 
 
 def oracle_soil(s: dict) -> dict:

@@ -9,7 +9,10 @@ closes its balance and is uniform along a level river.
 
 Interface conductivity: the harmonic mean reproduces the closed-form steady
 state across layers (series resistance), the arithmetic mean of Sec. 2.2
-does not."""
+does not.
+
+Brooks-Corey closure (the alternative Sec. 1 names): closed forms, C as
+d(theta)/dh, continuity at the air-entry head, a mass-conserving run."""
 import numpy as np
 import pytest
 
@@ -118,3 +121,45 @@ def test_harmonic_face_mean_gives_the_exact_layered_steady_state():
         err[fm] = np.max(np.abs(o.get_state()[0] - exact))
     assert err[1] <= 1e-9
     assert err[0] >= 1e-4
+
+
+BC_SOIL = dict(model=O.BROOKS_COREY, theta_r=0.05, theta_s=0.40, alpha=1 / 0.3, n=0.5, Ks=1e-5, S=1e-5)
+
+
+def test_brooks_corey_closed_forms():
+    # Brooks and Corey (the alternative closure named in Sec. 1): at twice the
+    # air-entry head Se = 2^-lambda, K = Ks 2^-(2 + 3 lambda); theta_s and Ks
+    # above the air-entry head; theta_r and 0 far below it
+    hb, lam = -0.3, 0.5
+    th, K, C = O.closure(BC_SOIL, 2 * hb)
+    assert th == pytest.approx(0.05 + 0.35 * 2 ** -lam, rel=1e-14)
+    assert K == pytest.approx(1e-5 * 2 ** -(2 + 3 * lam), rel=1e-13)
+    th, K, C = O.closure(BC_SOIL, 0.5 * hb)
+    assert (th, K, C) == (0.40, 1e-5, 0.0)
+    th, K, _ = O.closure(BC_SOIL, hb * (1 + 1e-12))
+    assert th == pytest.approx(0.40, rel=1e-10) and K == pytest.approx(1e-5, rel=1e-10)
+    th, K, _ = O.closure(BC_SOIL, -1e8)
+    assert th == pytest.approx(0.05, abs=1e-4) and K < 1e-20
+
+
+@pytest.mark.parametrize("h", [-0.31, -0.5, -2.0, -30.0])
+def test_brooks_corey_capacity_is_dtheta_dh(h):
+    e = 1e-6 * abs(h)
+    fd = (O.closure(BC_SOIL, h + e)[0] - O.closure(BC_SOIL, h - e)[0]) / (2 * e)
+    assert O.closure(BC_SOIL, h)[2] == pytest.approx(fd, rel=1e-6)
+
+
+def test_brooks_corey_column_conserves_mass():
+    # wetting from a top head below the air-entry head (lambda 2): no
+    # rejection, the balance closes, water enters
+    o = O.Oracle(1, 1, 50, 1.0, 1.0, 0.02, 0.0, None)
+    o.set_soils([dict(BC_SOIL, n=2.0)], None, None)
+    o.set_bc(O.ZMAX, O.DIRICHLET, np.array([0.0]), np.array([-0.5]))
+    o.set_bc(O.ZMIN, O.FREE_DRAINAGE)
+    o.set_params(tol_cg=1e-12)
+    o.set_state(np.full(50, -2.0), 0.0)
+    steps = o.run(3600.0)
+    mb = o.mass_balance()
+    assert sum(s.rejected for s in steps) == 0
+    assert mb["closure_rel"] <= 1e-11
+    assert mb["inflow_cum"] > 0.0
