@@ -67,6 +67,8 @@ def lib():
         L.or_closure_eval.argtypes = [C.c_int] + [C.c_double] * 7 + [dp]
         L.or_ebats_accept.argtypes = [dp, ip, C.c_int, C.c_int, C.c_int, C.c_double, C.c_double]
         L.or_ebats_reject.argtypes = [dp, ip, C.c_double, C.c_double]
+        L.or_time_error.argtypes = [vp, C.c_int]
+        L.or_time_error.restype = C.c_double
         _lib = L
     return _lib
 
@@ -203,6 +205,12 @@ class Oracle:
         steps = [StepInfo(r[0], r[1], int(r[2]), int(r[3]), int(r[4]), r[5]) for r in log[:min(ns.value, log_cap)]]
         self._check(st, "run")
         return steps
+
+    def time_error(self, largest=True):
+        """Richardson time control: the local error estimate of the largest
+        accepted step since the state was set (largest=True), or of the last
+        estimated step."""
+        return lib().or_time_error(self.h, 1 if largest else 0)
 
     def mass_balance(self):
         out = np.zeros(7)

@@ -80,6 +80,9 @@ typedef struct or_problem {
     int cg_max_it, n_inc, n_small, n_max, solver;
     int picard_form;     /* 0 classical Picard with chord capacity, 1 modified Picard */
     int face_mean;       /* interface K: 0 arithmetic (linear interpolation, Sec. 2.2), 1 harmonic */
+    int time_control;    /* 0 EBATS (Sec. 2.2), 1 Richardson step doubling */
+    double tol_time;     /* Richardson: bound on max |h(2 x dt/2) - h(dt)| per step [m] */
+    double err_last, err_max;   /* Richardson estimate of the last and the largest accepted step */
     double grav[3];      /* gradient of elevation in grid axes (x, y, z); (0, 0, 1) for z up.
                           * Eq. 1's gravity term for a grid aligned with a tilted slab */
 
@@ -183,6 +186,7 @@ or_problem *or_create(int nx, int ny, int nz, double dx, double dy, double dz, d
     P->dt0 = 1.0; P->dt_max = 600.0; P->dt_min = 1e-3; P->f_grow = 1.3; P->f_shrink = 1.3;
     P->n_inc = 10; P->n_small = 3; P->n_max = 8; P->eps_chord = 1e-10;
     P->grav[0] = 0.0; P->grav[1] = 0.0; P->grav[2] = 1.0;
+    P->tol_time = 1e-3;
     P->solver = OR_SOLVER_PCG;
     P->dt_nom = P->dt0;
     return P;
@@ -247,7 +251,8 @@ int or_set_param(or_problem *P, const char *name, double value)
     if (!strcmp(name, "grav_x")) { P->grav[0] = value; return OR_OK; }
     if (!strcmp(name, "grav_y")) { P->grav[1] = value; return OR_OK; }
     if (!strcmp(name, "grav_z")) { P->grav[2] = value; return OR_OK; }
-    IP(cg_max_it) IP(n_inc) IP(n_small) IP(n_max) IP(solver) IP(picard_form) IP(face_mean)
+    IP(cg_max_it) IP(n_inc) IP(n_small) IP(n_max) IP(solver) IP(picard_form) IP(face_mean) IP(time_control)
+    DP(tol_time)
 #undef DP
 #undef IP
     return OR_ERR_ARG;
@@ -285,6 +290,7 @@ int or_set_state(or_problem *P, const double *h, double t)
     P->easy = 0;
     P->storage0 = storage_of(P, P->h);
     P->inflow_cum = P->outflow_cum = P->closure_cum = P->defect_cum = 0.0;
+    P->err_last = P->err_max = 0.0;
     return OR_OK;
 }
 
@@ -791,7 +797,96 @@ static int do_step(or_problem *P, double t_stop, double *info)
     }
 }
 
-int or_step(or_problem *P, double *info) { return do_step(P, INFINITY, info); }
+/* The Richardson alternative to EBATS that Sec. 2.2 names for prescribing
+ * the temporal error: each step is taken once with dt and twice with dt/2
+ * from the same state; the difference of the two results estimates the
+ * local error of the dt step (backward Euler: O(dt^2)).  The step is
+ * accepted, with the more accurate two-half-step result, when the estimate
+ * is within tol_time; either way the next dt is dt * 0.9 sqrt(tol_time / err)
+ * (clamped to [0.2, 2] and to dt_max).  A Picard failure in any of the three
+ * solves divides dt by f_shrink as in EBATS. */
+static int do_step_richardson(or_problem *P, double t_stop, double *info)
+{
+    const double dt_nom0 = P->dt_nom, t0 = P->t;
+    const size_t nb = sizeof(double) * P->N;
+    int rejected = 0, cg_total = 0, pic_total = 0;
+    double *h0 = (double *)malloc(nb), *hf = (double *)malloc(nb), *hm = (double *)malloc(nb),
+           *h2 = (double *)malloc(nb);
+    memcpy(h0, P->h, nb);
+    int status = OR_OK;
+    for (;;) {
+        double dt = P->dt_nom;
+        const double bp = next_breakpoint(P, t0);
+        if (bp - t0 < dt) dt = bp - t0;
+        if (t_stop - t0 < dt) dt = t_stop - t0;
+        or_attempt Rf, R1, R2;
+        memset(&R1, 0, sizeof(R1));
+        memset(&R2, 0, sizeof(R2));
+        attempt(P, dt, hf, &Rf);
+        cg_total += Rf.cg; pic_total += Rf.picard;
+        int ok = Rf.converged;
+        if (ok) {
+            attempt(P, 0.5 * dt, hm, &R1);
+            cg_total += R1.cg; pic_total += R1.picard;
+            ok = R1.converged;
+        }
+        if (ok) {
+            memcpy(P->h, hm, nb);
+            P->t = t0 + 0.5 * dt;
+            attempt(P, 0.5 * dt, h2, &R2);
+            memcpy(P->h, h0, nb);
+            P->t = t0;
+            cg_total += R2.cg; pic_total += R2.picard;
+            ok = R2.converged;
+        }
+        if (!ok) {
+            rejected++;
+            P->dt_nom = dt / P->f_shrink;
+            if (P->dt_nom < P->dt_min) { P->dt_nom = dt_nom0; status = OR_ERR_DT_MIN; break; }
+            continue;
+        }
+        double err = 0.0;
+        for (int a = 0; a < P->na; a++) {
+            const int c = P->cell[a];
+            const double e = fabs(h2[c] - hf[c]);
+            if (e > err) err = e;
+        }
+        double fac = err > 0.0 ? 0.9 * sqrt(P->tol_time / err) : 2.0;
+        if (fac > 2.0) fac = 2.0;
+        if (fac < 0.2) fac = 0.2;
+        P->dt_nom = dt * fac < P->dt_max ? dt * fac : P->dt_max;
+        P->err_last = err;
+        if (err > P->tol_time) {
+            rejected++;
+            if (P->dt_nom < P->dt_min) { P->dt_nom = dt_nom0; status = OR_ERR_DT_MIN; break; }
+            continue;
+        }
+        if (err > P->err_max) P->err_max = err;
+        memcpy(P->h, h2, nb);
+        double tn = t0 + dt;
+        if (fabs(tn - bp) <= t_tol(tn)) tn = bp;
+        if (fabs(tn - t_stop) <= t_tol(tn)) tn = t_stop;
+        P->t = tn;
+        P->inflow_cum += R1.bnd_in + R2.bnd_in;
+        P->outflow_cum += R1.bnd_out + R2.bnd_out;
+        P->closure_cum += (R1.lin_change - (R1.bnd_in - R1.bnd_out)) + (R2.lin_change - (R2.bnd_in - R2.bnd_out));
+        P->defect_cum += R1.defect + R2.defect;
+        if (info) {
+            info[0] = dt; info[1] = P->t; info[2] = pic_total; info[3] = cg_total;
+            info[4] = rejected; info[5] = R2.max_dh;
+        }
+        break;
+    }
+    free(h0); free(hf); free(hm); free(h2);
+    return status;
+}
+
+double or_time_error(const or_problem *P, int which) { return which ? P->err_max : P->err_last; }
+
+int or_step(or_problem *P, double *info)
+{
+    return P->time_control == 1 ? do_step_richardson(P, INFINITY, info) : do_step(P, INFINITY, info);
+}
 
 /* Advance to t_end.  log: up to log_cap rows of the 6 step-info values. */
 int or_run(or_problem *P, double t_end, double *log, int log_cap, int *n_steps)
@@ -799,7 +894,7 @@ int or_run(or_problem *P, double t_end, double *log, int log_cap, int *n_steps)
     int ns = 0;
     while (P->t < t_end - t_tol(t_end)) {
         double info[6];
-        int st = do_step(P, t_end, info);
+        int st = P->time_control == 1 ? do_step_richardson(P, t_end, info) : do_step(P, t_end, info);
         if (st) { if (n_steps) *n_steps = ns; return st; }
         if (log && ns < log_cap) memcpy(&log[6 * ns], info, sizeof(info));
         ns++;

@@ -12,7 +12,11 @@ state across layers (series resistance), the arithmetic mean of Sec. 2.2
 does not.
 
 Brooks-Corey closure (the alternative Sec. 1 names): closed forms, C as
-d(theta)/dh, continuity at the air-entry head, a mass-conserving run."""
+d(theta)/dh, continuity at the air-entry head, a mass-conserving run.
+
+Richardson step-doubling time control (the alternative to EBATS Sec. 2.2
+names): the error estimate is second order in dt, accepted steps respect the
+tolerance, the global error falls with it."""
 import numpy as np
 import pytest
 
@@ -163,3 +167,44 @@ def test_brooks_corey_column_conserves_mass():
     assert sum(s.rejected for s in steps) == 0
     assert mb["closure_rel"] <= 1e-11
     assert mb["inflow_cum"] > 0.0
+
+
+def _column_state():
+    from paper_1809_10895_gb300 import workloads as W
+    from tests.helpers import oracle_from_case
+    case = W.infiltration_column(nz=60, dz=0.01, t_end=3600.0)
+    o = oracle_from_case(case)
+    o.run(600.0)
+    return case, oracle_from_case, o.get_state()
+
+
+def test_richardson_estimate_is_second_order():
+    # the step-doubling estimate of backward Euler's local error scales as dt^2
+    case, mk, (h0, meta) = _column_state()
+    errs = []
+    for dt in (8.0, 4.0, 2.0):
+        q = mk(case, time_control=1, tol_time=1e9, dt0=dt)
+        q.set_state(h0, meta["t"])
+        assert q.step().dt == dt
+        errs.append(q.time_error(largest=False))
+    for a, b in zip(errs, errs[1:]):
+        assert 3.0 <= a / b <= 5.0
+
+
+def test_richardson_control_bounds_the_error():
+    # every accepted step's estimate is within tol; the error against a fine
+    # fixed-dt reference shrinks with tol; the balance closes
+    case, mk, (h0, meta) = _column_state()
+    ref = mk(case, dt0=0.25, f_grow=1.0)
+    ref.set_state(h0, meta["t"])
+    ref.run(meta["t"] + 600.0)
+    hr = ref.get_state()[0]
+    glob = {}
+    for tol in (1e-2, 1e-4):
+        q = mk(case, time_control=1, tol_time=tol, dt0=1.0)
+        q.set_state(h0, meta["t"])
+        q.run(meta["t"] + 600.0)
+        assert q.time_error() <= tol
+        assert q.mass_balance()["closure_rel"] <= 1e-9
+        glob[tol] = np.max(np.abs(q.get_state()[0] - hr))
+    assert glob[1e-4] < 0.5 * glob[1e-2]
