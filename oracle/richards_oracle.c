@@ -81,6 +81,9 @@ typedef struct or_problem {
     int picard_form;     /* 0 classical Picard with chord capacity, 1 modified Picard */
     int face_mean;       /* interface K: 0 arithmetic (linear interpolation, Sec. 2.2), 1 harmonic */
     int time_control;    /* 0 EBATS (Sec. 2.2), 1 Richardson step doubling */
+    int time_scheme;     /* 0 backward Euler (Sec. 2.2), 1 variable-step BDF2 (needs picard_form 1) */
+    double *h_prev;      /* BDF2: h^{n-1} */
+    double dt_prev;      /* BDF2: the previous step's dt (0: no history, the step is backward Euler) */
     double tol_time;     /* Richardson: bound on max |h(2 x dt/2) - h(dt)| per step [m] */
     double err_last, err_max;   /* Richardson estimate of the last and the largest accepted step */
     double grav[3];      /* gradient of elevation in grid axes (x, y, z); (0, 0, 1) for z up.
@@ -180,6 +183,7 @@ or_problem *or_create(int nx, int ny, int nz, double dx, double dy, double dz, d
     P->zone = (unsigned char *)calloc(P->N, 1);
     P->Ks = (double *)calloc(P->N, sizeof(double));
     P->h = (double *)calloc(P->N, sizeof(double));
+    P->h_prev = (double *)calloc(P->N, sizeof(double));
     for (int f = 0; f < OR_NFACES; f++) P->bc[f].type = OR_ZERO_FLUX;
     /* defaults (readings): Picard 1e-6 m, CG 1e-10 relative, EBATS 10/3/8, f 1.3 */
     P->tol_picard = 1e-6; P->tol_cg = 1e-10; P->cg_max_it = 10000;
@@ -197,7 +201,7 @@ void or_destroy(or_problem *P)
     if (!P) return;
     for (int f = 0; f < OR_NFACES; f++) { free(P->bc[f].t); free(P->bc[f].v); }
     free(P->active); free(P->idx); free(P->cell); free(P->zones); free(P->zone);
-    free(P->Ks); free(P->h); free(P);
+    free(P->Ks); free(P->h); free(P->h_prev); free(P);
 }
 
 int or_num_active(const or_problem *P) { return P->na; }
@@ -252,6 +256,7 @@ int or_set_param(or_problem *P, const char *name, double value)
     if (!strcmp(name, "grav_y")) { P->grav[1] = value; return OR_OK; }
     if (!strcmp(name, "grav_z")) { P->grav[2] = value; return OR_OK; }
     IP(cg_max_it) IP(n_inc) IP(n_small) IP(n_max) IP(solver) IP(picard_form) IP(face_mean) IP(time_control)
+    IP(time_scheme)
     DP(tol_time)
 #undef DP
 #undef IP
@@ -291,6 +296,7 @@ int or_set_state(or_problem *P, const double *h, double t)
     P->storage0 = storage_of(P, P->h);
     P->inflow_cum = P->outflow_cum = P->closure_cum = P->defect_cum = 0.0;
     P->err_last = P->err_max = 0.0;
+    P->dt_prev = 0.0;
     return OR_OK;
 }
 
@@ -386,7 +392,19 @@ static void assemble(const or_problem *P, const double *hk, const double *hn, do
         closure(s, P->Ks[p], hn[p], &thn, &Kn, &Cn);
         S->K[a] = Kk;
         S->theta[a] = thk;
-        if (P->picard_form == 1) {
+        if (P->picard_form == 1 && P->time_scheme == 1 && P->dt_prev > 0.0) {
+            /* variable-step BDF2 (the multistep alternative Sec. 2.2 names),
+             * mixed form: V/dt [a0 theta^{n+1} - a1 theta^n + a2 theta^{n-1}]
+             * with w = dt / dt_prev, a0 = (1 + 2w)/(1 + w), a1 = 1 + w,
+             * a2 = w^2 / (1 + w); theta^{n+1} linearised about h^k as in the
+             * modified Picard form */
+            const double w = dt / P->dt_prev;
+            const double a0 = (1.0 + 2.0 * w) / (1.0 + w), a1 = 1.0 + w, a2 = w * w / (1.0 + w);
+            double thp, Kp, Cp;
+            closure(s, P->Ks[p], P->h_prev[p], &thp, &Kp, &Cp);
+            S->c[a] = a0 * V * Ck / dt;
+            S->s0[a] = S->c[a] * hk[p] - V * (a0 * thk - a1 * thn + a2 * thp) / dt;
+        } else if (P->picard_form == 1) {
             S->c[a] = V * Ck / dt;
             S->s0[a] = S->c[a] * hk[p] - V * (thk - thn) / dt;
         } else {
@@ -769,6 +787,10 @@ static int do_step(or_problem *P, double t_stop, double *info)
         attempt(P, dt, hk, &R);
         cg_total += R.cg;
         if (R.converged) {
+            if (P->time_scheme == 1) {
+                memcpy(P->h_prev, P->h, sizeof(double) * P->N);
+                P->dt_prev = dt;
+            }
             memcpy(P->h, hk, sizeof(double) * P->N);
             double tn = P->t + dt;
             if (fabs(tn - bp) <= t_tol(tn)) tn = bp;
@@ -883,8 +905,15 @@ static int do_step_richardson(or_problem *P, double t_stop, double *info)
 
 double or_time_error(const or_problem *P, int which) { return which ? P->err_max : P->err_last; }
 
+/* BDF2 runs in the mixed (modified Picard) form, under EBATS */
+static int scheme_ok(const or_problem *P)
+{
+    return P->time_scheme == 0 || (P->time_scheme == 1 && P->picard_form == 1 && P->time_control == 0);
+}
+
 int or_step(or_problem *P, double *info)
 {
+    if (!scheme_ok(P)) return OR_ERR_ARG;
     return P->time_control == 1 ? do_step_richardson(P, INFINITY, info) : do_step(P, INFINITY, info);
 }
 
@@ -892,6 +921,7 @@ int or_step(or_problem *P, double *info)
 int or_run(or_problem *P, double t_end, double *log, int log_cap, int *n_steps)
 {
     int ns = 0;
+    if (!scheme_ok(P)) return OR_ERR_ARG;
     while (P->t < t_end - t_tol(t_end)) {
         double info[6];
         int st = P->time_control == 1 ? do_step_richardson(P, t_end, info) : do_step(P, t_end, info);

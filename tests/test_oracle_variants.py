@@ -16,7 +16,10 @@ d(theta)/dh, continuity at the air-entry head, a mass-conserving run.
 
 Richardson step-doubling time control (the alternative to EBATS Sec. 2.2
 names): the error estimate is second order in dt, accepted steps respect the
-tolerance, the global error falls with it."""
+tolerance, the global error falls with it.
+
+Variable-step BDF2 (the multistep alternative Sec. 2.2 names): second order
+in time where backward Euler is first order."""
 import numpy as np
 import pytest
 
@@ -208,3 +211,43 @@ def test_richardson_control_bounds_the_error():
         assert q.mass_balance()["closure_rel"] <= 1e-9
         glob[tol] = np.max(np.abs(q.get_state()[0] - hr))
     assert glob[1e-4] < 0.5 * glob[1e-2]
+
+
+LOAM_O = dict(model=O.VG, theta_r=0.078, theta_s=0.43, alpha=3.6, n=1.56, Ks=2.89e-6, S=1e-5)
+
+
+def _fixed_dt_column(scheme, dt, T=1800.0, picard_form=1):
+    o = O.Oracle(1, 1, 40, 1.0, 1.0, 0.025, 0.0, None)
+    o.set_soils([LOAM_O], None, None)
+    o.set_bc(O.ZMAX, O.DIRICHLET, np.array([0.0]), np.array([-0.3]))
+    o.set_bc(O.ZMIN, O.FREE_DRAINAGE)
+    o.set_params(picard_form=picard_form, time_scheme=scheme, dt0=dt, dt_max=dt, f_grow=1.0, tol_picard=1e-11,
+                 tol_cg=1e-14)
+    o.set_state(np.full(40, -1.0), 0.0)
+    steps = o.run(T)
+    assert all(s.rejected == 0 for s in steps)
+    return o.get_state()[0], o.mass_balance()
+
+
+def test_bdf2_is_second_order_and_backward_euler_first():
+    # variable-step BDF2 (the multistep alternative Sec. 2.2 names), mixed
+    # form: halving dt divides the error at t = 30 min by ~4; backward Euler
+    # by ~2 (reference: BDF2 at dt = 0.94 s)
+    ref, _ = _fixed_dt_column(1, 0.9375)
+    err = {}
+    for scheme in (0, 1):
+        err[scheme] = []
+        for dt in (30.0, 15.0, 7.5):
+            h, mb = _fixed_dt_column(scheme, dt)
+            assert mb["closure_rel"] <= 1e-9
+            err[scheme].append(np.max(np.abs(h - ref)))
+    for a, b in zip(err[0], err[0][1:]):
+        assert 1.7 <= a / b <= 2.3
+    for a, b in zip(err[1], err[1][1:]):
+        assert 3.4 <= a / b <= 4.6
+    assert err[1][1] < 0.1 * err[0][1]
+
+
+def test_bdf2_needs_the_mixed_form():
+    with pytest.raises(RuntimeError):
+        _fixed_dt_column(1, 30.0, picard_form=0)
