@@ -21,19 +21,28 @@
  *     with the parameter picard_form = 1;
  *   - Sec. 2.3: the Picard exit test is a global max over the domain;
  *   - Appendix A: Gardner conductivity K = Ks exp(alpha h) (test model).
- * Readings of passages the paper leaves open (storage S for h >= 0, the form
- * of boundary terms, the CG stopping norm, EBATS details) are the ones listed
- * in the project design notes; each is restated where it is used below.
+ * Options for alternatives the paper names: the DIC preconditioner of
+ * Sec. 2.2 (natural and red-black order), Brooks-Corey closures (Sec. 1), a
+ * harmonic interface mean, Richardson step-doubling and variable-step BDF2
+ * time control (Sec. 2.2), and gravity along any grid axis for a grid
+ * aligned with the tilted slab of Sec. 4.2.  Readings of passages the paper
+ * leaves open (storage S for h >= 0, the form of boundary terms, the CG
+ * stopping norm, EBATS details) are restated where they are used below.
  *
  * The linear system is stored explicitly in CSR over the active cells and
- * solved by a textbook Jacobi-PCG, or by a dense Cholesky factorisation on
- * tiny grids.  No blocking, fusion or reordering beyond those definitions.
+ * solved by a textbook Jacobi-PCG or DIC-PCG, or by a dense Cholesky
+ * factorisation on tiny grids.  No blocking, fusion or reordering beyond
+ * those definitions.
  *
  * Pins (tests/test_oracle_*.py): closed forms of the closures, C = dtheta/dh
  * by finite differences, Mualem's integral for K, the hydrostatic fixed point,
  * the saturated linear (heat-equation) limit with exact discrete eigenmodes,
  * Appendix A's analytic Gardner profile, unit-gradient steady state, dense
- * Cholesky vs CG, global mass-balance closure and a scripted EBATS sequence.
+ * Cholesky vs CG, global mass-balance closure, a scripted EBATS sequence,
+ * exact linear steady states through seepage and Dirichlet faces, and for
+ * each option a closed form or an invariant (exact DIC on a tridiagonal
+ * column, axis-permutation invariance of gravity, the layered steady state
+ * of the harmonic mean, the temporal orders of BDF2 and Richardson).
  */
 #include <math.h>
 #include <stdio.h>

@@ -1,4 +1,4 @@
-"""The seeded input recipes have the properties the design notes state:
+"""The seeded input recipes have the properties their builders document:
 deterministic per seed, the stated sizes and ranges, and field statistics
 (the Gaussian random field's variance and correlation length, the terrain's
 range, the storm series' structure)."""
