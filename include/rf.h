@@ -138,7 +138,10 @@ typedef struct rf_allocator {
 
 /* Create a context for a mesh on the current CUDA device; cuda_stream is a
  * cudaStream_t (NULL = the legacy default stream).  All device memory is
- * allocated here (through alloc when given) and released by rf_destroy. */
+ * allocated here (through alloc when given) and released by rf_destroy.
+ * The mesh and params are checked before the device is queried: a bad value
+ * returns RF_ERR_ARG; no sm_103 device returns RF_ERR_NO_DEVICE (there is no
+ * CPU fallback).  *out is NULL on every error. */
 rf_status rf_mesh_create(const rf_mesh_desc *mesh, const rf_solver_params *params, void *cuda_stream,
                          const rf_allocator *alloc, rf_ctx **out);
 void rf_destroy(rf_ctx *ctx);
@@ -291,8 +294,11 @@ typedef struct rf_ens_stats {
     int ctas;                             /* CTAs that ran it in the last run (cluster size or 1) */
 } rf_ens_stats;
 
-/* Create an ensemble (instances copied; params as for rf_mesh_create; the
- * precision selects FP64 PCG or FP32 inner PCG in FP64 defect correction). */
+/* Create an ensemble (instances copied; params checked as for rf_mesh_create;
+ * the precision selects FP64 PCG or FP32 inner PCG in FP64 defect
+ * correction).  The ensemble runs the chord Picard form with Jacobi-PCG only:
+ * another picard_form or precond returns RF_ERR_ARG.  Instances and params are
+ * checked before the device is queried; *out is NULL on every error. */
 rf_status rf_ens_create(const rf_ens_instance *inst, int n, const rf_solver_params *params, void *cuda_stream,
                         const rf_allocator *alloc, rf_ens **out);
 void rf_ens_destroy(rf_ens *ens);

@@ -12,6 +12,11 @@
 #include "ensemble.cuh"
 #include "rf.h"
 
+namespace rf {
+// Validation of rf_solver_params shared with rf_mesh_create; sets the last error.
+rf_status check_solver_params(const rf_solver_params *p);
+}  // namespace rf
+
 using namespace rf;
 
 namespace {
@@ -172,26 +177,16 @@ extern "C" {
 rf_status rf_ens_create(const rf_ens_instance *inst, int n, const rf_solver_params *params, void *cuda_stream,
                         const rf_allocator *alloc, rf_ens **out)
 {
+    if (out) *out = nullptr;
     if (!inst || n < 1 || !out) return efail(RF_ERR_ARG, "rf_ens_create: need at least one instance");
-    *out = nullptr;
     rf_solver_params prm;
     rf_default_params(&prm);
     if (params) prm = *params;
-    if (prm.precision != RF_PREC_FP64 && prm.precision != RF_PREC_MIXED)
-        return efail(RF_ERR_ARG, "rf_ens_create: unknown precision");
+    if (rf_status st = check_solver_params(&prm)) return st;
     if (prm.picard_form != RF_PICARD_CHORD)
         return efail(RF_ERR_ARG, "rf_ens_create: the ensemble runs the classical (chord) Picard iteration only");
-    int ndev = 0;
-    if (cudaGetDeviceCount(&ndev) != cudaSuccess || ndev < 1) {
-        cudaGetLastError();
-        return efail(RF_ERR_NO_DEVICE, "no CUDA device visible; this library has no CPU fallback");
-    }
-    int dev = 0;
-    ECUDA(cudaGetDevice(&dev));
-    cudaDeviceProp prop;
-    ECUDA(cudaGetDeviceProperties(&prop, dev));
-    if (prop.major != 10 || prop.minor != 3)
-        return efail(RF_ERR_NO_DEVICE, "this library is built for sm_103a (GB300) only");
+    if (prm.precond != RF_PRECOND_JACOBI)
+        return efail(RF_ERR_ARG, "rf_ens_create: the ensemble's PCG is Jacobi-preconditioned only");
     long long total = 0;
     for (int i = 0; i < n; i++) {
         const rf_ens_instance &a = inst[i];
@@ -209,6 +204,18 @@ rf_status rf_ens_create(const rf_ens_instance *inst, int n, const rf_solver_para
         total += (long long)a.nx * a.ny * a.nz;
     }
     if (total > (1LL << 31) - 1) return efail(RF_ERR_ARG, "rf_ens_create: too many cells");
+
+    int ndev = 0;
+    if (cudaGetDeviceCount(&ndev) != cudaSuccess || ndev < 1) {
+        cudaGetLastError();
+        return efail(RF_ERR_NO_DEVICE, "no CUDA device visible; this library has no CPU fallback");
+    }
+    int dev = 0;
+    ECUDA(cudaGetDevice(&dev));
+    cudaDeviceProp prop;
+    ECUDA(cudaGetDeviceProperties(&prop, dev));
+    if (prop.major != 10 || prop.minor != 3)
+        return efail(RF_ERR_NO_DEVICE, "this library is built for sm_103a (GB300) only");
 
     rf_ens *e = new rf_ens();
     e->stream = static_cast<cudaStream_t>(cuda_stream);

@@ -676,6 +676,11 @@ rf_status storage_of_theta_n(rf_ctx *c, double *out)
 
 }  // namespace
 
+namespace rf {
+// rf_solver_params validation, shared with rf_ens_create
+rf_status check_solver_params(const rf_solver_params *p) { return check_params(p); }
+}  // namespace rf
+
 // =========================================================================
 extern "C" {
 
@@ -707,8 +712,8 @@ const char *rf_last_error(void) { return g_err.c_str(); }
 rf_status rf_mesh_create(const rf_mesh_desc *mesh, const rf_solver_params *params, void *cuda_stream,
                          const rf_allocator *alloc, rf_ctx **out)
 {
+    if (out) *out = nullptr;
     if (!mesh || !out) return fail(RF_ERR_ARG, "null argument");
-    *out = nullptr;
     if (mesh->nx < 1 || mesh->ny < 1 || mesh->nz < 1 || !(mesh->dx > 0) || !(mesh->dy > 0) || !(mesh->dz > 0))
         return fail(RF_ERR_ARG, "mesh sizes and spacings must be positive");
     const long long N = (long long)mesh->nx * mesh->ny * mesh->nz;
