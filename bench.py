@@ -123,11 +123,12 @@ class ClockSampler:
 
 
 # ------------------------------------------------------------ CPU baseline
-def oracle_steps(case, n_steps=None, budget_s=20.0):
-    """Time the CPU oracle (as it stands, single thread) on the first accepted
-    steps of the same workload; stops at n_steps or after budget_s."""
+def oracle_steps(case, n_steps=None, budget_s=20.0, openmp=False):
+    """Time the CPU oracle (as it stands: one thread, or the same source built
+    with OpenMP on all cores) on the first accepted steps of the same
+    workload; stops at n_steps or after budget_s."""
     from tests.helpers import oracle_from_case
-    o = oracle_from_case(case)
+    o = oracle_from_case(case, openmp=openmp)
     t0 = time.perf_counter()
     k = 0
     while (n_steps is None or k < n_steps) and time.perf_counter() - t0 < budget_s:
@@ -137,10 +138,27 @@ def oracle_steps(case, n_steps=None, budget_s=20.0):
     return k, dt
 
 
+def oracle_threads():
+    """Threads of the OpenMP build of the oracle (0 when it cannot be built)."""
+    from oracle import oracle as O
+    return O.num_threads(openmp=True)
+
+
 def cpu_baseline(case, budget_s=20.0):
-    k, dt = oracle_steps(case, None, budget_s)
-    return {"value": k * case.n_active() / dt, "unit": UNIT, "cores": 1, "kind": "oracle",
-            "sample": f"first {k} accepted steps of {WORKLOAD} from t=0 ({dt:.1f} s, single-thread C oracle)"}
+    """The oracle on the host cores: the OpenMP build on all of them, with the
+    one-thread build beside it, both over the same first steps (as many as the
+    one-thread build takes in half the budget)."""
+    k1, t1 = oracle_steps(case, None, budget_s / 2)
+    single = {"value": k1 * case.n_active() / t1, "unit": UNIT, "cores": 1, "kind": "oracle",
+              "sample": f"first {k1} accepted steps of {WORKLOAD} from t=0 ({t1:.1f} s, one-thread C oracle)"}
+    threads = oracle_threads()
+    if threads < 1:
+        return dict(single, note="OpenMP build of the oracle unavailable (gcc -fopenmp failed)")
+    k, t = oracle_steps(case, k1, budget_s / 2, openmp=True)
+    return {"value": k * case.n_active() / t, "unit": UNIT, "cores": threads, "kind": "oracle",
+            "sample": f"first {k} accepted steps of {WORKLOAD} from t=0 ({t:.1f} s, C oracle built with "
+                      f"OpenMP, {threads} threads)",
+            "single_thread": single}
 
 
 # ------------------------------------------------------------ native arm
@@ -622,7 +640,9 @@ def warmstart_leg(args, rank, rf, W, peaks):
 
 # ---------------------------------------------------------- reference arm
 def reference(args):
-    """The CPU oracle, as it stands, on the same workload and metric."""
+    """The CPU oracle, as it stands, on the same workload and metric: its
+    OpenMP build on all host cores, or the one-thread build where gcc cannot
+    build that."""
     rank = _env_int("RANK", 0)
     if rank != 0:
         return
@@ -635,7 +655,9 @@ def reference(args):
     w = min(args.warmup, 3)
     k = max(1, min(args.steps, 40))
     from tests.helpers import oracle_from_case
-    o = oracle_from_case(case)
+    threads = O.num_threads(openmp=True)          # all host cores; 0: one-thread build only
+    o = oracle_from_case(case, openmp=threads > 0)
+    cores = max(threads, 1)
     for _ in range(w):
         o.step()
     t0 = time.perf_counter()
@@ -647,8 +669,9 @@ def reference(args):
         "impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": 1, "steps": k, "warmup": w,
         "ms_per_step": dt * 1e3 / k, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
         "dtype": "f64", "data": "synthetic (seeded Gaussian random field, no dataset)", "config": config_dict(),
-        "cpu_baseline": {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle",
-                         "sample": f"accepted steps {w + 1}..{w + k} of {WORKLOAD} (single-thread C oracle)"},
+        "cpu_baseline": {"value": v, "unit": UNIT, "cores": cores, "kind": "oracle",
+                         "sample": f"accepted steps {w + 1}..{w + k} of {WORKLOAD} (C oracle, "
+                                   + (f"OpenMP, {threads} threads)" if threads else "one thread)")},
         "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }))
 

@@ -34,6 +34,13 @@
  * factorisation on tiny grids.  No blocking, fusion or reordering beyond
  * those definitions.
  *
+ * Built plainly it runs on one thread.  Built with -fopenmp, the loops that
+ * treat every cell on its own (closures, matrix rows, the Jacobi-PCG vector
+ * operations, the water balance) and the sums and maxima over cells run on
+ * all cores; a sum over cells is then added in another order, so results
+ * differ by rounding only.  The pins use the one-thread build; the threaded
+ * one serves the all-core CPU baseline.
+ *
  * Pins (tests/test_oracle_*.py): closed forms of the closures, C = dtheta/dh
  * by finite differences, Mualem's integral for K, the hydrostatic fixed point,
  * the saturated linear (heat-equation) limit with exact discrete eigenmodes,
@@ -48,6 +55,9 @@
 #include <stdio.h>
 #include <stdlib.h>
 #include <string.h>
+#ifdef _OPENMP
+#include <omp.h>
+#endif
 
 enum { OR_VG = 0, OR_GARDNER = 1, OR_BROOKS_COREY = 2 };
 enum { OR_ZERO_FLUX = 0, OR_DIRICHLET = 1, OR_FLUX = 2, OR_FREE_DRAINAGE = 3, OR_SEEPAGE = 4 };
@@ -98,6 +108,8 @@ typedef struct or_problem {
     double grav[3];      /* gradient of elevation in grid axes (x, y, z); (0, 0, 1) for z up.
                           * Eq. 1's gravity term for a grid aligned with a tilted slab */
 
+    int *row_ptr;        /* na + 1: CSR row starts, fixed by the active pattern */
+
     /* state */
     double *h;           /* N */
     double t, dt_nom;
@@ -106,6 +118,8 @@ typedef struct or_problem {
     /* mass balance */
     double storage0, inflow_cum, outflow_cum, closure_cum, defect_cum;
 } or_problem;
+
+static int neighbour(const or_problem *P, int i, int j, int k, int f);
 
 /* ------------------------------------------------------------------------ */
 /* Closures, Eq. 2-4 (van Genuchten / Mualem) and Appendix A (Gardner).      */
@@ -189,6 +203,17 @@ or_problem *or_create(int nx, int ny, int nz, double dx, double dy, double dz, d
         if (P->active[p]) { P->idx[p] = P->na; P->cell[P->na] = p; P->na++; }
         else P->idx[p] = -1;
     }
+    /* a matrix row holds the diagonal and one entry per active neighbour */
+    P->row_ptr = (int *)malloc(sizeof(int) * (P->na + 1));
+    P->row_ptr[0] = 0;
+    for (int a = 0; a < P->na; a++) {
+        int p = P->cell[a], i = p % nx, j = (p / nx) % ny, k = p / (nx * ny), nnz = 1;
+        for (int f = 0; f < 6; f++) {
+            int q = neighbour(P, i, j, k, f);
+            if (q >= 0 && P->active[q]) nnz++;
+        }
+        P->row_ptr[a + 1] = P->row_ptr[a] + nnz;
+    }
     P->zone = (unsigned char *)calloc(P->N, 1);
     P->Ks = (double *)calloc(P->N, sizeof(double));
     P->h = (double *)calloc(P->N, sizeof(double));
@@ -210,10 +235,20 @@ void or_destroy(or_problem *P)
     if (!P) return;
     for (int f = 0; f < OR_NFACES; f++) { free(P->bc[f].t); free(P->bc[f].v); }
     free(P->active); free(P->idx); free(P->cell); free(P->zones); free(P->zone);
-    free(P->Ks); free(P->h); free(P->h_prev); free(P);
+    free(P->Ks); free(P->h); free(P->h_prev); free(P->row_ptr); free(P);
 }
 
 int or_num_active(const or_problem *P) { return P->na; }
+
+/* threads the per-cell loops run on: 1 unless built with OpenMP */
+int or_num_threads(void)
+{
+#ifdef _OPENMP
+    return omp_get_max_threads();
+#else
+    return 1;
+#endif
+}
 
 int or_set_soils(or_problem *P, int nzones, const int *model, const double *theta_r,
                  const double *theta_s, const double *alpha, const double *n, const double *Ks,
@@ -286,6 +321,7 @@ static double series_at(const or_bc *b, double t)
 static double storage_of(const or_problem *P, const double *h)
 {
     double V = P->dx * P->dy * P->dz, s = 0.0;
+#pragma omp parallel for reduction(+ : s)
     for (int a = 0; a < P->na; a++) {
         int p = P->cell[a];
         double th, K, C;
@@ -393,6 +429,7 @@ static void assemble(const or_problem *P, const double *hk, const double *hn, do
      * c (h^{k+1} - h^n).  Modified Picard: C^k = C(h^k), storage
      * c (h^{k+1} - h^k) + V (theta*(h^k) - theta*(h^n)) / dt.  Both vanish
      * in the same way at a converged iterate, V (theta* - theta*^n) / dt. */
+#pragma omp parallel for
     for (int a = 0; a < P->na; a++) {
         int p = P->cell[a];
         const or_soil *s = &P->zones[P->zone[p]];
@@ -425,7 +462,7 @@ static void assemble(const or_problem *P, const double *hk, const double *hn, do
         }
     }
 
-    int nnz = 0;
+#pragma omp parallel for
     for (int a = 0; a < P->na; a++) {
         int p = P->cell[a];
         int i = p % P->nx, j = (p / P->nx) % P->ny, k = p / (P->nx * P->ny);
@@ -488,6 +525,7 @@ static void assemble(const or_problem *P, const double *hk, const double *hn, do
             }
         }
         /* CSR row with columns in ascending cell order */
+        int nnz = P->row_ptr[a];
         S->row_ptr[a] = nnz;
         const int order[7] = { OR_ZMIN, OR_YMIN, OR_XMIN, -1, OR_XMAX, OR_YMAX, OR_ZMAX };
         for (int o = 0; o < 7; o++) {
@@ -498,8 +536,8 @@ static void assemble(const or_problem *P, const double *hk, const double *hn, do
         S->diag[a] = diag;
         S->b[a] = rhs;
     }
-    S->row_ptr[P->na] = nnz;
-    S->nnz = nnz;
+    S->row_ptr[P->na] = P->row_ptr[P->na];
+    S->nnz = P->row_ptr[P->na];
 }
 
 /* ------------------------------------------------------------------------ */
@@ -507,6 +545,7 @@ static void assemble(const or_problem *P, const double *hk, const double *hn, do
 /* ------------------------------------------------------------------------ */
 static void csr_spmv(int n, const int *rp, const int *col, const double *val, const double *x, double *y)
 {
+#pragma omp parallel for
     for (int r = 0; r < n; r++) {
         double s = 0.0;
         for (int e = rp[r]; e < rp[r + 1]; e++) s += val[e] * x[col[e]];
@@ -517,6 +556,7 @@ static void csr_spmv(int n, const int *rp, const int *col, const double *val, co
 static double dot(int n, const double *a, const double *b)
 {
     double s = 0.0;
+#pragma omp parallel for reduction(+ : s)
     for (int i = 0; i < n; i++) s += a[i] * b[i];
     return s;
 }
@@ -531,25 +571,30 @@ static int pcg_jacobi(int n, const int *rp, const int *col, const double *val, c
     double *r = (double *)malloc(sizeof(double) * n), *z = (double *)malloc(sizeof(double) * n);
     double *p = (double *)malloc(sizeof(double) * n), *q = (double *)malloc(sizeof(double) * n);
     csr_spmv(n, rp, col, val, x, q);
+#pragma omp parallel for
     for (int i = 0; i < n; i++) r[i] = b[i] - q[i];
     double bnorm = sqrt(dot(n, b, b));
     double rnorm = sqrt(dot(n, r, r));
     int it = 0, status = 0;
     if (!(rnorm <= tol * bnorm)) {
+#pragma omp parallel for
         for (int i = 0; i < n; i++) { z[i] = r[i] / diag[i]; p[i] = z[i]; }
         double rz = dot(n, r, z);
         for (it = 1; it <= max_it; it++) {
             csr_spmv(n, rp, col, val, p, q);
             double pq = dot(n, p, q);
             double alpha = rz / pq;
+#pragma omp parallel for
             for (int i = 0; i < n; i++) { x[i] += alpha * p[i]; r[i] -= alpha * q[i]; }
             rnorm = sqrt(dot(n, r, r));
             if (!isfinite(rnorm)) { status = -2; break; }
             if (rnorm <= tol * bnorm) break;
+#pragma omp parallel for
             for (int i = 0; i < n; i++) z[i] = r[i] / diag[i];
             double rz_new = dot(n, r, z);
             double beta = rz_new / rz;
             rz = rz_new;
+#pragma omp parallel for
             for (int i = 0; i < n; i++) p[i] = z[i] + beta * p[i];
         }
         if (status == 0 && it > max_it) status = -1;
@@ -698,6 +743,7 @@ static void attempt(const or_problem *P, double dt, double *hk_out, or_attempt *
     memset(R, 0, sizeof(*R));
     for (int it = 1; it <= P->n_max; it++) {
         assemble(P, hk, P->h, dt, P->t, &S);
+#pragma omp parallel for
         for (int a = 0; a < na; a++) x[a] = hk[P->cell[a]];
         int cg;
         cg = solve_system(P, P->solver, &S, x, NULL);
@@ -706,11 +752,13 @@ static void attempt(const or_problem *P, double dt, double *hk_out, or_attempt *
         R->cg += cg;
         double dh = 0.0;
         int finite = 1;
+#pragma omp parallel for reduction(max : dh) reduction(min : finite)
         for (int a = 0; a < na; a++) {
             double e = fabs(x[a] - hk[P->cell[a]]);
             if (!isfinite(x[a])) finite = 0;
             if (e > dh) dh = e;
         }
+#pragma omp parallel for
         for (int a = 0; a < na; a++) hk[P->cell[a]] = x[a];
         R->max_dh = dh;
         if (!finite) { R->status = OR_ERR_CG; break; }
@@ -719,6 +767,7 @@ static void attempt(const or_problem *P, double dt, double *hk_out, or_attempt *
             /* mass balance of the last linear system (interior fluxes cancel) */
             const double V = P->dx * P->dy * P->dz;
             double lin = 0.0, bin = 0.0, bout = 0.0, ds = 0.0;
+#pragma omp parallel for reduction(+ : lin, bin, bout, ds)
             for (int a = 0; a < na; a++) {
                 int p = P->cell[a];
                 /* storage of the solved system: c (x - h^n), or for modified

@@ -17,8 +17,8 @@ def oracle_soil(s: dict) -> dict:
     return d
 
 
-def oracle_from_case(case, **param_overrides) -> O.Oracle:
-    o = O.Oracle(case.nx, case.ny, case.nz, case.dx, case.dy, case.dz, case.z_bottom, case.active)
+def oracle_from_case(case, openmp=False, **param_overrides) -> O.Oracle:
+    o = O.Oracle(case.nx, case.ny, case.nz, case.dx, case.dy, case.dz, case.z_bottom, case.active, openmp=openmp)
     o.set_soils([oracle_soil(s) for s in case.soils], case.zone_of_cell, case.Ks_cell)
     for bc in case.bcs:
         o.set_bc(_FACE[bc.face], _BC[bc.type], bc.t, bc.v)
