@@ -86,7 +86,14 @@ def lib(openmp: bool = False):
     build is not possible here)."""
     if openmp not in _libs:
         path = build(openmp=openmp)
-        _libs[openmp] = None if path is None else _configure(C.CDLL(path))
+        L = None
+        if path is not None:
+            try:
+                L = _configure(C.CDLL(path))
+            except OSError:                 # e.g. no OpenMP runtime to load
+                if not openmp:
+                    raise
+        _libs[openmp] = L
     return _libs[openmp]
 
 
