@@ -1,7 +1,9 @@
 """Pins of the oracle's closures (Eq. 2-4, Eq. A6) against facts that do not
 come from retyping those formulas: closed forms at special points, the
 identity C = d(theta)/dh, Mualem's integral definition of the relative
-conductivity, limits and monotonicity."""
+conductivity, limits and monotonicity; and, at 80 heads from -1e-5 to
+-1e3 m, K against Mualem's integral and C against the derivative of Eq. 2,
+both in 30-digit arithmetic, to the rounding of the FP64 literal forms."""
 import math
 
 import numpy as np
@@ -108,3 +110,85 @@ def test_gardner_closed_forms():
         fd = (O.closure(g, h + eps)[0] - O.closure(g, h - eps)[0]) / (2 * eps)
         assert C == pytest.approx(fd, rel=1e-7)
     assert O.closure(g, 0.0) == (0.4, 1e-6, 1e-5)
+
+
+# ---------------------------------------------------------------- high precision
+# Independent high-precision references (mpmath, 30 digits): Mualem's integral
+# for K (not Eq. 4's closed form) and the derivative of Eq. 2's retention
+# curve for C (not Eq. 3).  The oracle evaluates Eq. 3 and Eq. 4 literally in
+# FP64, so the tolerance follows the rounding of that literal form.
+try:
+    import mpmath as mp
+except ImportError:                      # the other pins of this file need no mpmath
+    mp = None
+needs_mpmath = pytest.mark.skipif(mp is None, reason="mpmath is not installed")
+EPS = np.finfo(float).eps
+H_DENSE = -np.logspace(-5, 3, 80)
+
+
+def _mualem_kr(s, h):
+    """Mualem's K_r = Se^(1/2) [I(Se) / I(1)]^2 with I(Se) = int_0^Se dx / |h(x)|
+    and |h(x)| = (x^(-1/m) - 1)^(1/n) / alpha, by tanh-sinh quadrature.  Near
+    x = 1 the integrand behaves as (m / (1 - x))^(1/n); with 1 - x = t^(1/m)
+    it becomes smooth in t, so the wet part is integrated in t and the wet
+    end taken as I(1) minus the part over x in [Se, 1]."""
+    with mp.workdps(30):
+        n = mp.mpf(s["n"])
+        m = 1 - 1 / n
+        f = lambda x: (x ** (-1 / m) - 1) ** (-1 / n)          # alpha cancels in the ratio
+
+        def wet(y_top):                                        # int over x in [1 - y_top, 1]
+            q = 1 / m
+            g = lambda t: mp.expm1(-mp.log1p(-t ** q) / m) ** (-1 / n) * q * t ** (q - 1)
+            return mp.quad(g, [0, y_top ** m])
+
+        se = (1 + (-mp.mpf(s["alpha"]) * mp.mpf(h)) ** n) ** (-m)
+        half = mp.mpf(1) / 2
+        i1 = mp.quad(f, [0, half]) + wet(half)
+        i_se = mp.quad(f, [0, se]) if se < half else i1 - wet(1 - se)
+        kr = mp.sqrt(se) * (i_se / i1) ** 2
+        # pieces of the literal form, for its rounding bound
+        s1 = se ** (1 / m)
+        u = 1 - s1
+        v = u ** m
+        w = 1 - v
+        return kr, float(s1), float(u), float(v), float(w), float(m)
+
+
+def _literal_rounding_bound(s1, u, v, w, m):
+    """Relative rounding error of Ks Se^(1/2) [1 - (1 - Se^(1/m))^m]^2 taken
+    literally: Se^(1/m) carries ~5 ulp, 1 - Se^(1/m) loses s1/u of it, the
+    m-th power keeps m times that, and 1 - (.)^m loses v/w; the square
+    doubles it.  A factor 4 of margin."""
+    rel_u = 5 * EPS * s1 / u + EPS
+    rel_v = m * rel_u + EPS
+    rel_w = (v / w) * rel_v + EPS
+    return 4 * (2 * rel_w + 4 * EPS)
+
+
+@needs_mpmath
+@pytest.mark.parametrize("s", SOILS)
+def test_conductivity_matches_mualem_integral_to_rounding(s):
+    worst = 0.0
+    for h in H_DENSE:
+        kr, s1, u, v, w, m = _mualem_kr(s, h)
+        K = O.closure(s, float(h))[1]
+        err = abs(K / s["Ks"] / float(kr) - 1)
+        bound = _literal_rounding_bound(s1, u, v, w, m)
+        assert err <= bound, (h, err, bound)
+        worst = max(worst, err)
+    assert worst < 1e-6                       # over 1e-5 .. 1e3 m of suction
+
+
+@needs_mpmath
+@pytest.mark.parametrize("s", SOILS)
+def test_capacity_is_the_high_precision_derivative_of_eq2(s):
+    with mp.workdps(30):
+        n, a = mp.mpf(s["n"]), mp.mpf(s["alpha"])
+        m = 1 - 1 / n
+        d = mp.mpf(s["theta_s"]) - mp.mpf(s["theta_r"])
+        theta = lambda h: mp.mpf(s["theta_r"]) + d * (1 + (-a * h) ** n) ** (-m)     # Eq. 2
+        for h in H_DENSE[::3]:
+            ref = mp.diff(theta, mp.mpf(h))
+            C = O.closure(s, float(h))[2]
+            assert abs(C / float(ref) - 1) <= 1e-12, h
