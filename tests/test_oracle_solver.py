@@ -255,3 +255,27 @@ def test_ponded_column_stalls_at_saturation_for_n_below_2():
         o.run(case.t_end)
     _, meta = o.get_state()
     assert 7200.0 < meta["t"] < 9000.0
+
+
+@pytest.mark.parametrize("nx,ny,dx,dy", [(3, 4, 0.02, 0.03), (5, 1, 0.5, 0.01), (1, 6, 0.01, 2.0)])
+def test_laterally_uniform_block_equals_its_column(nx, ny, dx, dy):
+    # With uniform soil, initial head and top/bottom conditions and zero-flux
+    # sides, no lateral gradient ever forms: each column of the block follows
+    # the 1 x 1 column exactly (lateral faces carry neither a pressure flux
+    # nor gravity), per unit area, whatever the plan cell sizes.  Both solve
+    # each linear system by the dense Cholesky factorisation, so the only
+    # difference left is rounding.
+    nz, dz = 24, 0.01
+    bcs = [W.BC("zmax", "flux", np.array([0.0, 900.0]), np.array([5e-6, 0.0])), W.BC("zmin", "free_drainage")]
+    params = dict(dt0=1.0, dt_max=120.0, solver=O.SOLVER_DENSE)
+    col = oracle_from_case(_box(1, 1, nz, 1.0, 1.0, dz, [VG_SOIL], np.full(nz, -0.8), bcs, params))
+    blk = oracle_from_case(_box(nx, ny, nz, dx, dy, dz, [VG_SOIL], np.full(nx * ny * nz, -0.8), bcs, params))
+    sc, sb = col.run(1800.0), blk.run(1800.0)
+    assert [(s.dt, s.picard, s.rejected) for s in sc] == [(s.dt, s.picard, s.rejected) for s in sb]
+    hc, _ = col.get_state()
+    hb, _ = blk.get_state()
+    assert np.max(np.abs(hb.reshape(nz, ny, nx) - hc[:, None, None])) <= 1e-12
+    mc, mb = col.mass_balance(), blk.mass_balance()
+    area = nx * dx * ny * dy
+    for k in ("storage", "inflow_cum", "outflow_cum"):
+        assert mb[k] / area == pytest.approx(mc[k], rel=1e-12), k
