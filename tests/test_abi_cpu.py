@@ -52,3 +52,64 @@ def test_no_gpu_means_no_device_error(lib):
     assert st == rf.RF_ERR_NO_DEVICE
     assert b"no CPU fallback" in lib.rf_last_error() or b"no CUDA device" in lib.rf_last_error()
     assert not h.value
+
+
+def _prototypes(header):
+    """(return type, name, [parameter types]) of every function declared in
+    the header, comments removed."""
+    import re
+    txt = re.sub(r"/\*.*?\*/", "", open(header).read(), flags=re.S)
+    txt = re.sub(r"#[^\n]*", "", txt)
+    out = []
+    for m in re.finditer(r"([A-Za-z_][A-Za-z_0-9 \*]*?)\b(rf_[a-z_0-9]+)\s*\(([^;{]*?)\)\s*;", txt):
+        ret, name, params = m.group(1).split("\n")[-1].strip(), m.group(2), m.group(3)
+        plist = [p.strip() for p in params.replace("\n", " ").split(",")]
+        plist = [] if plist == ["void"] or plist == [""] else plist
+        out.append((ret, name, plist))
+    return out
+
+
+def _header_kind(decl):
+    """The ABI class of a C declaration (parameter with or without a name)."""
+    if "*" in decl:
+        return "ptr"
+    words = decl.replace("const", "").split()
+    if words[:2] == ["unsigned", "long"]:
+        return "u64"
+    if words[:2] == ["long", "long"]:
+        return "i64"
+    if words[0] == "double":
+        return "f64"
+    if words[0] == "void":
+        return "void"
+    if words[0] in ("int", "rf_status", "rf_face", "rf_bc_type", "rf_precision", "rf_precond", "rf_picard_form"):
+        return "i32"
+    raise AssertionError(f"unclassified C type in {decl!r}")
+
+
+def _ctypes_kind(t):
+    if t is None:
+        return "void"
+    if t in (C.c_void_p, C.c_char_p) or (isinstance(t, type) and issubclass(t, C._Pointer)):
+        return "ptr"
+    return {C.c_int: "i32", C.c_double: "f64", C.c_longlong: "i64", C.c_ulonglong: "u64"}[t]
+
+
+def test_binding_signatures_match_header_prototypes():
+    protos = _prototypes(HEADER)
+    names = [n for _, n, _ in protos]
+    assert sorted(names) == rf.header_function_names(HEADER)
+    for ret, name, params in protos:
+        restype, argtypes = rf.SIGNATURES[name]
+        assert _ctypes_kind(restype) == _header_kind(ret), name
+        assert len(argtypes) == len(params), (name, len(argtypes), params)
+        for i, (a, p) in enumerate(zip(argtypes, params)):
+            assert _ctypes_kind(a) == _header_kind(p), (name, i, p)
+
+
+def test_binding_constants_match_header():
+    import re
+    txt = open(HEADER).read()
+    consts = dict(re.findall(r"#define\s+(RF_[A-Z_]+)\s+(\d+)", txt))
+    assert int(consts["RF_NOALLOC_MAX_CELLS"]) == rf.NOALLOC_MAX_CELLS
+    assert int(consts["RF_NN_PARAMS"]) == rf.NN_PARAMS
