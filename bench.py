@@ -161,6 +161,59 @@ def cpu_baseline(case, budget_s=20.0):
             "single_thread": single}
 
 
+def oracle_configs(args, W):
+    """The oracle on the other workloads, bounded samples of each: the 1-D
+    column over the GPU leg's timed steps (one thread), the first accepted
+    steps of the watershed from t = 0 (OpenMP build), and a stratified sample
+    of the ensemble's instances from t = 0 within its window (one thread)."""
+    from tests.helpers import oracle_from_case
+
+    def steps_within(o, budget_s, max_steps=None, t_stop=None):
+        t0 = time.perf_counter()
+        k = 0
+        while (max_steps is None or k < max_steps) and time.perf_counter() - t0 < budget_s:
+            info = o.step()
+            k += 1
+            if t_stop is not None and info.t >= t_stop - 1e-9:
+                break
+        return k, time.perf_counter() - t0
+
+    out = {}
+    col = W.infiltration_column()
+    o = oracle_from_case(col)
+    for _ in range(5):
+        o.step()
+    k, dt = steps_within(o, 10.0, max_steps=400)
+    out["infiltration_column_1x1x200"] = {
+        "value": k * col.N / dt, "unit": UNIT, "cores": 1, "kind": "oracle",
+        "sample": f"accepted steps 6..{5 + k} from t=0 (the GPU leg's timed steps), one-thread C oracle"}
+    del o
+    threads = oracle_threads()
+    ws = W.watershed(512, 512, 64, seed=args.seed, hours=24)
+    o = oracle_from_case(ws, openmp=threads > 0)
+    k, dt = steps_within(o, 10.0)
+    out["watershed_512x512x64"] = {
+        "value": k * ws.n_active() / dt, "unit": UNIT, "cores": max(threads, 1), "kind": "oracle",
+        "sample": f"first {k} accepted steps from t=0 ({dt:.1f} s, C oracle"
+                  + (f", OpenMP, {threads} threads)" if threads else ", one thread)")}
+    del o
+    cases = W.ensemble(256, seed=args.seed)
+    by_size = sorted(range(len(cases)), key=lambda i: cases[i].N)
+    sample = by_size[8::32]
+    cell_steps, total = 0, 0.0
+    for i in sample:
+        o = oracle_from_case(cases[i])
+        k, dt = steps_within(o, 1.5, t_stop=args.ensemble_window)
+        cell_steps += k * cases[i].n_active()
+        total += dt
+        del o
+    out["ensemble_256_uneven"] = {
+        "value": cell_steps / total, "unit": UNIT, "cores": 1, "kind": "oracle",
+        "sample": f"{len(sample)} of the 256 instances (every 32nd by size), each from t=0 for at most 1.5 s "
+                  f"or {args.ensemble_window:g} s simulated, one-thread C oracle"}
+    return out
+
+
 # ------------------------------------------------------------ native arm
 def max_over_ranks(x, world, device):
     """The largest x over all ranks: the job's time is its slowest rank's."""
@@ -441,6 +494,8 @@ def native(args):
         }
         if not args.no_baseline:
             line["cpu_baseline"] = cpu_baseline(case)
+            if not args.no_configs:
+                line["cpu_baseline_other_configs"] = oracle_configs(args, W)
         print(json.dumps(line))
     if world > 1:
         import torch.distributed as dist
