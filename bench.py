@@ -493,9 +493,16 @@ def native(args):
             "other_configs": cfg,
         }
         if not args.no_baseline:
-            line["cpu_baseline"] = cpu_baseline(case)
+            # host-side legs: an error is recorded in the line, never lost with it
+            try:
+                line["cpu_baseline"] = cpu_baseline(case)
+            except Exception as ex:
+                line["cpu_baseline"] = {"error": f"{type(ex).__name__}: {ex}"[:300]}
             if not args.no_configs:
-                line["cpu_baseline_other_configs"] = oracle_configs(args, W)
+                try:
+                    line["cpu_baseline_other_configs"] = oracle_configs(args, W)
+                except Exception as ex:
+                    line["cpu_baseline_other_configs"] = {"error": f"{type(ex).__name__}: {ex}"[:300]}
         print(json.dumps(line))
     if world > 1:
         import torch.distributed as dist
