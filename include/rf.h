@@ -50,8 +50,11 @@ typedef enum rf_status {
     RF_ERR_DEVICE_TIMEOUT = 9  /* a bounded device loop exhausted its budget          */
 } rf_status;
 
-/* Soil models: van Genuchten / Mualem (Eq. 2-4) and Gardner (Eq. A6, test). */
-typedef enum rf_soil_model { RF_VG = 0, RF_GARDNER = 1 } rf_soil_model;
+/* Soil models: van Genuchten / Mualem (Eq. 2-4), Gardner (Eq. A6, a test
+ * model) and Brooks-Corey (the alternative closure Sec. 1 names: air-entry
+ * head -1/alpha, pore-size index n > 0, Se = (h_b/h)^n below h_b, K = Ks
+ * Se^((2 + 3n)/n)). */
+typedef enum rf_soil_model { RF_VG = 0, RF_GARDNER = 1, RF_BROOKS_COREY = 2 } rf_soil_model;
 
 /* Boundary conditions.  RF_BC_FLUX: imposed total Darcy flux, m/s, positive
  * into the domain (the time-varying Neumann condition of Sec. 3.2).
@@ -68,11 +71,49 @@ typedef enum rf_bc_type {
  * lowest active cell.  Lateral faces touching an inactive cell are zero-flux. */
 typedef enum rf_face { RF_XMIN = 0, RF_XMAX, RF_YMIN, RF_YMAX, RF_ZMIN, RF_ZMAX } rf_face;
 
+/* Arithmetic of the linear solve (Sec. 2.2's PCG).  FP64: the plain path,
+ * an FP64 PCG on the FP64 operator.  MIXED: an FP32 inner PCG inside FP64
+ * defect correction; the operator is assembled in FP64 and the outer
+ * residual, the Picard test and the mass balance stay FP64.  The closures
+ * follow closure_arith (below). */
 typedef enum rf_precision {
-    RF_PREC_FP64 = 0,   /* plain: FP64 PCG                                         */
-    RF_PREC_MIXED = 1   /* FP32 inner PCG inside FP64 defect correction; Picard test,
-                           closures, outer residual and mass balance stay FP64     */
+    RF_PREC_FP64 = 0,
+    RF_PREC_MIXED = 1
 } rf_precision;
+
+/* Arithmetic of the closures (Eq. 2-4).  AUTO: FP64 on the RF_PREC_FP64
+ * path, double-float on the RF_PREC_MIXED path.  FP64: CUDA's FP64 log and
+ * exp.  DOUBLE_FLOAT: pairs of FP32 values (about 48 significant bits: theta*
+ * within 1.2e-14 relative, K and C within 2.4e-13), several times faster on
+ * GB300, whose FP64 pipe is narrow.  Storage, the chord difference, the
+ * operator, the Picard test and the balance are FP64 either way. */
+typedef enum rf_closure_arith {
+    RF_CLOSURE_AUTO = 0, RF_CLOSURE_FP64 = 1, RF_CLOSURE_DOUBLE_FLOAT = 2
+} rf_closure_arith;
+
+/* Interface conductivity of an interior face.  ARITHMETIC: (K_P + K_N)/2,
+ * the linear interpolation of Sec. 2.2 (the default).  HARMONIC: 2 K_P K_N /
+ * (K_P + K_N), the series conductance of two half cells (the interpolation
+ * alternative of Sec. 2.2; RF_PREC_FP64 only).  The same Kbar enters the
+ * Laplacian and the explicit gravity term. */
+typedef enum rf_face_mean { RF_FACE_ARITHMETIC = 0, RF_FACE_HARMONIC = 1 } rf_face_mean;
+
+/* Time discretisation (Sec. 2.2).  BACKWARD_EULER: the paper's scheme.  BDF2:
+ * variable-step second-order backward differentiation in the mixed form,
+ * V/dt [a0 theta^{n+1} - a1 theta^n + a2 theta^{n-1}] with w = dt/dt_prev,
+ * a0 = (1+2w)/(1+w), a1 = 1+w, a2 = w^2/(1+w) (the multistep alternative
+ * Sec. 2.2 names); needs picard_form MODIFIED and time_control EBATS; the
+ * first step after a state is set is backward Euler. */
+typedef enum rf_time_scheme { RF_TIME_BACKWARD_EULER = 0, RF_TIME_BDF2 = 1 } rf_time_scheme;
+
+/* Step-size control (Sec. 2.2).  EBATS: the paper's controller (below).
+ * RICHARDSON: step doubling, the alternative Sec. 2.2 names for prescribing
+ * the temporal error: each step is taken once with dt and twice with dt/2
+ * from the same state; the step is accepted, with the two-half-step result,
+ * when max |h(2 x dt/2) - h(dt)| <= tol_time; either way the next dt is
+ * dt 0.9 sqrt(tol_time / err) clamped to [0.2, 2] dt and to dt_max; a Picard
+ * failure divides dt by f_shrink as in EBATS. */
+typedef enum rf_time_control { RF_TIME_EBATS = 0, RF_TIME_RICHARDSON = 1 } rf_time_control;
 
 /* Preconditioner of the inner PCG.  MG and DIC need RF_PREC_MIXED.  DIC is
  * the diagonal incomplete Cholesky preconditioner Sec. 2.2 solves with, the
@@ -110,13 +151,23 @@ typedef struct rf_solver_params {
     double eps_chord;
     double tol_inner;
     int inner_max_it, outer_max_it;
-    int picard_form;  /* rf_picard_form */
+    int picard_form;    /* rf_picard_form   */
+    int closure_arith;  /* rf_closure_arith */
+    int face_mean;      /* rf_face_mean     */
+    int time_scheme;    /* rf_time_scheme   */
+    int time_control;   /* rf_time_control  */
+    double tol_time;    /* Richardson control: bound on max |h(2 x dt/2) - h(dt)| per step [m] */
+    double grav[3];     /* gradient of elevation along the grid's x, y, z axes: (0, 0, 1) for a
+                           z-up grid; for a grid aligned with a tilted slab (Sec. 4.2), Eq. 1's
+                           gravity term along each axis.  Gravity flux of a face = grad(elevation)
+                           . n_out times Kbar A; free drainage follows it */
 } rf_solver_params;
 
 /* Fill *p with the defaults: tol_picard 1e-6, tol_cg 1e-10, cg_max_it 10000,
  * Jacobi, FP64, dt0 1, dt_max 600, dt_min 1e-3, f 1.3/1.3, n_inc 10, n_small 3,
  * n_max 8, eps_chord 1e-10, tol_inner 1e-4, inner_max_it 2000, outer_max_it 30,
- * classical (chord) Picard. */
+ * classical (chord) Picard, AUTO closures, arithmetic face mean, backward
+ * Euler under EBATS, tol_time 1e-3, grav (0, 0, 1). */
 void rf_default_params(rf_solver_params *p);
 
 /* Structured mesh of equal cells (the paper's solver requires a constant cell
@@ -164,8 +215,11 @@ rf_status rf_soil_set(rf_ctx *ctx, const rf_soil *zones, int n_zones, const uint
  * FREE_DRAINAGE and SEEPAGE take no series (n = 0). */
 rf_status rf_bc_set(rf_ctx *ctx, rf_face face, rf_bc_type type, const double *t, const double *v, int n);
 
-/* Set the state h (N doubles, inactive entries are kept as given) at time t;
- * resets EBATS (dt = dt0) and the mass balance (storage0 = storage of h). */
+/* Set the state h (N doubles, inactive entries are kept as given) at time t:
+ * the pressure head of Eq. 1 at every cell centre.  Resets EBATS (dt = dt0,
+ * Sec. 2.2), the BDF2 history and the mass balance (storage0 = sum of V
+ * theta*(h) over active cells).  Non-finite heads on active cells return
+ * RF_ERR_ARG; RF_ERR_STATE before rf_soil_set. */
 rf_status rf_state_set(rf_ctx *ctx, const double *h, double t);
 rf_status rf_state_set_device(rf_ctx *ctx, const double *d_h, double t);
 
@@ -175,10 +229,18 @@ typedef struct rf_state_meta {
     int n_active;
     long long steps;   /* accepted steps since rf_state_set   */
 } rf_state_meta;
-rf_status rf_state_get(rf_ctx *ctx, double *h, rf_state_meta *meta);   /* h: host, N, or NULL */
-rf_status rf_state_get_device(rf_ctx *ctx, double *d_h);               /* d_h: device, N      */
+/* Read the state: h (host, N doubles, or NULL) and the time-stepping
+ * counters (t, EBATS dt_nom and easy-step counter of Sec. 2.2, active cells,
+ * accepted steps).  The device variant copies h into d_h (device, N). */
+rf_status rf_state_get(rf_ctx *ctx, double *h, rf_state_meta *meta);
+rf_status rf_state_get_device(rf_ctx *ctx, double *d_h);
 
-/* Restore EBATS and mass-balance counters (checkpoint / resume). */
+/* Restore EBATS and mass-balance counters (checkpoint / resume): meta's t,
+ * dt_nom, easy and steps; mass7 (NULL to keep them) holds the seven values of
+ * rf_mass_balance_t in order, of which storage0, inflow_cum, outflow_cum,
+ * closure_abs (as a signed sum) and nonlinear_defect_cum are restored.
+ * RF_ERR_STATE before a state is set.  A run resumed this way is
+ * bit-identical to an uninterrupted one. */
 rf_status rf_state_meta_set(rf_ctx *ctx, const rf_state_meta *meta, const double *mass7);
 
 typedef struct rf_step_info {
@@ -189,18 +251,31 @@ typedef struct rf_step_info {
     double max_dh;         /* last Picard update max|h^{k+1} - h^k|                 */
 } rf_step_info;
 
-/* One accepted backward-Euler step (with EBATS reruns). */
+/* One accepted time step of Sec. 2.2: Picard iterations from h^{n+1,0} = h^n
+ * (closures of Eq. 2-4, chord-slope capacity, assembly, PCG solve, the
+ * global max|dh| exit test of Sec. 2.3) until the test passes; a step that
+ * needs more than n_max iterations, or whose solve fails, is rerun from h^n
+ * with dt / f_shrink (EBATS, Sec. 2.2; or Richardson control, above).  The
+ * step is clipped to the next boundary-series breakpoint.  out (may be NULL)
+ * receives its record.  RF_ERR_DT_MIN when dt falls below dt_min; on any
+ * error the state is unchanged. */
 rf_status rf_step(rf_ctx *ctx, rf_step_info *out);
 
 typedef struct rf_run_stats {
     long long steps, picard_iters, cg_iters, rejected;
 } rf_run_stats;
 
-/* Advance to t_end (the last step is clipped to t_end).  log: up to log_cap
- * step records, or NULL. */
+/* Advance to t_end by repeated rf_step (Sec. 2.2), the last step clipped to
+ * t_end.  stats (may be NULL): steps, Picard and CG iterations, reruns.
+ * log: up to log_cap step records, or NULL.  Stops at the first failing
+ * step, whose error it returns; the steps before it stay taken. */
 rf_status rf_run(rf_ctx *ctx, double t_end, rf_run_stats *stats, rf_step_info *log, int log_cap);
 
-/* Global water balance since rf_state_set (volumes, m^3).  closure_abs is
+/* Global water balance since rf_state_set (volumes, m^3).  The paper takes
+ * the chord slope of Sec. 2.2 for its mass conservation but defines no
+ * balance; this one is: storage = sum of V theta*(h) over active cells;
+ * inflow_cum / outflow_cum sum dt times the boundary fluxes of each accepted
+ * step's last linear system, split per face by sign.  closure_abs is
  * |sum over steps of [sum_P V C^k (h^{n+1}-h^n) - dt Q_boundary]| of each
  * accepted step's last linear system; closure_rel divides it by storage0 +
  * inflow_cum + outflow_cum.  nonlinear_defect_cum is sum of [storage change -
@@ -229,6 +304,29 @@ rf_status rf_apply(rf_ctx *ctx, const double *d_x, double *d_y);
  * preconditioner; d_x holds x0 on entry and the solution on return.
  * *iters: CG iterations (FP64) or inner FP32 iterations summed (mixed). */
 rf_status rf_solve(rf_ctx *ctx, double *d_x, int *iters);
+
+/* The stencil step of the FP32 inner PCG of the mixed path (Sec. 2.2's PCG
+ * run in FP32, the kernel its iterations launch: TMA-staged planes when nx
+ * is a multiple of 4, plain tiles otherwise) on the last assembled system.
+ * With p = d_z + beta d_pold on active cells (beta == 0: p = d_z, d_pold
+ * unread), it writes d_p = p and d_q = A32 p, where
+ *     (A32 v)_P = cb_P v_P + sum_f w_f (K_P + K_N)/2 (v_P - v_N)
+ * over interior faces to active neighbours, w_f = A_f/d_f, K = FP32 K(h^k),
+ * cb = FP32 (c + Dirichlet half-cell terms); inactive entries are written 0.
+ * d_z, d_pold, d_p, d_q: N floats on the device (d_p and d_q must not alias
+ * the inputs).  *pq (may be NULL): p . q, FP32 sums within blocks, FP64
+ * across them.  Overwrites the context's inner-solve scratch. */
+rf_status rf_apply_inner(rf_ctx *ctx, const float *d_z, const float *d_pold, float beta, float *d_p, float *d_q,
+                         double *pq);
+
+/* Test hook for the bounded device waits (failure detection): polls that a
+ * wait for staged data (the TMA planes of the FP32 stencil) makes before it
+ * gives up; polls = 0 restores the default (about a second of suspending
+ * polls); polls < 0 makes each such wait a single non-blocking test.  A wait
+ * that gives up stops the solve, drains the copies still in flight with the
+ * default limit, and the call in progress returns RF_ERR_DEVICE_TIMEOUT with
+ * the state unchanged and the context usable. */
+rf_status rf_set_wait_limit(rf_ctx *ctx, int polls);
 
 /* Number of CUDA kernel launches this context has executed on the device,
  * counted by the kernels themselves (loop bodies replayed from CUDA graphs
@@ -349,9 +447,9 @@ rf_status rf_ens_model_makespan(const double *wide_s, const double *solo_s, cons
  * fixed at start-up.  rf_pcg_solve_noalloc solves the 7-point system
  *     (A x)_P = diag_P x_P - sum_f T_f x_N = b_P
  * with Jacobi-preconditioned CG and allocates nothing: its work vectors live
- * in one file-scope device array sized for RF_NOALLOC_MAX_CELLS cells (about
- * 3.5 MB), which every GPU that loads the library holds until the process
- * exits.
+ * in one file-scope device array sized for RF_NOALLOC_MAX_CELLS cells
+ * (3 343 104 bytes, about 3.3 MB), which every GPU that loads the library
+ * holds until the process exits.
  *
  *   nx, ny, nz   grid (cells indexed i + nx (j + ny k)); nx*ny*nz must not
  *                exceed RF_NOALLOC_MAX_CELLS, else RF_ERR_ARG
@@ -364,17 +462,22 @@ rf_status rf_ens_model_makespan(const double *wide_s, const double *solo_s, cons
  *   d_x          N doubles: x0 on entry, the solution on return
  *   tol, max_it  stop when ||b - A x||_2 <= tol ||b||_2 (recursive
  *                residual); RF_ERR_CG when max_it iterations do not reach it
- *   cuda_stream  cudaStream_t the work is ordered on (NULL: legacy stream);
- *                the call returns after synchronising it
+ *   cuda_stream  cudaStream_t the work is ordered on (NULL: legacy stream)
  *   iters        CG iterations done (may be NULL)
  * All pointers are device pointers on the current device, borrowed.
+ * Errors: RF_ERR_ARG (bad size or pointer), RF_ERR_NO_DEVICE (the current
+ * device is not sm_103), RF_ERR_CUDA (a launch or copy failed),
+ * RF_ERR_CG (max_it reached or a non-finite solve).
  *
- * The first call on a device looks up the array's device address (a
- * cudaGetSymbolAddress with that device current) and caches it; make that
- * first call before any stream capture.  Every call shares the one array:
- * calls that overlap on the GPU (other streams or host threads) race and
- * must be serialised by the caller.  Each call clears what has to start at
- * zero; nothing else of a previous call's contents is read. */
+ * The first call on a device checks the device and looks up the array's
+ * device address (a cudaGetSymbolAddress with that device current), then
+ * caches both.  Every call reads its iteration count back to the host and
+ * synchronises cuda_stream, so it must not be issued while that stream is
+ * being captured into a CUDA graph.  Every call shares the one array: calls
+ * that overlap on the GPU (other streams or host threads) race and must be
+ * serialised by the caller.  Each call clears what has to start at zero
+ * (solver scalars, reduction ticket, counters); nothing else of a previous
+ * call's contents is read. */
 #define RF_NOALLOC_MAX_CELLS 65536
 rf_status rf_pcg_solve_noalloc(int nx, int ny, int nz, const double *d_diag, const double *d_Tx,
                                const double *d_Ty, const double *d_Tz, const double *d_b, double *d_x,

@@ -22,8 +22,9 @@ Arrays are channels-last: ``x[b, z, y, x, c]``.  A weight is
 parameter vector lists, layer by layer, ``W.ravel()`` then ``b``.
 
 ``bf16=True`` rounds at the points where the BF16 network stores values:
-inputs, weights and hidden activations, and the gradients that enter an
-input-gradient convolution.  Everything else stays FP64.
+inputs, weights and hidden activations, and the output gradients of each
+convolution, which enter both its input-gradient and its weight-gradient
+contraction.  Everything else stays FP64.
 """
 from __future__ import annotations
 
@@ -149,20 +150,20 @@ def loss_and_grad(theta: np.ndarray, x: np.ndarray, target: np.ndarray, mask=Non
     dy = dy[..., None]
     grads = [None] * len(layers)
     a = acts["a"][-1]
-    grads[-1] = conv3d_weight_grad(a, dy)
+    grads[-1] = conv3d_weight_grad(a, rnd(dy))
     da = conv3d_input_grad(rnd(dy), layers[-1][0])
     for blk in reversed(range(N_BLOCKS)):
         a_out, a_in, u = acts["a"][blk + 1], acts["a"][blk], acts["u"][blk]
         W1 = layers[1 + 2 * blk][0]
         W2 = layers[2 + 2 * blk][0]
         g2 = da * (a_out > 0)                       # through the second ReLU
-        grads[2 + 2 * blk] = conv3d_weight_grad(u, g2)
+        grads[2 + 2 * blk] = conv3d_weight_grad(u, rnd(g2))
         du = conv3d_input_grad(rnd(g2), W2)
         g1 = du * (u > 0)
-        grads[1 + 2 * blk] = conv3d_weight_grad(a_in, g1)
+        grads[1 + 2 * blk] = conv3d_weight_grad(a_in, rnd(g1))
         da = conv3d_input_grad(rnd(g1), W1) + g2    # conv branch + identity branch
     g0 = da * (acts["a"][0] > 0)
-    grads[0] = conv3d_weight_grad(acts["x0"], g0)
+    grads[0] = conv3d_weight_grad(acts["x0"], rnd(g0))
     return L, flatten(grads)
 
 

@@ -66,6 +66,7 @@ def _configure(L):
     L.or_set_param.argtypes = [vp, C.c_char_p, C.c_double]
     L.or_set_state.argtypes = [vp, dp, C.c_double]
     L.or_get_state.argtypes = [vp, dp, dp]
+    L.or_set_clock.argtypes = [vp, C.c_double, C.c_double, C.c_int]
     L.or_step.argtypes = [vp, dp]
     L.or_run.argtypes = [vp, C.c_double, dp, C.c_int, ip]
     L.or_mass_balance.argtypes = [vp, dp]
@@ -219,6 +220,10 @@ class Oracle:
     def set_state(self, h, t=0.0):
         h = np.ascontiguousarray(h, dtype=np.float64).ravel()
         self._check(self._L.or_set_state(self.h, _d(h), float(t)), "set_state")
+
+    def set_clock(self, t, dt_nom, easy):
+        """Time and EBATS counters of a saved state (after set_state)."""
+        self._check(self._L.or_set_clock(self.h, float(t), float(dt_nom), int(easy)), "set_clock")
 
     def get_state(self):
         h = np.zeros(self.N)

@@ -345,6 +345,17 @@ int or_set_state(or_problem *P, const double *h, double t)
     return OR_OK;
 }
 
+/* Resume bookkeeping: the time and the EBATS nominal step and easy-step
+ * counter of a state saved elsewhere (the state itself via or_set_state). */
+int or_set_clock(or_problem *P, double t, double dt_nom, int easy)
+{
+    if (!(dt_nom > 0.0) || easy < 0) return OR_ERR_ARG;
+    P->t = t;
+    P->dt_nom = dt_nom;
+    P->easy = easy;
+    return OR_OK;
+}
+
 void or_get_state(const or_problem *P, double *h, double *meta4)
 {
     if (h) memcpy(h, P->h, sizeof(double) * P->N);

@@ -20,27 +20,11 @@ namespace rf {
 //     1 - ys would cancel)
 //   C = (theta_s-theta_r) alpha n m u^(n-1) (1+x)^-(m+1)
 //     = (theta_s-theta_r) alpha n m ys w                         (Eq. 3)
-// For h >= 0 (tie included): theta* = theta_s + S h, K = Ks, C = S, which
-// makes d(theta*)/dh equal to Eq. 3 on both branches.
-// Gardner (Eq. A6, a test model): K = Ks e^(alpha h), theta = theta_r +
-// (theta_s-theta_r) e^(alpha h), in FP64.
-__device__ __forceinline__ void closure(const DevSoil &s, double Ks, double h, const FFTables *__restrict__ tab,
-                                        double &th, double &K, double &C)
+// (h < 0 only; closure() below handles h >= 0 and the other models.)
+__device__ __forceinline__ void closure_vg_df(const DevSoil &s, double Ks, double h, const FFTables *__restrict__ tab,
+                                              double &th, double &K, double &C)
 {
-    if (h >= 0.0) {
-        th = s.theta_s + s.S * h;
-        K = Ks;
-        C = s.S;
-        return;
-    }
     const double dth = s.theta_s - s.theta_r;
-    if (s.model == M_GARDNER) {
-        const double e = exp(s.alpha * h);
-        K = Ks * e;
-        th = s.theta_r + dth * e;
-        C = dth * s.alpha * e;
-        return;
-    }
     const double ud = -s.alpha * h;
     if (ud < 1e-30) {                     // (-alpha h)^n underflows: the wet limit
         th = s.theta_s;
@@ -77,6 +61,88 @@ __device__ __forceinline__ void closure(const DevSoil &s, double Ks, double h, c
     C = s.cfac * ff_to_d(ff_mul(ys, w));
 }
 
+// The same van Genuchten / Mualem closures (h < 0) in FP64 with CUDA's FP64
+// log, exp, log1p and expm1: with u = -alpha h, L = log u, x = exp(n L),
+// l1 = log1p(x):
+//   Se = exp(-m l1), (x/(1+x))^m = exp(m (n L - l1)) = ys, w = 1/(1+x),
+//   K = Ks sqrt(Se) (1 - ys)^2 with 1 - ys = -expm1(m log1p(-w)) when
+//   ys > 1/2, C = (theta_s-theta_r) alpha n m ys w.
+// Beyond x = e^700 (a suction far outside any soil state) theta = theta_r +
+// dtheta x^-m and K = C = 0.
+__device__ __forceinline__ void closure_vg_fp64(const DevSoil &s, double Ks, double h, double &th, double &K,
+                                                double &C)
+{
+    const double dth = s.theta_s - s.theta_r;
+    const double u = -s.alpha * h;
+    const double nL = s.n * log(u);
+    if (nL > 700.0) {
+        th = s.theta_r + dth * exp(-s.m * nL);
+        K = 0.0;
+        C = 0.0;
+        return;
+    }
+    const double x = exp(nL);
+    const double l1 = log1p(x);
+    const double se = exp(-s.m * l1);
+    const double ys = exp(s.m * (nL - l1));
+    const double w = 1.0 / (1.0 + x);
+    const double omy = ys <= 0.5 ? 1.0 - ys : -expm1(s.m * log1p(-w));
+    th = s.theta_r + dth * se;
+    K = Ks * sqrt(se) * (omy * omy);
+    C = s.cfac * (ys * w);
+}
+
+// Brooks and Corey's closures (the alternative Sec. 1 names), FP64: air-entry
+// head h_b = -1/alpha, pore-size index lambda = n; Se = (h_b / h)^lambda below
+// h_b and 1 above; theta = theta_r + (theta_s - theta_r) Se, C = dtheta/dh =
+// -lambda (theta_s - theta_r) Se / h, K = Ks Se^((2 + 3 lambda)/lambda).
+__device__ __forceinline__ void closure_bc(const DevSoil &s, double Ks, double h, double &th, double &K, double &C)
+{
+    const double hb = -1.0 / s.alpha, lam = s.n;
+    if (h >= hb) {
+        th = s.theta_s;
+        K = Ks;
+        C = 0.0;
+        return;
+    }
+    const double ls = lam * log(hb / h);          // log Se
+    const double se = exp(ls);
+    const double dth = s.theta_s - s.theta_r;
+    th = s.theta_r + dth * se;
+    C = -lam * dth * se / h;
+    K = Ks * exp(ls * (2.0 + 3.0 * lam) / lam);
+}
+
+// Closures of one cell at head h: theta*, K, C.  For h >= 0 (tie included)
+// theta* = theta_s + S h, K = Ks, C = S, which makes d(theta*)/dh equal to
+// Eq. 3 on both branches.  fp64 selects FP64 van Genuchten arithmetic
+// instead of double-float.  Gardner (Eq. A6, a test model): K = Ks e^(alpha
+// h), theta = theta_r + (theta_s-theta_r) e^(alpha h), in FP64.
+__device__ __forceinline__ void closure(const DevSoil &s, double Ks, double h, const FFTables *__restrict__ tab,
+                                        bool fp64, double &th, double &K, double &C)
+{
+    if (h >= 0.0) {
+        th = s.theta_s + s.S * h;
+        K = Ks;
+        C = s.S;
+        return;
+    }
+    if (s.model == M_GARDNER) {
+        const double dth = s.theta_s - s.theta_r;
+        const double e = exp(s.alpha * h);
+        K = Ks * e;
+        th = s.theta_r + dth * e;
+        C = dth * s.alpha * e;
+        return;
+    }
+    if (s.model == M_BROOKS_COREY) {
+        closure_bc(s, Ks, h, th, K, C);
+        return;
+    }
+    if (fp64) closure_vg_fp64(s, Ks, h, th, K, C);
+    else closure_vg_df(s, Ks, h, tab, th, K, C);
+}
+
 // Neighbour across face f of cell p = (i,j,k); false when outside the grid.
 __device__ __forceinline__ bool neighbour(const Grid &g, long long p, int i, int j, int k, int f, long long &q)
 {
@@ -110,9 +176,13 @@ __device__ __forceinline__ double apply64(const Grid &g, long long p, const doub
 
 // One cell of the Picard system (Sec. 2.2; see k_assemble):
 //   c = V C^k / dt (chord slope of theta*, or C(h^k) when |h^k - h^n| <= eps),
-//   interior faces T_f = (K_P + K_N)/2 A_f/d_f with explicit gravity,
+//   interior faces T_f = Kbar_f A_f/d_f with Kbar_f = (K_P + K_N)/2 (or the
+//   harmonic mean 2 K_P K_N / (K_P + K_N)) and explicit gravity
+//   gf_f Kbar_f A_f, gf_f the elevation gradient along the face's outward
+//   normal (+1 top, -1 bottom, 0 lateral on a z-up grid),
 //   boundary terms of the face classes flagged in fl.
 // With RESID, sT = sum over interior faces of T_f h^k_N (for b - A h^k).
+// thp: theta*(h^{n-1}), read only by the BDF2 storage.
 struct CellSystem {
     double c, rhs, diag, cb, sT, KP;
     double s0;        // storage part of rhs
@@ -126,11 +196,18 @@ __device__ __forceinline__ void assemble_cell(const Grid &g, const DevSoil *__re
                                               const double *__restrict__ hk, const double *__restrict__ hn,
                                               const double *__restrict__ thk, const double *__restrict__ thn,
                                               const double *__restrict__ K, const double *__restrict__ Can,
-                                              double eps, double V_dt, CellSystem &out)
+                                              const double *__restrict__ thp, double eps, double V_dt,
+                                              CellSystem &out)
 {
     const double hkP = hk[p], hnP = hn[p], KP = K[p];
     double C, s0;
-    if (sp.modified) {
+    if (sp.bdf2) {
+        // variable-step BDF2 (the multistep alternative Sec. 2.2 names) in the
+        // mixed form V/dt [a0 theta^{n+1} - a1 theta^n + a2 theta^{n-1}],
+        // theta^{n+1} linearised about h^k as in the modified Picard form
+        C = sp.a0 * Can[p];
+        s0 = V_dt * (C * hkP - (sp.a0 * thk[p] - sp.a1 * thn[p] + sp.a2 * thp[p]));
+    } else if (sp.modified) {
         // modified Picard (Sec. 2.2, mass-conservative variant): theta*(h^{k+1})
         // ~ theta*(h^k) + C(h^k) (h^{k+1} - h^k), so the storage term is
         // c (h^{k+1} - h^k) + V (theta*(h^k) - theta*(h^n)) / dt
@@ -154,16 +231,17 @@ __device__ __forceinline__ void assemble_cell(const Grid &g, const DevSoil *__re
         if (neighbour(g, p, i, j, k, f, q)) {
             const double KN = K[q];
             if (__double_as_longlong(KN) >= 0) {          // active neighbour (K >= 0; inactive K = -1)
-                const double Ks2 = KP + KN;
-                const double T = Ks2 * g.hw[f];            // (K_P + K_N)/2 A/d
+                double Ks2 = KP + KN;                      // 2 Kbar
+                if (g.harmonic) Ks2 = Ks2 > 0.0 ? 4.0 * KP * KN / Ks2 : 0.0;
+                const double T = Ks2 * g.hw[f];            // Kbar A/d
                 diag += T;
-                if (f >= F_ZMIN) rhs = fma(Ks2, g.hg[f], rhs);   // explicit gravity, +-Kbar A_z
+                if (f >= F_ZMIN || g.tilted) rhs = fma(Ks2, g.hg[f], rhs);   // explicit gravity, gf Kbar A
                 if (f & 1) Tup[f >> 1] = T;
                 if (RESID) sT = fma(T, hk[q], sT);
                 continue;
             }
         }
-        const double gs = (f == F_ZMIN) ? -1.0 : (f == F_ZMAX ? 1.0 : 0.0);
+        const double gs = g.gf[f];
         if (!(fl & (1u << f))) continue;    // closed face (lateral face on an inactive cell)
         int type = sp.bc_type[f];
         double hD = 0.0;
@@ -176,7 +254,7 @@ __device__ __forceinline__ void assemble_cell(const Grid &g, const DevSoil *__re
         if (type == BC_DIRICHLET) {
             const DevSoil s = soils[zone[p]];
             double thD, KD, CD;
-            closure(s, Ks[p], hD, g.tab, thD, KD, CD);
+            closure(s, Ks[p], hD, g.tab, g.closure64, thD, KD, CD);
             const double T = KD * g.wb[f];
             diag += T;
             cb += T;
@@ -184,7 +262,7 @@ __device__ __forceinline__ void assemble_cell(const Grid &g, const DevSoil *__re
         } else if (type == BC_FLUX) {
             rhs += sp.bc_val[f] * g.A[f];
         } else if (type == BC_FREE_DRAINAGE) {
-            rhs += -KP * g.A[f];
+            rhs += gs * KP * g.A[f];       // unit gradient: gravity outflow K(h^k) A (gs = -1 at a z-up bottom)
         }
     }
     out.c = c;
@@ -201,8 +279,8 @@ __device__ __forceinline__ void assemble_cell(const Grid &g, const DevSoil *__re
 
 // Boundary inflow (fin >= 0) and outflow (fout >= 0) of one cell's boundary
 // faces in the linear system solved for x (the water balance of Sec. 2.2's
-// chord-slope scheme): Dirichlet T_D (h_D - x) +- K(h_D) A_z, imposed flux,
-// free drainage -K(h^k) A_z, seepage as Dirichlet 0 while h^n >= 0.
+// chord-slope scheme): Dirichlet T_D (h_D - x) + gf K(h_D) A, imposed flux,
+// free drainage gf K(h^k) A, seepage as Dirichlet 0 while h^n >= 0.
 __device__ __forceinline__ void boundary_fluxes(const Grid &g, const DevSoil &s, double Ksp, uint8_t fl,
                                                 const StepParams &sp, double xp, double hnP, double Kold,
                                                 double &fin, double &fout)
@@ -212,7 +290,7 @@ __device__ __forceinline__ void boundary_fluxes(const Grid &g, const DevSoil &s,
 #pragma unroll
     for (int f = 0; f < 6; f++) {
         if (!(fl & (1u << f))) continue;
-        const double gs = (f == F_ZMIN) ? -1.0 : (f == F_ZMAX ? 1.0 : 0.0);
+        const double gs = g.gf[f];
         int type = sp.bc_type[f];
         double hD = 0.0, flux = 0.0;
         if (type == BC_SEEPAGE) {
@@ -223,13 +301,13 @@ __device__ __forceinline__ void boundary_fluxes(const Grid &g, const DevSoil &s,
         }
         if (type == BC_DIRICHLET) {
             double thD, KD, CD;
-            closure(s, Ksp, hD, g.tab, thD, KD, CD);
+            closure(s, Ksp, hD, g.tab, g.closure64, thD, KD, CD);
             const double T = KD * g.wb[f];
             flux = T * hD + gs * KD * g.A[f] - T * xp;
         } else if (type == BC_FLUX) {
             flux = sp.bc_val[f] * g.A[f];
         } else if (type == BC_FREE_DRAINAGE) {
-            flux = -Kold * g.A[f];
+            flux = gs * Kold * g.A[f];
         }
         if (flux > 0.0) fin += flux;
         else fout -= flux;

@@ -36,7 +36,7 @@ __device__ __forceinline__ void closure_cells(const Grid &g, const DevSoil *__re
         }
         const DevSoil s = soils[zone[p]];
         double th, k, c;
-        closure(s, Ks[p], hp, g.tab, th, k, c);
+        closure(s, Ks[p], hp, g.tab, g.closure64, th, k, c);
         theta[p] = th;
         K[p] = k;
         Can[p] = c;
@@ -119,7 +119,8 @@ k_assemble(Grid g, const DevSoil *__restrict__ soils, const uint8_t *__restrict_
            double *__restrict__ c_out, double *__restrict__ b, double *__restrict__ Tx, double *__restrict__ Ty,
            double *__restrict__ Tz, double *__restrict__ diag_out, double *__restrict__ dinv,
            float *__restrict__ K32, float *__restrict__ cb32, float *__restrict__ dinv32, const int *skip,
-           SolveStart st, double *partials, unsigned int *ticket, double *__restrict__ s0_out)
+           SolveStart st, double *partials, unsigned int *ticket, double *__restrict__ s0_out,
+           const double *__restrict__ thp)
 {
     count_launch(g, KK_ASSEMBLE);
     if (skip && *skip) {
@@ -155,8 +156,8 @@ k_assemble(Grid g, const DevSoil *__restrict__ soils, const uint8_t *__restrict_
         cell_ijk(g, p, i, j, k);
         const double hkP = hk[p];
         CellSystem cs;
-        assemble_cell<MODE != ASM_ONLY>(g, soils, zone, Ks, fl, *spp, p, i, j, k, hk, hn, thk, thn, K, Can, eps, V_dt,
-                                        cs);
+        assemble_cell<MODE != ASM_ONLY>(g, soils, zone, Ks, fl, *spp, p, i, j, k, hk, hn, thk, thn, K, Can, thp, eps,
+                                        V_dt, cs);
         const double c = cs.c, rhs = cs.rhs, diag = cs.diag, cb = cs.cb, sT = cs.sT, KP = cs.KP;
         const double *Tup = cs.Tup;
         c_out[p] = c;
@@ -329,22 +330,23 @@ void launch_assemble(cudaStream_t s, int nblk, const Grid &g, const DevSoil *soi
                      const double *hn, const double *theta_k, const double *theta_n, const double *K,
                      const double *Can, double *c, double *b, double *Tx, double *Ty, double *Tz,
                      double *diag, double *dinv, float *K32, float *cb32, float *dinv32, const int *skip,
-                     int mode, const SolveStart *start, double *partials, unsigned int *ticket, double *s0)
+                     int mode, const SolveStart *start, double *partials, unsigned int *ticket, double *s0,
+                     const double *theta_p)
 {
     SolveStart st{};
     if (start) st = *start;
     if (mode == ASM_CG64)
         k_assemble<ASM_CG64><<<nblk, RED_THREADS, 0, s>>>(g, soils, zone, Ks, flags, sp, hk, hn, theta_k, theta_n, K,
                                                           Can, c, b, Tx, Ty, Tz, diag, dinv, K32, cb32, dinv32, skip,
-                                                          st, partials, ticket, s0);
+                                                          st, partials, ticket, s0, theta_p);
     else if (mode == ASM_MIXED)
         k_assemble<ASM_MIXED><<<nblk, RED_THREADS, 0, s>>>(g, soils, zone, Ks, flags, sp, hk, hn, theta_k, theta_n,
                                                            K, Can, c, b, Tx, Ty, Tz, diag, dinv, K32, cb32, dinv32,
-                                                           skip, st, partials, ticket, s0);
+                                                           skip, st, partials, ticket, s0, theta_p);
     else
         k_assemble<ASM_ONLY><<<nblk, RED_THREADS, 0, s>>>(g, soils, zone, Ks, flags, sp, hk, hn, theta_k, theta_n, K,
                                                           Can, c, b, Tx, Ty, Tz, diag, dinv, K32, cb32, dinv32, skip,
-                                                          st, partials, ticket, s0);
+                                                          st, partials, ticket, s0, theta_p);
 }
 
 void launch_accept(cudaStream_t s, int nblk, const Grid &g, const double *x_final, double *h,

@@ -365,7 +365,7 @@ k_ensemble(EnsDesc *__restrict__ D, int n_inst, EnsBuffers B, EnsParams P, const
                     else v[1] = 1.0;
                 }
                 double th, k, c;
-                closure(*soil, Ks[p], hp, g.tab, th, k, c);
+                closure(*soil, Ks[p], hp, g.tab, g.closure64, th, k, c);
                 thx[p] = th;
                 Kx[p] = k;
                 Can[p] = c;
@@ -414,7 +414,7 @@ k_ensemble(EnsDesc *__restrict__ D, int n_inst, EnsBuffers B, EnsParams P, const
                         cell_ijk(g, p, i, j, k);
                         CellSystem cs;
                         assemble_cell<true>(g, soil, zn, Ks, fl[p], sp, p, i, j, k, hk, hn, TH[tn ^ 1], TH[tn],
-                                            KB[kin], Can, P.eps_chord, V_dt, cs);
+                                            KB[kin], Can, nullptr, P.eps_chord, V_dt, cs);
                         const double di = rcp64(cs.diag);
                         cc[p] = cs.c;
                         bb[p] = cs.rhs;

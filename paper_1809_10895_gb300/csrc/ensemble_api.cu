@@ -187,6 +187,10 @@ rf_status rf_ens_create(const rf_ens_instance *inst, int n, const rf_solver_para
         return efail(RF_ERR_ARG, "rf_ens_create: the ensemble runs the classical (chord) Picard iteration only");
     if (prm.precond != RF_PRECOND_JACOBI)
         return efail(RF_ERR_ARG, "rf_ens_create: the ensemble's PCG is Jacobi-preconditioned only");
+    if (prm.face_mean != RF_FACE_ARITHMETIC || prm.time_scheme != RF_TIME_BACKWARD_EULER ||
+        prm.time_control != RF_TIME_EBATS || prm.grav[0] != 0.0 || prm.grav[1] != 0.0 || prm.grav[2] != 1.0)
+        return efail(RF_ERR_ARG, "rf_ens_create: the ensemble runs the default scheme (arithmetic face mean, "
+                                 "backward Euler under EBATS, z-up gravity) only");
     long long total = 0;
     for (int i = 0; i < n; i++) {
         const rf_ens_instance &a = inst[i];
@@ -270,8 +274,12 @@ rf_status rf_ens_create(const rf_ens_instance *inst, int n, const rf_solver_para
             g.w[f] = A[f] / dd[f];
             g.wb[f] = A[f] / (0.5 * dd[f]);
             g.hw[f] = 0.5 * (A[f] / dd[f]);
-            g.hg[f] = f == F_ZMIN ? -0.5 * A[f] : (f == F_ZMAX ? 0.5 * A[f] : 0.0);
+            g.gf[f] = f == F_ZMIN ? -1.0 : (f == F_ZMAX ? 1.0 : 0.0);
+            g.hg[f] = 0.5 * A[f] * g.gf[f];
         }
+        // closures in FP64 on the plain path, double-float inside the mixed one (AUTO)
+        g.closure64 = (prm.closure_arith == RF_CLOSURE_FP64 ||
+                       (prm.closure_arith == RF_CLOSURE_AUTO && prm.precision == RF_PREC_FP64)) ? 1 : 0;
         for (int ax = 0; ax < 3; ax++) g.w32[ax] = (float)(A[2 * ax] / dd[2 * ax]);
         g.fx = make_fastdiv((unsigned int)a.nx);
         g.fxy = make_fastdiv((unsigned int)g.sxy);

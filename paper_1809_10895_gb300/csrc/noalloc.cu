@@ -11,10 +11,12 @@
 // solution vector.
 //
 // The array is part of the library image: every GPU that loads the library
-// holds it until the process exits.  All calls share it, so calls whose work
-// overlaps on the GPU (different streams, or different host threads) race;
-// callers must serialise them.  Each call re-initialises what has to start at
-// zero; the rest keeps the previous call's contents, which no call reads.
+// holds it (3 343 104 bytes) until the process exits.  All calls share it, so
+// calls whose work overlaps on the GPU (different streams, or different host
+// threads) race; callers must serialise them.  Each call clears the solver
+// scalars, the reduction ticket and the launch counters before its first
+// kernel and overwrites every vector entry it later reads, so nothing of a
+// previous call's contents is read.
 #include <algorithm>
 #include <mutex>
 
@@ -42,6 +44,7 @@ constexpr size_t OFF_SCAL = OFF_PART + (size_t)8 * NOALLOC_MAX_BLOCKS * sizeof(d
 constexpr size_t OFF_TICKET = OFF_SCAL + 256;
 constexpr size_t OFF_CTR = OFF_TICKET + 256;
 constexpr size_t SCRATCH_BYTES = OFF_CTR + (((size_t)2 * KK_COUNT * sizeof(unsigned long long) + 255) & ~size_t(255));
+static_assert(SCRATCH_BYTES == 3343104, "the scratch size stated in rf.h");
 
 static __device__ __align__(256) unsigned char g_noalloc_scratch[SCRATCH_BYTES];
 
@@ -51,6 +54,7 @@ static __device__ __align__(256) unsigned char g_noalloc_scratch[SCRATCH_BYTES];
 std::mutex g_mutex;
 constexpr int MAX_DEVICES = 64;
 unsigned char *g_addr[MAX_DEVICES] = {nullptr};
+int g_sms[MAX_DEVICES] = {0};
 
 // dinv = 1/diag and the active flag (diag > 0) of every cell; clears the
 // reduction ticket and the launch counters.
@@ -90,20 +94,33 @@ extern "C" rf_status rf_pcg_solve_noalloc(int nx, int ny, int nz, const double *
     if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= MAX_DEVICES)
         return noalloc_fail(RF_ERR_NO_DEVICE, "rf_pcg_solve_noalloc: no usable CUDA device");
     unsigned char *base = nullptr;
+    int sms = 0;
     {
         std::lock_guard<std::mutex> lock(g_mutex);
         if (!g_addr[dev]) {
+            // the kernels are built for sm_103a only: refuse any other device
+            // before the first launch (as rf_mesh_create does)
+            int major = 0, minor = 0, nsm = 0;
+            if (cudaDeviceGetAttribute(&major, cudaDevAttrComputeCapabilityMajor, dev) != cudaSuccess ||
+                cudaDeviceGetAttribute(&minor, cudaDevAttrComputeCapabilityMinor, dev) != cudaSuccess ||
+                cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) {
+                cudaGetLastError();
+                return noalloc_fail(RF_ERR_CUDA, "rf_pcg_solve_noalloc: device query failed");
+            }
+            if (major != 10 || minor != 3)
+                return noalloc_fail(RF_ERR_NO_DEVICE, "rf_pcg_solve_noalloc: the device is not sm_103 (GB300)");
             void *ptr = nullptr;
             const cudaError_t e = cudaGetSymbolAddress(&ptr, g_noalloc_scratch);
-            if (e != cudaSuccess || !ptr)
+            if (e != cudaSuccess || !ptr) {
+                cudaGetLastError();
                 return noalloc_fail(RF_ERR_CUDA, "rf_pcg_solve_noalloc: cudaGetSymbolAddress failed");
+            }
+            g_sms[dev] = nsm;
             g_addr[dev] = static_cast<unsigned char *>(ptr);
         }
         base = g_addr[dev];
+        sms = g_sms[dev];
     }
-    int sms = 0;
-    if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
-        return noalloc_fail(RF_ERR_CUDA, "rf_pcg_solve_noalloc: device query failed");
     cudaStream_t s = static_cast<cudaStream_t>(cuda_stream);
 
     double *r = reinterpret_cast<double *>(base + OFF_R);
@@ -130,10 +147,17 @@ extern "C" rf_status rf_pcg_solve_noalloc(int nx, int ny, int nz, const double *
     const int nblk = (int)std::max(1LL, std::min(want, std::min((long long)sms * 8, (long long)NOALLOC_MAX_BLOCKS)));
     const CondSet none{0, 0};
 
+    // the scalars start from zero (done = 0) on every call; x0 is copied
+    // into q (free until the first stencil product writes it) so that the
+    // start kernel never reads the vector it writes
+    if (cudaMemsetAsync(sc, 0, sizeof(CgScal), s) != cudaSuccess ||
+        cudaMemcpyAsync(q, d_x, sizeof(double) * N, cudaMemcpyDeviceToDevice, s) != cudaSuccess)
+        return noalloc_fail(RF_ERR_CUDA, "rf_pcg_solve_noalloc: CUDA error before the solve");
     k_noalloc_setup<<<nblk, RED_THREADS, 0, s>>>(N, d_diag, dinv, flags, ticket, ctr);
-    // x0 is the caller's d_x; the solve writes the solution back into d_x
-    launch_cg64_init(s, nblk, g, flags, d_x, d_x, d_b, d_Tx, d_Ty, d_Tz, d_diag, dinv, r, z, tol, max_it, partials,
+    launch_cg64_init(s, nblk, g, flags, q, d_x, d_b, d_Tx, d_Ty, d_Tz, d_diag, dinv, r, z, tol, max_it, partials,
                      ticket, sc, nullptr, none);
+    if (cudaGetLastError() != cudaSuccess)
+        return noalloc_fail(RF_ERR_CUDA, "rf_pcg_solve_noalloc: kernel launch failed");
     CgScal host{};
     long long launched = 0;
     int chunk = 2;
@@ -143,6 +167,8 @@ extern "C" rf_status rf_pcg_solve_noalloc(int nx, int ny, int nz, const double *
             launch_cg64_spmv(s, nblk, g, flags, z, pin, pout, q, d_Tx, d_Ty, d_Tz, d_diag, partials, ticket, sc);
             launch_cg64_update(s, nblk, g, d_x, r, z, pout, q, dinv, partials, ticket, sc, none);
         }
+        if (cudaGetLastError() != cudaSuccess)
+            return noalloc_fail(RF_ERR_CUDA, "rf_pcg_solve_noalloc: kernel launch failed");
         if (cudaMemcpyAsync(&host, sc, sizeof(CgScal), cudaMemcpyDeviceToHost, s) != cudaSuccess ||
             cudaStreamSynchronize(s) != cudaSuccess)
             return noalloc_fail(RF_ERR_CUDA, "rf_pcg_solve_noalloc: CUDA error during the solve");

@@ -624,10 +624,13 @@ k_cg32_spmv_tma(Grid g, Tiles tw, const __grid_constant__ TmaMaps32 maps, int pi
                 tma_load_3d(sbuf[st][3], &maps.cb, &bar[st], x, y, kk);
             }
         };
-        // warp 0: poll stage st (bounded); false when the wait ran out
+        // warp 0: poll stage st (bounded); false when the wait ran out.  The
+        // grid's wait_tries (a test limit) replaces the default poll count;
+        // negative: a single non-blocking test
         auto poll = [&](int st) -> bool {
             if (!poller || !(pending & (1u << st))) return true;
-            return mbar_wait_bounded(&bar[st], (phase >> st) & 1u, TMA_WAIT_TRIES);
+            if (g.wait_tries < 0) return mbar_test_wait(&bar[st], (phase >> st) & 1u);
+            return mbar_wait_bounded(&bar[st], (phase >> st) & 1u, g.wait_tries > 0 ? g.wait_tries : TMA_WAIT_TRIES);
         };
         // after the barrier that follows a successful poll: confirm the phase
         // (completes at once) and form p for the own cells and halo cell of plane kk

@@ -107,6 +107,14 @@ struct rf_ctx {
     nn::WsScales ws_sc{};
     long long ws_guesses = 0, ws_fallbacks = 0;
 
+    // BDF2: theta*(h^{n-1}) and the previous step size (0: no history)
+    double *theta_p = nullptr;
+    double dt_prev = 0.0;
+    // Richardson control: saved state and the full-step result (allocated on first use)
+    double *rh0 = nullptr, *rthn0 = nullptr, *rhf = nullptr;
+    double err_last = 0.0, err_max = 0.0;
+    int wait_polls = 0;          // test limit of the bounded device waits (0: default)
+
     bool closure_at_h = false;   // K[0], Can hold the closures at h (the accepted state)
     bool soils_set = false, has_state = false;
     double t = 0.0, dt_nom = 1.0;
@@ -151,7 +159,38 @@ rf_status check_params(const rf_solver_params *p)
         return fail(RF_ERR_ARG, "the multigrid preconditioner serves the FP32 inner solve: use RF_PREC_MIXED");
     if (p->precond == RF_PRECOND_DIC && p->precision != RF_PREC_MIXED)
         return fail(RF_ERR_ARG, "the DIC preconditioner serves the FP32 inner solve: use RF_PREC_MIXED");
+    if (p->closure_arith < RF_CLOSURE_AUTO || p->closure_arith > RF_CLOSURE_DOUBLE_FLOAT)
+        return fail(RF_ERR_ARG, "unknown closure arithmetic");
+    if (p->face_mean != RF_FACE_ARITHMETIC && p->face_mean != RF_FACE_HARMONIC)
+        return fail(RF_ERR_ARG, "unknown interface mean");
+    if (p->face_mean == RF_FACE_HARMONIC && p->precision != RF_PREC_FP64)
+        return fail(RF_ERR_ARG, "the harmonic interface mean runs on the FP64 path (RF_PREC_FP64)");
+    if (p->time_scheme != RF_TIME_BACKWARD_EULER && p->time_scheme != RF_TIME_BDF2)
+        return fail(RF_ERR_ARG, "unknown time scheme");
+    if (p->time_control != RF_TIME_EBATS && p->time_control != RF_TIME_RICHARDSON)
+        return fail(RF_ERR_ARG, "unknown time control");
+    if (p->time_scheme == RF_TIME_BDF2 && (p->picard_form != RF_PICARD_MODIFIED || p->time_control != RF_TIME_EBATS))
+        return fail(RF_ERR_ARG, "BDF2 runs in the modified Picard form under EBATS");
+    if (!(p->tol_time > 0) || !std::isfinite(p->tol_time))
+        return fail(RF_ERR_ARG, "tol_time (the Richardson control's bound) must be finite and > 0");
+    if (!std::isfinite(p->grav[0]) || !std::isfinite(p->grav[1]) || !std::isfinite(p->grav[2]))
+        return fail(RF_ERR_ARG, "non-finite gravity direction");
     return RF_OK;
+}
+
+// Grid fields that follow the solver parameters: gravity factors per face,
+// the interface mean and the closure arithmetic.
+void apply_grid_params(Grid &g, const rf_solver_params &p)
+{
+    const double gv[6] = {-p.grav[0], p.grav[0], -p.grav[1], p.grav[1], -p.grav[2], p.grav[2]};
+    for (int f = 0; f < 6; f++) {
+        g.gf[f] = gv[f];
+        g.hg[f] = 0.5 * g.A[f] * gv[f];
+    }
+    g.tilted = (p.grav[0] != 0.0 || p.grav[1] != 0.0) ? 1 : 0;
+    g.harmonic = p.face_mean == RF_FACE_HARMONIC ? 1 : 0;
+    g.closure64 = (p.closure_arith == RF_CLOSURE_FP64 ||
+                   (p.closure_arith == RF_CLOSURE_AUTO && p.precision == RF_PREC_FP64)) ? 1 : 0;
 }
 
 double series_at(const BcSeries &b, double t)
@@ -175,8 +214,13 @@ rf_status sync(rf_ctx *c)
     CUDA_TRY(cudaGetLastError());
     if (c->dev_fault) CUDA_TRY(cudaMemcpyAsync(c->fault_h, c->dev_fault, sizeof(int), cudaMemcpyDeviceToHost, c->stream));
     CUDA_TRY(cudaStreamSynchronize(c->stream));
-    if (c->dev_fault && *c->fault_h)
+    if (c->dev_fault && *c->fault_h) {
+        // reported once: the flag is cleared so that the context stays usable
+        *c->fault_h = 0;
+        CUDA_TRY(cudaMemsetAsync(c->dev_fault, 0, sizeof(int), c->stream));
+        CUDA_TRY(cudaStreamSynchronize(c->stream));
         return fail(RF_ERR_DEVICE_TIMEOUT, "a device wait for staged data ran out (the solve was stopped)");
+    }
     return RF_OK;
 }
 
@@ -190,6 +234,17 @@ void fill_step_params(rf_ctx *c, double dt)
     s.t = c->t;
     s.eps_chord = c->prm.eps_chord;
     s.modified = c->prm.picard_form == RF_PICARD_MODIFIED ? 1 : 0;
+    s.bdf2 = 0;
+    s.a0 = 1.0;
+    s.a1 = 1.0;
+    s.a2 = 0.0;
+    if (c->prm.time_scheme == RF_TIME_BDF2 && c->dt_prev > 0.0) {
+        const double w = dt / c->dt_prev;
+        s.bdf2 = 1;
+        s.a0 = (1.0 + 2.0 * w) / (1.0 + w);
+        s.a1 = 1.0 + w;
+        s.a2 = w * w / (1.0 + w);
+    }
     for (int f = 0; f < 6; f++) {
         s.bc_type[f] = c->bc[f].type;
         s.bc_val[f] = c->bc[f].v.empty() ? 0.0 : series_at(c->bc[f], c->t);
@@ -208,7 +263,7 @@ void run_assemble(rf_ctx *c, const double *hk, const double *hn, const double *t
 {
     launch_assemble(c->stream, c->nblk, c->g, c->soils, c->zone, c->Ks, c->flags, c->sp, hk, hn, thk, thn,
                     c->K[0], c->Can, c->c, c->b, c->Tx, c->Ty, c->Tz, c->diag, c->dinv, c->K32, c->cb32,
-                    c->dinv32, nullptr, ASM_ONLY, nullptr, nullptr, nullptr, s0_of(c));
+                    c->dinv32, nullptr, ASM_ONLY, nullptr, nullptr, nullptr, s0_of(c), c->theta_p);
 }
 
 // ---------------------------------------------------------------------------
@@ -485,7 +540,7 @@ rf_status build_picard_graph(rf_ctx *c)
         launch_assemble(s, nb, g, c->soils, c->zone, c->Ks, c->flags, c->sp, hk, c->h, c->theta_k, c->theta_n, Kin,
                         c->Can, c->c, c->b, c->Tx, c->Ty, c->Tz, c->diag, c->dinv, c->K32, c->cb32, c->dinv32, skip,
                         c->prm.precision == RF_PREC_FP64 ? ASM_CG64 : ASM_MIXED, &st, c->partials, c->ticket,
-                        s0_of(c));
+                        s0_of(c), c->theta_p);
         RF_TRY(cap_end(c, deps));
         RF_TRY(capture_solve(c, G, body, deps, hk, x, skip, true, &st, deps));
         RF_TRY(cap_begin(c, body, deps));
@@ -582,6 +637,7 @@ rf_status attempt(rf_ctx *c, double dt, Attempt &A, bool guess)
         }
     }
     CUDA_TRY(cudaGraphLaunch(c->picard_exec, c->stream));
+    c->closure_at_h = false;     // the attempt overwrites K[0] and C; an accepted step sets it again
     CUDA_TRY(cudaMemcpyAsync(c->ctl_h, c->ctl, sizeof(PicardCtl), cudaMemcpyDeviceToHost, c->stream));
     CUDA_TRY(cudaMemcpyAsync(c->res_h, c->res, sizeof(StepResults), cudaMemcpyDeviceToHost, c->stream));
     RF_TRY(sync(c));
@@ -593,10 +649,12 @@ rf_status attempt(rf_ctx *c, double dt, Attempt &A, bool guess)
         A.mb = *c->res_h;
         // the last iterate and its closures: H[it & 1], K[it & 1]
         const int f = ctl.it & 1;
+        if (c->prm.time_scheme == RF_TIME_BDF2)    // theta*(h^{n-1}) for the next step
+            CUDA_TRY(cudaMemcpyAsync(c->theta_p, c->theta_n, sizeof(double) * c->g.N, cudaMemcpyDeviceToDevice,
+                                     c->stream));
         launch_accept(c->stream, c->nblk, c->g, f ? c->x : c->hk, c->h, c->theta_k, c->theta_n, c->K[1], c->K[0], f);
     } else {
         A.status = ctl.fail ? RF_ERR_CG : RF_ERR_PICARD;
-        c->closure_at_h = false;
         if (guess) c->ws_fallbacks++;
     }
     return RF_OK;
@@ -631,6 +689,7 @@ rf_status do_step(rf_ctx *c, double t_stop, rf_step_info *info)
         cg_total += A.cg;
         if (A.converged) {
             c->closure_at_h = true;
+            if (c->prm.time_scheme == RF_TIME_BDF2) c->dt_prev = dt;
             double tn = c->t + dt;
             if (std::fabs(tn - bp) <= t_tol(tn)) tn = bp;
             if (std::fabs(tn - t_stop) <= t_tol(tn)) tn = t_stop;
@@ -662,6 +721,139 @@ rf_status do_step(rf_ctx *c, double t_stop, rf_step_info *info)
                                            std::to_string(c->t));
         }
     }
+}
+
+// Richardson step doubling (the alternative to EBATS that Sec. 2.2 names for
+// prescribing the temporal error).  Each step runs once with dt and twice
+// with dt/2 from the same state; the local error estimate is max over active
+// cells |h(2 x dt/2) - h(dt)|; the step is accepted, with the two-half-step
+// result, when the estimate is within tol_time.  The next dt is
+// dt 0.9 sqrt(tol_time / err) clamped to [0.2, 2] dt and to dt_max either way;
+// a Picard failure in any of the three solves divides dt by f_shrink as in
+// EBATS.  attempt() accepts a converged solve into h, theta_n and K[0], so the
+// state at the step start is saved and put back around each solve.
+rf_status ensure_richardson(rf_ctx *c)
+{
+    if (c->rh0) return RF_OK;
+    if (!alloc_n(c, c->rh0, c->g.N) || !alloc_n(c, c->rthn0, c->g.N) || !alloc_n(c, c->rhf, c->g.N))
+        return fail(RF_ERR_NOMEM, "Richardson control: device allocation failed");
+    return RF_OK;
+}
+
+rf_status richardson_restore(rf_ctx *c)
+{
+    const size_t nb = sizeof(double) * c->g.N;
+    CUDA_TRY(cudaMemcpyAsync(c->h, c->rh0, nb, cudaMemcpyDeviceToDevice, c->stream));
+    CUDA_TRY(cudaMemcpyAsync(c->theta_n, c->rthn0, nb, cudaMemcpyDeviceToDevice, c->stream));
+    c->closure_at_h = false;
+    return RF_OK;
+}
+
+rf_status do_step_richardson(rf_ctx *c, double t_stop, rf_step_info *info)
+{
+    if (!c->soils_set || !c->has_state) return fail(RF_ERR_STATE, "set soils and state before stepping");
+    RF_TRY(ensure_richardson(c));
+    const double dt_nom0 = c->dt_nom, t0 = c->t;
+    const size_t nb = sizeof(double) * c->g.N;
+    CUDA_TRY(cudaMemcpyAsync(c->rh0, c->h, nb, cudaMemcpyDeviceToDevice, c->stream));
+    CUDA_TRY(cudaMemcpyAsync(c->rthn0, c->theta_n, nb, cudaMemcpyDeviceToDevice, c->stream));
+    int rejected = 0, cg_total = 0, pic_total = 0;
+    // on an error: the state at the step start, time and dt_nom put back
+    auto abort = [&](rf_status st) {
+        const std::string msg = g_err;
+        richardson_restore(c);
+        cudaStreamSynchronize(c->stream);
+        c->t = t0;
+        c->dt_nom = dt_nom0;
+        g_err = msg;
+        return st;
+    };
+    for (;;) {
+        double dt = c->dt_nom;
+        const double bp = next_breakpoint(c, t0);
+        if (bp - t0 < dt) dt = bp - t0;
+        if (t_stop - t0 < dt) dt = t_stop - t0;
+        Attempt Af, A1, A2;
+        c->t = t0;
+        if (rf_status st = attempt(c, dt, Af, false)) return abort(st);
+        cg_total += Af.cg;
+        pic_total += Af.picard;
+        bool ok = Af.converged;
+        if (ok) {
+            CUDA_TRY(cudaMemcpyAsync(c->rhf, c->h, nb, cudaMemcpyDeviceToDevice, c->stream));
+            RF_TRY(richardson_restore(c));
+            if (rf_status st = attempt(c, 0.5 * dt, A1, false)) return abort(st);
+            cg_total += A1.cg;
+            pic_total += A1.picard;
+            ok = A1.converged;
+        }
+        if (ok) {
+            c->t = t0 + 0.5 * dt;
+            if (rf_status st = attempt(c, 0.5 * dt, A2, false)) return abort(st);
+            c->t = t0;
+            cg_total += A2.cg;
+            pic_total += A2.picard;
+            ok = A2.converged;
+        }
+        if (!ok) {
+            RF_TRY(richardson_restore(c));
+            rejected++;
+            c->dt_nom = dt / c->prm.f_shrink;
+            if (c->dt_nom < c->prm.dt_min) {
+                c->dt_nom = dt_nom0;
+                return fail(RF_ERR_DT_MIN, "Richardson control: dt fell below dt_min without Picard convergence at t = " +
+                                               std::to_string(t0));
+            }
+            continue;
+        }
+        // h holds h(2 x dt/2): its closures (kept for the next step) and the
+        // error estimate max |h - h(dt)| in one pass
+        run_closure(c, c->h, c->rhf, c->theta_k, 0);
+        CUDA_TRY(cudaMemcpyAsync(c->res_h, c->res, sizeof(StepResults), cudaMemcpyDeviceToHost, c->stream));
+        if (rf_status st = sync(c)) return abort(st);
+        const double err = c->res_h->nonfinite ? INFINITY : c->res_h->max_dh;
+        double fac = err > 0.0 ? 0.9 * std::sqrt(c->prm.tol_time / err) : 2.0;
+        fac = std::min(2.0, std::max(0.2, fac));
+        c->dt_nom = std::min(dt * fac, c->prm.dt_max);
+        c->err_last = err;
+        if (!(err <= c->prm.tol_time)) {
+            RF_TRY(richardson_restore(c));
+            rejected++;
+            if (c->dt_nom < c->prm.dt_min) {
+                c->dt_nom = dt_nom0;
+                return fail(RF_ERR_DT_MIN, "Richardson control: dt fell below dt_min at t = " + std::to_string(t0));
+            }
+            continue;
+        }
+        c->closure_at_h = true;
+        c->err_max = std::max(c->err_max, err);
+        double tn = t0 + dt;
+        if (std::fabs(tn - bp) <= t_tol(tn)) tn = bp;
+        if (std::fabs(tn - t_stop) <= t_tol(tn)) tn = t_stop;
+        c->t = tn;
+        c->steps++;
+        c->in_cum += A1.mb.bnd_in + A2.mb.bnd_in;
+        c->out_cum += A1.mb.bnd_out + A2.mb.bnd_out;
+        c->closure_cum += (A1.mb.lin_change - (A1.mb.bnd_in - A1.mb.bnd_out)) +
+                          (A2.mb.lin_change - (A2.mb.bnd_in - A2.mb.bnd_out));
+        c->defect_cum += (A1.mb.dstore - (A1.mb.bnd_in - A1.mb.bnd_out)) +
+                         (A2.mb.dstore - (A2.mb.bnd_in - A2.mb.bnd_out));
+        if (info) {
+            info->dt = dt;
+            info->t = c->t;
+            info->picard_iters = pic_total;
+            info->cg_iters = cg_total;
+            info->rejected = rejected;
+            info->max_dh = A2.max_dh;
+        }
+        return RF_OK;
+    }
+}
+
+// One accepted step under the context's time control.
+rf_status step_any(rf_ctx *c, double t_stop, rf_step_info *info)
+{
+    return c->prm.time_control == RF_TIME_RICHARDSON ? do_step_richardson(c, t_stop, info) : do_step(c, t_stop, info);
 }
 
 rf_status storage_of_theta_n(rf_ctx *c, double *out)
@@ -705,6 +897,14 @@ void rf_default_params(rf_solver_params *p)
     p->inner_max_it = 2000;
     p->outer_max_it = 30;
     p->picard_form = RF_PICARD_CHORD;
+    p->closure_arith = RF_CLOSURE_AUTO;
+    p->face_mean = RF_FACE_ARITHMETIC;
+    p->time_scheme = RF_TIME_BACKWARD_EULER;
+    p->time_control = RF_TIME_EBATS;
+    p->tol_time = 1e-3;
+    p->grav[0] = 0.0;
+    p->grav[1] = 0.0;
+    p->grav[2] = 1.0;
 }
 
 const char *rf_last_error(void) { return g_err.c_str(); }
@@ -756,8 +956,8 @@ rf_status rf_mesh_create(const rf_mesh_desc *mesh, const rf_solver_params *param
         g.w[f] = A[f] / d[f];
         g.wb[f] = A[f] / (0.5 * d[f]);
         g.hw[f] = 0.5 * (A[f] / d[f]);
-        g.hg[f] = f == F_ZMIN ? -0.5 * A[f] : (f == F_ZMAX ? 0.5 * A[f] : 0.0);
     }
+    apply_grid_params(g, prm);
     for (int a = 0; a < 3; a++) g.w32[a] = (float)(A[2 * a] / d[2 * a]);
     g.fx = make_fastdiv((unsigned int)g.nx);
     g.fxy = make_fastdiv((unsigned int)g.sxy);
@@ -791,6 +991,7 @@ rf_status rf_mesh_create(const rf_mesh_desc *mesh, const rf_solver_params *param
               alloc_n(c, c->theta_n, N) && alloc_n(c, c->theta_k, N) && alloc_n(c, c->K[0], N) &&
               alloc_n(c, c->K[1], N) && alloc_n(c, c->Can, N) && alloc_n(c, c->c, N) && alloc_n(c, c->b, N) &&
               (c->prm.picard_form != RF_PICARD_MODIFIED || alloc_n(c, c->s0, N)) &&
+              (c->prm.time_scheme != RF_TIME_BDF2 || alloc_n(c, c->theta_p, N)) &&
               alloc_n(c, c->Tx, N) && alloc_n(c, c->Ty, N) && alloc_n(c, c->Tz, N) && alloc_n(c, c->diag, N) &&
               alloc_n(c, c->dinv, N) && alloc_n(c, c->r, N) && alloc_n(c, c->z, N) && alloc_n(c, c->p[0], N) &&
               alloc_n(c, c->p[1], N) && alloc_n(c, c->q, N) && alloc_n(c, c->K32, N) && alloc_n(c, c->cb32, N) &&
@@ -872,8 +1073,13 @@ rf_status rf_set_params(rf_ctx *c, const rf_solver_params *params)
     CUDA_TRY(cudaStreamSynchronize(c->stream));
     if (params->picard_form == RF_PICARD_MODIFIED && !c->s0 && !alloc_n(c, c->s0, c->g.N))
         return fail(RF_ERR_NOMEM, "rf_set_params: device allocation failed");
-    destroy_graphs(c);   // tolerances and caps are baked into the graphs
+    if (params->time_scheme == RF_TIME_BDF2 && !c->theta_p && !alloc_n(c, c->theta_p, c->g.N))
+        return fail(RF_ERR_NOMEM, "rf_set_params: device allocation failed");
+    destroy_graphs(c);   // tolerances, caps and grid fields are baked into the graphs
+    if (params->time_scheme != c->prm.time_scheme) c->dt_prev = 0.0;   // no BDF2 history across a switch
     c->prm = *params;
+    apply_grid_params(c->g, c->prm);
+    c->closure_at_h = false;   // the closure arithmetic may have changed
     return RF_OK;
 }
 
@@ -884,8 +1090,9 @@ rf_status rf_soil_set(rf_ctx *c, const rf_soil *zones, int n_zones, const uint8_
     std::vector<DevSoil> soils(256);
     for (int z = 0; z < n_zones; z++) {
         const rf_soil &s = zones[z];
-        if ((s.model != RF_VG && s.model != RF_GARDNER) || !(s.theta_s > s.theta_r) || !(s.alpha > 0) ||
-            !(s.Ks > 0) || !(s.S >= 0) || (s.model == RF_VG && !(s.n > 1.0)))
+        if ((s.model != RF_VG && s.model != RF_GARDNER && s.model != RF_BROOKS_COREY) || !(s.theta_s > s.theta_r) ||
+            !(s.alpha > 0) || !(s.Ks > 0) || !(s.S >= 0) || (s.model == RF_VG && !(s.n > 1.0)) ||
+            (s.model == RF_BROOKS_COREY && !(s.n > 0.0)))
             return fail(RF_ERR_ARG, "invalid soil parameters in zone " + std::to_string(z));
         const double m = s.model == RF_VG ? 1.0 - 1.0 / s.n : 0.0;
         const float nh = (float)s.n, mh = (float)m;
@@ -941,6 +1148,8 @@ static rf_status state_set_common(rf_ctx *c, double t)
     c->dt_nom = std::min(c->prm.dt0, c->prm.dt_max);
     c->easy = 0;
     c->steps = 0;
+    c->dt_prev = 0.0;           // the first step after a state is set is backward Euler
+    c->err_last = c->err_max = 0.0;
     run_closure(c, c->h, nullptr, c->theta_n, 0);
     // closure_at_h promises K[0], C and theta_k at h: theta_k too (the
     // modified Picard form reads theta*(h^k) on the first iteration)
@@ -959,13 +1168,26 @@ rf_status rf_state_set(rf_ctx *c, const double *h, double t)
     if (!c || !h) return fail(RF_ERR_ARG, "null argument");
     if (!c->soils_set) return fail(RF_ERR_STATE, "call rf_soil_set before rf_state_set");
     if (!std::isfinite(t)) return fail(RF_ERR_ARG, "non-finite time");
-    std::vector<double> hh(h, h + c->g.N);
+    // copied straight from the caller's buffer (a DMA when it is pinned);
+    // only non-finite values on inactive cells need a cleaned copy
+    bool clean = true;
     for (long long p = 0; p < c->g.N; p++) {
-        if (c->flags_h[p] && !std::isfinite(hh[p])) return fail(RF_ERR_ARG, "non-finite head on an active cell");
-        if (!c->flags_h[p] && !std::isfinite(hh[p])) hh[p] = 0.0;
+        if (std::isfinite(h[p])) continue;
+        if (c->flags_h[p]) return fail(RF_ERR_ARG, "non-finite head on an active cell");
+        clean = false;
     }
-    CUDA_TRY(cudaMemcpyAsync(c->h, hh.data(), sizeof(double) * c->g.N, cudaMemcpyHostToDevice, c->stream));
-    return state_set_common(c, t);
+    std::vector<double> hh;
+    const double *src = h;
+    if (!clean) {
+        hh.assign(h, h + c->g.N);
+        for (long long p = 0; p < c->g.N; p++)
+            if (!std::isfinite(hh[p])) hh[p] = 0.0;
+        src = hh.data();
+    }
+    CUDA_TRY(cudaMemcpyAsync(c->h, src, sizeof(double) * c->g.N, cudaMemcpyHostToDevice, c->stream));
+    const rf_status st = state_set_common(c, t);   // synchronises on success
+    if (st) cudaStreamSynchronize(c->stream);       // the host buffer is not read after the call
+    return st;
 }
 
 rf_status rf_state_set_device(rf_ctx *c, const double *d_h, double t)
@@ -1021,7 +1243,7 @@ rf_status rf_state_meta_set(rf_ctx *c, const rf_state_meta *meta, const double *
 rf_status rf_step(rf_ctx *c, rf_step_info *out)
 {
     if (!c) return fail(RF_ERR_ARG, "null context");
-    return do_step(c, INFINITY, out);
+    return step_any(c, INFINITY, out);
 }
 
 rf_status rf_run(rf_ctx *c, double t_end, rf_run_stats *stats, rf_step_info *log, int log_cap)
@@ -1032,7 +1254,7 @@ rf_status rf_run(rf_ctx *c, double t_end, rf_run_stats *stats, rf_step_info *log
     rf_status st = RF_OK;
     while (c->t < t_end - t_tol(t_end)) {
         rf_step_info info{};
-        st = do_step(c, t_end, &info);
+        st = step_any(c, t_end, &info);
         if (st) break;
         if (log && s.steps < log_cap) log[s.steps] = info;
         s.steps++;
@@ -1157,6 +1379,45 @@ rf_status rf_ws_get_stats(rf_ctx *c, rf_ws_stats *out)
     if (!c || !out) return fail(RF_ERR_ARG, "NULL argument");
     out->guesses = c->ws_guesses;
     out->fallbacks = c->ws_fallbacks;
+    return RF_OK;
+}
+
+rf_status rf_apply_inner(rf_ctx *c, const float *d_z, const float *d_pold, float beta, float *d_p, float *d_q,
+                         double *pq)
+{
+    if (!c || !d_z || !d_p || !d_q || (beta != 0.0f && !d_pold) || !std::isfinite(beta))
+        return fail(RF_ERR_ARG, "bad argument");
+    const Grid &g = c->g;
+    cudaStream_t s = c->stream;
+    const size_t nb = sizeof(float) * g.N;
+    // the kernel reads z and p_old from the context's arrays (the TMA maps
+    // describe them) and writes p into the other p buffer
+    CUDA_TRY(cudaMemcpyAsync(c->z32, d_z, nb, cudaMemcpyDeviceToDevice, s));
+    if (beta != 0.0f) CUDA_TRY(cudaMemcpyAsync(c->p32[1], d_pold, nb, cudaMemcpyDeviceToDevice, s));
+    CgScal &h = *c->sc_in_h;
+    h = CgScal{};
+    h.iter = beta != 0.0f ? 1 : 0;      // iteration 0: p = z
+    h.beta = beta;
+    h.rho = 1.0;
+    h.max_it = 1;
+    CUDA_TRY(cudaMemcpyAsync(c->sc_in, c->sc_in_h, sizeof(CgScal), cudaMemcpyHostToDevice, s));
+    launch_cg32_spmv(s, c->nblk, g, c->z32, c->p32[1], c->p32[0], c->q32, c->K32, c->cb32, c->partials, c->ticket,
+                     c->sc_in, c->tma_ok ? &c->tma : nullptr, c->dev_fault);
+    CUDA_TRY(cudaMemcpyAsync(d_p, c->p32[0], nb, cudaMemcpyDeviceToDevice, s));
+    CUDA_TRY(cudaMemcpyAsync(d_q, c->q32, nb, cudaMemcpyDeviceToDevice, s));
+    CUDA_TRY(cudaMemcpyAsync(c->sc_in_h, c->sc_in, sizeof(CgScal), cudaMemcpyDeviceToHost, s));
+    RF_TRY(sync(c));
+    if (pq) *pq = c->sc_in_h->pq;
+    return RF_OK;
+}
+
+rf_status rf_set_wait_limit(rf_ctx *c, int polls)
+{
+    if (!c) return fail(RF_ERR_ARG, "null context");
+    CUDA_TRY(cudaStreamSynchronize(c->stream));
+    c->wait_polls = polls;
+    c->g.wait_tries = polls;
+    destroy_graphs(c);        // the grid (and its limit) is baked into the graphs
     return RF_OK;
 }
 

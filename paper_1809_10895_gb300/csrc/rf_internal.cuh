@@ -13,7 +13,7 @@ namespace rf {
 // Face order used everywhere: 0 -x, 1 +x, 2 -y, 3 +y, 4 -z (bottom), 5 +z (top).
 enum { F_XMIN = 0, F_XMAX, F_YMIN, F_YMAX, F_ZMIN, F_ZMAX };
 enum { BC_ZERO_FLUX = 0, BC_DIRICHLET = 1, BC_FLUX = 2, BC_FREE_DRAINAGE = 3, BC_SEEPAGE = 4 };
-enum { M_VG = 0, M_GARDNER = 1 };
+enum { M_VG = 0, M_GARDNER = 1, M_BROOKS_COREY = 2 };
 
 // Per-cell flag byte: bit f (0..5) = face f is a boundary face on which the
 // boundary condition of face class f applies; bit 7 = active cell.
@@ -65,10 +65,15 @@ struct Grid {
     double w[6];      // A/d for interior faces
     double wb[6];     // A/(d/2) for boundary (half-cell) faces
     double hw[6];     // A/(2 d): T_f = (K_P + K_N) hw_f
-    double hg[6];     // gravity: +A_z/2 on the top face, -A_z/2 on the bottom face, 0 lateral
+    double gf[6];     // gravity flux factor of each face, grad(elevation) . n_out: (-gx, gx, -gy, gy, -gz, gz)
+    double hg[6];     // gf A / 2: explicit gravity of an interior face is (K_P + K_N) hg_f
     float w32[3];     // A/d per axis, FP32 (mixed-precision operator)
     FastDiv fx, fxy;  // division by nx and by nx*ny
     int cap;          // most blocks a tiled stencil kernel launches (partials hold 8 values per block)
+    int closure64;    // 1: closures in FP64 (CUDA's FP64 log / exp); 0: double-float arithmetic
+    int tilted;       // 1: the elevation gradient has x / y components (gravity on lateral faces)
+    int harmonic;     // 1: harmonic interface conductivity; 0: arithmetic mean (linear interpolation)
+    int wait_tries;   // polls of a bounded device wait before it gives up (set for tests; 0: default)
     const FFTables *tab;       // double-float exp/log tables (device)
     unsigned long long *ctr;   // per-kind counters: [2 kind] launches, [2 kind + 1] launches that did work
 };
@@ -80,6 +85,8 @@ struct StepParams {
     int bc_type[6];
     double bc_val[6];
     int modified;   // 1: modified Picard (tangent capacity, mixed-form storage); 0: chord capacity
+    int bdf2;       // 1: variable-step BDF2 storage (modified form) with the coefficients below
+    double a0, a1, a2;   // BDF2: V/dt [a0 theta^{n+1} - a1 theta^n + a2 theta^{n-1}]
 };
 
 // Device-side scalars of one PCG solve.
@@ -267,7 +274,7 @@ void launch_assemble(cudaStream_t s, int nblk, const Grid &g, const DevSoil *soi
                      const double *Can, double *c, double *b, double *Tx, double *Ty, double *Tz,
                      double *diag, double *dinv, float *K32, float *cb32, float *dinv32, const int *skip,
                      int mode = ASM_ONLY, const SolveStart *start = nullptr, double *partials = nullptr,
-                     unsigned int *ticket = nullptr, double *s0 = nullptr);
+                     unsigned int *ticket = nullptr, double *s0 = nullptr, const double *theta_p = nullptr);
 
 void launch_mass_balance(cudaStream_t s, int nblk, const Grid &g, const DevSoil *soils, const uint8_t *zone,
                          const double *Ks, const uint8_t *flags, const StepParams *sp, const double *x_odd,

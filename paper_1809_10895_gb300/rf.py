@@ -23,13 +23,20 @@ RF_OK, RF_ERR_ARG, RF_ERR_NO_DEVICE, RF_ERR_CUDA, RF_ERR_NOMEM, RF_ERR_STATE, RF
     RF_ERR_DT_MIN, RF_ERR_CG, RF_ERR_DEVICE_TIMEOUT = range(10)
 STATUS_NAMES = ("RF_OK", "RF_ERR_ARG", "RF_ERR_NO_DEVICE", "RF_ERR_CUDA", "RF_ERR_NOMEM", "RF_ERR_STATE",
                 "RF_ERR_PICARD", "RF_ERR_DT_MIN", "RF_ERR_CG", "RF_ERR_DEVICE_TIMEOUT")
-RF_VG, RF_GARDNER = 0, 1
+RF_VG, RF_GARDNER, RF_BROOKS_COREY = 0, 1, 2
 FACES = {"xmin": 0, "xmax": 1, "ymin": 2, "ymax": 3, "zmin": 4, "zmax": 5}
 BC_TYPES = {"zero_flux": 0, "dirichlet": 1, "flux": 2, "free_drainage": 3, "seepage": 4}
-MODELS = {"vg": RF_VG, "gardner": RF_GARDNER}
+MODELS = {"vg": RF_VG, "gardner": RF_GARDNER, "brooks_corey": RF_BROOKS_COREY}
 PRECISION = {"fp64": 0, "mixed": 1}
 PRECOND = {"jacobi": 0, "mg": 1, "dic": 2}
 PICARD_FORM = {"chord": 0, "modified": 1}
+CLOSURE_ARITH = {"auto": 0, "fp64": 1, "double_float": 2}
+FACE_MEAN = {"arithmetic": 0, "harmonic": 1}
+TIME_SCHEME = {"backward_euler": 0, "bdf2": 1}
+TIME_CONTROL = {"ebats": 0, "richardson": 1}
+_ENUM_PARAMS = {"precision": PRECISION, "precond": PRECOND, "picard_form": PICARD_FORM,
+                "closure_arith": CLOSURE_ARITH, "face_mean": FACE_MEAN, "time_scheme": TIME_SCHEME,
+                "time_control": TIME_CONTROL}
 
 
 class rf_solver_params(C.Structure):
@@ -37,7 +44,9 @@ class rf_solver_params(C.Structure):
                 ("precond", C.c_int), ("precision", C.c_int), ("dt0", C.c_double), ("dt_max", C.c_double),
                 ("dt_min", C.c_double), ("f_grow", C.c_double), ("f_shrink", C.c_double), ("n_inc", C.c_int),
                 ("n_small", C.c_int), ("n_max", C.c_int), ("eps_chord", C.c_double), ("tol_inner", C.c_double),
-                ("inner_max_it", C.c_int), ("outer_max_it", C.c_int), ("picard_form", C.c_int)]
+                ("inner_max_it", C.c_int), ("outer_max_it", C.c_int), ("picard_form", C.c_int),
+                ("closure_arith", C.c_int), ("face_mean", C.c_int), ("time_scheme", C.c_int),
+                ("time_control", C.c_int), ("tol_time", C.c_double), ("grav", C.c_double * 3)]
 
 
 class rf_mesh_desc(C.Structure):
@@ -127,6 +136,8 @@ SIGNATURES = {
     "rf_assemble": (C.c_int, [_VP, _VP, _VP, C.c_double, C.c_double, _VP, _VP, _VP, _VP, _VP]),
     "rf_apply": (C.c_int, [_VP, _VP, _VP]),
     "rf_solve": (C.c_int, [_VP, _VP, C.POINTER(C.c_int)]),
+    "rf_apply_inner": (C.c_int, [_VP, _VP, _VP, C.c_float, _VP, _VP, _DP]),
+    "rf_set_wait_limit": (C.c_int, [_VP, C.c_int]),
     "rf_launch_count": (C.c_ulonglong, [_VP]),
     "rf_profile_kernel": (C.c_int, [_VP, C.c_int, C.c_int, _DP, _DP]),
     "rf_launch_counts": (C.c_int, [_VP, C.POINTER(C.c_ulonglong), C.c_int]),
@@ -199,15 +210,25 @@ def _check(st: int, where: str):
 def default_params(**kw) -> rf_solver_params:
     p = rf_solver_params()
     load().rf_default_params(C.byref(p))
-    for k, v in kw.items():
-        if k == "precision" and isinstance(v, str):
-            v = PRECISION[v]
-        if k == "precond" and isinstance(v, str):
-            v = PRECOND[v]
-        if k == "picard_form" and isinstance(v, str):
-            v = PICARD_FORM[v]
-        setattr(p, k, v)
+    _set_params(p, kw)
     return p
+
+
+def _set_params(p: rf_solver_params, kw: dict):
+    """Parameter names as in rf_solver_params; enumerations may be given by
+    name; grav_x / grav_y / grav_z set the components of grav."""
+    for k, v in kw.items():
+        if k in _ENUM_PARAMS and isinstance(v, str):
+            v = _ENUM_PARAMS[k][v]
+        if k in ("grav_x", "grav_y", "grav_z"):
+            p.grav["xyz".index(k[-1])] = float(v)
+        elif k == "grav":
+            for i in range(3):
+                p.grav[i] = float(v[i])
+        elif k in dict(rf_solver_params._fields_):
+            setattr(p, k, v)
+        else:
+            raise KeyError(f"unknown solver parameter {k!r}")
 
 
 def _dptr(a: Optional[np.ndarray]):
@@ -287,9 +308,8 @@ class Solver:
     @classmethod
     def from_case(cls, case, **param_overrides) -> "Solver":
         """Build a solver from a workloads.Case (mesh, soils, BCs, params, state)."""
-        if tuple(getattr(case, "gravity", (0.0, 0.0, 1.0))) != (0.0, 0.0, 1.0):
-            raise NotImplementedError(f"{case.name}: gravity along {case.gravity}; this solver's grid is z-up")
         p = dict(case.params)
+        p["grav"] = tuple(getattr(case, "gravity", (0.0, 0.0, 1.0)))
         p.update(param_overrides)
         s = cls(case.nx, case.ny, case.nz, case.dx, case.dy, case.dz, case.z_bottom, case.active,
                 params=default_params(**p))
@@ -301,14 +321,7 @@ class Solver:
 
     def set_params(self, **kw):
         p = self.params
-        for k, v in kw.items():
-            if k == "precision" and isinstance(v, str):
-                v = PRECISION[v]
-            if k == "precond" and isinstance(v, str):
-                v = PRECOND[v]
-            if k == "picard_form" and isinstance(v, str):
-                v = PICARD_FORM[v]
-            setattr(p, k, v)
+        _set_params(p, kw)
         _check(load().rf_set_params(self.ctx, C.byref(p)), "rf_set_params")
 
     def set_soils(self, soils, zone_of_cell=None, Ks_cell=None):
@@ -399,6 +412,25 @@ class Solver:
         it = C.c_int(0)
         _check(load().rf_solve(self.ctx, C.c_void_p(x.data_ptr()), C.byref(it)), "rf_solve")
         return it.value
+
+    def apply_inner(self, z, p_out, q_out, pold=None, beta=0.0) -> float:
+        """The FP32 inner-solve stencil step on the last assembled system
+        (torch CUDA float32 tensors of N elements): p = z + beta pold,
+        q = A32 p; returns p . q."""
+        import torch
+        for name, a in (("z", z), ("p_out", p_out), ("q_out", q_out)) + ((("pold", pold),) if pold is not None else ()):
+            if not (a.is_cuda and a.dtype == torch.float32 and a.is_contiguous() and a.numel() == self.N):
+                raise ValueError(f"apply_inner: {name} must be a contiguous float32 CUDA tensor of {self.N} elements")
+        pq = C.c_double(0.0)
+        _check(load().rf_apply_inner(self.ctx, C.c_void_p(z.data_ptr()),
+                                     None if pold is None else C.c_void_p(pold.data_ptr()), float(beta),
+                                     C.c_void_p(p_out.data_ptr()), C.c_void_p(q_out.data_ptr()), C.byref(pq)),
+               "rf_apply_inner")
+        return pq.value
+
+    def set_wait_limit(self, polls: int):
+        """Test hook of the bounded device waits (0: default; < 0: one non-blocking test)."""
+        _check(load().rf_set_wait_limit(self.ctx, int(polls)), "rf_set_wait_limit")
 
     # -- learned warm start
     def ws_features(self, scales: "rf_ws_scales", t: float, dt: float, out, h=None):
@@ -592,6 +624,14 @@ def pcg_solve_noalloc(shape, diag, Tx, Ty, Tz, b, x, tol=1e-10, max_it=10000, st
     """rf_pcg_solve_noalloc on torch CUDA float64 tensors (x in/out)."""
     import torch
     nx, ny, nz = shape
+    n = int(nx) * int(ny) * int(nz)
+    dev = torch.cuda.current_device()
+    for name, a in (("diag", diag), ("Tx", Tx), ("Ty", Ty), ("Tz", Tz), ("b", b), ("x", x)):
+        # a short, strided or float32 tensor would be read out of bounds on the device
+        if not (isinstance(a, torch.Tensor) and a.is_cuda and a.device.index == dev and a.dtype == torch.float64
+                and a.is_contiguous() and a.numel() == n):
+            raise ValueError(f"pcg_solve_noalloc: {name} must be a contiguous float64 CUDA tensor of "
+                             f"{n} elements on the current device")
     st = stream if stream is not None else torch.cuda.current_stream()
     it = C.c_int(0)
     ptr = lambda a: C.c_void_p(a.data_ptr())

@@ -32,12 +32,15 @@ def test_default_params_match_documented_defaults(lib):
     assert (p.dt0, p.dt_max, p.dt_min, p.f_grow, p.f_shrink) == (1.0, 600.0, 1e-3, 1.3, 1.3)
     assert (p.n_inc, p.n_small, p.n_max) == (10, 3, 8)
     assert p.picard_form == rf.PICARD_FORM["chord"]
+    assert (p.closure_arith, p.face_mean, p.time_scheme, p.time_control) == (0, 0, 0, 0)
+    assert p.tol_time == 1e-3 and tuple(p.grav) == (0.0, 0.0, 1.0)
 
 
 def test_struct_layouts_match_header(lib):
     # sizes of the ABI structs on this platform (LP64)
-    # ... picard_form and the tail padding to 8 bytes
-    assert C.sizeof(rf.rf_solver_params) == 8 * 2 + 4 * 3 + 4 + 8 * 5 + 4 * 3 + 4 + 8 * 2 + 4 * 2 + 4 + 4
+    # ... picard_form, closure_arith, face_mean, time_scheme, time_control
+    # (+4 padding), tol_time, grav[3]
+    assert C.sizeof(rf.rf_solver_params) == 8 * 2 + 4 * 3 + 4 + 8 * 5 + 4 * 3 + 4 + 8 * 2 + 4 * 2 + 4 * 5 + 4 + 8 + 8 * 3
     # rf_ens_stats: t, dt_nom; 4 counters; status (+4); cells; 5 balances; busy_s; ctas (+4)
     assert C.sizeof(rf.rf_ens_stats) == 8 * 2 + 8 * 4 + 4 + 4 + 8 + 8 * 5 + 8 + 4 + 4
     assert C.sizeof(rf.rf_step_info) == 8 * 2 + 4 * 3 + 4 + 8
@@ -80,6 +83,8 @@ def _header_kind(decl):
         return "i64"
     if words[0] == "double":
         return "f64"
+    if words[0] == "float":
+        return "f32"
     if words[0] == "void":
         return "void"
     if words[0] in ("int", "rf_status", "rf_face", "rf_bc_type", "rf_precision", "rf_precond", "rf_picard_form"):
@@ -92,7 +97,7 @@ def _ctypes_kind(t):
         return "void"
     if t in (C.c_void_p, C.c_char_p) or (isinstance(t, type) and issubclass(t, C._Pointer)):
         return "ptr"
-    return {C.c_int: "i32", C.c_double: "f64", C.c_longlong: "i64", C.c_ulonglong: "u64"}[t]
+    return {C.c_int: "i32", C.c_double: "f64", C.c_float: "f32", C.c_longlong: "i64", C.c_ulonglong: "u64"}[t]
 
 
 def test_binding_signatures_match_header_prototypes():

@@ -56,25 +56,27 @@ def gpu(a):
     return torch.as_tensor(np.ascontiguousarray(a), dtype=torch.float64, device="cuda")
 
 
-# theta* from the GPU's double-float closures carries up to ~1.2e-14 relative
-# error (measured over alpha in [0.5, 5], n in [1.2, 2.6], h in [-1e3, -1e-6]);
-# bound it by 3e-14.
-THETA_REL = 3e-14
+# Relative error of theta* per closure arithmetic: FP64 (CUDA's log / exp
+# against the oracle's pow, a few units in the last place: 1e-15); the
+# double-float closures carry up to ~1.2e-14 (measured over alpha in
+# [0.5, 5], n in [1.2, 2.6], h in [-1e3, -1e-6]), bounded by 3e-14.
+THETA_REL = {"fp64": 1e-15, "double_float": 3e-14}
 
 
-def chord_tol(case, hk, hn, dt, act, c_ref):
+def chord_tol(case, hk, hn, dt, act, c_ref, arith="fp64"):
     """Bound on |c_gpu - c_oracle|: the chord slope divides a difference of
     theta values (<= 0.55) by h^k - h^n, so the theta error (two values) is
     amplified by 1/|h^k - h^n|; the rest is relative rounding."""
     V = case.dx * case.dy * case.dz
     dh = np.abs(hk - hn)[act]
-    return (V / dt) * 2 * THETA_REL * 0.55 / np.maximum(dh, 1e-300) + 2e-12 * np.abs(c_ref)
+    return (V / dt) * 2 * THETA_REL[arith] * 0.55 / np.maximum(dh, 1e-300) + 2e-12 * np.abs(c_ref)
 
 
-def test_assembly_matches_oracle():
+@pytest.mark.parametrize("arith", ["fp64", "double_float"])
+def test_assembly_matches_oracle(arith):
     case = masked_case()
     o = oracle_from_case(case)
-    s = rf.Solver.from_case(case)
+    s = rf.Solver.from_case(case, closure_arith=arith)
     rng = np.random.default_rng(9)
     hk = case.h0 + rng.normal(0, 0.05, case.N)
     out = {k: torch.zeros(case.N, dtype=torch.float64, device="cuda") for k in ("K", "theta", "c", "b", "diag")}
@@ -82,10 +84,12 @@ def test_assembly_matches_oracle():
         s.assemble(gpu(hk), gpu(case.h0), 37.0, t, **out)
         ref = o.assemble(hk, case.h0, 37.0, t)
         act = o.active_cells
-        for key in ("K", "theta"):
-            g = out[key].cpu().numpy()[act]
-            np.testing.assert_allclose(g, ref[key], rtol=2e-12, atol=0, err_msg=key)
-        tol_c = chord_tol(case, hk, case.h0, 37.0, act, ref["c"])
+        # K: the oracle's literal Eq. 4 loses digits to cancellation in wet
+        # soil (1 - Se^(1/m)); theta*: the closure arithmetic's own bound
+        np.testing.assert_allclose(out["K"].cpu().numpy()[act], ref["K"], rtol=2e-12, atol=0, err_msg="K")
+        np.testing.assert_allclose(out["theta"].cpu().numpy()[act], ref["theta"], rtol=THETA_REL[arith], atol=0,
+                                   err_msg="theta")
+        tol_c = chord_tol(case, hk, case.h0, 37.0, act, ref["c"], arith)
         assert np.all(np.abs(out["c"].cpu().numpy()[act] - ref["c"]) <= tol_c)
         assert np.all(np.abs(out["diag"].cpu().numpy()[act] - ref["diag"]) <= tol_c + 2e-12 * ref["diag"])
         bg = out["b"].cpu().numpy()[act]
@@ -120,14 +124,15 @@ def test_operator_and_solve_match_oracle():
     it = s.solve(x)
     xo, ito, _ = o.solve(hk, case.h0, 120.0)
     assert abs(it - ito) <= 1
-    # the two systems differ by the chord error of c (above); the solutions
-    # agree to 1e-9 m, two orders below the step-level 1e-8 m bound
-    assert np.max(np.abs(x.cpu().numpy()[act] - xo)) <= 1e-9
+    # the two systems differ by the chord error of c (above, FP64 closures);
+    # the solutions agree to 1e-10 m, two orders below the step-level 1e-8 m
+    assert np.max(np.abs(x.cpu().numpy()[act] - xo)) <= 1e-10
 
 
 def _run_pair(case, t_end, **over):
     s = rf.Solver.from_case(case, **over)
-    o = oracle_from_case(case, **{k: v for k, v in over.items() if k not in ("precision", "tol_inner")})
+    o = oracle_from_case(case, **{k: v for k, v in over.items()
+                                  if k not in ("precision", "tol_inner", "closure_arith", "precond")})
     sg = s.run(t_end)
     so = o.run(t_end)
     return s, o, sg, so
@@ -173,8 +178,10 @@ def test_heterogeneous_box_parity():
 
 
 def test_masked_watershed_parity():
-    case = W.watershed(24, 20, 16, dx=10.0, dz=0.5, seed=3, hours=24, tol_cg=1e-12)
-    s, o, sg, so = _run_pair(case, 12 * 3600.0)
+    # seed 0 rains from hour 11 (3.4 mm/h, 11.4 mm/h from hour 17)
+    case = W.watershed(24, 20, 16, dx=10.0, dz=0.5, seed=0, hours=24, tol_cg=1e-12)
+    s, o, sg, so = _run_pair(case, 20 * 3600.0)
+    assert s.mass_balance()["inflow_cum"] > 0.0
     _assert_same_sequence(sg, so)
     hg, _ = s.get_state()
     ho, _ = o.get_state()
@@ -283,12 +290,115 @@ def test_dt_min_failure_leaves_state_unchanged():
     assert np.array_equal(h0, h1) and m0 == m1
 
 
-def test_full_size_box_first_steps():
-    # the 128x128x64 heterogeneous box at full size: first steps vs oracle
+@pytest.mark.parametrize("precision,tol", [("fp64", TOL_PLAIN), ("mixed", TOL_MIXED)])
+def test_full_size_box_first_steps(precision, tol):
+    # the 128x128x64 heterogeneous box at full size (the mixed path runs the
+    # TMA-staged FP32 stencil over two x-tiles): first steps vs oracle
     case = W.heterogeneous_box(seed=0)
-    s = rf.Solver.from_case(case)
+    s = rf.Solver.from_case(case, precision=precision)
     o = oracle_from_case(case)
     for _ in range(3):
         a, b = s.step(), o.step()
         assert (a.dt, a.picard, a.rejected) == (b.dt, b.picard, b.rejected)
-    assert np.max(np.abs(s.get_state()[0] - o.get_state()[0])) <= TOL_PLAIN
+    assert np.max(np.abs(s.get_state()[0] - o.get_state()[0])) <= tol
+
+
+# Grids that take the mixed path's TMA-staged FP32 stencil (nx a multiple of
+# 4) across several 64-cell x-tiles with a ragged last tile, all active and
+# masked, and one that takes the plain-tile FP32 stencil (nx odd).
+def _box_multitile():
+    return W.heterogeneous_box(136, 20, 12, d=0.25, seed=21, water_table_depth=2.0, rain=4e-6, rain_hours=1.0,
+                               t_end=2 * 3600.0)
+
+
+def _watershed_multitile():
+    # seed 0 rains from hour 11 (3.4 mm/h, 11.4 mm/h from hour 17)
+    return W.watershed(132, 24, 16, dx=10.0, dz=0.5, seed=0, hours=24, tol_cg=1e-12)
+
+
+def _box_odd():
+    return W.heterogeneous_box(135, 21, 11, d=0.25, seed=22, water_table_depth=2.0, rain=4e-6, rain_hours=1.0,
+                               t_end=2 * 3600.0)
+
+
+@pytest.mark.parametrize("make,t_end", [(_box_multitile, 2 * 3600.0), (_watershed_multitile, 20 * 3600.0),
+                                        (_box_odd, 2 * 3600.0)], ids=["box136x20x12", "watershed132x24x16",
+                                                                      "box135x21x11"])
+def test_mixed_path_multitile_parity(make, t_end):
+    case = make()
+    s, o, sg, so = _run_pair(case, t_end, precision="mixed")
+    _assert_same_sequence(sg, so)
+    hg, _ = s.get_state()
+    ho, _ = o.get_state()
+    act = np.ones(case.N, bool) if case.active is None else case.active.astype(bool)
+    assert np.max(np.abs(hg - ho)[act]) <= TOL_MIXED
+    assert s.mass_balance()["closure_rel"] <= 1e-9
+
+
+def _inner_operator_bound(case, o, hk, hn, dt, p64, act):
+    """Element-wise bound on |q32 - A p| for the FP32 operator: FP32 rounding
+    of K, cb and w (one unit each) and of the products and sums that form q
+    (about ten per face), u = 2^-24 relative to the sum of term magnitudes,
+    plus the FP64 chord difference of c between the two sides times |p|."""
+    ref = o.assemble(hk, hn, dt)
+    absq = o.spmv(hk, hn, dt, np.abs(p64[act]))          # diag |p| - sum T |p_N| <= sum of magnitudes
+    # sum of term magnitudes = diag |p_P| + sum_f T_f |p_N| = 2 diag |p| - (A |p|)
+    mags = 2 * ref["diag"] * np.abs(p64[act]) - absq
+    u = 2.0 ** -24
+    return 16 * u * mags + chord_tol(case, hk, hn, dt, act, ref["c"]) * np.abs(p64[act])
+
+
+@pytest.mark.parametrize("make", [_box_multitile, _watershed_multitile, _box_odd],
+                         ids=["box136x20x12", "watershed132x24x16", "box135x21x11"])
+def test_inner_fp32_operator_matches_oracle(make):
+    case = make()
+    o = oracle_from_case(case)
+    s = rf.Solver.from_case(case, precision="mixed")
+    rng = np.random.default_rng(31)
+    hk = case.h0 + rng.normal(0, 0.02, case.N)
+    s.assemble(gpu(hk), gpu(case.h0), 90.0, 0.0)
+    act_mask = np.ones(case.N, bool) if case.active is None else case.active.astype(bool)
+    act = o.active_cells
+    f32 = dict(dtype=torch.float32, device="cuda")
+    z = rng.standard_normal(case.N).astype(np.float32)
+    pold = rng.standard_normal(case.N).astype(np.float32)
+    for beta in (0.0, 0.37):
+        p = torch.zeros(case.N, **f32)
+        q = torch.zeros(case.N, **f32)
+        pq = s.apply_inner(torch.as_tensor(z, **f32), p, q, pold=torch.as_tensor(pold, **f32), beta=beta)
+        pg, qg = p.cpu().numpy().astype(np.float64), q.cpu().numpy().astype(np.float64)
+        # p = fma(beta, p_old, z) in FP32 with beta an FP32 value: the exact
+        # value rounded once (half a unit), 0 off the active set
+        b32 = float(np.float32(beta))
+        pr = z.astype(np.float64) + b32 * pold.astype(np.float64)
+        mag = np.abs(z.astype(np.float64)) + np.abs(b32 * pold.astype(np.float64))
+        assert np.all(np.abs(pg - pr)[act_mask] <= 2.0 ** -24 * np.abs(pr[act_mask]) + 2.0 ** -50 * mag[act_mask])
+        assert np.all(pg[~act_mask] == 0) and np.all(qg[~act_mask] == 0)
+        # q = A p element by element against the oracle's CSR operator on the same p
+        qo = o.spmv(hk, case.h0, 90.0, pg[act])
+        tol = _inner_operator_bound(case, o, hk, case.h0, 90.0, pg, act)
+        err = np.abs(qg[act] - qo)
+        assert np.all(err <= tol), (beta, float(np.max(err / tol)))
+        assert pq == pytest.approx(float(pg[act] @ qo), rel=1e-5)
+
+
+def test_device_wait_timeout_is_reported_and_the_context_recovers():
+    # a wait for staged stencil data that gives up at its first test stops
+    # the solve; the copies in flight are drained with the normal limit, the
+    # step returns RF_ERR_DEVICE_TIMEOUT with the state unchanged, and the
+    # same context then steps exactly like the oracle
+    case = _box_multitile()
+    s = rf.Solver.from_case(case, precision="mixed")
+    h0, m0 = s.get_state()
+    s.set_wait_limit(-1)
+    with pytest.raises(rf.RFError) as e:
+        s.step()
+    assert e.value.status == rf.RF_ERR_DEVICE_TIMEOUT
+    h1, m1 = s.get_state()
+    assert np.array_equal(h0, h1) and m0 == m1
+    s.set_wait_limit(0)
+    o = oracle_from_case(case)
+    for _ in range(6):
+        a, b = s.step(), o.step()
+        assert (a.dt, a.picard, a.rejected) == (b.dt, b.picard, b.rejected)
+    assert np.max(np.abs(s.get_state()[0] - o.get_state()[0])) <= TOL_MIXED

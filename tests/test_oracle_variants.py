@@ -95,14 +95,6 @@ def test_tilted_slope_workload_in_the_oracle():
     assert spread[3.0] >= 1e-5
 
 
-def test_binding_refuses_tilted_gravity():
-    # the CUDA path is z-up: a tilted case must not run there silently
-    from paper_1809_10895_gb300 import rf
-    from paper_1809_10895_gb300 import workloads as W
-    with pytest.raises(NotImplementedError):
-        rf.Solver.from_case(W.tilted_slope(nx=4, ny=4, nz=4))
-
-
 def test_harmonic_face_mean_gives_the_exact_layered_steady_state():
     # saturated steady flow across two layers (Ks 1e-5 over 1e-7 m/s), heads
     # held at both ends: the exact solution is linear in total head within

@@ -57,7 +57,28 @@ BAD_PARAMS = [
     ("precision", 2, "unknown precision"),
     ("precond", 3, "unknown preconditioner"),
     ("picard_form", 2, "unknown Picard linearisation"),
+    ("closure_arith", 3, "unknown closure arithmetic"),
+    ("face_mean", 2, "unknown interface mean"),
+    ("time_scheme", 2, "unknown time scheme"),
+    ("time_control", 2, "unknown time control"),
+    ("tol_time", math.nan, "tol_time"),
 ]
+
+
+# combinations the solver does not run
+BAD_COMBOS = [
+    (dict(face_mean="harmonic", precision="mixed"), "RF_PREC_FP64"),
+    (dict(time_scheme="bdf2"), "modified Picard form under EBATS"),
+    (dict(time_scheme="bdf2", picard_form="modified", time_control="richardson"), "under EBATS"),
+    (dict(time_control="richardson", tol_time=0.0), "tol_time"),
+    (dict(grav=(0.0, math.inf, 1.0)), "gravity"),
+]
+
+
+@pytest.mark.parametrize("kw,why", BAD_COMBOS)
+def test_mesh_create_refuses_combinations(lib, kw, why):
+    st, msg, h = _mesh_create(lib, rf.default_params(**kw))
+    assert st == rf.RF_ERR_ARG and why in msg and h is None
 
 
 @pytest.mark.parametrize("field,value,why", BAD_PARAMS, ids=[f"{f}={v}" for f, v, _ in BAD_PARAMS])
@@ -97,7 +118,10 @@ def test_mesh_create_null_arguments(lib):
 
 @needs_no_gpu
 @pytest.mark.parametrize("kw", [{}, dict(precision="mixed", precond="mg"), dict(precision="mixed", precond="dic"),
-                                dict(picard_form="modified"), dict(f_grow=1.0, n_small=0, eps_chord=0.0)])
+                                dict(picard_form="modified"), dict(f_grow=1.0, n_small=0, eps_chord=0.0),
+                                dict(face_mean="harmonic"), dict(time_scheme="bdf2", picard_form="modified"),
+                                dict(time_control="richardson"), dict(grav=(0.34, 0.05, 0.94)),
+                                dict(closure_arith="double_float"), dict(precision="mixed", closure_arith="fp64")])
 def test_valid_params_reach_the_device_query(lib, kw):
     st, msg, h = _mesh_create(lib, rf.default_params(**kw))
     assert st == rf.RF_ERR_NO_DEVICE and "no CPU fallback" in msg and h is None
@@ -134,6 +158,10 @@ def test_ens_create_refuses_bad_params(lib, field, value, why):
     (dict(picard_form="modified"), "chord"),
     (dict(precision="mixed", precond="mg"), "Jacobi"),
     (dict(precision="mixed", precond="dic"), "Jacobi"),
+    (dict(face_mean="harmonic"), "default scheme"),
+    (dict(time_scheme="bdf2", picard_form="modified"), "chord"),
+    (dict(time_control="richardson"), "default scheme"),
+    (dict(grav=(0.34, 0.05, 0.94)), "default scheme"),
 ])
 def test_ens_create_refuses_forms_it_does_not_run(lib, kw, why):
     st, msg, h = _ens_create(lib, [_instance()], rf.default_params(**kw))
