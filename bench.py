@@ -1,20 +1,29 @@
 """Benchmark: cell-timesteps/s of the Picard / backward-Euler / PCG Richards
-solve on the 128x128x64 heterogeneous box (0.25 m cubes, log-normal Ks with
-exponential covariance, hydrostatic start, 6 h of rain), Picard tolerance
+solve on the 512x512x64 synthetic watershed (10 x 10 x 0.5 m cells,
+diamond-square terrain masking the cells above the surface, four sampled van
+Genuchten layers, hourly Poisson storms, seepage bottom), Picard tolerance
 1e-6 m.
 
 One "step" is one accepted backward-Euler time step: every Picard iteration
-(closures, assembly, PCG solve, global max|dh| test), EBATS reruns and the
-water balance.  ``value`` is the FP32-inner / FP64-defect-correction path
-(closures, Picard test and mass balance in FP64); the plain FP64 path is
-reported beside it.  Inputs are resident in HBM; L2 is flushed between timed
-steps.  ``e2e`` drives the same steps through the C ABI from pinned host
-buffers (state uploaded and downloaded every step).
+(closures, chord capacity, assembly, PCG solve, global max|dh| test), EBATS
+reruns and the water balance.  ``value`` is the plain FP64 path (FP64
+closures, FP64 Jacobi-PCG) over exactly K steps that start at the first hour
+of the seed's first storm, when EBATS has grown dt to dt_max; the state at
+that time is spun up from t = 0 by the solver, untimed, and every path starts
+from it.  The working set (several GB) is far larger than L2, so no flush is
+needed between steps.  Beside it: the FP64 path with double-float closures,
+the mixed path (FP32 inner PCG in FP64 defect correction) with Jacobi,
+multigrid and DIC preconditioners, the time to solution of the whole 30
+simulated days, the other synthetic configurations over their whole periods,
+per-kernel device times against their binding roofs, and the CPU oracle on
+the host cores over the same window.  ``e2e`` drives the headline steps
+through the C ABI from pinned host buffers (state uploaded and read back
+every step).
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl native|reference]
 
 With N > 1 (torchrun, one rank per GPU) every rank runs an independent replica
-(different seed): the solve of one box does not shard without a halo
+(different seed): the solve of one domain does not shard without a halo
 exchange, so this is replicas-only weak scaling.
 """
 from __future__ import annotations
@@ -32,7 +41,7 @@ import time
 ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
-WORKLOAD = "heterogeneous_box_128x128x64"
+WORKLOAD = "watershed_512x512x64"
 METRIC = "cell-timesteps/s at Picard tol 1e-6 m"
 UNIT = "cell-timesteps/s"
 
@@ -47,31 +56,35 @@ def _env_int(k, d):
 def parse():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=400)
-    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--steps", type=int, default=100)
+    ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="native", choices=["native", "reference"])
     ap.add_argument("--seed", type=int, default=0)
     ap.add_argument("--no-baseline", action="store_true", help="skip the CPU oracle baseline leg")
     ap.add_argument("--no-e2e", action="store_true")
-    ap.add_argument("--no-pcg-hbm", action="store_true", help="skip the large-grid PCG kernel bandwidth leg")
+    ap.add_argument("--no-full-period", action="store_true", help="skip the 30-day time-to-solution legs")
     ap.add_argument("--no-ensemble", action="store_true", help="skip the batched-ensemble leg")
-    ap.add_argument("--ensemble-window", type=float, default=600.0, help="simulated seconds of the ensemble leg")
+    ap.add_argument("--ensemble-window", type=float, default=2 * 86400.0, help="simulated seconds of the ensemble leg")
     ap.add_argument("--no-warmstart", action="store_true", help="skip the learned warm-start leg")
-    ap.add_argument("--no-configs", action="store_true", help="skip the column and watershed step legs")
-    ap.add_argument("--config-steps", type=int, default=20, help="timed steps of the watershed step leg")
+    ap.add_argument("--no-configs", action="store_true", help="skip the column and box legs")
     ap.add_argument("--ws-train-size", type=int, default=128, help="nx = ny of the training box (nz = 64)")
     ap.add_argument("--ws-eval-size", type=int, default=256, help="nx = ny of the held-out boxes (nz = 64)")
     ap.add_argument("--ws-eval-seeds", type=int, default=1, help="held-out seeds evaluated")
     ap.add_argument("--ws-snapshots", type=int, default=64, help="training snapshots (accepted plain steps)")
     ap.add_argument("--ws-train-steps", type=int, default=600, help="Adam steps (one full box per step)")
     ap.add_argument("--ws-eval-hours", type=float, default=1.0, help="simulated hours of each held-out run")
+    ap.add_argument("--ws-eval-start", type=float, default=3.0,
+                    help="simulated hour at which the held-out runs start (inside the 6 h of rain; spun up untimed)")
     return ap.parse_args()
 
 
 def config_dict(extra=None):
-    d = {"workload": WORKLOAD, "cells": 128 * 128 * 64, "cell_size_m": 0.25, "lnKs_sigma": 1.0,
-         "corr_len_cells": 8, "picard_tol_m": 1e-6, "cg_tol_rel": 1e-10, "ebats": "dt0 1 s, x1.3, max 600 s",
-         "step": "one accepted backward-Euler step from t=0 after warm-up", "l2": "flushed between timed steps"}
+    d = {"workload": WORKLOAD, "cells": 512 * 512 * 64, "cell_size_m": [10.0, 10.0, 0.5],
+         "terrain": "diamond-square 513^2, roughness 0.8, surface 16-32 m", "layers": 4,
+         "rain": "hourly Poisson storms, mean gap 48 h, Exp(6 h) durations, Exp(3 mm/h) intensities, 720 h",
+         "bottom": "seepage face", "picard_tol_m": 1e-6, "cg_tol_rel": 1e-10,
+         "ebats": "dt0 1 s, x1.3 after 10 easy steps, max 600 s",
+         "l2": "working set (several GB) larger than the 129 MB L2; not flushed"}
     if extra:
         d.update(extra)
     return d
@@ -123,19 +136,24 @@ class ClockSampler:
 
 
 # ------------------------------------------------------------ CPU baseline
-def oracle_steps(case, n_steps=None, budget_s=20.0, openmp=False):
-    """Time the CPU oracle (as it stands: one thread, or the same source built
-    with OpenMP on all cores) on the first accepted steps of the same
-    workload; stops at n_steps or after budget_s."""
+def oracle_from_state(case, h, meta, openmp=False):
+    """The CPU oracle on a workload, resumed at a saved state (time and EBATS
+    counters included)."""
     from tests.helpers import oracle_from_case
     o = oracle_from_case(case, openmp=openmp)
+    o.set_state(h, meta["t"])
+    o.set_clock(meta["t"], meta["dt_nom"], meta["easy"])
+    return o
+
+
+def oracle_steps(o, n_steps=None, budget_s=20.0):
+    """Time accepted oracle steps: n_steps, or as many as fit in budget_s."""
     t0 = time.perf_counter()
-    k = 0
+    k = picard = 0
     while (n_steps is None or k < n_steps) and time.perf_counter() - t0 < budget_s:
-        o.step()
+        picard += o.step().picard
         k += 1
-    dt = time.perf_counter() - t0
-    return k, dt
+    return k, time.perf_counter() - t0, picard
 
 
 def oracle_threads():
@@ -144,56 +162,61 @@ def oracle_threads():
     return O.num_threads(openmp=True)
 
 
-def cpu_baseline(case, budget_s=20.0):
-    """The oracle on the host cores: the OpenMP build on all of them, with the
-    one-thread build beside it, both over the same first steps (as many as the
-    one-thread build takes in half the budget)."""
-    k1, t1 = oracle_steps(case, None, budget_s / 2)
-    single = {"value": k1 * case.n_active() / t1, "unit": UNIT, "cores": 1, "kind": "oracle",
-              "sample": f"first {k1} accepted steps of {WORKLOAD} from t=0 ({t1:.1f} s, one-thread C oracle)"}
+def cpu_baseline(case, h, meta, budget_s=20.0):
+    """The oracle as it stands on the host cores (its OpenMP build on all of
+    them) over the first steps of the GPU's timed window, from the same state;
+    the one-thread build over its first step beside it."""
     threads = oracle_threads()
-    if threads < 1:
-        return dict(single, note="OpenMP build of the oracle unavailable (gcc -fopenmp failed)")
-    k, t = oracle_steps(case, k1, budget_s / 2, openmp=True)
-    return {"value": k * case.n_active() / t, "unit": UNIT, "cores": threads, "kind": "oracle",
-            "sample": f"first {k} accepted steps of {WORKLOAD} from t=0 ({t:.1f} s, C oracle built with "
-                      f"OpenMP, {threads} threads)",
-            "single_thread": single}
+    o = oracle_from_state(case, h, meta, openmp=threads > 0)
+    k, t, pic = oracle_steps(o, None, budget_s)
+    out = {"value": k * case.n_active() / t, "unit": UNIT, "cores": max(threads, 1), "kind": "oracle",
+           "sample": f"the first {k} accepted steps of the timed window of {WORKLOAD} (from t = {meta['t'] / 3600:.0f} h, "
+                     f"{pic} Picard iterations, {t:.1f} s; C oracle"
+                     + (f", OpenMP, {threads} threads)" if threads else ", one thread)")}
+    del o
+    if threads > 0:
+        o = oracle_from_state(case, h, meta)
+        k1, t1, _ = oracle_steps(o, 1, budget_s)
+        out["single_thread"] = {"value": k1 * case.n_active() / t1, "unit": UNIT, "cores": 1, "kind": "oracle",
+                                "sample": f"the first accepted step of the same window ({t1:.1f} s, one-thread C oracle)"}
+    return out
 
 
 def oracle_configs(args, W):
     """The oracle on the other workloads, bounded samples of each: the 1-D
-    column over the GPU leg's timed steps (one thread), the first accepted
-    steps of the watershed from t = 0 (OpenMP build), and a stratified sample
-    of the ensemble's instances from t = 0 within its window (one thread)."""
+    column over the GPU leg's whole window (one thread), the first accepted
+    steps of the box from t = 0 (OpenMP build), and a stratified sample of the
+    ensemble's instances from t = 0 (one thread)."""
     from tests.helpers import oracle_from_case
 
-    def steps_within(o, budget_s, max_steps=None, t_stop=None):
+    def steps_within(o, budget_s, t_stop=None):
         t0 = time.perf_counter()
         k = 0
-        while (max_steps is None or k < max_steps) and time.perf_counter() - t0 < budget_s:
-            info = o.step()
-            k += 1
-            if t_stop is not None and info.t >= t_stop - 1e-9:
+        while time.perf_counter() - t0 < budget_s:
+            info = o.step() if t_stop is None else o.run(t_stop, log_cap=1)
+            if t_stop is not None:
+                k += len(info) if isinstance(info, list) else 1
                 break
+            k += 1
         return k, time.perf_counter() - t0
 
     out = {}
-    col = W.infiltration_column()
+    col = W.infiltration_column(t_end=2 * 3600.0)
     o = oracle_from_case(col)
-    for _ in range(5):
-        o.step()
-    k, dt = steps_within(o, 10.0, max_steps=400)
+    t0 = time.perf_counter()
+    steps = o.run(col.t_end)
+    dt = time.perf_counter() - t0
     out["infiltration_column_1x1x200"] = {
-        "value": k * col.N / dt, "unit": UNIT, "cores": 1, "kind": "oracle",
-        "sample": f"accepted steps 6..{5 + k} from t=0 (the GPU leg's timed steps), one-thread C oracle"}
+        "value": len(steps) * col.N / dt, "unit": UNIT, "cores": 1, "kind": "oracle",
+        "sample": f"the GPU leg's whole window: {len(steps)} accepted steps over the first 2 simulated hours, "
+                  f"one-thread C oracle ({dt:.2f} s)"}
     del o
     threads = oracle_threads()
-    ws = W.watershed(512, 512, 64, seed=args.seed, hours=24)
-    o = oracle_from_case(ws, openmp=threads > 0)
-    k, dt = steps_within(o, 10.0)
-    out["watershed_512x512x64"] = {
-        "value": k * ws.n_active() / dt, "unit": UNIT, "cores": max(threads, 1), "kind": "oracle",
+    box = W.heterogeneous_box(128, 128, 64, seed=args.seed)
+    o = oracle_from_case(box, openmp=threads > 0)
+    k, dt, _ = oracle_steps(o, None, 10.0)
+    out["heterogeneous_box_128x128x64"] = {
+        "value": k * box.n_active() / dt, "unit": UNIT, "cores": max(threads, 1), "kind": "oracle",
         "sample": f"first {k} accepted steps from t=0 ({dt:.1f} s, C oracle"
                   + (f", OpenMP, {threads} threads)" if threads else ", one thread)")}
     del o
@@ -203,14 +226,14 @@ def oracle_configs(args, W):
     cell_steps, total = 0, 0.0
     for i in sample:
         o = oracle_from_case(cases[i])
-        k, dt = steps_within(o, 1.5, t_stop=args.ensemble_window)
+        k, dt, _ = oracle_steps(o, None, 1.5)
         cell_steps += k * cases[i].n_active()
         total += dt
         del o
     out["ensemble_256_uneven"] = {
         "value": cell_steps / total, "unit": UNIT, "cores": 1, "kind": "oracle",
-        "sample": f"{len(sample)} of the 256 instances (every 32nd by size), each from t=0 for at most 1.5 s "
-                  f"or {args.ensemble_window:g} s simulated, one-thread C oracle"}
+        "sample": f"{len(sample)} of the 256 instances (every 32nd by size), each from t=0 for at most 1.5 s, "
+                  f"one-thread C oracle"}
     return out
 
 
@@ -252,6 +275,32 @@ def traffic_for(kernel, cells):
     return None if e is None else e["dram_bytes_per_launch"] * cells / e["cells"]
 
 
+def storm_start(case, min_hours=7.0):
+    """Start of the timed window: the first hour of rain of the workload's
+    series at or after min_hours (EBATS has grown dt from 1 s to dt_max by
+    then), else min_hours."""
+    import numpy as np
+    top = next(b for b in case.bcs if b.face == "zmax")
+    t, v = np.asarray(top.t), np.asarray(top.v)
+    i = np.nonzero((v > 0) & (t >= min_hours * 3600.0))[0]
+    return float(t[i[0]]) if len(i) else min_hours * 3600.0
+
+
+def fp64_counts(kernel):
+    """FP64 arithmetic instructions per active cell of a kernel from the
+    committed ncu summary (None when absent or taken on another source)."""
+    p = os.path.join(ROOT, "profiles", "ncu_fp64_counts.json")
+    try:
+        d = json.load(open(p))
+        e = d["kernels"][kernel]
+        src = open(os.path.join(ROOT, "paper_1809_10895_gb300", "csrc", e["source"]), "rb").read()
+        if hashlib.sha256(src).hexdigest()[:16] != e["source_sha"]:
+            return None
+        return e
+    except Exception:
+        return None
+
+
 def native(args):
     import numpy as np
     import torch
@@ -268,9 +317,9 @@ def native(args):
         import torch.distributed as dist
         dist.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
     torch.cuda.set_device(local)
-    case = W.heterogeneous_box(seed=args.seed + rank)
+    case = W.watershed(512, 512, 64, seed=args.seed + rank, hours=720)
     n_act = case.n_active()
-    flush = torch.empty(256 * 1024 * 1024, dtype=torch.uint8, device="cuda")
+    t0_win = storm_start(case)
 
     def barrier():
         if world > 1:
@@ -278,45 +327,84 @@ def native(args):
             dist.barrier()
         torch.cuda.synchronize()
 
-    def timed_run(precision):
-        s = rf.Solver.from_case(case, precision=precision)
-        stream = s.stream
+    # ---- the window's start state: the mixed path (fastest) runs from t = 0
+    # to the storm's first hour, untimed; every leg starts from this state
+    sp = rf.Solver.from_case(case, precision="mixed")
+    sp.run(t0_win)
+    h_start = torch.empty(case.N, dtype=torch.float64, device="cuda")
+    sp.get_state_device(h_start)
+    _, meta0 = sp.get_state()
+    mb0 = sp.mass_balance()
+    mass7 = [mb0["storage0"], 0.0, mb0["inflow_cum"], mb0["outflow_cum"], 0.0, 0.0, mb0["nonlinear_defect_cum"]]
+    sp.close()
+    del sp
+
+    def start(s):
+        s.set_state_device(h_start, meta0["t"])
+        s.set_meta(meta0, mass7)
+
+    def timed_window(precision, **kw):
+        """W warm-up steps (graph capture included), back to the start state,
+        then exactly K steps timed by CUDA events on the solver's stream."""
+        s = rf.Solver.from_case(case, precision=precision, **kw)
+        start(s)
         for _ in range(args.warmup):
             s.step()
-        starts = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
-        ends = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+        start(s)
         c0 = s.launch_counts()
         picard = cg = rej = 0
+        ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         barrier()
         w0 = time.perf_counter()
-        for i in range(args.steps):
-            flush.zero_()
-            starts[i].record(stream)
+        ev0.record(s.stream)
+        for _ in range(args.steps):
             info = s.step()
-            ends[i].record(stream)
             picard += info.picard
             cg += info.cg
             rej += info.rejected
+        ev1.record(s.stream)
         barrier()
         wall = time.perf_counter() - w0
-        ms = sum(a.elapsed_time(b) for a, b in zip(starts, ends))
+        ms = ev0.elapsed_time(ev1)
         c1 = s.launch_counts()
         counts = {k: (c1[k][0] - c0[k][0], c1[k][1] - c0[k][1]) for k in c1}
-        return s, ms, wall, counts, dict(picard=picard, cg=cg, rejected=rej)
+        t_end = s.get_state()[1]["t"]
+        return s, ms, wall, counts, dict(picard=picard, cg=cg, rejected=rej, t_end=t_end)
 
+    # ---- headline: the plain FP64 path (FP64 closures, FP64 Jacobi-PCG)
     clocks = ClockSampler(local)
     clocks.start()
     time.sleep(0.5)        # let the sampler start before the timed region
-    s_mix, ms_mix, wall_mix, counts_mix, st_mix = timed_run("mixed")
+    s64, ms64, wall64, counts64, st64 = timed_window("fp64")
     clk = clocks.stop()
-    s64, ms64, wall64, counts64, st64 = timed_run("fp64")
-    launches_mix = sum(v[0] for v in counts_mix.values())
+    t64 = max_over_ranks(ms64 / 1e3, world, "cuda")
+    value = job_value(args.steps * n_act, world, t64)
+    launches = sum(v[0] for v in counts64.values())
 
-    t_mix, t64 = max_over_ranks(ms_mix / 1e3, world, "cuda"), max_over_ranks(ms64 / 1e3, world, "cuda")
-    value = job_value(args.steps * n_act, world, t_mix)
-    value64 = job_value(args.steps * n_act, world, t64)
+    def leg(precision, **kw):
+        try:
+            s, ms, wall, counts, st = timed_window(precision, **kw)
+            t = max_over_ranks(ms / 1e3, world, "cuda")
+            out = {"value": job_value(args.steps * n_act, world, t), "unit": UNIT, "ms_per_step": t * 1e3 / args.steps,
+                   "picard_per_step": st["picard"] / args.steps, "cg_iters": st["cg"], "rejected": st["rejected"],
+                   "wall_s": wall, "gpu_launches": sum(v[0] for v in counts.values())}
+            return s, out, counts
+        except Exception as ex:                           # recorded, not fatal to the other legs
+            return None, {"error": f"{type(ex).__name__}: {ex}"[:300]}, None
 
-    # ---- per-kernel device times on the state reached (roofline)
+    s_df, leg_df, _ = leg("fp64", closure_arith="double_float")
+    if s_df is not None:
+        s_df.close()
+    s_mix, leg_mix, counts_mix = leg("mixed")
+    others = {"fp64_double_float_closures": leg_df, "mixed_jacobi": leg_mix}
+    for pc in ("mg", "dic"):
+        s_, out, _ = leg("mixed", precond=pc)
+        others[f"mixed_{pc}"] = out
+        if s_ is not None:
+            s_.close()
+
+    # ---- per-kernel device times on the window's end state; shares of the
+    # headline leg from the device launch counters (launches that did work)
     peaks = {}
     try:
         peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
@@ -325,169 +413,151 @@ def native(args):
     hbm_peak = peaks.get("hbm_gbs")
     peak_src = "measured" if hbm_peak else "fallback"
     hbm_peak = hbm_peak or 6800.0
-    kern = {}
-    for kind in ("closure", "assemble", "resid64", "cg32_spmv", "cg32_update", "cg64_spmv", "cg64_update"):
-        avg_ms, by = s_mix.profile_kernel(kind, reps=30)
-        kern[kind] = {"avg_ms": avg_ms, "bytes": by, "gbs": by / (avg_ms * 1e-3) / 1e9}
-    # device time of each kernel in the timed region: launches that did work
-    # (device counters) x mean launch time (events); the closure kernel that
-    # ends a Picard iteration does the work of the timed closure kernel
-    work = {"closure": counts_mix["closure_picard"][1] + counts_mix["closure"][1],
-            "assemble": counts_mix["assemble"][1], "resid64": counts_mix["resid64"][1],
-            "cg32_spmv": counts_mix["cg32_spmv"][1], "cg32_update": counts_mix["cg32_update"][1]}
-    est = {k: work[k] * kern[k]["avg_ms"] for k in work}
-    tot_est = sum(est.values())
+    sms = torch.cuda.get_device_properties(local).multi_processor_count
+    fp64_peak = 2.0 * sms * peaks.get("sm_max_mhz", 2070.0) * 1e6 / 1e9    # G FP64 instructions / s
+
+    def kernel_table(s, kinds):
+        out = {}
+        for kind in kinds:
+            avg_ms, by = s.profile_kernel(kind, reps=20)
+            out[kind] = {"avg_ms": avg_ms, "bytes": by, "gbs": by / (avg_ms * 1e-3) / 1e9}
+        return out
+
+    names = {"closure": "k_closure_picard", "assemble": "k_assemble", "cg64_spmv": "k_cg64_spmv",
+             "cg64_update": "k_cg64_update", "resid64": "k_resid64", "cg32_spmv": "k_cg32_spmv_tma",
+             "cg32_update": "k_cg32_update"}
+    kern64 = kernel_table(s64, ("closure", "assemble", "cg64_spmv", "cg64_update"))
+    work64 = {"closure": counts64["closure_picard"][1] + counts64["closure"][1],
+              "assemble": counts64["assemble"][1], "cg64_spmv": counts64["cg64_spmv"][1],
+              "cg64_update": counts64["cg64_update"][1]}
+    est = {k: work64[k] * kern64[k]["avg_ms"] for k in work64}
     dom = max(est, key=lambda k: est[k])
-    kd = kern[dom]
-    names = {"closure": "k_closure_picard", "assemble": "k_assemble", "resid64": "k_resid64",
-             "cg32_spmv": "k_cg32_spmv", "cg32_update": "k_cg32_update"}
-    roof = {"kernel": names[dom], "bound": "hbm", "achieved": kd["gbs"], "peak": hbm_peak, "unit": "GB/s",
-            "frac": kd["gbs"] / hbm_peak, "peak_source": f"{peak_src} (MEASURED_PEAKS.json hbm_gbs)",
-            "traffic": traffic_for(names[dom], n_act), "algorithmic_bytes_per_launch": kd["bytes"],
-            "avg_launch_ms": kd["avg_ms"]}
-    # FP64-pipe roof: GB300 issues 2 FP64 thread instructions per clock per
-    # SM; a kernel whose FP64 arithmetic takes longer at that rate than its
-    # bytes at the HBM peak is bound by the FP64 pipe (reported as "alu")
-    ent = profile_entry(names[dom])
-    if ent and ent.get("fp64_arith_inst_per_cell"):
-        sms = torch.cuda.get_device_properties(local).multi_processor_count
-        fp64_peak = 2.0 * sms * peaks.get("sm_max_mhz", 2070.0) * 1e6 / 1e9   # G FP64 instructions / s
-        fp64_inst = ent["fp64_arith_inst_per_cell"] * n_act
-        if fp64_inst / (fp64_peak * 1e9) > kd["bytes"] / (hbm_peak * 1e9):
-            achieved = fp64_inst / (kd["avg_ms"] * 1e-3) / 1e9
-            roof = {"kernel": names[dom], "bound": "alu", "achieved": achieved, "peak": fp64_peak,
-                    "unit": "G FP64 inst/s", "frac": achieved / fp64_peak,
-                    "peak_source": f"derived: 2 FP64 instructions/clk/SM x {sms} SMs x "
-                                   f"{peaks.get('sm_max_mhz', 2070.0):.0f} MHz (MEASURED_PEAKS.json sm_max_mhz)",
-                    "traffic": traffic_for(names[dom], n_act), "algorithmic_fp64_inst_per_launch": fp64_inst,
-                    "fp64_arith_inst_per_cell": ent["fp64_arith_inst_per_cell"],
-                    "fp64_pipe_active_pct_ncu": ent.get("fp64_pipe_active_pct"),
-                    "algorithmic_bytes_per_launch": kd["bytes"], "avg_launch_ms": kd["avg_ms"],
-                    "hbm": {"achieved": kd["gbs"], "peak": hbm_peak, "unit": "GB/s", "frac": kd["gbs"] / hbm_peak}}
 
-    # ---- PCG stencil kernels on a grid far larger than L2 (HBM regime):
-    # the 512x512x64 watershed (16.8 M cells), kernels timed by events
-    pcg_hbm = None
-    if not args.no_pcg_hbm:
-        ws = W.watershed(512, 512, 64, seed=args.seed + rank, hours=24)
-        sw = rf.Solver.from_case(ws, precision="mixed")
-        pcg_hbm = {"workload": "watershed_512x512x64", "cells": ws.N, "active_cells": ws.n_active(),
-                   "peak_gbs": hbm_peak, "kernels": {}}
-        for kind in ("cg32_spmv", "cg32_update", "cg64_spmv", "cg64_update", "resid64"):
-            avg_ms, by = sw.profile_kernel(kind, reps=20)
-            gbs = by / (avg_ms * 1e-3) / 1e9
-            pcg_hbm["kernels"][kind] = {"avg_us": avg_ms * 1e3, "algorithmic_MB": by / 1e6, "GBps": gbs,
-                                        "frac_of_hbm_peak": gbs / hbm_peak}
-        sw.close()
-        del sw
-        # one stiff solve on that grid (x0 = 0, dt = 600 s): inner FP32 PCG
-        # preconditioned by Jacobi vs by the multigrid V-cycle
-        hk = torch.as_tensor(ws.h0, dtype=torch.float64, device="cuda")
-        pcg_hbm["solve_x0_zero"] = {}
-        for pc in ("jacobi", "mg", "dic"):
-            try:
-                sv = rf.Solver.from_case(ws, precision="mixed", precond=pc)
-                sv.assemble(hk, hk, 600.0, 0.0)
-                res = None
-                for rep in range(2):                      # the first call captures the graph
-                    x = torch.zeros(ws.N, dtype=torch.float64, device="cuda")
-                    a, b_ = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-                    a.record(sv.stream)
-                    its = sv.solve(x)
-                    b_.record(sv.stream)
-                    torch.cuda.synchronize()
-                    res = {"inner_iterations": its, "ms": a.elapsed_time(b_)}
-                pcg_hbm["solve_x0_zero"][pc] = res
-                sv.close()
-                del sv
-            except Exception as ex:                       # recorded, not fatal to the other legs
-                pcg_hbm["solve_x0_zero"][pc] = {"error": str(ex)[:200]}
+    def roof_of(kind, kd):
+        """The kernel against its binding roof: the FP64 pipe when its FP64
+        arithmetic per cell (ncu counts) takes longer at 2 instructions per
+        clock per SM than its algorithmic bytes at the HBM peak, else HBM."""
+        ent = fp64_counts(names[kind])
+        tr = traffic_for(names[kind], n_act)
+        hbm = {"achieved": kd["gbs"], "peak": hbm_peak, "unit": "GB/s", "frac": kd["gbs"] / hbm_peak}
+        if ent and ent.get("fp64_inst_per_cell"):
+            inst = ent["fp64_inst_per_cell"] * n_act
+            if inst / (fp64_peak * 1e9) > kd["bytes"] / (hbm_peak * 1e9):
+                ach = inst / (kd["avg_ms"] * 1e-3) / 1e9
+                return {"kernel": names[kind], "bound": "alu", "achieved": ach, "peak": fp64_peak,
+                        "unit": "G FP64 inst/s", "frac": ach / fp64_peak,
+                        "peak_source": f"derived: 2 FP64 instructions/clk/SM x {sms} SMs x "
+                                       f"{peaks.get('sm_max_mhz', 2070.0):.0f} MHz (MEASURED_PEAKS.json sm_max_mhz)",
+                        "traffic": tr, "fp64_inst_per_cell": ent["fp64_inst_per_cell"],
+                        "algorithmic_fp64_inst_per_launch": inst, "avg_launch_ms": kd["avg_ms"],
+                        "algorithmic_bytes_per_launch": kd["bytes"], "hbm": hbm}
+        return {"kernel": names[kind], "bound": "hbm", "achieved": kd["gbs"], "peak": hbm_peak, "unit": "GB/s",
+                "frac": kd["gbs"] / hbm_peak, "peak_source": f"{peak_src} (MEASURED_PEAKS.json hbm_gbs)",
+                "traffic": tr, "algorithmic_bytes_per_launch": kd["bytes"], "avg_launch_ms": kd["avg_ms"]}
 
-    # ---- batched ensemble: 256 uneven instances (1 cm cells, footprints
-    # 1..16 x 1..16, depths 50..400) in one persistent graph-launched kernel
+    roof = roof_of(dom, kern64[dom])
+    kernels64 = {names[k]: dict(roof_of(k, v), launches_worked=work64[k], est_ms=est[k],
+                                share_of_window=est[k] / ms64) for k, v in kern64.items()}
+    kernels_mix = None
+    if s_mix is not None:
+        km = kernel_table(s_mix, ("closure", "assemble", "resid64", "cg32_spmv", "cg32_update"))
+        wm = {"closure": counts_mix["closure_picard"][1] + counts_mix["closure"][1],
+              "assemble": counts_mix["assemble"][1], "resid64": counts_mix["resid64"][1],
+              "cg32_spmv": counts_mix["cg32_spmv"][1], "cg32_update": counts_mix["cg32_update"][1]}
+        kernels_mix = {names[k]: dict(roof_of(k, v), launches_worked=wm[k], est_ms=wm[k] * v["avg_ms"])
+                       for k, v in km.items()}
+        s_mix.close()
+
+    # ---- end to end through the C ABI with host buffers: every step uploads
+    # the state from pinned memory and reads it back
+    e2e = None
+    if not args.no_e2e:
+        h_pin = torch.empty(case.N, dtype=torch.float64, pin_memory=True)
+        h_pin.copy_(h_start)
+        h_np = h_pin.numpy()
+        meta = dict(meta0)
+        start(s64)
+        barrier()
+        w0 = time.perf_counter()
+        for _ in range(args.steps):
+            s64.set_state(h_np, meta["t"])
+            s64.set_meta(meta, mass7)
+            s64.step()
+            h_np[:], meta = s64.get_state()
+        barrier()
+        te = max_over_ranks(time.perf_counter() - w0, world, "cuda")
+        e2e = {"value": job_value(args.steps * n_act, world, te), "unit": UNIT, "h2d_bytes_per_step": 8 * case.N,
+               "d2h_bytes_per_step": 8 * case.N, "precision": "fp64"}
+    s64.close()
+
+    # ---- time to solution of the whole 30 simulated days, from t = 0
+    full = None
+    if not args.no_full_period:
+        full = {}
+        for name, prec, kw in (("fp64", "fp64", {}), ("mixed", "mixed", {})):
+            s = rf.Solver.from_case(case, precision=prec, **kw)
+            s.step()                                   # graph capture outside the timing
+            s.set_state(case.h0, 0.0)
+            ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            barrier()
+            ev0.record(s.stream)
+            steps = s.run(case.t_end)
+            ev1.record(s.stream)
+            barrier()
+            ms = ev0.elapsed_time(ev1)
+            mb = s.mass_balance()
+            full[name] = {"simulated_s": case.t_end, "time_to_solution_s": ms / 1e3, "steps": len(steps),
+                          "picard": sum(x.picard for x in steps), "cg_iters": sum(x.cg for x in steps),
+                          "rejected": sum(x.rejected for x in steps),
+                          "value": len(steps) * n_act / (ms / 1e3), "unit": UNIT,
+                          "closure_rel": mb["closure_rel"]}
+            s.close()
+
+    # ---- batched ensemble: 256 uneven instances over their whole 2 days
     ens = None
     if not args.no_ensemble:
-        cases = W.ensemble(256, seed=args.seed + rank)
-        e = rf.Ensemble.from_cases(cases, precision="mixed")
-        cluster, cta_threads, n_wide, probe_ms = e.tune(min(20.0, args.ensemble_window))
-        barrier()
-        ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        ev0.record(e.stream)
-        e.run(args.ensemble_window)
-        ev1.record(e.stream)
-        torch.cuda.synchronize()
-        ens_ms = ev0.elapsed_time(ev1)
-        cell_steps = 0
-        stats = [e.get(i, want_h=False)[1] for i in range(len(cases))]
-        cell_steps = sum(st["steps"] * st["cells"] for st in stats)
-        ens = {"workload": "ensemble_256_uneven", "instances": len(cases), "cells": sum(c.N for c in cases),
-               "simulated_window_s": args.ensemble_window, "cluster_ctas": cluster, "cta_threads": cta_threads, "wide_instances": n_wide,
-               "tuner_probe_ms": probe_ms,
-               "kernel_ms": ens_ms, "cell_timesteps": cell_steps, "value": cell_steps / (ens_ms * 1e-3),
-               "unit": UNIT, "steps_total": sum(st["steps"] for st in stats),
-               "picard_total": sum(st["picard_iters"] for st in stats),
-               "failed_instances": sum(1 for st in stats if st["status"] != 0), "precision": "mixed"}
-        e.close()
-        del e
+        try:
+            ens = ensemble_leg(args, rank, rf, W, barrier)
+        except Exception as ex:
+            ens = {"error": f"{type(ex).__name__}: {ex}"[:300]}
 
-    # ---- learned warm start: snapshots from the plain solver on one box,
-    # Adam training by the library's kernels, then held-out boxes run with and
-    # without the network's first Picard iterate (same tolerance, same EBATS)
+    # ---- learned warm start
     wsl = None
     if not args.no_warmstart:
-        wsl = warmstart_leg(args, rank, rf, W, peaks)
+        try:
+            wsl = warmstart_leg(args, rank, rf, W, peaks)
+        except Exception as ex:
+            wsl = {"error": f"{type(ex).__name__}: {ex}"[:300]}
 
-    # ---- the other synthetic configurations, whole steps: the 1-D column
-    # (plain FP64 path) and the 512x512x64 watershed (mixed, Jacobi and MG)
+    # ---- the other synthetic configurations
     cfg = None
     if not args.no_configs:
         cfg = configs_leg(args, rank, rf, W)
 
-    # ---- end to end through host buffers
-    e2e = None
-    if not args.no_e2e:
-        s = rf.Solver.from_case(case, precision="mixed")
-        for _ in range(args.warmup):
-            s.step()
-        h_pin = torch.empty(case.N, dtype=torch.float64, pin_memory=True)
-        h_np = h_pin.numpy()
-        h_np[:], meta = s.get_state()
-        mb = s.mass_balance()
-        mass7 = [mb["storage0"], 0, mb["inflow_cum"], mb["outflow_cum"], 0, 0, mb["nonlinear_defect_cum"]]
-        barrier()
-        t0 = time.perf_counter()
-        for _ in range(args.steps):
-            s.set_state(h_np, meta["t"])
-            s.set_meta(meta, mass7)
-            s.step()
-            h_np[:], meta = s.get_state()
-        barrier()
-        te = time.perf_counter() - t0
-        te = max_over_ranks(te, world, "cuda")
-        e2e = {"value": job_value(args.steps * n_act, world, te), "unit": UNIT, "h2d_bytes_per_step": 8 * case.N,
-               "d2h_bytes_per_step": 8 * case.N}
-
     if rank == 0:
         line = {
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
-            "warmup": args.warmup, "ms_per_step": t_mix * 1e3 / args.steps, "higher_is_better": True,
-            "scaling": "weak", "vs_baseline": None, "dtype": "f32 inner PCG / f64 closures, residual, Picard test",
-            "data": "synthetic (seeded Gaussian random field, no dataset)",
-            "config": config_dict({"precision": "mixed", "parallelism": "replicas" if world > 1 else "single GPU",
-                                   "picard_iters": st_mix["picard"], "cg_inner_iters": st_mix["cg"],
-                                   "rejected": st_mix["rejected"], "wall_s": wall_mix}),
-            "plain_fp64": {"value": value64, "unit": UNIT, "ms_per_step": t64 * 1e3 / args.steps,
-                           "picard_iters": st64["picard"], "cg_iters": st64["cg"], "wall_s": wall64},
-            "speedup_mixed_vs_fp64": value / value64,
-            "gpu_launches": launches_mix,
-            "launch_counts": {k: {"launched": v[0], "worked": v[1]} for k, v in counts_mix.items() if v[0]},
-            "kernel_time_shares": {k: {"launches": work[k], "est_ms": est[k], "share_of_step_time":
-                                       est[k] / (t_mix * 1e3)} for k in est},
+            "warmup": args.warmup, "ms_per_step": t64 * 1e3 / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None,
+            "dtype": "f64 (closures, operator, PCG, Picard test, balance)",
+            "data": "synthetic (seeded diamond-square terrain, sampled soil layers, Poisson storms; no dataset)",
+            "config": config_dict({"window": f"{args.steps} accepted steps from t = {t0_win / 3600:.0f} h "
+                                             f"(the first hour of the seed's first storm, dt grown to dt_max), "
+                                             f"state spun up from t = 0 untimed",
+                                   "window_end_s": st64["t_end"], "precision": "fp64", "precond": "jacobi",
+                                   "parallelism": "replicas" if world > 1 else "single GPU",
+                                   "active_cells": n_act, "picard_iters": st64["picard"], "cg_iters": st64["cg"],
+                                   "rejected": st64["rejected"], "wall_s": wall64}),
+            "gpu_launches": launches,
+            "launch_counts": {k: {"launched": v[0], "worked": v[1]} for k, v in counts64.items() if v[0]},
             "roofline": roof,
-            "kernels": {k: {"avg_us": v["avg_ms"] * 1e3, "GBps": v["gbs"]} for k, v in kern.items()},
+            "kernels": kernels64,
+            "kernels_mixed": kernels_mix,
             "clocks": clk,
             "e2e": e2e,
-            "pcg_hbm": pcg_hbm,
+            "other_paths": others,
+            "speedup_mixed_vs_fp64": (leg_mix["value"] / value) if "value" in leg_mix else None,
+            "time_to_solution": full,
             "ensemble": ens,
             "warmstart": wsl,
             "other_configs": cfg,
@@ -495,7 +565,7 @@ def native(args):
         if not args.no_baseline:
             # host-side legs: an error is recorded in the line, never lost with it
             try:
-                line["cpu_baseline"] = cpu_baseline(case)
+                line["cpu_baseline"] = cpu_baseline(case, h_start.cpu().numpy(), meta0, budget_s=20.0)
             except Exception as ex:
                 line["cpu_baseline"] = {"error": f"{type(ex).__name__}: {ex}"[:300]}
             if not args.no_configs:
@@ -509,62 +579,72 @@ def native(args):
         dist.destroy_process_group()
 
 
+def ensemble_leg(args, rank, rf, W, barrier):
+    import torch
+    cases = W.ensemble(256, seed=args.seed + rank)
+    e = rf.Ensemble.from_cases(cases, precision="mixed")
+    cluster, cta_threads, n_wide, probe_ms = e.tune(min(20.0, args.ensemble_window))
+    barrier()
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    ev0.record(e.stream)
+    e.run(args.ensemble_window)
+    ev1.record(e.stream)
+    torch.cuda.synchronize()
+    ens_ms = ev0.elapsed_time(ev1)
+    stats = [e.get(i, want_h=False)[1] for i in range(len(cases))]
+    cell_steps = sum(st["steps"] * st["cells"] for st in stats)
+    out = {"workload": "ensemble_256_uneven", "instances": len(cases), "cells": sum(c.N for c in cases),
+           "simulated_window_s": args.ensemble_window, "cluster_ctas": cluster, "cta_threads": cta_threads,
+           "wide_instances": n_wide, "tuner_probe_ms": probe_ms, "kernel_ms": ens_ms, "time_to_solution_s": ens_ms / 1e3,
+           "cell_timesteps": cell_steps, "value": cell_steps / (ens_ms * 1e-3), "unit": UNIT,
+           "steps_total": sum(st["steps"] for st in stats), "picard_total": sum(st["picard_iters"] for st in stats),
+           "failed_instances": sum(1 for st in stats if st["status"] != 0), "precision": "mixed",
+           "max_closure_rel": max(st["closure_abs"] / max(st["storage0"] + st["inflow_cum"] + st["outflow_cum"], 1e-300)
+                                  for st in stats)}
+    e.close()
+    return out
+
+
 def configs_leg(args, rank, rf, W):
     import torch
 
-    def timed_steps(s, n):
+    def timed_run(s, t_end):
         a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         a.record(s.stream)
-        picard = 0
-        for _ in range(n):
-            picard += s.step().picard
+        steps = s.run(t_end)
         b.record(s.stream)
         torch.cuda.synchronize()
-        return a.elapsed_time(b), picard
+        return a.elapsed_time(b), steps
 
     out = {}
-    col = W.infiltration_column()
+    # 1-D column: its feasible window, the first 2 simulated hours (R-stall), plain FP64
+    col = W.infiltration_column(t_end=2 * 3600.0)
     s = rf.Solver.from_case(col, precision="fp64")
-    for _ in range(5):
-        s.step()
-    n = 400
-    ms, pic = timed_steps(s, n)
-    out["infiltration_column_1x1x200"] = {"precision": "fp64", "steps": n, "ms_per_step": ms / n,
-                                          "picard_per_step": pic / n, "value": n * col.N / (ms / 1e3), "unit": UNIT,
-                                          "note": "200 cells: launch- and synchronisation-bound"}
+    s.step()
+    s.set_state(col.h0, 0.0)
+    ms, steps = timed_run(s, col.t_end)
+    out["infiltration_column_1x1x200"] = {"precision": "fp64", "simulated_s": col.t_end, "steps": len(steps),
+                                          "time_to_solution_s": ms / 1e3, "ms_per_step": ms / len(steps),
+                                          "picard_per_step": sum(x.picard for x in steps) / len(steps),
+                                          "value": len(steps) * col.N / (ms / 1e3), "unit": UNIT}
     s.close()
-    ws = W.watershed(512, 512, 64, seed=args.seed + rank, hours=24)
-    for pc in ("jacobi", "mg", "dic"):
-        try:
-            s = rf.Solver.from_case(ws, precision="mixed", precond=pc)
-            for _ in range(3):
-                s.step()
-            n = args.config_steps
-            ms, pic = timed_steps(s, n)
-            out[f"watershed_512x512x64_{pc}"] = {"precision": "mixed", "precond": pc, "steps": n,
-                                                  "ms_per_step": ms / n, "picard_per_step": pic / n,
-                                                  "active_cells": ws.n_active(),
-                                                  "value": n * ws.n_active() / (ms / 1e3), "unit": UNIT}
-            s.close()
-        except Exception as ex:                           # recorded, not fatal to the other legs
-            out[f"watershed_512x512x64_{pc}"] = {"error": str(ex)[:200]}
-    # the benchmark box with the classical (chord) and the modified Picard
-    # linearisation (Sec. 2.2), mixed precision, same steps from t = 0
+    # the heterogeneous box over its whole 48 h, both paths
     box = W.heterogeneous_box(128, 128, 64, seed=args.seed + rank)
-    for form in ("chord", "modified"):
-        s = rf.Solver.from_case(box, precision="mixed", picard_form=form)
-        for _ in range(args.warmup):
+    for prec in ("fp64", "mixed"):
+        try:
+            s = rf.Solver.from_case(box, precision=prec)
             s.step()
-        n = args.steps
-        ms, pic = timed_steps(s, n)
-        mb = s.mass_balance()
-        scale = mb["storage0"] + mb["inflow_cum"] + mb["outflow_cum"]
-        out[f"heterogeneous_box_128x128x64_{form}_picard"] = {
-            "precision": "mixed", "picard_form": form, "steps": n, "ms_per_step": ms / n,
-            "picard_per_step": pic / n, "simulated_s": s.get_state()[1]["t"],
-            "closure_rel": mb["closure_rel"], "nonlinear_defect_rel": abs(mb["nonlinear_defect_cum"]) / scale,
-            "value": n * box.n_active() / (ms / 1e3), "unit": UNIT}
-        s.close()
+            s.set_state(box.h0, 0.0)
+            ms, steps = timed_run(s, box.t_end)
+            mb = s.mass_balance()
+            out[f"heterogeneous_box_128x128x64_{prec}"] = {
+                "precision": prec, "simulated_s": box.t_end, "steps": len(steps), "time_to_solution_s": ms / 1e3,
+                "picard_per_step": sum(x.picard for x in steps) / len(steps),
+                "cg_iters": sum(x.cg for x in steps), "closure_rel": mb["closure_rel"],
+                "value": len(steps) * box.n_active() / (ms / 1e3), "unit": UNIT}
+            s.close()
+        except Exception as ex:
+            out[f"heterogeneous_box_128x128x64_{prec}"] = {"error": str(ex)[:200]}
     return out
 
 
@@ -625,10 +705,18 @@ def warmstart_leg(args, rank, rf, W, peaks):
     fwd_flop = 2.0 * 27 * (8 * 32 + 8 * 32 * 32 + 32 * 8) * ec.N
     bf16_peak = peaks.get("bf16_tflops")
     runs = {}
-    t_eval = args.ws_eval_hours * 3600.0
+    t0_ev = args.ws_eval_start * 3600.0
+    t_eval = t0_ev + args.ws_eval_hours * 3600.0
     max_diff = 0.0
     for seed in range(args.ws_eval_seeds):
         ec = W.heterogeneous_box(n_ev, n_ev, 64, seed=2000 + 97 * seed + rank)
+        # the window's start state (inside the rain, dt grown), spun up by the plain mixed path
+        sp = rf.Solver.from_case(ec, precision="mixed")
+        sp.run(t0_ev)
+        h_s = torch.empty(ec.N, dtype=torch.float64, device="cuda")
+        sp.get_state_device(h_s)
+        meta_s = sp.get_state()[1]
+        sp.close()
         states = {}
         for prec in ("fp64", "mixed"):
             for warm in (False, True):
@@ -637,14 +725,14 @@ def warmstart_leg(args, rank, rf, W, peaks):
                 if warm:
                     s.ws_attach(net, sc)
                 s.step()                            # graph capture, workspaces: outside the timing
-                h0 = torch.as_tensor(ec.h0, dtype=torch.float64, device="cuda")
-                s.set_state_device(h0, 0.0)
+                s.set_state_device(h_s, t0_ev)
+                s.set_meta(meta_s)
                 if warm:
                     s.ws_attach(net, sc)            # counters from zero
                 a, b = ev(), ev()
                 a.record(s.stream)
                 steps = picard = rej = 0
-                t = 0.0
+                t = t0_ev
                 while t < t_eval * (1 - 1e-12):
                     info = s.step()
                     t = info.t
@@ -682,11 +770,20 @@ def warmstart_leg(args, rank, rf, W, peaks):
     for r in runs.values():
         r["picard_per_step"] = r["picard"] / max(r["steps"], 1)
         r["time_to_solution_s"] = r["ms"] / 1e3
+        r["ms_per_picard"] = r["ms"] / max(r["picard"], 1)
         if r["guesses"]:
             r["fallback_rate"] = r["fallbacks"] / r["guesses"]
+    # break-even: the guess (one forward pass per step) pays when it saves
+    # more Picard iterations per step than forward_ms / (ms per Picard iteration)
+    pm, wm = runs["plain_mixed"], runs["warm_mixed"]
+    break_even = {"forward_ms_per_guess": fwd_ms, "plain_mixed_ms_per_picard": pm["ms_per_picard"],
+                  "picard_saved_needed_per_step": fwd_ms / pm["ms_per_picard"],
+                  "picard_saved_per_step": pm["picard_per_step"] - wm["picard_per_step"],
+                  "plain_fp64_ms_per_picard": runs["plain_fp64"]["ms_per_picard"]}
     return {
         "train_workload": f"heterogeneous_box_{n_tr}x{n_tr}x64", "eval_workload": f"heterogeneous_box_{n_ev}x{n_ev}x64",
-        "eval_seeds": args.ws_eval_seeds, "eval_window_s": t_eval, "snapshots": len(snaps),
+        "eval_seeds": args.ws_eval_seeds, "eval_window_s": [t0_ev, t_eval], "snapshots": len(snaps),
+        "break_even": break_even,
         "snapshot_collect_ms": collect_ms, "train_steps": args.ws_train_steps, "train_ms": train_ms,
         "train_voxels_per_s": args.ws_train_steps * vox / (train_ms / 1e3),
         "train_tflops": 3 * flop_fwd * args.ws_train_steps / (train_ms / 1e3) / 1e12,
@@ -702,38 +799,39 @@ def warmstart_leg(args, rank, rf, W, peaks):
 
 # ---------------------------------------------------------- reference arm
 def reference(args):
-    """The CPU oracle, as it stands, on the same workload and metric: its
-    OpenMP build on all host cores, or the one-thread build where gcc cannot
-    build that."""
+    """The CPU oracle, as it stands, on the same workload, window and metric:
+    its OpenMP build on all host cores (the one-thread build where gcc cannot
+    build that).  The oracle spins the watershed up from t = 0 to the window's
+    start itself (untimed), then times the window's first steps, at most K and
+    at most about a minute of them."""
     rank = _env_int("RANK", 0)
     if rank != 0:
         return
     from oracle import oracle as O
     from paper_1809_10895_gb300 import workloads as W
-    O.build()
-    case = W.heterogeneous_box(seed=args.seed)
-    # each step is one accepted oracle step; warm-up and timed steps are
-    # bounded so the whole run stays within a few minutes
-    w = min(args.warmup, 3)
-    k = max(1, min(args.steps, 40))
     from tests.helpers import oracle_from_case
+    O.build()
+    O.build(openmp=True)
+    case = W.watershed(512, 512, 64, seed=args.seed, hours=720)
+    t0_win = storm_start(case)
     threads = O.num_threads(openmp=True)          # all host cores; 0: one-thread build only
     o = oracle_from_case(case, openmp=threads > 0)
     cores = max(threads, 1)
-    for _ in range(w):
-        o.step()
-    t0 = time.perf_counter()
-    for _ in range(k):
-        o.step()
-    dt = time.perf_counter() - t0
+    w0 = time.perf_counter()
+    o.run(t0_win)
+    spin = time.perf_counter() - w0
+    k, dt, pic = oracle_steps(o, max(1, args.steps), 60.0)
     v = k * case.n_active() / dt
+    sample = (f"accepted steps 1..{k} of the timed window of {WORKLOAD} (from t = {t0_win / 3600:.0f} h, "
+              f"{pic} Picard iterations, {dt:.1f} s) after an untimed spin-up from t = 0 ({spin:.0f} s); C oracle, "
+              + (f"OpenMP, {threads} threads" if threads else "one thread"))
     print(json.dumps({
-        "impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": 1, "steps": k, "warmup": w,
+        "impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": 1, "steps": k, "warmup": 0,
         "ms_per_step": dt * 1e3 / k, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-        "dtype": "f64", "data": "synthetic (seeded Gaussian random field, no dataset)", "config": config_dict(),
-        "cpu_baseline": {"value": v, "unit": UNIT, "cores": cores, "kind": "oracle",
-                         "sample": f"accepted steps {w + 1}..{w + k} of {WORKLOAD} (C oracle, "
-                                   + (f"OpenMP, {threads} threads)" if threads else "one thread)")},
+        "dtype": "f64", "data": "synthetic (seeded diamond-square terrain, sampled soil layers, Poisson storms; no dataset)",
+        "config": config_dict({"window": f"steps from t = {t0_win / 3600:.0f} h (the first hour of the seed's first "
+                                         f"storm), state spun up from t = 0 untimed", "precision": "fp64"}),
+        "cpu_baseline": {"value": v, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": sample},
         "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }))
 

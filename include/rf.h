@@ -548,6 +548,29 @@ rf_status rf_nn_train_step(rf_nn *net, const float *d_x, const float *d_target, 
 /* Kernel launches issued by this network so far (host count). */
 long long rf_nn_launch_count(const rf_nn *net);
 
+/* Trace of a gradient evaluation, for checking each layer's kernels element
+ * by element: after rf_nn_set_trace(net, 1), every rf_nn_loss_grad /
+ * rf_nn_train_step also keeps each layer's BF16 output gradient (the values
+ * its weight-gradient and input-gradient contractions read), and
+ * rf_nn_trace_get copies one stored tensor of the last evaluation into host
+ * memory, channels-last over its M = B*D*H*W voxels:
+ *   RF_NN_TRACE_INPUT     index 0: BF16 features, M x 8 (4 features, 4 zero)
+ *   RF_NN_TRACE_BLOCK_OUT index 0..4: BF16 activation after the input
+ *                         convolution (0) and after residual block i (i), M x 32
+ *   RF_NN_TRACE_BLOCK_MID index 0..3: BF16 activation between the two
+ *                         convolutions of residual block i + 1, M x 32
+ *   RF_NN_TRACE_OUT_GRAD  index 0..9: BF16 gradient of the loss with respect
+ *                         to layer index's output (after its ReLU mask),
+ *                         M x 32 (layer 9: M x 8, channel 0 used)
+ *   RF_NN_TRACE_OUTPUT    index 0: FP32 network output, M x 8 (channel 0 used)
+ * BF16 values are copied as their 16-bit patterns.  count must equal the
+ * tensor's element count (RF_ERR_ARG otherwise); RF_ERR_STATE when no traced
+ * evaluation exists.  Synchronises the network's stream. */
+enum { RF_NN_TRACE_INPUT = 0, RF_NN_TRACE_BLOCK_OUT = 1, RF_NN_TRACE_BLOCK_MID = 2, RF_NN_TRACE_OUT_GRAD = 3,
+       RF_NN_TRACE_OUTPUT = 4 };
+rf_status rf_nn_set_trace(rf_nn *net, int on);
+rf_status rf_nn_trace_get(rf_nn *net, int what, int index, void *host, long long count);
+
 /* Features of a state of the mesh for a step of size dt from time t (the
  * top flux feature takes the top condition's value at t): d_h is N doubles
  * on the device, or NULL for the context's current state; d_x receives N*4

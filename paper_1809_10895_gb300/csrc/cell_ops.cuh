@@ -5,6 +5,7 @@
 
 #include <math.h>
 
+#include "f64m.cuh"
 #include "rf_internal.cuh"
 
 namespace rf {
@@ -61,32 +62,40 @@ __device__ __forceinline__ void closure_vg_df(const DevSoil &s, double Ks, doubl
     C = s.cfac * ff_to_d(ff_mul(ys, w));
 }
 
-// The same van Genuchten / Mualem closures (h < 0) in FP64 with CUDA's FP64
-// log, exp, log1p and expm1: with u = -alpha h, L = log u, x = exp(n L),
-// l1 = log1p(x):
-//   Se = exp(-m l1), (x/(1+x))^m = exp(m (n L - l1)) = ys, w = 1/(1+x),
+// The same van Genuchten / Mualem closures (h < 0) in FP64, with the
+// table-driven exp / log of f64m.cuh: with u = -alpha h, L = log u (as a
+// double-double), x = exp(n L), l1 = log1p(x) (double-double):
+//   Se = exp(-m l1), w = 1/(1+x), ys = (x/(1+x))^m = (x/u) Se,
 //   K = Ks sqrt(Se) (1 - ys)^2 with 1 - ys = -expm1(m log1p(-w)) when
 //   ys > 1/2, C = (theta_s-theta_r) alpha n m ys w.
+// n L and m l1 are formed with their rounding errors (two-product), so x and
+// Se keep a few units in the last place however large |L| or l1 are.
 // Beyond x = e^700 (a suction far outside any soil state) theta = theta_r +
-// dtheta x^-m and K = C = 0.
-__device__ __forceinline__ void closure_vg_fp64(const DevSoil &s, double Ks, double h, double &th, double &K,
-                                                double &C)
+// dtheta x^-m and K = C = 0; below u = 1e-30 (h within 1e-30/alpha of 0) ys
+// is taken as exp(m (n L - l1)), the quotient x/u being out of range.
+__device__ __forceinline__ void closure_vg_fp64(const DevSoil &s, double Ks, double h,
+                                                const FFTables *__restrict__ tab, double &th, double &K, double &C)
 {
     const double dth = s.theta_s - s.theta_r;
     const double u = -s.alpha * h;
-    const double nL = s.n * log(u);
-    if (nL > 700.0) {
-        th = s.theta_r + dth * exp(-s.m * nL);
+    double Lh, Ll;
+    f64_log_dd(u, tab, Lh, Ll);
+    const double nh = s.n * Lh;
+    const double nl = fma(s.n, Lh, -nh) + s.n * Ll;
+    if (nh > 700.0) {
+        th = s.theta_r + dth * f64_exp(-s.m * nh, tab);
         K = 0.0;
         C = 0.0;
         return;
     }
-    const double x = exp(nL);
-    const double l1 = log1p(x);
-    const double se = exp(-s.m * l1);
-    const double ys = exp(s.m * (nL - l1));
-    const double w = 1.0 / (1.0 + x);
-    const double omy = ys <= 0.5 ? 1.0 - ys : -expm1(s.m * log1p(-w));
+    const double x = f64_exp_dd(nh, nl, tab);
+    double l1h, l1l;
+    f64_log1p_dd(x, tab, l1h, l1l);
+    const double sh = -s.m * l1h;
+    const double se = f64_exp_dd(sh, fma(-s.m, l1h, -sh) - s.m * l1l, tab);
+    const double w = rcp64(1.0 + x);
+    const double ys = u >= 1e-30 ? (x * rcp64(u)) * se : f64_exp(s.m * ((nh - l1h) + (nl - l1l)), tab);
+    const double omy = ys <= 0.5 ? 1.0 - ys : -f64_expm1_neg(s.m * f64_log1p(-w, tab), tab);
     th = s.theta_r + dth * se;
     K = Ks * sqrt(se) * (omy * omy);
     C = s.cfac * (ys * w);
@@ -139,7 +148,7 @@ __device__ __forceinline__ void closure(const DevSoil &s, double Ks, double h, c
         closure_bc(s, Ks, h, th, K, C);
         return;
     }
-    if (fp64) closure_vg_fp64(s, Ks, h, th, K, C);
+    if (fp64) closure_vg_fp64(s, Ks, h, tab, th, K, C);
     else closure_vg_df(s, Ks, h, tab, th, K, C);
 }
 

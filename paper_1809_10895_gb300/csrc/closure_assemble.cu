@@ -295,8 +295,23 @@ k_accept(Grid g, const double *__restrict__ xf, double *__restrict__ h, const do
     }
 }
 
+// Both precisions' tables: the double-float ones from double arithmetic,
+// the FP64 ones from long double (extended or quadruple precision on the
+// hosts this builds for), each rounded once.
 void make_ff_tables(FFTables *t)
 {
+    for (int j = 0; j < 64; j++) {
+        const long double e = exp2l((long double)j / 64.0L);
+        t->e2h[j] = (double)e;
+        t->e2l[j] = (double)(e - (long double)t->e2h[j]);
+    }
+    for (int j = 0; j <= 64; j++) {
+        const long double F = 1.0L + (long double)j / 64.0L;
+        const long double lf = logl(F);
+        t->lFh[j] = (double)(rintl(lf * 4398046511104.0L) / 4398046511104.0L);   // 2^42 grid
+        t->lFl[j] = (double)(lf - (long double)t->lFh[j]);
+        t->invF[j] = (double)(1.0L / F);
+    }
     for (int j = 0; j < 64; j++) {
         const double e = exp2((double)j / 64.0);
         const double c = 1.0 + ((double)j + 0.5) / 64.0;

@@ -403,6 +403,7 @@ rf_status rf_ens_set_schedule(rf_ens *e, const int *order, int n_wide)
 
 rf_status rf_ens_run(rf_ens *e, double t_end)
 {
+    rf::NvtxRange range("rf_ens_run");
     if (!e || !std::isfinite(t_end)) return efail(RF_ERR_ARG, "rf_ens_run: bad argument");
     if (!e->exec || e->graph_cluster != e->cluster || e->graph_threads != e->threads)
         if (rf_status st = build_graph(e)) return st;

@@ -1,0 +1,166 @@
+// f64m.cuh -- FP64 exp, log, log1p and expm1 for the closures of the plain
+// FP64 path, by table-driven argument reduction.
+//
+// Method: P. T. P. Tang, "Table-driven implementation of the exponential
+// function in IEEE floating-point arithmetic", ACM TOMS 15 (1989) 144-157,
+// and "Table-driven implementation of the logarithm function in IEEE
+// floating-point arithmetic", ACM TOMS 16 (1990) 378-400, with 64-entry
+// tables computed on the host in extended precision:
+//   exp(y)  = 2^M 2^(j/64) exp(r),  y = (64 M + j) ln2/64 + r, |r| <= ln2/128,
+//             exp(r) - 1 by its Taylor series to r^6 (truncation < 2^-57);
+//   log(u)  = E ln2 + log(F) + log1p(f/F),  u = 2^E m, F = 1 + j/64 nearest
+//             to m, f = m - F exact, |f/F| <= 1/128, log1p by its Taylor
+//             series to v^7 (truncation < 2^-59);
+// log1p(x) and expm1(z) reuse them with the exact corrections of 1 + x and
+// of 2^M 2^(j/64) - 1 (Sterbenz), and short Taylor series near 0.  Each
+// result is within a few units in the last place; the closures' parity
+// tests bound theta* to 1e-15 relative against the oracle's pow forms.
+//
+// The tables live in FFTables (ff.cuh) beside the double-float ones.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "ff.cuh"
+
+namespace rf {
+
+#ifdef __CUDACC__
+// ln 2 split for exact products with integers of up to 11 bits: L_HI has 42
+// significant bits.
+constexpr double F64_LN2_HI = 0.6931471805598903;      // 0x3FE62E42FEFA3800
+constexpr double F64_LN2_LO = 5.497923018708371e-14;   // ln 2 - F64_LN2_HI
+constexpr double F64_INV_LN2_64 = 92.33248261689366;   // 64 / ln 2
+constexpr double F64_LN2_64_HI = F64_LN2_HI / 64.0;    // exact (a power-of-two scaling)
+constexpr double F64_LN2_64_LO = F64_LN2_LO / 64.0;
+
+// 2^k for integer k in [-1022, 1023] from its bit pattern.
+__device__ __forceinline__ double f64_pow2i(int k)
+{
+    return __longlong_as_double((long long)(k + 1023) << 52);
+}
+
+// exp(y) for y in [-1400, 709.7]; 0 below about -745 (underflow), +inf
+// above 709.78.
+__device__ __forceinline__ double f64_exp(double y, const FFTables *__restrict__ tab)
+{
+    if (!(y < 709.782712893384)) return y != y ? y : __longlong_as_double(0x7ff0000000000000LL);
+    if (y < -745.2) return 0.0;
+    // N = nearest integer to y 64/ln2 (round-to-nearest through the 1.5 2^52 shift)
+    const double shifter = 6755399441055744.0;
+    const double t = fma(y, F64_INV_LN2_64, shifter);
+    const int n = (int)(__double_as_longlong(t) & 0xffffffffLL);
+    const double N = t - shifter;
+    const double r = fma(-N, F64_LN2_64_LO, fma(-N, F64_LN2_64_HI, y));   // |r| <= ln2/128
+    // exp(r) - 1 = r + r^2 (1/2 + r (1/6 + r (1/24 + r (1/120 + r/720))))
+    const double q = fma(r, fma(r, fma(r, fma(r, 1.0 / 720.0, 1.0 / 120.0), 1.0 / 24.0), 1.0 / 6.0), 0.5);
+    const double p = fma(r * r, q, r);
+    const int j = n & 63;
+    const int M = n >> 6;                          // arithmetic shift: floor(n / 64)
+    const double Th = tab->e2h[j], Tl = tab->e2l[j];
+    const double v = Th + fma(Th, p, Tl);          // 2^(j/64) exp(r)
+    if (M >= -1022) return v * f64_pow2i(M);
+    return (v * f64_pow2i(M + 600)) * f64_pow2i(-600);   // subnormal result
+}
+
+// log(u) for u > 0 (finite) as an unevaluated sum hi + lo (|lo| <= ulp(hi)):
+// the exact part E ln2_hi + log(F)_hi and the rest, summed once.  u <= 0 or
+// non-finite u are handled by the caller.
+__device__ __forceinline__ void f64_log_dd(double u, const FFTables *__restrict__ tab, double &hi, double &lo)
+{
+    long long b = __double_as_longlong(u);
+    int E = (int)(b >> 52) - 1023;
+    if (E == -1023) {                              // subnormal: scale into the normal range
+        b = __double_as_longlong(u * 18014398509481984.0);   // 2^54
+        E = (int)(b >> 52) - 1023 - 54;
+    }
+    const long long mant = b & 0x000fffffffffffffLL;
+    const double m = __longlong_as_double(mant | 0x3ff0000000000000LL);    // [1, 2)
+    const int j = (int)((mant + (1LL << 45)) >> 46);                       // nearest 1 + j/64, j in [0, 64]
+    const double F = 1.0 + (double)j * 0.015625;
+    const double f = m - F;                        // exact, |f| <= 1/128
+    const double v = f * tab->invF[j];
+    // log1p(v) = v + v^2 (-1/2 + v (1/3 + v (-1/4 + v (1/5 + v (-1/6 + v/7)))))
+    const double q = fma(v, fma(v, fma(v, fma(v, fma(v, 1.0 / 7.0, -1.0 / 6.0), 0.2), -0.25), 1.0 / 3.0), -0.5);
+    const double p = fma(v * v, q, v);
+    const double e = (double)E;
+    const double A = fma(e, F64_LN2_HI, tab->lFh[j]);            // exact: both on a 2^-42 grid
+    const double B = fma(e, F64_LN2_LO, tab->lFl[j]) + p;
+    hi = A + B;
+    lo = (A - hi) + B;                             // Fast2Sum (|A| >= |B| or A = 0)
+}
+
+// log(u) for u > 0 (finite); -inf at 0, NaN below.
+__device__ __forceinline__ double f64_log(double u, const FFTables *__restrict__ tab)
+{
+    if (!(u > 0.0)) return u == 0.0 ? __longlong_as_double(0xfff0000000000000LL) : __longlong_as_double(0x7ff8000000000000LL);
+    if (u == __longlong_as_double(0x7ff0000000000000LL)) return u;
+    double hi, lo;
+    f64_log_dd(u, tab, hi, lo);
+    return hi;
+}
+
+// exp(hi + lo) for |lo| <= ulp(hi): exp(hi) (1 + lo).
+__device__ __forceinline__ double f64_exp_dd(double hi, double lo, const FFTables *__restrict__ tab)
+{
+    const double e = f64_exp(hi, tab);
+    return fma(e, lo, e);
+}
+
+// log(1 + x) for x > -1 as hi + lo.
+__device__ __forceinline__ void f64_log1p_dd(double x, const FFTables *__restrict__ tab, double &hi, double &lo)
+{
+    if (fabs(x) < 0.0078125) {
+        // x - x^2/2 + ... + x^8 / 8 (truncation < 2^-63 relative)
+        const double q = fma(x, fma(x, fma(x, fma(x, fma(x, fma(x, -0.125, 1.0 / 7.0), -1.0 / 6.0), 0.2), -0.25),
+                                    1.0 / 3.0), -0.5);
+        hi = fma(x * x, q, x);
+        lo = 0.0;
+        return;
+    }
+    const double u = 1.0 + x;
+    // 1 + x = u + c exactly (c = 0 for x in [-1, 1]); log(u + c) = log u + c/u
+    // to first order (|c/u| < 2^-53); an FP32 quotient serves the correction,
+    // which falls below the last place of log u once u exceeds 1e30
+    const double c = x - (u - 1.0);
+    f64_log_dd(u, tab, hi, lo);
+    if (u < 1e30) lo += (double)((float)c * __frcp_rn((float)u));
+}
+
+__device__ __forceinline__ double f64_log1p(double x, const FFTables *__restrict__ tab)
+{
+    double hi, lo;
+    f64_log1p_dd(x, tab, hi, lo);
+    return hi + lo;
+}
+
+// exp(z) - 1 for z in [-745, 0].
+__device__ __forceinline__ double f64_expm1_neg(double z, const FFTables *__restrict__ tab)
+{
+    if (z > -0.0078125) {
+        // z + z^2/2 + ... + z^7/7! (truncation < 2^-66 relative)
+        const double q = fma(z, fma(z, fma(z, fma(z, fma(z, 1.0 / 5040.0, 1.0 / 720.0), 1.0 / 120.0), 1.0 / 24.0),
+                                    1.0 / 6.0), 0.5);
+        return fma(z * z, q, z);
+    }
+    if (z < -40.0) return -1.0 + f64_exp(z, tab);
+    const double shifter = 6755399441055744.0;
+    const double t = fma(z, F64_INV_LN2_64, shifter);
+    const int n = (int)(__double_as_longlong(t) & 0xffffffffLL);
+    const double N = t - shifter;
+    const double r = fma(-N, F64_LN2_64_LO, fma(-N, F64_LN2_64_HI, z));
+    const double q = fma(r, fma(r, fma(r, fma(r, 1.0 / 720.0, 1.0 / 120.0), 1.0 / 24.0), 1.0 / 6.0), 0.5);
+    const double p = fma(r * r, q, r);
+    const int j = n & 63;
+    const double s = f64_pow2i(n >> 6);
+    const double Th = tab->e2h[j] * s, Tl = tab->e2l[j] * s;
+    // 2^M 2^(j/64) (1 + p) - 1 = (Th - 1) + (Tl + Th p); Th - 1 is exact for Th in [1/2, 2]
+    return (Th - 1.0) + fma(Th, p, Tl);
+}
+#endif
+
+// Host: fill the FP64 tables of *t (extended-precision host arithmetic).
+void make_f64_tables(FFTables *t);
+
+}  // namespace rf

@@ -28,6 +28,10 @@ struct FFTables {
     float2 exp2j[64];   // 2^(j/64)
     float2 logc[64];    // log(c_j), c_j = 1 + (j + 1/2)/64
     float2 invc[64];    // 1/c_j
+    // FP64 tables of f64m.cuh: 2^(j/64) = e2h + e2l; log(1 + j/64) = lFh +
+    // lFl with lFh on the 2^-42 grid; invF = 1/(1 + j/64) rounded
+    double e2h[64], e2l[64];
+    double lFh[65], lFl[65], invF[65];
 };
 
 #ifdef __CUDACC__

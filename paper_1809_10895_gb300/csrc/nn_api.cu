@@ -55,6 +55,12 @@ struct rf_nn {
     long long cap_tr = 0;
     __nv_bfloat16 *tx = nullptr, *ta[5] = {}, *tu[4] = {}, *tdyb = nullptr, *tgb = nullptr;
     float *ty = nullptr, *tdy = nullptr, *tgA = nullptr, *tgB = nullptr, *tgC = nullptr;
+    // trace of the last gradient evaluation (rf_nn_set_trace): the BF16
+    // output gradient of every layer, kept as each layer's weight gradient
+    // and input gradient read it
+    bool trace = false;
+    long long trace_cap = 0, trace_M = 0;
+    __nv_bfloat16 *trace_g[nn::N_LAYERS] = {};
 
     void *dalloc(size_t bytes)
     {
@@ -284,17 +290,38 @@ rf_status loss_grad(rf_nn *n, const float *x4, const float *target, const float 
     NN_CUDA(cudaMemsetAsync(n->G, 0, sizeof(float) * n->nP, s));
     const long long MH = M * nn::C_HID;
     // output convolution
+    if (n->trace && n->trace_cap < M) {
+        for (auto &p : n->trace_g) {
+            n->dfree(p);
+            p = nullptr;
+        }
+        n->trace_cap = 0;
+        for (int l = 0; l < nn::N_LAYERS; l++)
+            if (!nalloc(n, n->trace_g[l], M * nn::C_HID))
+                return nfail(RF_ERR_NOMEM, "warm-start network: trace allocation failed");
+        n->trace_cap = M;
+    }
+    // keep the BF16 output gradient of layer l (M x channels) for the trace
+    auto keep = [&](int l, const __nv_bfloat16 *src, long long count) -> rf_status {
+        if (n->trace)
+            NN_CUDA(cudaMemcpyAsync(n->trace_g[l], src, sizeof(__nv_bfloat16) * count, cudaMemcpyDeviceToDevice, s));
+        return RF_OK;
+    };
+    n->trace_M = n->trace ? M : 0;
     nn::to_bf16(s, n->tdy, n->tdyb, M * nn::C_OUT_P);
+    NN_TRY(keep(9, n->tdyb, M * nn::C_OUT_P));
     NN_TRY(wgrad_tc(n, s, 9, n->ta[4], n->tdyb, B, D, H, W));
     NN_TRY(conv(n, s, 9, true, n->tdyb, nullptr, nullptr, n->tgA, B, D, H, W, 0));   // dL/da4
     n->launches += 2;   // mse, to_bf16
     for (int blk = 3; blk >= 0; blk--) {
         nn::relu_bwd(s, n->ta[blk + 1], n->tgA, n->tgB, MH, nullptr);                  // g2
         nn::to_bf16(s, n->tgB, n->tgb, MH);
+        NN_TRY(keep(2 + 2 * blk, n->tgb, MH));
         NN_TRY(wgrad_tc(n, s, 2 + 2 * blk, n->tu[blk], n->tgb, B, D, H, W));
         NN_TRY(conv(n, s, 2 + 2 * blk, true, n->tgb, nullptr, nullptr, n->tgA, B, D, H, W, 0));   // du
         nn::relu_bwd(s, n->tu[blk], n->tgA, n->tgC, MH, nullptr);                      // g1
         nn::to_bf16(s, n->tgC, n->tgb, MH);
+        NN_TRY(keep(1 + 2 * blk, n->tgb, MH));
         NN_TRY(wgrad_tc(n, s, 1 + 2 * blk, n->ta[blk], n->tgb, B, D, H, W));
         NN_TRY(conv(n, s, 1 + 2 * blk, true, n->tgb, nullptr, nullptr, n->tgA, B, D, H, W, 0));
         nn::add(s, n->tgA, n->tgB, MH);                                                 // + identity branch
@@ -302,6 +329,7 @@ rf_status loss_grad(rf_nn *n, const float *x4, const float *target, const float 
     }
     nn::relu_bwd(s, n->ta[0], n->tgA, n->tgC, MH, nullptr);
     nn::to_bf16(s, n->tgC, n->tgb, MH);
+    NN_TRY(keep(0, n->tgb, MH));
     NN_TRY(wgrad_tc(n, s, 0, n->tx, n->tgb, B, D, H, W));
     n->launches += 2;   // relu_bwd, to_bf16
     return RF_OK;
@@ -460,6 +488,7 @@ rf_status rf_nn_get_params(rf_nn *n, float *params, long long count)
 
 rf_status rf_nn_forward(rf_nn *n, const float *d_x, int B, int D, int H, int W, float *d_y)
 {
+    rf::NvtxRange range("rf_nn_forward");
     if (!n || !d_x || !d_y) return nfail(RF_ERR_ARG, "NULL argument");
     if (!aligned16(d_x)) return nfail(RF_ERR_ARG, "d_x must be 16-byte aligned");
     NN_TRY(check_dims(B, D, H, W));
@@ -478,6 +507,7 @@ rf_status rf_nn_forward(rf_nn *n, const float *d_x, int B, int D, int H, int W, 
 rf_status rf_nn_loss_grad(rf_nn *n, const float *d_x, const float *d_target, const float *d_mask, int B, int D,
                           int H, int W, float *loss, float *grad)
 {
+    rf::NvtxRange range("rf_nn_loss_grad");
     if (!n || !d_x || !d_target) return nfail(RF_ERR_ARG, "NULL argument");
     if (!aligned16(d_x)) return nfail(RF_ERR_ARG, "d_x must be 16-byte aligned");
     NN_TRY(check_dims(B, D, H, W));
@@ -494,6 +524,7 @@ rf_status rf_nn_loss_grad(rf_nn *n, const float *d_x, const float *d_target, con
 rf_status rf_nn_train_step(rf_nn *n, const float *d_x, const float *d_target, const float *d_mask, int B, int D,
                            int H, int W, const rf_adam *opt, float *loss)
 {
+    rf::NvtxRange range("rf_nn_train_step");
     if (!n || !d_x || !d_target || !opt) return nfail(RF_ERR_ARG, "NULL argument");
     if (!aligned16(d_x)) return nfail(RF_ERR_ARG, "d_x must be 16-byte aligned");
     if (!(opt->lr > 0) || !(opt->beta1 >= 0 && opt->beta1 < 1) || !(opt->beta2 >= 0 && opt->beta2 < 1) ||
@@ -519,5 +550,52 @@ rf_status rf_nn_train_step(rf_nn *n, const float *d_x, const float *d_target, co
 }
 
 long long rf_nn_launch_count(const rf_nn *n) { return n ? n->launches : 0; }
+
+rf_status rf_nn_set_trace(rf_nn *n, int on)
+{
+    if (!n) return nfail(RF_ERR_ARG, "NULL argument");
+    n->trace = on != 0;
+    n->trace_M = 0;
+    return RF_OK;
+}
+
+rf_status rf_nn_trace_get(rf_nn *n, int what, int index, void *host, long long count)
+{
+    if (!n || !host) return nfail(RF_ERR_ARG, "NULL argument");
+    const long long M = n->trace_M;
+    if (M < 1) return nfail(RF_ERR_STATE, "no traced gradient evaluation (rf_nn_set_trace, then rf_nn_loss_grad)");
+    const void *src = nullptr;
+    long long expect = 0;
+    size_t elem = sizeof(__nv_bfloat16);
+    switch (what) {
+    case RF_NN_TRACE_INPUT:
+        if (index != 0) break;
+        src = n->tx, expect = M * nn::C_IN_P;
+        break;
+    case RF_NN_TRACE_BLOCK_OUT:
+        if (index < 0 || index > 4) break;
+        src = n->ta[index], expect = M * nn::C_HID;
+        break;
+    case RF_NN_TRACE_BLOCK_MID:
+        if (index < 0 || index > 3) break;
+        src = n->tu[index], expect = M * nn::C_HID;
+        break;
+    case RF_NN_TRACE_OUT_GRAD:
+        if (index < 0 || index >= nn::N_LAYERS) break;
+        src = n->trace_g[index], expect = M * (index == nn::N_LAYERS - 1 ? nn::C_OUT_P : nn::C_HID);
+        break;
+    case RF_NN_TRACE_OUTPUT:
+        if (index != 0) break;
+        src = n->ty, expect = M * nn::C_OUT_P, elem = sizeof(float);
+        break;
+    default:
+        break;
+    }
+    if (!src) return nfail(RF_ERR_ARG, "rf_nn_trace_get: unknown tensor or index");
+    if (count != expect) return nfail(RF_ERR_ARG, "rf_nn_trace_get: count does not match the tensor's size");
+    NN_CUDA(cudaStreamSynchronize(n->stream));
+    NN_CUDA(cudaMemcpy(host, src, elem * (size_t)count, cudaMemcpyDeviceToHost));
+    return RF_OK;
+}
 
 }  // extern "C"

@@ -549,8 +549,12 @@ k_cg32_spmv(Grid g, Tiles tw, const float *__restrict__ z, const float *__restri
 // The FP32 stencil step with planes staged by TMA.  Per plane the block
 // copies four 72 x 10 boxes (z, p_old, K, cb) around its 64 x 8 tile into
 // shared memory with bulk tensor copies; each thread owns two x-adjacent
-// cells.  A ring of stages holds the planes below, at and above the current
-// one and the next ones in flight.  Warp 0 alone polls the copy's mbarrier
+// cells.  Each face term w (K_P + K_N)(p_P - p_N) is formed once: the face
+// between a thread's two cells serves both (with opposite signs), and the
+// face between planes k and k + 1 is formed at plane k and carried in
+// registers into plane k + 1.  A plane therefore needs only itself and the
+// plane above, so the ring of stages holds planes k and k + 1 and keeps the
+// next TMA_STAGES - 2 in flight.  Warp 0 alone polls the copy's mbarrier
 // (bounded); the others meet it at the one barrier per plane and then
 // confirm the completed phase once.  When a plane arrives each thread forms
 // p = z + beta p_old (in place of z) for its own cells and one halo cell.  A
@@ -562,13 +566,13 @@ k_cg32_spmv(Grid g, Tiles tw, const float *__restrict__ z, const float *__restri
 constexpr int TMA_WAIT_TRIES = 1 << 20;   // about a second of suspending polls
 constexpr int TMA_HALO = 2 * TY + 2 * TMA_TX;
 
-// TMA_STAGES = planes k-1, k, k+1 resident plus TMA_STAGES - 3 in flight.
+// TMA_STAGES = planes k, k+1 resident plus TMA_STAGES - 2 in flight.
 template <int TMA_STAGES>
 __global__ void __launch_bounds__(RED_THREADS)
 k_cg32_spmv_tma(Grid g, Tiles tw, const __grid_constant__ TmaMaps32 maps, int pin_sel, float *__restrict__ p_out,
                 float *__restrict__ q, double *partials, unsigned int *ticket, CgScal *sc, int *fault)
 {
-    static_assert(TMA_STAGES >= 4 && TMA_STAGES <= 8, "the ring needs planes k-1..k+1 plus one in flight");
+    static_assert(TMA_STAGES >= 3 && TMA_STAGES <= 8, "the ring needs planes k, k+1 plus one in flight");
     count_launch(g, KK_CG32_SPMV);
     if (sc->done) return;
     count_work(g, KK_CG32_SPMV);
@@ -603,6 +607,10 @@ k_cg32_spmv_tma(Grid g, Tiles tw, const __grid_constant__ TmaMaps32 maps, int pi
     uint32_t phase = 0, pending = 0;   // per stage: parity of its next completion; copy in flight
     float acc = 0.0f;
     auto ld2 = [](const float *a, int e) { return *reinterpret_cast<const float2 *>(a + e); };
+    // face term of cell P towards cell N, zero unless the face exists and both are active
+    auto face = [](bool in, float kP, float pP, float kN, float pN, float w) -> float {
+        return (in && kP >= 0.0f && kN >= 0.0f) ? (w * (kP + kN)) * (pP - pN) : 0.0f;
+    };
     for (long long item = blockIdx.x; item < tw.items && !s_timeout; item += gridDim.x) {
         const TileItem it = tile_item(g, tw, item);
         const int i = it.i0 + 2 * tx, j = it.j0 + ty;      // first cell of the pair (nx is even)
@@ -650,60 +658,55 @@ k_cg32_spmv_tma(Grid g, Tiles tw, const __grid_constant__ TmaMaps32 maps, int pi
             }
         };
         auto next = [](int st) { return st + 1 == TMA_STAGES ? 0 : st + 1; };
-        for (int L = 0; L < TMA_STAGES - 1; L++) issue(it.k0 - 1 + L, L);
+        for (int L = 0; L < TMA_STAGES; L++) issue(it.k0 - 1 + L, L);
         if (!(poll(0) && poll(1))) s_timeout = 1;
         __syncthreads();
         if (s_timeout) break;
         take(it.k0 - 1, 0);
         take(it.k0, 1);
-        // stages of planes k-1, k, k+1 and of plane k + TMA_STAGES - 2 (copied into the stage of k-2)
-        int s_m = 0, s_c = 1, s_p = 2, s_i = TMA_STAGES - 1;
+        // the bottom-face term of plane k0 (from plane k0 - 1, staged for
+        // this only); later planes receive it from the plane below
+        float2 carry = make_float2(0.0f, 0.0f);
+        if (inside && it.k0 > 0) {
+            const float2 kc = ld2(sbuf[1][2], idx), pc = ld2(sbuf[1][0], idx);
+            const float2 kb = ld2(sbuf[0][2], idx), pb = ld2(sbuf[0][0], idx);
+            carry.x = face(true, kc.x, pc.x, kb.x, pb.x, wz);
+            carry.y = face(true, kc.y, pc.y, kb.y, pb.y, wz);
+        }
+        // stages of planes k and k + 1, and the one plane k - 1 held (refilled with plane k + TMA_STAGES - 1)
+        int s_c = 1, s_p = 2 % TMA_STAGES, s_i = 0;
         long long c = i + (long long)g.nx * j + g.sxy * it.k0;
         for (int k = it.k0; k < it.k1; k++, c += g.sxy) {
             if (!poll(s_p)) s_timeout = 1;
-            __syncthreads();              // plane k+1 landed; plane k-2 is no longer read
+            __syncthreads();              // plane k+1 landed; plane k-1 is no longer read
             if (s_timeout) break;
-            issue(k + TMA_STAGES - 2, s_i);
+            issue(k + TMA_STAGES - 1, s_i);
             take(k + 1, s_p);
             if (inside) {
                 const float *P0 = sbuf[s_c][0], *K0 = sbuf[s_c][2];
                 const float2 kc = ld2(K0, idx), pc = ld2(P0, idx), cb = ld2(sbuf[s_c][3], idx);
                 const float2 kym = ld2(K0, idx - TMA_BX), pym = ld2(P0, idx - TMA_BX);
                 const float2 kyp = ld2(K0, idx + TMA_BX), pyp = ld2(P0, idx + TMA_BX);
-                const float2 kzm = ld2(sbuf[s_m][2], idx), pzm = ld2(sbuf[s_m][0], idx);
                 const float2 kzp = ld2(sbuf[s_p][2], idx), pzp = ld2(sbuf[s_p][0], idx);
-                // (A p)_P = cb_P p_P + sum_f w_f (K_P + K_N)/2 (p_P - p_N), faces -x +x -y +y -z +z
-                auto cell = [&](float kP, float pP, float cbP, bool inxm, float kxm, float pxm, bool inxp, float kxp,
-                                float pxp, float kym_, float pym_, float kyp_, float pyp_, float kzm_, float pzm_,
-                                float kzp_, float pzp_, float &pout, float &qout) {
-                    if (!(kP >= 0.0f)) {
-                        pout = 0.0f;
-                        qout = 0.0f;
-                        return;
-                    }
-                    float qp = cbP * pP;
-                    auto face = [&](bool in, float KN, float vN, float w) {
-                        if (in && KN >= 0.0f) qp = fmaf(w * (kP + KN), pP - vN, qp);
-                    };
-                    face(inxm, kxm, pxm, wx);
-                    face(inxp, kxp, pxp, wx);
-                    face(fym, kym_, pym_, wy);
-                    face(fyp, kyp_, pyp_, wy);
-                    face(k > 0, kzm_, pzm_, wz);
-                    face(k < g.nz - 1, kzp_, pzp_, wz);
-                    pout = pP;
-                    qout = qp;
-                    acc = fmaf(pP, qp, acc);
-                };
-                float2 po, qo;
-                cell(kc.x, pc.x, cb.x, fxm, K0[idx - 1], P0[idx - 1], true, kc.y, pc.y, kym.x, pym.x, kyp.x, pyp.x,
-                     kzm.x, pzm.x, kzp.x, pzp.x, po.x, qo.x);
-                cell(kc.y, pc.y, cb.y, true, kc.x, pc.x, fxp, K0[idx + 2], P0[idx + 2], kym.y, pym.y, kyp.y, pyp.y,
-                     kzm.y, pzm.y, kzp.y, pzp.y, po.y, qo.y);
+                const bool top = k < g.nz - 1;
+                // (A p)_P = cb_P p_P + sum_f w_f (K_P + K_N)/2 (p_P - p_N)
+                const float t01 = face(true, kc.x, pc.x, kc.y, pc.y, wx);           // between the pair
+                const float tzx = face(top, kc.x, pc.x, kzp.x, pzp.x, wz);          // top faces
+                const float tzy = face(top, kc.y, pc.y, kzp.y, pzp.y, wz);
+                float q0 = fmaf(cb.x, pc.x, carry.x) + t01 + tzx;
+                float q1 = fmaf(cb.y, pc.y, carry.y) - t01 + tzy;
+                q0 += face(fxm, kc.x, pc.x, K0[idx - 1], P0[idx - 1], wx);
+                q1 += face(fxp, kc.y, pc.y, K0[idx + 2], P0[idx + 2], wx);
+                q0 += face(fym, kc.x, pc.x, kym.x, pym.x, wy) + face(fyp, kc.x, pc.x, kyp.x, pyp.x, wy);
+                q1 += face(fym, kc.y, pc.y, kym.y, pym.y, wy) + face(fyp, kc.y, pc.y, kyp.y, pyp.y, wy);
+                carry = make_float2(-tzx, -tzy);
+                const bool a0 = kc.x >= 0.0f, a1 = kc.y >= 0.0f;
+                const float2 po = make_float2(a0 ? pc.x : 0.0f, a1 ? pc.y : 0.0f);
+                const float2 qo = make_float2(a0 ? q0 : 0.0f, a1 ? q1 : 0.0f);
+                acc = fmaf(po.x, qo.x, fmaf(po.y, qo.y, acc));
                 *reinterpret_cast<float2 *>(p_out + c) = po;
                 *reinterpret_cast<float2 *>(q + c) = qo;
             }
-            s_m = s_c;
             s_c = s_p;
             s_p = next(s_p);
             s_i = next(s_i);

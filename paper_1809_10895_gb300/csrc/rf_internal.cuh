@@ -5,10 +5,21 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <nvtx3/nvToolsExt.h>
+
 #include "ff.cuh"
 #include "tma.cuh"
 
 namespace rf {
+
+// An NVTX range over a host scope (visible to profilers that record NVTX;
+// NVTX 3 is header-only and costs next to nothing when no tool is attached).
+struct NvtxRange {
+    explicit NvtxRange(const char *name) { nvtxRangePushA(name); }
+    ~NvtxRange() { nvtxRangePop(); }
+    NvtxRange(const NvtxRange &) = delete;
+    NvtxRange &operator=(const NvtxRange &) = delete;
+};
 
 // Face order used everywhere: 0 -x, 1 +x, 2 -y, 3 +y, 4 -z (bottom), 5 +z (top).
 enum { F_XMIN = 0, F_XMAX, F_YMIN, F_YMAX, F_ZMIN, F_ZMAX };

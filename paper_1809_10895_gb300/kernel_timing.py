@@ -4,6 +4,8 @@ network), for profiling one kernel at a time.
 
     python -m paper_1809_10895_gb300.kernel_timing box --kinds assemble,resid64
     python -m paper_1809_10895_gb300.kernel_timing watershed --nx 512 --ny 256 --kinds cg32_spmv
+    python -m paper_1809_10895_gb300.kernel_timing watershed --nx 512 --ny 256 --precision fp64 --t-start 11 \
+        --kinds closure,assemble,cg64_spmv,cg64_update
     python -m paper_1809_10895_gb300.kernel_timing network --nx 128 --ny 128 --nz 64
     python -m paper_1809_10895_gb300.kernel_timing training --nx 128 --ny 128 --nz 64
     python -m paper_1809_10895_gb300.kernel_timing ensemble --instances 64 --window 10 --cluster 4
@@ -31,6 +33,8 @@ def main(argv=None):
     ap.add_argument("--nz", type=int, default=64)
     ap.add_argument("--kinds", default="assemble,closure,resid64,cg32_spmv,cg32_update")
     ap.add_argument("--steps", type=int, default=5, help="accepted steps before timing (box)")
+    ap.add_argument("--t-start", type=float, default=0.0,
+                    help="watershed: simulated hours run before timing (11: the first storm of seed 0)")
     ap.add_argument("--reps", type=int, default=24)
     ap.add_argument("--precision", default="mixed")
     ap.add_argument("--instances", type=int, default=64, help="ensemble instances")
@@ -108,6 +112,8 @@ def main(argv=None):
         if a.workload == "box":
             for _ in range(a.steps):
                 s.step()
+        elif a.t_start > 0:
+            s.run(a.t_start * 3600.0)
         out.update(cells=case.N, active=case.n_active(), kernels={})
         for k in a.kinds.split(","):
             ms, by = s.profile_kernel(k, reps=a.reps)

@@ -163,6 +163,8 @@ SIGNATURES = {
     "rf_nn_train_step": (C.c_int, [_VP, _VP, _VP, _VP, C.c_int, C.c_int, C.c_int, C.c_int, C.POINTER(rf_adam),
                                    C.POINTER(C.c_float)]),
     "rf_nn_launch_count": (C.c_longlong, [_VP]),
+    "rf_nn_set_trace": (C.c_int, [_VP, C.c_int]),
+    "rf_nn_trace_get": (C.c_int, [_VP, C.c_int, C.c_int, _VP, C.c_longlong]),
     "rf_ws_features": (C.c_int, [_VP, C.POINTER(rf_ws_scales), _VP, C.c_double, C.c_double, _VP]),
     "rf_ws_target": (C.c_int, [_VP, C.POINTER(rf_ws_scales), _VP, C.c_double, _VP, _VP]),
     "rf_ws_attach": (C.c_int, [_VP, _VP, C.POINTER(rf_ws_scales)]),
@@ -170,6 +172,7 @@ SIGNATURES = {
 }
 NOALLOC_MAX_CELLS = 65536
 NN_PARAMS = 225793
+NN_LAYERS = 10
 COUNTER_KINDS = ("closure", "closure_picard", "assemble", "cg64_init", "cg64_spmv", "cg64_update", "apply64",
                  "mixed_start", "resid64", "cg32_spmv", "cg32_update", "add_correction", "mass_balance",
                  "storage", "accept")
@@ -523,6 +526,26 @@ class Network:
 
     def launch_count(self) -> int:
         return int(load().rf_nn_launch_count(self.handle))
+
+    def set_trace(self, on: bool = True):
+        _check(load().rf_nn_set_trace(self.handle, 1 if on else 0), "rf_nn_set_trace")
+
+    TRACE = {"input": (0, 8, "bf16"), "block_out": (1, 32, "bf16"), "block_mid": (2, 32, "bf16"),
+             "out_grad": (3, 32, "bf16"), "output": (4, 8, "f32")}
+
+    def trace_get(self, what: str, index: int, shape):
+        """A stored tensor of the last traced gradient evaluation as float64,
+        shape (B, D, H, W, channels)."""
+        code, ch, kind = self.TRACE[what]
+        if what == "out_grad" and index == NN_LAYERS - 1:
+            ch = 8
+        M = int(np.prod(shape))
+        buf = np.empty(M * ch, dtype=np.uint16 if kind == "bf16" else np.float32)
+        _check(load().rf_nn_trace_get(self.handle, code, int(index), buf.ctypes.data_as(_VP), buf.size),
+               "rf_nn_trace_get")
+        if kind == "bf16":
+            buf = (buf.astype(np.uint32) << 16).view(np.float32)
+        return buf.astype(np.float64).reshape(tuple(shape) + (ch,))
 
 
 class Ensemble:

@@ -49,9 +49,12 @@ def _run_pair(case, t_end, **over):
     return s, o, sg, so
 
 
-def _check(case, s, o, sg, so, tol, closure=1e-9):
+def _check(case, s, o, sg, so, tol, closure=1e-9, dt_rtol=0.0):
     assert len(sg) == len(so) and len(sg) > 3
-    assert np.array_equal([a.dt for a in sg], [b.dt for b in so])
+    if dt_rtol == 0.0:
+        assert np.array_equal([a.dt for a in sg], [b.dt for b in so])
+    else:
+        np.testing.assert_allclose([a.dt for a in sg], [b.dt for b in so], rtol=dt_rtol, atol=0)
     assert [a.picard for a in sg] == [b.picard for b in so]
     assert [a.rejected for a in sg] == [b.rejected for b in so]
     hg, _ = s.get_state()
@@ -125,9 +128,13 @@ def test_bdf2_time_scheme(precision, tol):
 
 
 def test_richardson_time_control():
+    # the next dt is a continuous function of the error estimate, a difference
+    # of two solutions each known to the CG tolerance: GPU and oracle agree on
+    # it to about 1e-7 relative, not bit for bit as under EBATS's discrete
+    # factors; Picard counts and reruns stay identical
     case = _small_box(seed=13, time_control=1, tol_time=2e-3)
     s, o, sg, so = _run_pair(case, case.t_end)
-    _check(case, s, o, sg, so, TOL_PLAIN)
+    _check(case, s, o, sg, so, TOL_PLAIN, dt_rtol=1e-5)
     # the controller moved dt (neither EBATS' sequence nor a constant)
     dts = [x.dt for x in sg]
     assert len(set(np.round(dts, 9))) > 3
