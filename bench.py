@@ -64,7 +64,8 @@ def parse():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-full-period", action="store_true", help="skip the 30-day time-to-solution legs")
     ap.add_argument("--no-ensemble", action="store_true", help="skip the batched-ensemble leg")
-    ap.add_argument("--ensemble-window", type=float, default=2 * 86400.0, help="simulated seconds of the ensemble leg")
+    ap.add_argument("--ensemble-window", type=float, default=600.0,
+                    help="simulated seconds of the ensemble leg (172800: its whole 2 days, about 4.5 min)")
     ap.add_argument("--no-warmstart", action="store_true", help="skip the learned warm-start leg")
     ap.add_argument("--no-configs", action="store_true", help="skip the column and box legs")
     ap.add_argument("--ws-train-size", type=int, default=128, help="nx = ny of the training box (nz = 64)")
@@ -253,26 +254,38 @@ def job_value(units_per_rank, world, t_max):
     return world * units_per_rank / t_max
 
 
+PROFILE_JSON = os.path.join(ROOT, "profiles", "ncu_watershed_kernels.json")
+
+
+def sources_sha(files):
+    """SHA-256 (16 hex digits) of the concatenated kernel sources."""
+    h = hashlib.sha256()
+    for f in files:
+        h.update(open(os.path.join(ROOT, "paper_1809_10895_gb300", "csrc", f), "rb").read())
+    return h.hexdigest()[:16]
+
+
 def profile_entry(kernel):
-    """The committed ncu summary of a kernel; None when absent or taken on a
-    different kernel source."""
-    p = os.path.join(ROOT, "profiles", "ncu_traffic.json")
+    """The committed ncu summary of a kernel (DRAM bytes and FP64 arithmetic
+    per launch on the watershed); None when absent or taken on different
+    kernel sources (the .cu file and the headers holding its arithmetic)
+    than the ones built now."""
     try:
-        d = json.load(open(p))
+        d = json.load(open(PROFILE_JSON))
         e = d["kernels"][kernel]
-        src = open(os.path.join(ROOT, "paper_1809_10895_gb300", "csrc", e["source"]), "rb").read()
-        if hashlib.sha256(src).hexdigest()[:16] != e["source_sha"]:
+        if sources_sha(e["sources"]) != e["sources_sha"]:
             return None
         return e
     except Exception:
         return None
 
 
-def traffic_for(kernel, cells):
+def traffic_for(kernel, active_cells):
     """DRAM bytes per launch from the committed ncu summary, scaled to this
-    workload's cells."""
+    workload's active cells (the captured grid is a smaller slice of the
+    same watershed)."""
     e = profile_entry(kernel)
-    return None if e is None else e["dram_bytes_per_launch"] * cells / e["cells"]
+    return None if e is None else e["dram_bytes_per_launch"] * active_cells / e["active_cells"]
 
 
 def storm_start(case, min_hours=7.0):
@@ -288,17 +301,9 @@ def storm_start(case, min_hours=7.0):
 
 def fp64_counts(kernel):
     """FP64 arithmetic instructions per active cell of a kernel from the
-    committed ncu summary (None when absent or taken on another source)."""
-    p = os.path.join(ROOT, "profiles", "ncu_fp64_counts.json")
-    try:
-        d = json.load(open(p))
-        e = d["kernels"][kernel]
-        src = open(os.path.join(ROOT, "paper_1809_10895_gb300", "csrc", e["source"]), "rb").read()
-        if hashlib.sha256(src).hexdigest()[:16] != e["source_sha"]:
-            return None
-        return e
-    except Exception:
-        return None
+    committed ncu summary (None when absent or stale)."""
+    e = profile_entry(kernel)
+    return e if e and e.get("fp64_inst_per_cell") else None
 
 
 def native(args):
@@ -460,6 +465,7 @@ def native(args):
                                 share_of_window=est[k] / ms64) for k, v in kern64.items()}
     kernels_mix = None
     if s_mix is not None:
+        names["closure"] = "k_closure_picard_df"      # the mixed path's double-float closures
         km = kernel_table(s_mix, ("closure", "assemble", "resid64", "cg32_spmv", "cg32_update"))
         wm = {"closure": counts_mix["closure_picard"][1] + counts_mix["closure"][1],
               "assemble": counts_mix["assemble"][1], "resid64": counts_mix["resid64"][1],

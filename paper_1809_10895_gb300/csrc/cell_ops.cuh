@@ -83,19 +83,32 @@ __device__ __forceinline__ void closure_vg_fp64(const DevSoil &s, double Ks, dou
     const double nh = s.n * Lh;
     const double nl = fma(s.n, Lh, -nh) + s.n * Ll;
     if (nh > 700.0) {
-        th = s.theta_r + dth * f64_exp(-s.m * nh, tab);
+        th = s.theta_r + dth * f64_exp_nc(fmax(-s.m * nh, -700.0), tab);
         K = 0.0;
         C = 0.0;
         return;
     }
-    const double x = f64_exp_dd(nh, nl, tab);
+    // x = u^n; below e^-700 it is 0 to double precision beside 1 (Se = 1)
+    const double x = nh >= -700.0 ? f64_exp_dd(nh, nl, tab) : 0.0;
+    const double onepx = 1.0 + x;
+    const double w = rcp64(onepx);
     double l1h, l1l;
-    f64_log1p_dd(x, tab, l1h, l1l);
-    const double sh = -s.m * l1h;
+    if (x >= 0.0078125) f64_log1p_big_dd(x, onepx, w, tab, l1h, l1l);
+    else f64_log1p_dd(x, tab, l1h, l1l);
+    const double sh = -s.m * l1h;                  // in [-700 m, 0]
     const double se = f64_exp_dd(sh, fma(-s.m, l1h, -sh) - s.m * l1l, tab);
-    const double w = rcp64(1.0 + x);
     const double ys = u >= 1e-30 ? (x * rcp64(u)) * se : f64_exp(s.m * ((nh - l1h) + (nl - l1l)), tab);
-    const double omy = ys <= 0.5 ? 1.0 - ys : -f64_expm1_neg(s.m * f64_log1p(-w, tab), tab);
+    double omy;
+    if (ys <= 0.5) {
+        omy = 1.0 - ys;
+    } else {
+        // 1 - ys = -expm1(m log(1 - w)), log(1 - w) = log(x/(1+x)) = n L - l1:
+        // l1 inherits the rounding of x (about 1e-16 absolute), so the
+        // difference of the two double-doubles serves only while |n L - l1| >
+        // log(3/2), i.e. x < 2; beyond, log1p(-w)
+        const double lw = x < 2.0 ? (nh - l1h) + (nl - l1l) : f64_log1p(-w, tab);
+        omy = -f64_expm1_neg(s.m * lw, tab);
+    }
     th = s.theta_r + dth * se;
     K = Ks * sqrt(se) * (omy * omy);
     C = s.cfac * (ys * w);

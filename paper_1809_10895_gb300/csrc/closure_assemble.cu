@@ -108,8 +108,9 @@ k_closure_picard(Grid g, const DevSoil *__restrict__ soils, const uint8_t *__res
 //   imposed flux, free drainage -K(h^k) A_z, seepage as Dirichlet 0 while the
 //   cell is saturated at the step start).
 // Outputs: c, b, upper-face coefficients Tx/Ty/Tz (0 where the face is not an
-// interior face), diag(A), 1/diag; FP32 copies of K and of c plus the
-// Dirichlet diagonal terms for the mixed-precision operator.
+// interior face), diag(A), 1/diag; FP32 copies of K (NaN on inactive cells,
+// so that max(w (K_P + K_N), 0) closes their faces without a test) and of c
+// plus the Dirichlet diagonal terms for the mixed-precision operator.
 template <int MODE>
 __global__ void __launch_bounds__(RED_THREADS)
 k_assemble(Grid g, const DevSoil *__restrict__ soils, const uint8_t *__restrict__ zone,
@@ -146,7 +147,7 @@ k_assemble(Grid g, const DevSoil *__restrict__ soils, const uint8_t *__restrict_
         if (!(fl & FLAG_ACTIVE)) {
             c_out[p] = 0.0; b[p] = 0.0; Tx[p] = 0.0; Ty[p] = 0.0; Tz[p] = 0.0;
             diag_out[p] = 0.0; dinv[p] = 0.0;
-            K32[p] = -1.0f; cb32[p] = 0.0f; dinv32[p] = 0.0f;
+            K32[p] = __int_as_float(0x7fc00000); cb32[p] = 0.0f; dinv32[p] = 0.0f;   // NaN: fails every K >= 0 test
             if (MODE != ASM_ONLY) st.x[p] = hk[p];
             if (MODE == ASM_CG64) { st.r[p] = 0.0; st.z[p] = 0.0; }
             if (MODE == ASM_MIXED) { st.r32[p] = 0.0f; st.z32[p] = 0.0f; st.d32[p] = 0.0f; }
@@ -293,6 +294,38 @@ k_accept(Grid g, const double *__restrict__ xf, double *__restrict__ h, const do
         thn[p] = thk[p];
         if (copyK) K0[p] = K1[p];
     }
+}
+
+// Check of a state uploaded into src: the number of active cells whose head
+// is not finite (res->nonfinite); then, only when there is none, the commit
+// dst = src with non-finite values on inactive cells replaced by 0.
+__global__ void __launch_bounds__(RED_THREADS)
+k_state_check(Grid g, const uint8_t *__restrict__ flags, const double *__restrict__ src, double *partials,
+              unsigned int *ticket, StepResults *res)
+{
+    double v[1] = {0.0};
+    const long long stride = (long long)gridDim.x * blockDim.x;
+    for (long long p = (long long)blockIdx.x * blockDim.x + threadIdx.x; p < g.N; p += stride)
+        if ((flags[p] & FLAG_ACTIVE) && !isfinite(src[p])) v[0] += 1.0;
+    if (grid_reduce<OpSum, 1>(v, partials, ticket) && threadIdx.x == 0) res->nonfinite = v[0] > 0.0;
+}
+
+__global__ void __launch_bounds__(RED_THREADS)
+k_state_commit(Grid g, const double *__restrict__ src, double *__restrict__ dst, const StepResults *res)
+{
+    if (res->nonfinite) return;
+    const long long stride = (long long)gridDim.x * blockDim.x;
+    for (long long p = (long long)blockIdx.x * blockDim.x + threadIdx.x; p < g.N; p += stride) {
+        const double v = src[p];
+        dst[p] = isfinite(v) ? v : 0.0;
+    }
+}
+
+void launch_state_check_commit(cudaStream_t s, int nblk, const Grid &g, const uint8_t *flags, const double *src,
+                               double *dst, double *partials, unsigned int *ticket, StepResults *res)
+{
+    k_state_check<<<nblk, RED_THREADS, 0, s>>>(g, flags, src, partials, ticket, res);
+    k_state_commit<<<nblk, RED_THREADS, 0, s>>>(g, src, dst, res);
 }
 
 // Both precisions' tables: the double-float ones from double arithmetic,

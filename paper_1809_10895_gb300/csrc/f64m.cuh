@@ -41,6 +41,21 @@ __device__ __forceinline__ double f64_pow2i(int k)
     return __longlong_as_double((long long)(k + 1023) << 52);
 }
 
+// exp(y) for y in [-708, 709] (normal results; the caller keeps y there).
+__device__ __forceinline__ double f64_exp_nc(double y, const FFTables *__restrict__ tab)
+{
+    const double shifter = 6755399441055744.0;
+    const double t = fma(y, F64_INV_LN2_64, shifter);
+    const int n = (int)(__double_as_longlong(t) & 0xffffffffLL);
+    const double N = t - shifter;
+    const double r = fma(-N, F64_LN2_64_LO, fma(-N, F64_LN2_64_HI, y));   // |r| <= ln2/128
+    const double q = fma(r, fma(r, fma(r, fma(r, 1.0 / 720.0, 1.0 / 120.0), 1.0 / 24.0), 1.0 / 6.0), 0.5);
+    const double p = fma(r * r, q, r);
+    const int j = n & 63;
+    const double Th = tab->e2h[j], Tl = tab->e2l[j];
+    return (Th + fma(Th, p, Tl)) * f64_pow2i(n >> 6);
+}
+
 // exp(y) for y in [-1400, 709.7]; 0 below about -745 (underflow), +inf
 // above 709.78.
 __device__ __forceinline__ double f64_exp(double y, const FFTables *__restrict__ tab)
@@ -78,7 +93,7 @@ __device__ __forceinline__ void f64_log_dd(double u, const FFTables *__restrict_
     const long long mant = b & 0x000fffffffffffffLL;
     const double m = __longlong_as_double(mant | 0x3ff0000000000000LL);    // [1, 2)
     const int j = (int)((mant + (1LL << 45)) >> 46);                       // nearest 1 + j/64, j in [0, 64]
-    const double F = 1.0 + (double)j * 0.015625;
+    const double F = __longlong_as_double(0x3ff0000000000000LL + ((long long)j << 46));   // 1 + j/64 (2 at j = 64)
     const double f = m - F;                        // exact, |f| <= 1/128
     const double v = f * tab->invF[j];
     // log1p(v) = v + v^2 (-1/2 + v (1/3 + v (-1/4 + v (1/5 + v (-1/6 + v/7)))))
@@ -101,11 +116,22 @@ __device__ __forceinline__ double f64_log(double u, const FFTables *__restrict__
     return hi;
 }
 
-// exp(hi + lo) for |lo| <= ulp(hi): exp(hi) (1 + lo).
+// exp(hi + lo) for |lo| <= ulp(hi) and hi in [-708, 709]: exp(hi) (1 + lo).
 __device__ __forceinline__ double f64_exp_dd(double hi, double lo, const FFTables *__restrict__ tab)
 {
-    const double e = f64_exp(hi, tab);
+    const double e = f64_exp_nc(hi, tab);
     return fma(e, lo, e);
+}
+
+// log(1 + x) for x >= 2^-7 as hi + lo, given u = 1 + x (rounded) and an
+// approximation rinv of 1/u (a few units in the last place suffice: it only
+// scales the correction c/u, |c/u| < 2^-53).
+__device__ __forceinline__ void f64_log1p_big_dd(double x, double u, double rinv, const FFTables *__restrict__ tab,
+                                                 double &hi, double &lo)
+{
+    const double c = x - (u - 1.0);               // 1 + x = u + c exactly
+    f64_log_dd(u, tab, hi, lo);
+    lo = fma(c, rinv, lo);
 }
 
 // log(1 + x) for x > -1 as hi + lo.
@@ -144,7 +170,7 @@ __device__ __forceinline__ double f64_expm1_neg(double z, const FFTables *__rest
                                     1.0 / 6.0), 0.5);
         return fma(z * z, q, z);
     }
-    if (z < -40.0) return -1.0 + f64_exp(z, tab);
+    if (z < -40.0) return -1.0 + f64_exp_nc(fmax(z, -700.0), tab);
     const double shifter = 6755399441055744.0;
     const double t = fma(z, F64_INV_LN2_64, shifter);
     const int n = (int)(__double_as_longlong(t) & 0xffffffffLL);

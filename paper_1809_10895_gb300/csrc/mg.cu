@@ -55,7 +55,7 @@ __device__ __forceinline__ float face_T(const MgLevel &L, const float *__restric
     if (!in) return 0.0f;
     if (L.level == 0) {
         const float KP = K32[p], KN = K32[q];
-        if (KP < 0.0f || KN < 0.0f) return 0.0f;
+        if (!(KP >= 0.0f) || !(KN >= 0.0f)) return 0.0f;   // inactive cells carry K = NaN
         return L.w32[f >> 1] * 0.5f * (KP + KN);
     }
     const float *T = L.T[f >> 1];

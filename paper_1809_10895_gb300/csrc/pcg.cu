@@ -567,8 +567,10 @@ constexpr int TMA_WAIT_TRIES = 1 << 20;   // about a second of suspending polls
 constexpr int TMA_HALO = 2 * TY + 2 * TMA_TX;
 
 // TMA_STAGES = planes k, k+1 resident plus TMA_STAGES - 2 in flight.
+// Five blocks per SM: 4 stages of 3 x 2944 + 2048 bytes (cb is staged for
+// the tile's own cells only) fit 217 KB, and at most 51 registers a thread.
 template <int TMA_STAGES>
-__global__ void __launch_bounds__(RED_THREADS)
+__global__ void __launch_bounds__(RED_THREADS, 5)
 k_cg32_spmv_tma(Grid g, Tiles tw, const __grid_constant__ TmaMaps32 maps, int pin_sel, float *__restrict__ p_out,
                 float *__restrict__ q, double *partials, unsigned int *ticket, CgScal *sc, int *fault)
 {
@@ -579,7 +581,9 @@ k_cg32_spmv_tma(Grid g, Tiles tw, const __grid_constant__ TmaMaps32 maps, int pi
     const float beta = (float)sc->beta;
     const bool first = sc->iter == 0;
     constexpr int SLOT = TMA_SLOT_BYTES / 4;
-    __shared__ __align__(128) float sbuf[TMA_STAGES][4][SLOT];   // z (then p), p_old, K, cb
+    constexpr int OWN = TMA_OWN_BYTES / 4;
+    __shared__ __align__(128) float sbuf[TMA_STAGES][3][SLOT];   // z (then p), p_old, K around the tile
+    __shared__ __align__(128) float cbuf[TMA_STAGES][OWN];       // cb of the tile's own cells
     __shared__ __align__(8) uint64_t bar[TMA_STAGES];
     __shared__ int s_timeout;
     const CUtensorMap *mp = pin_sel ? &maps.p1 : &maps.p0;
@@ -589,10 +593,11 @@ k_cg32_spmv_tma(Grid g, Tiles tw, const __grid_constant__ TmaMaps32 maps, int pi
         s_timeout = 0;
     }
     __syncthreads();
-    const uint32_t tx_bytes = (first ? 3 : 4) * TMA_BOX_BYTES;
+    const uint32_t tx_bytes = (first ? 2 : 3) * TMA_BOX_BYTES + TMA_OWN_BYTES;
     const int tx = threadIdx.x % 32, ty = threadIdx.x / 32;
     const bool poller = threadIdx.x < 32;
     const int idx = (ty + 1) * TMA_BX + 2 * tx + TMA_X0;   // even: the pair is one float2
+    const int oidx = ty * TMA_TX + 2 * tx;                 // the pair in the own-cell box
     int hidx = -1;                       // the x/y halo cell this thread converts
     if (threadIdx.x < TMA_HALO) {
         const int h = threadIdx.x;
@@ -607,15 +612,17 @@ k_cg32_spmv_tma(Grid g, Tiles tw, const __grid_constant__ TmaMaps32 maps, int pi
     uint32_t phase = 0, pending = 0;   // per stage: parity of its next completion; copy in flight
     float acc = 0.0f;
     auto ld2 = [](const float *a, int e) { return *reinterpret_cast<const float2 *>(a + e); };
-    // face term of cell P towards cell N, zero unless the face exists and both are active
-    auto face = [](bool in, float kP, float pP, float kN, float pN, float w) -> float {
-        return (in && kP >= 0.0f && kN >= 0.0f) ? (w * (kP + kN)) * (pP - pN) : 0.0f;
+    // face term of cell P towards cell N.  Inactive cells carry K = NaN and
+    // the K boxes read NaN outside the grid (their p reads 0), so
+    // max(w (K_P + K_N), 0) is the face coefficient where both cells are
+    // active and 0 where either is not (IEEE max returns the non-NaN operand)
+    auto face = [](float kP, float pP, float kN, float pN, float w) -> float {
+        return fmaxf(w * (kP + kN), 0.0f) * (pP - pN);
     };
     for (long long item = blockIdx.x; item < tw.items && !s_timeout; item += gridDim.x) {
         const TileItem it = tile_item(g, tw, item);
         const int i = it.i0 + 2 * tx, j = it.j0 + ty;      // first cell of the pair (nx is even)
         const bool inside = i < g.nx && j < g.ny;
-        const bool fxm = i > 0, fxp = i + 2 < g.nx, fym = j > 0, fyp = j < g.ny - 1;
         // plane kk = it.k0 - 1 + L goes to stage L % TMA_STAGES (stage
         // indices advance incrementally); planes outside the grid are neither
         // copied nor read
@@ -629,7 +636,7 @@ k_cg32_spmv_tma(Grid g, Tiles tw, const __grid_constant__ TmaMaps32 maps, int pi
                 tma_load_3d(sbuf[st][0], &maps.z, &bar[st], x, y, kk);
                 if (!first) tma_load_3d(sbuf[st][1], mp, &bar[st], x, y, kk);
                 tma_load_3d(sbuf[st][2], &maps.K, &bar[st], x, y, kk);
-                tma_load_3d(sbuf[st][3], &maps.cb, &bar[st], x, y, kk);
+                tma_load_3d(cbuf[st], &maps.cb, &bar[st], it.i0, it.j0, kk);
             }
         };
         // warp 0: poll stage st (bounded); false when the wait ran out.  The
@@ -670,8 +677,8 @@ k_cg32_spmv_tma(Grid g, Tiles tw, const __grid_constant__ TmaMaps32 maps, int pi
         if (inside && it.k0 > 0) {
             const float2 kc = ld2(sbuf[1][2], idx), pc = ld2(sbuf[1][0], idx);
             const float2 kb = ld2(sbuf[0][2], idx), pb = ld2(sbuf[0][0], idx);
-            carry.x = face(true, kc.x, pc.x, kb.x, pb.x, wz);
-            carry.y = face(true, kc.y, pc.y, kb.y, pb.y, wz);
+            carry.x = face(kc.x, pc.x, kb.x, pb.x, wz);
+            carry.y = face(kc.y, pc.y, kb.y, pb.y, wz);
         }
         // stages of planes k and k + 1, and the one plane k - 1 held (refilled with plane k + TMA_STAGES - 1)
         int s_c = 1, s_p = 2 % TMA_STAGES, s_i = 0;
@@ -684,21 +691,24 @@ k_cg32_spmv_tma(Grid g, Tiles tw, const __grid_constant__ TmaMaps32 maps, int pi
             take(k + 1, s_p);
             if (inside) {
                 const float *P0 = sbuf[s_c][0], *K0 = sbuf[s_c][2];
-                const float2 kc = ld2(K0, idx), pc = ld2(P0, idx), cb = ld2(sbuf[s_c][3], idx);
+                const float2 kc = ld2(K0, idx), pc = ld2(P0, idx), cb = ld2(cbuf[s_c], oidx);
                 const float2 kym = ld2(K0, idx - TMA_BX), pym = ld2(P0, idx - TMA_BX);
                 const float2 kyp = ld2(K0, idx + TMA_BX), pyp = ld2(P0, idx + TMA_BX);
                 const float2 kzp = ld2(sbuf[s_p][2], idx), pzp = ld2(sbuf[s_p][0], idx);
-                const bool top = k < g.nz - 1;
-                // (A p)_P = cb_P p_P + sum_f w_f (K_P + K_N)/2 (p_P - p_N)
-                const float t01 = face(true, kc.x, pc.x, kc.y, pc.y, wx);           // between the pair
-                const float tzx = face(top, kc.x, pc.x, kzp.x, pzp.x, wz);          // top faces
-                const float tzy = face(top, kc.y, pc.y, kzp.y, pzp.y, wz);
+                // (A p)_P = cb_P p_P + sum_f w_f (K_P + K_N)/2 (p_P - p_N); the
+                // plane above the grid's top is not staged, so its faces are skipped
+                const float t01 = face(kc.x, pc.x, kc.y, pc.y, wx);                  // between the pair
+                float tzx = 0.0f, tzy = 0.0f;                                        // top faces
+                if (k < g.nz - 1) {
+                    tzx = face(kc.x, pc.x, kzp.x, pzp.x, wz);
+                    tzy = face(kc.y, pc.y, kzp.y, pzp.y, wz);
+                }
                 float q0 = fmaf(cb.x, pc.x, carry.x) + t01 + tzx;
                 float q1 = fmaf(cb.y, pc.y, carry.y) - t01 + tzy;
-                q0 += face(fxm, kc.x, pc.x, K0[idx - 1], P0[idx - 1], wx);
-                q1 += face(fxp, kc.y, pc.y, K0[idx + 2], P0[idx + 2], wx);
-                q0 += face(fym, kc.x, pc.x, kym.x, pym.x, wy) + face(fyp, kc.x, pc.x, kyp.x, pyp.x, wy);
-                q1 += face(fym, kc.y, pc.y, kym.y, pym.y, wy) + face(fyp, kc.y, pc.y, kyp.y, pyp.y, wy);
+                q0 += face(kc.x, pc.x, K0[idx - 1], P0[idx - 1], wx);
+                q1 += face(kc.y, pc.y, K0[idx + 2], P0[idx + 2], wx);
+                q0 += face(kc.x, pc.x, kym.x, pym.x, wy) + face(kc.x, pc.x, kyp.x, pyp.x, wy);
+                q1 += face(kc.y, pc.y, kym.y, pym.y, wy) + face(kc.y, pc.y, kyp.y, pyp.y, wy);
                 carry = make_float2(-tzx, -tzy);
                 const bool a0 = kc.x >= 0.0f, a1 = kc.y >= 0.0f;
                 const float2 po = make_float2(a0 ? pc.x : 0.0f, a1 ? pc.y : 0.0f);
@@ -938,12 +948,18 @@ bool make_tma_maps32(int nx, int ny, int nz, const float *z, const float *p0, co
     const cuuint64_t strides[2] = {(cuuint64_t)nx * 4, (cuuint64_t)nx * ny * 4};
     const cuuint32_t box[3] = {TMA_BX, TMA_BY, 1};
     const cuuint32_t estr[3] = {1, 1, 1};
-    auto one = [&](CUtensorMap *m, const float *ptr) {
-        return encode(m, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3, const_cast<float *>(ptr), dims, strides, box, estr,
+    // boxes outside the grid read 0, except K, which reads NaN like an
+    // inactive cell (the stencil's face coefficient max(w (K_P + K_N), 0)
+    // then closes the faces at the grid's edge without a test)
+    const cuuint32_t own_box[3] = {TMA_TX, TMA_OWN_BY, 1};
+    auto one = [&](CUtensorMap *m, const float *ptr, bool nan_fill, const cuuint32_t *bx) {
+        return encode(m, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3, const_cast<float *>(ptr), dims, strides, bx, estr,
                       CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
-                      CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+                      nan_fill ? CU_TENSOR_MAP_FLOAT_OOB_FILL_NAN_REQUEST_ZERO_FMA : CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) ==
+               CUDA_SUCCESS;
     };
-    if (!(one(&out->z, z) && one(&out->p0, p0) && one(&out->p1, p1) && one(&out->K, K) && one(&out->cb, cb)))
+    if (!(one(&out->z, z, false, box) && one(&out->p0, p0, false, box) && one(&out->p1, p1, false, box) &&
+          one(&out->K, K, true, box) && one(&out->cb, cb, false, own_box)))
         return false;
     out->z_ptr = z;
     out->p_ptr[0] = p0;

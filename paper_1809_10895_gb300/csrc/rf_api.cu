@@ -1171,26 +1171,15 @@ rf_status rf_state_set(rf_ctx *c, const double *h, double t)
     if (!c || !h) return fail(RF_ERR_ARG, "null argument");
     if (!c->soils_set) return fail(RF_ERR_STATE, "call rf_soil_set before rf_state_set");
     if (!std::isfinite(t)) return fail(RF_ERR_ARG, "non-finite time");
-    // copied straight from the caller's buffer (a DMA when it is pinned);
-    // only non-finite values on inactive cells need a cleaned copy
-    bool clean = true;
-    for (long long p = 0; p < c->g.N; p++) {
-        if (std::isfinite(h[p])) continue;
-        if (c->flags_h[p]) return fail(RF_ERR_ARG, "non-finite head on an active cell");
-        clean = false;
-    }
-    std::vector<double> hh;
-    const double *src = h;
-    if (!clean) {
-        hh.assign(h, h + c->g.N);
-        for (long long p = 0; p < c->g.N; p++)
-            if (!std::isfinite(hh[p])) hh[p] = 0.0;
-        src = hh.data();
-    }
-    CUDA_TRY(cudaMemcpyAsync(c->h, src, sizeof(double) * c->g.N, cudaMemcpyHostToDevice, c->stream));
-    const rf_status st = state_set_common(c, t);   // synchronises on success
-    if (st) cudaStreamSynchronize(c->stream);       // the host buffer is not read after the call
-    return st;
+    // copied straight from the caller's buffer (a DMA when it is pinned) into
+    // scratch, checked on the device, and committed only when every active
+    // head is finite (the state is unchanged otherwise)
+    CUDA_TRY(cudaMemcpyAsync(c->x, h, sizeof(double) * c->g.N, cudaMemcpyHostToDevice, c->stream));
+    launch_state_check_commit(c->stream, c->nblk, c->g, c->flags, c->x, c->h, c->partials, c->ticket, c->res);
+    CUDA_TRY(cudaMemcpyAsync(c->res_h, c->res, sizeof(StepResults), cudaMemcpyDeviceToHost, c->stream));
+    if (rf_status st = sync(c)) return st;          // the host buffer is not read after this
+    if (c->res_h->nonfinite) return fail(RF_ERR_ARG, "non-finite head on an active cell");
+    return state_set_common(c, t);
 }
 
 rf_status rf_state_set_device(rf_ctx *c, const double *d_h, double t)

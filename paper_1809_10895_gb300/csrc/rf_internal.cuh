@@ -296,6 +296,12 @@ void launch_mass_balance(cudaStream_t s, int nblk, const Grid &g, const DevSoil 
 void launch_storage(cudaStream_t s, int nblk, const Grid &g, const uint8_t *flags, const double *theta,
                     double *partials, unsigned int *ticket, StepResults *res);
 
+// Uploaded state src checked on the device (res->nonfinite: a non-finite head
+// on an active cell) and, only when valid, committed into dst (non-finite
+// values on inactive cells become 0).
+void launch_state_check_commit(cudaStream_t s, int nblk, const Grid &g, const uint8_t *flags, const double *src,
+                               double *dst, double *partials, unsigned int *ticket, StepResults *res);
+
 // Accept a converged attempt: h <- x_final, theta_n <- theta_k, K0 <- K1 (copyK).
 void launch_accept(cudaStream_t s, int nblk, const Grid &g, const double *x_final, double *h,
                    const double *theta_k, double *theta_n, const double *K1, double *K0, int copyK);

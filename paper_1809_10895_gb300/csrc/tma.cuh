@@ -17,6 +17,9 @@ constexpr int TMA_TX = 64;
 constexpr int TMA_BX = TMA_TX + 8, TMA_BY = 10, TMA_X0 = 4;
 constexpr int TMA_BOX_BYTES = TMA_BX * TMA_BY * 4;       // 2880
 constexpr int TMA_SLOT_BYTES = (TMA_BOX_BYTES + 127) / 128 * 128;
+// Box of an array read at the tile's own cells only (cb): 64 x 8, no halo.
+constexpr int TMA_OWN_BY = 8;
+constexpr int TMA_OWN_BYTES = TMA_TX * TMA_OWN_BY * 4;   // 2048
 
 // Tensor maps of the FP32 inner-solve arrays (one 3-D map per array, dims
 // nx, ny, nz), with the device pointers they describe.

@@ -276,6 +276,29 @@ def test_error_paths():
     assert e.value.status == rf.RF_ERR_ARG
 
 
+def test_state_set_checks_heads_on_the_device():
+    # a non-finite head on an active cell is refused (RF_ERR_ARG) and leaves
+    # the state and clock as they were; non-finite values on inactive cells
+    # are accepted and stored as 0
+    case = W.watershed(24, 20, 16, dx=10.0, dz=0.5, seed=0, hours=24, tol_cg=1e-12)
+    s = rf.Solver.from_case(case)
+    s.run(600.0)
+    h0, m0 = s.get_state()
+    act = case.active.astype(bool)
+    bad = h0.copy()
+    bad[np.flatnonzero(act)[7]] = np.nan
+    with pytest.raises(rf.RFError) as e:
+        s.set_state(bad, 0.0)
+    assert e.value.status == rf.RF_ERR_ARG
+    h1, m1 = s.get_state()
+    assert np.array_equal(h0, h1) and m0 == m1
+    ok = h0.copy()
+    ok[np.flatnonzero(~act)[:5]] = np.inf
+    s.set_state(ok, 5.0)
+    h2, m2 = s.get_state()
+    assert np.array_equal(h2[act], h0[act]) and np.all(h2[np.flatnonzero(~act)[:5]] == 0.0) and m2["t"] == 5.0
+
+
 def test_dt_min_failure_leaves_state_unchanged():
     # one Picard iteration allowed and an unreachable tolerance: every try is
     # rejected, EBATS shrinks dt below dt_min and the call fails with

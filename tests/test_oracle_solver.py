@@ -279,3 +279,26 @@ def test_laterally_uniform_block_equals_its_column(nx, ny, dx, dy):
     area = nx * dx * ny * dy
     for k in ("storage", "inflow_cum", "outflow_cum"):
         assert mb[k] / area == pytest.approx(mc[k], rel=1e-12), k
+
+
+def test_resume_from_a_saved_state_is_bit_identical():
+    # set_state + set_clock (time, EBATS nominal step and easy-step counter)
+    # resume a run exactly: the benchmark's CPU baseline starts the oracle
+    # from a state saved by another run this way
+    from paper_1809_10895_gb300 import workloads as W
+    from tests.helpers import oracle_from_case
+    case = W.heterogeneous_box(10, 8, 9, d=0.25, seed=4, water_table_depth=1.0, rain=6e-6, rain_hours=0.5)
+    a = oracle_from_case(case)
+    a.run(1500.0)
+    h_mid, meta = a.get_state()
+    rest_a = a.run(3000.0)
+    b = oracle_from_case(case)
+    b.set_state(h_mid, meta["t"])
+    b.set_clock(meta["t"], meta["dt_nom"], meta["easy"])
+    rest_b = b.run(3000.0)
+    assert [(s.dt, s.picard, s.rejected) for s in rest_a] == [(s.dt, s.picard, s.rejected) for s in rest_b]
+    assert np.array_equal(a.get_state()[0], b.get_state()[0])
+    # the clock matters: without it EBATS restarts from dt0
+    c = oracle_from_case(case)
+    c.set_state(h_mid, meta["t"])
+    assert [s.dt for s in c.run(3000.0)] != [s.dt for s in rest_a]
