@@ -65,7 +65,9 @@ def parse():
     ap.add_argument("--no-full-period", action="store_true", help="skip the 30-day time-to-solution legs")
     ap.add_argument("--no-ensemble", action="store_true", help="skip the batched-ensemble leg")
     ap.add_argument("--ensemble-window", type=float, default=600.0,
-                    help="simulated seconds of the ensemble leg (172800: its whole 2 days, about 4.5 min)")
+                    help="simulated seconds of the ensemble leg (172800: its whole 2 days)")
+    ap.add_argument("--ensemble-precond", default="zline", choices=["zline", "jacobi"],
+                    help="inner PCG preconditioner of the ensemble leg (vertical-line solve or Jacobi)")
     ap.add_argument("--no-warmstart", action="store_true", help="skip the learned warm-start leg")
     ap.add_argument("--no-configs", action="store_true", help="skip the column and box legs")
     ap.add_argument("--ws-train-size", type=int, default=128, help="nx = ny of the training box (nz = 64)")
@@ -588,7 +590,7 @@ def native(args):
 def ensemble_leg(args, rank, rf, W, barrier):
     import torch
     cases = W.ensemble(256, seed=args.seed + rank)
-    e = rf.Ensemble.from_cases(cases, precision="mixed")
+    e = rf.Ensemble.from_cases(cases, precision="mixed", precond=args.ensemble_precond)
     cluster, cta_threads, n_wide, probe_ms = e.tune(min(20.0, args.ensemble_window))
     barrier()
     ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -604,7 +606,9 @@ def ensemble_leg(args, rank, rf, W, barrier):
            "wide_instances": n_wide, "tuner_probe_ms": probe_ms, "kernel_ms": ens_ms, "time_to_solution_s": ens_ms / 1e3,
            "cell_timesteps": cell_steps, "value": cell_steps / (ens_ms * 1e-3), "unit": UNIT,
            "steps_total": sum(st["steps"] for st in stats), "picard_total": sum(st["picard_iters"] for st in stats),
+           "inner_pcg_total": sum(st["cg_iters"] for st in stats),
            "failed_instances": sum(1 for st in stats if st["status"] != 0), "precision": "mixed",
+           "precond": args.ensemble_precond,
            "max_closure_rel": max(st["closure_abs"] / max(st["storage0"] + st["inflow_cum"] + st["outflow_cum"], 1e-300)
                                   for st in stats)}
     e.close()

@@ -115,11 +115,21 @@ typedef enum rf_time_scheme { RF_TIME_BACKWARD_EULER = 0, RF_TIME_BDF2 = 1 } rf_
  * failure divides dt by f_shrink as in EBATS. */
 typedef enum rf_time_control { RF_TIME_EBATS = 0, RF_TIME_RICHARDSON = 1 } rf_time_control;
 
-/* Preconditioner of the inner PCG.  MG and DIC need RF_PREC_MIXED.  DIC is
- * the diagonal incomplete Cholesky preconditioner Sec. 2.2 solves with, the
- * cells eliminated in red-black order (colour (i + j + k) mod 2) so that its
- * sweeps are data-parallel. */
-typedef enum rf_precond { RF_PRECOND_JACOBI = 0, RF_PRECOND_MG = 1, RF_PRECOND_DIC = 2 } rf_precond;
+/* Preconditioner of the inner PCG.  MG, DIC and ZLINE need RF_PREC_MIXED.
+ * DIC is the diagonal incomplete Cholesky preconditioner Sec. 2.2 solves
+ * with, the cells eliminated in red-black order (colour (i + j + k) mod 2) so
+ * that its sweeps are data-parallel.  ZLINE (no counterpart in the paper;
+ * ensemble only, rf_mesh_create and rf_set_params refuse it) is the operator
+ * without its horizontal faces -- per column the tridiagonal matrix of the
+ * storage term and the vertical faces -- solved exactly per column; it is
+ * exact on residuals that are uniform across the columns, the vertical flow
+ * of the ensemble's instances. */
+typedef enum rf_precond {
+    RF_PRECOND_JACOBI = 0,
+    RF_PRECOND_MG = 1,
+    RF_PRECOND_DIC = 2,
+    RF_PRECOND_ZLINE = 3
+} rf_precond;
 
 /* Solver parameters (Sec. 2.2 leaves their values to the user).
  *   tol_picard  Picard exit test: max over active cells |h^{k+1} - h^k| <= tol [m]
@@ -394,8 +404,9 @@ typedef struct rf_ens_stats {
 
 /* Create an ensemble (instances copied; params checked as for rf_mesh_create;
  * the precision selects FP64 PCG or FP32 inner PCG in FP64 defect
- * correction).  The ensemble runs the chord Picard form with Jacobi-PCG only:
- * another picard_form or precond returns RF_ERR_ARG.  Instances and params are
+ * correction).  The ensemble runs the chord Picard form with Jacobi-PCG, or
+ * with RF_PREC_MIXED and RF_PRECOND_ZLINE the vertical-line-preconditioned
+ * inner PCG: another picard_form or precond returns RF_ERR_ARG.  Instances and params are
  * checked before the device is queried; *out is NULL on every error. */
 rf_status rf_ens_create(const rf_ens_instance *inst, int n, const rf_solver_params *params, void *cuda_stream,
                         const rf_allocator *alloc, rf_ens **out);

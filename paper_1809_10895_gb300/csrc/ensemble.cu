@@ -200,22 +200,138 @@ __device__ __forceinline__ float apply32_i(const Geo32 &g, int p, const float *_
     return acc;
 }
 
-// Inner FP32 Jacobi-PCG of one defect-correction pass, A d = r32 from d = 0,
-// on this CTA's cells [lo, hi) of an instance (views offset to the
-// instance); scalars in FP32 too, since every thread computes them.  Kept
-// out of line so that its loops get registers of their own, apart from the
-// instance state of the caller.  Returns false on breakdown; its = inner
-// iterations.
+// Vertical-line preconditioner M: the FP32 operator without its horizontal
+// faces.  Per column (i, j) of an instance it is the tridiagonal matrix with
+// diagonal cb_k + the two vertical face terms and off-diagonals
+// -wz (K_k + K_k+1)/2: symmetric and diagonally dominant with cb > 0, so the
+// Thomas recurrence needs no pivoting.  A - M is the horizontal graph
+// Laplacian (positive semi-definite), so every eigenvalue of M^-1 A is >= 1,
+// and M^-1 is exact on residuals that are uniform across the columns, where
+// the horizontal faces carry no flux.  Each column belongs to one thread
+// (columns dealt round-robin over the unit's threads); the same thread
+// factors and solves it, so the factors need no barrier.
+constexpr int ZB = 8;   // cells of a column loaded ahead of the recurrence
+
+// Factor: lt_inv_k = 1 / pivot_k and lt_c_k = c_k / pivot_k per cell.
+__device__ __noinline__ void zline_factor32(const ClusterCtx &C, const Geo32 g, const float *__restrict__ K32,
+                                            const float *__restrict__ cb32, float *__restrict__ lt_inv,
+                                            float *__restrict__ lt_c)
+{
+    const int bd = (int)blockDim.x, nz = g.nz, s = g.sxy;
+    const float hw = 0.5f * g.w[2];
+    for (int col = C.rank * bd + (int)threadIdx.x; col < s; col += C.ncta * bd) {
+        float Kk = K32[col];
+        float a = 0.0f, cp = 0.0f;   // coupling to the cell below; c'_{k-1}
+        for (int k0 = 0; k0 < nz; k0 += ZB) {
+            float Kup[ZB], cbv[ZB];
+#pragma unroll
+            for (int u = 0; u < ZB; u++) {
+                const int k = k0 + u;
+                Kup[u] = k + 1 < nz ? K32[col + (k + 1) * s] : 0.0f;
+                cbv[u] = k < nz ? cb32[col + k * s] : 1.0f;
+            }
+#pragma unroll
+            for (int u = 0; u < ZB; u++) {
+                const int k = k0 + u;
+                if (k < nz) {
+                    const float c = k + 1 < nz ? -hw * (Kk + Kup[u]) : 0.0f;
+                    const float inv = 1.0f / fmaf(-a, cp, cbv[u] - a - c);
+                    cp = c * inv;
+                    lt_inv[col + k * s] = inv;
+                    lt_c[col + k * s] = cp;
+                    a = c;
+                    Kk = Kup[u];
+                }
+            }
+        }
+    }
+}
+
+// Solve z = M^-1 r on this thread's columns (forward elimination into z,
+// then back substitution in place); returns this thread's share of r . z.
+__device__ __noinline__ float zline_solve32(const ClusterCtx &C, const Geo32 g, const float *__restrict__ K32,
+                                            const float *__restrict__ lt_inv, const float *__restrict__ lt_c,
+                                            const float *__restrict__ r32, float *__restrict__ z32)
+{
+    const int bd = (int)blockDim.x, nz = g.nz, s = g.sxy;
+    const float hw = 0.5f * g.w[2];
+    float rz = 0.0f;
+    for (int col = C.rank * bd + (int)threadIdx.x; col < s; col += C.ncta * bd) {
+        // y_k = (r_k - a_k y_{k-1}) / pivot_k, a_k = -wz (K_{k-1} + K_k)/2
+        float y = 0.0f, Kb = 0.0f;
+        for (int k0 = 0; k0 < nz; k0 += ZB) {
+            float rv[ZB], Kv[ZB], iv[ZB];
+#pragma unroll
+            for (int u = 0; u < ZB; u++) {
+                const int k = k0 + u;
+                const bool in = k < nz;
+                rv[u] = in ? r32[col + k * s] : 0.0f;
+                Kv[u] = in ? K32[col + k * s] : 0.0f;
+                iv[u] = in ? lt_inv[col + k * s] : 0.0f;
+            }
+#pragma unroll
+            for (int u = 0; u < ZB; u++) {
+                const int k = k0 + u;
+                if (k < nz) {
+                    const float a = k > 0 ? -hw * (Kb + Kv[u]) : 0.0f;
+                    y = fmaf(-a, y, rv[u]) * iv[u];
+                    z32[col + k * s] = y;
+                    Kb = Kv[u];
+                }
+            }
+        }
+        // z_k = y_k - c'_k z_{k+1}, top to bottom
+        float zn = 0.0f;
+        for (int k0 = nz - 1; k0 >= 0; k0 -= ZB) {
+            float yv[ZB], cv[ZB], rv[ZB];
+#pragma unroll
+            for (int u = 0; u < ZB; u++) {
+                const int k = k0 - u;
+                const bool in = k >= 0;
+                yv[u] = in ? z32[col + k * s] : 0.0f;
+                cv[u] = in ? lt_c[col + k * s] : 0.0f;
+                rv[u] = in ? r32[col + k * s] : 0.0f;
+            }
+#pragma unroll
+            for (int u = 0; u < ZB; u++) {
+                const int k = k0 - u;
+                if (k >= 0) {
+                    zn = fmaf(-cv[u], zn, yv[u]);
+                    z32[col + k * s] = zn;
+                    rz = fmaf(rv[u], zn, rz);
+                }
+            }
+        }
+    }
+    return rz;
+}
+
+// Inner FP32 PCG of one defect-correction pass, A d = r32 from d = 0, on
+// this CTA's cells [lo, hi) of an instance (views offset to the instance);
+// scalars in FP32 too, since every thread computes them.  Preconditioner:
+// Jacobi (z32 and rho = r.z from the caller), or with zline the vertical-line
+// solve (factors lt_inv, lt_c).  Kept out of line so that its loops get
+// registers of their own, apart from the instance state of the caller.
+// Returns false on breakdown; its = inner iterations.
+template <bool zline>
 __device__ __noinline__ bool inner_pcg32(ClusterCtx &C, const Geo32 g, int lo, int hi, const float *__restrict__ K32,
                                          const float *__restrict__ cb32, const float *__restrict__ di32,
                                          float *__restrict__ r32, float *__restrict__ z32, float *__restrict__ pa_,
                                          float *__restrict__ pb_, float *__restrict__ q32, float *__restrict__ d32,
+                                         const float *__restrict__ lt_inv, const float *__restrict__ lt_c,
                                          float rho, float stop, int max_it, int &its)
 {
     float beta = 0.0f;
     int pi = 0;
     its = 0;
     const int bd = (int)blockDim.x;
+    if constexpr (zline) {
+        // r32 was published by the caller's reduction barrier
+        float w0[1] = {zline_solve32(C, g, K32, lt_inv, lt_c, r32, z32)};
+        cl_reduce_f32<1>(C, w0);   // also publishes z32
+        rho = w0[0];
+        if (!(rho > 0.0f) || !isfinite(rho)) return false;
+    }
     for (;;) {
         float *pin = pi ? pb_ : pa_, *pout = pi ? pa_ : pb_;
         const bool first = its == 0;
@@ -245,6 +361,16 @@ __device__ __noinline__ bool inner_pcg32(ClusterCtx &C, const Geo32 g, int lo, i
         const float af = rho / w1[0];
         if (!(w1[0] > 0.0f) || !isfinite(af)) return false;
         float b0 = 0.0f, b1 = 0.0f;
+        if constexpr (zline) {
+            for (int p = lo + (int)threadIdx.x; p < hi; p += bd) {
+                const float r2 = fmaf(-af, q32[p], r32[p]);
+                d32[p] = fmaf(af, pout[p], d32[p]);
+                r32[p] = r2;
+                b0 = fmaf(r2, r2, b0);
+            }
+            unit_sync(C);   // the columns cross the CTAs' cell ranges
+            b1 = zline_solve32(C, g, K32, lt_inv, lt_c, r32, z32);
+        } else
         for (int p = lo + (int)threadIdx.x; p < hi; p += 2 * bd) {
             const bool has2 = p + bd < hi;
             const int p2 = has2 ? p + bd : p;
@@ -344,6 +470,7 @@ k_ensemble(EnsDesc *__restrict__ D, int n_inst, EnsBuffers B, EnsParams P, const
         float *K32 = B.K32 + off, *cb32 = B.cb32 + off, *di32 = B.dinv32 + off;
         float *r32 = B.r32 + off, *z32 = B.z32 + off, *P32[2] = {B.p32[0] + off, B.p32[1] + off};
         float *q32 = B.q32 + off, *d32 = B.d32 + off;
+        float *LTi = P.zline ? B.lt_inv + off : nullptr, *LTc = P.zline ? B.lt_c + off : nullptr;
         const uint8_t *fl = B.flags + off, *zn = B.zone + off;
         const double *Ks = B.Ks + off;
         const DevSoil *soil = &d.soil;
@@ -497,6 +624,8 @@ k_ensemble(EnsDesc *__restrict__ D, int n_inst, EnsBuffers B, EnsParams P, const
                         }
                     } else {
                         // ---- FP32 inner PCG inside FP64 defect correction
+                        // (the assembly's reduction barrier published K32, cb32)
+                        if (P.zline) zline_factor32(C, geo32(g), K32, cb32, LTi, LTc);
                         int outer = 1;
                         for (;;) {
                             const bool finite = isfinite(v[0]) && isfinite(v[1]) && isfinite(v[2]) && isfinite(v[3]);
@@ -505,10 +634,16 @@ k_ensemble(EnsDesc *__restrict__ D, int n_inst, EnsBuffers B, EnsParams P, const
                             if (outer >= P.outer_max_it) { lin_ok = false; break; }
                             // inner solve A d = r32 from d = 0, FP32 throughout
                             int inner_it = 0;
-                            if (v[2] > 0.0)
-                                lin_ok = inner_pcg32(C, geo32(g), (int)lo, (int)hi, K32, cb32, di32, r32, z32, P32[0], P32[1],
-                                                     q32, d32, (float)v[3], (float)(P.tol_inner * sqrt(v[2])),
-                                                     P.inner_max_it, inner_it);
+                            if (v[2] > 0.0) {
+                                const float stop = (float)(P.tol_inner * sqrt(v[2]));
+                                lin_ok = P.zline
+                                             ? inner_pcg32<true>(C, geo32(g), (int)lo, (int)hi, K32, cb32, di32, r32,
+                                                                 z32, P32[0], P32[1], q32, d32, LTi, LTc, 0.0f, stop,
+                                                                 P.inner_max_it, inner_it)
+                                             : inner_pcg32<false>(C, geo32(g), (int)lo, (int)hi, K32, cb32, di32, r32,
+                                                                  z32, P32[0], P32[1], q32, d32, nullptr, nullptr,
+                                                                  (float)v[3], stop, P.inner_max_it, inner_it);
+                            }
                             cg_it += inner_it;
                             if (!lin_ok) break;
                             for (long long p = lo + threadIdx.x; p < hi; p += blockDim.x) x[p] += (double)d32[p];

@@ -32,6 +32,7 @@ struct EnsBuffers {
     double *Can, *c, *b, *Tx, *Ty, *Tz, *diag, *dinv;
     double *r, *z, *p[2], *q;
     float *K32, *cb32, *dinv32, *r32, *z32, *p32[2], *q32, *d32;
+    float *lt_inv, *lt_c;   // vertical-line factors (RF_PRECOND_ZLINE; null otherwise)
     uint8_t *flags, *zone;
     double *Ks;
 };
@@ -39,6 +40,7 @@ struct EnsBuffers {
 struct EnsParams {
     double tol_picard, tol_cg, tol_inner, dt_max, dt_min, f_grow, f_shrink, eps_chord;
     int n_inc, n_small, n_max, cg_max_it, inner_max_it, outer_max_it;
+    int zline;              // inner PCG preconditioned by the vertical-line solve
     long long step_budget;
 };
 

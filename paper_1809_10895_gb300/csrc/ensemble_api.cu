@@ -185,8 +185,8 @@ rf_status rf_ens_create(const rf_ens_instance *inst, int n, const rf_solver_para
     if (rf_status st = check_solver_params(&prm)) return st;
     if (prm.picard_form != RF_PICARD_CHORD)
         return efail(RF_ERR_ARG, "rf_ens_create: the ensemble runs the classical (chord) Picard iteration only");
-    if (prm.precond != RF_PRECOND_JACOBI)
-        return efail(RF_ERR_ARG, "rf_ens_create: the ensemble's PCG is Jacobi-preconditioned only");
+    if (prm.precond != RF_PRECOND_JACOBI && prm.precond != RF_PRECOND_ZLINE)
+        return efail(RF_ERR_ARG, "rf_ens_create: the ensemble's PCG is Jacobi- or vertical-line-preconditioned only");
     if (prm.face_mean != RF_FACE_ARITHMETIC || prm.time_scheme != RF_TIME_BACKWARD_EULER ||
         prm.time_control != RF_TIME_EBATS || prm.grav[0] != 0.0 || prm.grav[1] != 0.0 || prm.grav[2] != 1.0)
         return efail(RF_ERR_ARG, "rf_ens_create: the ensemble runs the default scheme (arithmetic face mean, "
@@ -247,6 +247,7 @@ rf_status rf_ens_create(const rf_ens_instance *inst, int n, const rf_solver_para
          e->get(e->B.cb32, N) && e->get(e->B.dinv32, N) && e->get(e->B.r32, N) && e->get(e->B.z32, N) &&
          e->get(e->B.q32, N) && e->get(e->B.d32, N) && e->get(e->B.flags, N) && e->get(e->B.zone, N) &&
          e->get(e->B.Ks, N);
+    if (ok && prm.precond == RF_PRECOND_ZLINE) ok = e->get(e->B.lt_inv, N) && e->get(e->B.lt_c, N);
     if (!ok || cudaMallocHost(&e->t_end_h, sizeof(double)) != cudaSuccess) {
         rf_ens_destroy(e);
         return efail(RF_ERR_NOMEM, "rf_ens_create: allocation failed");
@@ -333,6 +334,7 @@ rf_status rf_ens_create(const rf_ens_instance *inst, int n, const rf_solver_para
     P.cg_max_it = prm.cg_max_it;
     P.inner_max_it = prm.inner_max_it;
     P.outer_max_it = prm.outer_max_it;
+    P.zline = prm.precond == RF_PRECOND_ZLINE;
     P.step_budget = 10000000;
     cudaError_t err = cudaMemcpyAsync(e->tab, &tab, sizeof(FFTables), cudaMemcpyHostToDevice, e->stream);
     if (err == cudaSuccess) err = cudaMemcpyAsync(e->B.flags, flags.data(), N, cudaMemcpyHostToDevice, e->stream);

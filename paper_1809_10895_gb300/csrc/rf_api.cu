@@ -151,7 +151,8 @@ rf_status check_params(const rf_solver_params *p)
         return fail(RF_ERR_ARG, "invalid solver parameters");
     if (p->precision != RF_PREC_FP64 && p->precision != RF_PREC_MIXED)
         return fail(RF_ERR_ARG, "unknown precision mode");
-    if (p->precond != RF_PRECOND_JACOBI && p->precond != RF_PRECOND_MG && p->precond != RF_PRECOND_DIC)
+    if (p->precond != RF_PRECOND_JACOBI && p->precond != RF_PRECOND_MG && p->precond != RF_PRECOND_DIC &&
+        p->precond != RF_PRECOND_ZLINE)
         return fail(RF_ERR_ARG, "unknown preconditioner");
     if (p->picard_form != RF_PICARD_CHORD && p->picard_form != RF_PICARD_MODIFIED)
         return fail(RF_ERR_ARG, "unknown Picard linearisation");
@@ -159,6 +160,8 @@ rf_status check_params(const rf_solver_params *p)
         return fail(RF_ERR_ARG, "the multigrid preconditioner serves the FP32 inner solve: use RF_PREC_MIXED");
     if (p->precond == RF_PRECOND_DIC && p->precision != RF_PREC_MIXED)
         return fail(RF_ERR_ARG, "the DIC preconditioner serves the FP32 inner solve: use RF_PREC_MIXED");
+    if (p->precond == RF_PRECOND_ZLINE && p->precision != RF_PREC_MIXED)
+        return fail(RF_ERR_ARG, "the vertical-line preconditioner serves the FP32 inner solve: use RF_PREC_MIXED");
     if (p->closure_arith < RF_CLOSURE_AUTO || p->closure_arith > RF_CLOSURE_DOUBLE_FLOAT)
         return fail(RF_ERR_ARG, "unknown closure arithmetic");
     if (p->face_mean != RF_FACE_ARITHMETIC && p->face_mean != RF_FACE_HARMONIC)
@@ -924,6 +927,8 @@ rf_status rf_mesh_create(const rf_mesh_desc *mesh, const rf_solver_params *param
     rf_default_params(&prm);
     if (params) prm = *params;
     if (rf_status st = check_params(&prm)) return st;
+    if (prm.precond == RF_PRECOND_ZLINE)
+        return fail(RF_ERR_ARG, "the vertical-line preconditioner serves the ensemble (rf_ens_create) only");
 
     int ndev = 0;
     if (cudaGetDeviceCount(&ndev) != cudaSuccess || ndev < 1) {
@@ -1072,6 +1077,8 @@ rf_status rf_set_params(rf_ctx *c, const rf_solver_params *params)
 {
     if (!c || !params) return fail(RF_ERR_ARG, "null argument");
     if (rf_status st = check_params(params)) return st;
+    if (params->precond == RF_PRECOND_ZLINE)
+        return fail(RF_ERR_ARG, "the vertical-line preconditioner serves the ensemble (rf_ens_create) only");
     CUDA_TRY(cudaStreamSynchronize(c->stream));
     if (params->picard_form == RF_PICARD_MODIFIED && !c->s0 && !alloc_n(c, c->s0, c->g.N))
         return fail(RF_ERR_NOMEM, "rf_set_params: device allocation failed");

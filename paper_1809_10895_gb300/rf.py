@@ -28,7 +28,7 @@ FACES = {"xmin": 0, "xmax": 1, "ymin": 2, "ymax": 3, "zmin": 4, "zmax": 5}
 BC_TYPES = {"zero_flux": 0, "dirichlet": 1, "flux": 2, "free_drainage": 3, "seepage": 4}
 MODELS = {"vg": RF_VG, "gardner": RF_GARDNER, "brooks_corey": RF_BROOKS_COREY}
 PRECISION = {"fp64": 0, "mixed": 1}
-PRECOND = {"jacobi": 0, "mg": 1, "dic": 2}
+PRECOND = {"jacobi": 0, "mg": 1, "dic": 2, "zline": 3}
 PICARD_FORM = {"chord": 0, "modified": 1}
 CLOSURE_ARITH = {"auto": 0, "fp64": 1, "double_float": 2}
 FACE_MEAN = {"arithmetic": 0, "harmonic": 1}

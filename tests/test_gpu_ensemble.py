@@ -2,8 +2,9 @@
 oracle run instance by instance: identical step / Picard / rejection totals,
 heads within 1e-8 m (FP64) or 1e-6 m (mixed), for single-CTA and multi-CTA
 cluster work units, every CTA size, and clusters that hand the smaller
-instances to single CTAs; laterally uniform instances equal their 1x1
-column; the tuner picks a working tile."""
+instances to single CTAs; the vertical-line preconditioner on the same
+tilings, and its exactness on vertical flow; laterally uniform instances
+equal their 1x1 column; the tuner picks a working tile."""
 import numpy as np
 import pytest
 
@@ -79,6 +80,56 @@ def test_ensemble_mixed_matches_oracle(oracle_runs):
         assert np.max(np.abs(h - ho)) <= 1e-6, i
         scale = st["storage0"] + st["inflow_cum"] + st["outflow_cum"]
         assert st["closure_abs"] / scale <= 10 * mbo["closure_rel"] + 1e-12
+
+
+@pytest.mark.parametrize("cluster,threads,wide", [(1, 512, 0), (4, 128, 0), (8, 256, 2)])
+def test_ensemble_vertical_line_preconditioner_matches_oracle(oracle_runs, cluster, threads, wide):
+    """Mixed path with the vertical-line preconditioner: same heads as the
+    oracle within the mixed path's 1e-6 m, on single CTAs and on clusters
+    whose CTAs' cell ranges cut every column (the columns' solves read and
+    write across the CTAs)."""
+    cases, ref = oracle_runs
+    e = rf.Ensemble.from_cases(cases, precision="mixed", precond="zline")
+    e.set_tiling(cluster, threads)
+    if wide:
+        e.set_schedule(None, wide)
+    e.run(cases[0].t_end)
+    for i, (c, (ho, so, mbo)) in enumerate(zip(cases, ref)):
+        h, st = e.get(i)
+        assert st["status"] == 0 and st["t"] == pytest.approx(c.t_end, abs=1e-6)
+        assert np.max(np.abs(h - ho)) <= 1e-6, i
+        scale = st["storage0"] + st["inflow_cum"] + st["outflow_cum"]
+        assert st["closure_abs"] / scale <= 10 * mbo["closure_rel"] + 1e-12
+
+
+def test_vertical_line_preconditioner_is_exact_on_vertical_flow():
+    """On 1x1 columns and on laterally uniform blocks the line solve is the
+    inverse of the operator (no horizontal flux), so each inner PCG ends
+    after one iteration (to FP32 rounding, far below the inner tolerance
+    1e-4): inner iterations = defect-correction passes, two or three per
+    Picard iteration at the outer tolerance 1e-10, where Jacobi needs
+    several times more on 1 cm cells."""
+    base = small_ensemble(3, seed=5)
+    cases = []
+    for c in base:
+        for nx, ny in ((1, 1), (3, 2)):
+            cases.append(W.Case(name=f"{c.name}_{nx}x{ny}", nx=nx, ny=ny, nz=c.nz, dx=c.dx, dy=c.dy, dz=c.dz,
+                                soils=c.soils, bcs=c.bcs, params=c.params,
+                                h0=np.full(nx * ny * c.nz, c.h0[0]), t_end=c.t_end))
+    runs = {}
+    for pc in ("jacobi", "zline"):
+        e = rf.Ensemble.from_cases(cases, precision="mixed", precond=pc)
+        e.set_tiling(2, 128)
+        e.run(cases[0].t_end)
+        runs[pc] = [e.get(i) for i in range(len(cases))]
+    tot = {pc: [sum(st[k] for _, st in runs[pc]) for k in ("cg_iters", "picard_iters")] for pc in runs}
+    for i, c in enumerate(cases):
+        (hj, sj), (hz, sz) = runs["jacobi"][i], runs["zline"][i]
+        assert sz["status"] == 0 and sj["status"] == 0
+        assert sz["cg_iters"] <= 4 * sz["picard_iters"], c.name
+        assert np.max(np.abs(hz - hj)) <= 2e-6, c.name
+    assert tot["zline"][0] <= 3 * tot["zline"][1]
+    assert tot["jacobi"][0] >= 2 * tot["zline"][0]
 
 
 def test_laterally_uniform_instance_equals_its_column():

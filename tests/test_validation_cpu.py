@@ -55,7 +55,7 @@ BAD_PARAMS = [
     ("inner_max_it", 0, "invalid solver parameters"),
     ("outer_max_it", 0, "invalid solver parameters"),
     ("precision", 2, "unknown precision"),
-    ("precond", 3, "unknown preconditioner"),
+    ("precond", 4, "unknown preconditioner"),
     ("picard_form", 2, "unknown Picard linearisation"),
     ("closure_arith", 3, "unknown closure arithmetic"),
     ("face_mean", 2, "unknown interface mean"),
@@ -89,10 +89,17 @@ def test_mesh_create_refuses_bad_params(lib, field, value, why):
     assert st == rf.RF_ERR_ARG and why in msg and h is None
 
 
-@pytest.mark.parametrize("precond", ["mg", "dic"])
+@pytest.mark.parametrize("precond", ["mg", "dic", "zline"])
 def test_fp32_preconditioners_need_the_mixed_path(lib, precond):
     st, msg, h = _mesh_create(lib, rf.default_params(precision="fp64", precond=precond))
     assert st == rf.RF_ERR_ARG and "RF_PREC_MIXED" in msg and h is None
+    st, msg, h = _ens_create(lib, [_instance()], rf.default_params(precision="fp64", precond=precond))
+    assert st == rf.RF_ERR_ARG and "RF_PREC_MIXED" in msg and h is None
+
+
+def test_the_vertical_line_preconditioner_is_the_ensembles(lib):
+    st, msg, h = _mesh_create(lib, rf.default_params(precision="mixed", precond="zline"))
+    assert st == rf.RF_ERR_ARG and "ensemble" in msg and h is None
 
 
 @pytest.mark.parametrize("dims,why", [
@@ -200,9 +207,10 @@ def test_ens_create_needs_an_instance(lib):
 
 
 @needs_no_gpu
-def test_valid_ensemble_reaches_the_device_query(lib):
+@pytest.mark.parametrize("precond", ["jacobi", "zline"])
+def test_valid_ensemble_reaches_the_device_query(lib, precond):
     st, msg, h = _ens_create(lib, [_instance(), _instance(nx=16, ny=16, nz=400)],
-                             rf.default_params(precision="mixed"))
+                             rf.default_params(precision="mixed", precond=precond))
     assert st == rf.RF_ERR_NO_DEVICE and "no CPU fallback" in msg and h is None
 
 
