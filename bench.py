@@ -638,6 +638,22 @@ def configs_leg(args, rank, rf, W):
                                           "picard_per_step": sum(x.picard for x in steps) / len(steps),
                                           "value": len(steps) * col.N / (ms / 1e3), "unit": UNIT}
     s.close()
+    # the same column on the device-resident integrator (the ensemble kernel
+    # with one instance on one CTA: EBATS, Picard and PCG all on the device)
+    e = rf.Ensemble.from_cases([col], precision="fp64")
+    e.set_tiling(1, 128)
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    a.record(e.stream)
+    e.run(col.t_end)
+    b.record(e.stream)
+    torch.cuda.synchronize()
+    ms = a.elapsed_time(b)
+    st = e.get(0, want_h=False)[1]
+    out["infiltration_column_1x1x200"]["device_resident"] = {
+        "steps": st["steps"], "picard_iters": st["picard_iters"], "cg_iters": st["cg_iters"],
+        "time_to_solution_s": ms / 1e3, "ms_per_step": ms / max(1, st["steps"]),
+        "value": st["steps"] * col.N / (ms / 1e3), "unit": UNIT}
+    e.close()
     # the heterogeneous box over its whole 48 h, both paths
     box = W.heterogeneous_box(128, 128, 64, seed=args.seed + rank)
     for prec in ("fp64", "mixed"):

@@ -40,7 +40,16 @@ struct ClusterCtx {
     double (*red)[RB_SLOTS][RB_WARPS];     // shared [2][RB_SLOTS][RB_WARPS]: per-warp FP64 partials
     double (*bc)[RB_SLOTS];                // shared [2][RB_SLOTS]: FP64 totals for the whole CTA
     float (*redf)[RB_SLOTS][RB_WARPS];     // shared [2][RB_SLOTS][RB_WARPS]: per-warp FP32 partials
+    double *part;                          // shared [RB_PART][blockDim]: per-thread FP64 partials
     int rb;                                // reduction double-buffer index (same in every CTA)
+};
+
+constexpr int RB_PART = 4;   // FP64 values a single-CTA reduction stages per thread
+
+// Finisher of a reduction that derives nothing.
+struct NoFin {
+    template <int NV>
+    __device__ void operator()(const double (&)[NV], double *) const {}
 };
 
 // Barrier over the threads that share the current instance.
@@ -75,51 +84,83 @@ __device__ __forceinline__ double warp_reduce_lane0(double x)
 }
 
 // Sum (or max) NV FP64 values over all threads of the instance's CTAs; every
-// thread gets the totals, bit-identical in every CTA.  FP64 runs on a narrow
-// pipe on this GPU, so the FP64 adds are kept to one tree per warp plus one
-// fold in warp 0: each warp reduces its values to lane 0, which publishes
-// them; one barrier (block or cluster); warp 0 of every CTA folds all
-// partials of all CTAs (lane l reads partials l, l+32, ..., remote ones
-// through distributed shared memory, all loads in flight at once), in the
-// same order in every CTA, and a block barrier hands the totals to the other
-// warps.  The double-buffered slots are rewritten two reductions later,
-// after the next barrier, which every reader has passed.
-template <class Op, int NV>
-__device__ __forceinline__ void cl_reduce(ClusterCtx &C, double (&v)[NV])
+// thread gets the totals, bit-identical in every CTA, and the ND scalars
+// fin(totals, d) derives from them (computed once, by one thread, and
+// broadcast: a divide or square root that every thread repeated would cost
+// the narrow FP64 pipe of this GPU hundreds of cycles).  FP64 adds are kept
+// few for the same reason.  On one CTA every thread stages its values in
+// shared memory and warp 0 sums them (nw values a lane, then one tree).  On
+// a cluster each warp reduces its values to lane 0, which publishes them;
+// one cluster barrier; warp 0 of every CTA folds all partials of all CTAs
+// (lane l reads partials l, l+32, ..., remote ones through distributed
+// shared memory, all loads in flight at once), in the same order in every
+// CTA.  A block barrier then hands the results to the other warps.  The
+// double-buffered slots are rewritten two reductions later, after the next
+// barrier, which every reader has passed; the per-thread slots are rewritten
+// only after this reduction's last barrier.
+template <class Op, int NV, int ND = 0, class Fin = NoFin>
+__device__ __forceinline__ void cl_reduce(ClusterCtx &C, double (&v)[NV], double *d = nullptr, Fin fin = Fin{})
 {
+    static_assert(NV + ND <= RB_SLOTS && NV <= RB_PART, "reduction slots");
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    double t[NV];
+    if (C.ncta == 1) {
 #pragma unroll
-    for (int i = 0; i < NV; i++) v[i] = warp_reduce_lane0<Op>(v[i]);
-    if (lane == 0) {
+        for (int i = 0; i < NV; i++) C.part[i * blockDim.x + threadIdx.x] = v[i];
+        __syncthreads();
+        if (wid == 0) {
 #pragma unroll
-        for (int i = 0; i < NV; i++) C.red[C.rb][i][wid] = v[i];
-    }
-    unit_sync(C);
-    if (wid == 0) {
-        const int total = C.ncta * nw;   // <= 8 * 16
-        double t[NV];
+            for (int i = 0; i < NV; i++) t[i] = Op::id();
+            for (int w = 0; w < nw; w++) {
 #pragma unroll
-        for (int i = 0; i < NV; i++) t[i] = Op::id();
-#pragma unroll
-        for (int u = 0; u < 4; u++) {
-            const int s = lane + 32 * u;
-            if (s < total) {
-                const int r = s / nw, w = s - r * nw;
-                const double *src = C.solo ? &C.red[C.rb][0][w] : C.cl.map_shared_rank(&C.red[C.rb][0][w], r);
-#pragma unroll
-                for (int i = 0; i < NV; i++) t[i] = Op::op(t[i], src[i * RB_WARPS]);
+                for (int i = 0; i < NV; i++) t[i] = Op::op(t[i], C.part[i * blockDim.x + 32 * w + lane]);
             }
         }
+    } else {
+#pragma unroll
+        for (int i = 0; i < NV; i++) v[i] = warp_reduce_lane0<Op>(v[i]);
+        if (lane == 0) {
+#pragma unroll
+            for (int i = 0; i < NV; i++) C.red[C.rb][i][wid] = v[i];
+        }
+        unit_sync(C);
+        if (wid == 0) {
+            const int total = C.ncta * nw;   // <= 8 * 16
+#pragma unroll
+            for (int i = 0; i < NV; i++) t[i] = Op::id();
+#pragma unroll
+            for (int u = 0; u < 4; u++) {
+                const int s = lane + 32 * u;
+                if (s < total) {
+                    const int r = s / nw, w = s - r * nw;
+                    const double *src = C.cl.map_shared_rank(&C.red[C.rb][0][w], r);
+#pragma unroll
+                    for (int i = 0; i < NV; i++) t[i] = Op::op(t[i], src[i * RB_WARPS]);
+                }
+            }
+        }
+    }
+    if (wid == 0) {
 #pragma unroll
         for (int i = 0; i < NV; i++) t[i] = warp_reduce_lane0<Op>(t[i]);
         if (lane == 0) {
 #pragma unroll
             for (int i = 0; i < NV; i++) C.bc[C.rb][i] = t[i];
+            if constexpr (ND > 0) {
+                double dd[ND];
+                fin(t, dd);
+#pragma unroll
+                for (int i = 0; i < ND; i++) C.bc[C.rb][NV + i] = dd[i];
+            }
         }
     }
     __syncthreads();
 #pragma unroll
     for (int i = 0; i < NV; i++) v[i] = C.bc[C.rb][i];
+    if constexpr (ND > 0) {
+#pragma unroll
+        for (int i = 0; i < ND; i++) d[i] = C.bc[C.rb][NV + i];
+    }
     C.rb ^= 1;
 }
 
@@ -210,7 +251,7 @@ __device__ __forceinline__ float apply32_i(const Geo32 &g, int p, const float *_
 // the horizontal faces carry no flux.  Each column belongs to one thread
 // (columns dealt round-robin over the unit's threads); the same thread
 // factors and solves it, so the factors need no barrier.
-constexpr int ZB = 8;   // cells of a column loaded ahead of the recurrence
+constexpr int ZB = 16;  // cells of a column loaded ahead of the recurrence
 
 // Factor: lt_inv_k = 1 / pivot_k and lt_c_k = c_k / pivot_k per cell.
 __device__ __noinline__ void zline_factor32(const ClusterCtx &C, const Geo32 g, const float *__restrict__ K32,
@@ -417,7 +458,8 @@ k_ensemble(EnsDesc *__restrict__ D, int n_inst, EnsBuffers B, EnsParams P, const
     __shared__ double bc[2][RB_SLOTS];
     __shared__ float redf[2][RB_SLOTS][RB_WARPS];
     __shared__ int s_inst;
-    ClusterCtx C{cg::this_cluster(), 0, 1, false, red, bc, redf, 0};
+    __shared__ double part[RB_PART * THREADS];
+    ClusterCtx C{cg::this_cluster(), 0, 1, false, red, bc, redf, part, 0};
     const int cl_rank = (int)C.cl.block_rank(), cl_size = (int)C.cl.num_blocks();
     C.rank = cl_rank;
     C.ncta = cl_size;
@@ -508,6 +550,11 @@ k_ensemble(EnsDesc *__restrict__ D, int n_inst, EnsBuffers B, EnsParams P, const
             status = ENS_RUNNING;
         }
         bool closure_valid = true;
+        auto sqrt3 = [](const double (&t)[4], double *o) {
+            o[0] = sqrt(t[0]);
+            o[1] = sqrt(t[1]);
+            o[2] = sqrt(t[2]);
+        };
 
         while (status == ENS_RUNNING && t < t_end - t_tol_d(t_end)) {
             if (--budget < 0) { status = ENS_BUDGET; break; }
@@ -576,16 +623,17 @@ k_ensemble(EnsDesc *__restrict__ D, int n_inst, EnsBuffers B, EnsParams P, const
                             v[3] += (double)(rf * zf);
                         }
                     }
-                    cl_reduce<OpSum, 4>(C, v);
+                    double sq[3];   // square roots of the first three sums
+                    cl_reduce<OpSum, 4, 3>(C, v, sq, sqrt3);
                     int cg_it = 0;
                     bool lin_ok = true;
                     if (PREC == 0) {
                         // ---- FP64 Jacobi-PCG
                         double rho = v[0];
-                        const double stop = P.tol_cg * sqrt(v[2]);
+                        const double stop = P.tol_cg * sq[2];
                         bool done = !(isfinite(v[0]) && isfinite(v[1]) && isfinite(v[2]));
                         if (done) lin_ok = false;
-                        else done = sqrt(v[1]) <= stop;
+                        else done = sq[1] <= stop;
                         double beta = 0.0;
                         int pi = 0;
                         while (!done) {
@@ -600,8 +648,9 @@ k_ensemble(EnsDesc *__restrict__ D, int n_inst, EnsBuffers B, EnsParams P, const
                                 q64[p] = qp;
                                 w1[0] += pp * qp;
                             }
-                            cl_reduce<OpSum, 1>(C, w1);
-                            const double alpha = rho / w1[0];
+                            double alpha;
+                            cl_reduce<OpSum, 1, 1>(C, w1, &alpha,
+                                                   [&](const double (&t)[1], double *o) { o[0] = rho / t[0]; });
                             if (!(w1[0] > 0.0) || !isfinite(alpha)) { lin_ok = false; break; }
                             double w2[2] = {0.0, 0.0};
                             for (long long p = lo + threadIdx.x; p < hi; p += blockDim.x) {
@@ -613,13 +662,17 @@ k_ensemble(EnsDesc *__restrict__ D, int n_inst, EnsBuffers B, EnsParams P, const
                                 w2[0] += rp2 * rp2;
                                 w2[1] += rp2 * zp2;
                             }
-                            cl_reduce<OpSum, 2>(C, w2);
+                            double fb[2];   // stop test passed (1 or 0), beta
+                            cl_reduce<OpSum, 2, 2>(C, w2, fb, [&](const double (&t)[2], double *o) {
+                                o[0] = sqrt(t[0]) <= stop ? 1.0 : 0.0;
+                                o[1] = t[1] / rho;
+                            });
                             cg_it++;
                             pi ^= 1;
                             if (!isfinite(w2[0]) || !isfinite(w2[1])) { lin_ok = false; break; }
-                            if (sqrt(w2[0]) <= stop) break;
+                            if (fb[0] != 0.0) break;
                             if (cg_it >= P.cg_max_it) { lin_ok = false; break; }
-                            beta = w2[1] / rho;
+                            beta = fb[1];
                             rho = w2[1];
                         }
                     } else {
@@ -630,12 +683,12 @@ k_ensemble(EnsDesc *__restrict__ D, int n_inst, EnsBuffers B, EnsParams P, const
                         for (;;) {
                             const bool finite = isfinite(v[0]) && isfinite(v[1]) && isfinite(v[2]) && isfinite(v[3]);
                             if (!finite) { lin_ok = false; break; }
-                            if (sqrt(v[0]) <= P.tol_cg * sqrt(v[1])) break;
+                            if (sq[0] <= P.tol_cg * sq[1]) break;
                             if (outer >= P.outer_max_it) { lin_ok = false; break; }
                             // inner solve A d = r32 from d = 0, FP32 throughout
                             int inner_it = 0;
                             if (v[2] > 0.0) {
-                                const float stop = (float)(P.tol_inner * sqrt(v[2]));
+                                const float stop = (float)(P.tol_inner * sq[2]);
                                 lin_ok = P.zline
                                              ? inner_pcg32<true>(C, geo32(g), (int)lo, (int)hi, K32, cb32, di32, r32,
                                                                  z32, P32[0], P32[1], q32, d32, LTi, LTc, 0.0f, stop,
@@ -663,7 +716,7 @@ k_ensemble(EnsDesc *__restrict__ D, int n_inst, EnsBuffers B, EnsParams P, const
                                 v[2] += (double)(rf * rf);
                                 v[3] += (double)(rf * zf);
                             }
-                            cl_reduce<OpSum, 4>(C, v);
+                            cl_reduce<OpSum, 4, 3>(C, v, sq, sqrt3);
                             outer++;
                         }
                     }
