@@ -67,7 +67,10 @@ __device__ __forceinline__ void closure_vg_df(const DevSoil &s, double Ks, doubl
 // double-double), x = exp(n L), l1 = log1p(x) (double-double):
 //   Se = exp(-m l1), w = 1/(1+x), ys = (x/(1+x))^m = (x/u) Se,
 //   K = Ks sqrt(Se) (1 - ys)^2 with 1 - ys = -expm1(m log1p(-w)) when
-//   ys > 1/2, C = (theta_s-theta_r) alpha n m ys w.
+//   ys > 1/2, C = (theta_s-theta_r) alpha n m ys w;
+// sqrt(Se) = exp(-m l1 / 2) and Se its square (f64_exp_sqr), 1/u and w
+// from the one reciprocal 1/(u (1 + x)), since each divide, square root
+// and exponential costs GB300's narrow FP64 pipe a dozen instructions.
 // n L and m l1 are formed with their rounding errors (two-product), so x and
 // Se keep a few units in the last place however large |L| or l1 are.
 // Beyond x = e^700 (a suction far outside any soil state) theta = theta_r +
@@ -91,13 +94,28 @@ __device__ __forceinline__ void closure_vg_fp64(const DevSoil &s, double Ks, dou
     // x = u^n; below e^-700 it is 0 to double precision beside 1 (Se = 1)
     const double x = nh >= -700.0 ? f64_exp_dd(nh, nl, tab) : 0.0;
     const double onepx = 1.0 + x;
-    const double w = rcp64(onepx);
+    // one reciprocal serves w = 1/(1 + x) and 1/u (separate ones where the
+    // product would overflow)
+    const double uo = u * onepx;
+    double w, iu;
+    if (uo < 1e300) {
+        const double q = rcp64(uo);
+        w = q * u;
+        iu = q * onepx;
+    } else {
+        w = rcp64(onepx);
+        iu = rcp64(u);
+    }
     double l1h, l1l;
     if (x >= 0.0078125) f64_log1p_big_dd(x, onepx, w, tab, l1h, l1l);
     else f64_log1p_dd(x, tab, l1h, l1l);
-    const double sh = -s.m * l1h;                  // in [-700 m, 0]
-    const double se = f64_exp_dd(sh, fma(-s.m, l1h, -sh) - s.m * l1l, tab);
-    const double ys = u >= 1e-30 ? (x * rcp64(u)) * se : f64_exp(s.m * ((nh - l1h) + (nl - l1l)), tab);
+    // Se^(1/2) = exp(-m l1 / 2), with Se = (Se^(1/2))^2 from the same
+    // exponential (K needs the root, theta and C need Se)
+    const double hm = 0.5 * s.m;
+    const double sh = -hm * l1h;                   // in [-350, 0]
+    double s2, se;
+    f64_exp_sqr(sh, fma(-hm, l1h, -sh) - hm * l1l, tab, s2, se);
+    const double ys = u >= 1e-30 ? (x * iu) * se : f64_exp(s.m * ((nh - l1h) + (nl - l1l)), tab);
     double omy;
     if (ys <= 0.5) {
         omy = 1.0 - ys;
@@ -110,7 +128,7 @@ __device__ __forceinline__ void closure_vg_fp64(const DevSoil &s, double Ks, dou
         omy = -f64_expm1_neg(s.m * lw, tab);
     }
     th = s.theta_r + dth * se;
-    K = Ks * sqrt(se) * (omy * omy);
+    K = Ks * s2 * (omy * omy);
     C = s.cfac * (ys * w);
 }
 

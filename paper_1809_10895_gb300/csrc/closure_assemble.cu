@@ -333,13 +333,13 @@ void launch_state_check_commit(cudaStream_t s, int nblk, const Grid &g, const ui
 // hosts this builds for), each rounded once.
 void make_ff_tables(FFTables *t)
 {
-    for (int j = 0; j < 64; j++) {
-        const long double e = exp2l((long double)j / 64.0L);
+    for (int j = 0; j < F64_TAB; j++) {
+        const long double e = exp2l((long double)j / (long double)F64_TAB);
         t->e2h[j] = (double)e;
         t->e2l[j] = (double)(e - (long double)t->e2h[j]);
     }
-    for (int j = 0; j <= 64; j++) {
-        const long double F = 1.0L + (long double)j / 64.0L;
+    for (int j = 0; j <= F64_TAB; j++) {
+        const long double F = 1.0L + (long double)j / (long double)F64_TAB;
         const long double lf = logl(F);
         t->lFh[j] = (double)(rintl(lf * 4398046511104.0L) / 4398046511104.0L);   // 2^42 grid
         t->lFl[j] = (double)(lf - (long double)t->lFh[j]);

@@ -4,17 +4,20 @@
 // Method: P. T. P. Tang, "Table-driven implementation of the exponential
 // function in IEEE floating-point arithmetic", ACM TOMS 15 (1989) 144-157,
 // and "Table-driven implementation of the logarithm function in IEEE
-// floating-point arithmetic", ACM TOMS 16 (1990) 378-400, with 64-entry
-// tables computed on the host in extended precision:
-//   exp(y)  = 2^M 2^(j/64) exp(r),  y = (64 M + j) ln2/64 + r, |r| <= ln2/128,
-//             exp(r) - 1 by its Taylor series to r^6 (truncation < 2^-57);
-//   log(u)  = E ln2 + log(F) + log1p(f/F),  u = 2^E m, F = 1 + j/64 nearest
-//             to m, f = m - F exact, |f/F| <= 1/128, log1p by its Taylor
-//             series to v^7 (truncation < 2^-59);
+// floating-point arithmetic", ACM TOMS 16 (1990) 378-400, with 1024-entry
+// tables computed on the host in extended precision (F64_TAB below):
+//   exp(y)  = 2^M 2^(j/1024) exp(r),  y = (1024 M + j) ln2/1024 + r,
+//             |r| <= ln2/2048, exp(r) - 1 by its Taylor series to r^4
+//             (truncation < 2^-64);
+//   log(u)  = E ln2 + log(F) + log1p(f/F),  u = 2^E m, F = 1 + j/1024
+//             nearest to m, f = m - F exact, |f/F| <= 2^-11, log1p by its
+//             Taylor series to v^5 (truncation < 2^-57 relative);
 // log1p(x) and expm1(z) reuse them with the exact corrections of 1 + x and
-// of 2^M 2^(j/64) - 1 (Sterbenz), and short Taylor series near 0.  Each
-// result is within a few units in the last place; the closures' parity
-// tests bound theta* to 1e-15 relative against the oracle's pow forms.
+// of 2^M 2^(j/1024) - 1, and short Taylor series near 0.  The large tables
+// buy the short polynomials: GB300's FP64 pipe, not memory, bounds the
+// closures.  Each result is within a few units in the last place; the
+// closures' parity tests bound theta* to 1e-15 relative against the
+// oracle's pow forms.
 //
 // The tables live in FFTables (ff.cuh) beside the double-float ones.
 #pragma once
@@ -31,9 +34,9 @@ namespace rf {
 // significant bits.
 constexpr double F64_LN2_HI = 0.6931471805598903;      // 0x3FE62E42FEFA3800
 constexpr double F64_LN2_LO = 5.497923018708371e-14;   // ln 2 - F64_LN2_HI
-constexpr double F64_INV_LN2_64 = 92.33248261689366;   // 64 / ln 2
-constexpr double F64_LN2_64_HI = F64_LN2_HI / 64.0;    // exact (a power-of-two scaling)
-constexpr double F64_LN2_64_LO = F64_LN2_LO / 64.0;
+constexpr double F64_INV_LN2_N = 1477.3197218702985;   // F64_TAB / ln 2
+constexpr double F64_LN2_N_HI = F64_LN2_HI / F64_TAB;  // exact (a power-of-two scaling)
+constexpr double F64_LN2_N_LO = F64_LN2_LO / F64_TAB;
 
 // 2^k for integer k in [-1022, 1023] from its bit pattern.
 __device__ __forceinline__ double f64_pow2i(int k)
@@ -41,19 +44,33 @@ __device__ __forceinline__ double f64_pow2i(int k)
     return __longlong_as_double((long long)(k + 1023) << 52);
 }
 
+// exp(y) = (th + th p + tl) 2^M: the table entry 2^(j/1024) = th + tl and
+// p = exp(r) - 1, for y in [-745, 709.8].
+__device__ __forceinline__ void f64_exp_core(double y, const FFTables *__restrict__ tab, double &th, double &tl,
+                                             double &p, int &M)
+{
+    // N = nearest integer to y 1024/ln2 (round-to-nearest through the 1.5 2^52 shift)
+    const double shifter = 6755399441055744.0;
+    const double t = fma(y, F64_INV_LN2_N, shifter);
+    const int n = (int)(__double_as_longlong(t) & 0xffffffffLL);
+    const double N = t - shifter;
+    const double r = fma(-N, F64_LN2_N_LO, fma(-N, F64_LN2_N_HI, y));   // |r| <= ln2/2048
+    // exp(r) - 1 = r + r^2 (1/2 + r (1/6 + r/24))
+    const double q = fma(r, fma(r, 1.0 / 24.0, 1.0 / 6.0), 0.5);
+    p = fma(r * r, q, r);
+    const int j = n & (F64_TAB - 1);
+    M = n >> F64_TAB_BITS;                          // arithmetic shift: floor(n / 1024)
+    th = tab->e2h[j];
+    tl = tab->e2l[j];
+}
+
 // exp(y) for y in [-708, 709] (normal results; the caller keeps y there).
 __device__ __forceinline__ double f64_exp_nc(double y, const FFTables *__restrict__ tab)
 {
-    const double shifter = 6755399441055744.0;
-    const double t = fma(y, F64_INV_LN2_64, shifter);
-    const int n = (int)(__double_as_longlong(t) & 0xffffffffLL);
-    const double N = t - shifter;
-    const double r = fma(-N, F64_LN2_64_LO, fma(-N, F64_LN2_64_HI, y));   // |r| <= ln2/128
-    const double q = fma(r, fma(r, fma(r, fma(r, 1.0 / 720.0, 1.0 / 120.0), 1.0 / 24.0), 1.0 / 6.0), 0.5);
-    const double p = fma(r * r, q, r);
-    const int j = n & 63;
-    const double Th = tab->e2h[j], Tl = tab->e2l[j];
-    return (Th + fma(Th, p, Tl)) * f64_pow2i(n >> 6);
+    double th, tl, p;
+    int M;
+    f64_exp_core(y, tab, th, tl, p, M);
+    return (th + fma(th, p, tl)) * f64_pow2i(M);
 }
 
 // exp(y) for y in [-1400, 709.7]; 0 below about -745 (underflow), +inf
@@ -62,21 +79,27 @@ __device__ __forceinline__ double f64_exp(double y, const FFTables *__restrict__
 {
     if (!(y < 709.782712893384)) return y != y ? y : __longlong_as_double(0x7ff0000000000000LL);
     if (y < -745.2) return 0.0;
-    // N = nearest integer to y 64/ln2 (round-to-nearest through the 1.5 2^52 shift)
-    const double shifter = 6755399441055744.0;
-    const double t = fma(y, F64_INV_LN2_64, shifter);
-    const int n = (int)(__double_as_longlong(t) & 0xffffffffLL);
-    const double N = t - shifter;
-    const double r = fma(-N, F64_LN2_64_LO, fma(-N, F64_LN2_64_HI, y));   // |r| <= ln2/128
-    // exp(r) - 1 = r + r^2 (1/2 + r (1/6 + r (1/24 + r (1/120 + r/720))))
-    const double q = fma(r, fma(r, fma(r, fma(r, 1.0 / 720.0, 1.0 / 120.0), 1.0 / 24.0), 1.0 / 6.0), 0.5);
-    const double p = fma(r * r, q, r);
-    const int j = n & 63;
-    const int M = n >> 6;                          // arithmetic shift: floor(n / 64)
-    const double Th = tab->e2h[j], Tl = tab->e2l[j];
-    const double v = Th + fma(Th, p, Tl);          // 2^(j/64) exp(r)
+    double th, tl, p;
+    int M;
+    f64_exp_core(y, tab, th, tl, p, M);
+    const double v = th + fma(th, p, tl);           // 2^(j/1024) exp(r)
     if (M >= -1022) return v * f64_pow2i(M);
     return (v * f64_pow2i(M + 600)) * f64_pow2i(-600);   // subnormal result
+}
+
+// E = exp(hi + lo) and E^2, for |lo| <= ulp(hi) and hi in [-350, 350]: with
+// E 2^-M = th + vl, vl = tl + th (p + lo) (to within p lo), E rounds th + vl
+// once, and E^2 = th^2 + vl (2 th + vl) rounds once, th^2 exact inside the
+// fused multiply-add.  Both within about half a unit in the last place.
+__device__ __forceinline__ void f64_exp_sqr(double hi, double lo, const FFTables *__restrict__ tab, double &e,
+                                            double &e2)
+{
+    double th, tl, p;
+    int M;
+    f64_exp_core(hi, tab, th, tl, p, M);
+    const double vl = fma(th, p + lo, tl);
+    e = (th + vl) * f64_pow2i(M);
+    e2 = fma(th, th, vl * fma(2.0, th, vl)) * f64_pow2i(2 * M);
 }
 
 // log(u) for u > 0 (finite) as an unevaluated sum hi + lo (|lo| <= ulp(hi)):
@@ -92,12 +115,13 @@ __device__ __forceinline__ void f64_log_dd(double u, const FFTables *__restrict_
     }
     const long long mant = b & 0x000fffffffffffffLL;
     const double m = __longlong_as_double(mant | 0x3ff0000000000000LL);    // [1, 2)
-    const int j = (int)((mant + (1LL << 45)) >> 46);                       // nearest 1 + j/64, j in [0, 64]
-    const double F = __longlong_as_double(0x3ff0000000000000LL + ((long long)j << 46));   // 1 + j/64 (2 at j = 64)
-    const double f = m - F;                        // exact, |f| <= 1/128
+    constexpr int SH = 52 - F64_TAB_BITS;
+    const int j = (int)((mant + (1LL << (SH - 1))) >> SH);                 // nearest 1 + j/1024, j in [0, 1024]
+    const double F = __longlong_as_double(0x3ff0000000000000LL + ((long long)j << SH));   // 2 at j = 1024
+    const double f = m - F;                        // exact, |f| <= 2^-11
     const double v = f * tab->invF[j];
-    // log1p(v) = v + v^2 (-1/2 + v (1/3 + v (-1/4 + v (1/5 + v (-1/6 + v/7)))))
-    const double q = fma(v, fma(v, fma(v, fma(v, fma(v, 1.0 / 7.0, -1.0 / 6.0), 0.2), -0.25), 1.0 / 3.0), -0.5);
+    // log1p(v) = v + v^2 (-1/2 + v (1/3 + v (-1/4 + v/5)))
+    const double q = fma(v, fma(v, fma(v, 0.2, -0.25), 1.0 / 3.0), -0.5);
     const double p = fma(v * v, q, v);
     const double e = (double)E;
     const double A = fma(e, F64_LN2_HI, tab->lFh[j]);            // exact: both on a 2^-42 grid
@@ -171,22 +195,14 @@ __device__ __forceinline__ double f64_expm1_neg(double z, const FFTables *__rest
         return fma(z * z, q, z);
     }
     if (z < -40.0) return -1.0 + f64_exp_nc(fmax(z, -700.0), tab);
-    const double shifter = 6755399441055744.0;
-    const double t = fma(z, F64_INV_LN2_64, shifter);
-    const int n = (int)(__double_as_longlong(t) & 0xffffffffLL);
-    const double N = t - shifter;
-    const double r = fma(-N, F64_LN2_64_LO, fma(-N, F64_LN2_64_HI, z));
-    const double q = fma(r, fma(r, fma(r, fma(r, 1.0 / 720.0, 1.0 / 120.0), 1.0 / 24.0), 1.0 / 6.0), 0.5);
-    const double p = fma(r * r, q, r);
-    const int j = n & 63;
-    const double s = f64_pow2i(n >> 6);
-    const double Th = tab->e2h[j] * s, Tl = tab->e2l[j] * s;
-    // 2^M 2^(j/64) (1 + p) - 1 = (Th - 1) + (Tl + Th p); Th - 1 is exact for Th in [1/2, 2]
+    double th, tl, p;
+    int M;
+    f64_exp_core(z, tab, th, tl, p, M);
+    const double s = f64_pow2i(M);
+    const double Th = th * s, Tl = tl * s;
+    // 2^M 2^(j/1024) (1 + p) - 1 = (Th - 1) + (Tl + Th p); Th - 1 is exact for Th in [1/2, 2]
     return (Th - 1.0) + fma(Th, p, Tl);
 }
 #endif
-
-// Host: fill the FP64 tables of *t (extended-precision host arithmetic).
-void make_f64_tables(FFTables *t);
 
 }  // namespace rf

@@ -24,14 +24,18 @@ struct ff {
 };
 
 // 64-entry tables, filled on the host (see make_ff_tables).
+// Entries of the FP64 argument-reduction tables (f64m.cuh).
+constexpr int F64_TAB_BITS = 10;
+constexpr int F64_TAB = 1 << F64_TAB_BITS;
+
 struct FFTables {
     float2 exp2j[64];   // 2^(j/64)
     float2 logc[64];    // log(c_j), c_j = 1 + (j + 1/2)/64
     float2 invc[64];    // 1/c_j
-    // FP64 tables of f64m.cuh: 2^(j/64) = e2h + e2l; log(1 + j/64) = lFh +
-    // lFl with lFh on the 2^-42 grid; invF = 1/(1 + j/64) rounded
-    double e2h[64], e2l[64];
-    double lFh[65], lFl[65], invF[65];
+    // FP64 tables of f64m.cuh: 2^(j/N) = e2h + e2l; log(1 + j/N) = lFh + lFl
+    // with lFh on the 2^-42 grid; invF = 1/(1 + j/N) rounded (N = F64_TAB)
+    double e2h[F64_TAB], e2l[F64_TAB];
+    double lFh[F64_TAB + 1], lFl[F64_TAB + 1], invF[F64_TAB + 1];
 };
 
 #ifdef __CUDACC__
