@@ -335,14 +335,14 @@ void make_ff_tables(FFTables *t)
 {
     for (int j = 0; j < F64_TAB; j++) {
         const long double e = exp2l((long double)j / (long double)F64_TAB);
-        t->e2h[j] = (double)e;
-        t->e2l[j] = (double)(e - (long double)t->e2h[j]);
+        const double hi = (double)e;
+        t->e2[j] = make_double2(hi, (double)(e - (long double)hi));
     }
     for (int j = 0; j <= F64_TAB; j++) {
         const long double F = 1.0L + (long double)j / (long double)F64_TAB;
         const long double lf = logl(F);
-        t->lFh[j] = (double)(rintl(lf * 4398046511104.0L) / 4398046511104.0L);   // 2^42 grid
-        t->lFl[j] = (double)(lf - (long double)t->lFh[j]);
+        const double hi = (double)(rintl(lf * 4398046511104.0L) / 4398046511104.0L);   // 2^42 grid
+        t->lF[j] = make_double2(hi, (double)(lf - (long double)hi));
         t->invF[j] = (double)(1.0L / F);
     }
     for (int j = 0; j < 64; j++) {

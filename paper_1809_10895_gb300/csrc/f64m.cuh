@@ -60,8 +60,9 @@ __device__ __forceinline__ void f64_exp_core(double y, const FFTables *__restric
     p = fma(r * r, q, r);
     const int j = n & (F64_TAB - 1);
     M = n >> F64_TAB_BITS;                          // arithmetic shift: floor(n / 1024)
-    th = tab->e2h[j];
-    tl = tab->e2l[j];
+    const double2 T = tab->e2[j];
+    th = T.x;
+    tl = T.y;
 }
 
 // exp(y) for y in [-708, 709] (normal results; the caller keeps y there).
@@ -124,8 +125,9 @@ __device__ __forceinline__ void f64_log_dd(double u, const FFTables *__restrict_
     const double q = fma(v, fma(v, fma(v, 0.2, -0.25), 1.0 / 3.0), -0.5);
     const double p = fma(v * v, q, v);
     const double e = (double)E;
-    const double A = fma(e, F64_LN2_HI, tab->lFh[j]);            // exact: both on a 2^-42 grid
-    const double B = fma(e, F64_LN2_LO, tab->lFl[j]) + p;
+    const double2 LF = tab->lF[j];
+    const double A = fma(e, F64_LN2_HI, LF.x);                   // exact: both on a 2^-42 grid
+    const double B = fma(e, F64_LN2_LO, LF.y) + p;
     hi = A + B;
     lo = (A - hi) + B;                             // Fast2Sum (|A| >= |B| or A = 0)
 }

@@ -32,10 +32,13 @@ struct FFTables {
     float2 exp2j[64];   // 2^(j/64)
     float2 logc[64];    // log(c_j), c_j = 1 + (j + 1/2)/64
     float2 invc[64];    // 1/c_j
-    // FP64 tables of f64m.cuh: 2^(j/N) = e2h + e2l; log(1 + j/N) = lFh + lFl
-    // with lFh on the 2^-42 grid; invF = 1/(1 + j/N) rounded (N = F64_TAB)
-    double e2h[F64_TAB], e2l[F64_TAB];
-    double lFh[F64_TAB + 1], lFl[F64_TAB + 1], invF[F64_TAB + 1];
+    // FP64 tables of f64m.cuh (N = F64_TAB): e2[j] = (hi, lo) with
+    // 2^(j/N) = hi + lo; lF[j] = (hi, lo) with log(1 + j/N) = hi + lo, hi on
+    // the 2^-42 grid; invF = 1/(1 + j/N) rounded.  Each pair is one 16-byte
+    // load: the lookups are gathers, one L1 wavefront per lane's line.
+    double2 e2[F64_TAB];
+    double2 lF[F64_TAB + 1];
+    double invF[F64_TAB + 1];
 };
 
 #ifdef __CUDACC__
