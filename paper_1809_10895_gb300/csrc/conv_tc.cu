@@ -389,8 +389,260 @@ k_conv3d_tc(TcParams p, const __grid_constant__ CUtensorMap in_map, int cin_mem,
         asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(S::TMEM_COLS) : "memory");
 }
 
+// ------------------------------------------------------------ weight gradient
+// Weight and bias gradient of a 32 -> 32 convolution on the tcgen05 tensor
+// cores:
+//   dW[co][tap 32 + ci] += sum_v X[v + off(tap)][ci] G[v][co],   db[co] += sum_v G[v][co].
+// GEMM: M = (dy, ci), N = co, K = voxels.  The contraction runs over the
+// voxels, the outer index of both channels-last operands, so both are
+// transposed into K-major tiles in shared memory.  Per tile of 32 x 4 x 2
+// output voxels:
+//   X's halo tile (34 x 6 x 4 voxels) lands by four bulk tensor copies (one
+//     per 8-channel plane, 16-byte rows in halo-linear order), and is
+//     transposed by ldmatrix.trans into three copies
+//     T_dx[(z', y', ci)][x] = X[x + dx][y'][z'][ci], dx = -1, 0, 1, over the
+//     tile's halo rows (z', y') and its 32 x positions;
+//   G_T[(z, y)][co][x] = G[x][y][z][co] over the interior rows (zero outside
+//     the volume), from 4-byte pairs loaded a tile ahead and transposed by
+//     movmatrix.
+// For tap (dz, dy, dx) and output row (y, z) the A operand is T_dx at row
+// (z + dz, y + dy); the three dy taps are consecutive blocks of 32 rows, so
+// one M = 128 MMA covers dy = -1, 0, 1 (its fourth block of 32 rows is
+// discarded).  Per output row: 9 (dz, dx) chains of K = 32 (two MMAs of
+// K = 16) into 9 accumulators of 32 TMEM columns, which hold the CTA's sums
+// over all its tiles; then one atomic add per weight per CTA.  The bias
+// gradient is summed from the G pairs as they arrive.  The next tile's copy
+// is issued as soon as the current one is transposed, so it flies while the
+// MMAs run; the transposed operands are single-buffered (every thread waits,
+// bounded, for the MMAs before they are rewritten).
+constexpr int WT_TX = 32, WT_TY = 4, WT_TZ = 2;
+constexpr int WT_HX = WT_TX + 2, WT_HY = WT_TY + 2, WT_HZ = WT_TZ + 2;
+constexpr int WT_ROWS = (WT_HZ * WT_HY + 1) * 32;   // (z', y', ci) rows, plus one block of 32 read into discarded rows
+constexpr int WT_LBO = WT_ROWS * 16;                // bytes between the K groups (8 x positions) of a copy
+constexpr int WT_COPY = 4 * WT_LBO;                 // one dx copy: 32 x positions
+constexpr int WT_GROW = 4 * 32 * 16;                // one interior row of G_T: 4 K groups x 32 co x 16 bytes
+constexpr int WT_XPLANE = WT_HX * WT_HY * WT_HZ * 16;   // one 8-channel plane of the halo tile
+constexpr int WT_OFF_G = 3 * WT_COPY, WT_OFF_X = WT_OFF_G + WT_TY * WT_TZ * WT_GROW;
+constexpr int WT_SMEM = WT_OFF_X + 4 * WT_XPLANE + 1024;
+constexpr int WT_THREADS = 256, WT_WARPS = WT_THREADS / 32;
+constexpr int WT_XQUADS = 3 * WT_HZ * WT_HY * 4;    // ldmatrix.x4 of the three copies (4 K groups each)
+constexpr int WT_TMEM_COLS = 512;                   // 9 x 32 used
+constexpr int WT_KP = 27 * 32;                      // weights per output channel
+static_assert(WT_XQUADS % WT_WARPS == 0, "whole rounds of transposes");
+static_assert(WT_TY * WT_TZ * 4 * 2 == 2 * 32, "G_T blocks: 16 per warp, the warp's channel block fixed");
+static_assert(WT_SMEM <= 227 * 1024, "shared memory");
+static_assert(WT_LBO / 16 < (1 << 14), "descriptor offset field");
+static_assert(WT_XPLANE % 128 == 0 && WT_OFF_X % 128 == 0, "tensor-copy destinations 128-byte aligned");
+
+// Transpose of an 8 x 8 BF16 matrix held one 4-byte pair per lane (lane l:
+// row l / 4, columns 2 (l % 4), 2 (l % 4) + 1), in the same layout.
+__device__ __forceinline__ uint32_t movm_t(uint32_t a)
+{
+    uint32_t d;
+    asm volatile("movmatrix.sync.aligned.m8n8.trans.b16 %0, %1;" : "=r"(d) : "r"(a));
+    return d;
+}
+
+// Four 8 x 8 BF16 matrices from shared memory, transposed (lanes 8j..8j+7
+// give the 16-byte rows of matrix j).
+__device__ __forceinline__ void ldsm_t4(uint32_t addr, uint32_t (&r)[4])
+{
+    asm volatile("ldmatrix.sync.aligned.m8n8.x4.trans.shared.b16 {%0,%1,%2,%3}, [%4];"
+                 : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3])
+                 : "r"(addr));
+}
+
+__device__ __forceinline__ float bf16_lo(uint32_t v) { return __uint_as_float(v << 16); }
+__device__ __forceinline__ float bf16_hi(uint32_t v) { return __uint_as_float(v & 0xffff0000u); }
+
+struct WtTile {
+    int b, x0, y0, z0;
+};
+
+__device__ __forceinline__ WtTile wt_tile(long long tile, int ntx, int nty, int ntz)
+{
+    long long q = tile;
+    const int tx = (int)(q % ntx);
+    q /= ntx;
+    const int ty = (int)(q % nty);
+    q /= nty;
+    const int tz = (int)(q % ntz);
+    return WtTile{(int)(q / ntz), tx * WT_TX, ty * WT_TY, tz * WT_TZ};
+}
+
+__global__ void __launch_bounds__(WT_THREADS, 1)
+k_wgrad_tc(const __grid_constant__ CUtensorMap x_map, const __nv_bfloat16 *__restrict__ G, int B, int D, int H,
+           int W, int ntx, int nty, int ntz, long long tiles, float *__restrict__ dW, float *__restrict__ db,
+           int *fault)
+{
+    extern __shared__ unsigned char smem_raw[];
+    unsigned char *smem = reinterpret_cast<unsigned char *>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
+    unsigned char *sT = smem;                  // the three copies T_dx
+    unsigned char *sG = smem + WT_OFF_G;       // G_T
+    unsigned char *sX = smem + WT_OFF_X;       // X's halo tile, four 8-channel planes
+    __shared__ __align__(8) uint64_t x_bar, mma_bar;
+    __shared__ uint32_t s_tmem;
+    __shared__ int s_abort;
+    const int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
+    if (threadIdx.x == 0) {
+        mbar_init(&x_bar, 1);
+        mbar_init(&mma_bar, 1);
+        mbar_init_fence();
+        s_abort = 0;
+    }
+    if (warp == 0) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_addr(&s_tmem)),
+                     "r"(WT_TMEM_COLS)
+                     : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    }
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tmem = s_tmem;
+    volatile int *abort_flag = &s_abort;
+    const uint32_t *G2 = reinterpret_cast<const uint32_t *>(G);   // BF16 pairs
+    const long long HW = (long long)H * W;
+    const int r = lane >> 2, cp = lane & 3;   // the lane's row and channel pair in a G block
+    const int cbg = warp & 3;                 // the warp's channel block of G
+    float bs0 = 0.0f, bs1 = 0.0f;             // bias sums of channels 8 cbg + 2 cp, + 1
+    // thread 0: X tiles copied / waited for, MMA batches committed / waited for
+    int x_issued = 0, x_waited = 0, committed = 0, waited = 0;
+    auto issue_x = [&](long long tile) {
+        const WtTile t = wt_tile(tile, ntx, nty, ntz);
+        mbar_expect_tx(&x_bar, 4 * WT_XPLANE);
+        for (int cg = 0; cg < 4; cg++)
+            asm volatile(
+                "cp.async.bulk.tensor.5d.shared::cluster.global.mbarrier::complete_tx::bytes"
+                " [%0], [%1, {%3, %4, %5, %6, %7}], [%2];"
+                ::"r"(smem_addr(sX + cg * WT_XPLANE)), "l"(reinterpret_cast<uint64_t>(&x_map)),
+                  "r"(smem_addr(&x_bar)), "r"(cg * 8), "r"(t.x0 - 1), "r"(t.y0 - 1), "r"(t.z0 - 1), "r"(t.b)
+                : "memory");
+        x_issued++;
+    };
+    // the warp's 16 G blocks of a tile: pairs (row, kg) j = warp / 4 + 2 s, channel block cbg
+    auto load_g = [&](long long tile, uint32_t (&v)[16]) {
+        const WtTile t = wt_tile(tile, ntx, nty, ntz);
+        const long long vb = HW * (long long)D * t.b;
+#pragma unroll
+        for (int s = 0; s < 16; s++) {
+            const int j = (warp >> 2) + 2 * s;
+            const int row = j >> 2, kg = j & 3;
+            const int gx = t.x0 + 8 * kg + r, gy = t.y0 + row % WT_TY, gz = t.z0 + row / WT_TY;
+            v[s] = 0u;   // voxels outside the volume add nothing
+            if (gx < W && gy < H && gz < D)
+                v[s] = __ldg(G2 + (((gx + (long long)W * gy + HW * gz + vb) * 32 + 8 * cbg) >> 1) + cp);
+        }
+    };
+    uint32_t gv[16];
+    long long tile = blockIdx.x;
+    if (threadIdx.x == 0) issue_x(tile);
+    load_g(tile, gv);
+    for (int i = 0; tile < tiles; tile += gridDim.x, i++) {
+        const bool okx = wait_or_abort(&x_bar, (uint32_t)(i & 1), abort_flag);
+        if (threadIdx.x == 0 && okx) x_waited++;
+        __syncthreads();
+        if (*abort_flag) break;
+        // ---- X -> T_dx: quad q = ((dx + 1) HZ + z') HY + y') 4 + cb, matrix j = K group
+        const uint32_t xb = smem_addr(sX);
+        for (int qd = warp; qd < WT_XQUADS; qd += WT_WARPS) {
+            const int cb = qd & 3;
+            int t = qd >> 2;
+            const int yq = t % WT_HY;
+            t /= WT_HY;
+            const int zq = t % WT_HZ, dxi = t / WT_HZ;
+            // halo x of interior x = 8 kg + row is 8 kg + row + 1 + dx
+            const int hl = (zq * WT_HY + yq) * WT_HX + dxi + 8 * (lane >> 3) + (lane & 7);
+            uint32_t v[4];
+            ldsm_t4(xb + (uint32_t)(cb * WT_XPLANE + hl * 16), v);
+            unsigned char *dst = sT + dxi * WT_COPY + ((zq * WT_HY + yq) * 4 + cb) * 128 + lane * 4;
+#pragma unroll
+            for (int kg = 0; kg < 4; kg++) *reinterpret_cast<uint32_t *>(dst + kg * WT_LBO) = v[kg];
+        }
+        // ---- G -> G_T (and the bias sums)
+#pragma unroll
+        for (int s = 0; s < 16; s++) {
+            const int j = (warp >> 2) + 2 * s;
+            bs0 += bf16_lo(gv[s]);
+            bs1 += bf16_hi(gv[s]);
+            *reinterpret_cast<uint32_t *>(sG + (j >> 2) * WT_GROW + (j & 3) * 512 + cbg * 128 + lane * 4) = movm_t(gv[s]);
+        }
+        fence_proxy_async_smem();   // generic stores, read next by the tensor cores
+        __syncthreads();            // operands written, X's stage free
+        const bool more = tile + gridDim.x < tiles;
+        if (threadIdx.x == 0) {
+            if (more) issue_x(tile + gridDim.x);   // lands while the MMAs run
+            tc_fence_after();
+            const uint32_t tb = smem_addr(sT), gb = smem_addr(sG);
+            for (int c9 = 0; c9 < 9; c9++) {
+                const int dz = c9 / 3 - 1, dxi = c9 % 3;
+                const uint32_t d = tmem + (uint32_t)(c9 * 32);
+                for (int iz = 0; iz < WT_TZ; iz++)
+                    for (int iy = 0; iy < WT_TY; iy++) {
+                        const int m0 = ((iz + 1 + dz) * WT_HY + iy) * 32;   // rows of dy = -1
+                        for (int ks = 0; ks < 2; ks++) {
+                            const uint64_t ad =
+                                smem_desc(tb + (uint32_t)(dxi * WT_COPY + 2 * ks * WT_LBO + m0 * 16), WT_LBO, 128);
+                            const uint64_t bd =
+                                smem_desc(gb + (uint32_t)((iz * WT_TY + iy) * WT_GROW + 2 * ks * 512), 512, 128);
+                            tc_mma(d, ad, bd, TcShape<32, 32>::IDESC, (committed | iz | iy | ks) ? 1u : 0u);
+                        }
+                    }
+            }
+            tc_commit(&mma_bar);
+            committed++;
+        }
+        if (more) load_g(tile + gridDim.x, gv);   // in flight during the MMAs
+        // the operands are rewritten only after the MMAs completed; the
+        // barrier makes the decision to stop the same in every thread
+        const bool ok = wait_or_abort(&mma_bar, (uint32_t)(i & 1), abort_flag);
+        if (threadIdx.x == 0 && ok) waited++;
+        tc_fence_after();
+        __syncthreads();
+        if (*abort_flag) break;
+    }
+    __syncthreads();
+    if (*abort_flag) {
+        if (threadIdx.x == 0) {
+            atomicExch(fault, 1);
+            // copies and MMA batches still in flight
+            for (int j = x_waited; j < x_issued; j++) mbar_wait_bounded(&x_bar, (uint32_t)(j & 1), TC_WAIT_TRIES);
+            for (int j = waited; j < committed; j++) mbar_wait_bounded(&mma_bar, (uint32_t)(j & 1), TC_WAIT_TRIES);
+        }
+    } else {
+        if (warp < 3) {
+            // TMEM lanes 32 warp + lane: dy = warp - 1, ci = lane
+            for (int c9 = 0; c9 < 9; c9++) {
+                float v[32];
+                __syncwarp();
+                tc_ld32(tmem + ((uint32_t)(32 * warp) << 16) + (uint32_t)(c9 * 32), v);
+                const int tap = (c9 / 3) * 9 + warp * 3 + c9 % 3;
+#pragma unroll
+                for (int co = 0; co < 32; co++) atomicAdd(&dW[(long long)co * WT_KP + tap * 32 + lane], v[co]);
+            }
+        }
+        // bias: sum over the 8 rows of a block (lanes with the same channel pair)
+#pragma unroll
+        for (int o = 4; o < 32; o <<= 1) {
+            bs0 += __shfl_xor_sync(0xffffffffu, bs0, o);
+            bs1 += __shfl_xor_sync(0xffffffffu, bs1, o);
+        }
+        if (db && lane < 4) {
+            atomicAdd(&db[8 * cbg + 2 * lane], bs0);
+            atomicAdd(&db[8 * cbg + 2 * lane + 1], bs1);
+        }
+    }
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    __syncwarp();
+    if (warp == 0)
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(WT_TMEM_COLS) : "memory");
+}
+
 // ------------------------------------------------------------------- host
-static bool encode_activation_map(CUtensorMap *m, const void *in, int cin_mem, int B, int D, int H, int W)
+static bool encode_activation_map(CUtensorMap *m, const void *in, int cin_mem, int B, int D, int H, int W,
+                                  int bx = TC_HX, int by = TC_HY, int bz = TC_HZ)
 {
     static void *fn = nullptr;
     if (!fn) {
@@ -408,7 +660,7 @@ static bool encode_activation_map(CUtensorMap *m, const void *in, int cin_mem, i
     const cuuint64_t row = (cuuint64_t)cin_mem * 2;   // bytes per voxel
     const cuuint64_t dims[5] = {(cuuint64_t)cin_mem, (cuuint64_t)W, (cuuint64_t)H, (cuuint64_t)D, (cuuint64_t)B};
     const cuuint64_t strides[4] = {row, (cuuint64_t)W * row, (cuuint64_t)H * W * row, (cuuint64_t)D * H * W * row};
-    const cuuint32_t box[5] = {8, TC_HX, TC_HY, TC_HZ, 1};
+    const cuuint32_t box[5] = {8, (cuuint32_t)bx, (cuuint32_t)by, (cuuint32_t)bz, 1};
     const cuuint32_t estr[5] = {1, 1, 1, 1, 1};
     return encode(m, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 5, const_cast<void *>(in), dims, strides, box, estr,
                   CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
@@ -464,6 +716,28 @@ cudaError_t conv3d_tc(cudaStream_t s, int cin_mem, int cinp, int nout, int out_c
     if (cinp == 32 && nout == 16)
         return launch_tc<32, 16>(s, map, p, cin_mem, out_ch, Wb, bias, res, out_b, out_f, relu, fault, num_sms);
     return cudaErrorInvalidValue;
+}
+
+cudaError_t wgrad_tc32(cudaStream_t s, const void *X, const void *G, int B, int D, int H, int W, float *dW,
+                       float *db, int *fault, int num_sms)
+{
+    if ((reinterpret_cast<uintptr_t>(X) & 15u) || (reinterpret_cast<uintptr_t>(G) & 3u) || !fault)
+        return cudaErrorInvalidValue;
+    CUtensorMap map;
+    if (!encode_activation_map(&map, X, 32, B, D, H, W, WT_HX, WT_HY, WT_HZ)) return cudaErrorInvalidValue;
+    static bool attr = false;
+    if (!attr) {
+        cudaError_t e = cudaFuncSetAttribute(k_wgrad_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, WT_SMEM);
+        if (e != cudaSuccess) return e;
+        attr = true;
+    }
+    const int ntx = (W + WT_TX - 1) / WT_TX, nty = (H + WT_TY - 1) / WT_TY, ntz = (D + WT_TZ - 1) / WT_TZ;
+    const long long tiles = (long long)ntx * nty * ntz * B;
+    if (tiles < 1) return cudaSuccess;
+    const int grid = (int)(tiles < num_sms ? tiles : num_sms);
+    k_wgrad_tc<<<grid, WT_THREADS, WT_SMEM, s>>>(map, static_cast<const __nv_bfloat16 *>(G), B, D, H, W, ntx, nty,
+                                                ntz, tiles, dW, db, fault);
+    return cudaGetLastError();
 }
 
 // Weights for the tensor-core kernel: dst[n][tap cinp + c] = src[n][tap cin + c]

@@ -47,6 +47,12 @@ void prep_tc_weights(cudaStream_t s, const void *src, int n_src, int cin, int kp
 // (cin, cout) in {(32, 32), (8, 32), (32, 8)}.
 cudaError_t wgrad_mma(cudaStream_t s, int cin, int cout, const void *X, const void *G, int B, int D, int H, int W,
                       float *dW, float *db, int num_sms);
+// The 32 -> 32 weight (and bias) gradient on the tcgen05 tensor cores
+// (conv_tc.cu), same arguments and accumulation as wgrad_mma; X and G 4-byte
+// aligned (X 16 bytes).  A device wait that runs out sets *fault (the sums are then
+// incomplete).
+cudaError_t wgrad_tc32(cudaStream_t s, const void *X, const void *G, int B, int D, int H, int W, float *dW,
+                       float *db, int *fault, int num_sms);
 void relu_bwd(cudaStream_t s, const void *y, const float *dy, float *dx, long long n, const float *add);
 void to_bf16(cudaStream_t s, const float *a, void *b, long long n);
 void add(cudaStream_t s, float *a, const float *b, long long n);

@@ -266,13 +266,17 @@ __global__ void k_take0(const float *__restrict__ y8, float *__restrict__ y, lon
         y[i] = y8[i * nn::C_OUT_P];
 }
 
-// Weight gradient of a 32 -> 32 layer from its BF16 input and BF16 output
-// gradient, on the tensor cores.
+// Weight gradient of a layer from its BF16 input and BF16 output gradient, on
+// the tensor cores: tcgen05 for the 32 -> 32 layers, mma.sync for the input
+// and output layers (8 padded channels on one side).
 rf_status wgrad_tc(rf_nn *n, cudaStream_t s, int l, const void *in, const void *g_bf16, int B, int D, int H, int W)
 {
     const LayerDims &d = n->L[l];
     n->launches++;
-    NN_CUDA(nn::wgrad_mma(s, d.cinp, d.coutp, in, g_bf16, B, D, H, W, n->G + d.w, n->G + d.b, n->num_sms));
+    if (d.cinp == 32 && d.coutp == 32)
+        NN_CUDA(nn::wgrad_tc32(s, in, g_bf16, B, D, H, W, n->G + d.w, n->G + d.b, n->fault, n->num_sms));
+    else
+        NN_CUDA(nn::wgrad_mma(s, d.cinp, d.coutp, in, g_bf16, B, D, H, W, n->G + d.w, n->G + d.b, n->num_sms));
     return RF_OK;
 }
 

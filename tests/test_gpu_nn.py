@@ -85,7 +85,7 @@ def _in_round_interval(got, v, e, relu=False):
     return (got >= lo) & (got <= hi)
 
 
-@pytest.mark.parametrize("shape", [(1, 5, 7, 9), (2, 4, 6, 5)])
+@pytest.mark.parametrize("shape", [(1, 5, 7, 9), (2, 4, 6, 5), (1, 3, 6, 41)])
 def test_gradient_layers_match_oracle_elementwise(shape):
     """Every layer of the gradient evaluation, element by element, against
     the oracle evaluated on the GPU's own stored inputs of that layer (the
