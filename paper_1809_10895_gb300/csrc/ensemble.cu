@@ -244,68 +244,145 @@ __device__ __forceinline__ float apply32_i(const Geo32 &g, int p, const float *_
 // Vertical-line preconditioner M: the FP32 operator without its horizontal
 // faces.  Per column (i, j) of an instance it is the tridiagonal matrix with
 // diagonal cb_k + the two vertical face terms and off-diagonals
-// -wz (K_k + K_k+1)/2: symmetric and diagonally dominant with cb > 0, so the
-// Thomas recurrence needs no pivoting.  A - M is the horizontal graph
-// Laplacian (positive semi-definite), so every eigenvalue of M^-1 A is >= 1,
-// and M^-1 is exact on residuals that are uniform across the columns, where
-// the horizontal faces carry no flux.  Each column belongs to one thread
-// (columns dealt round-robin over the unit's threads); the same thread
-// factors and solves it, so the factors need no barrier.
-constexpr int ZB = 16;  // cells of a column loaded ahead of the recurrence
+// lo_k = -wz (K_{k-1} + K_k)/2 (row k to k - 1) and up_k = lo_{k+1}:
+// symmetric and diagonally dominant with cb > 0, so elimination needs no
+// pivoting.  A - M is the horizontal graph Laplacian (positive
+// semi-definite), so every eigenvalue of M^-1 A is >= 1, and M^-1 is exact on
+// residuals that are uniform across the columns, where the horizontal faces
+// carry no flux.
+//
+// Each column is solved by the partition method (substructuring), cut into
+// Pn segments of L cells so that a deep column uses many threads: work item
+// (column, segment) s = [a, b) with local matrix M_s (the rows of the
+// segment without its couplings to cells a - 1 and b) holds, per cell,
+// the local factors (1/pivot, c/pivot) and P_k = lo_a (M_s^-1 e_a)_k,
+// Q_k = up_{b-1} (M_s^-1 e_{b-1})_k.  With y = M_s^-1 r on the segment, the
+// solution is z_k = y_k - P_k z_{a-1} - Q_k z_b, and the segments' end values
+// E_s = z_a, F_s = z_{b-1} solve a reduced system with one forward and one
+// backward sweep per column over its segments (factors kept at each
+// segment's first cell).  Segments: as many as the unit has threads per
+// column, at most 32, at least 4 cells each.
+constexpr int ZB = 16;      // cells of a segment loaded ahead of its recurrence
+constexpr int ZSEG_MAX = 32;
 
-// Factor: lt_inv_k = 1 / pivot_k and lt_c_k = c_k / pivot_k per cell.
-__device__ __noinline__ void zline_factor32(const ClusterCtx &C, const Geo32 g, const float *__restrict__ K32,
-                                            const float *__restrict__ cb32, float *__restrict__ lt_inv,
-                                            float *__restrict__ lt_c)
+struct ZSeg {
+    int L, Pn;              // cells per segment, segments per column
+};
+
+__device__ __forceinline__ ZSeg zline_segs(const ClusterCtx &C, const Geo32 &g)
 {
-    const int bd = (int)blockDim.x, nz = g.nz, s = g.sxy;
+    int P = (C.ncta * (int)blockDim.x) / g.sxy;
+    P = min(P, ZSEG_MAX);
+    P = min(P, g.nz / 4);
+    P = max(P, 1);
+    const int L = (g.nz + P - 1) / P;
+    return ZSeg{L, (g.nz + L - 1) / L};
+}
+
+// Factors of every (column, segment), then the reduced system's per column.
+// Contains a unit barrier: every thread of the unit calls it.
+__device__ __noinline__ void zline_factor32(ClusterCtx &C, const Geo32 g, const float *__restrict__ K32,
+                                            const float *__restrict__ cb32, float *__restrict__ lt_inv,
+                                            float *__restrict__ lt_c, float *__restrict__ lt_P,
+                                            float *__restrict__ lt_Q, float4 *__restrict__ lt_rs)
+{
+    const int T = C.ncta * (int)blockDim.x, t0 = C.rank * (int)blockDim.x + (int)threadIdx.x;
+    const int nz = g.nz, s = g.sxy;
     const float hw = 0.5f * g.w[2];
-    for (int col = C.rank * bd + (int)threadIdx.x; col < s; col += C.ncta * bd) {
-        float Kk = K32[col];
-        float a = 0.0f, cp = 0.0f;   // coupling to the cell below; c'_{k-1}
-        for (int k0 = 0; k0 < nz; k0 += ZB) {
+    const ZSeg zs = zline_segs(C, g);
+    for (int w = t0; w < s * zs.Pn; w += T) {
+        const int col = w % s, seg = w / s;
+        const int a = seg * zs.L, b = min(a + zs.L, nz);
+        // forward: pivots, c' and w = M_s^-1 e_a before back substitution (kept in lt_P)
+        float Kk = K32[col + a * s], Kb = a > 0 ? K32[col + (a - 1) * s] : 0.0f;   // K of cells k and k - 1
+        float lo = 0.0f, cp = 0.0f, wv = 0.0f;   // coupling to the cell below (0 at the segment's start); c'_{k-1}; w_{k-1}
+        for (int k0 = a; k0 < b; k0 += ZB) {
             float Kup[ZB], cbv[ZB];
 #pragma unroll
             for (int u = 0; u < ZB; u++) {
                 const int k = k0 + u;
-                Kup[u] = k + 1 < nz ? K32[col + (k + 1) * s] : 0.0f;
-                cbv[u] = k < nz ? cb32[col + k * s] : 1.0f;
+                Kup[u] = k + 1 < nz && k < b ? K32[col + (k + 1) * s] : 0.0f;
+                cbv[u] = k < b ? cb32[col + k * s] : 1.0f;
             }
 #pragma unroll
             for (int u = 0; u < ZB; u++) {
                 const int k = k0 + u;
-                if (k < nz) {
-                    const float c = k + 1 < nz ? -hw * (Kk + Kup[u]) : 0.0f;
-                    const float inv = 1.0f / fmaf(-a, cp, cbv[u] - a - c);
-                    cp = c * inv;
+                if (k < b) {
+                    const float up = k + 1 < nz ? -hw * (Kk + Kup[u]) : 0.0f;   // row k to k + 1 (full operator)
+                    const float lof = k > 0 ? -hw * (Kb + Kk) : 0.0f;
+                    const float diag = cbv[u] - lof - up;
+                    const float upl = k + 1 < b ? up : 0.0f;   // within the segment
+                    const float inv = 1.0f / fmaf(-lo, cp, diag);
+                    wv = k == a ? inv : -lo * wv * inv;
+                    cp = upl * inv;
                     lt_inv[col + k * s] = inv;
                     lt_c[col + k * s] = cp;
-                    a = c;
+                    lt_P[col + k * s] = wv;
+                    lo = upl;
+                    Kb = Kk;
                     Kk = Kup[u];
                 }
             }
         }
+        // backward: p = M_s^-1 e_a, q = M_s^-1 e_{b-1}, scaled by the outside couplings
+        const float la = a > 0 ? -hw * (K32[col + (a - 1) * s] + K32[col + a * s]) : 0.0f;
+        const float ub = b < nz ? -hw * (K32[col + (b - 1) * s] + K32[col + b * s]) : 0.0f;
+        float pn = 0.0f, qn = 0.0f;
+        for (int k = b - 1; k >= a; k--) {
+            const float c = lt_c[col + k * s], wk = lt_P[col + k * s];
+            const float pk = k == b - 1 ? wk : fmaf(-c, pn, wk);
+            const float qk = k == b - 1 ? lt_inv[col + k * s] : -c * qn;
+            lt_P[col + k * s] = la * pk;
+            lt_Q[col + k * s] = ub * qk;
+            pn = pk;
+            qn = qk;
+        }
+    }
+    if (zs.Pn == 1) return;   // one segment: no reduced system (uniform over the unit)
+    unit_sync(C);             // every segment's P, Q published
+    for (int col = t0; col < s; col += T) {
+        float gp = 0.0f;
+        for (int seg = 0; seg < zs.Pn; seg++) {
+            const int a = seg * zs.L, b = min(a + zs.L, nz);
+            const float al = lt_P[col + a * s], ga = lt_P[col + (b - 1) * s];
+            const float be = lt_Q[col + a * s], de = lt_Q[col + (b - 1) * s];
+            const float iv = 1.0f / fmaf(-al, gp, 1.0f);
+            const float h = be * iv;
+            const float gn = fmaf(ga * gp, h, de);
+            lt_rs[col + a * s] = make_float4(iv, h, gn, ga * gp);
+            gp = gn;
+        }
     }
 }
 
-// Solve z = M^-1 r on this thread's columns (forward elimination into z,
-// then back substitution in place); returns this thread's share of r . z.
-__device__ __noinline__ float zline_solve32(const ClusterCtx &C, const Geo32 g, const float *__restrict__ K32,
+// z = M^-1 r on this thread's work items: y = M_s^-1 r per segment (into
+// z32), the reduced system per column (segment end values into ef), then
+// z = y - P F_{s-1} - Q E_{s+1}; returns this thread's share of r . z.
+// With several segments per column it contains two unit barriers: every
+// thread of the unit calls it.  ef is scratch of the instance's size.
+__device__ __noinline__ float zline_solve32(ClusterCtx &C, const Geo32 g, const float *__restrict__ K32,
                                             const float *__restrict__ lt_inv, const float *__restrict__ lt_c,
-                                            const float *__restrict__ r32, float *__restrict__ z32)
+                                            const float *__restrict__ lt_P, const float *__restrict__ lt_Q,
+                                            const float4 *__restrict__ lt_rs, const float *__restrict__ r32,
+                                            float *__restrict__ z32, float *__restrict__ ef)
 {
-    const int bd = (int)blockDim.x, nz = g.nz, s = g.sxy;
+    const int T = C.ncta * (int)blockDim.x, t0 = C.rank * (int)blockDim.x + (int)threadIdx.x;
+    const int nz = g.nz, s = g.sxy;
     const float hw = 0.5f * g.w[2];
+    const ZSeg zs = zline_segs(C, g);
+    const bool one = zs.Pn == 1;
     float rz = 0.0f;
-    for (int col = C.rank * bd + (int)threadIdx.x; col < s; col += C.ncta * bd) {
-        // y_k = (r_k - a_k y_{k-1}) / pivot_k, a_k = -wz (K_{k-1} + K_k)/2
+    for (int w = t0; w < s * zs.Pn; w += T) {
+        const int col = w % s, seg = w / s;
+        const int a = seg * zs.L, b = min(a + zs.L, nz);
+        // forward: t_k = (r_k - lo_k t_{k-1}) / pivot_k, lo_k = -wz (K_{k-1} + K_k)/2 inside the segment
         float y = 0.0f, Kb = 0.0f;
-        for (int k0 = 0; k0 < nz; k0 += ZB) {
+        for (int k0 = a; k0 < b; k0 += ZB) {
             float rv[ZB], Kv[ZB], iv[ZB];
 #pragma unroll
             for (int u = 0; u < ZB; u++) {
                 const int k = k0 + u;
-                const bool in = k < nz;
+                const bool in = k < b;
                 rv[u] = in ? r32[col + k * s] : 0.0f;
                 Kv[u] = in ? K32[col + k * s] : 0.0f;
                 iv[u] = in ? lt_inv[col + k * s] : 0.0f;
@@ -313,35 +390,109 @@ __device__ __noinline__ float zline_solve32(const ClusterCtx &C, const Geo32 g, 
 #pragma unroll
             for (int u = 0; u < ZB; u++) {
                 const int k = k0 + u;
-                if (k < nz) {
-                    const float a = k > 0 ? -hw * (Kb + Kv[u]) : 0.0f;
-                    y = fmaf(-a, y, rv[u]) * iv[u];
+                if (k < b) {
+                    const float lo = k > a ? -hw * (Kb + Kv[u]) : 0.0f;
+                    y = fmaf(-lo, y, rv[u]) * iv[u];
                     z32[col + k * s] = y;
                     Kb = Kv[u];
                 }
             }
         }
-        // z_k = y_k - c'_k z_{k+1}, top to bottom
-        float zn = 0.0f;
-        for (int k0 = nz - 1; k0 >= 0; k0 -= ZB) {
-            float yv[ZB], cv[ZB], rv[ZB];
+        // backward: y_k = t_k - c'_k y_{k+1} (c' = 0 at the segment's last cell)
+        float yn = 0.0f;
+        for (int k0 = b - 1; k0 >= a; k0 -= ZB) {
+            float tv[ZB], cv[ZB], rv[ZB];
 #pragma unroll
             for (int u = 0; u < ZB; u++) {
                 const int k = k0 - u;
-                const bool in = k >= 0;
-                yv[u] = in ? z32[col + k * s] : 0.0f;
+                const bool in = k >= a;
+                tv[u] = in ? z32[col + k * s] : 0.0f;
                 cv[u] = in ? lt_c[col + k * s] : 0.0f;
-                rv[u] = in ? r32[col + k * s] : 0.0f;
+                rv[u] = in && one ? r32[col + k * s] : 0.0f;
             }
 #pragma unroll
             for (int u = 0; u < ZB; u++) {
                 const int k = k0 - u;
-                if (k >= 0) {
-                    zn = fmaf(-cv[u], zn, yv[u]);
-                    z32[col + k * s] = zn;
-                    rz = fmaf(rv[u], zn, rz);
+                if (k >= a) {
+                    yn = fmaf(-cv[u], yn, tv[u]);
+                    z32[col + k * s] = yn;
+                    rz = fmaf(rv[u], yn, rz);   // one segment: y is z
                 }
             }
+        }
+    }
+    if (one) return rz;   // uniform over the unit
+    unit_sync(C);
+    // reduced system, one thread per column: forward over the segments
+    // (e'_s, f'_s into ef at the segment's ends), then backward (E_s, F_s)
+    constexpr int ZR = 8;
+    for (int col = t0; col < s; col += T) {
+        float f = 0.0f;
+        for (int s0 = 0; s0 < zs.Pn; s0 += ZR) {
+            float ya[ZR], yb[ZR], al[ZR], ga[ZR];
+            float4 rs[ZR];
+#pragma unroll
+            for (int u = 0; u < ZR; u++) {
+                const int sg = s0 + u;
+                const int a = sg * zs.L, b = min(a + zs.L, nz);
+                const bool in = sg < zs.Pn;
+                ya[u] = in ? z32[col + a * s] : 0.0f;
+                yb[u] = in ? z32[col + (b - 1) * s] : 0.0f;
+                al[u] = in ? lt_P[col + a * s] : 0.0f;
+                ga[u] = in ? lt_P[col + (b - 1) * s] : 0.0f;
+                rs[u] = in ? lt_rs[col + a * s] : make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+            }
+#pragma unroll
+            for (int u = 0; u < ZR; u++) {
+                const int sg = s0 + u;
+                if (sg < zs.Pn) {
+                    const int a = sg * zs.L, b = min(a + zs.L, nz);
+                    const float e = fmaf(-al[u], f, ya[u]) * rs[u].x;
+                    f = fmaf(rs[u].w, e, fmaf(-ga[u], f, yb[u]));
+                    ef[col + a * s] = e;
+                    ef[col + (b - 1) * s] = f;   // the same cell when the segment has one cell (then f = e)
+                }
+            }
+        }
+        float En = 0.0f;
+        for (int s0 = zs.Pn - 1; s0 >= 0; s0 -= ZR) {
+            float ev[ZR], fv[ZR];
+            float4 rs[ZR];
+#pragma unroll
+            for (int u = 0; u < ZR; u++) {
+                const int sg = s0 - u;
+                const int a = sg * zs.L, b = min(a + zs.L, nz);
+                const bool in = sg >= 0;
+                ev[u] = in ? ef[col + a * s] : 0.0f;
+                fv[u] = in ? ef[col + (b - 1) * s] : 0.0f;
+                rs[u] = in ? lt_rs[col + a * s] : make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+            }
+#pragma unroll
+            for (int u = 0; u < ZR; u++) {
+                const int sg = s0 - u;
+                if (sg >= 0) {
+                    const int a = sg * zs.L, b = min(a + zs.L, nz);
+                    const float E = fmaf(-rs[u].y, En, ev[u]), F = fmaf(-rs[u].z, En, fv[u]);
+                    ef[col + a * s] = E;
+                    ef[col + (b - 1) * s] = F;
+                    En = E;
+                }
+            }
+        }
+    }
+    unit_sync(C);
+    // combination, every segment in parallel
+    for (int w = t0; w < s * zs.Pn; w += T) {
+        const int col = w % s, seg = w / s;
+        const int a = seg * zs.L, b = min(a + zs.L, nz);
+        const float Fp = seg > 0 ? ef[col + (a - 1) * s] : 0.0f;
+        const float En = seg + 1 < zs.Pn ? ef[col + b * s] : 0.0f;
+#pragma unroll 4
+        for (int k = a; k < b; k++) {
+            const int p = col + k * s;
+            const float z = fmaf(-lt_Q[p], En, fmaf(-lt_P[p], Fp, z32[p]));
+            z32[p] = z;
+            rz = fmaf(r32[p], z, rz);
         }
     }
     return rz;
@@ -360,7 +511,8 @@ __device__ __noinline__ bool inner_pcg32(ClusterCtx &C, const Geo32 g, int lo, i
                                          float *__restrict__ r32, float *__restrict__ z32, float *__restrict__ pa_,
                                          float *__restrict__ pb_, float *__restrict__ q32, float *__restrict__ d32,
                                          const float *__restrict__ lt_inv, const float *__restrict__ lt_c,
-                                         float rho, float stop, int max_it, int &its)
+                                         const float *__restrict__ lt_P, const float *__restrict__ lt_Q,
+                                         const float4 *__restrict__ lt_rs, float rho, float stop, int max_it, int &its)
 {
     float beta = 0.0f;
     int pi = 0;
@@ -368,7 +520,7 @@ __device__ __noinline__ bool inner_pcg32(ClusterCtx &C, const Geo32 g, int lo, i
     const int bd = (int)blockDim.x;
     if constexpr (zline) {
         // r32 was published by the caller's reduction barrier
-        float w0[1] = {zline_solve32(C, g, K32, lt_inv, lt_c, r32, z32)};
+        float w0[1] = {zline_solve32(C, g, K32, lt_inv, lt_c, lt_P, lt_Q, lt_rs, r32, z32, q32)};
         cl_reduce_f32<1>(C, w0);   // also publishes z32
         rho = w0[0];
         if (!(rho > 0.0f) || !isfinite(rho)) return false;
@@ -410,7 +562,7 @@ __device__ __noinline__ bool inner_pcg32(ClusterCtx &C, const Geo32 g, int lo, i
                 b0 = fmaf(r2, r2, b0);
             }
             unit_sync(C);   // the columns cross the CTAs' cell ranges
-            b1 = zline_solve32(C, g, K32, lt_inv, lt_c, r32, z32);
+            b1 = zline_solve32(C, g, K32, lt_inv, lt_c, lt_P, lt_Q, lt_rs, r32, z32, q32);   // q32 is free here
         } else
         for (int p = lo + (int)threadIdx.x; p < hi; p += 2 * bd) {
             const bool has2 = p + bd < hi;
@@ -513,6 +665,8 @@ k_ensemble(EnsDesc *__restrict__ D, int n_inst, EnsBuffers B, EnsParams P, const
         float *r32 = B.r32 + off, *z32 = B.z32 + off, *P32[2] = {B.p32[0] + off, B.p32[1] + off};
         float *q32 = B.q32 + off, *d32 = B.d32 + off;
         float *LTi = P.zline ? B.lt_inv + off : nullptr, *LTc = P.zline ? B.lt_c + off : nullptr;
+        float *LTP = P.zline ? B.lt_P + off : nullptr, *LTQ = P.zline ? B.lt_Q + off : nullptr;
+        float4 *LTR = P.zline ? B.lt_rs + off : nullptr;
         const uint8_t *fl = B.flags + off, *zn = B.zone + off;
         const double *Ks = B.Ks + off;
         const DevSoil *soil = &d.soil;
@@ -678,7 +832,7 @@ k_ensemble(EnsDesc *__restrict__ D, int n_inst, EnsBuffers B, EnsParams P, const
                     } else {
                         // ---- FP32 inner PCG inside FP64 defect correction
                         // (the assembly's reduction barrier published K32, cb32)
-                        if (P.zline) zline_factor32(C, geo32(g), K32, cb32, LTi, LTc);
+                        if (P.zline) zline_factor32(C, geo32(g), K32, cb32, LTi, LTc, LTP, LTQ, LTR);
                         int outer = 1;
                         for (;;) {
                             const bool finite = isfinite(v[0]) && isfinite(v[1]) && isfinite(v[2]) && isfinite(v[3]);
@@ -691,11 +845,12 @@ k_ensemble(EnsDesc *__restrict__ D, int n_inst, EnsBuffers B, EnsParams P, const
                                 const float stop = (float)(P.tol_inner * sq[2]);
                                 lin_ok = P.zline
                                              ? inner_pcg32<true>(C, geo32(g), (int)lo, (int)hi, K32, cb32, di32, r32,
-                                                                 z32, P32[0], P32[1], q32, d32, LTi, LTc, 0.0f, stop,
-                                                                 P.inner_max_it, inner_it)
+                                                                 z32, P32[0], P32[1], q32, d32, LTi, LTc, LTP, LTQ,
+                                                                 LTR, 0.0f, stop, P.inner_max_it, inner_it)
                                              : inner_pcg32<false>(C, geo32(g), (int)lo, (int)hi, K32, cb32, di32, r32,
                                                                   z32, P32[0], P32[1], q32, d32, nullptr, nullptr,
-                                                                  (float)v[3], stop, P.inner_max_it, inner_it);
+                                                                  nullptr, nullptr, nullptr, (float)v[3], stop,
+                                                                  P.inner_max_it, inner_it);
                             }
                             cg_it += inner_it;
                             if (!lin_ok) break;

@@ -32,7 +32,8 @@ struct EnsBuffers {
     double *Can, *c, *b, *Tx, *Ty, *Tz, *diag, *dinv;
     double *r, *z, *p[2], *q;
     float *K32, *cb32, *dinv32, *r32, *z32, *p32[2], *q32, *d32;
-    float *lt_inv, *lt_c;   // vertical-line factors (RF_PRECOND_ZLINE; null otherwise)
+    float *lt_inv, *lt_c, *lt_P, *lt_Q;   // vertical-line factors (RF_PRECOND_ZLINE; null otherwise)
+    float4 *lt_rs;                         // its reduced-system factors, at each segment's first cell
     uint8_t *flags, *zone;
     double *Ks;
 };

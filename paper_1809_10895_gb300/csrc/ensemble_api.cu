@@ -247,7 +247,9 @@ rf_status rf_ens_create(const rf_ens_instance *inst, int n, const rf_solver_para
          e->get(e->B.cb32, N) && e->get(e->B.dinv32, N) && e->get(e->B.r32, N) && e->get(e->B.z32, N) &&
          e->get(e->B.q32, N) && e->get(e->B.d32, N) && e->get(e->B.flags, N) && e->get(e->B.zone, N) &&
          e->get(e->B.Ks, N);
-    if (ok && prm.precond == RF_PRECOND_ZLINE) ok = e->get(e->B.lt_inv, N) && e->get(e->B.lt_c, N);
+    if (ok && prm.precond == RF_PRECOND_ZLINE)
+        ok = e->get(e->B.lt_inv, N) && e->get(e->B.lt_c, N) && e->get(e->B.lt_P, N) && e->get(e->B.lt_Q, N) &&
+             e->get(e->B.lt_rs, N);
     if (!ok || cudaMallocHost(&e->t_end_h, sizeof(double)) != cudaSuccess) {
         rf_ens_destroy(e);
         return efail(RF_ERR_NOMEM, "rf_ens_create: allocation failed");
