@@ -491,7 +491,7 @@ def native(args):
             s64.set_state(h_np, meta["t"])
             s64.set_meta(meta, mass7)
             s64.step()
-            h_np[:], meta = s64.get_state()
+            _, meta = s64.get_state(out=h_np)
         barrier()
         te = max_over_ranks(time.perf_counter() - w0, world, "cuda")
         e2e = {"value": job_value(args.steps * n_act, world, te), "unit": UNIT, "h2d_bytes_per_step": 8 * case.N,

@@ -366,8 +366,16 @@ class Solver:
         _check(st, "rf_run")
         return steps
 
-    def get_state(self):
-        h = np.zeros(self.N)
+    def get_state(self, out=None):
+        """(h, meta); h is written into out (a contiguous float64 array of N
+        cells, e.g. a view of pinned memory, so the copy runs at full rate)
+        when given, else into a new array."""
+        if out is None:
+            h = np.empty(self.N)
+        else:
+            h = out
+            if not (isinstance(h, np.ndarray) and h.dtype == np.float64 and h.size == self.N and h.flags.c_contiguous):
+                raise ValueError("get_state: out must be a contiguous float64 array of N cells")
         meta = rf_state_meta()
         _check(load().rf_state_get(self.ctx, _dptr(h), C.byref(meta)), "rf_state_get")
         return h, dict(t=meta.t, dt_nom=meta.dt_nom, easy=meta.easy, n_active=meta.n_active, steps=meta.steps)

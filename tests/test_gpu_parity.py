@@ -226,6 +226,12 @@ def test_checkpoint_resume_is_bit_identical():
     b.set_meta(meta, mass7)
     b.run(1800.0)
     assert np.array_equal(a.get_state()[0], b.get_state()[0])
+    # the state read into a caller's pinned buffer is the same
+    pinned = torch.empty(case.N, dtype=torch.float64, pin_memory=True).numpy()
+    h, meta_b = b.get_state(out=pinned)
+    assert h is pinned and np.array_equal(pinned, a.get_state()[0]) and meta_b["t"] == a.get_state()[1]["t"]
+    with pytest.raises(ValueError):
+        b.get_state(out=np.empty(case.N, dtype=np.float32))
 
 
 @pytest.mark.parametrize("shape", [(1, 1, 1), (1, 1, 2), (3, 1, 1), (2, 3, 1), (1, 5, 7), (33, 1, 9)])
