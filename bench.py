@@ -70,6 +70,7 @@ def parse():
                     help="inner PCG preconditioner of the ensemble leg (vertical-line solve or Jacobi)")
     ap.add_argument("--no-warmstart", action="store_true", help="skip the learned warm-start leg")
     ap.add_argument("--no-configs", action="store_true", help="skip the column and box legs")
+    ap.add_argument("--no-stiff", action="store_true", help="skip the stiff-solve preconditioner comparison")
     ap.add_argument("--ws-train-size", type=int, default=128, help="nx = ny of the training box (nz = 64)")
     ap.add_argument("--ws-eval-size", type=int, default=256, help="nx = ny of the held-out boxes (nz = 64)")
     ap.add_argument("--ws-eval-seeds", type=int, default=1, help="held-out seeds evaluated")
@@ -541,6 +542,9 @@ def native(args):
     cfg = None
     if not args.no_configs:
         cfg = configs_leg(args, rank, rf, W)
+    stiff = None
+    if not args.no_stiff:
+        stiff = stiff_leg(rf, W)
 
     if rank == 0:
         line = {
@@ -569,6 +573,7 @@ def native(args):
             "ensemble": ens,
             "warmstart": wsl,
             "other_configs": cfg,
+            "stiff_solve": stiff,
         }
         if not args.no_baseline:
             # host-side legs: an error is recorded in the line, never lost with it
@@ -612,6 +617,35 @@ def ensemble_leg(args, rank, rf, W, barrier):
            "max_closure_rel": max(st["closure_abs"] / max(st["storage0"] + st["inflow_cum"] + st["outflow_cum"], 1e-300)
                                   for st in stats)}
     e.close()
+    return out
+
+
+def stiff_leg(rf, W):
+    """One linear solve from x = 0 on a stiff system (saturated, 10:1
+    anisotropic, storage-poor 256x256x64 block) per preconditioner of the
+    mixed path, at two time steps: inner iterations and event-timed ms."""
+    import torch
+    case = W.stiff_block(256, 256, 64)
+    dev = dict(dtype=torch.float64, device="cuda")
+    hk = torch.as_tensor(case.h0, **dev)
+    out = {"workload": case.name, "cells": case.N, "tol_cg_rel": case.params["tol_cg"], "precision": "mixed"}
+    for dt in (60.0, 3600.0):
+        for pc in ("jacobi", "mg", "dic"):
+            try:
+                s = rf.Solver.from_case(case, precision="mixed", precond=pc)
+                s.assemble(hk, hk, dt, 0.0)
+                x = torch.zeros(case.N, **dev)
+                s.solve(x)                      # first solve builds the graphs
+                x.zero_()
+                a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                a.record(s.stream)
+                its = s.solve(x)
+                b.record(s.stream)
+                torch.cuda.synchronize()
+                out[f"{pc}_dt{int(dt)}"] = {"inner_iters": its, "ms": a.elapsed_time(b)}
+                s.close()
+            except Exception as ex:
+                out[f"{pc}_dt{int(dt)}"] = {"error": str(ex)[:200]}
     return out
 
 

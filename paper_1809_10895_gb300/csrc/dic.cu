@@ -20,6 +20,7 @@
 // sum_f T_f.  A pivot that is not positive (possible only without any
 // storage or boundary term in a whole neighbourhood) falls back to 1 / a_PP.
 #include "dic.cuh"
+#include "rf_reduce.cuh"
 
 namespace rf {
 
@@ -121,21 +122,142 @@ k_dic_sweep(Grid g, const float *__restrict__ K32, const float *__restrict__ rd3
     }
 }
 
+// The inner PCG's update (x += alpha p, r -= alpha q, ||r||^2 and the stop
+// test, as for the multigrid path) with DIC's first pass on the new residual
+// fused in: u = r / d on the red cells.  Inactive cells keep x, r and z = 0.
+__global__ void __launch_bounds__(RED_THREADS)
+k_cg32_update_dic(Grid g, float *__restrict__ x, float *__restrict__ r, float *__restrict__ z,
+                  const float *__restrict__ pd, const float *__restrict__ q, const float *__restrict__ dinv,
+                  const float *__restrict__ rd32, double *partials, unsigned int *ticket, CgScal *sc)
+{
+    count_launch(g, KK_CG32_UPDATE);
+    if (sc->done) return;
+    count_work(g, KK_CG32_UPDATE);
+    const float alpha = (float)sc->alpha;
+    float a0 = 0.0f;
+    for (long long p = (long long)blockIdx.x * blockDim.x + threadIdx.x; p < g.N;
+         p += (long long)gridDim.x * blockDim.x) {
+        if (dinv[p] == 0.0f) continue;
+        x[p] = fmaf(alpha, pd[p], x[p]);
+        const float rp = fmaf(-alpha, q[p], r[p]);
+        r[p] = rp;
+        a0 = fmaf(rp, rp, a0);
+        int i, j, k;
+        if (colour_of(g, p, i, j, k) == 0) z[p] = rd32[p] * rp;
+    }
+    float vf[1] = {a0};
+    double v[1];
+    if (grid_reduce_f32<1>(vf, v, partials, ticket) && threadIdx.x == 0) {
+        sc->iter += 1;
+        sc->total += 1;
+        sc->rr = v[0];
+        if (!isfinite(v[0])) {
+            sc->status = CG_NONFINITE;
+            sc->done = 1;
+        } else if (sqrt(v[0]) <= sc->stop2) {
+            sc->done = 1;
+        } else if (sc->iter >= sc->max_it) {
+            sc->status = CG_MAXIT;
+            sc->done = 1;
+        }
+    }
+}
+
+// DIC's black pass, z_b = (r_b + sum T u) / d_b, with the black cells' share
+// of r.z (into sc->rz_part).
+__global__ void __launch_bounds__(RED_THREADS)
+k_dic_black(Grid g, const float *__restrict__ K32, const float *__restrict__ rd32, const float *__restrict__ r,
+            float *__restrict__ z, double *partials, unsigned int *ticket, CgScal *sc)
+{
+    if (sc->done) return;
+    float a0 = 0.0f;
+    const long long stride = (long long)gridDim.x * blockDim.x;
+    for (long long p = (long long)blockIdx.x * blockDim.x + threadIdx.x; p < g.N; p += stride) {
+        int i, j, k;
+        if (colour_of(g, p, i, j, k) != 1) continue;
+        const float rd = rd32[p];
+        if (rd == 0.0f) {                 // inactive
+            z[p] = 0.0f;
+            continue;
+        }
+        const float rp = r[p];
+        float s = rp;
+        active_faces(g, K32, p, i, j, k, K32[p], [&](long long q, float t) { s = fmaf(t, z[q], s); });
+        const float zp = rd * s;
+        z[p] = zp;
+        a0 = fmaf(rp, zp, a0);
+    }
+    float vf[1] = {a0};
+    double v[1];
+    if (grid_reduce_f32<1>(vf, v, partials, ticket) && threadIdx.x == 0) sc->rz_part = v[0];
+}
+
+// DIC's red back-substitution, z_r = u_r + sum T z_b / d_r, finishing r.z:
+// start = 1 sets rho (first preconditioned residual of an inner solve),
+// otherwise beta = r.z / rho; always sets the inner loop condition.
+__global__ void __launch_bounds__(RED_THREADS)
+k_dic_red(Grid g, const float *__restrict__ K32, const float *__restrict__ rd32, const float *__restrict__ r,
+          float *__restrict__ z, double *partials, unsigned int *ticket, CgScal *sc, int start, CondSet cond)
+{
+    if (sc->done) {
+        if (blockIdx.x == 0 && threadIdx.x == 0) set_cond(cond, 0);
+        return;
+    }
+    float a0 = 0.0f;
+    const long long stride = (long long)gridDim.x * blockDim.x;
+    for (long long p = (long long)blockIdx.x * blockDim.x + threadIdx.x; p < g.N; p += stride) {
+        int i, j, k;
+        if (colour_of(g, p, i, j, k) != 0) continue;
+        const float rd = rd32[p];
+        if (rd == 0.0f) continue;         // inactive: z stays 0
+        float s = 0.0f;
+        active_faces(g, K32, p, i, j, k, K32[p], [&](long long q, float t) { s = fmaf(t, z[q], s); });
+        const float zp = fmaf(rd, s, z[p]);
+        z[p] = zp;
+        a0 = fmaf(r[p], zp, a0);
+    }
+    float vf[1] = {a0};
+    double v[1];
+    if (grid_reduce_f32<1>(vf, v, partials, ticket) && threadIdx.x == 0) {
+        const double rz = v[0] + sc->rz_part;
+        if (!isfinite(rz) || !(rz > 0.0)) {
+            // a zero or non-finite r.z with a non-zero residual: breakdown
+            sc->status = CG_NONFINITE;
+            sc->done = 1;
+        } else if (start) {
+            sc->rho = rz;
+            sc->beta = 0.0;
+        } else {
+            sc->beta = rz / sc->rho;
+            sc->rho = rz;
+        }
+        set_cond(cond, sc->done ? 0 : 1);
+    }
+}
+
 }  // namespace
+
+void launch_cg32_update_dic(cudaStream_t s, int nblk, const Grid &g, float *x, float *r, float *z, const float *p,
+                            const float *q, const float *dinv, const float *rd32, double *partials,
+                            unsigned int *ticket, CgScal *sc)
+{
+    k_cg32_update_dic<<<nblk, RED_THREADS, 0, s>>>(g, x, r, z, p, q, dinv, rd32, partials, ticket, sc);
+}
+
+void launch_dic_apply_rz(cudaStream_t s, int nblk, const Grid &g, const float *K32, const float *rd32, const float *r,
+                         float *z, double *partials, unsigned int *ticket, CgScal *sc, int start, bool red_done,
+                         CondSet cond)
+{
+    if (!red_done) k_dic_sweep<0><<<nblk, RED_THREADS, 0, s>>>(g, K32, rd32, r, z, &sc->done);
+    k_dic_black<<<nblk, RED_THREADS, 0, s>>>(g, K32, rd32, r, z, partials, ticket, sc);
+    k_dic_red<<<nblk, RED_THREADS, 0, s>>>(g, K32, rd32, r, z, partials, ticket, sc, start, cond);
+}
 
 void launch_dic_setup(cudaStream_t s, int nblk, const Grid &g, const float *K32, const float *cb32, float *diag32,
                       float *rd32, const int *skip)
 {
     k_dic_diag<<<nblk, RED_THREADS, 0, s>>>(g, K32, cb32, diag32, skip);
     k_dic_pivots<<<nblk, RED_THREADS, 0, s>>>(g, K32, diag32, rd32, skip);
-}
-
-void launch_dic_apply(cudaStream_t s, int nblk, const Grid &g, const float *K32, const float *rd32, const float *r,
-                      float *z, const int *done)
-{
-    k_dic_sweep<0><<<nblk, RED_THREADS, 0, s>>>(g, K32, rd32, r, z, done);
-    k_dic_sweep<1><<<nblk, RED_THREADS, 0, s>>>(g, K32, rd32, r, z, done);
-    k_dic_sweep<2><<<nblk, RED_THREADS, 0, s>>>(g, K32, rd32, r, z, done);
 }
 
 }  // namespace rf

@@ -412,11 +412,8 @@ rf_status capture_solve(rf_ctx *c, cudaGraph_t top, cudaGraph_t parent, std::vec
     const CondSet co = start->cond, ci = start->cond_inner;
     const bool mg = c->prm.precond == RF_PRECOND_MG, dic = c->prm.precond == RF_PRECOND_DIC;
     const int *idone = &c->sc_in->done;
-    // z = M r for the MG and DIC preconditioners
-    auto precondition = [&]() {
-        if (mg) launch_mg_vcycle(s, nb, c->mg, c->K32, c->r32, c->z32, idone);
-        else launch_dic_apply(s, nb, g, c->K32, c->dic_rd, c->r32, c->z32, idone);
-    };
+    // z = M r for the MG preconditioner
+    auto precondition = [&]() { launch_mg_vcycle(s, nb, c->mg, c->K32, c->r32, c->z32, idone); };
     const CondSet none{0, 0};
     if (!fused) {
         RF_TRY(cap_begin(c, parent, deps));
@@ -426,14 +423,24 @@ rf_status capture_solve(rf_ctx *c, cudaGraph_t top, cudaGraph_t parent, std::vec
                        c->ticket, c->sc, c->sc_in, co, ci);
         RF_TRY(cap_end(c, deps));
     }
+    // z = M r and rho = r.z (start) or beta (inner iterations); DIC folds
+    // r.z into its two sweeps, and within the loop its red pass into the update
+    auto precondition_rz = [&](int first, bool red_done) {
+        if (dic) {
+            launch_dic_apply_rz(s, nb, g, c->K32, c->dic_rd, c->r32, c->z32, c->partials, c->ticket, c->sc_in,
+                                first, red_done, ci);
+        } else {
+            precondition();
+            launch_cg32_rz(s, nb, g, c->r32, c->z32, c->partials, c->ticket, c->sc_in, first, ci);
+        }
+    };
     if (mg || dic) {
         // coarse operators (MG) or pivots (DIC) from this assembly, then
         // z0 = M r0 and rho = r0.z0
         RF_TRY(cap_begin(c, parent, deps));
         if (mg) launch_mg_build(s, nb, c->mg, c->K32, skip);
         else launch_dic_setup(s, nb, g, c->K32, c->cb32, c->dic_diag, c->dic_rd, skip);
-        precondition();
-        launch_cg32_rz(s, nb, g, c->r32, c->z32, c->partials, c->ticket, c->sc_in, 1, ci);
+        precondition_rz(1, false);
         RF_TRY(cap_end(c, deps));
     }
     cudaGraphNode_t wo, wi;
@@ -445,10 +452,13 @@ rf_status capture_solve(rf_ctx *c, cudaGraph_t top, cudaGraph_t parent, std::vec
         float *pin = c->p32[half], *pout = c->p32[half ^ 1];
         launch_cg32_spmv(s, nb, g, c->z32, pin, pout, c->q32, c->K32, c->cb32, c->partials, c->ticket, c->sc_in,
                          c->tma_ok ? &c->tma : nullptr, c->dev_fault);
-        if (mg || dic) {
+        if (dic) {
+            launch_cg32_update_dic(s, nb, g, c->d32, c->r32, c->z32, pout, c->q32, c->dinv32, c->dic_rd, c->partials,
+                                   c->ticket, c->sc_in);
+            precondition_rz(0, true);
+        } else if (mg) {
             launch_cg32_update_mg(s, nb, g, c->d32, c->r32, pout, c->q32, c->dinv32, c->partials, c->ticket, c->sc_in);
-            precondition();
-            launch_cg32_rz(s, nb, g, c->r32, c->z32, c->partials, c->ticket, c->sc_in, 0, ci);
+            precondition_rz(0, false);
         } else {
             launch_cg32_update(s, nb, g, c->d32, c->r32, c->z32, pout, c->q32, c->dinv32, c->partials, c->ticket,
                                c->sc_in, ci);
@@ -461,10 +471,7 @@ rf_status capture_solve(rf_ctx *c, cudaGraph_t top, cudaGraph_t parent, std::vec
     launch_resid64(s, nb, g, c->flags, x, c->b, c->Tx, c->Ty, c->Tz, c->diag, c->dinv32, c->r32, c->z32, c->d32,
                    c->prm.tol_cg, c->prm.tol_inner, c->prm.inner_max_it, c->prm.outer_max_it, c->partials, c->ticket,
                    c->sc, c->sc_in, co, ci);
-    if (mg || dic) {
-        precondition();
-        launch_cg32_rz(s, nb, g, c->r32, c->z32, c->partials, c->ticket, c->sc_in, 1, ci);
-    }
+    if (mg || dic) precondition_rz(1, false);
     (void)none;
     RF_TRY(cap_end(c, tmp));
     out = {wo};

@@ -108,6 +108,7 @@ struct CgScal {
     double rr;        // ||r||^2 (recursive)
     double stop2;     // converged when ||r|| <= stop2
     double bb;        // ||b||^2 (FP64) / ||r0||^2 (inner)
+    double rz_part;   // r.z over the black cells (DIC, between its two sweeps)
     int iter;         // iterations of this solve
     int done;
     int status;       // CG_OK, CG_MAXIT, CG_NONFINITE

@@ -134,6 +134,24 @@ def gaussian_random_field(shape, corr_len_cells: float, seed: int) -> np.ndarray
 # --------------------------------------------------------------------------
 # 3-D heterogeneous box
 # --------------------------------------------------------------------------
+def stiff_block(nx: int = 256, ny: int = 256, nz: int = 64, seed: int = 12, sigma_lnK: float = 1.5) -> Case:
+    """A stiff linear system for comparing preconditioners: saturated soil
+    (hydrostatic head above a Dirichlet bottom), log-normal Ks (geometric mean
+    1e-4 m/s, uncorrelated, sigma_lnK), 10:1 anisotropic cells (1 x 1 x 0.1 m),
+    a specific storage of 1e-6 1/m so that the capacity term is far below the
+    face conductances, and a top flux of 5e-5 m/s."""
+    rng = np.random.default_rng(seed)
+    N = nx * ny * nz
+    Ks = np.exp(np.log(1e-4) + sigma_lnK * rng.standard_normal(N))
+    c = Case(name=f"stiff_block_{nx}x{ny}x{nz}", nx=nx, ny=ny, nz=nz, dx=1.0, dy=1.0, dz=0.1,
+             soils=[dict(model="vg", theta_r=0.05, theta_s=0.4, alpha=2.0, n=1.8, Ks=1e-4, S=1e-6)],
+             Ks_cell=Ks, params=default_params(tol_cg=1e-10))
+    c.h0 = (nz * 0.1 + 2.0) - c.z_centres()
+    c.bcs = [BC("zmin", "dirichlet", np.array([0.0]), np.array([nz * 0.1 + 1.5])),
+             BC("zmax", "flux", np.array([0.0]), np.array([5e-5]))]
+    return c
+
+
 def heterogeneous_box(nx: int = 128, ny: int = 128, nz: int = 64, d: float = 0.25, seed: int = 0,
                       t_end: float = 48 * 3600.0, rain: float = 1e-6, rain_hours: float = 6.0,
                       water_table_depth: float = 10.0, sigma_lnK: float = 1.0,
