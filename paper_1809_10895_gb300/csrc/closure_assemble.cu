@@ -167,12 +167,21 @@ k_assemble(Grid g, const DevSoil *__restrict__ soils, const uint8_t *__restrict_
         Tx[p] = Tup[0];
         Ty[p] = Tup[1];
         Tz[p] = Tup[2];
-        const double di = rcp64(diag);
+        // 1/diag: in FP64 for the FP64 PCG; the mixed path's Jacobi scaling
+        // is FP32 only (its FP64 copy is not read), so it skips the FP64
+        // reciprocal, a dozen instructions on the narrow FP64 pipe
+        double di = 0.0;
+        float di32;
+        if (MODE == ASM_MIXED) {
+            di32 = __frcp_rn((float)diag);
+        } else {
+            di = rcp64(diag);
+            dinv[p] = di;
+            di32 = (float)di;
+        }
         diag_out[p] = diag;
-        dinv[p] = di;
         K32[p] = (float)KP;
         cb32[p] = (float)cb;
-        const float di32 = (float)di;
         dinv32[p] = di32;
         if (MODE != ASM_ONLY) {
             // first residual of the linear solve from x0 = h^k
