@@ -41,6 +41,8 @@ def main(argv=None):
     ap.add_argument("--window", type=float, default=10.0, help="simulated seconds (ensemble)")
     ap.add_argument("--cluster", type=int, default=4, help="CTAs per cluster (ensemble)")
     ap.add_argument("--threads", type=int, default=512, help="threads per CTA (ensemble)")
+    ap.add_argument("--precond", default="jacobi", choices=["jacobi", "zline"],
+                    help="inner PCG preconditioner (ensemble, mixed precision)")
     a = ap.parse_args(argv)
 
     import torch
@@ -52,7 +54,8 @@ def main(argv=None):
     out = {"workload": a.workload}
     if a.workload == "ensemble":
         cases = W.ensemble(a.instances, seed=0)
-        e = rf.Ensemble.from_cases(cases, precision=a.precision)
+        e = rf.Ensemble.from_cases(cases, precision=a.precision,
+                                   **({"precond": a.precond} if a.precond != "jacobi" else {}))
         e.set_tiling(a.cluster, a.threads)
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         e0.record(e.stream)
