@@ -547,30 +547,32 @@ k_cg32_spmv(Grid g, Tiles tw, const float *__restrict__ z, const float *__restri
 }
 
 // The FP32 stencil step with planes staged by TMA.  Per plane the block
-// copies four 72 x 10 boxes (z, p_old, K, cb) around its 64 x 8 tile into
-// shared memory with bulk tensor copies; each thread owns two x-adjacent
-// cells.  Each face term w (K_P + K_N)(p_P - p_N) is formed once: the face
-// between a thread's two cells serves both (with opposite signs), and the
-// face between planes k and k + 1 is formed at plane k and carried in
-// registers into plane k + 1.  A plane therefore needs only itself and the
+// copies three 136 x 10 boxes (z, p_old, K) around its 128 x 8 tile and the
+// tile's own 128 x 8 cb into shared memory with bulk tensor copies; each
+// thread owns four x-adjacent cells (one float4), so the per-plane work of
+// a thread -- poll, barrier, addressing -- is spread over four cells.  Each
+// face term w (K_P + K_N)(p_P - p_N) is formed once: a face between two of a
+// thread's cells serves both (with opposite signs), and the face between
+// planes k and k + 1 is formed at plane k and carried in registers into
+// plane k + 1.  A plane therefore needs only itself and the
 // plane above, so the ring of stages holds planes k and k + 1 and keeps the
 // next TMA_STAGES - 2 in flight.  Warp 0 alone polls the copy's mbarrier
 // (bounded); the others meet it at the one barrier per plane and then
 // confirm the completed phase once.  When a plane arrives each thread forms
-// p = z + beta p_old (in place of z) for its own cells and one halo cell.  A
+// p = z + beta p_old (in place of z) for its own cells and at most one halo
+// quad or cell.  A
 // wait that runs out sets *fault, ends the solve and drains the copies in
 // flight.
 #ifndef RF_TMA_STAGES
 #define RF_TMA_STAGES 4
 #endif
 constexpr int TMA_WAIT_TRIES = 1 << 20;   // about a second of suspending polls
-constexpr int TMA_HALO = 2 * TY + 2 * TMA_TX;
 
 // TMA_STAGES = planes k, k+1 resident plus TMA_STAGES - 2 in flight.
-// Five blocks per SM: 4 stages of 3 x 2944 + 2048 bytes (cb is staged for
-// the tile's own cells only) fit 217 KB, and at most 51 registers a thread.
+// Two blocks per SM: 4 stages of 3 x 5504 + 4096 bytes (cb is staged for the
+// tile's own cells only), 82.9 KB a block.
 template <int TMA_STAGES>
-__global__ void __launch_bounds__(RED_THREADS, 5)
+__global__ void __launch_bounds__(RED_THREADS, 2)
 k_cg32_spmv_tma(Grid g, Tiles tw, const __grid_constant__ TmaMaps32 maps, int pin_sel, float *__restrict__ p_out,
                 float *__restrict__ q, double *partials, unsigned int *ticket, CgScal *sc, int *fault)
 {
@@ -596,22 +598,26 @@ k_cg32_spmv_tma(Grid g, Tiles tw, const __grid_constant__ TmaMaps32 maps, int pi
     const uint32_t tx_bytes = (first ? 2 : 3) * TMA_BOX_BYTES + TMA_OWN_BYTES;
     const int tx = threadIdx.x % 32, ty = threadIdx.x / 32;
     const bool poller = threadIdx.x < 32;
-    const int idx = (ty + 1) * TMA_BX + 2 * tx + TMA_X0;   // even: the pair is one float2
-    const int oidx = ty * TMA_TX + 2 * tx;                 // the pair in the own-cell box
-    int hidx = -1;                       // the x/y halo cell this thread converts
-    if (threadIdx.x < TMA_HALO) {
-        const int h = threadIdx.x;
-        int hx, hy;
-        if (h < TY) { hx = -1; hy = h; }
-        else if (h < 2 * TY) { hx = TMA_TX; hy = h - TY; }
-        else if (h < 2 * TY + TMA_TX) { hx = h - 2 * TY; hy = -1; }
-        else { hx = h - 2 * TY - TMA_TX; hy = TY; }
+    const int idx = (ty + 1) * TMA_BX + 4 * tx + TMA_X0;   // a multiple of 4: the quad is one float4
+    const int oidx = ty * TMA_TX + 4 * tx;                 // the quad in the own-cell box
+    // halo this thread converts: threads 0-63 a quad of the rows below and
+    // above the tile, threads 64-79 one cell left or right of it
+    int hidx4 = -1, hidx = -1;
+    if (threadIdx.x < 64) {
+        const int hy = threadIdx.x < 32 ? -1 : TY;
+        hidx4 = (hy + 1) * TMA_BX + 4 * (threadIdx.x % 32) + TMA_X0;
+    } else if (threadIdx.x < 64 + 2 * TY) {
+        const int h = threadIdx.x - 64;
+        const int hx = h < TY ? -1 : TMA_TX, hy = h % TY;
         hidx = (hy + 1) * TMA_BX + hx + TMA_X0;
     }
     const float wx = g.w32[0] * 0.5f, wy = g.w32[1] * 0.5f, wz = g.w32[2] * 0.5f;
     uint32_t phase = 0, pending = 0;   // per stage: parity of its next completion; copy in flight
     float acc = 0.0f;
-    auto ld2 = [](const float *a, int e) { return *reinterpret_cast<const float2 *>(a + e); };
+    auto ld4 = [](const float *a, int e) { return *reinterpret_cast<const float4 *>(a + e); };
+    auto fma4 = [](float b, float4 o, float4 z) {
+        return make_float4(fmaf(b, o.x, z.x), fmaf(b, o.y, z.y), fmaf(b, o.z, z.z), fmaf(b, o.w, z.w));
+    };
     // face term of cell P towards cell N.  Inactive cells carry K = NaN and
     // the K boxes read NaN outside the grid (their p reads 0), so
     // max(w (K_P + K_N), 0) is the face coefficient where both cells are
@@ -621,7 +627,7 @@ k_cg32_spmv_tma(Grid g, Tiles tw, const __grid_constant__ TmaMaps32 maps, int pi
     };
     for (long long item = blockIdx.x; item < tw.items && !s_timeout; item += gridDim.x) {
         const TileItem it = tile_item(g, tw, item);
-        const int i = it.i0 + 2 * tx, j = it.j0 + ty;      // first cell of the pair (nx is even)
+        const int i = it.i0 + 4 * tx, j = it.j0 + ty;      // first cell of the quad (nx is a multiple of 4)
         const bool inside = i < g.nx && j < g.ny;
         // plane kk = it.k0 - 1 + L goes to stage L % TMA_STAGES (stage
         // indices advance incrementally); planes outside the grid are neither
@@ -658,8 +664,8 @@ k_cg32_spmv_tma(Grid g, Tiles tw, const __grid_constant__ TmaMaps32 maps, int pi
             if (!first && present(kk)) {
                 float *pz = sbuf[st][0];
                 const float *po = sbuf[st][1];
-                const float2 z2 = ld2(pz, idx), o2 = ld2(po, idx);
-                *reinterpret_cast<float2 *>(pz + idx) = make_float2(fmaf(beta, o2.x, z2.x), fmaf(beta, o2.y, z2.y));
+                *reinterpret_cast<float4 *>(pz + idx) = fma4(beta, ld4(po, idx), ld4(pz, idx));
+                if (hidx4 >= 0) *reinterpret_cast<float4 *>(pz + hidx4) = fma4(beta, ld4(po, hidx4), ld4(pz, hidx4));
                 if (hidx >= 0) pz[hidx] = fmaf(beta, po[hidx], pz[hidx]);
                 fence_proxy_async_smem();   // the stage is refilled by tensor copies later
             }
@@ -673,12 +679,12 @@ k_cg32_spmv_tma(Grid g, Tiles tw, const __grid_constant__ TmaMaps32 maps, int pi
         take(it.k0, 1);
         // the bottom-face term of plane k0 (from plane k0 - 1, staged for
         // this only); later planes receive it from the plane below
-        float2 carry = make_float2(0.0f, 0.0f);
+        float4 carry = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
         if (inside && it.k0 > 0) {
-            const float2 kc = ld2(sbuf[1][2], idx), pc = ld2(sbuf[1][0], idx);
-            const float2 kb = ld2(sbuf[0][2], idx), pb = ld2(sbuf[0][0], idx);
-            carry.x = face(kc.x, pc.x, kb.x, pb.x, wz);
-            carry.y = face(kc.y, pc.y, kb.y, pb.y, wz);
+            const float4 kc = ld4(sbuf[1][2], idx), pc = ld4(sbuf[1][0], idx);
+            const float4 kb = ld4(sbuf[0][2], idx), pb = ld4(sbuf[0][0], idx);
+            carry = make_float4(face(kc.x, pc.x, kb.x, pb.x, wz), face(kc.y, pc.y, kb.y, pb.y, wz),
+                                face(kc.z, pc.z, kb.z, pb.z, wz), face(kc.w, pc.w, kb.w, pb.w, wz));
         }
         // stages of planes k and k + 1, and the one plane k - 1 held (refilled with plane k + TMA_STAGES - 1)
         int s_c = 1, s_p = 2 % TMA_STAGES, s_i = 0;
@@ -691,31 +697,37 @@ k_cg32_spmv_tma(Grid g, Tiles tw, const __grid_constant__ TmaMaps32 maps, int pi
             take(k + 1, s_p);
             if (inside) {
                 const float *P0 = sbuf[s_c][0], *K0 = sbuf[s_c][2];
-                const float2 kc = ld2(K0, idx), pc = ld2(P0, idx), cb = ld2(cbuf[s_c], oidx);
-                const float2 kym = ld2(K0, idx - TMA_BX), pym = ld2(P0, idx - TMA_BX);
-                const float2 kyp = ld2(K0, idx + TMA_BX), pyp = ld2(P0, idx + TMA_BX);
-                const float2 kzp = ld2(sbuf[s_p][2], idx), pzp = ld2(sbuf[s_p][0], idx);
+                const float4 kc = ld4(K0, idx), pc = ld4(P0, idx), cb = ld4(cbuf[s_c], oidx);
+                const float4 kym = ld4(K0, idx - TMA_BX), pym = ld4(P0, idx - TMA_BX);
+                const float4 kyp = ld4(K0, idx + TMA_BX), pyp = ld4(P0, idx + TMA_BX);
                 // (A p)_P = cb_P p_P + sum_f w_f (K_P + K_N)/2 (p_P - p_N); the
                 // plane above the grid's top is not staged, so its faces are skipped
-                const float t01 = face(kc.x, pc.x, kc.y, pc.y, wx);                  // between the pair
-                float tzx = 0.0f, tzy = 0.0f;                                        // top faces
+                const float t01 = face(kc.x, pc.x, kc.y, pc.y, wx);   // faces inside the quad
+                const float t12 = face(kc.y, pc.y, kc.z, pc.z, wx);
+                const float t23 = face(kc.z, pc.z, kc.w, pc.w, wx);
+                float4 tz = make_float4(0.0f, 0.0f, 0.0f, 0.0f);       // top faces
                 if (k < g.nz - 1) {
-                    tzx = face(kc.x, pc.x, kzp.x, pzp.x, wz);
-                    tzy = face(kc.y, pc.y, kzp.y, pzp.y, wz);
+                    const float4 kzp = ld4(sbuf[s_p][2], idx), pzp = ld4(sbuf[s_p][0], idx);
+                    tz = make_float4(face(kc.x, pc.x, kzp.x, pzp.x, wz), face(kc.y, pc.y, kzp.y, pzp.y, wz),
+                                     face(kc.z, pc.z, kzp.z, pzp.z, wz), face(kc.w, pc.w, kzp.w, pzp.w, wz));
                 }
-                float q0 = fmaf(cb.x, pc.x, carry.x) + t01 + tzx;
-                float q1 = fmaf(cb.y, pc.y, carry.y) - t01 + tzy;
+                float q0 = fmaf(cb.x, pc.x, carry.x) + t01 + tz.x;
+                float q1 = fmaf(cb.y, pc.y, carry.y) - t01 + t12 + tz.y;
+                float q2 = fmaf(cb.z, pc.z, carry.z) - t12 + t23 + tz.z;
+                float q3 = fmaf(cb.w, pc.w, carry.w) - t23 + tz.w;
                 q0 += face(kc.x, pc.x, K0[idx - 1], P0[idx - 1], wx);
-                q1 += face(kc.y, pc.y, K0[idx + 2], P0[idx + 2], wx);
+                q3 += face(kc.w, pc.w, K0[idx + 4], P0[idx + 4], wx);
                 q0 += face(kc.x, pc.x, kym.x, pym.x, wy) + face(kc.x, pc.x, kyp.x, pyp.x, wy);
                 q1 += face(kc.y, pc.y, kym.y, pym.y, wy) + face(kc.y, pc.y, kyp.y, pyp.y, wy);
-                carry = make_float2(-tzx, -tzy);
-                const bool a0 = kc.x >= 0.0f, a1 = kc.y >= 0.0f;
-                const float2 po = make_float2(a0 ? pc.x : 0.0f, a1 ? pc.y : 0.0f);
-                const float2 qo = make_float2(a0 ? q0 : 0.0f, a1 ? q1 : 0.0f);
-                acc = fmaf(po.x, qo.x, fmaf(po.y, qo.y, acc));
-                *reinterpret_cast<float2 *>(p_out + c) = po;
-                *reinterpret_cast<float2 *>(q + c) = qo;
+                q2 += face(kc.z, pc.z, kym.z, pym.z, wy) + face(kc.z, pc.z, kyp.z, pyp.z, wy);
+                q3 += face(kc.w, pc.w, kym.w, pym.w, wy) + face(kc.w, pc.w, kyp.w, pyp.w, wy);
+                carry = make_float4(-tz.x, -tz.y, -tz.z, -tz.w);
+                const bool a0 = kc.x >= 0.0f, a1 = kc.y >= 0.0f, a2 = kc.z >= 0.0f, a3 = kc.w >= 0.0f;
+                const float4 po = make_float4(a0 ? pc.x : 0.0f, a1 ? pc.y : 0.0f, a2 ? pc.z : 0.0f, a3 ? pc.w : 0.0f);
+                const float4 qo = make_float4(a0 ? q0 : 0.0f, a1 ? q1 : 0.0f, a2 ? q2 : 0.0f, a3 ? q3 : 0.0f);
+                acc = fmaf(po.x, qo.x, fmaf(po.y, qo.y, fmaf(po.z, qo.z, fmaf(po.w, qo.w, acc))));
+                *reinterpret_cast<float4 *>(p_out + c) = po;
+                *reinterpret_cast<float4 *>(q + c) = qo;
             }
             s_c = s_p;
             s_p = next(s_p);

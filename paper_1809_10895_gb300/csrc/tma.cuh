@@ -9,17 +9,17 @@
 
 namespace rf {
 
-// Box of one staged plane: 72 x 10 cells around a 64 x 8 tile.  The box
+// Box of one staged plane: 136 x 10 cells around a 128 x 8 tile.  The box
 // starts 4 cells before the tile in x so that its x coordinate is a multiple
 // of 4 floats (16 bytes), as every tensor copy requires; the -x halo cell is
 // box column 3, the tile's first cell column 4.  Rows: y from j0 - 1.
-constexpr int TMA_TX = 64;
+constexpr int TMA_TX = 128;
 constexpr int TMA_BX = TMA_TX + 8, TMA_BY = 10, TMA_X0 = 4;
-constexpr int TMA_BOX_BYTES = TMA_BX * TMA_BY * 4;       // 2880
+constexpr int TMA_BOX_BYTES = TMA_BX * TMA_BY * 4;       // 5440
 constexpr int TMA_SLOT_BYTES = (TMA_BOX_BYTES + 127) / 128 * 128;
-// Box of an array read at the tile's own cells only (cb): 64 x 8, no halo.
+// Box of an array read at the tile's own cells only (cb): 128 x 8, no halo.
 constexpr int TMA_OWN_BY = 8;
-constexpr int TMA_OWN_BYTES = TMA_TX * TMA_OWN_BY * 4;   // 2048
+constexpr int TMA_OWN_BYTES = TMA_TX * TMA_OWN_BY * 4;   // 4096
 
 // Tensor maps of the FP32 inner-solve arrays (one 3-D map per array, dims
 // nx, ny, nz), with the device pointers they describe.

@@ -333,8 +333,8 @@ def test_full_size_box_first_steps(precision, tol):
 
 
 # Grids that take the mixed path's TMA-staged FP32 stencil (nx a multiple of
-# 4) across several 64-cell x-tiles with a ragged last tile, all active and
-# masked, and one that takes the plain-tile FP32 stencil (nx odd).
+# 4) across 128-cell x-tiles with a ragged last tile, all active and masked,
+# and one that takes the plain-tile FP32 stencil (nx odd).
 def _box_multitile():
     return W.heterogeneous_box(136, 20, 12, d=0.25, seed=21, water_table_depth=2.0, rain=4e-6, rain_hours=1.0,
                                t_end=2 * 3600.0)
@@ -343,6 +343,12 @@ def _box_multitile():
 def _watershed_multitile():
     # seed 0 rains from hour 11 (3.4 mm/h, 11.4 mm/h from hour 17)
     return W.watershed(132, 24, 16, dx=10.0, dz=0.5, seed=0, hours=24, tol_cg=1e-12)
+
+
+def _box_wide():
+    # three x-tiles of the TMA stencil, the last one 8 cells wide
+    return W.heterogeneous_box(264, 12, 6, d=0.25, seed=23, water_table_depth=1.0, rain=4e-6, rain_hours=1.0,
+                               t_end=3600.0)
 
 
 def _box_odd():
@@ -377,8 +383,8 @@ def _inner_operator_bound(case, o, hk, hn, dt, p64, act):
     return 16 * u * mags + chord_tol(case, hk, hn, dt, act, ref["c"]) * np.abs(p64[act])
 
 
-@pytest.mark.parametrize("make", [_box_multitile, _watershed_multitile, _box_odd],
-                         ids=["box136x20x12", "watershed132x24x16", "box135x21x11"])
+@pytest.mark.parametrize("make", [_box_multitile, _watershed_multitile, _box_wide, _box_odd],
+                         ids=["box136x20x12", "watershed132x24x16", "box264x12x6", "box135x21x11"])
 def test_inner_fp32_operator_matches_oracle(make):
     case = make()
     o = oracle_from_case(case)
