@@ -60,10 +60,17 @@ def test_watershed_full_size(precond):
     assert np.all(np.abs(bg - br) <= tol_b)
 
 
-def test_ensemble_full_size():
+@pytest.mark.parametrize("precond,tiling", [("jacobi", None), ("zline", (8, 256))])
+def test_ensemble_full_size(precond, tiling):
+    """The 256-instance workload (the bench's ensemble: vertical-line
+    preconditioner on 8-CTA clusters of 256 threads) over its first minute:
+    every instance's balance closes; the two smallest and two largest
+    instances match the oracle."""
     cases = W.ensemble(256, seed=0)
     window = 60.0
-    e = rf.Ensemble.from_cases(cases, precision="mixed")
+    e = rf.Ensemble.from_cases(cases, precision="mixed", precond=precond)
+    if tiling:
+        e.set_tiling(*tiling)
     e.run(window)
     stats = [e.get(i, want_h=False)[1] for i in range(len(cases))]
     for st in stats:
