@@ -71,6 +71,8 @@ def parse():
     ap.add_argument("--no-warmstart", action="store_true", help="skip the learned warm-start leg")
     ap.add_argument("--no-configs", action="store_true", help="skip the column and box legs")
     ap.add_argument("--no-stiff", action="store_true", help="skip the stiff-solve preconditioner comparison")
+    ap.add_argument("--slope", action="store_true",
+                    help="add the tilted slope's 10 days (36 M cells, the paper's strong-scaling case; about 2 min)")
     ap.add_argument("--ws-train-size", type=int, default=128, help="nx = ny of the training box (nz = 64)")
     ap.add_argument("--ws-eval-size", type=int, default=256, help="nx = ny of the held-out boxes (nz = 64)")
     ap.add_argument("--ws-eval-seeds", type=int, default=1, help="held-out seeds evaluated")
@@ -545,6 +547,9 @@ def native(args):
     stiff = None
     if not args.no_stiff:
         stiff = stiff_leg(rf, W)
+    slope = None
+    if args.slope:
+        slope = slope_leg(rf, W)
 
     if rank == 0:
         line = {
@@ -574,6 +579,7 @@ def native(args):
             "warmstart": wsl,
             "other_configs": cfg,
             "stiff_solve": stiff,
+            "tilted_slope": slope,
         }
         if not args.no_baseline:
             # host-side legs: an error is recorded in the line, never lost with it
@@ -617,6 +623,35 @@ def ensemble_leg(args, rank, rf, W, barrier):
            "max_closure_rel": max(st["closure_abs"] / max(st["storage0"] + st["inflow_cum"] + st["outflow_cum"], 1e-300)
                                   for st in stats)}
     e.close()
+    return out
+
+
+def slope_leg(rf, W):
+    """Time to solution of the tilted slope (850 x 850 x 50 cells of 2 x 2 x
+    0.2 m, 10 days, Picard 1 mm, dt 0.1 s .. 30 min), FP64 and mixed paths,
+    event-timed from t = 0 (after one untimed warm-up step and a reset)."""
+    import torch
+    case = W.tilted_slope()
+    out = {"workload": case.name, "cells": case.N, "simulated_s": case.t_end}
+    for prec in ("fp64", "mixed"):
+        try:
+            s = rf.Solver.from_case(case, precision=prec)
+            s.step()
+            s.set_state(case.h0, 0.0)
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(s.stream)
+            steps = s.run(case.t_end)
+            b.record(s.stream)
+            torch.cuda.synchronize()
+            ms = a.elapsed_time(b)
+            mb = s.mass_balance()
+            out[prec] = {"time_to_solution_s": ms / 1e3, "steps": len(steps),
+                         "picard": sum(x.picard for x in steps), "cg_iters": sum(x.cg for x in steps),
+                         "rejected": sum(x.rejected for x in steps), "closure_rel": mb["closure_rel"],
+                         "value": len(steps) * case.N / (ms / 1e3), "unit": UNIT}
+            s.close()
+        except Exception as ex:
+            out[prec] = {"error": f"{type(ex).__name__}: {ex}"[:300]}
     return out
 
 
