@@ -254,13 +254,53 @@ k_cg64_spmv(Grid g, Tiles tw, const uint8_t *__restrict__ flags, const double *_
             const long long cm = i + (long long)g.nx * j + g.sxy * (it.k0 - 1);
             tzm = (flags[cm] & FLAG_ACTIVE) ? Tz[cm] : 0.0;
         }
+        // the plane's coefficients and halo, loaded a plane ahead so that
+        // their round trip overlaps the previous plane's work (the kernel is
+        // latency-bound: few FP64 instructions a cell, one barrier a plane)
+        struct Pl {
+            bool act, hact;
+            double dg, txp, typ, tzp, hp, htx, hty;
+        };
+        auto load = [&](int k, long long c) {
+            Pl l;
+            l.act = inside && (flags[c] & FLAG_ACTIVE);
+            l.dg = l.txp = l.typ = l.tzp = 0.0;
+            if (l.act) {
+                l.dg = diag[c];
+                l.txp = Tx[c];
+                l.typ = Ty[c];
+                l.tzp = Tz[c];
+            }
+            l.hact = false;
+            l.hp = l.htx = l.hty = 0.0;
+            if (threadIdx.x < HALO) {
+                const int ii = it.i0 + hx, jj = it.j0 + hy;
+                const bool in = ii >= 0 && ii < g.nx && jj >= 0 && jj < g.ny;
+                const long long hc = ii + (long long)g.nx * jj + g.sxy * k;
+                l.hact = in && (flags[hc] & FLAG_ACTIVE);
+                if (l.hact) {
+                    l.hp = val(hc);
+                    if (hx == -1) l.htx = Tx[hc];
+                    if (hy == -1) l.hty = Ty[hc];
+                }
+            }
+            return l;
+        };
+        Pl nxt = load(it.k0, i + (long long)g.nx * j + g.sxy * it.k0);
         for (int k = it.k0; k < it.k1; k++) {
             const int buf = k & 1;
             const long long c = i + (long long)g.nx * j + g.sxy * k;
-            bool act;
-            double dg, txp, typ, tzp;
-            stage64(g, it, k, buf, tx, ty, hx, hy, inside, c, flags, Tx, Ty, Tz, diag, pc, val, sP, sF, act, dg,
-                    txp, typ, tzp);
+            const Pl cur = nxt;
+            if (k + 1 < it.k1) nxt = load(k + 1, c + g.sxy);
+            sP[buf][ty + 1][tx + 1] = pc;
+            sF.ty[buf][ty + 1][tx] = cur.typ;
+            if (threadIdx.x < HALO) {
+                sP[buf][hy + 1][hx + 1] = cur.hp;
+                if (hx == -1) sF.tx[buf][hy] = cur.htx;
+                if (hy == -1) sF.ty[buf][0][hx] = cur.hty;
+            }
+            const bool act = cur.act;
+            const double dg = cur.dg, txp = cur.txp, typ = cur.typ, tzp = cur.tzp;
             const double pn = pval(i, j, k + 1);
             const double txm_lane = __shfl_up_sync(0xffffffffu, txp, 1);
             __syncthreads();
